@@ -1,0 +1,169 @@
+"""FP64 CPU oracle for first-hit LiDAR ray casting (paper Sec. IV-C).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, ``__graft_entry__.smoke()`` and
+the CPU-baseline leg of ``bench.py``; never by the library it checks.  It
+shares no code with ``paper_2509_17390_gb300``.
+
+The C++ source (``oracle.cpp``) is compiled on first use (or by
+``build()``) with ``-ffp-contract=off`` into ``oracle/_build/liboracle.so``.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.cpp")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+FLAG_EDGE, FLAG_TIE, FLAG_RANGE = 1, 2, 4
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so (g++, FP64, no FMA contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+               "-shared", "-pthread", _SRC, "-o", tmp]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_LIB_PATH)
+            P, I64, I32, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+            L.orc_version.restype = I32
+            L.orc_sensor_dirs.argtypes = [P, P, I64, P]
+            L.orc_world_rays.argtypes = [P, I64, P, I64, P, P]
+            L.orc_scene_create.argtypes = [P, I64, P, I64, I32]
+            L.orc_scene_create.restype = P
+            L.orc_scene_free.argtypes = [P]
+            L.orc_scene_depth.argtypes = [P]
+            L.orc_scene_depth.restype = I32
+            L.orc_cast.argtypes = [P, P, P, I64, D, I32, P, P, P]
+            L.orc_validate.argtypes = [P, P, P, I64, D, P, P, I32, P]
+            L.orc_tri_test.argtypes = [P, P, P, P, P, P]
+            L.orc_tri_test.restype = I32
+            _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def sensor_dirs(elev: np.ndarray, azim: np.ndarray) -> np.ndarray:
+    """float32 [n,3] sensor-frame unit directions from (elev, azim)."""
+    el = np.ascontiguousarray(elev, np.float32)
+    az = np.ascontiguousarray(azim, np.float32)
+    out = np.empty((len(el), 3), np.float32)
+    lib().orc_sensor_dirs(_ptr(el), _ptr(az), len(el), _ptr(out))
+    return out
+
+
+def world_rays(dirs: np.ndarray, poses: np.ndarray):
+    """float32 world rays (o, d), each [n_env * n_rays, 3], ray e*n_rays+j."""
+    dirs = np.ascontiguousarray(dirs, np.float32).reshape(-1, 3)
+    poses = np.ascontiguousarray(poses, np.float32).reshape(-1, 12)
+    n = len(dirs) * len(poses)
+    o = np.empty((n, 3), np.float32)
+    d = np.empty((n, 3), np.float32)
+    lib().orc_world_rays(_ptr(dirs), len(dirs), _ptr(poses), len(poses), _ptr(o), _ptr(d))
+    return o, d
+
+
+def tri_test(o, d, v0, v1, v2):
+    """FP64 signed-volume test of one ray against one triangle: t or None."""
+    args = [np.ascontiguousarray(x, np.float64) for x in (o, d, v0, v1, v2)]
+    t = np.zeros(1, np.float64)
+    hit = lib().orc_tri_test(*[_ptr(a) for a in args], _ptr(t))
+    return float(t[0]) if hit else None
+
+
+class Scene:
+    """Oracle scene: brute force over all triangles (bvh=False) or a
+    median-split FP64 BVH (bvh=True); both give identical answers."""
+
+    def __init__(self, verts: np.ndarray, tris: np.ndarray, bvh: bool = True):
+        self.verts = np.ascontiguousarray(verts, np.float32).reshape(-1, 3)
+        self.tris = np.ascontiguousarray(tris, np.int32).reshape(-1, 3)
+        self._h = lib().orc_scene_create(_ptr(self.verts), len(self.verts), _ptr(self.tris),
+                                         len(self.tris), 1 if bvh else 0)
+        if not self._h:
+            raise ValueError("invalid scene (vertex id out of range or non-finite vertex)")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().orc_scene_free(h)
+            self._h = None
+
+    @property
+    def depth(self) -> int:
+        return lib().orc_scene_depth(self._h)
+
+    def cast(self, o: np.ndarray, d: np.ndarray, max_range: float, flags: bool = True,
+             nthreads: int = 0):
+        """Nearest hit (eq. t_j*): (range f64, id i32, flags u8 or None)."""
+        o = np.ascontiguousarray(o, np.float32).reshape(-1, 3)
+        d = np.ascontiguousarray(d, np.float32).reshape(-1, 3)
+        n = len(o)
+        t = np.empty(n, np.float64)
+        ids = np.empty(n, np.int32)
+        fl = np.empty(n, np.uint8) if flags else None
+        lib().orc_cast(self._h, _ptr(o), _ptr(d), n, float(max_range), int(nthreads), _ptr(t),
+                       _ptr(ids), _ptr(fl) if flags else None)
+        return t, ids, fl
+
+    def validate(self, o, d, max_range, rng, ids, nthreads: int = 0) -> np.ndarray:
+        """Per ray: is (range, id) an acceptable FP32 answer?  (bool array)"""
+        o = np.ascontiguousarray(o, np.float32).reshape(-1, 3)
+        d = np.ascontiguousarray(d, np.float32).reshape(-1, 3)
+        r = np.ascontiguousarray(rng, np.float32)
+        i = np.ascontiguousarray(ids, np.int32)
+        ok = np.empty(len(o), np.uint8)
+        lib().orc_validate(self._h, _ptr(o), _ptr(d), len(o), float(max_range), _ptr(r), _ptr(i),
+                           int(nthreads), _ptr(ok))
+        return ok.astype(bool)
+
+
+def compare(range_gpu, id_gpu, range_orc, id_orc, flags, max_range):
+    """Element-wise parity under the tolerance contract.
+
+    Unflagged rays: hit/miss and triangle id equal, and
+    |range_gpu - range_orc| <= 1e-4 + 1e-6 * range_orc (a miss must report
+    max_range exactly).  TIE-flagged rays: range checked, id exempt.
+    EDGE/RANGE-flagged rays: exempt here (check them with Scene.validate).
+    Returns (bad_mask, checked_mask).
+    """
+    rg = np.asarray(range_gpu, np.float64)
+    ig = np.asarray(id_gpu)
+    ro = np.asarray(range_orc, np.float64)
+    io = np.asarray(id_orc)
+    fl = np.asarray(flags)
+    hard = (fl & (FLAG_EDGE | FLAG_RANGE)) != 0
+    tie = (fl & FLAG_TIE) != 0
+    checked = ~hard
+    tolr = 1e-4 + 1e-6 * np.abs(ro)
+    bad = np.zeros(len(rg), bool)
+    hit_o = io >= 0
+    hit_g = ig >= 0
+    bad |= checked & (hit_o != hit_g)
+    bad |= checked & ~tie & (io != ig)
+    bad |= checked & hit_o & hit_g & (np.abs(rg - ro) > tolr)
+    bad |= checked & ~hit_o & ~hit_g & (rg != np.float32(max_range))
+    return bad, checked
