@@ -1,0 +1,404 @@
+#!/usr/bin/env python3
+"""Benchmark: batched LiDAR ray casting, 4096 environments x 1M triangles.
+
+Workload (one "step" = one simulation step of every environment): the
+1,000,300-triangle indoor mesh, 4,096 environments each at its own pose of a
+seeded SE(3) random walk, 16 x 360 rays per environment = 23,592,960 rays per
+step, max range 120 m.  A step copies that step's poses into the
+device-resident pose state and replays one CUDA graph (work-queue table copy +
+one persistent kernel).  L2 is flushed (256 MiB write) between timed steps.
+
+Printed JSON line (rank 0):
+  value            Grays/s of the batched persistent kernel, inputs in HBM
+  e2e              same metric through fgl_cast_batched_host with pinned host
+                   buffers (poses H2D and ranges+ids D2H inside the timed region)
+  per_env_launch   the plain form: one fgl_cast launch per environment
+  roofline         algorithmic node+triangle+I/O bytes per launch / kernel time
+                   against the measured HBM copy bandwidth
+  cpu_baseline     the FP64 oracle on the host cores over a bounded sample
+
+--impl reference times the FP64 CPU oracle (the only reference this method
+has) on the same workload and metric.  With --gpus N under torchrun every
+rank runs its own replica (the path needs no exchange between GPUs).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Grays/s @4096 envs x 1M tris; p50/p99 scan latency, served vs per-env launch"
+UNIT = "Grays/s"
+WORKLOAD = ("batched_walk: 4096 envs x (16 beams -15..+15 deg x 360 az) = 23,592,960 rays/step "
+            "on the 1,000,300-tri seeded indoor mesh (20x15x4 m room, 2000 icospheres, 834 "
+            "boxes), per-env seeded SE(3) random walk 0.1 m / 2 deg per step, max range 120 m")
+KERNEL_SOURCES = ["paper_2509_17390_gb300/csrc/trace.cuh", "paper_2509_17390_gb300/csrc/kernels.cu"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, p), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def read_peaks():
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def read_traffic(name: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources."""
+    try:
+        d = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        e = d.get(name)
+        if e and e.get("kernel_hash") == kernel_hash():
+            return float(e["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = max(smax, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(n_gpus: int):
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return ws, rank, local
+
+
+def barrier_max(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline / reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(w, step_poses, n_env_sample: int, seed: int = 0, osc=None):
+    import oracle
+    if osc is None:
+        osc = oracle.Scene(w.verts, w.tris, bvh=True)
+    rng = np.random.default_rng(seed)
+    envs = np.sort(rng.choice(step_poses.shape[0], n_env_sample, replace=False))
+    dirs = oracle.sensor_dirs(w.sensor.elev, w.sensor.azim)
+    o, d = oracle.world_rays(dirs, step_poses[envs])
+    return osc, o, d, envs
+
+
+def time_oracle(osc, o, d, max_range):
+    t0 = time.perf_counter()
+    osc.cast(o, d, max_range, flags=False)
+    return time.perf_counter() - t0
+
+
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n-env", type=int, default=4096)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-per-env", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--packet", type=int, default=0)
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--sdepth", type=int, default=0)
+    ap.add_argument("--refill", type=int, default=0)
+    ap.add_argument("--postpone", type=int, default=0)
+    ap.add_argument("--width", type=int, default=8)
+    ap.add_argument("--tile", type=str, default="")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    from synth import workloads
+
+    n_steps = args.warmup + args.steps
+    if args.impl == "reference":
+        return run_reference(args, n_steps)
+
+    import torch
+    import paper_2509_17390_gb300 as fgl
+
+    ws, rank, local = dist_setup(args.gpus)
+    w = workloads.batched_walk(2, n_env=args.n_env, n_steps=min(n_steps, 100))
+    n_env = args.n_env
+    walk = w.poses                                    # [S, n_env, 3, 4]
+    S = walk.shape[0]
+    scene = fgl.Scene(w.verts, w.tris, width=args.width)
+    tr, tc = (int(x) for x in args.tile.split("x")) if args.tile else (0, 0)
+    sensor = fgl.Sensor.from_table(w.sensor, tr, tc)
+    n_rays = n_env * sensor.n_rays
+    dev = torch.device("cuda", torch.cuda.current_device())
+    walk_d = torch.from_numpy(walk).to(dev)          # all steps' poses resident
+    pose_state = torch.empty((n_env, 3, 4), dtype=torch.float32, device=dev)
+    out_r = torch.empty(n_rays, dtype=torch.float32, device=dev)
+    out_i = torch.empty(n_rays, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    opts = fgl.BatchOpts(packet_rays=args.packet, block_threads=args.block, stack_smem=args.sdepth,
+                         refill_min=args.refill, postpone_pct=args.postpone, use_graph=1)
+    items = [(scene, sensor, pose_state, w.max_range, out_r, out_i)]
+    arr = fgl.make_items(items)
+
+    def step(s):
+        with torch.cuda.stream(stream):
+            pose_state.copy_(walk_d[s % S])
+        fgl.cast_batched(items, opts, stream=stream, arr=arr)
+
+    # warm-up (graph capture happens on the first call)
+    for s in range(args.warmup):
+        step(s)
+    fgl.sync(stream)
+
+    # work counters for the roofline (one step, outside the timed region)
+    copts = fgl.BatchOpts(packet_rays=args.packet, block_threads=args.block, stack_smem=args.sdepth,
+                          refill_min=args.refill, postpone_pct=args.postpone, count_work=1)
+    fgl.work_counters()
+    with torch.cuda.stream(stream):
+        pose_state.copy_(walk_d[args.warmup % S])
+    fgl.cast_batched(items, copts, stream=stream)
+    fgl.sync(stream)
+    c_rays, c_nodes, c_tris = fgl.work_counters()
+    st = scene.stats()
+    b_ray = (c_nodes * st["node_stride"] + c_tris * 48) / max(1, c_rays) + 16 + 8 + 48.0 / sensor.n_rays
+
+    # timed region: per step flush L2 (untimed), then events around the step
+    barrier(ws)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(k & 0xFF)
+                ev[k][0].record(stream)
+            step(args.warmup + k)
+            with torch.cuda.stream(stream):
+                ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    fgl.sync(stream)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = barrier_max(sum(step_ms) / 1e3, ws)
+    ms = total_s * 1e3 / args.steps
+    value = ws * n_rays * args.steps / total_s / 1e9
+    clocks = clk.summary()
+
+    # kernel-only time for the roofline: graph = 1 tiny memcpy + 1 kernel
+    kern_ms = float(np.mean(step_ms))
+    peak, peak_kind = read_peaks()
+    achieved = b_ray * n_rays / (kern_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": read_traffic("k_persistent"),
+                "peak_source": peak_kind, "bytes_per_ray": round(b_ray, 1),
+                "node_visits_per_ray": round(c_nodes / max(1, c_rays), 2),
+                "tri_tests_per_ray": round(c_tris / max(1, c_rays), 2)}
+
+    # per-env launch (plain form): one fgl_cast per environment
+    per_env = None
+    if not args.no_per_env:
+        L = fgl.lib()
+        sh = stream.cuda_stream
+        base_p = pose_state.data_ptr()
+        base_r, base_i = out_r.data_ptr(), out_i.data_ptr()
+        nr = sensor.n_rays
+        reps = 2
+        torch.cuda.synchronize()
+        tot = 0.0
+        for k in range(reps):
+            with torch.cuda.stream(stream):
+                pose_state.copy_(walk_d[(args.warmup + k) % S])
+                flush.fill_(k & 0xFF)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for e in range(n_env):
+                st_ = L.fgl_cast(scene.handle, sensor.handle, base_p + 48 * e, 1, w.max_range,
+                                 base_r + 4 * nr * e, base_i + 4 * nr * e, sh)
+                if st_:
+                    raise RuntimeError(L.fgl_last_error())
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        fgl.sync(stream)
+        pms = tot / reps
+        per_env = {"value": round(n_rays / (pms / 1e3) / 1e9, 4), "unit": UNIT,
+                   "ms_per_step": round(pms, 3), "launches_per_step": n_env}
+
+    # end to end through the host-buffer entry point
+    e2e = None
+    if not args.no_e2e:
+        hp = torch.empty((n_env, 3, 4), dtype=torch.float32).pin_memory()
+        hr = torch.empty(n_rays, dtype=torch.float32).pin_memory()
+        hi = torch.empty(n_rays, dtype=torch.int32).pin_memory()
+        hitems = [(scene, sensor, hp, w.max_range, hr, hi)]
+        for s in range(2):
+            hp.copy_(torch.from_numpy(walk[s % S]))
+            fgl.cast_batched_host(hitems, opts, stream=stream)
+        ksteps = max(3, min(args.steps, 10))
+        tot = 0.0
+        for k in range(ksteps):
+            hp.copy_(torch.from_numpy(walk[(args.warmup + k) % S]))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fgl.cast_batched_host(hitems, opts, stream=stream)
+            tot += time.perf_counter() - t0
+        tot = barrier_max(tot, ws)
+        e2e = {"value": round(ws * n_rays * ksteps / tot / 1e9, 4), "unit": UNIT,
+               "h2d_bytes_per_step": n_env * 48, "d2h_bytes_per_step": n_rays * 8,
+               "ms_per_step": round(tot * 1e3 / ksteps, 3)}
+
+    # CPU oracle on a bounded sample (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        osc, o, d, envs = oracle_sample(w, walk[args.warmup % S], 256)
+        t = time_oracle(osc, o, d, w.max_range)
+        cpu = {"value": round(len(o) / t / 1e9, 6), "unit": UNIT, "cores": os.cpu_count(),
+               "kind": "oracle",
+               "sample": f"{len(envs)} of {n_env} envs x {sensor.n_rays} rays (one step), FP64 "
+                         f"median-split BVH, no ambiguity flags, {t:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "parallelism": f"replicas x{ws}", "l2": "flushed "
+                       "between timed steps (256 MiB write)", "bvh_width": st["width"],
+                       "opts": opts.as_dict(), "scene_tris": st["n_tris"],
+                       "rays_per_step": n_rays, "frames_per_s": round(ws * n_env / (ms / 1e3), 1)},
+            "gpu_launches": args.steps, "roofline": roofline, "e2e": e2e,
+            "per_env_launch": per_env, "served": None, "cpu_baseline": cpu, "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_reference(args, n_steps):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from synth import workloads
+    w = workloads.batched_walk(2, n_env=args.n_env, n_steps=min(n_steps, 100))
+    S = w.poses.shape[0]
+    n_sample = 64
+    times, nrays = [], 0
+    osc = None
+    for k in range(n_steps):
+        osc, o, d, envs = oracle_sample(w, w.poses[k % S], n_sample, seed=k, osc=osc)
+        t = time_oracle(osc, o, d, w.max_range)
+        if k >= args.warmup:
+            times.append(t)
+            nrays = len(o)
+    tot = sum(times)
+    v = nrays * len(times) / tot / 1e9
+    line = {"metric": METRIC, "value": round(v, 6), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(tot * 1e3 / len(times), 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "parallelism": "host cores"},
+            "cpu_baseline": {"value": round(v, 6), "unit": UNIT, "kind": "oracle",
+                             "cores": os.cpu_count(),
+                             "sample": f"per step {n_sample} of {args.n_env} envs x "
+                                       f"{w.sensor.n_rays} rays, FP64 median-split BVH"},
+            "e2e": {"value": round(v, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

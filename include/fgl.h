@@ -1,0 +1,220 @@
+/*
+ * fgl.h -- batched LiDAR ray casting on GB300 (sm_103a).
+ *
+ * The operation is the LiDAR measurement model of FGGS-LiDAR (arXiv
+ * 2509.17390), Sec. IV-C:
+ *   eq. r_j   : beam j of a sensor with pose T_s = [R_s | t_s] in SE(3) is
+ *               the ray r_j(t) = x_s + t d_j, with origin x_s = t_s and unit
+ *               direction d_j = R_s * (its sensor-frame direction);
+ *   eq. t_j*  : its return is the nearest intersection parameter with the
+ *               triangle mesh M, over (t_min, t_max] = (0, max_range];
+ *   cost model: the mesh sits in a bounding-volume hierarchy and every ray
+ *               walks it, pruned by its best-so-far t (Sec. IV-C,
+ *               "GPU-accelerated ray-casting", eq. cost(r_j)).
+ * Results are reported per ray as a float32 range (the ray parameter t;
+ * directions are unit length up to float32 rounding, so t is metres) and
+ * the int32 id of the hit triangle (its index in the input triangle array).
+ * A miss reports (max_range, -1).  Ties in t go to the smaller triangle id,
+ * so results never depend on traversal order, BVH width, packet shape,
+ * stack depth, block size or batching.
+ *
+ * Conventions
+ *   - Sensor frame: x forward, y left, z up.  Beam direction from elevation
+ *     el and azimuth az (radians): (cos el cos az, cos el sin az, sin el),
+ *     evaluated on the host in float64 and rounded once to float32.
+ *   - Pose: float32 [3][4] row-major [R | t] (sensor -> world), 48 bytes per
+ *     environment, environments contiguous.  The world direction is
+ *     computed in float32 with every product and sum rounded separately, row
+ *     i as ((R[i][0]*d0) + (R[i][1]*d1)) + (R[i][2]*d2).
+ *   - Output layout: ray (env e, beam r) at index e * n_rays + r, where r is
+ *     the beam's position in the table given to fgl_sensor_create.
+ *   - Pointers marked "device" are CUDA device pointers owned by the caller;
+ *     calls that take a stream are asynchronous on it.  Argument errors are
+ *     reported synchronously; asynchronous CUDA errors and device-side
+ *     traversal errors surface on fgl_sync() or the next call.
+ *   - Every call returns an fgl_status; on failure fgl_last_error() gives a
+ *     thread-local message.
+ */
+#ifndef FGL_H
+#define FGL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st* fgl_stream;
+
+typedef enum {
+  FGL_OK = 0,
+  FGL_ERR_INVALID = 1,   /* bad argument (null pointer, size, NaN, id range) */
+  FGL_ERR_OOM = 2,       /* device or host allocation failed */
+  FGL_ERR_CUDA = 3,      /* a CUDA runtime call failed */
+  FGL_ERR_BUDGET = 4,    /* serving: request larger than the HBM budget */
+  FGL_ERR_TIMEOUT = 5,   /* serving: wait timed out */
+  FGL_ERR_CANCELLED = 6, /* serving: request cancelled */
+  FGL_ERR_DEVICE = 7     /* a kernel reported an error (traversal stack overflow) */
+} fgl_status;
+
+typedef struct fgl_scene_s* fgl_scene;
+typedef struct fgl_sensor_s* fgl_sensor;
+
+/* ------------------------------------------------------------------------ */
+/* Scenes                                                                    */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  int32_t width;      /* children per BVH node: 4 or 8 (0 = 8) */
+  int32_t sah_bins;   /* binned-SAH bins per axis (0 = 32) */
+  int32_t n_threads;  /* host build threads (0 = all cores) */
+  int32_t upload;     /* 1 = upload to the current CUDA device (default when
+                         opts is NULL); 0 = host-only build (tests, offline) */
+} fgl_build_opts;
+
+typedef struct {
+  int64_t n_tris;       /* triangles in the scene */
+  int64_t n_nodes;      /* wide BVH nodes */
+  int64_t node_bytes;   /* bytes of the node array (node_stride * n_nodes) */
+  int64_t tri_bytes;    /* bytes of the leaf triangle array (48 * n_tris) */
+  int32_t width;        /* children per node */
+  int32_t node_stride;  /* bytes per node record (80 for width 8, 64 for 4) */
+  int32_t depth;        /* levels of the wide tree (root = 1) */
+  int32_t resident;     /* 1 when the arrays are on the device */
+  double sah_cost;      /* SAH cost of the wide tree (node visits + tri tests, area-weighted) */
+  double build_ms;      /* host build time */
+  float bounds_lo[3];   /* scene bounds */
+  float bounds_hi[3];
+  float margin;         /* outward margin added to every quantized child box (metres) */
+} fgl_scene_stats;
+
+/* Build a scene from a triangle mesh (the mesh M of eq. t_j*).
+ *   verts: host float32 [nv][3]; tris: host int32 [nt][3] vertex ids.
+ *   Builds a binned-SAH binary BVH, collapses it to `width`-wide nodes with
+ *   8-bit child boxes rounded outward (plus a margin covering float32
+ *   rounding of the traversal's slab test), re-orders triangles into leaf
+ *   order (48 bytes each) and, when opts->upload != 0, copies both arrays to
+ *   the current device (synchronously).  The scene owns its device memory
+ *   until fgl_scene_destroy and keeps its host copy for re-upload.
+ *   Errors: FGL_ERR_INVALID for nv<1, nt<1, null pointers, non-finite
+ *   vertices or ids outside [0,nv); FGL_ERR_OOM; FGL_ERR_CUDA. */
+fgl_status fgl_scene_build(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
+                           const fgl_build_opts* opts, fgl_scene* out);
+fgl_status fgl_scene_destroy(fgl_scene scene);
+fgl_status fgl_scene_get_stats(fgl_scene scene, fgl_scene_stats* out);
+/* Copy the host node / triangle arrays (sizes from the stats) -- for tests. */
+fgl_status fgl_scene_export(fgl_scene scene, void* nodes, int64_t node_bytes, void* tris,
+                            int64_t tri_bytes);
+/* Check, with the float32 decode arithmetic of the traversal, that every
+ * quantized child box contains its subtree's triangles grown by the margin.
+ * Writes the number of violations to *n_bad (0 for a correct build). */
+fgl_status fgl_scene_verify(fgl_scene scene, int64_t* n_bad);
+/* Upload (if evicted) / drop the device copy, keeping the host copy. */
+fgl_status fgl_scene_upload(fgl_scene scene);
+fgl_status fgl_scene_evict(fgl_scene scene);
+
+/* ------------------------------------------------------------------------ */
+/* Sensors (scan patterns, the d_j of eq. r_j)                               */
+/* ------------------------------------------------------------------------ */
+
+/* Create a sensor from per-beam elevation/azimuth (host float32 radians,
+ * n_rays entries).  rows x cols describes the beam grid of a spinning sensor
+ * (rows * cols == n_rays, beam r = row * cols + col); pass rows = 1,
+ * cols = n_rays for a pattern with no grid.  tile_rows x tile_cols (0 = the
+ * default 4 x 8) is the angular tile that consecutive rays of one warp are
+ * drawn from; it changes speed only, never results.  Directions are computed
+ * on the host in float64, rounded to float32 and uploaded (synchronously).
+ * Errors: FGL_ERR_INVALID for n_rays<1, rows*cols != n_rays, non-finite
+ * angles, tiles < 0. */
+fgl_status fgl_sensor_create(const float* elev_rad, const float* azim_rad, int32_t n_rays,
+                             int32_t rows, int32_t cols, int32_t tile_rows, int32_t tile_cols,
+                             fgl_sensor* out);
+fgl_status fgl_sensor_destroy(fgl_sensor sensor);
+fgl_status fgl_sensor_n_rays(fgl_sensor sensor, int32_t* n_rays);
+/* Host copy of the float32 sensor-frame directions [n_rays][3], beam order. */
+fgl_status fgl_sensor_dirs(fgl_sensor sensor, float* out_dirs);
+
+/* ------------------------------------------------------------------------ */
+/* Casting                                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Plain form: one kernel launch, one thread per ray, over n_env poses of one
+ * sensor against one scene.
+ *   poses:     device float32 [n_env][3][4]
+ *   out_range: device float32 [n_env * n_rays]; out_tri: device int32, same.
+ * n_env == 0 is a no-op.  Errors: FGL_ERR_INVALID (null handle/pointer,
+ * n_env < 0, max_range not finite and > 0, scene not resident). */
+fgl_status fgl_cast(fgl_scene scene, fgl_sensor sensor, const float* poses, int32_t n_env,
+                    float max_range, float* out_range, int32_t* out_tri, fgl_stream stream);
+
+typedef struct {
+  fgl_scene scene;
+  fgl_sensor sensor;
+  const float* poses;   /* device float32 [n_env][3][4] */
+  int32_t n_env;
+  float max_range;
+  float* out_range;     /* device float32 [n_env * n_rays] */
+  int32_t* out_tri;     /* device int32  [n_env * n_rays] */
+} fgl_cast_item;
+
+typedef struct {
+  int32_t packet_rays;    /* rays per work packet (0 = 64; multiple of 32) */
+  int32_t block_threads;  /* threads per block (0 = 128; multiple of 32, <= 512) */
+  int32_t stack_smem;     /* traversal stack entries kept in shared memory (0 = 12) */
+  int32_t blocks_per_sm;  /* persistent blocks per SM (0 = as many as fit) */
+  int32_t use_graph;      /* 1 = capture the launch sequence in a CUDA graph and
+                             replay it while the item layout is unchanged */
+  int32_t refill_min;     /* idle lanes before a warp pulls new rays (0 = 8) */
+  int32_t postpone_pct;   /* postpone leaf tests when fewer than this % of the
+                             warp's tracing lanes want them (0 = 20; -1 = never) */
+  int32_t count_work;     /* 1 = count node visits and triangle tests (slower);
+                             read with fgl_work_counters */
+} fgl_batch_opts;
+
+/* fgl_cast with explicit launch options: block_threads, stack_smem,
+ * postpone_pct and count_work apply; the other fields are ignored.  Results
+ * are identical for every valid option set (only speed changes). */
+fgl_status fgl_cast_opts(fgl_scene scene, fgl_sensor sensor, const float* poses, int32_t n_env,
+                         float max_range, float* out_range, int32_t* out_tri,
+                         const fgl_batch_opts* opts, fgl_stream stream);
+
+/* Batched form: every item (scene, sensor, poses) goes into one device work
+ * queue of ray packets drained by one persistent kernel (per BVH width
+ * present in the batch).  Uneven ray counts, sensors and scenes mix freely.
+ * Scratch (queue head, item table) is library-owned and cached per stream.
+ * Errors: as fgl_cast for each item; FGL_ERR_INVALID for n_items < 0. */
+fgl_status fgl_cast_batched(const fgl_cast_item* items, int32_t n_items,
+                            const fgl_batch_opts* opts, fgl_stream stream);
+
+/* End-to-end form of fgl_cast_batched for callers holding HOST buffers:
+ * items[i].poses / out_range / out_tri are host pointers (page-locked for
+ * full speed).  Copies poses to library-owned device staging, runs the
+ * batched kernel, copies results back and synchronizes the stream. */
+fgl_status fgl_cast_batched_host(const fgl_cast_item* items, int32_t n_items,
+                                 const fgl_batch_opts* opts, fgl_stream stream);
+
+/* Wait for the stream, then report any asynchronous CUDA error or
+ * device-side traversal error (FGL_ERR_DEVICE) raised since the last check. */
+fgl_status fgl_sync(fgl_stream stream);
+
+/* Totals accumulated by count_work launches since the last call (then reset):
+ * rays traced, wide-node visits, triangle tests. */
+fgl_status fgl_work_counters(uint64_t* rays, uint64_t* node_visits, uint64_t* tri_tests);
+
+/* Debug export of the float32 world rays the kernels trace (eq. r_j):
+ * out_o, out_d device float32 [n_env * n_rays][3]. */
+fgl_status fgl_world_rays(fgl_sensor sensor, const float* poses, int32_t n_env, float* out_o,
+                          float* out_d, fgl_stream stream);
+
+/* Thread-local message for the last non-OK status of this thread. */
+const char* fgl_last_error(void);
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int32_t fgl_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FGL_H */

@@ -1,0 +1,341 @@
+"""Python binding of libfgl (include/fgl.h): batched LiDAR ray casting on GB300.
+
+Argument marshalling only -- every step of the ray-casting path runs in the
+CUDA kernels of libfgl.so.  Device buffers are torch CUDA tensors (their
+data_ptr is passed through); streams are torch.cuda.Stream objects or raw
+cudaStream_t integers.  There is no CPU fallback: if the native library is
+missing and cannot be built, importing the binding's functions raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Iterable, Optional, Sequence
+
+import numpy as np
+
+from . import build_native
+
+__all__ = ["Scene", "Sensor", "BatchOpts", "cast", "cast_opts", "cast_batched",
+           "cast_batched_host", "world_rays", "sync", "work_counters", "FglError", "lib"]
+
+FGL_OK, FGL_ERR_INVALID, FGL_ERR_OOM, FGL_ERR_CUDA = 0, 1, 2, 3
+FGL_ERR_BUDGET, FGL_ERR_TIMEOUT, FGL_ERR_CANCELLED, FGL_ERR_DEVICE = 4, 5, 6, 7
+STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "BUDGET", 5: "TIMEOUT",
+                6: "CANCELLED", 7: "DEVICE"}
+
+
+class FglError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"fgl {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+P = ctypes.c_void_p
+I32, I64, F32, F64, U64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_double, ctypes.c_uint64
+
+
+class BuildOpts(ctypes.Structure):
+    _fields_ = [("width", I32), ("sah_bins", I32), ("n_threads", I32), ("upload", I32)]
+
+
+class SceneStats(ctypes.Structure):
+    _fields_ = [("n_tris", I64), ("n_nodes", I64), ("node_bytes", I64), ("tri_bytes", I64),
+                ("width", I32), ("node_stride", I32), ("depth", I32), ("resident", I32),
+                ("sah_cost", F64), ("build_ms", F64), ("bounds_lo", F32 * 3),
+                ("bounds_hi", F32 * 3), ("margin", F32)]
+
+
+class CastItem(ctypes.Structure):
+    _fields_ = [("scene", P), ("sensor", P), ("poses", P), ("n_env", I32), ("max_range", F32),
+                ("out_range", P), ("out_tri", P)]
+
+
+class BatchOpts(ctypes.Structure):
+    """Launch options (fgl_batch_opts); 0 in a field selects its default."""
+    _fields_ = [("packet_rays", I32), ("block_threads", I32), ("stack_smem", I32),
+                ("blocks_per_sm", I32), ("use_graph", I32), ("refill_min", I32),
+                ("postpone_pct", I32), ("count_work", I32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load (building in-tree first if needed) libfgl.so."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build_native.LIB
+            if not os.path.exists(path):
+                build_native.build()
+            L = ctypes.CDLL(path)
+            sig = {
+                "fgl_scene_build": ([P, I64, P, I64, P, P], I32),
+                "fgl_scene_destroy": ([P], I32),
+                "fgl_scene_get_stats": ([P, P], I32),
+                "fgl_scene_export": ([P, P, I64, P, I64], I32),
+                "fgl_scene_verify": ([P, P], I32),
+                "fgl_scene_upload": ([P], I32),
+                "fgl_scene_evict": ([P], I32),
+                "fgl_sensor_create": ([P, P, I32, I32, I32, I32, I32, P], I32),
+                "fgl_sensor_destroy": ([P], I32),
+                "fgl_sensor_n_rays": ([P, P], I32),
+                "fgl_sensor_dirs": ([P, P], I32),
+                "fgl_cast": ([P, P, P, I32, F32, P, P, P], I32),
+                "fgl_cast_opts": ([P, P, P, I32, F32, P, P, P, P], I32),
+                "fgl_cast_batched": ([P, I32, P, P], I32),
+                "fgl_cast_batched_host": ([P, I32, P, P], I32),
+                "fgl_sync": ([P], I32),
+                "fgl_work_counters": ([P, P, P], I32),
+                "fgl_world_rays": ([P, P, I32, P, P, P], I32),
+                "fgl_last_error": ([], ctypes.c_char_p),
+                "fgl_version": ([], I32),
+            }
+            for name, (args, res) in sig.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != FGL_OK:
+        raise FglError(status, lib().fgl_last_error().decode(errors="replace"))
+
+
+def _np_ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream or None
+    if isinstance(stream, int):
+        return stream or None
+    return stream.cuda_stream or None
+
+
+def _dev_ptr(t, dtype_name: str, numel: int, what: str) -> int:
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{what} must be a CUDA tensor")
+    if str(t.dtype) != "torch." + dtype_name:
+        raise TypeError(f"{what} must be {dtype_name}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    if t.numel() < numel:
+        raise ValueError(f"{what} has {t.numel()} elements, needs {numel}")
+    return t.data_ptr()
+
+
+class Scene:
+    """A triangle mesh with its wide BVH (fgl_scene_build)."""
+
+    def __init__(self, verts, tris, width: int = 8, sah_bins: int = 32, n_threads: int = 0,
+                 upload: bool = True):
+        v = np.ascontiguousarray(verts, np.float32).reshape(-1, 3)
+        t = np.ascontiguousarray(tris, np.int32).reshape(-1, 3)
+        o = BuildOpts(width, sah_bins, n_threads, 1 if upload else 0)
+        h = P()
+        _check(lib().fgl_scene_build(_np_ptr(v), len(v), _np_ptr(t), len(t), ctypes.byref(o),
+                                     ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def stats(self) -> dict:
+        s = SceneStats()
+        _check(lib().fgl_scene_get_stats(self._h, ctypes.byref(s)))
+        d = {k: getattr(s, k) for k, _ in SceneStats._fields_}
+        for k in ("bounds_lo", "bounds_hi"):
+            d[k] = list(d[k])
+        return d
+
+    def export(self):
+        st = self.stats()
+        nodes = np.empty(st["node_bytes"], np.uint8)
+        tris = np.empty(st["tri_bytes"] // 4, np.float32)
+        _check(lib().fgl_scene_export(self._h, _np_ptr(nodes), nodes.nbytes, _np_ptr(tris),
+                                      tris.nbytes))
+        return nodes, tris.reshape(-1, 12)
+
+    def verify(self) -> int:
+        n = ctypes.c_int64(0)
+        _check(lib().fgl_scene_verify(self._h, ctypes.byref(n)))
+        return int(n.value)
+
+    def upload(self):
+        _check(lib().fgl_scene_upload(self._h))
+
+    def evict(self):
+        _check(lib().fgl_scene_evict(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fgl_scene_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Sensor:
+    """A scan pattern (fgl_sensor_create) from per-beam elevation/azimuth."""
+
+    def __init__(self, elev, azim, rows: int = 1, cols: Optional[int] = None,
+                 tile_rows: int = 0, tile_cols: int = 0):
+        el = np.ascontiguousarray(elev, np.float32).reshape(-1)
+        az = np.ascontiguousarray(azim, np.float32).reshape(-1)
+        if cols is None:
+            cols = len(el) // max(rows, 1)
+        h = P()
+        _check(lib().fgl_sensor_create(_np_ptr(el), _np_ptr(az), len(el), rows, cols, tile_rows,
+                                       tile_cols, ctypes.byref(h)))
+        self._h = h
+        self.n_rays = len(el)
+        self.rows, self.cols = rows, cols
+
+    @classmethod
+    def from_table(cls, table, tile_rows: int = 0, tile_cols: int = 0):
+        return cls(table.elev, table.azim, table.rows, table.cols, tile_rows, tile_cols)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def dirs(self) -> np.ndarray:
+        out = np.empty((self.n_rays, 3), np.float32)
+        _check(lib().fgl_sensor_dirs(self._h, _np_ptr(out)))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fgl_sensor_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _outputs(n, device, out_range, out_tri):
+    import torch
+    if out_range is None:
+        out_range = torch.empty(n, dtype=torch.float32, device=device)
+    if out_tri is None:
+        out_tri = torch.empty(n, dtype=torch.int32, device=device)
+    return out_range, out_tri
+
+
+def cast(scene: Scene, sensor: Sensor, poses, max_range: float, out_range=None, out_tri=None,
+         stream=None):
+    """Plain form (fgl_cast): one launch, one thread per ray."""
+    n_env = poses.shape[0] if poses.dim() == 3 else poses.numel() // 12
+    n = n_env * sensor.n_rays
+    out_range, out_tri = _outputs(n, poses.device, out_range, out_tri)
+    _check(lib().fgl_cast(scene.handle, sensor.handle, _dev_ptr(poses, "float32", n_env * 12, "poses"),
+                          n_env, float(max_range), _dev_ptr(out_range, "float32", n, "out_range"),
+                          _dev_ptr(out_tri, "int32", n, "out_tri"), _stream_handle(stream)))
+    return out_range, out_tri
+
+
+def cast_opts(scene: Scene, sensor: Sensor, poses, max_range: float, opts: BatchOpts,
+              out_range=None, out_tri=None, stream=None):
+    """Plain form with explicit launch options (fgl_cast_opts)."""
+    n_env = poses.shape[0] if poses.dim() == 3 else poses.numel() // 12
+    n = n_env * sensor.n_rays
+    out_range, out_tri = _outputs(n, poses.device, out_range, out_tri)
+    _check(lib().fgl_cast_opts(scene.handle, sensor.handle,
+                               _dev_ptr(poses, "float32", n_env * 12, "poses"), n_env,
+                               float(max_range), _dev_ptr(out_range, "float32", n, "out_range"),
+                               _dev_ptr(out_tri, "int32", n, "out_tri"), ctypes.byref(opts),
+                               _stream_handle(stream)))
+    return out_range, out_tri
+
+
+def make_items(items: Sequence[tuple]):
+    """items: (scene, sensor, poses, max_range, out_range, out_tri) tuples with
+    torch CUDA tensors; returns the ctypes array."""
+    arr = (CastItem * max(1, len(items)))()
+    for i, (sc, se, poses, rmax, orng, otri) in enumerate(items):
+        n_env = poses.shape[0] if poses.dim() == 3 else poses.numel() // 12
+        n = n_env * se.n_rays
+        arr[i] = CastItem(sc.handle, se.handle, _dev_ptr(poses, "float32", n_env * 12, "poses"),
+                          n_env, float(rmax), _dev_ptr(orng, "float32", n, "out_range"),
+                          _dev_ptr(otri, "int32", n, "out_tri"))
+    return arr
+
+
+def cast_batched(items: Sequence[tuple], opts: Optional[BatchOpts] = None, stream=None, arr=None):
+    """Batched form (fgl_cast_batched) over (scene, sensor, poses, max_range,
+    out_range, out_tri) tuples.  Pass a prepared ``arr`` (make_items) to skip
+    re-marshalling in a loop."""
+    if arr is None:
+        arr = make_items(items)
+    _check(lib().fgl_cast_batched(arr, len(items), ctypes.byref(opts) if opts else None,
+                                  _stream_handle(stream)))
+
+
+def cast_batched_host(items: Sequence[tuple], opts: Optional[BatchOpts] = None, stream=None):
+    """End-to-end batched form (fgl_cast_batched_host): poses and outputs are
+    host tensors/arrays (page-locked for full speed); blocks until done."""
+    arr = (CastItem * max(1, len(items)))()
+    for i, (sc, se, poses, rmax, orng, otri) in enumerate(items):
+        n_env = int(np.prod(poses.shape)) // 12
+        arr[i] = CastItem(sc.handle, se.handle, _host_ptr(poses), n_env, float(rmax),
+                          _host_ptr(orng), _host_ptr(otri))
+    _check(lib().fgl_cast_batched_host(arr, len(items), ctypes.byref(opts) if opts else None,
+                                       _stream_handle(stream)))
+
+
+def _host_ptr(x) -> int:
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("host arrays must be contiguous")
+        return x.ctypes.data
+    import torch
+    if isinstance(x, torch.Tensor):
+        if x.is_cuda or not x.is_contiguous():
+            raise ValueError("host tensors must be contiguous CPU tensors")
+        return x.data_ptr()
+    raise TypeError("expected a numpy array or a CPU tensor")
+
+
+def world_rays(sensor: Sensor, poses, stream=None):
+    """Float32 world rays exactly as the kernels trace them: (o, d) [n, 3]."""
+    import torch
+    n_env = poses.shape[0] if poses.dim() == 3 else poses.numel() // 12
+    n = n_env * sensor.n_rays
+    o = torch.empty((n, 3), dtype=torch.float32, device=poses.device)
+    d = torch.empty((n, 3), dtype=torch.float32, device=poses.device)
+    _check(lib().fgl_world_rays(sensor.handle, _dev_ptr(poses, "float32", n_env * 12, "poses"),
+                                n_env, o.data_ptr(), d.data_ptr(), _stream_handle(stream)))
+    return o, d
+
+
+def sync(stream=None):
+    """Wait for the stream and surface asynchronous / device-side errors."""
+    _check(lib().fgl_sync(_stream_handle(stream)))
+
+
+def work_counters():
+    """(rays, node visits, triangle tests) counted by count_work launches."""
+    r, n, t = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().fgl_work_counters(ctypes.byref(r), ctypes.byref(n), ctypes.byref(t)))
+    return int(r.value), int(n.value), int(t.value)

@@ -1,0 +1,689 @@
+// C-ABI of the ray caster (include/fgl.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "fgl.h"
+#include "fgl_internal.h"
+#include "kernels.h"
+
+using namespace fgl;
+
+struct fgl_scene_s {
+  HostBVH bvh;
+  void* d_nodes = nullptr;
+  void* d_tris = nullptr;
+  int device = -1;
+};
+
+struct fgl_sensor_s {
+  int32_t n_rays = 0, rows = 1, cols = 1, tile_rows = 4, tile_cols = 8;
+  std::vector<float> dirs;       // beam order, 3 per ray
+  std::vector<float> dev_order;  // tile order, 4 per ray (xyz + beam index bits)
+  void* d_dirs = nullptr;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+fgl_status fail(fgl_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+fgl_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(FGL_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define FGL_CUDA(call)                                      \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);     \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// per-device one-time set-up
+// ---------------------------------------------------------------------------
+struct DeviceInfo {
+  int sm_count = 0;
+  size_t smem_optin = 0;
+};
+std::mutex g_dev_mu;
+std::unordered_map<int, DeviceInfo> g_dev;
+
+fgl_status device_info(DeviceInfo* out) {
+  int dev = 0;
+  FGL_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  auto it = g_dev.find(dev);
+  if (it == g_dev.end()) {
+    DeviceInfo di;
+    FGL_CUDA(cudaDeviceGetAttribute(&di.sm_count, cudaDevAttrMultiProcessorCount, dev));
+    int optin = 0;
+    FGL_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    di.smem_optin = (size_t)optin;
+    it = g_dev.emplace(dev, di).first;
+  }
+  *out = it->second;
+  return FGL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// option defaults
+// ---------------------------------------------------------------------------
+struct Opts {
+  int packet = 64, block = 128, sdepth = 12, bpsm = 0, graph = 0, refill = 8, postpone = 20,
+      count = 0;
+};
+
+fgl_status resolve_opts(const fgl_batch_opts* o, Opts* r) {
+  Opts d;
+  if (o) {
+    if (o->packet_rays) d.packet = o->packet_rays;
+    if (o->block_threads) d.block = o->block_threads;
+    if (o->stack_smem) d.sdepth = o->stack_smem;
+    if (o->blocks_per_sm) d.bpsm = o->blocks_per_sm;
+    d.graph = o->use_graph ? 1 : 0;
+    if (o->refill_min) d.refill = o->refill_min;
+    if (o->postpone_pct) d.postpone = o->postpone_pct;
+    d.count = o->count_work ? 1 : 0;
+  }
+  if (d.packet < 32 || d.packet % 32 || d.packet > (1 << 20))
+    return fail(FGL_ERR_INVALID, "packet_rays must be a positive multiple of 32");
+  if (d.block < 32 || d.block % 32 || d.block > 512)
+    return fail(FGL_ERR_INVALID, "block_threads must be a multiple of 32 in [32, 512]");
+  if (d.sdepth < 0 || d.sdepth > 64) return fail(FGL_ERR_INVALID, "stack_smem must be in [0, 64]");
+  if (d.bpsm < 0 || d.bpsm > 64) return fail(FGL_ERR_INVALID, "blocks_per_sm must be in [0, 64]");
+  if (d.refill < 1 || d.refill > 32) return fail(FGL_ERR_INVALID, "refill_min must be in [1, 32]");
+  if (d.postpone > 100) return fail(FGL_ERR_INVALID, "postpone_pct must be <= 100");
+  DeviceInfo di;
+  fgl_status s = device_info(&di);
+  if (s != FGL_OK) return s;
+  if (stack_smem_bytes(d.block, d.sdepth) > di.smem_optin)
+    return fail(FGL_ERR_INVALID, "block_threads * stack_smem * 8 exceeds shared memory");
+  *r = d;
+  return FGL_OK;
+}
+
+fgl_status check_item(const fgl_cast_item& it, int idx) {
+  std::string w = "item " + std::to_string(idx) + ": ";
+  if (!it.scene || !it.sensor) return fail(FGL_ERR_INVALID, w + "null scene or sensor");
+  if (it.n_env < 0) return fail(FGL_ERR_INVALID, w + "n_env < 0");
+  if (!(std::isfinite(it.max_range) && it.max_range > 0.f))
+    return fail(FGL_ERR_INVALID, w + "max_range must be finite and > 0");
+  if (it.n_env > 0 && (!it.poses || !it.out_range || !it.out_tri))
+    return fail(FGL_ERR_INVALID, w + "null poses or output pointer");
+  if (!it.scene->d_nodes) return fail(FGL_ERR_INVALID, w + "scene is not resident on the device");
+  if ((int64_t)it.n_env * it.sensor->n_rays > ((int64_t)1 << 40))
+    return fail(FGL_ERR_INVALID, w + "too many rays");
+  return FGL_OK;
+}
+
+ItemDesc make_desc(const fgl_cast_item& it) {
+  ItemDesc d;
+  std::memset(&d, 0, sizeof(d));
+  d.nodes = it.scene->d_nodes;
+  d.tris = it.scene->d_tris;
+  d.dirs = it.sensor->d_dirs;
+  d.poses = it.poses;
+  d.out_range = it.out_range;
+  d.out_tri = it.out_tri;
+  d.n_env = it.n_env;
+  d.n_rays = it.sensor->n_rays;
+  d.max_range = it.max_range;
+  return d;
+}
+
+// ---------------------------------------------------------------------------
+// per-stream batch context: device scratch (work queue + item table), pinned
+// staging of the table, CUDA graph, and end-to-end staging buffers
+// ---------------------------------------------------------------------------
+struct BatchCtx {
+  int device = -1;
+  void* d_scratch = nullptr;
+  size_t scratch_cap = 0;
+  void* h_staging = nullptr;  // pinned
+  size_t staging_cap = 0;
+  size_t table_bytes = 0;
+  cudaEvent_t staged = nullptr;  // recorded after the table copy
+  bool staged_pending = false;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<uint8_t> gkey;
+  // end-to-end staging
+  void* d_io = nullptr;
+  size_t io_cap = 0;
+  std::mutex mu;
+};
+std::mutex g_ctx_mu;
+std::unordered_map<uint64_t, std::unique_ptr<BatchCtx>> g_ctx;
+
+BatchCtx* get_ctx(cudaStream_t s) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  uint64_t key = (uint64_t)(uintptr_t)s ^ ((uint64_t)dev << 56);
+  std::lock_guard<std::mutex> lk(g_ctx_mu);
+  auto& p = g_ctx[key];
+  if (!p) {
+    p.reset(new BatchCtx());
+    p->device = dev;
+  }
+  return p.get();
+}
+
+struct Group {
+  int W;
+  std::vector<ItemDesc> items;
+  int64_t n_packets = 0;
+};
+
+// Build the work-queue table for every BVH width present: for each group a
+// BatchHeader (head = 0) followed by its ItemDesc records; packets are
+// numbered per group.  Returns the byte offset of each group's header.
+void build_table(const fgl_cast_item* items, int n, int P, std::vector<Group>& groups,
+                 std::vector<uint8_t>& table, std::vector<size_t>& offsets) {
+  groups.clear();
+  for (int W : {8, 4}) {
+    Group g;
+    g.W = W;
+    for (int i = 0; i < n; ++i) {
+      if (items[i].scene->bvh.width != W || items[i].n_env == 0) continue;
+      ItemDesc d = make_desc(items[i]);
+      d.pk_per_env = (d.n_rays + P - 1) / P;
+      d.pk_begin = g.n_packets;
+      g.n_packets += (int64_t)d.pk_per_env * d.n_env;
+      g.items.push_back(d);
+    }
+    if (!g.items.empty()) groups.push_back(std::move(g));
+  }
+  table.clear();
+  offsets.clear();
+  for (const Group& g : groups) {
+    size_t off = table.size();
+    offsets.push_back(off);
+    BatchHeader h;
+    std::memset(&h, 0, sizeof(h));
+    h.head = 0;
+    h.n_packets = g.n_packets;
+    h.n_items = (int32_t)g.items.size();
+    h.packet_rays = P;
+    table.resize(off + sizeof(BatchHeader) + g.items.size() * sizeof(ItemDesc));
+    std::memcpy(table.data() + off, &h, sizeof(h));
+    std::memcpy(table.data() + off + sizeof(h), g.items.data(), g.items.size() * sizeof(ItemDesc));
+  }
+}
+
+struct LaunchCfg {
+  int grid = 0;
+};
+
+fgl_status grid_for(int W, const Opts& o, int* grid) {
+  DeviceInfo di;
+  fgl_status s = device_info(&di);
+  if (s != FGL_OK) return s;
+  int bpsm = o.bpsm ? o.bpsm : persistent_blocks_per_sm(W, o.count != 0, o.block, o.sdepth);
+  *grid = std::max(1, di.sm_count * bpsm);
+  return FGL_OK;
+}
+
+fgl_status enqueue_batch(BatchCtx& c, const std::vector<Group>& groups,
+                         const std::vector<size_t>& offsets, const Opts& o, cudaStream_t s) {
+  FGL_CUDA(cudaMemcpyAsync(c.d_scratch, c.h_staging, c.table_bytes, cudaMemcpyHostToDevice, s));
+  FGL_CUDA(cudaEventRecord(c.staged, s));
+  for (size_t g = 0; g < groups.size(); ++g) {
+    int grid = 0;
+    fgl_status st = grid_for(groups[g].W, o, &grid);
+    if (st != FGL_OK) return st;
+    FGL_CUDA(launch_persistent(groups[g].W, o.count != 0, (char*)c.d_scratch + offsets[g], grid,
+                               o.block, o.sdepth, o.refill, o.postpone, s));
+  }
+  return FGL_OK;
+}
+
+fgl_status run_batched(const fgl_cast_item* items, int n, const Opts& o, cudaStream_t s) {
+  BatchCtx& c = *get_ctx(s);
+  std::lock_guard<std::mutex> lk(c.mu);
+  std::vector<Group> groups;
+  std::vector<uint8_t> table;
+  std::vector<size_t> offsets;
+  build_table(items, n, o.packet, groups, table, offsets);
+  if (groups.empty()) return FGL_OK;
+  // warm the occupancy query (sets kernel attributes) outside any capture
+  for (const Group& g : groups) {
+    int grid;
+    fgl_status st = grid_for(g.W, o, &grid);
+    if (st != FGL_OK) return st;
+  }
+  if (!c.staged) FGL_CUDA(cudaEventCreateWithFlags(&c.staged, cudaEventDisableTiming));
+  bool realloc = false;
+  if (table.size() > c.scratch_cap) {
+    if (c.d_scratch) {
+      FGL_CUDA(cudaStreamSynchronize(s));
+      cudaFree(c.d_scratch);
+    }
+    size_t cap = std::max<size_t>(table.size() * 2, 4096);
+    if (cudaMalloc(&c.d_scratch, cap) != cudaSuccess) {
+      c.d_scratch = nullptr;
+      c.scratch_cap = 0;
+      return fail(FGL_ERR_OOM, "cannot allocate batch scratch");
+    }
+    c.scratch_cap = cap;
+    realloc = true;
+  }
+  if (table.size() > c.staging_cap) {
+    if (c.h_staging) {
+      cudaEventSynchronize(c.staged);
+      cudaFreeHost(c.h_staging);
+    }
+    size_t cap = std::max<size_t>(table.size() * 2, 4096);
+    if (cudaMallocHost(&c.h_staging, cap) != cudaSuccess) {
+      c.h_staging = nullptr;
+      c.staging_cap = 0;
+      return fail(FGL_ERR_OOM, "cannot allocate pinned staging");
+    }
+    c.staging_cap = cap;
+    realloc = true;
+    c.table_bytes = 0;
+  }
+  bool same_table = !realloc && c.table_bytes == table.size() &&
+                    std::memcmp(c.h_staging, table.data(), table.size()) == 0;
+  if (!same_table) {
+    // the previous table copy must have been consumed before overwriting
+    FGL_CUDA(cudaEventSynchronize(c.staged));
+    std::memcpy(c.h_staging, table.data(), table.size());
+    c.table_bytes = table.size();
+  }
+  if (!o.graph) return enqueue_batch(c, groups, offsets, o, s);
+
+  // graph key: the table bytes plus the launch configuration
+  std::vector<uint8_t> key(table);
+  const int cfg[8] = {o.packet, o.block, o.sdepth, o.bpsm, o.refill, o.postpone, o.count,
+                      (int)(uintptr_t)c.d_scratch};
+  key.insert(key.end(), (const uint8_t*)cfg, (const uint8_t*)cfg + sizeof(cfg));
+  if (realloc || !c.gexec || key != c.gkey) {
+    if (c.gexec) {
+      cudaGraphExecDestroy(c.gexec);
+      c.gexec = nullptr;
+    }
+    if (s == nullptr) return fail(FGL_ERR_INVALID, "use_graph needs a non-default stream");
+    cudaGraph_t graph = nullptr;
+    FGL_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    fgl_status st = enqueue_batch(c, groups, offsets, o, s);
+    cudaError_t e = cudaStreamEndCapture(s, &graph);
+    if (st != FGL_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&c.gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      c.gexec = nullptr;
+      return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    c.gkey.swap(key);
+  }
+  FGL_CUDA(cudaGraphLaunch(c.gexec, s));
+  return FGL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fgl_last_error(void) { return g_err.c_str(); }
+
+int32_t fgl_version(void) { return 100; }
+
+fgl_status fgl_scene_build(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
+                           const fgl_build_opts* opts, fgl_scene* out) {
+  if (!out) return fail(FGL_ERR_INVALID, "out is null");
+  *out = nullptr;
+  if (!verts || !tris) return fail(FGL_ERR_INVALID, "null vertex or triangle pointer");
+  if (nv < 1 || nt < 1) return fail(FGL_ERR_INVALID, "mesh needs at least one vertex and triangle");
+  int width = 8, bins = 32, threads = 0, upload = 1;
+  if (opts) {
+    if (opts->width) width = opts->width;
+    if (opts->sah_bins) bins = opts->sah_bins;
+    threads = opts->n_threads;
+    upload = opts->upload;
+  }
+  if (width != 4 && width != 8) return fail(FGL_ERR_INVALID, "width must be 4 or 8");
+  if (bins < 2 || bins > 256) return fail(FGL_ERR_INVALID, "sah_bins must be in [2, 256]");
+  std::unique_ptr<fgl_scene_s> s(new (std::nothrow) fgl_scene_s());
+  if (!s) return fail(FGL_ERR_OOM, "host allocation failed");
+  std::string err;
+  try {
+    if (build_bvh(verts, nv, tris, nt, width, bins, threads, &s->bvh, &err))
+      return fail(FGL_ERR_INVALID, err);
+  } catch (const std::bad_alloc&) {
+    return fail(FGL_ERR_OOM, "host allocation failed during the BVH build");
+  }
+  std::string verr;
+  if (verify_bvh(s->bvh, &verr) != 0) return fail(FGL_ERR_INVALID, "BVH self-check failed: " + verr);
+  if (upload) {
+    fgl_status st = fgl_scene_upload(s.get());
+    if (st != FGL_OK) return st;
+  }
+  *out = s.release();
+  return FGL_OK;
+}
+
+fgl_status fgl_scene_upload(fgl_scene s) {
+  if (!s) return fail(FGL_ERR_INVALID, "null scene");
+  if (s->d_nodes) return FGL_OK;
+  size_t nb = s->bvh.nodes.size(), tb = s->bvh.tris.size() * sizeof(float);
+  cudaError_t ae = cudaMalloc(&s->d_nodes, nb);
+  if (ae != cudaSuccess) {
+    s->d_nodes = nullptr;
+    cudaGetLastError();
+    if (ae == cudaErrorMemoryAllocation) return fail(FGL_ERR_OOM, "cannot allocate device BVH nodes");
+    return cuda_fail(ae, "cudaMalloc(BVH nodes)");
+  }
+  if (cudaMalloc(&s->d_tris, tb) != cudaSuccess) {
+    cudaFree(s->d_nodes);
+    s->d_nodes = s->d_tris = nullptr;
+    cudaGetLastError();
+    return fail(FGL_ERR_OOM, "cannot allocate device triangles");
+  }
+  cudaError_t e = cudaMemcpy(s->d_nodes, s->bvh.nodes.data(), nb, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(s->d_tris, s->bvh.tris.data(), tb, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(s->d_nodes);
+    cudaFree(s->d_tris);
+    s->d_nodes = s->d_tris = nullptr;
+    return cuda_fail(e, "scene upload");
+  }
+  cudaGetDevice(&s->device);
+  return FGL_OK;
+}
+
+fgl_status fgl_scene_evict(fgl_scene s) {
+  if (!s) return fail(FGL_ERR_INVALID, "null scene");
+  if (s->d_nodes) {
+    cudaDeviceSynchronize();
+    cudaFree(s->d_nodes);
+    cudaFree(s->d_tris);
+    s->d_nodes = s->d_tris = nullptr;
+  }
+  return FGL_OK;
+}
+
+fgl_status fgl_scene_destroy(fgl_scene s) {
+  if (!s) return FGL_OK;
+  fgl_scene_evict(s);
+  delete s;
+  return FGL_OK;
+}
+
+fgl_status fgl_scene_get_stats(fgl_scene s, fgl_scene_stats* o) {
+  if (!s || !o) return fail(FGL_ERR_INVALID, "null argument");
+  const HostBVH& b = s->bvh;
+  o->n_tris = b.n_tris;
+  o->n_nodes = b.n_nodes;
+  o->node_bytes = (int64_t)b.nodes.size();
+  o->tri_bytes = (int64_t)(b.tris.size() * sizeof(float));
+  o->width = b.width;
+  o->node_stride = b.stride;
+  o->depth = b.depth;
+  o->resident = s->d_nodes ? 1 : 0;
+  o->sah_cost = b.sah_cost;
+  o->build_ms = b.build_ms;
+  for (int a = 0; a < 3; ++a) {
+    o->bounds_lo[a] = b.lo[a];
+    o->bounds_hi[a] = b.hi[a];
+  }
+  o->margin = b.margin;
+  return FGL_OK;
+}
+
+fgl_status fgl_scene_export(fgl_scene s, void* nodes, int64_t node_bytes, void* tris,
+                            int64_t tri_bytes) {
+  if (!s) return fail(FGL_ERR_INVALID, "null scene");
+  if (nodes) {
+    if (node_bytes != (int64_t)s->bvh.nodes.size()) return fail(FGL_ERR_INVALID, "node_bytes mismatch");
+    std::memcpy(nodes, s->bvh.nodes.data(), node_bytes);
+  }
+  if (tris) {
+    if (tri_bytes != (int64_t)(s->bvh.tris.size() * sizeof(float)))
+      return fail(FGL_ERR_INVALID, "tri_bytes mismatch");
+    std::memcpy(tris, s->bvh.tris.data(), tri_bytes);
+  }
+  return FGL_OK;
+}
+
+fgl_status fgl_scene_verify(fgl_scene s, int64_t* n_bad) {
+  if (!s || !n_bad) return fail(FGL_ERR_INVALID, "null argument");
+  std::string e;
+  *n_bad = verify_bvh(s->bvh, &e);
+  if (*n_bad) g_err = e;
+  return FGL_OK;
+}
+
+fgl_status fgl_sensor_create(const float* el, const float* az, int32_t n, int32_t rows,
+                             int32_t cols, int32_t tile_rows, int32_t tile_cols, fgl_sensor* out) {
+  if (!out) return fail(FGL_ERR_INVALID, "out is null");
+  *out = nullptr;
+  if (!el || !az) return fail(FGL_ERR_INVALID, "null angle pointer");
+  if (n < 1) return fail(FGL_ERR_INVALID, "n_rays must be >= 1");
+  if (rows < 1 || cols < 1 || (int64_t)rows * cols != n)
+    return fail(FGL_ERR_INVALID, "rows * cols must equal n_rays");
+  if (tile_rows < 0 || tile_cols < 0) return fail(FGL_ERR_INVALID, "tile sizes must be >= 0");
+  std::unique_ptr<fgl_sensor_s> s(new fgl_sensor_s());
+  s->n_rays = n;
+  s->rows = rows;
+  s->cols = cols;
+  s->tile_rows = std::min(rows, tile_rows ? tile_rows : 4);
+  s->tile_cols = std::min(cols, tile_cols ? tile_cols : 8);
+  s->dirs.resize(3 * (size_t)n);
+  for (int32_t i = 0; i < n; ++i) {
+    if (!std::isfinite(el[i]) || !std::isfinite(az[i]))
+      return fail(FGL_ERR_INVALID, "non-finite angle at ray " + std::to_string(i));
+    double e = (double)el[i], a = (double)az[i];
+    s->dirs[3 * i + 0] = (float)(std::cos(e) * std::cos(a));
+    s->dirs[3 * i + 1] = (float)(std::cos(e) * std::sin(a));
+    s->dirs[3 * i + 2] = (float)std::sin(e);
+  }
+  // tile order: tiles row-major over the grid, rays row-major inside a tile
+  s->dev_order.reserve(4 * (size_t)n);
+  const int th = s->tile_rows, tw = s->tile_cols;
+  for (int r0 = 0; r0 < rows; r0 += th)
+    for (int c0 = 0; c0 < cols; c0 += tw)
+      for (int r = r0; r < std::min(rows, r0 + th); ++r)
+        for (int c = c0; c < std::min(cols, c0 + tw); ++c) {
+          int32_t j = r * cols + c;
+          float w;
+          std::memcpy(&w, &j, 4);
+          s->dev_order.push_back(s->dirs[3 * j]);
+          s->dev_order.push_back(s->dirs[3 * j + 1]);
+          s->dev_order.push_back(s->dirs[3 * j + 2]);
+          s->dev_order.push_back(w);
+        }
+  size_t bytes = s->dev_order.size() * sizeof(float);
+  cudaError_t ae = cudaMalloc(&s->d_dirs, bytes);
+  if (ae != cudaSuccess) {
+    s->d_dirs = nullptr;
+    cudaGetLastError();
+    if (ae == cudaErrorMemoryAllocation) return fail(FGL_ERR_OOM, "cannot allocate sensor table");
+    return cuda_fail(ae, "cudaMalloc(sensor table)");
+  }
+  cudaError_t e = cudaMemcpy(s->d_dirs, s->dev_order.data(), bytes, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(s->d_dirs);
+    return cuda_fail(e, "sensor upload");
+  }
+  *out = s.release();
+  return FGL_OK;
+}
+
+fgl_status fgl_sensor_destroy(fgl_sensor s) {
+  if (!s) return FGL_OK;
+  if (s->d_dirs) {
+    cudaDeviceSynchronize();
+    cudaFree(s->d_dirs);
+  }
+  delete s;
+  return FGL_OK;
+}
+
+fgl_status fgl_sensor_n_rays(fgl_sensor s, int32_t* n) {
+  if (!s || !n) return fail(FGL_ERR_INVALID, "null argument");
+  *n = s->n_rays;
+  return FGL_OK;
+}
+
+fgl_status fgl_sensor_dirs(fgl_sensor s, float* out) {
+  if (!s || !out) return fail(FGL_ERR_INVALID, "null argument");
+  std::memcpy(out, s->dirs.data(), s->dirs.size() * sizeof(float));
+  return FGL_OK;
+}
+
+fgl_status fgl_cast(fgl_scene scene, fgl_sensor sensor, const float* poses, int32_t n_env,
+                    float max_range, float* out_range, int32_t* out_tri, fgl_stream stream) {
+  fgl_cast_item it{scene, sensor, poses, n_env, max_range, out_range, out_tri};
+  fgl_status st = check_item(it, 0);
+  if (st != FGL_OK) return st;
+  if (n_env == 0) return FGL_OK;
+  Opts o;
+  ItemDesc d = make_desc(it);
+  FGL_CUDA(launch_plain(scene->bvh.width, false, d, o.block, o.sdepth, o.postpone,
+                        (cudaStream_t)stream));
+  return FGL_OK;
+}
+
+fgl_status fgl_cast_opts(fgl_scene scene, fgl_sensor sensor, const float* poses,
+                               int32_t n_env, float max_range, float* out_range, int32_t* out_tri,
+                               const fgl_batch_opts* opts, fgl_stream stream) {
+  fgl_cast_item it{scene, sensor, poses, n_env, max_range, out_range, out_tri};
+  fgl_status st = check_item(it, 0);
+  if (st != FGL_OK) return st;
+  Opts o;
+  st = resolve_opts(opts, &o);
+  if (st != FGL_OK) return st;
+  if (n_env == 0) return FGL_OK;
+  ItemDesc d = make_desc(it);
+  FGL_CUDA(launch_plain(scene->bvh.width, o.count != 0, d, o.block, o.sdepth, o.postpone,
+                        (cudaStream_t)stream));
+  return FGL_OK;
+}
+
+fgl_status fgl_cast_batched(const fgl_cast_item* items, int32_t n_items, const fgl_batch_opts* opts,
+                            fgl_stream stream) {
+  if (n_items < 0) return fail(FGL_ERR_INVALID, "n_items < 0");
+  if (n_items > 0 && !items) return fail(FGL_ERR_INVALID, "items is null");
+  for (int i = 0; i < n_items; ++i) {
+    fgl_status st = check_item(items[i], i);
+    if (st != FGL_OK) return st;
+  }
+  Opts o;
+  fgl_status st = resolve_opts(opts, &o);
+  if (st != FGL_OK) return st;
+  if (n_items == 0) return FGL_OK;
+  return run_batched(items, n_items, o, (cudaStream_t)stream);
+}
+
+fgl_status fgl_cast_batched_host(const fgl_cast_item* items, int32_t n_items,
+                                 const fgl_batch_opts* opts, fgl_stream stream) {
+  if (n_items < 0) return fail(FGL_ERR_INVALID, "n_items < 0");
+  if (n_items > 0 && !items) return fail(FGL_ERR_INVALID, "items is null");
+  for (int i = 0; i < n_items; ++i) {
+    fgl_status st = check_item(items[i], i);
+    if (st != FGL_OK) return st;
+  }
+  Opts o;
+  fgl_status st = resolve_opts(opts, &o);
+  if (st != FGL_OK) return st;
+  if (n_items == 0) return FGL_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  // device staging: poses then outputs of every item, 256-byte aligned
+  std::vector<size_t> pose_off(n_items), out_off(n_items);
+  size_t total = 0;
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  for (int i = 0; i < n_items; ++i) {
+    pose_off[i] = total;
+    total = al(total + (size_t)items[i].n_env * 48);
+  }
+  for (int i = 0; i < n_items; ++i) {
+    out_off[i] = total;
+    total = al(total + (size_t)items[i].n_env * items[i].sensor->n_rays * 8);
+  }
+  BatchCtx& c = *get_ctx(s);
+  {
+    std::lock_guard<std::mutex> lk(c.mu);
+    if (total > c.io_cap) {
+      if (c.d_io) {
+        FGL_CUDA(cudaStreamSynchronize(s));
+        cudaFree(c.d_io);
+      }
+      if (cudaMalloc(&c.d_io, total) != cudaSuccess) {
+        c.d_io = nullptr;
+        c.io_cap = 0;
+        cudaGetLastError();
+        return fail(FGL_ERR_OOM, "cannot allocate end-to-end staging");
+      }
+      c.io_cap = total;
+    }
+  }
+  std::vector<fgl_cast_item> dev(items, items + n_items);
+  for (int i = 0; i < n_items; ++i) {
+    size_t nr = (size_t)items[i].n_env * items[i].sensor->n_rays;
+    float* dp = (float*)((char*)c.d_io + pose_off[i]);
+    float* dr = (float*)((char*)c.d_io + out_off[i]);
+    int32_t* dt = (int32_t*)(dr + nr);
+    if (items[i].n_env)
+      FGL_CUDA(cudaMemcpyAsync(dp, items[i].poses, (size_t)items[i].n_env * 48,
+                               cudaMemcpyHostToDevice, s));
+    dev[i].poses = dp;
+    dev[i].out_range = dr;
+    dev[i].out_tri = dt;
+  }
+  st = run_batched(dev.data(), n_items, o, s);
+  if (st != FGL_OK) return st;
+  for (int i = 0; i < n_items; ++i) {
+    size_t nr = (size_t)items[i].n_env * items[i].sensor->n_rays;
+    if (!nr) continue;
+    FGL_CUDA(cudaMemcpyAsync(items[i].out_range, dev[i].out_range, nr * 4, cudaMemcpyDeviceToHost, s));
+    FGL_CUDA(cudaMemcpyAsync(items[i].out_tri, dev[i].out_tri, nr * 4, cudaMemcpyDeviceToHost, s));
+  }
+  return fgl_sync(stream);
+}
+
+fgl_status fgl_sync(fgl_stream stream) {
+  FGL_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  FGL_CUDA(cudaGetLastError());
+  unsigned st = 0;
+  FGL_CUDA(read_and_clear_status(&st));
+  if (st) return fail(FGL_ERR_DEVICE, "traversal stack overflow in a kernel");
+  return FGL_OK;
+}
+
+fgl_status fgl_work_counters(uint64_t* rays, uint64_t* nodes, uint64_t* tris) {
+  unsigned long long c[3];
+  FGL_CUDA(cudaDeviceSynchronize());
+  FGL_CUDA(read_and_clear_counters(c));
+  if (rays) *rays = c[0];
+  if (nodes) *nodes = c[1];
+  if (tris) *tris = c[2];
+  return FGL_OK;
+}
+
+fgl_status fgl_world_rays(fgl_sensor sensor, const float* poses, int32_t n_env, float* out_o,
+                          float* out_d, fgl_stream stream) {
+  if (!sensor) return fail(FGL_ERR_INVALID, "null sensor");
+  if (n_env < 0) return fail(FGL_ERR_INVALID, "n_env < 0");
+  if (n_env == 0) return FGL_OK;
+  if (!poses || !out_o || !out_d) return fail(FGL_ERR_INVALID, "null pointer");
+  FGL_CUDA(launch_world_rays(sensor->d_dirs, poses, n_env, sensor->n_rays, out_o, out_d,
+                             (cudaStream_t)stream));
+  return FGL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,539 @@
+// Host BVH builder: binned-SAH binary tree -> greedy collapse to W-wide nodes
+// -> octant codes -> 8-bit quantized child boxes rounded outward.
+//
+// The paper traverses a triangle LBVH built with Karras' method (Sec. IV-C,
+// "GPU-accelerated ray-casting"; Sec. IV-A for the LBVH routine).  Here the
+// tree is built once per scene on the host with the surface-area heuristic,
+// which gives fewer node visits per ray (the N_nodes term of eq. cost(r_j)),
+// and stored as compressed wide nodes so that one 80-byte read tests eight
+// children (the "memory layout" point at the end of Sec. IV-C).
+//
+// Compiled without FMA contraction; the one fused operation the traversal
+// relies on (box decode) is written as std::fmaf explicitly.
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <mutex>
+#include <thread>
+
+#include "fgl_internal.h"
+
+namespace fgl {
+namespace {
+
+struct Box {
+  float lo[3], hi[3];
+  void reset() {
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = std::numeric_limits<float>::infinity();
+      hi[a] = -std::numeric_limits<float>::infinity();
+    }
+  }
+  void grow(const Box& b) {
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = std::min(lo[a], b.lo[a]);
+      hi[a] = std::max(hi[a], b.hi[a]);
+    }
+  }
+  double area() const {
+    if (!(hi[0] >= lo[0])) return 0.0;
+    double dx = (double)hi[0] - lo[0], dy = (double)hi[1] - lo[1], dz = (double)hi[2] - lo[2];
+    return 2.0 * (dx * dy + dy * dz + dz * dx);
+  }
+};
+
+struct BNode {
+  Box box;
+  int32_t left = -1, right = -1;  // children; -1 for a leaf
+  int32_t first = 0, count = 0;   // primitive range in the index array
+};
+
+struct BinaryBuilder {
+  const std::vector<Box>& tbox;
+  const std::vector<float>& cen;  // 3 per triangle
+  std::vector<int32_t> idx;
+  std::vector<BNode> nodes;
+  std::atomic<int32_t> next_node{0};
+  std::atomic<int> free_threads{0};
+  int bins;
+
+  BinaryBuilder(const std::vector<Box>& tb, const std::vector<float>& c, int64_t n, int b, int thr)
+      : tbox(tb), cen(c), idx(n), nodes(std::max<int64_t>(1, 2 * n - 1)), bins(b) {
+    for (int64_t i = 0; i < n; ++i) idx[i] = (int32_t)i;
+    free_threads = std::max(0, thr - 1);
+  }
+
+  int32_t alloc() { return next_node.fetch_add(1); }
+
+  void build(int32_t ni, int32_t first, int32_t count, int depth) {
+    BNode& nd = nodes[ni];
+    nd.first = first;
+    nd.count = count;
+    nd.box.reset();
+    Box cb;
+    cb.reset();
+    for (int32_t i = first; i < first + count; ++i) {
+      int32_t k = idx[i];
+      nd.box.grow(tbox[k]);
+      for (int a = 0; a < 3; ++a) {
+        cb.lo[a] = std::min(cb.lo[a], cen[3 * k + a]);
+        cb.hi[a] = std::max(cb.hi[a], cen[3 * k + a]);
+      }
+    }
+    if (count <= 1) return;
+
+    int32_t mid = -1;
+    int axis = 0;
+    for (int a = 1; a < 3; ++a)
+      if (cb.hi[a] - cb.lo[a] > cb.hi[axis] - cb.lo[axis]) axis = a;
+    bool flat = !(cb.hi[axis] > cb.lo[axis]);
+
+    if (!flat && depth < 48) {
+      // binned SAH over all three axes
+      double best = std::numeric_limits<double>::infinity();
+      int best_axis = -1, best_split = -1;
+      std::vector<Box> bb(bins);
+      std::vector<int32_t> bc(bins);
+      std::vector<double> rarea(bins);
+      std::vector<int32_t> rcnt(bins);
+      for (int a = 0; a < 3; ++a) {
+        double ext = (double)cb.hi[a] - cb.lo[a];
+        if (!(ext > 0)) continue;
+        double sc = bins / ext;
+        for (int b = 0; b < bins; ++b) {
+          bb[b].reset();
+          bc[b] = 0;
+        }
+        for (int32_t i = first; i < first + count; ++i) {
+          int32_t k = idx[i];
+          int b = (int)((cen[3 * k + a] - (double)cb.lo[a]) * sc);
+          b = std::min(bins - 1, std::max(0, b));
+          bb[b].grow(tbox[k]);
+          bc[b]++;
+        }
+        Box acc;
+        acc.reset();
+        int32_t n = 0;
+        for (int b = bins - 1; b > 0; --b) {
+          acc.grow(bb[b]);
+          n += bc[b];
+          rarea[b] = acc.area();
+          rcnt[b] = n;
+        }
+        acc.reset();
+        n = 0;
+        for (int b = 0; b < bins - 1; ++b) {
+          acc.grow(bb[b]);
+          n += bc[b];
+          if (n == 0 || rcnt[b + 1] == 0) continue;
+          double c = acc.area() * n + rarea[b + 1] * rcnt[b + 1];
+          if (c < best) {
+            best = c;
+            best_axis = a;
+            best_split = b + 1;
+          }
+        }
+      }
+      if (best_axis >= 0) {
+        int a = best_axis;
+        double sc = bins / ((double)cb.hi[a] - cb.lo[a]);
+        auto it = std::partition(idx.begin() + first, idx.begin() + first + count, [&](int32_t k) {
+          int b = (int)((cen[3 * k + a] - (double)cb.lo[a]) * sc);
+          b = std::min(bins - 1, std::max(0, b));
+          return b < best_split;
+        });
+        mid = (int32_t)(it - idx.begin());
+        if (mid == first || mid == first + count) mid = -1;
+      }
+    }
+    if (mid < 0) {
+      // object median on the widest centroid axis (also bounds the depth)
+      mid = first + count / 2;
+      std::nth_element(idx.begin() + first, idx.begin() + mid, idx.begin() + first + count,
+                       [&](int32_t p, int32_t q) {
+                         float cp = cen[3 * p + axis], cq = cen[3 * q + axis];
+                         return cp < cq || (cp == cq && p < q);
+                       });
+    }
+    int32_t l = alloc(), r = alloc();
+    nd.left = l;
+    nd.right = r;
+    int32_t nl = mid - first, nr = first + count - mid;
+    bool spawn = false;
+    if (nl > 32768 && nr > 32768) {
+      int f = free_threads.load();
+      while (f > 0 && !free_threads.compare_exchange_weak(f, f - 1)) {
+      }
+      spawn = f > 0;
+    }
+    if (spawn) {
+      std::thread t([&, l, first, nl, depth]() { build(l, first, nl, depth + 1); });
+      build(r, mid, nr, depth + 1);
+      t.join();
+      free_threads.fetch_add(1);
+    } else {
+      build(l, first, nl, depth + 1);
+      build(r, mid, nr, depth + 1);
+    }
+  }
+};
+
+// Give each child the octant code (bit a: 1 = positive side along axis a,
+// relative to the parent's centre) that best matches its position, greedily
+// by decreasing alignment; codes within a node are distinct.
+void assign_codes(const std::vector<Box>& kids, const Box& parent, std::vector<int>& code) {
+  int n = (int)kids.size();
+  double pc[3];
+  for (int a = 0; a < 3; ++a) pc[a] = 0.5 * ((double)parent.lo[a] + parent.hi[a]);
+  struct Cand {
+    double s;
+    int k, c;
+  };
+  std::vector<Cand> cands;
+  for (int k = 0; k < n; ++k) {
+    for (int c = 0; c < 8; ++c) {
+      double s = 0;
+      for (int a = 0; a < 3; ++a) {
+        double off = 0.5 * ((double)kids[k].lo[a] + kids[k].hi[a]) - pc[a];
+        s += ((c >> a) & 1) ? off : -off;
+      }
+      cands.push_back({s, k, c});
+    }
+  }
+  std::stable_sort(cands.begin(), cands.end(), [](const Cand& x, const Cand& y) { return x.s > y.s; });
+  code.assign(n, -1);
+  bool used[8] = {false};
+  int left = n;
+  for (const Cand& c : cands) {
+    if (!left) break;
+    if (code[c.k] >= 0 || used[c.c]) continue;
+    code[c.k] = c.c;
+    used[c.c] = true;
+    --left;
+  }
+}
+
+inline float decode(uint8_t q, float scale, float p) { return std::fmaf((float)q, scale, p); }
+
+}  // namespace
+
+int build_bvh(const float* V, int64_t nv, const int32_t* T, int64_t nt, int width, int bins,
+              int threads, HostBVH* out, std::string* err) {
+  auto t0 = std::chrono::steady_clock::now();
+  if (width != 4 && width != 8) {
+    *err = "width must be 4 or 8";
+    return 1;
+  }
+  if (nt < 1 || nv < 1) {
+    *err = "empty mesh";
+    return 1;
+  }
+  if (nt > (int64_t)1 << 30) {
+    *err = "too many triangles (max 2^30)";
+    return 1;
+  }
+  if (bins <= 1) bins = 32;
+  if (threads <= 0) threads = (int)std::max(1u, std::thread::hardware_concurrency());
+
+  std::vector<Box> tbox(nt);
+  std::vector<float> cen(3 * nt);
+  Box scene;
+  scene.reset();
+  double M = 1.0;
+  for (int64_t k = 0; k < nt; ++k) {
+    Box b;
+    b.reset();
+    for (int i = 0; i < 3; ++i) {
+      int32_t vi = T[3 * k + i];
+      if (vi < 0 || vi >= nv) {
+        *err = "triangle " + std::to_string(k) + " has a vertex id out of range";
+        return 1;
+      }
+      for (int a = 0; a < 3; ++a) {
+        float x = V[3 * (int64_t)vi + a];
+        if (!std::isfinite(x)) {
+          *err = "non-finite vertex coordinate (vertex " + std::to_string(vi) + ")";
+          return 1;
+        }
+        b.lo[a] = std::min(b.lo[a], x);
+        b.hi[a] = std::max(b.hi[a], x);
+        M = std::max(M, (double)std::fabs(x));
+      }
+    }
+    tbox[k] = b;
+    for (int a = 0; a < 3; ++a) cen[3 * k + a] = 0.5f * b.lo[a] + 0.5f * b.hi[a];
+    scene.grow(b);
+  }
+  // Outward margin on every quantized box: covers the float32 rounding of
+  // the traversal's slab test for ray origins with coordinates up to M.
+  const double margin = std::ldexp(M, -17);
+
+  BinaryBuilder bb(tbox, cen, nt, bins, threads);
+  int32_t root = bb.alloc();
+  bb.build(root, 0, (int32_t)nt, 0);
+  const std::vector<BNode>& bn = bb.nodes;
+  const std::vector<int32_t>& idx = bb.idx;
+
+  // ---- greedy collapse to W-wide nodes, breadth first --------------------
+  const int W = width;
+  const int S = node_stride(W);
+  std::vector<int32_t> wsrc;   // binary node of each wide node
+  std::vector<int> wdepth;
+  wsrc.reserve(nt / 2 + 1);
+  wsrc.push_back(root);
+  wdepth.push_back(1);
+  std::vector<uint8_t> nodes;
+  nodes.reserve((size_t)(nt / 2 + 1) * S);
+  std::vector<float> otris;
+  otris.reserve((size_t)nt * kTriFloats);
+  double root_area = std::max(1e-30, bn[root].box.area());
+  double sah = 0.0;
+  int max_depth = 1;
+
+  for (size_t w = 0; w < wsrc.size(); ++w) {
+    int32_t b = wsrc[w];
+    std::vector<int32_t> kids;
+    if (bn[b].count <= kMaxLeafTris && w == 0) {
+      kids.push_back(b);  // tiny scene: the root holds one leaf
+    } else {
+      kids.push_back(bn[b].left);
+      kids.push_back(bn[b].right);
+      while ((int)kids.size() < W) {
+        int best = -1;
+        double ba = -1.0;
+        for (int i = 0; i < (int)kids.size(); ++i) {
+          const BNode& c = bn[kids[i]];
+          if (c.left < 0) continue;
+          double a = c.box.area();
+          if (a > ba) {
+            ba = a;
+            best = i;
+          }
+        }
+        if (best < 0) break;
+        int32_t c = kids[best];
+        kids[best] = bn[c].left;
+        kids.push_back(bn[c].right);
+      }
+    }
+    int n = (int)kids.size();
+    std::vector<Box> kb(n);
+    for (int i = 0; i < n; ++i) kb[i] = bn[kids[i]].box;
+    std::vector<int> code;
+    assign_codes(kb, bn[b].box, code);
+    // positions in increasing code
+    std::vector<int> pos(n);
+    for (int i = 0; i < n; ++i) pos[i] = i;
+    std::sort(pos.begin(), pos.end(), [&](int x, int y) { return code[x] < code[y]; });
+
+    sah += bn[b].box.area() / root_area;  // one node visit
+    uint32_t imask = 0;
+    int32_t child_base = (int32_t)wsrc.size();
+    int64_t tri_base = (int64_t)(otris.size() / kTriFloats);
+    uint8_t meta[8] = {0};
+    int tri_off = 0;
+    for (int j = 0; j < n; ++j) {
+      int i = pos[j];
+      const BNode& c = bn[kids[i]];
+      bool inner = c.count > kMaxLeafTris;
+      if (inner) {
+        imask |= 1u << code[i];
+        meta[j] = (uint8_t)((1u << 5) | (24u + (uint32_t)code[i]));
+        wsrc.push_back(kids[i]);
+        wdepth.push_back(wdepth[w] + 1);
+        max_depth = std::max(max_depth, wdepth[w] + 1);
+      } else {
+        int cnt = c.count;
+        meta[j] = (uint8_t)((((1u << cnt) - 1u) << 5) | (uint32_t)tri_off);
+        for (int t = 0; t < cnt; ++t) {
+          int32_t k = idx[c.first + t];
+          for (int v = 0; v < 3; ++v) {
+            int64_t vi = T[3 * (int64_t)k + v];
+            otris.push_back(V[3 * vi + 0]);
+            otris.push_back(V[3 * vi + 1]);
+            otris.push_back(V[3 * vi + 2]);
+            float w4 = 0.f;
+            if (v == 0) std::memcpy(&w4, &k, 4);
+            otris.push_back(w4);
+          }
+        }
+        tri_off += cnt;
+        sah += c.box.area() / root_area * cnt;
+      }
+    }
+    if (tri_off > kMaxNodeTris) {
+      *err = "internal error: node holds more than 24 triangles";
+      return 1;
+    }
+
+    // ---- quantize the child boxes ----------------------------------------
+    float p[3];
+    int e[3];
+    uint8_t q[6][8];
+    std::memset(q, 0, sizeof(q));
+    for (int a = 0; a < 3; ++a) {
+      double lo_t = std::numeric_limits<double>::infinity(), hi_t = -lo_t;
+      for (int i = 0; i < n; ++i) {
+        lo_t = std::min(lo_t, (double)kb[i].lo[a] - margin);
+        hi_t = std::max(hi_t, (double)kb[i].hi[a] + margin);
+      }
+      float pa = (float)lo_t;
+      if ((double)pa > lo_t) pa = std::nextafterf(pa, -std::numeric_limits<float>::infinity());
+      p[a] = pa;
+      double ext = hi_t - (double)pa;
+      int k = (int)std::ceil(std::log2(ext / 255.0));
+      k = std::max(k, -126);
+      for (;; ++k) {
+        if (k > 127) {
+          *err = "scene extent too large to quantize";
+          return 1;
+        }
+        float scale = std::ldexp(1.0f, k);
+        bool ok = true;
+        for (int j = 0; j < n && ok; ++j) {
+          int i = pos[j];
+          double lt = (double)kb[i].lo[a] - margin, ht = (double)kb[i].hi[a] + margin;
+          double ql = std::floor((lt - (double)pa) / scale);
+          double qh = std::ceil((ht - (double)pa) / scale);
+          ql = std::max(0.0, std::min(255.0, ql));
+          while (ql > 0 && (double)decode((uint8_t)ql, scale, pa) > lt) ql -= 1.0;
+          if (qh < 0) qh = 0;
+          while (qh <= 255 && (double)decode((uint8_t)std::min(qh, 255.0), scale, pa) < ht) qh += 1.0;
+          if (qh > 255) {
+            ok = false;
+            break;
+          }
+          q[a][j] = (uint8_t)ql;
+          q[3 + a][j] = (uint8_t)qh;
+        }
+        if (ok) break;
+      }
+      e[a] = k + 127;
+    }
+
+    size_t off = nodes.size();
+    nodes.resize(off + S, 0);
+    uint8_t* rec = nodes.data() + off;
+    std::memcpy(rec + 0, &p[0], 4);
+    std::memcpy(rec + 4, &p[1], 4);
+    std::memcpy(rec + 8, &p[2], 4);
+    uint32_t packed = (uint32_t)e[0] | ((uint32_t)e[1] << 8) | ((uint32_t)e[2] << 16) | (imask << 24);
+    std::memcpy(rec + 12, &packed, 4);
+    uint32_t cb = (uint32_t)child_base, tb = (uint32_t)tri_base;
+    std::memcpy(rec + 16, &cb, 4);
+    std::memcpy(rec + 20, &tb, 4);
+    std::memcpy(rec + 24, meta, W);
+    for (int r = 0; r < 6; ++r) std::memcpy(rec + 32 + r * W, q[r], W);
+  }
+
+  if (max_depth > kMaxWideDepth) {
+    *err = "BVH too deep (" + std::to_string(max_depth) + " levels > " +
+           std::to_string(kMaxWideDepth) + ")";
+    return 1;
+  }
+  out->width = W;
+  out->stride = S;
+  out->n_tris = nt;
+  out->n_nodes = (int64_t)wsrc.size();
+  out->depth = max_depth;
+  out->margin = (float)margin;
+  out->sah_cost = sah;
+  for (int a = 0; a < 3; ++a) {
+    out->lo[a] = scene.lo[a];
+    out->hi[a] = scene.hi[a];
+  }
+  out->nodes.swap(nodes);
+  out->tris.swap(otris);
+  out->build_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return 0;
+}
+
+int64_t verify_bvh(const HostBVH& b, std::string* first_error) {
+  const int W = b.width, S = b.stride;
+  const int64_t N = b.n_nodes;
+  int64_t bad = 0;
+  auto fail = [&](const std::string& m) {
+    if (bad == 0 && first_error) *first_error = m;
+    ++bad;
+  };
+  // content box of every node, children before parents (children have
+  // larger indices than their parent in breadth-first order)
+  std::vector<Box> content(N);
+  std::vector<int64_t> tri_seen(b.n_tris, 0);
+  const double m = b.margin;
+  for (int64_t ni = N - 1; ni >= 0; --ni) {
+    const uint8_t* rec = b.nodes.data() + ni * S;
+    float p[3];
+    uint32_t packed, cbase, tbase;
+    std::memcpy(p, rec, 12);
+    std::memcpy(&packed, rec + 12, 4);
+    std::memcpy(&cbase, rec + 16, 4);
+    std::memcpy(&tbase, rec + 20, 4);
+    uint32_t imask = packed >> 24;
+    float scale[3];
+    for (int a = 0; a < 3; ++a) {
+      uint32_t bits = ((packed >> (8 * a)) & 0xFFu) << 23;
+      std::memcpy(&scale[a], &bits, 4);
+    }
+    Box all;
+    all.reset();
+    for (int j = 0; j < W; ++j) {
+      uint8_t mt = rec[24 + j];
+      if (mt == 0) continue;
+      Box cbx;
+      cbx.reset();
+      if ((mt & 0x18) == 0x18) {
+        int c = (mt & 31) - 24;
+        if (!((imask >> c) & 1u)) fail("meta/imask mismatch at node " + std::to_string(ni));
+        int64_t child = (int64_t)cbase + __builtin_popcount(imask & ((1u << c) - 1u));
+        if (child <= ni || child >= N) {
+          fail("child index out of range at node " + std::to_string(ni));
+          continue;
+        }
+        cbx = content[child];
+      } else {
+        int off = mt & 31, cnt = __builtin_popcount(mt >> 5);
+        for (int t = 0; t < cnt; ++t) {
+          int64_t ti = (int64_t)tbase + off + t;
+          if (ti >= b.n_tris) {
+            fail("triangle index out of range at node " + std::to_string(ni));
+            continue;
+          }
+          const float* tr = b.tris.data() + ti * kTriFloats;
+          int32_t id;
+          std::memcpy(&id, tr + 3, 4);
+          if (id < 0 || id >= b.n_tris) fail("bad triangle id");
+          else tri_seen[id]++;
+          for (int v = 0; v < 3; ++v)
+            for (int a = 0; a < 3; ++a) {
+              cbx.lo[a] = std::min(cbx.lo[a], tr[4 * v + a]);
+              cbx.hi[a] = std::max(cbx.hi[a], tr[4 * v + a]);
+            }
+        }
+      }
+      for (int a = 0; a < 3; ++a) {
+        float dlo = decode(rec[32 + a * W + j], scale[a], p[a]);
+        float dhi = decode(rec[32 + (3 + a) * W + j], scale[a], p[a]);
+        if (!((double)dlo <= (double)cbx.lo[a] - m) || !((double)dhi >= (double)cbx.hi[a] + m))
+          fail("child box does not contain its content (node " + std::to_string(ni) + ", pos " +
+               std::to_string(j) + ", axis " + std::to_string(a) + ")");
+      }
+      all.grow(cbx);
+    }
+    content[ni] = all;
+  }
+  for (int64_t k = 0; k < b.n_tris; ++k)
+    if (tri_seen[k] != 1) {
+      fail("triangle " + std::to_string(k) + " referenced " + std::to_string(tri_seen[k]) +
+           " times");
+      break;
+    }
+  return bad;
+}
+
+}  // namespace fgl

@@ -1,0 +1,113 @@
+// Internal layouts shared by the host BVH builder, the C-ABI layer and the
+// CUDA kernels.  Nothing here is part of the public interface (fgl.h).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#ifdef __CUDACC__
+#define FGL_HD __host__ __device__
+#else
+#define FGL_HD
+#endif
+
+namespace fgl {
+
+// ---------------------------------------------------------------------------
+// Wide BVH node record (W children, W in {4, 8}); 16-byte aligned so the
+// traversal reads it with 16-byte vector loads.
+//
+//   bytes  0..15 : float px, py, pz          quantization origin (node corner)
+//                  uint32  ex | ey<<8 | ez<<16 | imask<<24
+//                          e* = biased float exponent of the per-axis scale
+//                          2^(e-127); imask bit c set when the child with
+//                          octant code c is an internal node
+//   bytes 16..31 : uint32 child_base         node index of the first internal child
+//                  uint32 tri_base           index of the node's first leaf triangle
+//                  uint8  meta[W] (+pad)     per child position:
+//                     0                       empty position
+//                     0b001_11ccc             internal child with octant code ccc
+//                     0bNNN_ooooo (ooooo<24)  leaf: NNN = unary triangle count
+//                                             (001, 011, 111), ooooo = offset of
+//                                             its first triangle from tri_base
+//   bytes 32..   : uint8 q[6][W]             child boxes in units of the scale:
+//                                             lo_x, lo_y, lo_z, hi_x, hi_y, hi_z
+//
+// Decoding a box coordinate is fmaf(q, 2^(e-127), p) in float32; the builder
+// rounds outward and adds `margin` on every side, and verifies the decoded
+// boxes with exactly that arithmetic.
+//
+// Internal children of a node are stored contiguously from child_base in
+// increasing octant code; child index = child_base + popc(imask & ((1<<c)-1)).
+// A ray with direction-sign bits `oct` (bit a set when d_a < 0) visits
+// children in increasing (c ^ oct), which approximates near-to-far order
+// because the builder gives each child the code of the octant it sits in
+// relative to its siblings.
+// ---------------------------------------------------------------------------
+constexpr int kMaxLeafTris = 3;
+constexpr int kMaxNodeTris = 24;
+
+FGL_HD constexpr int node_stride(int width) { return width == 8 ? 80 : 64; }
+
+// Leaf triangle record: 3 x float4 = 48 bytes
+//   {v0.x, v0.y, v0.z, id as int bits}, {v1.xyz, 0}, {v2.xyz, 0}
+constexpr int kTriFloats = 12;
+
+// Traversal stack: `stack_smem` entries in shared memory, the rest of the
+// stack in a per-thread local array of kStackLocal entries.  A ray pushes at
+// most two entries per level of the wide tree, so the builder rejects trees
+// deeper than kMaxWideDepth.
+constexpr int kStackLocal = 64;
+constexpr int kMaxWideDepth = 30;
+
+struct HostBVH {
+  int width = 8;
+  int stride = 80;
+  int64_t n_tris = 0;
+  int64_t n_nodes = 0;
+  int depth = 0;
+  float margin = 0.f;
+  double sah_cost = 0.0;
+  double build_ms = 0.0;
+  float lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  std::vector<uint8_t> nodes;  // n_nodes * stride
+  std::vector<float> tris;     // n_tris * kTriFloats
+};
+
+// Host build (bvh_build.cpp).  Returns 0 on success, else writes *err.
+int build_bvh(const float* verts, int64_t nv, const int32_t* tris, int64_t nt, int width,
+              int bins, int threads, HostBVH* out, std::string* err);
+// Containment / structure check with the float32 decode arithmetic; returns
+// the number of violations.
+int64_t verify_bvh(const HostBVH& b, std::string* first_error);
+
+// ---------------------------------------------------------------------------
+// Work description for the kernels
+// ---------------------------------------------------------------------------
+struct alignas(16) ItemDesc {
+  const void* nodes;     // wide node records
+  const void* tris;      // leaf triangle records
+  const void* dirs;      // float4 per ray in tile order: xyz + beam index bits
+  const float* poses;    // [n_env][12]
+  float* out_range;
+  int32_t* out_tri;
+  int64_t pk_begin;      // first packet of this item in the batch
+  int32_t n_env;
+  int32_t n_rays;
+  int32_t pk_per_env;    // packets per environment
+  float max_range;
+  int32_t pad[2];
+};
+static_assert(sizeof(ItemDesc) == 80, "ItemDesc layout");
+
+struct alignas(16) BatchHeader {
+  unsigned long long head;   // next packet to hand out (atomic)
+  int64_t n_packets;
+  int32_t n_items;
+  int32_t packet_rays;
+  int32_t pad[10];
+};
+static_assert(sizeof(BatchHeader) == 64, "BatchHeader layout");
+
+}  // namespace fgl

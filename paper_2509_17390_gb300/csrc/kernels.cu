@@ -1,0 +1,272 @@
+// Kernels and their launchers.
+//
+//   k_plain      : one thread per ray of a single (scene, sensor, poses) item
+//                  -- the paper's "one thread per beam" form (Sec. IV-C).
+//   k_persistent : a grid of (SM count x resident blocks) that drains a device
+//                  work queue of ray packets spanning many items; a warp
+//                  pulls a new packet when its current one is used up, and
+//                  hands fresh rays to lanes whose ray has finished once
+//                  enough lanes are idle, so warps stay full while the
+//                  per-ray work (eq. cost(r_j)) varies.
+//   k_world_rays : debug export of the float32 rays of eq. r_j.
+#include <cuda_runtime.h>
+
+#include "kernels.h"
+#include "trace.cuh"
+
+namespace fgl {
+
+__device__ unsigned int g_status;
+__device__ unsigned long long g_counters[3];  // rays, node visits, triangle tests
+
+namespace {
+
+template <bool COUNT>
+__device__ __forceinline__ void flush_counters(uint32_t rays, uint32_t nodes, uint32_t tris) {
+  if (!COUNT) return;
+  const unsigned full = __activemask();
+  unsigned long long r = __reduce_add_sync(full, rays);
+  unsigned long long n = __reduce_add_sync(full, nodes);
+  unsigned long long t = __reduce_add_sync(full, tris);
+  if ((threadIdx.x & 31) == (__ffs(full) - 1)) {
+    atomicAdd(&g_counters[0], r);
+    atomicAdd(&g_counters[1], n);
+    atomicAdd(&g_counters[2], t);
+  }
+}
+
+__device__ __forceinline__ int postpone_threshold(int pct) {
+  if (pct <= 0) return 0;
+  return (__popc(__activemask()) * pct + 99) / 100;
+}
+
+template <int W, bool COUNT>
+__global__ void __launch_bounds__(512) k_plain(const ItemDesc it, int sdepth, int postpone_pct) {
+  extern __shared__ uint2 smem_stack[];
+  const int64_t total = (int64_t)it.n_env * it.n_rays;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= total) return;
+  const int env = (int)(gid / it.n_rays);
+  const int j = (int)(gid - (int64_t)env * it.n_rays);
+  const float4 ds = __ldg((const float4*)it.dirs + j);
+  float ox, oy, oz, dx, dy, dz;
+  dev::world_ray(it.poses + 12 * (int64_t)env, ds, ox, oy, oz, dx, dy, dz);
+  dev::Tracer<W, COUNT> tr;
+  dev::setup_ray(tr.r, ox, oy, oz, dx, dy, dz);
+  tr.start(it.nodes, it.tris, it.max_range);
+  uint2 ls[kStackLocal];
+  uint2* ss = smem_stack + threadIdx.x;
+  for (;;) {
+    const int pl = postpone_threshold(postpone_pct);
+    if (tr.step(ss, blockDim.x, sdepth, ls, pl, &g_status)) break;
+  }
+  float rg;
+  int32_t id;
+  tr.result(rg, id);
+  const int64_t o = (int64_t)env * it.n_rays + __float_as_int(ds.w);
+  it.out_range[o] = rg;
+  it.out_tri[o] = id;
+  if (COUNT) flush_counters<COUNT>(1u, tr.n_nodes, tr.n_tris);
+}
+
+template <int W, bool COUNT>
+__global__ void __launch_bounds__(512) k_persistent(BatchHeader* __restrict__ hdr,
+                                                    const ItemDesc* __restrict__ items, int sdepth,
+                                                    int refill_min, int postpone_pct) {
+  extern __shared__ uint2 smem_stack[];
+  const unsigned FULL = 0xFFFFFFFFu;
+  const int lane = threadIdx.x & 31;
+  const int64_t n_packets = hdr->n_packets;
+  const int n_items = hdr->n_items;
+  const int P = hdr->packet_rays;
+  uint2 ls[kStackLocal];
+  uint2* ss = smem_stack + threadIdx.x;
+
+  // warp-uniform packet cursor
+  int pk_item = 0, pk_env = 0, pk_next = 0, pk_end = 0;
+  bool drained = false;
+  // lane state
+  dev::Tracer<W, COUNT> tr;
+  bool active = false;
+  float* out_r = nullptr;
+  int32_t* out_t = nullptr;
+  uint32_t c_rays = 0, c_nodes = 0, c_tris = 0;
+
+  for (;;) {
+    unsigned idle = __ballot_sync(FULL, !active);
+    if (!drained && (idle == FULL || __popc(idle) >= refill_min)) {
+      while (idle) {
+        if (pk_next >= pk_end) {
+          unsigned long long p = 0;
+          if (lane == 0) p = atomicAdd(&hdr->head, 1ull);
+          p = __shfl_sync(FULL, p, 0);
+          if ((int64_t)p >= n_packets) {
+            drained = true;
+            break;
+          }
+          int lo = 0, hi = n_items - 1;
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (items[mid].pk_begin <= (int64_t)p) lo = mid;
+            else hi = mid - 1;
+          }
+          const int64_t local = (int64_t)p - items[lo].pk_begin;
+          const int ppe = items[lo].pk_per_env;
+          pk_item = lo;
+          pk_env = (int)(local / ppe);
+          const int chunk = (int)(local - (int64_t)pk_env * ppe);
+          pk_next = chunk * P;
+          pk_end = min(pk_next + P, items[lo].n_rays);
+        }
+        const int avail = pk_end - pk_next;
+        const int rank = __popc(idle & ((1u << lane) - 1u));
+        if (((idle >> lane) & 1u) && rank < avail) {
+          const ItemDesc& it = items[pk_item];
+          const float4 ds = __ldg((const float4*)it.dirs + pk_next + rank);
+          float ox, oy, oz, dx, dy, dz;
+          dev::world_ray(it.poses + 12 * (int64_t)pk_env, ds, ox, oy, oz, dx, dy, dz);
+          dev::setup_ray(tr.r, ox, oy, oz, dx, dy, dz);
+          tr.start(it.nodes, it.tris, it.max_range);
+          const int64_t o = (int64_t)pk_env * it.n_rays + __float_as_int(ds.w);
+          out_r = it.out_range + o;
+          out_t = it.out_tri + o;
+          active = true;
+        }
+        pk_next += min(__popc(idle), avail);
+        idle = __ballot_sync(FULL, !active);
+      }
+    }
+    const unsigned act = __ballot_sync(FULL, active);
+    if (act == 0) {
+      if (drained) break;
+      continue;
+    }
+    if (active) {
+      const int pl = postpone_pct > 0 ? (__popc(act) * postpone_pct + 99) / 100 : 0;
+      if (tr.step(ss, blockDim.x, sdepth, ls, pl, &g_status)) {
+        float rg;
+        int32_t id;
+        tr.result(rg, id);
+        *out_r = rg;
+        *out_t = id;
+        active = false;
+        if (COUNT) {
+          ++c_rays;
+          c_nodes += tr.n_nodes;
+          c_tris += tr.n_tris;
+        }
+      }
+    }
+  }
+  if (COUNT) flush_counters<COUNT>(c_rays, c_nodes, c_tris);
+}
+
+__global__ void k_world_rays(const float4* __restrict__ dirs, const float* __restrict__ poses,
+                             int n_env, int n_rays, float* __restrict__ out_o,
+                             float* __restrict__ out_d) {
+  const int64_t total = (int64_t)n_env * n_rays;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= total) return;
+  const int env = (int)(gid / n_rays);
+  const int j = (int)(gid - (int64_t)env * n_rays);
+  const float4 ds = dirs[j];
+  float ox, oy, oz, dx, dy, dz;
+  dev::world_ray(poses + 12 * (int64_t)env, ds, ox, oy, oz, dx, dy, dz);
+  const int64_t o = 3 * ((int64_t)env * n_rays + __float_as_int(ds.w));
+  out_o[o] = ox;
+  out_o[o + 1] = oy;
+  out_o[o + 2] = oz;
+  out_d[o] = dx;
+  out_d[o + 1] = dy;
+  out_d[o + 2] = dz;
+}
+
+template <int W, bool COUNT>
+void* plain_fn() {
+  return (void*)k_plain<W, COUNT>;
+}
+template <int W, bool COUNT>
+void* persistent_fn() {
+  return (void*)k_persistent<W, COUNT>;
+}
+
+void* pick_plain(int W, bool count) {
+  if (W == 8) return count ? plain_fn<8, true>() : plain_fn<8, false>();
+  return count ? plain_fn<4, true>() : plain_fn<4, false>();
+}
+void* pick_persistent(int W, bool count) {
+  if (W == 8) return count ? persistent_fn<8, true>() : persistent_fn<8, false>();
+  return count ? persistent_fn<4, true>() : persistent_fn<4, false>();
+}
+
+}  // namespace
+
+size_t stack_smem_bytes(int block, int sdepth) { return (size_t)block * (size_t)sdepth * sizeof(uint2); }
+
+cudaError_t launch_plain(int W, bool count, const ItemDesc& it, int block, int sdepth,
+                         int postpone_pct, cudaStream_t s) {
+  const int64_t total = (int64_t)it.n_env * it.n_rays;
+  if (total == 0) return cudaSuccess;
+  const int64_t grid = (total + block - 1) / block;
+  const size_t smem = stack_smem_bytes(block, sdepth);
+  void* fn = pick_plain(W, count);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  ItemDesc arg = it;
+  void* args[] = {&arg, &sdepth, &postpone_pct};
+  return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(block), args, smem, s);
+}
+
+int persistent_blocks_per_sm(int W, bool count, int block, int sdepth) {
+  void* fn = pick_persistent(W, count);
+  const size_t smem = stack_smem_bytes(block, sdepth);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, block, smem) != cudaSuccess) return 1;
+  return n > 0 ? n : 1;
+}
+
+cudaError_t launch_persistent(int W, bool count, void* scratch, int grid, int block, int sdepth,
+                              int refill_min, int postpone_pct, cudaStream_t s) {
+  void* fn = pick_persistent(W, count);
+  const size_t smem = stack_smem_bytes(block, sdepth);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  BatchHeader* hdr = (BatchHeader*)scratch;
+  const ItemDesc* items = (const ItemDesc*)((char*)scratch + sizeof(BatchHeader));
+  void* args[] = {&hdr, &items, &sdepth, &refill_min, &postpone_pct};
+  return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, s);
+}
+
+cudaError_t launch_world_rays(const void* dirs, const float* poses, int n_env, int n_rays,
+                              float* out_o, float* out_d, cudaStream_t s) {
+  const int64_t total = (int64_t)n_env * n_rays;
+  if (total == 0) return cudaSuccess;
+  const int block = 256;
+  k_world_rays<<<(unsigned)((total + block - 1) / block), block, 0, s>>>(
+      (const float4*)dirs, poses, n_env, n_rays, out_o, out_d);
+  return cudaGetLastError();
+}
+
+cudaError_t read_and_clear_status(unsigned* st) {
+  cudaError_t e = cudaMemcpyFromSymbol(st, g_status, sizeof(unsigned));
+  if (e != cudaSuccess) return e;
+  if (*st) {
+    unsigned z = 0;
+    e = cudaMemcpyToSymbol(g_status, &z, sizeof(unsigned));
+  }
+  return e;
+}
+
+cudaError_t read_and_clear_counters(unsigned long long* c3) {
+  cudaError_t e = cudaMemcpyFromSymbol(c3, g_counters, 3 * sizeof(unsigned long long));
+  if (e != cudaSuccess) return e;
+  unsigned long long z[3] = {0, 0, 0};
+  return cudaMemcpyToSymbol(g_counters, z, sizeof(z));
+}
+
+}  // namespace fgl

@@ -1,0 +1,33 @@
+// Launchers of the ray-casting kernels (kernels.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "fgl_internal.h"
+
+namespace fgl {
+
+// Dynamic shared memory of the traversal stacks of one block.
+size_t stack_smem_bytes(int block, int sdepth);
+
+// One thread per ray of one item (grid = ceil(n_env * n_rays / block)).
+cudaError_t launch_plain(int W, bool count, const ItemDesc& it, int block, int sdepth,
+                         int postpone_pct, cudaStream_t s);
+
+// Resident blocks per SM of the persistent kernel for this configuration.
+int persistent_blocks_per_sm(int W, bool count, int block, int sdepth);
+
+// Persistent kernel over the work queue in `scratch`: a BatchHeader
+// followed by n_items ItemDesc records (device memory).
+cudaError_t launch_persistent(int W, bool count, void* scratch, int grid, int block, int sdepth,
+                              int refill_min, int postpone_pct, cudaStream_t s);
+
+// Debug export of world rays (beam order).
+cudaError_t launch_world_rays(const void* dirs, const float* poses, int n_env, int n_rays,
+                              float* out_o, float* out_d, cudaStream_t s);
+
+// Device-side error word (bit 0: traversal stack overflow) and work counters.
+cudaError_t read_and_clear_status(unsigned* st);
+cudaError_t read_and_clear_counters(unsigned long long* c3);
+
+}  // namespace fgl

@@ -1,0 +1,308 @@
+// Device side of the ray caster: ray generation (eq. r_j), wide-BVH stack
+// traversal pruned by the best-so-far t, watertight float32 ray/triangle
+// tests, and the nearest-hit reduction of eq. t_j* (paper Sec. IV-C).
+//
+// Result determinism: every (ray, triangle) pair is evaluated with the same
+// float32 operations wherever it happens, and the kept hit is the
+// lexicographic minimum of (t, triangle id); boxes are culled only when their
+// entry exceeds the best t strictly, and quantized boxes are conservative
+// with a margin, so no variant (width, stack split, packet shape, postponing,
+// batching) can change a result.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fgl_internal.h"
+
+namespace fgl {
+namespace dev {
+
+constexpr int32_t kNoHit = 0x7FFFFFFF;
+
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+
+// Byte `sel & 3` of `w` as an exact float: the byte is placed under the
+// exponent of 2^23 (giving 2^23 + b) and 2^23 is subtracted.
+__device__ __forceinline__ float byte_f(uint32_t w, uint32_t sel) {
+  return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7440u | sel)) - 8388608.0f;
+}
+
+__device__ __forceinline__ float sel3(float x, float y, float z, uint32_t k) {
+  return k == 0 ? x : (k == 1 ? y : z);
+}
+
+__device__ __forceinline__ uint4 ldg4(const uint4* p) { return __ldg(p); }
+__device__ __forceinline__ float4 ldg4f(const float4* p) { return __ldg(p); }
+
+// Per-ray constants.
+struct Ray {
+  float ox, oy, oz;   // origin x_s = t_s
+  float ix, iy, iz;   // reciprocal direction, |d_a| clamped to >= 1e-30
+  float Sx, Sy, Sz;   // shear constants of the watertight test
+  uint32_t k;         // kx | ky << 2 | kz << 4
+  uint32_t oct;       // bit a set when the direction is negative along a
+};
+
+// eq. r_j: o = t, d = R d_s with every product and sum rounded separately,
+// row i as ((R[i][0]*d0) + (R[i][1]*d1)) + (R[i][2]*d2).
+__device__ __forceinline__ void world_ray(const float* __restrict__ P, float4 ds, float& ox,
+                                          float& oy, float& oz, float& dx, float& dy, float& dz) {
+  float p[12];
+#pragma unroll
+  for (int i = 0; i < 12; ++i) p[i] = __ldg(P + i);
+  dx = __fadd_rn(__fadd_rn(__fmul_rn(p[0], ds.x), __fmul_rn(p[1], ds.y)), __fmul_rn(p[2], ds.z));
+  dy = __fadd_rn(__fadd_rn(__fmul_rn(p[4], ds.x), __fmul_rn(p[5], ds.y)), __fmul_rn(p[6], ds.z));
+  dz = __fadd_rn(__fadd_rn(__fmul_rn(p[8], ds.x), __fmul_rn(p[9], ds.y)), __fmul_rn(p[10], ds.z));
+  ox = p[3];
+  oy = p[7];
+  oz = p[11];
+}
+
+__device__ __forceinline__ float safe_rcp(float d) {
+  const float eps = 1e-30f;
+  float a = fabsf(d) < eps ? copysignf(eps, d) : d;
+  return __frcp_rn(a);
+}
+
+__device__ __forceinline__ void setup_ray(Ray& r, float ox, float oy, float oz, float dx, float dy,
+                                          float dz) {
+  r.ox = ox;
+  r.oy = oy;
+  r.oz = oz;
+  r.ix = safe_rcp(dx);
+  r.iy = safe_rcp(dy);
+  r.iz = safe_rcp(dz);
+  r.oct = (r.ix < 0.f ? 1u : 0u) | (r.iy < 0.f ? 2u : 0u) | (r.iz < 0.f ? 4u : 0u);
+  // Watertight test set-up (Woop, Benthin & Wald 2013): kz = dominant axis,
+  // (kx, ky) the other two in cyclic order, swapped when d[kz] < 0 so the
+  // projected winding is preserved.
+  float ax = fabsf(dx), ay = fabsf(dy), az = fabsf(dz);
+  uint32_t kz = (ax >= ay) ? (ax >= az ? 0u : 2u) : (ay >= az ? 1u : 2u);
+  uint32_t kx = kz == 2u ? 0u : kz + 1u;
+  uint32_t ky = kx == 2u ? 0u : kx + 1u;
+  float dkz = sel3(dx, dy, dz, kz);
+  if (dkz < 0.f) {
+    uint32_t t = kx;
+    kx = ky;
+    ky = t;
+  }
+  r.k = kx | (ky << 2) | (kz << 4);
+  r.Sx = __fdiv_rn(sel3(dx, dy, dz, kx), dkz);
+  r.Sy = __fdiv_rn(sel3(dx, dy, dz, ky), dkz);
+  r.Sz = __frcp_rn(dkz);
+}
+
+// Watertight float32 ray/triangle test (Woop, Benthin & Wald 2013, JCGT 2(1)):
+// translate the vertices to the ray origin, shear so the ray is the +z axis
+// of the (kx, ky, kz) frame, and take the signs of the three 2D edge
+// functions, falling back to float64 for an exactly-zero edge function.
+// Returns the hit t (> 0) or a negative value for a miss; `tbest` only
+// prunes hits that certainly lie beyond it.
+__device__ __forceinline__ float tri_hit(const Ray& r, float4 a, float4 b, float4 c, float tbest) {
+  const uint32_t kx = r.k & 3u, ky = (r.k >> 2) & 3u, kz = (r.k >> 4) & 3u;
+  float A0 = __fsub_rn(a.x, r.ox), A1 = __fsub_rn(a.y, r.oy), A2 = __fsub_rn(a.z, r.oz);
+  float B0 = __fsub_rn(b.x, r.ox), B1 = __fsub_rn(b.y, r.oy), B2 = __fsub_rn(b.z, r.oz);
+  float C0 = __fsub_rn(c.x, r.ox), C1 = __fsub_rn(c.y, r.oy), C2 = __fsub_rn(c.z, r.oz);
+  float Akz = sel3(A0, A1, A2, kz), Bkz = sel3(B0, B1, B2, kz), Ckz = sel3(C0, C1, C2, kz);
+  float Ax = __fsub_rn(sel3(A0, A1, A2, kx), __fmul_rn(r.Sx, Akz));
+  float Ay = __fsub_rn(sel3(A0, A1, A2, ky), __fmul_rn(r.Sy, Akz));
+  float Bx = __fsub_rn(sel3(B0, B1, B2, kx), __fmul_rn(r.Sx, Bkz));
+  float By = __fsub_rn(sel3(B0, B1, B2, ky), __fmul_rn(r.Sy, Bkz));
+  float Cx = __fsub_rn(sel3(C0, C1, C2, kx), __fmul_rn(r.Sx, Ckz));
+  float Cy = __fsub_rn(sel3(C0, C1, C2, ky), __fmul_rn(r.Sy, Ckz));
+  float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+  float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+  float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+  if (U == 0.f || V == 0.f || W == 0.f) {
+    // products of two floats are exact in double; one rounding per difference
+    double u = (double)Cx * (double)By - (double)Cy * (double)Bx;
+    double v = (double)Ax * (double)Cy - (double)Ay * (double)Cx;
+    double w = (double)Bx * (double)Ay - (double)By * (double)Ax;
+    U = (float)u;
+    V = (float)v;
+    W = (float)w;
+  }
+  if ((U < 0.f || V < 0.f || W < 0.f) && (U > 0.f || V > 0.f || W > 0.f)) return -1.f;
+  float det = __fadd_rn(__fadd_rn(U, V), W);
+  if (det == 0.f) return -1.f;
+  float Az = __fmul_rn(r.Sz, Akz), Bz = __fmul_rn(r.Sz, Bkz), Cz = __fmul_rn(r.Sz, Ckz);
+  float T = __fadd_rn(__fadd_rn(__fmul_rn(U, Az), __fmul_rn(V, Bz)), __fmul_rn(W, Cz));
+  // t = T/det must be > 0: same sign, T != 0
+  if (((__float_as_uint(T) ^ __float_as_uint(det)) >> 31) || T == 0.f) return -1.f;
+  // certainly beyond tbest: |T| > tbest*|det|*(1+2^-20) implies fl(T/det) > tbest
+  if (fabsf(T) > __fmul_rn(__fmul_rn(tbest, fabsf(det)), 1.00000095367431640625f)) return -1.f;
+  return __fdiv_rn(T, det);
+}
+
+// Slab test of the W children of one quantized node.  Child box planes are
+// p + q * 2^e along each axis, so the ray parameter of a plane is
+// fma(q, 2^e * inv_d, (p - o) * inv_d): one FMA per plane.  Returns the
+// node group (child_base, pending-child bits << 24 | imask) and the triangle
+// group (tri_base, leaf triangle bits).
+template <int W>
+__device__ __forceinline__ void intersect_node(const Ray& r, const uint4* __restrict__ nd,
+                                               float tmax, uint2& ng, uint2& tg) {
+  const uint4 h0 = ldg4(nd), h1 = ldg4(nd + 1);
+  uint32_t lox[2], loy[2], loz[2], hix[2], hiy[2], hiz[2];
+  if (W == 8) {
+    const uint4 q0 = ldg4(nd + 2), q1 = ldg4(nd + 3), q2 = ldg4(nd + 4);
+    lox[0] = q0.x; lox[1] = q0.y; loy[0] = q0.z; loy[1] = q0.w;
+    loz[0] = q1.x; loz[1] = q1.y; hix[0] = q1.z; hix[1] = q1.w;
+    hiy[0] = q2.x; hiy[1] = q2.y; hiz[0] = q2.z; hiz[1] = q2.w;
+  } else {
+    const uint4 q0 = ldg4(nd + 2), q1 = ldg4(nd + 3);
+    lox[0] = q0.x; loy[0] = q0.y; loz[0] = q0.z; hix[0] = q0.w;
+    hiy[0] = q1.x; hiz[0] = q1.y;
+    lox[1] = loy[1] = loz[1] = hix[1] = hiy[1] = hiz[1] = 0;
+  }
+  const uint32_t e = h0.w;
+  const float sx = __uint_as_float((e & 0xFFu) << 23);
+  const float sy = __uint_as_float(((e >> 8) & 0xFFu) << 23);
+  const float sz = __uint_as_float(((e >> 16) & 0xFFu) << 23);
+  const float Sx = __fmul_rn(sx, r.ix), Sy = __fmul_rn(sy, r.iy), Sz = __fmul_rn(sz, r.iz);
+  const float Bx = __fmul_rn(__fsub_rn(__uint_as_float(h0.x), r.ox), r.ix);
+  const float By = __fmul_rn(__fsub_rn(__uint_as_float(h0.y), r.oy), r.iy);
+  const float Bz = __fmul_rn(__fsub_rn(__uint_as_float(h0.z), r.oz), r.iz);
+  const bool fx = r.oct & 1u, fy = r.oct & 2u, fz = r.oct & 4u;
+  const uint32_t meta_w[2] = {h1.z, h1.w};
+  uint32_t hits = 0;
+#pragma unroll
+  for (int i = 0; i < W; ++i) {
+    const int w = i >> 2;
+    const uint32_t s = (uint32_t)(i & 3);
+    const uint32_t nxw = fx ? hix[w] : lox[w], fxw = fx ? lox[w] : hix[w];
+    const uint32_t nyw = fy ? hiy[w] : loy[w], fyw = fy ? loy[w] : hiy[w];
+    const uint32_t nzw = fz ? hiz[w] : loz[w], fzw = fz ? loz[w] : hiz[w];
+    const float tnx = fmaf(byte_f(nxw, s), Sx, Bx);
+    const float tny = fmaf(byte_f(nyw, s), Sy, By);
+    const float tnz = fmaf(byte_f(nzw, s), Sz, Bz);
+    const float tfx = fmaf(byte_f(fxw, s), Sx, Bx);
+    const float tfy = fmaf(byte_f(fyw, s), Sy, By);
+    const float tfz = fmaf(byte_f(fzw, s), Sz, Bz);
+    const float tn = max3f(tnx, tny, fmaxf(tnz, 0.f));
+    const float tf = min3f(tfx, tfy, fminf(tfz, tmax));
+    const uint32_t m = (meta_w[w] >> (8 * s)) & 0xFFu;
+    const uint32_t pos = (m & 31u) ^ (((m & 0x18u) == 0x18u) ? r.oct : 0u);
+    if (tn <= tf) hits |= (m >> 5) << pos;
+  }
+  ng = make_uint2(h1.x, (hits & 0xFF000000u) | (e >> 24));
+  tg = make_uint2(h1.y, hits & 0x00FFFFFFu);
+}
+
+// Per-thread traversal state and stack.  The stack's first `smem_depth`
+// entries live in shared memory (column `threadIdx.x` of a
+// [smem_depth][blockDim.x] array, so a warp's accesses are conflict-free);
+// deeper entries go to a local-memory array.
+template <int W, bool COUNT>
+struct Tracer {
+  Ray r;
+  float best_t;
+  int32_t best_id;
+  uint2 ng, tg;
+  int sp;
+  const uint4* __restrict__ nodes;
+  const float4* __restrict__ tris;
+  uint32_t n_nodes, n_tris;
+
+  __device__ __forceinline__ void start(const void* node_ptr, const void* tri_ptr, float max_range) {
+    nodes = (const uint4*)node_ptr;
+    tris = (const float4*)tri_ptr;
+    best_t = max_range;
+    best_id = kNoHit;
+    // root group: one internal child (the root node, code 0)
+    ng = make_uint2(0u, (1u << (24 + r.oct)) | 1u);
+    tg = make_uint2(0u, 0u);
+    sp = 0;
+    if (COUNT) n_nodes = n_tris = 0;
+  }
+
+  __device__ __forceinline__ bool push(uint2 v, uint2* ss, int stride, int sdepth, uint2* ls) {
+    if (sp < sdepth) {
+      ss[sp * stride] = v;
+    } else {
+      int li = sp - sdepth;
+      if (li >= kStackLocal) return false;
+      ls[li] = v;
+    }
+    ++sp;
+    return true;
+  }
+  __device__ __forceinline__ uint2 pop(uint2* ss, int stride, int sdepth, uint2* ls) {
+    --sp;
+    return sp < sdepth ? ss[sp * stride] : ls[sp - sdepth];
+  }
+
+  // One traversal step: descend into the nearest pending child (or take a
+  // popped triangle group), test the node's leaf triangles unless few lanes
+  // of the warp want to (then they are postponed onto the stack), and pop
+  // when the current node group is exhausted.  Returns true when the ray is
+  // finished.  `postpone_lanes` = 0 disables postponing.
+  __device__ __forceinline__ bool step(uint2* ss, int stride, int sdepth, uint2* ls,
+                                       int postpone_lanes, unsigned* status) {
+    if (ng.y & 0xFF000000u) {
+      const uint32_t pos = __ffs(ng.y >> 24) - 1;
+      const uint32_t code = pos ^ r.oct;
+      ng.y &= ~(1u << (24 + pos));
+      const uint32_t child = ng.x + __popc((ng.y & 0xFFu) & ((1u << code) - 1u));
+      if (ng.y & 0xFF000000u) {
+        if (!push(ng, ss, stride, sdepth, ls)) {
+          atomicOr(status, 1u);
+          return true;
+        }
+      }
+      intersect_node<W>(r, nodes + (size_t)child * (node_stride(W) / 16), best_t, ng, tg);
+      if (COUNT) ++n_nodes;
+    } else {
+      tg = ng;
+      ng = make_uint2(0u, 0u);
+    }
+    while (tg.y) {
+      if (postpone_lanes > 0 && (ng.y & 0xFF000000u)) {
+        if (__popc(__activemask()) < postpone_lanes) {
+          if (!push(tg, ss, stride, sdepth, ls)) {
+            atomicOr(status, 1u);
+            return true;
+          }
+          tg.y = 0;
+          break;
+        }
+      }
+      const uint32_t pos = __ffs(tg.y) - 1;
+      tg.y &= tg.y - 1;
+      const float4* tp = tris + 3 * ((size_t)tg.x + pos);
+      const float4 a = ldg4f(tp), b = ldg4f(tp + 1), c = ldg4f(tp + 2);
+      const float t = tri_hit(r, a, b, c, best_t);
+      if (COUNT) ++n_tris;
+      if (t > 0.f) {
+        const int32_t id = __float_as_int(a.w);
+        if (t < best_t || (t == best_t && id < best_id)) {
+          best_t = t;
+          best_id = id;
+        }
+      }
+    }
+    if (!(ng.y & 0xFF000000u)) {
+      if (sp == 0) return true;
+      ng = pop(ss, stride, sdepth, ls);
+    }
+    return false;
+  }
+
+  __device__ __forceinline__ void result(float& range, int32_t& id) const {
+    range = best_t;  // == max_range when nothing was hit
+    id = best_id == kNoHit ? -1 : best_id;
+  }
+};
+
+}  // namespace dev
+}  // namespace fgl

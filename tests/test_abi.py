@@ -1,0 +1,173 @@
+"""CPU-side checks of the C-ABI library: it loads, exports every entry point
+include/fgl.h declares, validates arguments, and its host BVH builder makes
+conservative quantized boxes (checked here independently of the library's
+own verifier)."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+import paper_2509_17390_gb300 as fgl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "fgl.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fgl_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = fgl.lib()
+    names = declared_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(L, n), n
+    assert L.fgl_version() >= 100
+
+
+def test_header_compiles_as_c(tmp_path):
+    c = tmp_path / "t.c"
+    c.write_text('#include "fgl.h"\nint main(void){return (int)FGL_OK;}\n')
+    import subprocess
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        "-c", str(c), "-o", str(tmp_path / "t.o")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+
+
+# ---------------------------------------------------------------------------
+# host builder
+# ---------------------------------------------------------------------------
+def decode_nodes(nodes: np.ndarray, width: int):
+    S = 80 if width == 8 else 64
+    rec = nodes.reshape(-1, S)
+    p = rec[:, 0:12].copy().view(np.float32)
+    packed = rec[:, 12:16].copy().view(np.uint32)[:, 0]
+    e = np.stack([(packed >> (8 * a)) & 0xFF for a in range(3)], 1).astype(np.uint32)
+    scale = (e << 23).view(np.float32)
+    imask = packed >> 24
+    base = rec[:, 16:24].copy().view(np.uint32)
+    meta = rec[:, 24:24 + width]
+    q = rec[:, 32:32 + 6 * width].reshape(-1, 6, width).astype(np.float32)
+    lo = (q[:, 0:3] * scale[:, :, None]).astype(np.float32) + p[:, :, None]   # q*2^e is exact
+    hi = (q[:, 3:6] * scale[:, :, None]).astype(np.float32) + p[:, :, None]
+    return dict(p=p, imask=imask, child_base=base[:, 0], tri_base=base[:, 1], meta=meta, lo=lo, hi=hi)
+
+
+def check_tree(v, t, width):
+    sc = fgl.Scene(v, t, width=width, upload=False)
+    st = sc.stats()
+    nodes, tris = sc.export()
+    D = decode_nodes(nodes, width)
+    ids = tris[:, 3].copy().view(np.int32)
+    assert np.array_equal(np.sort(ids), np.arange(len(t)))         # every triangle exactly once
+    tv = tris.reshape(-1, 3, 4)[:, :, :3]
+    assert np.array_equal(tv, v[t[ids]])                           # leaf records hold the mesh's vertices
+    m = st["margin"]
+    # content box per node, children (larger index) before parents
+    N = st["n_nodes"]
+    clo = np.full((N, 3), np.inf)
+    chi = np.full((N, 3), -np.inf)
+    for ni in range(N - 1, -1, -1):
+        for j in range(width):
+            mt = int(D["meta"][ni, j])
+            if mt == 0:
+                continue
+            if (mt & 0x18) == 0x18:
+                c = (mt & 31) - 24
+                assert (D["imask"][ni] >> c) & 1
+                child = int(D["child_base"][ni]) + bin(int(D["imask"][ni]) & ((1 << c) - 1)).count("1")
+                assert ni < child < N
+                lo, hi = clo[child], chi[child]
+            else:
+                off, cnt = mt & 31, bin(mt >> 5).count("1")
+                assert 1 <= cnt <= 3
+                k = int(D["tri_base"][ni]) + off
+                pts = tv[k:k + cnt].reshape(-1, 3).astype(np.float64)
+                lo, hi = pts.min(0), pts.max(0)
+            assert np.all(D["lo"][ni, :, j].astype(np.float64) <= lo - m), (ni, j)
+            assert np.all(D["hi"][ni, :, j].astype(np.float64) >= hi + m), (ni, j)
+            clo[ni] = np.minimum(clo[ni], lo)
+            chi[ni] = np.maximum(chi[ni], hi)
+    assert sc.verify() == 0
+    return st
+
+
+@pytest.mark.parametrize("width", [8, 4])
+def test_builder_boxes_conservative_tiny_room(width):
+    v, t, _ = synth.tiny_room_scene(1)
+    st = check_tree(v, t, width)
+    assert st["width"] == width and st["node_stride"] == (80 if width == 8 else 64)
+
+
+@pytest.mark.parametrize("width", [8, 4])
+def test_builder_boxes_conservative_random_soup(width):
+    rng = np.random.default_rng(3)
+    c = rng.uniform(-30, 30, (3000, 1, 3))
+    v = (c + rng.uniform(0.001, 2.0, (3000, 1, 1)) * rng.standard_normal((3000, 3, 3))).reshape(-1, 3)
+    v = v.astype(np.float32)
+    t = np.arange(len(v), dtype=np.int32).reshape(-1, 3)
+    check_tree(v, t, width)
+
+
+def test_builder_degenerate_inputs():
+    # single triangle, zero-area triangles, duplicates, many coincident triangles
+    v1 = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0]], np.float32)
+    check_tree(v1, np.array([[0, 1, 2]], np.int32), 8)
+    vd = np.zeros((3, 3), np.float32)
+    check_tree(vd, np.zeros((5, 3), np.int32), 8)
+    check_tree(v1, np.tile(np.array([[0, 1, 2]], np.int32), (5000, 1)), 8)
+    check_tree(v1, np.tile(np.array([[0, 1, 2]], np.int32), (5000, 1)), 4)
+    # huge and tiny coordinates together
+    vb = np.array([[1e4, 1e4, 1e4], [1e4 + 1e-3, 1e4, 1e4], [1e4, 1e4 + 1e-3, 1e4],
+                   [-1e4, 0, 0], [-1e4, 1, 0], [-1e4, 0, 1]], np.float32)
+    check_tree(vb, np.array([[0, 1, 2], [3, 4, 5]], np.int32), 8)
+
+
+def test_builder_sah_no_worse_than_median():
+    v, t, _ = synth.tiny_room_scene(2)
+    sc = fgl.Scene(v, t, upload=False)
+    st = sc.stats()
+    assert st["depth"] <= 6 and st["sah_cost"] > 0
+
+
+def test_builder_rejects_bad_input():
+    v = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0]], np.float32)
+    with pytest.raises(fgl.FglError) as e:
+        fgl.Scene(v, np.array([[0, 1, 3]], np.int32), upload=False)
+    assert e.value.status == fgl.FGL_ERR_INVALID
+    vn = v.copy()
+    vn[1, 2] = np.nan
+    with pytest.raises(fgl.FglError):
+        fgl.Scene(vn, np.array([[0, 1, 2]], np.int32), upload=False)
+    with pytest.raises(fgl.FglError):
+        fgl.Scene(v, np.zeros((0, 3), np.int32), upload=False)
+    with pytest.raises(fgl.FglError):
+        fgl.Scene(v, np.array([[0, 1, 2]], np.int32), width=5, upload=False)
+
+
+def test_cast_argument_validation_without_gpu():
+    L = fgl.lib()
+    v, t, _ = synth.tiny_room_scene(1)
+    sc = fgl.Scene(v, t, upload=False)
+    P = ctypes.c_void_p
+    # null sensor / non-resident scene are rejected before any CUDA call
+    st = L.fgl_cast(sc.handle, None, None, 1, 10.0, None, None, None)
+    assert st == fgl.FGL_ERR_INVALID
+    assert b"null" in L.fgl_last_error()
+    item = fgl.CastItem(sc.handle, None, None, 1, 10.0, None, None)
+    assert L.fgl_cast_batched(ctypes.byref(item), 1, None, None) == fgl.FGL_ERR_INVALID
+    assert L.fgl_cast_batched(None, -1, None, None) == fgl.FGL_ERR_INVALID
+    out = P()
+    assert L.fgl_sensor_create(None, None, 0, 1, 0, 0, 0, ctypes.byref(out)) == fgl.FGL_ERR_INVALID
+    el = np.zeros(6, np.float32)
+    assert L.fgl_sensor_create(el.ctypes.data, el.ctypes.data, 6, 4, 2, 0, 0,
+                               ctypes.byref(out)) == fgl.FGL_ERR_INVALID   # rows*cols != n
+    el[2] = np.inf
+    assert L.fgl_sensor_create(el.ctypes.data, el.ctypes.data, 6, 1, 6, 0, 0,
+                               ctypes.byref(out)) == fgl.FGL_ERR_INVALID

@@ -1,0 +1,239 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the FP64 oracle.
+
+Contract (per ray): hit/miss and triangle id equal to the oracle's, range
+within 1e-4 m + 1e-6 * range, except on rays the oracle flags as ambiguous
+(edge-grazing, depth tie, range boundary); those must still pass the
+oracle's plausibility check.  Results must be bitwise identical across every
+launch variant (BVH width, stack split, postponing, block size, packet size,
+refill threshold, graph capture, batched vs plain).
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from synth import workloads
+from tests.helpers import assert_parity, parity_report
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+fgl = pytest.importorskip("paper_2509_17390_gb300")
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    w = workloads.tiny_cast(1)
+    P = np.concatenate([w.poses, synth.sample_free_pose(np.random.default_rng(9), w.obstacles, 7,
+                                                        upright=False)])
+    return w, P
+
+
+@pytest.fixture(scope="module")
+def indoor():
+    w = workloads.indoor_scan(2)
+    return w
+
+
+@pytest.fixture(scope="module")
+def indoor_scenes(indoor):
+    return {W: fgl.Scene(indoor.verts, indoor.tris, width=W) for W in (8, 4)}
+
+
+@pytest.fixture(scope="module")
+def indoor_oracle(indoor):
+    return oracle.Scene(indoor.verts, indoor.tris, bvh=True)
+
+
+def run_plain(scene, sensor, P, max_range, opts=None):
+    poses = torch.from_numpy(np.ascontiguousarray(P, np.float32)).cuda()
+    if opts is None:
+        r, i = fgl.cast(scene, sensor, poses, max_range)
+    else:
+        r, i = fgl.cast_opts(scene, sensor, poses, max_range, opts)
+    fgl.sync()
+    return r.cpu().numpy(), i.cpu().numpy()
+
+
+def run_batched(items_np, opts=None, stream=None):
+    """items_np: (scene, sensor, poses np, max_range)."""
+    items, outs = [], []
+    for sc, se, P, R in items_np:
+        poses = torch.from_numpy(np.ascontiguousarray(P, np.float32)).cuda()
+        n = P.shape[0] * se.n_rays
+        r = torch.full((n,), -7.0, dtype=torch.float32, device="cuda")
+        i = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+        items.append((sc, se, poses, R, r, i))
+        outs.append((r, i))
+    fgl.cast_batched(items, opts, stream=stream)
+    fgl.sync(stream)
+    return [(r.cpu().numpy(), i.cpu().numpy()) for r, i in outs]
+
+
+# ---------------------------------------------------------------------------
+# ray generation (eq. r_j) is bit-identical to the oracle's
+# ---------------------------------------------------------------------------
+def test_sensor_dirs_bit_exact():
+    for tab in (synth.grid_sensor(16, -15, 15, 360), synth.grid_sensor(32, -16, 15, 1800),
+                synth.rosette_sensor(20000, 3)):
+        se = fgl.Sensor.from_table(tab)
+        assert np.array_equal(se.dirs(), oracle.sensor_dirs(tab.elev, tab.azim))
+
+
+def test_world_rays_bit_exact(tiny):
+    w, P = tiny
+    for tab, tiles in ((w.sensor, (4, 8)), (synth.grid_sensor(7, -3, 20, 33), (3, 5)),
+                       (synth.rosette_sensor(1000, 1), (1, 32))):
+        se = fgl.Sensor.from_table(tab, *tiles)
+        poses = torch.from_numpy(P).cuda()
+        go, gd = fgl.world_rays(se, poses)
+        fgl.sync()
+        oo, od = oracle.world_rays(oracle.sensor_dirs(tab.elev, tab.azim), P)
+        assert np.array_equal(go.cpu().numpy(), oo)
+        assert np.array_equal(gd.cpu().numpy(), od)
+
+
+# ---------------------------------------------------------------------------
+# parity against the oracle
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("width", [8, 4])
+def test_tiny_cast_vs_brute_force(tiny, width):
+    w, P = tiny
+    sc = fgl.Scene(w.verts, w.tris, width=width)
+    se = fgl.Sensor.from_table(w.sensor)
+    gr, gi = run_plain(sc, se, P, w.max_range)
+    o, d = oracle.world_rays(oracle.sensor_dirs(w.sensor.elev, w.sensor.azim), P)
+    rep = parity_report(oracle.Scene(w.verts, w.tris, bvh=False), o, d, w.max_range, gr, gi)
+    assert_parity(rep)
+    assert rep["hits"] == rep["n"]          # closed room: every ray hits
+
+
+@pytest.mark.parametrize("width", [8, 4])
+def test_indoor_scan_vs_bvh_oracle(indoor, indoor_scenes, indoor_oracle, width):
+    w = indoor
+    se = fgl.Sensor.from_table(w.sensor)
+    gr, gi = run_plain(indoor_scenes[width], se, w.poses, w.max_range)
+    o, d = oracle.world_rays(oracle.sensor_dirs(w.sensor.elev, w.sensor.azim), w.poses)
+    rep = parity_report(indoor_oracle, o, d, w.max_range, gr, gi)
+    assert_parity(rep)
+    assert rep["flagged"] < 0.01 * rep["n"]
+
+
+def test_indoor_random_poses_and_short_range(indoor, indoor_scenes, indoor_oracle):
+    w = indoor
+    P = synth.sample_free_pose(np.random.default_rng(31), w.obstacles, 6, upright=False)
+    tab = synth.grid_sensor(16, -15, 15, 360)
+    se = fgl.Sensor.from_table(tab)
+    o, d = oracle.world_rays(oracle.sensor_dirs(tab.elev, tab.azim), P)
+    for R in (120.0, 0.75):                 # short range: many misses
+        gr, gi = run_plain(indoor_scenes[8], se, P, R)
+        rep = parity_report(indoor_oracle, o, d, R, gr, gi)
+        assert_parity(rep)
+        if R < 1:
+            assert rep["hits"] < rep["n"]
+
+
+# ---------------------------------------------------------------------------
+# variant invariance (bitwise)
+# ---------------------------------------------------------------------------
+def test_plain_variants_bitwise(indoor, indoor_scenes):
+    w = indoor
+    P = synth.sample_free_pose(np.random.default_rng(5), w.obstacles, 3, upright=False)
+    tab = synth.grid_sensor(16, -15, 15, 360)
+    base = None
+    for tiles in ((4, 8), (1, 32), (16, 2)):
+        se = fgl.Sensor.from_table(tab, *tiles)
+        for W in (8, 4):
+            for sdepth, postpone, block in ((12, 20, 128), (2, 100, 64), (1, -1, 256), (30, 50, 32)):
+                opts = fgl.BatchOpts(block_threads=block, stack_smem=sdepth, postpone_pct=postpone)
+                out = run_plain(indoor_scenes[W], se, P, w.max_range, opts)
+                if base is None:
+                    base = out
+                else:
+                    assert np.array_equal(out[0], base[0]) and np.array_equal(out[1], base[1]), \
+                        (tiles, W, sdepth, postpone, block)
+
+
+def test_batched_variants_bitwise_and_equal_plain(indoor, indoor_scenes, tiny):
+    w = indoor
+    tw, tP = tiny
+    tscene = fgl.Scene(tw.verts, tw.tris)
+    P1 = synth.sample_free_pose(np.random.default_rng(6), w.obstacles, 5, upright=False)
+    P2 = synth.sample_free_pose(np.random.default_rng(7), w.obstacles, 3)
+    s1 = fgl.Sensor.from_table(synth.grid_sensor(16, -15, 15, 360))
+    s2 = fgl.Sensor.from_table(synth.grid_sensor(7, -3, 20, 33), 2, 4)     # ragged
+    s3 = fgl.Sensor.from_table(synth.rosette_sensor(1000, 2))
+    plain = [run_plain(indoor_scenes[8], s1, P1, 120.0),
+             run_plain(indoor_scenes[4], s2, P2, 50.0),
+             run_plain(tscene, s3, tP, 100.0),
+             run_plain(indoor_scenes[8], s3, P2, 3.0)]
+    items = [(indoor_scenes[8], s1, P1, 120.0), (indoor_scenes[4], s2, P2, 50.0),
+             (tscene, s3, tP, 100.0), (indoor_scenes[8], s3, P2, 3.0)]
+    stream = torch.cuda.Stream()
+    for packet, block, sdepth, refill, postpone, graph in (
+            (64, 128, 12, 8, 20, 0), (32, 32, 0, 1, -1, 0), (256, 256, 4, 32, 100, 1),
+            (96, 64, 2, 4, 30, 1), (64, 128, 12, 8, 20, 1)):
+        opts = fgl.BatchOpts(packet_rays=packet, block_threads=block, stack_smem=sdepth,
+                             refill_min=refill, postpone_pct=postpone, use_graph=graph)
+        for rep in range(2 if graph else 1):          # graph replay too
+            outs = run_batched(items, opts, stream=stream if graph else None)
+            for (pr, pi), (br, bi) in zip(plain, outs):
+                assert np.array_equal(pr, br) and np.array_equal(pi, bi), (packet, block, sdepth)
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+def test_edge_cases(tiny):
+    w, P = tiny
+    sc = fgl.Scene(w.verts, w.tris)
+    se = fgl.Sensor.from_table(w.sensor)
+    # n_env = 0 is a no-op; an empty batch too
+    poses = torch.zeros((0, 3, 4), dtype=torch.float32, device="cuda")
+    r, i = fgl.cast(sc, se, poses, 10.0)
+    assert r.numel() == 0
+    fgl.cast_batched([])
+    # tiny max_range: everything misses with (max_range, -1)
+    gr, gi = run_plain(sc, se, P, 1e-3)
+    assert np.all(gi == -1) and np.all(gr == np.float32(1e-3))
+    # a sensor inside a closed box sees the box from inside (two-sided test)
+    v, t = synth.aabb_box((0, 0, 0), (1, 1, 1), 3)
+    bsc = fgl.Scene(v, t)
+    Pin = synth.pose_from_yaw([[0.5, 0.5, 0.5]], [0.3])
+    gr, gi = run_plain(bsc, se, Pin, 100.0)
+    assert np.all(gi >= 0) and np.all(gr <= np.sqrt(3) / 2 + 1e-5)
+    o, d = oracle.world_rays(oracle.sensor_dirs(w.sensor.elev, w.sensor.azim), Pin)
+    assert_parity(parity_report(oracle.Scene(v, t, bvh=False), o, d, 100.0, gr, gi))
+    # single-triangle scene
+    v1 = np.array([[2, -50, -50], [2, 50, -50], [2, 0, 50]], np.float32)
+    s1 = fgl.Scene(v1, np.array([[0, 1, 2]], np.int32))
+    Pz = synth.pose_from_yaw([[0, 0, 0]], [0.0])
+    gr, gi = run_plain(s1, se, Pz, 100.0)
+    o, d = oracle.world_rays(oracle.sensor_dirs(w.sensor.elev, w.sensor.azim), Pz)
+    assert_parity(parity_report(oracle.Scene(v1, np.array([[0, 1, 2]], np.int32), bvh=False),
+                                o, d, 100.0, gr, gi))
+    assert (gi == 0).any() and (gi == -1).any()
+
+
+def test_argument_errors(tiny):
+    w, P = tiny
+    sc = fgl.Scene(w.verts, w.tris)
+    se = fgl.Sensor.from_table(w.sensor)
+    poses = torch.from_numpy(P).cuda()
+    with pytest.raises(fgl.FglError):
+        fgl.cast(sc, se, poses, float("nan"))
+    with pytest.raises(fgl.FglError):
+        fgl.cast(sc, se, poses, -1.0)
+    with pytest.raises(fgl.FglError):
+        fgl.cast_opts(sc, se, poses, 10.0, fgl.BatchOpts(block_threads=33))
+    with pytest.raises(fgl.FglError):
+        fgl.cast_batched([(sc, se, poses, 10.0, torch.empty(len(P) * se.n_rays, device="cuda"),
+                           torch.empty(len(P) * se.n_rays, dtype=torch.int32, device="cuda"))],
+                         fgl.BatchOpts(packet_rays=48))
+    sc.evict()
+    with pytest.raises(fgl.FglError):
+        fgl.cast(sc, se, poses, 10.0)
+    sc.upload()
+    fgl.cast(sc, se, poses, 10.0)
+    fgl.sync()
