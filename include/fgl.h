@@ -166,14 +166,18 @@ typedef struct {
   int32_t use_graph;      /* 1 = capture the launch sequence in a CUDA graph and
                              replay it while the item layout is unchanged */
   int32_t refill_min;     /* idle lanes before a warp pulls new rays (0 = 8) */
-  int32_t postpone_pct;   /* postpone leaf tests when fewer than this % of the
-                             warp's tracing lanes want them (0 = 20; -1 = never) */
+  int32_t postpone_pct;   /* tri_mode 1 only: postpone leaf tests when fewer than
+                             this % of the warp's tracing lanes want them
+                             (0 = 20; -1 = never) */
   int32_t count_work;     /* 1 = count node visits and triangle tests (slower);
                              read with fgl_work_counters */
+  int32_t tri_mode;       /* leaf triangle tests: 0 = pooled across the warp
+                             (default), 1 = each lane tests its own, postponing
+                             per postpone_pct */
 } fgl_batch_opts;
 
 /* fgl_cast with explicit launch options: block_threads, stack_smem,
- * postpone_pct and count_work apply; the other fields are ignored.  Results
+ * tri_mode, postpone_pct and count_work apply; the other fields are ignored.  Results
  * are identical for every valid option set (only speed changes). */
 fgl_status fgl_cast_opts(fgl_scene scene, fgl_sensor sensor, const float* poses, int32_t n_env,
                          float max_range, float* out_range, int32_t* out_tri,

@@ -57,7 +57,7 @@ class BatchOpts(ctypes.Structure):
     """Launch options (fgl_batch_opts); 0 in a field selects its default."""
     _fields_ = [("packet_rays", I32), ("block_threads", I32), ("stack_smem", I32),
                 ("blocks_per_sm", I32), ("use_graph", I32), ("refill_min", I32),
-                ("postpone_pct", I32), ("count_work", I32)]
+                ("postpone_pct", I32), ("count_work", I32), ("tri_mode", I32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -82,7 +82,7 @@ fgl_status device_info(DeviceInfo* out) {
 // ---------------------------------------------------------------------------
 struct Opts {
   int packet = 64, block = 128, sdepth = 12, bpsm = 0, graph = 0, refill = 8, postpone = 20,
-      count = 0;
+      count = 0, tri_mode = 0;
 };
 
 fgl_status resolve_opts(const fgl_batch_opts* o, Opts* r) {
@@ -96,6 +96,7 @@ fgl_status resolve_opts(const fgl_batch_opts* o, Opts* r) {
     if (o->refill_min) d.refill = o->refill_min;
     if (o->postpone_pct) d.postpone = o->postpone_pct;
     d.count = o->count_work ? 1 : 0;
+    d.tri_mode = o->tri_mode;
   }
   if (d.packet < 32 || d.packet % 32 || d.packet > (1 << 20))
     return fail(FGL_ERR_INVALID, "packet_rays must be a positive multiple of 32");
@@ -105,6 +106,7 @@ fgl_status resolve_opts(const fgl_batch_opts* o, Opts* r) {
   if (d.bpsm < 0 || d.bpsm > 64) return fail(FGL_ERR_INVALID, "blocks_per_sm must be in [0, 64]");
   if (d.refill < 1 || d.refill > 32) return fail(FGL_ERR_INVALID, "refill_min must be in [1, 32]");
   if (d.postpone > 100) return fail(FGL_ERR_INVALID, "postpone_pct must be <= 100");
+  if (d.tri_mode != 0 && d.tri_mode != 1) return fail(FGL_ERR_INVALID, "tri_mode must be 0 or 1");
   DeviceInfo di;
   fgl_status s = device_info(&di);
   if (s != FGL_OK) return s;
@@ -155,7 +157,6 @@ struct BatchCtx {
   size_t staging_cap = 0;
   size_t table_bytes = 0;
   cudaEvent_t staged = nullptr;  // recorded after the table copy
-  bool staged_pending = false;
   cudaGraphExec_t gexec = nullptr;
   std::vector<uint8_t> gkey;
   // end-to-end staging
@@ -234,16 +235,18 @@ fgl_status grid_for(int W, const Opts& o, int* grid) {
   return FGL_OK;
 }
 
+// Table copy + one persistent launch per width group.  The `staged` event
+// (host may rewrite the pinned table once it has fired) is recorded by the
+// caller outside any graph capture.
 fgl_status enqueue_batch(BatchCtx& c, const std::vector<Group>& groups,
                          const std::vector<size_t>& offsets, const Opts& o, cudaStream_t s) {
   FGL_CUDA(cudaMemcpyAsync(c.d_scratch, c.h_staging, c.table_bytes, cudaMemcpyHostToDevice, s));
-  FGL_CUDA(cudaEventRecord(c.staged, s));
   for (size_t g = 0; g < groups.size(); ++g) {
     int grid = 0;
     fgl_status st = grid_for(groups[g].W, o, &grid);
     if (st != FGL_OK) return st;
     FGL_CUDA(launch_persistent(groups[g].W, o.count != 0, (char*)c.d_scratch + offsets[g], grid,
-                               o.block, o.sdepth, o.refill, o.postpone, s));
+                               o.block, o.sdepth, o.refill, o.tri_mode, o.postpone, s));
   }
   return FGL_OK;
 }
@@ -301,12 +304,17 @@ fgl_status run_batched(const fgl_cast_item* items, int n, const Opts& o, cudaStr
     std::memcpy(c.h_staging, table.data(), table.size());
     c.table_bytes = table.size();
   }
-  if (!o.graph) return enqueue_batch(c, groups, offsets, o, s);
+  if (!o.graph) {
+    fgl_status st = enqueue_batch(c, groups, offsets, o, s);
+    if (st != FGL_OK) return st;
+    FGL_CUDA(cudaEventRecord(c.staged, s));
+    return FGL_OK;
+  }
 
   // graph key: the table bytes plus the launch configuration
   std::vector<uint8_t> key(table);
-  const int cfg[8] = {o.packet, o.block, o.sdepth, o.bpsm, o.refill, o.postpone, o.count,
-                      (int)(uintptr_t)c.d_scratch};
+  const int cfg[9] = {o.packet, o.block, o.sdepth, o.bpsm, o.refill, o.postpone, o.count,
+                      o.tri_mode, (int)(uintptr_t)c.d_scratch};
   key.insert(key.end(), (const uint8_t*)cfg, (const uint8_t*)cfg + sizeof(cfg));
   if (realloc || !c.gexec || key != c.gkey) {
     if (c.gexec) {
@@ -332,6 +340,7 @@ fgl_status run_batched(const fgl_cast_item* items, int n, const Opts& o, cudaStr
     c.gkey.swap(key);
   }
   FGL_CUDA(cudaGraphLaunch(c.gexec, s));
+  FGL_CUDA(cudaEventRecord(c.staged, s));
   return FGL_OK;
 }
 
@@ -554,7 +563,7 @@ fgl_status fgl_cast(fgl_scene scene, fgl_sensor sensor, const float* poses, int3
   if (n_env == 0) return FGL_OK;
   Opts o;
   ItemDesc d = make_desc(it);
-  FGL_CUDA(launch_plain(scene->bvh.width, false, d, o.block, o.sdepth, o.postpone,
+  FGL_CUDA(launch_plain(scene->bvh.width, false, d, o.block, o.sdepth, o.tri_mode, o.postpone,
                         (cudaStream_t)stream));
   return FGL_OK;
 }
@@ -570,7 +579,7 @@ fgl_status fgl_cast_opts(fgl_scene scene, fgl_sensor sensor, const float* poses,
   if (st != FGL_OK) return st;
   if (n_env == 0) return FGL_OK;
   ItemDesc d = make_desc(it);
-  FGL_CUDA(launch_plain(scene->bvh.width, o.count != 0, d, o.block, o.sdepth, o.postpone,
+  FGL_CUDA(launch_plain(scene->bvh.width, o.count != 0, d, o.block, o.sdepth, o.tri_mode, o.postpone,
                         (cudaStream_t)stream));
   return FGL_OK;
 }

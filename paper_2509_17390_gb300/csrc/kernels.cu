@@ -40,53 +40,96 @@ __device__ __forceinline__ int postpone_threshold(int pct) {
   return (__popc(__activemask()) * pct + 99) / 100;
 }
 
+// Dynamic shared memory: one 64-bit hit key per thread (the warp-compacted
+// leaf tests merge into these), then the [sdepth][blockDim] stack array.
+struct Smem {
+  unsigned long long* keys;  // this warp's 32 keys
+  uint2* ss;                 // this thread's stack column
+};
+__device__ __forceinline__ Smem smem_layout() {
+  extern __shared__ unsigned long long smem_u64[];
+  Smem m;
+  m.keys = smem_u64 + (threadIdx.x & ~31u);
+  m.ss = reinterpret_cast<uint2*>(smem_u64 + blockDim.x) + threadIdx.x;
+  return m;
+}
+
 template <int W, bool COUNT>
-__global__ void __launch_bounds__(512) k_plain(const ItemDesc it, int sdepth, int postpone_pct) {
-  extern __shared__ uint2 smem_stack[];
+__global__ void __launch_bounds__(512) k_plain(const ItemDesc it, int sdepth, int tri_mode,
+                                               int postpone_pct) {
+  const unsigned FULL = 0xFFFFFFFFu;
+  const Smem sm = smem_layout();
+  const int lane = threadIdx.x & 31;
   const int64_t total = (int64_t)it.n_env * it.n_rays;
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= total) return;
-  const int env = (int)(gid / it.n_rays);
-  const int j = (int)(gid - (int64_t)env * it.n_rays);
-  const float4 ds = __ldg((const float4*)it.dirs + j);
-  float ox, oy, oz, dx, dy, dz;
-  dev::world_ray(it.poses + 12 * (int64_t)env, ds, ox, oy, oz, dx, dy, dz);
+  bool done = gid >= total;
+  int env = 0;
+  float4 ds = make_float4(0.f, 0.f, 0.f, 0.f);
   dev::Tracer<W, COUNT> tr;
-  dev::setup_ray(tr.r, ox, oy, oz, dx, dy, dz);
-  tr.start(it.nodes, it.tris, it.max_range);
-  uint2 ls[kStackLocal];
-  uint2* ss = smem_stack + threadIdx.x;
-  for (;;) {
-    const int pl = postpone_threshold(postpone_pct);
-    if (tr.step(ss, blockDim.x, sdepth, ls, pl, &g_status)) break;
+  tr.tg = make_uint2(0u, 0u);
+  tr.ng = make_uint2(0u, 0u);
+  if (COUNT) tr.n_nodes = tr.n_tris = 0;
+  if (!done) {
+    env = (int)(gid / it.n_rays);
+    const int j = (int)(gid - (int64_t)env * it.n_rays);
+    ds = __ldg((const float4*)it.dirs + j);
+    float ox, oy, oz, dx, dy, dz;
+    dev::world_ray(it.poses + 12 * (int64_t)env, ds, ox, oy, oz, dx, dy, dz);
+    dev::setup_ray(tr.r, ox, oy, oz, dx, dy, dz);
+    tr.start(it.nodes, it.tris, it.max_range);
   }
-  float rg;
-  int32_t id;
-  tr.result(rg, id);
-  const int64_t o = (int64_t)env * it.n_rays + __float_as_int(ds.w);
-  it.out_range[o] = rg;
-  it.out_tri[o] = id;
-  if (COUNT) flush_counters<COUNT>(1u, tr.n_nodes, tr.n_tris);
+  uint2 ls[kStackLocal];
+  if (tri_mode == 0) {
+    while (__any_sync(FULL, !done)) {
+      bool ok = true;
+      if (!done) ok = tr.descend(sm.ss, blockDim.x, sdepth, ls);
+      dev::tri_phase_warp(tr, sm.keys, lane);
+      if (!done) {
+        if (!ok) {
+          atomicOr(&g_status, 1u);
+          done = true;
+        } else {
+          done = tr.finish(sm.ss, blockDim.x, sdepth, ls);
+        }
+      }
+    }
+  } else if (!done) {
+    for (;;) {
+      const int pl = postpone_threshold(postpone_pct);
+      if (tr.step(sm.ss, blockDim.x, sdepth, ls, pl, &g_status)) break;
+    }
+  }
+  if (gid < total) {
+    float rg;
+    int32_t id;
+    tr.result(rg, id);
+    const int64_t o = (int64_t)env * it.n_rays + __float_as_int(ds.w);
+    it.out_range[o] = rg;
+    it.out_tri[o] = id;
+  }
+  if (COUNT) flush_counters<COUNT>(gid < total ? 1u : 0u, tr.n_nodes, tr.n_tris);
 }
 
 template <int W, bool COUNT>
 __global__ void __launch_bounds__(512) k_persistent(BatchHeader* __restrict__ hdr,
                                                     const ItemDesc* __restrict__ items, int sdepth,
-                                                    int refill_min, int postpone_pct) {
-  extern __shared__ uint2 smem_stack[];
+                                                    int refill_min, int tri_mode, int postpone_pct) {
   const unsigned FULL = 0xFFFFFFFFu;
+  const Smem sm = smem_layout();
   const int lane = threadIdx.x & 31;
   const int64_t n_packets = hdr->n_packets;
   const int n_items = hdr->n_items;
   const int P = hdr->packet_rays;
   uint2 ls[kStackLocal];
-  uint2* ss = smem_stack + threadIdx.x;
 
   // warp-uniform packet cursor
   int pk_item = 0, pk_env = 0, pk_next = 0, pk_end = 0;
   bool drained = false;
   // lane state
   dev::Tracer<W, COUNT> tr;
+  tr.tg = make_uint2(0u, 0u);
+  tr.ng = make_uint2(0u, 0u);
+  if (COUNT) tr.n_nodes = tr.n_tris = 0;
   bool active = false;
   float* out_r = nullptr;
   int32_t* out_t = nullptr;
@@ -126,6 +169,10 @@ __global__ void __launch_bounds__(512) k_persistent(BatchHeader* __restrict__ hd
           float ox, oy, oz, dx, dy, dz;
           dev::world_ray(it.poses + 12 * (int64_t)pk_env, ds, ox, oy, oz, dx, dy, dz);
           dev::setup_ray(tr.r, ox, oy, oz, dx, dy, dz);
+          if (COUNT) {
+            c_nodes += tr.n_nodes;
+            c_tris += tr.n_tris;
+          }
           tr.start(it.nodes, it.tris, it.max_range);
           const int64_t o = (int64_t)pk_env * it.n_rays + __float_as_int(ds.w);
           out_r = it.out_range + o;
@@ -141,24 +188,34 @@ __global__ void __launch_bounds__(512) k_persistent(BatchHeader* __restrict__ hd
       if (drained) break;
       continue;
     }
-    if (active) {
-      const int pl = postpone_pct > 0 ? (__popc(act) * postpone_pct + 99) / 100 : 0;
-      if (tr.step(ss, blockDim.x, sdepth, ls, pl, &g_status)) {
-        float rg;
-        int32_t id;
-        tr.result(rg, id);
-        *out_r = rg;
-        *out_t = id;
-        active = false;
-        if (COUNT) {
-          ++c_rays;
-          c_nodes += tr.n_nodes;
-          c_tris += tr.n_tris;
+    bool fin = false;
+    if (tri_mode == 0) {
+      bool ok = true;
+      if (active) ok = tr.descend(sm.ss, blockDim.x, sdepth, ls);
+      dev::tri_phase_warp(tr, sm.keys, lane);
+      if (active) {
+        if (!ok) {
+          atomicOr(&g_status, 1u);
+          fin = true;
+        } else {
+          fin = tr.finish(sm.ss, blockDim.x, sdepth, ls);
         }
       }
+    } else if (active) {
+      const int pl = postpone_pct > 0 ? (__popc(act) * postpone_pct + 99) / 100 : 0;
+      fin = tr.step(sm.ss, blockDim.x, sdepth, ls, pl, &g_status);
+    }
+    if (fin) {
+      float rg;
+      int32_t id;
+      tr.result(rg, id);
+      *out_r = rg;
+      *out_t = id;
+      active = false;
+      if (COUNT) ++c_rays;
     }
   }
-  if (COUNT) flush_counters<COUNT>(c_rays, c_nodes, c_tris);
+  if (COUNT) flush_counters<COUNT>(c_rays, c_nodes + tr.n_nodes, c_tris + tr.n_tris);
 }
 
 __global__ void k_world_rays(const float4* __restrict__ dirs, const float* __restrict__ poses,
@@ -201,10 +258,12 @@ void* pick_persistent(int W, bool count) {
 
 }  // namespace
 
-size_t stack_smem_bytes(int block, int sdepth) { return (size_t)block * (size_t)sdepth * sizeof(uint2); }
+size_t stack_smem_bytes(int block, int sdepth) {
+  return (size_t)block * sizeof(unsigned long long) + (size_t)block * (size_t)sdepth * sizeof(uint2);
+}
 
 cudaError_t launch_plain(int W, bool count, const ItemDesc& it, int block, int sdepth,
-                         int postpone_pct, cudaStream_t s) {
+                         int tri_mode, int postpone_pct, cudaStream_t s) {
   const int64_t total = (int64_t)it.n_env * it.n_rays;
   if (total == 0) return cudaSuccess;
   const int64_t grid = (total + block - 1) / block;
@@ -215,7 +274,7 @@ cudaError_t launch_plain(int W, bool count, const ItemDesc& it, int block, int s
     if (e != cudaSuccess) return e;
   }
   ItemDesc arg = it;
-  void* args[] = {&arg, &sdepth, &postpone_pct};
+  void* args[] = {&arg, &sdepth, &tri_mode, &postpone_pct};
   return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(block), args, smem, s);
 }
 
@@ -229,7 +288,7 @@ int persistent_blocks_per_sm(int W, bool count, int block, int sdepth) {
 }
 
 cudaError_t launch_persistent(int W, bool count, void* scratch, int grid, int block, int sdepth,
-                              int refill_min, int postpone_pct, cudaStream_t s) {
+                              int refill_min, int tri_mode, int postpone_pct, cudaStream_t s) {
   void* fn = pick_persistent(W, count);
   const size_t smem = stack_smem_bytes(block, sdepth);
   if (smem > 48 * 1024) {
@@ -238,7 +297,7 @@ cudaError_t launch_persistent(int W, bool count, void* scratch, int grid, int bl
   }
   BatchHeader* hdr = (BatchHeader*)scratch;
   const ItemDesc* items = (const ItemDesc*)((char*)scratch + sizeof(BatchHeader));
-  void* args[] = {&hdr, &items, &sdepth, &refill_min, &postpone_pct};
+  void* args[] = {&hdr, &items, &sdepth, &refill_min, &tri_mode, &postpone_pct};
   return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, s);
 }
 

@@ -7,12 +7,14 @@
 
 namespace fgl {
 
-// Dynamic shared memory of the traversal stacks of one block.
+// Dynamic shared memory of one block: a 64-bit hit key per thread plus the
+// shared part of the traversal stacks.
 size_t stack_smem_bytes(int block, int sdepth);
 
 // One thread per ray of one item (grid = ceil(n_env * n_rays / block)).
+// tri_mode 0: warp-compacted leaf tests; 1: lane-serial with postponing.
 cudaError_t launch_plain(int W, bool count, const ItemDesc& it, int block, int sdepth,
-                         int postpone_pct, cudaStream_t s);
+                         int tri_mode, int postpone_pct, cudaStream_t s);
 
 // Resident blocks per SM of the persistent kernel for this configuration.
 int persistent_blocks_per_sm(int W, bool count, int block, int sdepth);
@@ -20,7 +22,7 @@ int persistent_blocks_per_sm(int W, bool count, int block, int sdepth);
 // Persistent kernel over the work queue in `scratch`: a BatchHeader
 // followed by n_items ItemDesc records (device memory).
 cudaError_t launch_persistent(int W, bool count, void* scratch, int grid, int block, int sdepth,
-                              int refill_min, int postpone_pct, cudaStream_t s);
+                              int refill_min, int tri_mode, int postpone_pct, cudaStream_t s);
 
 // Debug export of world rays (beam order).
 cudaError_t launch_world_rays(const void* dirs, const float* poses, int n_env, int n_rays,

@@ -174,7 +174,17 @@ __device__ __forceinline__ void intersect_node(const Ray& r, const uint4* __rest
   const float By = __fmul_rn(__fsub_rn(__uint_as_float(h0.y), r.oy), r.iy);
   const float Bz = __fmul_rn(__fsub_rn(__uint_as_float(h0.z), r.oz), r.iz);
   const bool fx = r.oct & 1u, fy = r.oct & 2u, fz = r.oct & 4u;
-  const uint32_t meta_w[2] = {h1.z, h1.w};
+  // Per 4-child meta word, byte-parallel: bit position of each child's first
+  // hit bit (internal children: 24 + (code ^ oct); leaves: triangle offset)
+  // and its bit count (unary triangle count; 1 for an internal child).
+  uint32_t idx_w[2], cnt_w[2];
+#pragma unroll
+  for (int w = 0; w < (W + 3) / 4; ++w) {
+    const uint32_t mw = w == 0 ? h1.z : h1.w;
+    const uint32_t inner = (mw & (mw << 1)) & 0x10101010u;  // bytes 24..31
+    idx_w[w] = (mw & 0x1F1F1F1Fu) ^ ((inner >> 4) * r.oct);
+    cnt_w[w] = (mw >> 5) & 0x07070707u;
+  }
   uint32_t hits = 0;
 #pragma unroll
   for (int i = 0; i < W; ++i) {
@@ -191,9 +201,9 @@ __device__ __forceinline__ void intersect_node(const Ray& r, const uint4* __rest
     const float tfz = fmaf(byte_f(fzw, s), Sz, Bz);
     const float tn = max3f(tnx, tny, fmaxf(tnz, 0.f));
     const float tf = min3f(tfx, tfy, fminf(tfz, tmax));
-    const uint32_t m = (meta_w[w] >> (8 * s)) & 0xFFu;
-    const uint32_t pos = (m & 31u) ^ (((m & 0x18u) == 0x18u) ? r.oct : 0u);
-    if (tn <= tf) hits |= (m >> 5) << pos;
+    const uint32_t pos = __byte_perm(idx_w[w], 0u, 0x4440u | s);
+    const uint32_t cb = __byte_perm(cnt_w[w], 0u, 0x4440u | s);
+    if (tn <= tf) hits |= cb << pos;
   }
   ng = make_uint2(h1.x, (hits & 0xFF000000u) | (e >> 24));
   tg = make_uint2(h1.y, hits & 0x00FFFFFFu);
@@ -203,6 +213,12 @@ __device__ __forceinline__ void intersect_node(const Ray& r, const uint4* __rest
 // entries live in shared memory (column `threadIdx.x` of a
 // [smem_depth][blockDim.x] array, so a warp's accesses are conflict-free);
 // deeper entries go to a local-memory array.
+//
+// One traversal step is: descend() -- visit the nearest pending child of the
+// current node group, leaving the visited node's hit leaf triangles in `tg`
+// -- then the leaf triangle tests, either lane by lane (tri_serial) or pooled
+// across the warp (tri_phase_warp), then finish() -- pop the next node group
+// when the current one is exhausted.
 template <int W, bool COUNT>
 struct Tracer {
   Ray r;
@@ -242,23 +258,17 @@ struct Tracer {
     return sp < sdepth ? ss[sp * stride] : ls[sp - sdepth];
   }
 
-  // One traversal step: descend into the nearest pending child (or take a
-  // popped triangle group), test the node's leaf triangles unless few lanes
-  // of the warp want to (then they are postponed onto the stack), and pop
-  // when the current node group is exhausted.  Returns true when the ray is
-  // finished.  `postpone_lanes` = 0 disables postponing.
-  __device__ __forceinline__ bool step(uint2* ss, int stride, int sdepth, uint2* ls,
-                                       int postpone_lanes, unsigned* status) {
+  // Descend into the nearest pending child of the current node group (the
+  // remaining siblings go onto the stack), or take a popped triangle group.
+  // Returns false on stack overflow (the ray is then abandoned).
+  __device__ __forceinline__ bool descend(uint2* ss, int stride, int sdepth, uint2* ls) {
     if (ng.y & 0xFF000000u) {
       const uint32_t pos = __ffs(ng.y >> 24) - 1;
       const uint32_t code = pos ^ r.oct;
       ng.y &= ~(1u << (24 + pos));
       const uint32_t child = ng.x + __popc((ng.y & 0xFFu) & ((1u << code) - 1u));
       if (ng.y & 0xFF000000u) {
-        if (!push(ng, ss, stride, sdepth, ls)) {
-          atomicOr(status, 1u);
-          return true;
-        }
+        if (!push(ng, ss, stride, sdepth, ls)) return false;
       }
       intersect_node<W>(r, nodes + (size_t)child * (node_stride(W) / 16), best_t, ng, tg);
       if (COUNT) ++n_nodes;
@@ -266,13 +276,25 @@ struct Tracer {
       tg = ng;
       ng = make_uint2(0u, 0u);
     }
+    return true;
+  }
+
+  __device__ __forceinline__ void consider(float t, int32_t id) {
+    if (t > 0.f && (t < best_t || (t == best_t && id < best_id))) {
+      best_t = t;
+      best_id = id;
+    }
+  }
+
+  // Lane-serial leaf tests; when fewer than `postpone_lanes` lanes of the
+  // warp are testing triangles and this lane still has nodes to visit, its
+  // triangle group is pushed and tested later.  Returns false on overflow.
+  __device__ __forceinline__ bool tri_serial(uint2* ss, int stride, int sdepth, uint2* ls,
+                                             int postpone_lanes) {
     while (tg.y) {
       if (postpone_lanes > 0 && (ng.y & 0xFF000000u)) {
         if (__popc(__activemask()) < postpone_lanes) {
-          if (!push(tg, ss, stride, sdepth, ls)) {
-            atomicOr(status, 1u);
-            return true;
-          }
+          if (!push(tg, ss, stride, sdepth, ls)) return false;
           tg.y = 0;
           break;
         }
@@ -281,16 +303,15 @@ struct Tracer {
       tg.y &= tg.y - 1;
       const float4* tp = tris + 3 * ((size_t)tg.x + pos);
       const float4 a = ldg4f(tp), b = ldg4f(tp + 1), c = ldg4f(tp + 2);
-      const float t = tri_hit(r, a, b, c, best_t);
       if (COUNT) ++n_tris;
-      if (t > 0.f) {
-        const int32_t id = __float_as_int(a.w);
-        if (t < best_t || (t == best_t && id < best_id)) {
-          best_t = t;
-          best_id = id;
-        }
-      }
+      consider(tri_hit(r, a, b, c, best_t), __float_as_int(a.w));
     }
+    return true;
+  }
+
+  // After the leaf tests: pop the next group once the current node group has
+  // no pending child.  Returns true when the ray is finished.
+  __device__ __forceinline__ bool finish(uint2* ss, int stride, int sdepth, uint2* ls) {
     if (!(ng.y & 0xFF000000u)) {
       if (sp == 0) return true;
       ng = pop(ss, stride, sdepth, ls);
@@ -298,11 +319,110 @@ struct Tracer {
     return false;
   }
 
+  // Lane-serial step (descend + tri_serial + finish).  Returns true when the
+  // ray is finished.
+  __device__ __forceinline__ bool step(uint2* ss, int stride, int sdepth, uint2* ls,
+                                       int postpone_lanes, unsigned* status) {
+    if (!descend(ss, stride, sdepth, ls) || !tri_serial(ss, stride, sdepth, ls, postpone_lanes)) {
+      atomicOr(status, 1u);
+      return true;
+    }
+    return finish(ss, stride, sdepth, ls);
+  }
+
   __device__ __forceinline__ void result(float& range, int32_t& id) const {
     range = best_t;  // == max_range when nothing was hit
     id = best_id == kNoHit ? -1 : best_id;
   }
 };
+
+// Position of the k-th (0-based) set bit of `m` (k < popc(m)).
+__device__ __forceinline__ uint32_t nth_set_bit(uint32_t m, uint32_t k) {
+  uint32_t pos = 0;
+  uint32_t c = __popc(m & 0xFFFFu);
+  if (k >= c) { k -= c; m >>= 16; pos += 16; }
+  c = __popc(m & 0xFFu);
+  if (k >= c) { k -= c; m >>= 8; pos += 8; }
+  c = __popc(m & 0xFu);
+  if (k >= c) { k -= c; m >>= 4; pos += 4; }
+  c = __popc(m & 0x3u);
+  if (k >= c) { k -= c; m >>= 2; pos += 2; }
+  c = m & 1u;
+  if (k >= c) pos += 1;
+  return pos;
+}
+
+__device__ __forceinline__ unsigned long long hit_key(float t, int32_t id) {
+  return ((unsigned long long)__float_as_uint(t) << 32) | (uint32_t)id;
+}
+
+// Warp-compacted leaf tests: the (ray, triangle) pairs pending on all lanes
+// are numbered by a warp prefix sum and handed out 32 at a time, so every
+// lane tests a triangle (of any lane's ray) in every round instead of
+// waiting for the lane with the most triangles.  Each result is merged into
+// its ray's best (t, id) by a 64-bit atomic minimum on a per-lane
+// shared-memory key -- the same lexicographic minimum as the lane-serial
+// path.  All 32 lanes of the warp must call this together; lanes without a
+// ray simply have no triangles.  `keys` points at the warp's 32 slots.
+template <int W, bool COUNT>
+__device__ __forceinline__ void tri_phase_warp(Tracer<W, COUNT>& tr, unsigned long long* keys,
+                                               int lane) {
+  const unsigned FULL = 0xFFFFFFFFu;
+  const uint32_t bits = tr.tg.y & 0x00FFFFFFu;
+  const int cnt = __popc(bits);
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(FULL, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const int total = __shfl_sync(FULL, incl, 31);
+  if (total == 0) return;
+  if (cnt) keys[lane] = hit_key(tr.best_t, tr.best_id);
+  __syncwarp();
+  const uint64_t tri_ptr = (uint64_t)tr.tris;
+  for (int b = 0; b < total; b += 32) {
+    const int p = b + lane;
+    int lo = 0;
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+      const int v = __shfl_sync(FULL, incl, lo + s - 1);
+      if (v <= p) lo += s;
+    }
+    const int owner = lo < 31 ? lo : 31;
+    const int o_incl = __shfl_sync(FULL, incl, owner);
+    const int o_cnt = __shfl_sync(FULL, cnt, owner);
+    const uint32_t o_bits = __shfl_sync(FULL, bits, owner);
+    const uint32_t o_base = __shfl_sync(FULL, tr.tg.x, owner);
+    const uint32_t tp_lo = __shfl_sync(FULL, (uint32_t)tri_ptr, owner);
+    const uint32_t tp_hi = __shfl_sync(FULL, (uint32_t)(tri_ptr >> 32), owner);
+    Ray q;
+    q.ox = __shfl_sync(FULL, tr.r.ox, owner);
+    q.oy = __shfl_sync(FULL, tr.r.oy, owner);
+    q.oz = __shfl_sync(FULL, tr.r.oz, owner);
+    q.Sx = __shfl_sync(FULL, tr.r.Sx, owner);
+    q.Sy = __shfl_sync(FULL, tr.r.Sy, owner);
+    q.Sz = __shfl_sync(FULL, tr.r.Sz, owner);
+    q.k = __shfl_sync(FULL, tr.r.k, owner);
+    const float o_best = __shfl_sync(FULL, tr.best_t, owner);
+    if (p < total) {
+      const uint32_t k = (uint32_t)(p - (o_incl - o_cnt));
+      const uint32_t pos = nth_set_bit(o_bits, k);
+      const float4* tp = (const float4*)(((uint64_t)tp_hi << 32) | tp_lo) + 3 * ((size_t)o_base + pos);
+      const float4 a = ldg4f(tp), bb = ldg4f(tp + 1), c = ldg4f(tp + 2);
+      if (COUNT) ++tr.n_tris;
+      const float t = tri_hit(q, a, bb, c, o_best);
+      if (t > 0.f) atomicMin(&keys[owner], hit_key(t, __float_as_int(a.w)));
+    }
+  }
+  __syncwarp();
+  if (cnt) {
+    const unsigned long long k = keys[lane];
+    tr.best_t = __uint_as_float((uint32_t)(k >> 32));
+    tr.best_id = (int32_t)(uint32_t)k;
+  }
+  tr.tg.y = 0;
+}
 
 }  // namespace dev
 }  // namespace fgl

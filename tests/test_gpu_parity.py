@@ -145,14 +145,17 @@ def test_plain_variants_bitwise(indoor, indoor_scenes):
     for tiles in ((4, 8), (1, 32), (16, 2)):
         se = fgl.Sensor.from_table(tab, *tiles)
         for W in (8, 4):
-            for sdepth, postpone, block in ((12, 20, 128), (2, 100, 64), (1, -1, 256), (30, 50, 32)):
-                opts = fgl.BatchOpts(block_threads=block, stack_smem=sdepth, postpone_pct=postpone)
+            for sdepth, tri_mode, postpone, block in ((12, 0, 0, 128), (12, 1, 20, 128),
+                                                      (2, 1, 100, 64), (1, 1, -1, 256),
+                                                      (30, 0, 0, 32), (0, 0, 0, 512)):
+                opts = fgl.BatchOpts(block_threads=block, stack_smem=sdepth, postpone_pct=postpone,
+                                     tri_mode=tri_mode)
                 out = run_plain(indoor_scenes[W], se, P, w.max_range, opts)
                 if base is None:
                     base = out
                 else:
                     assert np.array_equal(out[0], base[0]) and np.array_equal(out[1], base[1]), \
-                        (tiles, W, sdepth, postpone, block)
+                        (tiles, W, sdepth, tri_mode, postpone, block)
 
 
 def test_batched_variants_bitwise_and_equal_plain(indoor, indoor_scenes, tiny):
@@ -171,11 +174,12 @@ def test_batched_variants_bitwise_and_equal_plain(indoor, indoor_scenes, tiny):
     items = [(indoor_scenes[8], s1, P1, 120.0), (indoor_scenes[4], s2, P2, 50.0),
              (tscene, s3, tP, 100.0), (indoor_scenes[8], s3, P2, 3.0)]
     stream = torch.cuda.Stream()
-    for packet, block, sdepth, refill, postpone, graph in (
-            (64, 128, 12, 8, 20, 0), (32, 32, 0, 1, -1, 0), (256, 256, 4, 32, 100, 1),
-            (96, 64, 2, 4, 30, 1), (64, 128, 12, 8, 20, 1)):
+    for packet, block, sdepth, refill, tri_mode, postpone, graph in (
+            (64, 128, 12, 8, 0, 0, 0), (32, 32, 0, 1, 1, -1, 0), (256, 256, 4, 32, 1, 100, 1),
+            (96, 64, 2, 4, 0, 30, 1), (64, 128, 12, 8, 1, 20, 1), (64, 512, 8, 16, 0, 0, 1)):
         opts = fgl.BatchOpts(packet_rays=packet, block_threads=block, stack_smem=sdepth,
-                             refill_min=refill, postpone_pct=postpone, use_graph=graph)
+                             refill_min=refill, postpone_pct=postpone, use_graph=graph,
+                             tri_mode=tri_mode)
         for rep in range(2 if graph else 1):          # graph replay too
             outs = run_batched(items, opts, stream=stream if graph else None)
             for (pr, pi), (br, bi) in zip(plain, outs):
