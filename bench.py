@@ -197,6 +197,7 @@ def main():
     ap.add_argument("--refill", type=int, default=0)
     ap.add_argument("--postpone", type=int, default=0)
     ap.add_argument("--width", type=int, default=8)
+    ap.add_argument("--tri", type=int, default=0)
     ap.add_argument("--tile", type=str, default="")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -228,7 +229,8 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.Stream(device=dev)
     opts = fgl.BatchOpts(packet_rays=args.packet, block_threads=args.block, stack_smem=args.sdepth,
-                         refill_min=args.refill, postpone_pct=args.postpone, use_graph=1)
+                         refill_min=args.refill, postpone_pct=args.postpone, use_graph=1,
+                         tri_mode=args.tri)
     items = [(scene, sensor, pose_state, w.max_range, out_r, out_i)]
     arr = fgl.make_items(items)
 
@@ -244,7 +246,8 @@ def main():
 
     # work counters for the roofline (one step, outside the timed region)
     copts = fgl.BatchOpts(packet_rays=args.packet, block_threads=args.block, stack_smem=args.sdepth,
-                          refill_min=args.refill, postpone_pct=args.postpone, count_work=1)
+                          refill_min=args.refill, postpone_pct=args.postpone, count_work=1,
+                          tri_mode=args.tri)
     fgl.work_counters()
     with torch.cuda.stream(stream):
         pose_state.copy_(walk_d[args.warmup % S])

@@ -107,7 +107,8 @@ fgl_status fgl_scene_get_stats(fgl_scene scene, fgl_scene_stats* out);
 fgl_status fgl_scene_export(fgl_scene scene, void* nodes, int64_t node_bytes, void* tris,
                             int64_t tri_bytes);
 /* Check, with the float32 decode arithmetic of the traversal, that every
- * quantized child box contains its subtree's triangles grown by the margin.
+ * quantized child box contains its subtree's triangles grown by the margin
+ * plus one quantum of that node's axis scale.
  * Writes the number of violations to *n_bad (0 for a correct build). */
 fgl_status fgl_scene_verify(fgl_scene scene, int64_t* n_bad);
 /* Upload (if evicted) / drop the device copy, keeping the host copy. */
@@ -165,7 +166,8 @@ typedef struct {
   int32_t blocks_per_sm;  /* persistent blocks per SM (0 = as many as fit) */
   int32_t use_graph;      /* 1 = capture the launch sequence in a CUDA graph and
                              replay it while the item layout is unchanged */
-  int32_t refill_min;     /* idle lanes before a warp pulls new rays (0 = 8) */
+  int32_t refill_min;     /* idle lanes before a warp pulls new rays (0 = 32:
+                             refill once the whole warp is idle) */
   int32_t postpone_pct;   /* tri_mode 1 only: postpone leaf tests when fewer than
                              this % of the warp's tracing lanes want them
                              (0 = 20; -1 = never) */

@@ -81,7 +81,7 @@ fgl_status device_info(DeviceInfo* out) {
 // option defaults
 // ---------------------------------------------------------------------------
 struct Opts {
-  int packet = 64, block = 128, sdepth = 12, bpsm = 0, graph = 0, refill = 8, postpone = 20,
+  int packet = 64, block = 128, sdepth = 12, bpsm = 0, graph = 0, refill = 32, postpone = 20,
       count = 0, tri_mode = 0;
 };
 

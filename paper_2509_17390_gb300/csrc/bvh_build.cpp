@@ -371,47 +371,51 @@ int build_bvh(const float* V, int64_t nv, const int32_t* T, int64_t nt, int widt
     }
 
     // ---- quantize the child boxes ----------------------------------------
+    // Each decoded child box must contain the child's content grown by the
+    // margin plus one quantum 2^k on every side (the traversal's plane
+    // offsets round by up to half a quantum).
     float p[3];
     int e[3];
     uint8_t q[6][8];
     std::memset(q, 0, sizeof(q));
     for (int a = 0; a < 3; ++a) {
-      double lo_t = std::numeric_limits<double>::infinity(), hi_t = -lo_t;
+      double lo_c = std::numeric_limits<double>::infinity(), hi_c = -lo_c;
       for (int i = 0; i < n; ++i) {
-        lo_t = std::min(lo_t, (double)kb[i].lo[a] - margin);
-        hi_t = std::max(hi_t, (double)kb[i].hi[a] + margin);
+        lo_c = std::min(lo_c, (double)kb[i].lo[a] - margin);
+        hi_c = std::max(hi_c, (double)kb[i].hi[a] + margin);
       }
-      float pa = (float)lo_t;
-      if ((double)pa > lo_t) pa = std::nextafterf(pa, -std::numeric_limits<float>::infinity());
-      p[a] = pa;
-      double ext = hi_t - (double)pa;
-      int k = (int)std::ceil(std::log2(ext / 255.0));
+      int k = (int)std::ceil(std::log2((hi_c - lo_c) / 253.0));
       k = std::max(k, -126);
+      float pa = 0.f;
       for (;; ++k) {
-        if (k > 127) {
+        if (k > 120) {
           *err = "scene extent too large to quantize";
           return 1;
         }
-        float scale = std::ldexp(1.0f, k);
+        const float scale = std::ldexp(1.0f, k);
+        const double sq = (double)scale;
+        pa = (float)(lo_c - sq);
+        if ((double)pa > lo_c - sq) pa = std::nextafterf(pa, -std::numeric_limits<float>::infinity());
         bool ok = true;
         for (int j = 0; j < n && ok; ++j) {
           int i = pos[j];
-          double lt = (double)kb[i].lo[a] - margin, ht = (double)kb[i].hi[a] + margin;
-          double ql = std::floor((lt - (double)pa) / scale);
-          double qh = std::ceil((ht - (double)pa) / scale);
+          const double lt = (double)kb[i].lo[a] - margin - sq;
+          const double ht = (double)kb[i].hi[a] + margin + sq;
+          double ql = std::floor((lt - (double)pa) / sq);
+          double qh = std::ceil((ht - (double)pa) / sq);
           ql = std::max(0.0, std::min(255.0, ql));
           while (ql > 0 && (double)decode((uint8_t)ql, scale, pa) > lt) ql -= 1.0;
+          if ((double)decode((uint8_t)ql, scale, pa) > lt) ok = false;
           if (qh < 0) qh = 0;
           while (qh <= 255 && (double)decode((uint8_t)std::min(qh, 255.0), scale, pa) < ht) qh += 1.0;
-          if (qh > 255) {
-            ok = false;
-            break;
-          }
+          if (qh > 255) ok = false;
+          if (!ok) break;
           q[a][j] = (uint8_t)ql;
           q[3 + a][j] = (uint8_t)qh;
         }
         if (ok) break;
       }
+      p[a] = pa;
       e[a] = k + 127;
     }
 
@@ -519,7 +523,8 @@ int64_t verify_bvh(const HostBVH& b, std::string* first_error) {
       for (int a = 0; a < 3; ++a) {
         float dlo = decode(rec[32 + a * W + j], scale[a], p[a]);
         float dhi = decode(rec[32 + (3 + a) * W + j], scale[a], p[a]);
-        if (!((double)dlo <= (double)cbx.lo[a] - m) || !((double)dhi >= (double)cbx.hi[a] + m))
+        const double g = m + (double)scale[a];  // margin plus one quantum
+        if (!((double)dlo <= (double)cbx.lo[a] - g) || !((double)dhi >= (double)cbx.hi[a] + g))
           fail("child box does not contain its content (node " + std::to_string(ni) + ", pos " +
                std::to_string(j) + ", axis " + std::to_string(a) + ")");
       }

@@ -35,8 +35,9 @@ namespace fgl {
 //                                             lo_x, lo_y, lo_z, hi_x, hi_y, hi_z
 //
 // Decoding a box coordinate is fmaf(q, 2^(e-127), p) in float32; the builder
-// rounds outward and adds `margin` on every side, and verifies the decoded
-// boxes with exactly that arithmetic.
+// rounds outward so that every decoded child box contains the child's content
+// grown by `margin` plus one quantum 2^(e-127) on every side, and verifies the
+// decoded boxes with exactly that arithmetic.
 //
 // Internal children of a node are stored contiguously from child_base in
 // increasing octant code; child index = child_base + popc(imask & ((1<<c)-1)).

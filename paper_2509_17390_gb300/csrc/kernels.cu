@@ -40,8 +40,8 @@ __device__ __forceinline__ int postpone_threshold(int pct) {
   return (__popc(__activemask()) * pct + 99) / 100;
 }
 
-// Dynamic shared memory: one 64-bit hit key per thread (the warp-compacted
-// leaf tests merge into these), then the [sdepth][blockDim] stack array.
+// Dynamic shared memory: one 64-bit hit key per thread (pooled leaf tests
+// merge into these), then the [sdepth][blockDim] stack array.
 struct Smem {
   unsigned long long* keys;  // this warp's 32 keys
   uint2* ss;                 // this thread's stack column
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(512) k_plain(const ItemDesc it, int sdepth, in
     tr.start(it.nodes, it.tris, it.max_range);
   }
   uint2 ls[kStackLocal];
-  if (tri_mode == 0) {
+  if (tri_mode != 1) {
     while (__any_sync(FULL, !done)) {
       bool ok = true;
       if (!done) ok = tr.descend(sm.ss, blockDim.x, sdepth, ls);
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(512) k_persistent(BatchHeader* __restrict__ hd
             c_tris += tr.n_tris;
           }
           tr.start(it.nodes, it.tris, it.max_range);
-          const int64_t o = (int64_t)pk_env * it.n_rays + __float_as_int(ds.w);
+                const int64_t o = (int64_t)pk_env * it.n_rays + __float_as_int(ds.w);
           out_r = it.out_range + o;
           out_t = it.out_tri + o;
           active = true;
@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(512) k_persistent(BatchHeader* __restrict__ hd
       continue;
     }
     bool fin = false;
-    if (tri_mode == 0) {
+    if (tri_mode != 1) {
       bool ok = true;
       if (active) ok = tr.descend(sm.ss, blockDim.x, sdepth, ls);
       dev::tri_phase_warp(tr, sm.keys, lane);

@@ -12,7 +12,7 @@ namespace fgl {
 size_t stack_smem_bytes(int block, int sdepth);
 
 // One thread per ray of one item (grid = ceil(n_env * n_rays / block)).
-// tri_mode 0: warp-compacted leaf tests; 1: lane-serial with postponing.
+// tri_mode 0: warp-pooled leaf tests; 1: lane-serial with postponing.
 cudaError_t launch_plain(int W, bool count, const ItemDesc& it, int block, int sdepth,
                          int tri_mode, int postpone_pct, cudaStream_t s);
 

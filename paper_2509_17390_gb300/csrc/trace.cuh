@@ -14,27 +14,17 @@
 #include <stdint.h>
 
 #include "fgl_internal.h"
+#include "ptx_ops.cuh"
 
 namespace fgl {
 namespace dev {
 
 constexpr int32_t kNoHit = 0x7FFFFFFF;
 
-__device__ __forceinline__ float max3f(float a, float b, float c) {
-  float r;
-  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-  return r;
-}
-__device__ __forceinline__ float min3f(float a, float b, float c) {
-  float r;
-  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-  return r;
-}
-
-// Byte `sel & 3` of `w` as an exact float: the byte is placed under the
-// exponent of 2^23 (giving 2^23 + b) and 2^23 is subtracted.
-__device__ __forceinline__ float byte_f(uint32_t w, uint32_t sel) {
-  return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7440u | sel)) - 8388608.0f;
+// Byte `sel & 3` of `w` placed under the exponent of 2^23: the float
+// 2^23 + b, exactly.  The traversal folds the -2^23 into its plane offsets.
+__device__ __forceinline__ float byte_magic(uint32_t w, uint32_t sel) {
+  return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7440u | sel));
 }
 
 __device__ __forceinline__ float sel3(float x, float y, float z, uint32_t k) {
@@ -47,7 +37,7 @@ __device__ __forceinline__ float4 ldg4f(const float4* p) { return __ldg(p); }
 // Per-ray constants.
 struct Ray {
   float ox, oy, oz;   // origin x_s = t_s
-  float ix, iy, iz;   // reciprocal direction, |d_a| clamped to >= 1e-30
+  float ix, iy, iz;   // reciprocal direction, |d_a| clamped to >= 1e-20
   float Sx, Sy, Sz;   // shear constants of the watertight test
   uint32_t k;         // kx | ky << 2 | kz << 4
   uint32_t oct;       // bit a set when the direction is negative along a
@@ -68,10 +58,13 @@ __device__ __forceinline__ void world_ray(const float* __restrict__ P, float4 ds
   oz = p[11];
 }
 
+// Reciprocal direction for the slab tests, |d| clamped to >= 1e-20.  The
+// approximate reciprocal scales every plane parameter of a ray by the same
+// factor (1 + e), |e| < 2^-22, which the builder's box margin covers.
 __device__ __forceinline__ float safe_rcp(float d) {
-  const float eps = 1e-30f;
+  const float eps = 1e-20f;
   float a = fabsf(d) < eps ? copysignf(eps, d) : d;
-  return __frcp_rn(a);
+  return rcp_approx(a);
 }
 
 __device__ __forceinline__ void setup_ray(Ray& r, float ox, float oy, float oz, float dx, float dy,
@@ -97,9 +90,11 @@ __device__ __forceinline__ void setup_ray(Ray& r, float ox, float oy, float oz, 
     ky = t;
   }
   r.k = kx | (ky << 2) | (kz << 4);
-  r.Sx = __fdiv_rn(sel3(dx, dy, dz, kx), dkz);
-  r.Sy = __fdiv_rn(sel3(dx, dy, dz, ky), dkz);
+  // Any fixed shear keeps the test watertight (it is applied identically to
+  // every vertex); S = (d_kx, d_ky, 1) / d_kz from one reciprocal.
   r.Sz = __frcp_rn(dkz);
+  r.Sx = __fmul_rn(sel3(dx, dy, dz, kx), r.Sz);
+  r.Sy = __fmul_rn(sel3(dx, dy, dz, ky), r.Sz);
 }
 
 // Watertight float32 ray/triangle test (Woop, Benthin & Wald 2013, JCGT 2(1)):
@@ -144,11 +139,15 @@ __device__ __forceinline__ float tri_hit(const Ray& r, float4 a, float4 b, float
   return __fdiv_rn(T, det);
 }
 
-// Slab test of the W children of one quantized node.  Child box planes are
-// p + q * 2^e along each axis, so the ray parameter of a plane is
-// fma(q, 2^e * inv_d, (p - o) * inv_d): one FMA per plane.  Returns the
-// node group (child_base, pending-child bits << 24 | imask) and the triangle
-// group (tri_base, leaf triangle bits).
+// Slab test of the W children of one quantized node.  A child box plane is
+// p + q * 2^e along each axis, so its ray parameter is q * S + B with
+// S = 2^e * inv_d and B = (p - o) * inv_d.  The byte q is read as the float
+// 2^23 + q (one byte permute) and the plane offset absorbs the 2^23 once per
+// node: t = fma(2^23 + q, S, B - 2^23 * S).  Rounding B - 2^23 * S costs at
+// most half a quantum, which the builder covers by growing every child box
+// one extra quantum.  The near and far planes of an axis go through one
+// packed f32x2 FMA.  Returns the node group (child_base, pending-child bits
+// << 24 | imask) and the triangle group (tri_base, leaf triangle bits).
 template <int W>
 __device__ __forceinline__ void intersect_node(const Ray& r, const uint4* __restrict__ nd,
                                                float tmax, uint2& ng, uint2& tg) {
@@ -166,13 +165,14 @@ __device__ __forceinline__ void intersect_node(const Ray& r, const uint4* __rest
     lox[1] = loy[1] = loz[1] = hix[1] = hiy[1] = hiz[1] = 0;
   }
   const uint32_t e = h0.w;
-  const float sx = __uint_as_float((e & 0xFFu) << 23);
-  const float sy = __uint_as_float(((e >> 8) & 0xFFu) << 23);
-  const float sz = __uint_as_float(((e >> 16) & 0xFFu) << 23);
-  const float Sx = __fmul_rn(sx, r.ix), Sy = __fmul_rn(sy, r.iy), Sz = __fmul_rn(sz, r.iz);
-  const float Bx = __fmul_rn(__fsub_rn(__uint_as_float(h0.x), r.ox), r.ix);
-  const float By = __fmul_rn(__fsub_rn(__uint_as_float(h0.y), r.oy), r.iy);
-  const float Bz = __fmul_rn(__fsub_rn(__uint_as_float(h0.z), r.oz), r.iz);
+  const float Sx = __fmul_rn(__uint_as_float((e & 0xFFu) << 23), r.ix);
+  const float Sy = __fmul_rn(__uint_as_float(((e >> 8) & 0xFFu) << 23), r.iy);
+  const float Sz = __fmul_rn(__uint_as_float(((e >> 16) & 0xFFu) << 23), r.iz);
+  const float Bx = fmaf(-8388608.0f, Sx, __fmul_rn(__fsub_rn(__uint_as_float(h0.x), r.ox), r.ix));
+  const float By = fmaf(-8388608.0f, Sy, __fmul_rn(__fsub_rn(__uint_as_float(h0.y), r.oy), r.iy));
+  const float Bz = fmaf(-8388608.0f, Sz, __fmul_rn(__fsub_rn(__uint_as_float(h0.z), r.oz), r.iz));
+  const uint64_t S2x = pack2f(Sx, Sx), S2y = pack2f(Sy, Sy), S2z = pack2f(Sz, Sz);
+  const uint64_t B2x = pack2f(Bx, Bx), B2y = pack2f(By, By), B2z = pack2f(Bz, Bz);
   const bool fx = r.oct & 1u, fy = r.oct & 2u, fz = r.oct & 4u;
   // Per 4-child meta word, byte-parallel: bit position of each child's first
   // hit bit (internal children: 24 + (code ^ oct); leaves: triangle offset)
@@ -193,12 +193,10 @@ __device__ __forceinline__ void intersect_node(const Ray& r, const uint4* __rest
     const uint32_t nxw = fx ? hix[w] : lox[w], fxw = fx ? lox[w] : hix[w];
     const uint32_t nyw = fy ? hiy[w] : loy[w], fyw = fy ? loy[w] : hiy[w];
     const uint32_t nzw = fz ? hiz[w] : loz[w], fzw = fz ? loz[w] : hiz[w];
-    const float tnx = fmaf(byte_f(nxw, s), Sx, Bx);
-    const float tny = fmaf(byte_f(nyw, s), Sy, By);
-    const float tnz = fmaf(byte_f(nzw, s), Sz, Bz);
-    const float tfx = fmaf(byte_f(fxw, s), Sx, Bx);
-    const float tfy = fmaf(byte_f(fyw, s), Sy, By);
-    const float tfz = fmaf(byte_f(fzw, s), Sz, Bz);
+    float tnx, tfx, tny, tfy, tnz, tfz;
+    unpack2f(ffma2(pack2f(byte_magic(nxw, s), byte_magic(fxw, s)), S2x, B2x), tnx, tfx);
+    unpack2f(ffma2(pack2f(byte_magic(nyw, s), byte_magic(fyw, s)), S2y, B2y), tny, tfy);
+    unpack2f(ffma2(pack2f(byte_magic(nzw, s), byte_magic(fzw, s)), S2z, B2z), tnz, tfz);
     const float tn = max3f(tnx, tny, fmaxf(tnz, 0.f));
     const float tf = min3f(tfx, tfy, fminf(tfz, tmax));
     const uint32_t pos = __byte_perm(idx_w[w], 0u, 0x4440u | s);

@@ -56,7 +56,8 @@ def decode_nodes(nodes: np.ndarray, width: int):
     q = rec[:, 32:32 + 6 * width].reshape(-1, 6, width).astype(np.float32)
     lo = (q[:, 0:3] * scale[:, :, None]).astype(np.float32) + p[:, :, None]   # q*2^e is exact
     hi = (q[:, 3:6] * scale[:, :, None]).astype(np.float32) + p[:, :, None]
-    return dict(p=p, imask=imask, child_base=base[:, 0], tri_base=base[:, 1], meta=meta, lo=lo, hi=hi)
+    return dict(p=p, imask=imask, child_base=base[:, 0], tri_base=base[:, 1], meta=meta, lo=lo, hi=hi,
+                scale=scale)
 
 
 def check_tree(v, t, width):
@@ -90,8 +91,9 @@ def check_tree(v, t, width):
                 k = int(D["tri_base"][ni]) + off
                 pts = tv[k:k + cnt].reshape(-1, 3).astype(np.float64)
                 lo, hi = pts.min(0), pts.max(0)
-            assert np.all(D["lo"][ni, :, j].astype(np.float64) <= lo - m), (ni, j)
-            assert np.all(D["hi"][ni, :, j].astype(np.float64) >= hi + m), (ni, j)
+            g = m + D["scale"][ni].astype(np.float64)        # margin + one quantum
+            assert np.all(D["lo"][ni, :, j].astype(np.float64) <= lo - g), (ni, j)
+            assert np.all(D["hi"][ni, :, j].astype(np.float64) >= hi + g), (ni, j)
             clo[ni] = np.minimum(clo[ni], lo)
             chi[ni] = np.maximum(chi[ni], hi)
     assert sc.verify() == 0

@@ -145,7 +145,7 @@ def test_plain_variants_bitwise(indoor, indoor_scenes):
     for tiles in ((4, 8), (1, 32), (16, 2)):
         se = fgl.Sensor.from_table(tab, *tiles)
         for W in (8, 4):
-            for sdepth, tri_mode, postpone, block in ((12, 0, 0, 128), (12, 1, 20, 128),
+            for sdepth, tri_mode, postpone, block in ((12, 0, 0, 128), (12, 1, 20, 128), (8, 0, 0, 96),
                                                       (2, 1, 100, 64), (1, 1, -1, 256),
                                                       (30, 0, 0, 32), (0, 0, 0, 512)):
                 opts = fgl.BatchOpts(block_threads=block, stack_smem=sdepth, postpone_pct=postpone,
@@ -176,7 +176,7 @@ def test_batched_variants_bitwise_and_equal_plain(indoor, indoor_scenes, tiny):
     stream = torch.cuda.Stream()
     for packet, block, sdepth, refill, tri_mode, postpone, graph in (
             (64, 128, 12, 8, 0, 0, 0), (32, 32, 0, 1, 1, -1, 0), (256, 256, 4, 32, 1, 100, 1),
-            (96, 64, 2, 4, 0, 30, 1), (64, 128, 12, 8, 1, 20, 1), (64, 512, 8, 16, 0, 0, 1)):
+            (96, 64, 2, 4, 0, 30, 1), (64, 128, 12, 8, 1, 20, 1), (64, 512, 8, 16, 0, 0, 1), (64, 128, 12, 32, 0, 0, 1)):
         opts = fgl.BatchOpts(packet_rays=packet, block_threads=block, stack_smem=sdepth,
                              refill_min=refill, postpone_pct=postpone, use_graph=graph,
                              tri_mode=tri_mode)
