@@ -200,6 +200,24 @@ fgl_status fgl_cast_batched(const fgl_cast_item* items, int32_t n_items,
 fgl_status fgl_cast_batched_host(const fgl_cast_item* items, int32_t n_items,
                                  const fgl_batch_opts* opts, fgl_stream stream);
 
+/* fgl_cast_batched for callers that cannot allocate device memory (code
+ * running during CUDA graph capture, real-time loops that must not trigger an
+ * allocator's device synchronisation, processes whose device memory belongs to
+ * a pool they do not own).  The paper has no counterpart: this is an
+ * interface for such callers, not part of the method.
+ *   Same arguments, layouts and results as fgl_cast_batched (use_graph is
+ *   ignored); the caller still owns poses and outputs.  The work-queue scratch
+ *   is a fixed array of ~20 KiB inside the library (held by every GPU that
+ *   loads it until the process exits), so a call allocates nothing on the
+ *   device, and nothing on the host when it succeeds.
+ *   Limit: at most 256 items per call; more is rejected with FGL_ERR_INVALID.
+ *   The first call on each device looks up the array's device address (with
+ *   that device current); make that first call before any stream capture.
+ *   All calls share the array and reset its queue head: calls whose work
+ *   overlaps on the GPU race, so issue them on one stream or order them. */
+fgl_status fgl_cast_batched_static(const fgl_cast_item* items, int32_t n_items,
+                                   const fgl_batch_opts* opts, fgl_stream stream);
+
 /* Wait for the stream, then report any asynchronous CUDA error or
  * device-side traversal error (FGL_ERR_DEVICE) raised since the last check. */
 fgl_status fgl_sync(fgl_stream stream);

@@ -19,7 +19,7 @@ import numpy as np
 from . import build_native
 
 __all__ = ["Scene", "Sensor", "BatchOpts", "cast", "cast_opts", "cast_batched",
-           "cast_batched_host", "world_rays", "sync", "work_counters", "FglError", "lib"]
+           "cast_batched_host", "cast_batched_static", "world_rays", "sync", "work_counters", "FglError", "lib"]
 
 FGL_OK, FGL_ERR_INVALID, FGL_ERR_OOM, FGL_ERR_CUDA = 0, 1, 2, 3
 FGL_ERR_BUDGET, FGL_ERR_TIMEOUT, FGL_ERR_CANCELLED, FGL_ERR_DEVICE = 4, 5, 6, 7
@@ -92,6 +92,7 @@ def lib():
                 "fgl_cast_opts": ([P, P, P, I32, F32, P, P, P, P], I32),
                 "fgl_cast_batched": ([P, I32, P, P], I32),
                 "fgl_cast_batched_host": ([P, I32, P, P], I32),
+                "fgl_cast_batched_static": ([P, I32, P, P], I32),
                 "fgl_sync": ([P], I32),
                 "fgl_work_counters": ([P, P, P], I32),
                 "fgl_world_rays": ([P, P, I32, P, P, P], I32),
@@ -290,6 +291,17 @@ def cast_batched(items: Sequence[tuple], opts: Optional[BatchOpts] = None, strea
         arr = make_items(items)
     _check(lib().fgl_cast_batched(arr, len(items), ctypes.byref(opts) if opts else None,
                                   _stream_handle(stream)))
+
+
+def cast_batched_static(items: Sequence[tuple], opts: Optional[BatchOpts] = None, stream=None,
+                        arr=None):
+    """fgl_cast_batched_static: the batched form without any allocation (work
+    queue in a fixed library array, at most 256 items; calls that overlap on
+    the GPU race)."""
+    if arr is None:
+        arr = make_items(items)
+    _check(lib().fgl_cast_batched_static(arr, len(items), ctypes.byref(opts) if opts else None,
+                                         _stream_handle(stream)))
 
 
 def cast_batched_host(items: Sequence[tuple], opts: Optional[BatchOpts] = None, stream=None):

@@ -346,6 +346,29 @@ fgl_status run_batched(const fgl_cast_item* items, int n, const Opts& o, cudaStr
 
 }  // namespace
 
+namespace fgl {
+
+// Item check + descriptor fill for fgl_cast_batched_static (static_batch.cu):
+// the same rules as check_item/make_desc, with constant messages so that a
+// valid item costs no allocation.  Returns nullptr when the item is valid.
+const char* static_item_desc(const fgl_cast_item& it, ItemDesc* d, int* width) {
+  if (!it.scene || !it.sensor) return "null scene or sensor in an item";
+  if (it.n_env < 0) return "n_env < 0 in an item";
+  if (!(std::isfinite(it.max_range) && it.max_range > 0.f))
+    return "max_range must be finite and > 0";
+  if (it.n_env > 0 && (!it.poses || !it.out_range || !it.out_tri))
+    return "null poses or output pointer in an item";
+  if (!it.scene->d_nodes) return "scene is not resident on the device";
+  if ((int64_t)it.n_env * it.sensor->n_rays > ((int64_t)1 << 40)) return "too many rays in an item";
+  *d = make_desc(it);
+  *width = it.scene->bvh.width;
+  return nullptr;
+}
+
+void record_error(int status, const char* msg) { fail((fgl_status)status, msg); }
+
+}  // namespace fgl
+
 extern "C" {
 
 const char* fgl_last_error(void) { return g_err.c_str(); }

@@ -1,0 +1,192 @@
+// fgl_cast_batched_static: the batched cast for callers that cannot allocate
+// device memory.
+//
+// Some callers must not call cudaMalloc (or any allocator) at all: code that
+// runs while a CUDA graph is being captured, host threads of a real-time
+// simulation loop where an allocation's implicit device synchronisation is
+// not acceptable, or processes whose device memory is fully handed to a
+// pooling allocator they do not own.  fgl_cast_batched keeps its work-queue
+// scratch (queue head + item table) in library-allocated, per-stream device
+// memory; this entry point instead keeps it in one fixed, file-scope device
+// array, so a call allocates nothing on the device (and nothing on the host
+// when it succeeds).
+//
+// The array holds at most kStaticMaxItems items.  It belongs to every GPU that
+// loads the library until the process exits, and every call shares it: the
+// queue head is reset by each call, and the array keeps the last call's
+// contents.  Calls whose kernels overlap on the GPU therefore race -- issue
+// them on one stream, or order them.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <mutex>
+
+#include "fgl.h"
+#include "fgl_internal.h"
+#include "kernels.h"
+
+namespace fgl {
+// Allocation-free item check + descriptor fill, and error recording (api.cu).
+const char* static_item_desc(const fgl_cast_item& it, ItemDesc* d, int* width);
+void record_error(int status, const char* msg);
+}  // namespace fgl
+
+using namespace fgl;
+
+namespace {
+
+constexpr int kStaticMaxItems = 256;
+constexpr int kMaxGroups = 2;  // one per BVH width (8 and 4)
+constexpr size_t kStaticBytes = kMaxGroups * sizeof(BatchHeader) + kStaticMaxItems * sizeof(ItemDesc);
+constexpr size_t kStaticWords = kStaticBytes / 16;
+static_assert(kStaticBytes % 16 == 0, "scratch is copied in 16-byte words");
+
+// The scratch itself.  In host code this name is only a host-side stand-in;
+// its device address comes from cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+
+// The table image travels as a kernel parameter (about 20.6 KB, within the
+// 32,764-byte parameter limit), so no host staging buffer is needed either.
+struct StaticImage {
+  uint32_t n_words;
+  uint32_t pad[3];
+  uint4 words[kStaticWords];
+};
+
+__global__ void k_static_table(const StaticImage img, uint4* __restrict__ dst) {
+  for (uint32_t i = threadIdx.x; i < img.n_words; i += blockDim.x) dst[i] = img.words[i];
+}
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void* g_ptr[kMaxDevices];
+bool g_ready[kMaxDevices];
+
+// Device address of the scratch array on the current device (looked up once
+// per device, on the first call made with that device current).
+cudaError_t scratch_ptr(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_ready[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return e;
+    g_ptr[dev] = p;
+    g_ready[dev] = true;
+  }
+  *out = g_ptr[dev];
+  return cudaSuccess;
+}
+
+fgl_status err(int status, const char* msg) {
+  record_error(status, msg);
+  return (fgl_status)status;
+}
+
+fgl_status cuda_err(cudaError_t e) {
+  record_error(FGL_ERR_CUDA, cudaGetErrorString(e));
+  return FGL_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" fgl_status fgl_cast_batched_static(const fgl_cast_item* items, int32_t n_items,
+                                              const fgl_batch_opts* opts, fgl_stream stream) {
+  if (n_items < 0) return err(FGL_ERR_INVALID, "n_items < 0");
+  if (n_items > kStaticMaxItems)
+    return err(FGL_ERR_INVALID,
+               "fgl_cast_batched_static: more than 256 items (the fixed scratch array's maximum); "
+               "split the batch or use fgl_cast_batched");
+  if (n_items > 0 && !items) return err(FGL_ERR_INVALID, "items is null");
+
+  // launch options (same meaning and defaults as fgl_cast_batched; use_graph is ignored)
+  int packet = 64, block = 128, sdepth = 12, bpsm = 0, refill = 32, postpone = 20, count = 0,
+      tri_mode = 0;
+  if (opts) {
+    if (opts->packet_rays) packet = opts->packet_rays;
+    if (opts->block_threads) block = opts->block_threads;
+    if (opts->stack_smem) sdepth = opts->stack_smem;
+    if (opts->blocks_per_sm) bpsm = opts->blocks_per_sm;
+    if (opts->refill_min) refill = opts->refill_min;
+    if (opts->postpone_pct) postpone = opts->postpone_pct;
+    count = opts->count_work ? 1 : 0;
+    tri_mode = opts->tri_mode;
+  }
+  if (packet < 32 || packet % 32 || packet > (1 << 20))
+    return err(FGL_ERR_INVALID, "packet_rays must be a positive multiple of 32");
+  if (block < 32 || block % 32 || block > 512)
+    return err(FGL_ERR_INVALID, "block_threads must be a multiple of 32 in [32, 512]");
+  if (sdepth < 0 || sdepth > 64) return err(FGL_ERR_INVALID, "stack_smem must be in [0, 64]");
+  if (bpsm < 0 || bpsm > 64) return err(FGL_ERR_INVALID, "blocks_per_sm must be in [0, 64]");
+  if (refill < 1 || refill > 32) return err(FGL_ERR_INVALID, "refill_min must be in [1, 32]");
+  if (postpone > 100) return err(FGL_ERR_INVALID, "postpone_pct must be <= 100");
+  if (tri_mode != 0 && tri_mode != 1) return err(FGL_ERR_INVALID, "tri_mode must be 0 or 1");
+
+  // item descriptors, grouped by BVH width, written straight into the image
+  StaticImage img;
+  img.n_words = 0;
+  size_t group_off[kMaxGroups] = {0, 0};
+  int group_w[kMaxGroups] = {0, 0};
+  int n_groups = 0;
+  size_t used = 0;
+  for (int W : {8, 4}) {
+    BatchHeader h;
+    std::memset(&h, 0, sizeof(h));
+    const size_t hdr_off = used;
+    size_t off = used + sizeof(BatchHeader);
+    int n_in = 0;
+    int64_t packets = 0;
+    for (int i = 0; i < n_items; ++i) {
+      ItemDesc d;
+      int width = 0;
+      const char* msg = static_item_desc(items[i], &d, &width);
+      if (msg) return err(FGL_ERR_INVALID, msg);
+      if (width != W || d.n_env == 0) continue;
+      d.pk_per_env = (d.n_rays + packet - 1) / packet;
+      d.pk_begin = packets;
+      packets += (int64_t)d.pk_per_env * d.n_env;
+      std::memcpy((char*)img.words + off, &d, sizeof(d));
+      off += sizeof(d);
+      ++n_in;
+    }
+    if (n_in == 0) continue;
+    h.head = 0;  // the queue starts empty on every call
+    h.n_packets = packets;
+    h.n_items = n_in;
+    h.packet_rays = packet;
+    std::memcpy((char*)img.words + hdr_off, &h, sizeof(h));
+    group_off[n_groups] = hdr_off;
+    group_w[n_groups] = W;
+    ++n_groups;
+    used = off;
+  }
+  if (n_groups == 0) return FGL_OK;
+  img.n_words = (uint32_t)(used / 16);
+
+  cudaStream_t s = (cudaStream_t)stream;
+  void* scratch = nullptr;
+  cudaError_t e = scratch_ptr(&scratch);
+  if (e != cudaSuccess) return cuda_err(e);
+  int dev = 0, sms = 0, optin = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_err(e);
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return cuda_err(e);
+  if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
+    return cuda_err(e);
+  if (stack_smem_bytes(block, sdepth) > (size_t)optin)
+    return err(FGL_ERR_INVALID, "block_threads * stack_smem * 8 exceeds shared memory");
+
+  k_static_table<<<1, 256, 0, s>>>(img, (uint4*)scratch);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_err(e);
+  for (int g = 0; g < n_groups; ++g) {
+    const int per_sm = bpsm ? bpsm : persistent_blocks_per_sm(group_w[g], count != 0, block, sdepth);
+    const int grid = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+    e = launch_persistent(group_w[g], count != 0, (char*)scratch + group_off[g], grid, block,
+                          sdepth, refill, tri_mode, postpone, s);
+    if (e != cudaSuccess) return cuda_err(e);
+  }
+  return FGL_OK;
+}
