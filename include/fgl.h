@@ -218,6 +218,31 @@ fgl_status fgl_cast_batched_host(const fgl_cast_item* items, int32_t n_items,
 fgl_status fgl_cast_batched_static(const fgl_cast_item* items, int32_t n_items,
                                    const fgl_batch_opts* opts, fgl_stream stream);
 
+/* Autotuner for the batched form: picks the launch options (packet size,
+ * block size, shared-memory stack depth, refill threshold, leaf-test mode)
+ * that run `items` fastest, by coordinate descent from the defaults, timing
+ * each candidate with CUDA events on `stream` (median of `reps` runs after one
+ * warm-up).  The items are really cast (their outputs are overwritten).  BVH
+ * width and sensor tile shape are properties of the scene and sensor objects;
+ * tune them by building variants and calling this once per variant.  The
+ * paper fixes none of these; they change speed only, never results.
+ *   best: in = starting point and use_graph/count_work settings (NULL fields
+ *         = defaults), out = the fastest options found.
+ *   Errors: as fgl_cast_batched. */
+typedef struct {
+  int32_t reps;        /* timed runs per candidate (0 = 3) */
+  int32_t passes;      /* coordinate-descent passes over the dimensions (0 = 2) */
+} fgl_tune_opts;
+
+typedef struct {
+  double best_ms;      /* median time of the chosen options */
+  double start_ms;     /* median time of the starting options */
+  int32_t trials;      /* candidates timed */
+} fgl_tune_result;
+
+fgl_status fgl_autotune(const fgl_cast_item* items, int32_t n_items, const fgl_tune_opts* topts,
+                        fgl_batch_opts* best, fgl_tune_result* result, fgl_stream stream);
+
 /* Wait for the stream, then report any asynchronous CUDA error or
  * device-side traversal error (FGL_ERR_DEVICE) raised since the last check. */
 fgl_status fgl_sync(fgl_stream stream);
@@ -230,6 +255,89 @@ fgl_status fgl_work_counters(uint64_t* rays, uint64_t* node_visits, uint64_t* tr
  * out_o, out_d device float32 [n_env * n_rays][3]. */
 fgl_status fgl_world_rays(fgl_sensor sensor, const float* poses, int32_t n_env, float* out_o,
                           float* out_d, fgl_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* Serving: continuous batching of scan requests                             */
+/* ------------------------------------------------------------------------ */
+/* The paper batches thousands of environments on one GPU (Sec. IV-C; Table
+ * I) but describes no request serving; this layer schedules the same casts.
+ * Requests (scene, sensor, n_env host poses, host output buffers) arrive at
+ * any time.  A worker admits them in arrival order while their device memory
+ * (poses + results) plus any scene that must be uploaded fits the HBM budget,
+ * evicting least-recently-used idle scenes (the scene keeps its host copy, so
+ * re-admission is an upload).  Every tick packs up to tick_rays rays from all
+ * admitted requests into one batched launch, so large requests advance over
+ * several ticks and requests that arrive meanwhile join the next tick.
+ * Results are copied to the caller's host buffers before the request
+ * completes; latency is submission -> results in host memory.  mode 1 serves
+ * the same requests the plain way (one fgl_cast per environment, one request
+ * at a time) for comparison. */
+typedef struct fgl_server_s* fgl_server;
+
+typedef struct {
+  int64_t hbm_budget_bytes;  /* device bytes for resident scenes + admitted
+                                requests (0 = 150 GiB) */
+  int64_t tick_rays;         /* rays per tick (0 = 16 Mi) */
+  int32_t max_active;        /* admitted requests at once (0 = 4096) */
+  int32_t mode;              /* 0 = continuous batching, 1 = one launch per env */
+  fgl_batch_opts opts;       /* launch options of a tick (use_graph ignored) */
+} fgl_server_opts;
+
+typedef struct {
+  int32_t scene_id;          /* from fgl_server_add_scene */
+  int32_t sensor_id;         /* from fgl_server_add_sensor */
+  int32_t n_env;             /* >= 1 */
+  float max_range;
+  const float* poses;        /* host float32 [n_env][3][4]; copied by submit */
+  float* out_range;          /* host float32 [n_env * n_rays]; page-locked is fastest */
+  int32_t* out_tri;          /* host int32  [n_env * n_rays] */
+} fgl_request;
+
+typedef struct {
+  int32_t status;            /* the request's fgl_status */
+  double queue_ms;           /* submission -> admission */
+  double latency_ms;         /* submission -> results in host memory */
+  int64_t rays;
+} fgl_request_info;
+
+typedef struct {
+  int64_t submitted, completed, rejected, cancelled;
+  int64_t evictions, uploads, ticks;
+  int64_t rays;              /* rays of completed requests */
+  double p50_ms, p99_ms, mean_ms;  /* latency of completed requests */
+  double busy_s;             /* first submission -> last completion */
+  double rays_per_s;         /* rays / busy_s */
+  int64_t device_bytes;      /* held now (resident scenes + admitted requests) */
+  int64_t pending, active;   /* requests waiting / admitted now */
+} fgl_server_stats;
+
+/* Create a server on the current device (worker + completion threads, two
+ * streams).  Errors: FGL_ERR_INVALID (mode), FGL_ERR_CUDA. */
+fgl_status fgl_server_create(const fgl_server_opts* opts, fgl_server* out);
+/* Register a scene / sensor (the caller keeps ownership and must keep them
+ * alive until fgl_server_destroy; the server uploads / evicts scenes). */
+fgl_status fgl_server_add_scene(fgl_server server, fgl_scene scene, int32_t* scene_id);
+fgl_status fgl_server_add_sensor(fgl_server server, fgl_sensor sensor, int32_t* sensor_id);
+/* Queue a request.  Errors (synchronous): FGL_ERR_INVALID for unknown ids,
+ * n_env < 1, null buffers, non-finite poses or max_range; FGL_ERR_BUDGET when
+ * the request and its scene exceed the whole budget. */
+fgl_status fgl_server_submit(fgl_server server, const fgl_request* req, int64_t* ticket);
+/* Wait for a request (timeout_ms < 0: forever); on return the ticket is
+ * released.  Returns the request's status (FGL_ERR_TIMEOUT if still running,
+ * the ticket stays valid then; FGL_ERR_CANCELLED; FGL_ERR_OOM when its device
+ * allocation failed). */
+fgl_status fgl_server_wait(fgl_server server, int64_t ticket, int32_t timeout_ms,
+                           fgl_request_info* info);
+/* Cancel a request: pending ones finish at once, running ones stop taking
+ * new ticks and finish when their in-flight chunks are done. */
+fgl_status fgl_server_cancel(fgl_server server, int64_t ticket);
+fgl_status fgl_server_get_stats(fgl_server server, fgl_server_stats* out);
+fgl_status fgl_server_reset_stats(fgl_server server);
+/* Fault injection for tests: the next n admissions fail their device
+ * allocation (those requests complete with FGL_ERR_OOM). */
+fgl_status fgl_server_inject_alloc_failures(fgl_server server, int32_t n);
+/* Wait (up to 60 s) for in-flight ticks, stop the threads, free buffers. */
+fgl_status fgl_server_destroy(fgl_server server);
 
 /* Thread-local message for the last non-OK status of this thread. */
 const char* fgl_last_error(void);

@@ -19,7 +19,7 @@ import numpy as np
 from . import build_native
 
 __all__ = ["Scene", "Sensor", "BatchOpts", "cast", "cast_opts", "cast_batched",
-           "cast_batched_host", "cast_batched_static", "world_rays", "sync", "work_counters", "FglError", "lib"]
+           "cast_batched_host", "cast_batched_static", "autotune", "TuneOpts", "world_rays", "sync", "work_counters", "FglError", "lib"]
 
 FGL_OK, FGL_ERR_INVALID, FGL_ERR_OOM, FGL_ERR_CUDA = 0, 1, 2, 3
 FGL_ERR_BUDGET, FGL_ERR_TIMEOUT, FGL_ERR_CANCELLED, FGL_ERR_DEVICE = 4, 5, 6, 7
@@ -93,6 +93,17 @@ def lib():
                 "fgl_cast_batched": ([P, I32, P, P], I32),
                 "fgl_cast_batched_host": ([P, I32, P, P], I32),
                 "fgl_cast_batched_static": ([P, I32, P, P], I32),
+                "fgl_autotune": ([P, I32, P, P, P, P], I32),
+                "fgl_server_create": ([P, P], I32),
+                "fgl_server_add_scene": ([P, P, P], I32),
+                "fgl_server_add_sensor": ([P, P, P], I32),
+                "fgl_server_submit": ([P, P, P], I32),
+                "fgl_server_wait": ([P, I64, I32, P], I32),
+                "fgl_server_cancel": ([P, I64], I32),
+                "fgl_server_get_stats": ([P, P], I32),
+                "fgl_server_reset_stats": ([P], I32),
+                "fgl_server_inject_alloc_failures": ([P, I32], I32),
+                "fgl_server_destroy": ([P], I32),
                 "fgl_sync": ([P], I32),
                 "fgl_work_counters": ([P, P, P], I32),
                 "fgl_world_rays": ([P, P, I32, P, P, P], I32),
@@ -304,6 +315,26 @@ def cast_batched_static(items: Sequence[tuple], opts: Optional[BatchOpts] = None
                                          _stream_handle(stream)))
 
 
+class TuneOpts(ctypes.Structure):
+    _fields_ = [("reps", I32), ("passes", I32)]
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("best_ms", F64), ("start_ms", F64), ("trials", I32)]
+
+
+def autotune(items: Sequence[tuple], start: Optional[BatchOpts] = None, reps: int = 3,
+             passes: int = 2, stream=None):
+    """fgl_autotune: fastest launch options for these items.  Returns
+    (BatchOpts, {"best_ms", "start_ms", "trials"})."""
+    arr = make_items(items)
+    best = BatchOpts() if start is None else BatchOpts(*[getattr(start, k) for k, _ in BatchOpts._fields_])
+    res = TuneResult()
+    _check(lib().fgl_autotune(arr, len(items), ctypes.byref(TuneOpts(reps, passes)), ctypes.byref(best),
+                              ctypes.byref(res), _stream_handle(stream)))
+    return best, {"best_ms": res.best_ms, "start_ms": res.start_ms, "trials": res.trials}
+
+
 def cast_batched_host(items: Sequence[tuple], opts: Optional[BatchOpts] = None, stream=None):
     """End-to-end batched form (fgl_cast_batched_host): poses and outputs are
     host tensors/arrays (page-locked for full speed); blocks until done."""
@@ -351,3 +382,94 @@ def work_counters():
     r, n, t = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
     _check(lib().fgl_work_counters(ctypes.byref(r), ctypes.byref(n), ctypes.byref(t)))
     return int(r.value), int(n.value), int(t.value)
+
+
+# ---------------------------------------------------------------------------
+# serving (fgl_server_*)
+# ---------------------------------------------------------------------------
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", I64), ("tick_rays", I64), ("max_active", I32),
+                ("mode", I32), ("opts", BatchOpts)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("scene_id", I32), ("sensor_id", I32), ("n_env", I32), ("max_range", F32),
+                ("poses", P), ("out_range", P), ("out_tri", P)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("status", I32), ("queue_ms", F64), ("latency_ms", F64), ("rays", I64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", I64), ("completed", I64), ("rejected", I64), ("cancelled", I64),
+                ("evictions", I64), ("uploads", I64), ("ticks", I64), ("rays", I64),
+                ("p50_ms", F64), ("p99_ms", F64), ("mean_ms", F64), ("busy_s", F64),
+                ("rays_per_s", F64), ("device_bytes", I64), ("pending", I64), ("active", I64)]
+
+
+class Server:
+    """Continuous-batching scan server (fgl_server_*).  Scenes and sensors
+    registered with it must stay alive until close()."""
+
+    def __init__(self, hbm_budget_bytes: int = 0, tick_rays: int = 0, max_active: int = 0,
+                 mode: int = 0, opts: Optional[BatchOpts] = None):
+        o = ServerOpts(hbm_budget_bytes, tick_rays, max_active, mode, opts or BatchOpts())
+        h = P()
+        _check(lib().fgl_server_create(ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        self._keep = []
+
+    def add_scene(self, scene: Scene) -> int:
+        i = I32()
+        _check(lib().fgl_server_add_scene(self._h, scene.handle, ctypes.byref(i)))
+        self._keep.append(scene)
+        return i.value
+
+    def add_sensor(self, sensor: Sensor) -> int:
+        i = I32()
+        _check(lib().fgl_server_add_sensor(self._h, sensor.handle, ctypes.byref(i)))
+        self._keep.append(sensor)
+        return i.value
+
+    def submit(self, scene_id: int, sensor_id: int, poses, max_range: float, out_range, out_tri) -> int:
+        """poses: host float32 [n_env,3,4]; outputs: host arrays/tensors."""
+        n_env = int(np.prod(poses.shape)) // 12
+        r = Request(scene_id, sensor_id, n_env, float(max_range), _host_ptr(poses),
+                    _host_ptr(out_range), _host_ptr(out_tri))
+        t = I64()
+        _check(lib().fgl_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = -1, check: bool = True) -> dict:
+        info = RequestInfo()
+        st = lib().fgl_server_wait(self._h, ticket, timeout_ms, ctypes.byref(info))
+        if check:
+            _check(st)
+        return {"status": st, "queue_ms": info.queue_ms, "latency_ms": info.latency_ms,
+                "rays": info.rays}
+
+    def cancel(self, ticket: int):
+        _check(lib().fgl_server_cancel(self._h, ticket))
+
+    def inject_alloc_failures(self, n: int):
+        _check(lib().fgl_server_inject_alloc_failures(self._h, n))
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(lib().fgl_server_get_stats(self._h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in ServerStats._fields_}
+
+    def reset_stats(self):
+        _check(lib().fgl_server_reset_stats(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fgl_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -688,6 +688,101 @@ fgl_status fgl_cast_batched_host(const fgl_cast_item* items, int32_t n_items,
   return fgl_sync(stream);
 }
 
+fgl_status fgl_autotune(const fgl_cast_item* items, int32_t n_items, const fgl_tune_opts* topts,
+                        fgl_batch_opts* best, fgl_tune_result* result, fgl_stream stream) {
+  if (!best) return fail(FGL_ERR_INVALID, "best is null");
+  if (n_items < 1 || !items) return fail(FGL_ERR_INVALID, "autotune needs at least one item");
+  for (int i = 0; i < n_items; ++i) {
+    fgl_status st = check_item(items[i], i);
+    if (st != FGL_OK) return st;
+  }
+  const int reps = (topts && topts->reps > 0) ? topts->reps : 3;
+  const int passes = (topts && topts->passes > 0) ? topts->passes : 2;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  FGL_CUDA(cudaEventCreate(&e0));
+  FGL_CUDA(cudaEventCreate(&e1));
+  int trials = 0;
+  auto time_opts = [&](const fgl_batch_opts& bo, double* ms) -> fgl_status {
+    Opts o;
+    fgl_status st = resolve_opts(&bo, &o);
+    if (st != FGL_OK) return st;
+    st = run_batched(items, n_items, o, s);  // warm-up (and graph capture)
+    if (st != FGL_OK) return st;
+    std::vector<float> t(reps);
+    for (int r = 0; r < reps; ++r) {
+      FGL_CUDA(cudaEventRecord(e0, s));
+      st = run_batched(items, n_items, o, s);
+      if (st != FGL_OK) return st;
+      FGL_CUDA(cudaEventRecord(e1, s));
+      FGL_CUDA(cudaEventSynchronize(e1));
+      FGL_CUDA(cudaEventElapsedTime(&t[r], e0, e1));
+    }
+    std::sort(t.begin(), t.end());
+    *ms = t[reps / 2];
+    ++trials;
+    return FGL_OK;
+  };
+  struct Dim {
+    int32_t fgl_batch_opts::*field;
+    std::vector<int32_t> values;
+  };
+  const Dim dims[] = {
+      {&fgl_batch_opts::tri_mode, {0, 1}},
+      {&fgl_batch_opts::refill_min, {8, 16, 32}},
+      {&fgl_batch_opts::packet_rays, {32, 64, 128, 256}},
+      {&fgl_batch_opts::block_threads, {64, 128, 256}},
+      {&fgl_batch_opts::stack_smem, {4, 8, 12, 16}},
+  };
+  fgl_batch_opts cur = *best;
+  // start from the defaults explicitly so that every dimension has a value
+  if (!cur.packet_rays) cur.packet_rays = 64;
+  if (!cur.block_threads) cur.block_threads = 128;
+  if (!cur.stack_smem) cur.stack_smem = 12;
+  if (!cur.refill_min) cur.refill_min = 32;
+  double cur_ms = 0.0;
+  fgl_status st = time_opts(cur, &cur_ms);
+  if (st != FGL_OK) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+  }
+  const double start_ms = cur_ms;
+  for (int pass = 0; pass < passes; ++pass) {
+    bool changed = false;
+    for (const Dim& dm : dims) {
+      for (int32_t v : dm.values) {
+        if (cur.*dm.field == v) continue;
+        fgl_batch_opts cand = cur;
+        cand.*dm.field = v;
+        double ms = 0.0;
+        st = time_opts(cand, &ms);
+        if (st == FGL_ERR_INVALID) continue;  // e.g. shared memory too large
+        if (st != FGL_OK) {
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          return st;
+        }
+        if (ms < cur_ms * 0.99) {
+          cur = cand;
+          cur_ms = ms;
+          changed = true;
+        }
+      }
+    }
+    if (!changed) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *best = cur;
+  if (result) {
+    result->best_ms = cur_ms;
+    result->start_ms = start_ms;
+    result->trials = trials;
+  }
+  return FGL_OK;
+}
+
 fgl_status fgl_sync(fgl_stream stream) {
   FGL_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
   FGL_CUDA(cudaGetLastError());

@@ -241,3 +241,35 @@ def test_argument_errors(tiny):
     sc.upload()
     fgl.cast(sc, se, poses, 10.0)
     fgl.sync()
+
+
+# ---------------------------------------------------------------------------
+# the bench workload at full size, in the bench's launch configuration
+# ---------------------------------------------------------------------------
+def test_batched_walk_full_size_sampled(indoor_oracle):
+    w = workloads.batched_walk(2, n_env=4096, n_steps=2)
+    scene = fgl.Scene(w.verts, w.tris, width=8)
+    sensor = fgl.Sensor.from_table(w.sensor)
+    P = w.poses[1]
+    n = P.shape[0] * sensor.n_rays
+    poses = torch.from_numpy(P).cuda()
+    r = torch.full((n,), -3.0, dtype=torch.float32, device="cuda")
+    i = torch.full((n,), -3, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.Stream()
+    opts = fgl.BatchOpts(use_graph=1)
+    for _ in range(2):
+        fgl.cast_batched([(scene, sensor, poses, w.max_range, r, i)], opts, stream=stream)
+    fgl.sync(stream)
+    gr, gi = r.cpu().numpy(), i.cpu().numpy()
+    # every output written, every range within [0, max_range], misses well formed
+    assert np.all(gi >= -1) and np.all(gr > 0) and np.all(gr <= np.float32(w.max_range))
+    assert np.all(gr[gi < 0] == np.float32(w.max_range))
+    # sample: 24 whole environments + 20,000 random rays of the others
+    rng = np.random.default_rng(77)
+    envs = rng.choice(P.shape[0], 24, replace=False)
+    idx = np.concatenate([(e * sensor.n_rays + np.arange(sensor.n_rays)) for e in envs] +
+                         [rng.choice(n, 20000, replace=False)])
+    idx = np.unique(idx)
+    o, d = oracle.world_rays(oracle.sensor_dirs(w.sensor.elev, w.sensor.azim), P)
+    rep = parity_report(indoor_oracle, o[idx], d[idx], w.max_range, gr[idx], gi[idx])
+    assert_parity(rep)

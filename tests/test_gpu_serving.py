@@ -1,0 +1,169 @@
+"""GPU tests of the batching runtime: autotuner and serving loop.
+
+The serving contract: every request's result is the same as casting it
+alone (bitwise here; the task's contract only asks for the tolerance), under
+continuous batching with other requests of different sizes, with eviction
+under a small HBM budget, and with host-side faults (injected allocation
+failures, cancellations, malformed requests) affecting only their own
+requests.
+"""
+
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from synth import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+fgl = pytest.importorskip("paper_2509_17390_gb300")
+from paper_2509_17390_gb300 import tuning  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def world():
+    tiny = workloads.tiny_cast(1)
+    indoor = workloads.indoor_scan(2)
+    scenes = [fgl.Scene(tiny.verts, tiny.tris), fgl.Scene(indoor.verts, indoor.tris, width=8),
+              fgl.Scene(indoor.verts, indoor.tris, width=4)]
+    tables = [synth.grid_sensor(16, -15, 15, 360), synth.grid_sensor(7, -3, 20, 33),
+              synth.rosette_sensor(1000, 4)]
+    sensors = [fgl.Sensor.from_table(t) for t in tables]
+    obs = [tiny.obstacles, indoor.obstacles, indoor.obstacles]
+    return scenes, sensors, obs
+
+
+def alone(scene, sensor, P, R):
+    scene.upload()          # a server may have evicted it (no-op when resident)
+    poses = torch.from_numpy(np.ascontiguousarray(P, np.float32)).cuda()
+    r, i = fgl.cast(scene, sensor, poses, R)
+    fgl.sync()
+    return r.cpu().numpy(), i.cpu().numpy()
+
+
+def make_requests(world, n, seed, max_env=40):
+    scenes, sensors, obs = world
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for k in range(n):
+        si = int(rng.integers(len(scenes)))
+        ti = int(rng.integers(len(sensors)))
+        n_env = int(np.exp(rng.uniform(0, np.log(max_env))))
+        P = synth.sample_free_pose(rng, obs[si], n_env, upright=bool(k % 2))
+        R = float(rng.choice([5.0, 50.0, 120.0]))
+        reqs.append((si, ti, P, R))
+    return reqs
+
+
+def serve_and_check(world, srv, reqs):
+    scenes, sensors, _ = world
+    sid = [srv.add_scene(s) for s in scenes]
+    tid = [srv.add_sensor(s) for s in sensors]
+    outs, tickets = [], []
+    for si, ti, P, R in reqs:
+        n = P.shape[0] * sensors[ti].n_rays
+        r = torch.empty(n, dtype=torch.float32).pin_memory()
+        i = torch.empty(n, dtype=torch.int32).pin_memory()
+        tickets.append(srv.submit(sid[si], tid[ti], P, R, r, i))
+        outs.append((r, i))
+    infos = [srv.wait(t, timeout_ms=120000) for t in tickets]
+    for (si, ti, P, R), (r, i) in zip(reqs, outs):
+        ar, ai = alone(scenes[si], sensors[ti], P, R)
+        assert np.array_equal(ar, r.numpy()) and np.array_equal(ai, i.numpy())
+    return infos
+
+
+def test_serving_results_equal_alone(world):
+    srv = fgl.Server(tick_rays=200_000)            # small ticks: requests span several ticks
+    reqs = make_requests(world, 24, seed=1)
+    infos = serve_and_check(world, srv, reqs)
+    st = srv.stats()
+    assert st["completed"] == len(reqs) and st["ticks"] > 1
+    assert st["p99_ms"] >= st["p50_ms"] > 0 and st["rays_per_s"] > 0
+    assert all(x["latency_ms"] >= x["queue_ms"] >= 0 for x in infos)
+    srv.close()
+
+
+def test_serving_per_env_mode_equal_alone(world):
+    srv = fgl.Server(mode=1)
+    serve_and_check(world, srv, make_requests(world, 6, seed=2, max_env=8))
+    srv.close()
+
+
+def test_serving_evicts_under_small_budget(world):
+    scenes, _, _ = world
+    st0 = scenes[1].stats()
+    big = st0["node_bytes"] + st0["tri_bytes"]
+    # room for one large scene plus requests, not two: forces evictions
+    srv = fgl.Server(hbm_budget_bytes=int(big * 1.6), tick_rays=300_000)
+    reqs = [r for r in make_requests(world, 16, seed=3, max_env=12)]
+    serve_and_check(world, srv, reqs)
+    st = srv.stats()
+    assert st["evictions"] > 0 and st["uploads"] > 0
+    srv.close()
+    for s in scenes:       # leave every scene resident for the other tests
+        s.upload()
+
+
+def test_serving_budget_rejection_and_faults(world):
+    scenes, sensors, obs = world
+    srv = fgl.Server(hbm_budget_bytes=200 << 20)
+    sid = srv.add_scene(scenes[0])
+    tid = srv.add_sensor(sensors[0])
+    P = synth.sample_free_pose(np.random.default_rng(5), obs[0], 8)
+    huge = np.repeat(P, 8000, axis=0)        # 64k envs x 5760 rays x 8 B = 2.9 GB
+    r = np.empty(huge.shape[0] * sensors[0].n_rays, np.float32)
+    i = np.empty_like(r, dtype=np.int32)
+    with pytest.raises(fgl.FglError) as e:
+        srv.submit(sid, tid, huge, 10.0, r, i)
+    assert e.value.status == fgl.FGL_ERR_BUDGET
+    # malformed requests are rejected at submission
+    ro = np.empty(8 * sensors[0].n_rays, np.float32)
+    io = np.empty_like(ro, dtype=np.int32)
+    bad = P.copy()
+    bad[0, 0, 0] = np.nan
+    for args in ((sid, tid, bad, 10.0), (sid + 7, tid, P, 10.0), (sid, tid, P, float("nan"))):
+        with pytest.raises(fgl.FglError) as e:
+            srv.submit(*args, ro, io)
+        assert e.value.status == fgl.FGL_ERR_INVALID
+    # output buffers must stay alive until the request completes
+    bufs = [(np.empty_like(ro), np.empty_like(io)) for _ in range(10)]
+    # injected allocation failures hit exactly the next two admissions
+    srv.inject_alloc_failures(2)
+    tk = [srv.submit(sid, tid, P, 10.0, *bufs[k]) for k in range(4)]
+    st = [srv.wait(t, 60000, check=False)["status"] for t in tk]
+    assert st == [fgl.FGL_ERR_OOM, fgl.FGL_ERR_OOM, fgl.FGL_OK, fgl.FGL_OK]
+    # cancelling a request: it ends cancelled (or already done), others unaffected
+    tk = [srv.submit(sid, tid, P, 10.0, *bufs[4 + k]) for k in range(6)]
+    srv.cancel(tk[3])
+    st = [srv.wait(t, 60000, check=False)["status"] for t in tk]
+    assert st[3] in (fgl.FGL_ERR_CANCELLED, fgl.FGL_OK)
+    assert all(s == fgl.FGL_OK for k, s in enumerate(st) if k != 3)
+    srv.close()
+
+
+def test_autotune_keeps_results_and_caches(world, tmp_path):
+    scenes, sensors, obs = world
+    P = synth.sample_free_pose(np.random.default_rng(8), obs[1], 64, upright=False)
+    poses = torch.from_numpy(P).cuda()
+    n = 64 * sensors[0].n_rays
+    r = torch.empty(n, device="cuda")
+    i = torch.empty(n, dtype=torch.int32, device="cuda")
+    items = [(scenes[1], sensors[0], poses, 120.0, r, i)]
+    best, res = fgl.autotune(items, reps=2, passes=1)
+    assert res["trials"] >= 5 and res["best_ms"] <= res["start_ms"] * 1.05
+    fgl.cast_batched(items, best)
+    fgl.sync()
+    ar, ai = alone(scenes[1], sensors[0], P, 120.0)
+    assert np.array_equal(ar, r.cpu().numpy()) and np.array_equal(ai, i.cpu().numpy())
+    tab = synth.grid_sensor(16, -15, 15, 360)
+    indoor = workloads.indoor_scan(2)
+    path = str(tmp_path / "tune.json")
+    t1 = tuning.tune_workload(indoor.verts, indoor.tris, tab, poses, 120.0, widths=(8, 4),
+                              tiles=((4, 8), (1, 32)), cache_path=path, reps=2, passes=1,
+                              scenes={8: scenes[1], 4: scenes[2]})
+    assert t1["width"] in (8, 4) and not t1["cached"] and os.path.exists(path)
+    t2 = tuning.tune_workload(indoor.verts, indoor.tris, tab, poses, 120.0, cache_path=path)
+    assert t2["cached"] and t2["width"] == t1["width"] and t2["opts"] == t1["opts"]
