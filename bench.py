@@ -181,6 +181,82 @@ def time_oracle(osc, o, d, max_range):
 
 
 # ---------------------------------------------------------------------------
+# serving: trace replay
+# ---------------------------------------------------------------------------
+class OutputArena:
+    """Page-locked result space reused in arrival order: a request takes the
+    next slice; when the arena wraps onto slices still in use, the replayer
+    first waits for those requests (back-pressure, counted in latency)."""
+
+    def __init__(self, nbytes: int):
+        import torch
+        self.buf = torch.empty(nbytes // 4, dtype=torch.int32).pin_memory()
+        self.n = self.buf.numel()
+        self.head = 0
+
+    def take(self, n_vals: int):
+        if n_vals * 2 > self.n:
+            raise ValueError("request larger than the output arena")
+        if self.head + 2 * n_vals > self.n:
+            self.head = 0
+        a = self.head
+        self.head += 2 * n_vals
+        r = self.buf[a:a + n_vals].view(dtype=__import__("torch").float32)
+        i = self.buf[a + n_vals:a + 2 * n_vals]
+        return (a, a + 2 * n_vals), r, i
+
+
+def make_trace(rng, rate: float, window_s: float, max_env: int, pose_pool, n_scenes: int,
+               sensor_pick, n_req_cap: int = 10 ** 9):
+    """Poisson arrivals (rate per second) over a window; n_env log-uniform on
+    [1, max_env]; poses drawn from pose_pool[scene] ([m, 3, 4])."""
+    t, out = 0.0, []
+    while len(out) < n_req_cap:
+        t += rng.exponential(1.0 / rate)
+        if t > window_s:
+            break
+        sc = int(rng.integers(n_scenes))
+        n_env = int(np.exp(rng.uniform(0.0, np.log(max_env))))
+        pool = pose_pool[sc]
+        P = pool[rng.integers(len(pool), size=n_env)]
+        out.append((t, sc, sensor_pick(rng, sc), np.ascontiguousarray(P, np.float32)))
+    return out
+
+
+def replay(server, trace, scene_ids, sensor_ids, n_rays_of, arena, max_range, timeout_s=600):
+    """Submit each request at its arrival time; latency = arrival -> results
+    in host memory.  Returns stats."""
+    live = []     # (ticket, submission delay behind the arrival time in ms, slice)
+    lat, rays = [], 0
+    t0 = time.perf_counter()
+
+    def retire(k):
+        tk, delay_ms, _ = live.pop(k)
+        info = server.wait(tk, int(timeout_s * 1000))
+        lat.append(info["latency_ms"] + delay_ms)    # arrival -> results in host memory
+
+    for (ta, sc, se, P) in trace:
+        n = P.shape[0] * n_rays_of[se]
+        now = time.perf_counter() - t0
+        if now < ta:
+            time.sleep(ta - now)
+        sl, r, i = arena.take(n)
+        while live and any(not (sl[1] <= a or b <= sl[0]) for _, _, (a, b) in live):
+            retire(0)
+        delay_ms = max(0.0, (time.perf_counter() - t0 - ta) * 1e3)
+        tk = server.submit(scene_ids[sc], sensor_ids[se], P, max_range, r, i)
+        live.append((tk, delay_ms, sl))
+        rays += n
+    while live:
+        retire(0)
+    busy = time.perf_counter() - t0
+    lat = np.asarray(lat)
+    return {"requests": len(trace), "rays": rays, "wall_s": round(busy, 3),
+            "rays_per_s": rays / busy, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean())}
+
+
+# ---------------------------------------------------------------------------
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -199,6 +275,8 @@ def main():
     ap.add_argument("--width", type=int, default=8)
     ap.add_argument("--tri", type=int, default=0)
     ap.add_argument("--tile", type=str, default="")
+    ap.add_argument("--workload", default="walk", choices=["walk", "hetero", "serve"])
+    ap.add_argument("--no-serve", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -208,6 +286,10 @@ def main():
     n_steps = args.warmup + args.steps
     if args.impl == "reference":
         return run_reference(args, n_steps)
+    if args.workload == "hetero":
+        return run_hetero(args)
+    if args.workload == "serve":
+        return run_serve(args)
 
     import torch
     import paper_2509_17390_gb300 as fgl
@@ -341,6 +423,11 @@ def main():
                "h2d_bytes_per_step": n_env * 48, "d2h_bytes_per_step": n_rays * 8,
                "ms_per_step": round(tot * 1e3 / ksteps, 3)}
 
+    # served: continuous batching vs one launch per env on Poisson traces
+    served = None
+    if not args.no_serve:
+        served = served_walk(fgl, scene, sensor, walk, w.max_range, value, rank)
+
     # CPU oracle on a bounded sample (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -362,12 +449,232 @@ def main():
                        "opts": opts.as_dict(), "scene_tris": st["n_tris"],
                        "rays_per_step": n_rays, "frames_per_s": round(ws * n_env / (ms / 1e3), 1)},
             "gpu_launches": args.steps, "roofline": roofline, "e2e": e2e,
-            "per_env_launch": per_env, "served": None, "cpu_baseline": cpu, "clocks": clocks,
+            "per_env_launch": per_env, "served": served, "cpu_baseline": cpu, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def served_walk(fgl, scene, sensor, walk, max_range, grays, rank):
+    """Poisson requests of 1-4096 walk poses (log-uniform) at 70% of the
+    measured batched capacity for 2 s through the continuous-batching server;
+    the first requests of the same trace also through the server that issues
+    one launch per environment, and again through the batched server."""
+    rng = np.random.default_rng(11 + rank)
+    pool = {0: walk.reshape(-1, 3, 4)}
+    mean_env = (4096 - 1) / np.log(4096)
+    rate = 0.7 * grays * 1e9 / (mean_env * sensor.n_rays)
+    trace = make_trace(rng, rate, 2.0, 4096, pool, 1, lambda r, sc: 0)
+    arena = OutputArena(2 << 30)
+    out = {"load": "Poisson, 70% of the measured batched capacity, 2 s window; n_env log-uniform 1-4096",
+           "rate_req_per_s": round(rate, 1)}
+    srv = fgl.Server(tick_rays=16 << 20)
+    sid, tid = srv.add_scene(scene), srv.add_sensor(sensor)
+    res = replay(srv, trace, [sid], [tid], [sensor.n_rays], arena, max_range)
+    out.update({"requests": res["requests"], "p50_ms": round(res["p50_ms"], 2),
+                "p99_ms": round(res["p99_ms"], 2), "value": round(res["rays_per_s"] / 1e9, 4),
+                "unit": "Grays/s"})
+    # the same trace prefix through both servers (the plain server falls behind)
+    pre, acc = [], 0
+    for tr in trace:
+        acc += tr[3].shape[0] * sensor.n_rays
+        pre.append(tr)
+        if acc > 2.5e8:
+            break
+    resb = replay(srv, pre, [sid], [tid], [sensor.n_rays], arena, max_range)
+    srv.close()
+    srvp = fgl.Server(mode=1)
+    sid, tid = srvp.add_scene(scene), srvp.add_sensor(sensor)
+    resp = replay(srvp, pre, [sid], [tid], [sensor.n_rays], arena, max_range)
+    srvp.close()
+    f = lambda r: {"p50_ms": round(r["p50_ms"], 2), "p99_ms": round(r["p99_ms"], 2),
+                   "Grays_s": round(r["rays_per_s"] / 1e9, 4)}
+    out["same_prefix"] = {"requests": len(pre), "batched": f(resb), "per_env_launch": f(resp)}
+    return out
+
+
+def hetero_setup(fgl, seed=4, n_env=256, ladder=None):
+    """Meshes, scenes (width picked per mesh by timing), sensors and the
+    batched items of the heterogeneous workload."""
+    import torch
+    from synth import workloads
+    t0 = time.perf_counter()
+    meshes = workloads.hetero_meshes(seed, ladder)
+    t_mesh = time.perf_counter() - t0
+    tables = workloads.hetero_sensors(seed)
+    envs = workloads.hetero_envs(seed, meshes, n_env)
+    groups = {}
+    for m, sidx, P in envs:
+        groups.setdefault((m, sidx), []).append(P)
+    keys = sorted(groups)
+    sensors = {k: fgl.Sensor.from_table(tables[k]) for k in sorted({s for _, s in keys})}
+    t0 = time.perf_counter()
+    scenes = {m: {W: fgl.Scene(spec.verts, spec.tris, width=W) for W in (8, 4)}
+              for m, spec in enumerate(meshes)}
+    t_build = time.perf_counter() - t0
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.Stream(device=dev)
+    poses = {k: torch.from_numpy(np.stack(groups[k])).to(dev) for k in keys}
+    outs = {k: (torch.empty(poses[k].shape[0] * sensors[k[1]].n_rays, dtype=torch.float32, device=dev),
+                torch.empty(poses[k].shape[0] * sensors[k[1]].n_rays, dtype=torch.int32, device=dev))
+            for k in keys}
+
+    def items_for(widths, only_mesh=None):
+        return [(scenes[k[0]][widths[k[0]]], sensors[k[1]], poses[k], 30.0, outs[k][0], outs[k][1])
+                for k in keys if only_mesh is None or k[0] == only_mesh]
+
+    widths = {}
+    for m in range(len(meshes)):            # BVH width per mesh, by timing its own items
+        best = None
+        for W in (8, 4):
+            its = items_for({mm: W for mm in range(len(meshes))}, only_mesh=m)
+            if not its:
+                continue
+            _, res = fgl.autotune(its, fgl.BatchOpts(use_graph=1), reps=2, passes=1, stream=stream)
+            if best is None or res["best_ms"] < best[1]:
+                best = (W, res["best_ms"])
+        widths[m] = best[0] if best else 8
+    items = items_for(widths)
+    opts, tune = fgl.autotune(items, fgl.BatchOpts(use_graph=1), reps=3, passes=2, stream=stream)
+    info = {"meshes": [{"tris": int(len(sp.tris)), "gaussians": sp.n_gauss, "voxel_m": sp.voxel,
+                        "width": widths[m]} for m, sp in enumerate(meshes)],
+            "mesher_s": round(t_mesh, 1), "bvh_build_s": round(t_build, 1),
+            "autotune": {"opts": opts.as_dict(), "best_ms": round(tune["best_ms"], 3),
+                         "start_ms": round(tune["start_ms"], 3), "trials": tune["trials"]}}
+    return meshes, tables, envs, groups, scenes, sensors, widths, items, opts, stream, info
+
+
+def run_hetero(args):
+    import torch
+    import paper_2509_17390_gb300 as fgl
+    ws, rank, local = dist_setup(args.gpus)
+    meshes, tables, envs, groups, scenes, sensors, widths, items, opts, stream, info = hetero_setup(fgl)
+    n_rays = sum(it[2].shape[0] * it[1].n_rays for it in items)
+    arr = fgl.make_items(items)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        fgl.cast_batched(items, opts, stream=stream, arr=arr)
+    fgl.sync(stream)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(k & 0xFF)
+                ev[k][0].record(stream)
+            fgl.cast_batched(items, opts, stream=stream, arr=arr)
+            with torch.cuda.stream(stream):
+                ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    fgl.sync(stream)
+    tot = barrier_max(sum(a.elapsed_time(b) for a, b in ev) / 1e3, ws)
+    value = ws * n_rays * args.steps / tot / 1e9
+    # the plain form: one fgl_cast launch per environment
+    L = fgl.lib()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for sc, se, P, R, r, i in items:
+        for e in range(P.shape[0]):
+            st = L.fgl_cast(sc.handle, se.handle, P.data_ptr() + 48 * e, 1, R,
+                            r.data_ptr() + 4 * se.n_rays * e, i.data_ptr() + 4 * se.n_rays * e,
+                            stream.cuda_stream)
+            assert st == 0, L.fgl_last_error()
+    e1.record(stream)
+    e1.synchronize()
+    per_env = {"value": round(n_rays / (e0.elapsed_time(e1) / 1e3) / 1e9, 4), "unit": UNIT,
+               "launches_per_step": len(envs)}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        import oracle
+        rng = np.random.default_rng(5)
+        tot_r, tot_t = 0, 0.0
+        for (m, sidx) in sorted(groups)[:24]:
+            tab = tables[sidx]
+            o, d = oracle.world_rays(oracle.sensor_dirs(tab.elev, tab.azim), np.stack(groups[(m, sidx)][:1]))
+            idx = rng.choice(len(o), min(len(o), 4000), replace=False)
+            osc = oracle.Scene(meshes[m].verts, meshes[m].tris, bvh=True)
+            t_ = time.perf_counter()
+            osc.cast(o[idx], d[idx], 30.0, flags=False)
+            tot_t += time.perf_counter() - t_
+            tot_r += len(idx)
+        cpu = {"value": round(tot_r / tot_t / 1e9, 6), "unit": UNIT, "cores": os.cpu_count(),
+               "kind": "oracle", "sample": f"{tot_r} rays from 24 (mesh, sensor) groups, FP64 BVH"}
+    if rank == 0:
+        line = {"metric": "Grays/s, heterogeneous batch (8 meshes 90k-5.2M tris, 256 envs, mixed sensors)",
+                "value": round(value, 4), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": round(tot * 1e3 / args.steps, 3),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": "hetero_batch: 8 meshes from the host TSDF + marching-tetrahedra "
+                                       "mesher over 50k-2M seeded Gaussians (voxels 5->2 cm), 256 envs "
+                                       "round-robin, sensors 16/32/64/128 beams x 360-2048 az or a 20k "
+                                       "rosette, max range 30 m", "rays_per_step": n_rays,
+                           "l2": "flushed between timed steps (256 MiB write)", **info},
+                "gpu_launches": args.steps * len(set(widths.values())), "per_env_launch": per_env,
+                "cpu_baseline": cpu, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+
+
+def run_serve(args):
+    """Serving workload: Poisson requests (mean 2,000/s over a 0.25 s window,
+    then 70% of the capacity measured there over 3 s) of 1-4096 env poses
+    (log-uniform) over the 8 resident heterogeneous scenes with mixed
+    sensors, 150 GiB budget; the first requests also through the server that
+    issues one launch per environment."""
+    import paper_2509_17390_gb300 as fgl
+    from synth import poses as _poses
+    ws, rank, local = dist_setup(args.gpus)
+    meshes, tables, envs, groups, scenes, _, widths, items, opts, stream, info = hetero_setup(fgl)
+    rng = np.random.default_rng(21)
+    all_sensors = [fgl.Sensor.from_table(t) for t in tables]
+    pool = {m: _poses.sample_free_pose(rng, spec.obstacles, 2048, margin=0.25)
+            for m, spec in enumerate(meshes)}
+    n_rays_of = [s.n_rays for s in all_sensors]
+    pick = lambda r, sc: int(r.integers(len(all_sensors)))
+    arena = OutputArena(24 << 30)
+    opts.use_graph = 0
+    srv = fgl.Server(hbm_budget_bytes=150 << 30, tick_rays=32 << 20, opts=opts)
+    sids = [srv.add_scene(scenes[m][widths[m]]) for m in range(len(meshes))]
+    tids = [srv.add_sensor(s) for s in all_sensors]
+    sat_trace = make_trace(rng, 2000.0, 0.25, 4096, pool, len(meshes), pick)
+    sat = replay(srv, sat_trace, sids, tids, n_rays_of, arena, 30.0)
+    mean_rays = float(np.mean([t[3].shape[0] * n_rays_of[t[2]] for t in sat_trace]))
+    rate = 0.7 * sat["rays_per_s"] / mean_rays
+    srv.reset_stats()
+    cal_trace = make_trace(rng, rate, 3.0, 4096, pool, len(meshes), pick)
+    cal = replay(srv, cal_trace, sids, tids, n_rays_of, arena, 30.0)
+    st = srv.stats()
+    pre, acc = [], 0
+    for tr in cal_trace:
+        acc += tr[3].shape[0] * n_rays_of[tr[2]]
+        pre.append(tr)
+        if acc > 2.5e8:
+            break
+    preb = replay(srv, pre, sids, tids, n_rays_of, arena, 30.0)
+    srv.close()
+    srvp = fgl.Server(mode=1, hbm_budget_bytes=150 << 30)
+    sidp = [srvp.add_scene(scenes[m][widths[m]]) for m in range(len(meshes))]
+    tidp = [srvp.add_sensor(s) for s in all_sensors]
+    prep = replay(srvp, pre, sidp, tidp, n_rays_of, arena, 30.0)
+    srvp.close()
+    if rank == 0:
+        f = lambda r: {"requests": r["requests"], "Grays_s": round(r["rays_per_s"] / 1e9, 4),
+                       "p50_ms": round(r["p50_ms"], 2), "p99_ms": round(r["p99_ms"], 2)}
+        line = {"metric": "served Grays/s and p50/p99 scan latency (8 resident scenes, mixed sensors)",
+                "value": round(cal["rays_per_s"] / 1e9, 4), "unit": UNIT, "n_gpus": ws,
+                "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+                "p50_ms": round(cal["p50_ms"], 2), "p99_ms": round(cal["p99_ms"], 2),
+                "saturation_2000rps": f(sat), "at_70pct": {**f(cal), "rate_req_per_s": round(rate, 2)},
+                "same_prefix": {"batched": f(preb), "per_env_launch": f(prep)},
+                "server": {"evictions": st["evictions"], "uploads": st["uploads"], "ticks": st["ticks"]},
+                "config": {"workload": "serve: Poisson arrivals of 1-4096 env poses (log-uniform) over the "
+                                       "8 heterogeneous scenes, 21 sensors, 150 GiB budget, 32 Mi-ray ticks",
+                           **info}}
+        print(json.dumps(line), flush=True)
 
 
 def run_reference(args, n_steps):

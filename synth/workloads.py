@@ -9,6 +9,12 @@
                   seeded SE(3) random walk (0.1 m / 2 deg per step) over 100
                   steps, 16 x 360 rays per environment (23.6 M rays per step),
                   max range 120 m.
+  hetero_batch  : 8 meshes extracted by the host mesher (TSDF + marching
+                  tetrahedra) from 50k-2M seeded Gaussians on open-topped
+                  rooms of growing size, voxels 5 cm -> 2 cm (about 50k -> 5M
+                  triangles); 256 environments assigned round-robin to the
+                  meshes, each with a sensor drawn from 16/32/64/128 beams x
+                  360-2048 azimuths or the 20k-ray rosette.
 """
 
 from __future__ import annotations
@@ -64,3 +70,64 @@ def batched_walk(seed: int = 2, n_env: int = 4096, n_steps: int = 100) -> Worklo
     v, t, obs = indoor_mesh(seed)
     W = _poses.random_walk(np.random.default_rng(seed + 2000), obs, n_env, n_steps)
     return Workload("batched_walk", v, t, _sensors.grid_sensor(16, -15.0, 15.0, 360), W, 120.0, obs)
+
+
+# (room extent m, boxes, spheres, Gaussians, voxel m): about 17 * area / voxel^2
+# triangles each, from ~50k to ~5M
+HETERO_LADDER = [
+    ((2.0, 1.5, 1.0), 1, 1, 50_000, 0.05),
+    ((2.5, 2.0, 1.2), 2, 1, 85_000, 0.05),
+    ((3.0, 2.5, 1.5), 2, 2, 145_000, 0.04),
+    ((3.5, 3.0, 1.8), 3, 2, 250_000, 0.035),
+    ((4.5, 3.5, 2.0), 3, 3, 420_000, 0.03),
+    ((5.0, 4.0, 2.5), 4, 3, 720_000, 0.025),
+    ((6.0, 4.5, 2.6), 5, 4, 1_200_000, 0.022),
+    ((6.0, 5.0, 3.0), 6, 4, 2_000_000, 0.02),
+]
+
+
+@dataclasses.dataclass
+class MeshSpec:
+    verts: np.ndarray
+    tris: np.ndarray
+    obstacles: object
+    voxel: float
+    n_gauss: int
+    stats: dict
+
+
+_HETERO_CACHE: dict = {}
+
+
+def hetero_meshes(seed: int = 4, ladder=None) -> List[MeshSpec]:
+    """The heterogeneous workload's meshes (cached per process)."""
+    from . import gaussians
+    ladder = HETERO_LADDER if ladder is None else ladder
+    key = (seed, tuple(map(tuple, [(r, b, s, n, h) for r, b, s, n, h in ladder])))
+    if key not in _HETERO_CACHE:
+        out = []
+        for k, (room, nb, ns, ng, h) in enumerate(ladder):
+            gs, obs = gaussians.gaussian_room(seed * 100 + k, room, ng, nb, ns, with_obstacles=True)
+            v, t, st = gaussians.mesh_from_gaussians(gs, h)
+            out.append(MeshSpec(v, t, obs, h, ng, st))
+        _HETERO_CACHE[key] = out
+    return _HETERO_CACHE[key]
+
+
+def hetero_sensors(seed: int = 4):
+    return _sensors.mixed_sensors(seed)
+
+
+def hetero_envs(seed: int, meshes: List[MeshSpec], n_env: int = 256):
+    """Environments assigned round-robin to the meshes, each with a sensor
+    index into hetero_sensors() and a free upright pose (random yaw) in its
+    room.  Returns a list of (mesh index, sensor index, pose[3,4])."""
+    rng = np.random.default_rng(seed + 7)
+    n_sensors = len(_sensors.MIXED_BEAMS) * len(_sensors.MIXED_AZ) + 1
+    envs = []
+    for e in range(n_env):
+        m = e % len(meshes)
+        s = int(rng.integers(n_sensors))
+        P = _poses.sample_free_pose(rng, meshes[m].obstacles, 1, margin=0.25)
+        envs.append((m, s, P[0]))
+    return envs

@@ -273,3 +273,33 @@ def test_batched_walk_full_size_sampled(indoor_oracle):
     o, d = oracle.world_rays(oracle.sensor_dirs(w.sensor.elev, w.sensor.azim), P)
     rep = parity_report(indoor_oracle, o[idx], d[idx], w.max_range, gr[idx], gi[idx])
     assert_parity(rep)
+
+
+# ---------------------------------------------------------------------------
+# heterogeneous batch: meshes from the host mesher, mixed sensors, one launch
+# ---------------------------------------------------------------------------
+def test_hetero_batch_vs_oracle():
+    ladder = workloads.HETERO_LADDER[:4]
+    meshes = workloads.hetero_meshes(4, ladder)
+    tables = workloads.hetero_sensors(4)
+    envs = workloads.hetero_envs(4, meshes, n_env=48)
+    scenes = [fgl.Scene(m.verts, m.tris, width=8 if k % 2 == 0 else 4) for k, m in enumerate(meshes)]
+    groups = {}
+    for m, s, P in envs:
+        groups.setdefault((m, s), []).append(P)
+    sensors = {s: fgl.Sensor.from_table(tables[s]) for (_, s) in groups}
+    items, keys = [], []
+    for (m, s), Ps in sorted(groups.items()):
+        P = np.stack(Ps)
+        items.append((scenes[m], sensors[s], P, 30.0))
+        keys.append((m, s, P))
+    outs = run_batched(items, fgl.BatchOpts(packet_rays=128))
+    rng = np.random.default_rng(3)
+    for (m, s, P), (gr, gi) in zip(keys, outs):
+        tab = tables[s]
+        o, d = oracle.world_rays(oracle.sensor_dirs(tab.elev, tab.azim), P)
+        idx = rng.choice(len(o), min(len(o), 4000), replace=False)
+        osc = oracle.Scene(meshes[m].verts, meshes[m].tris, bvh=True)
+        rep = parity_report(osc, o[idx], d[idx], 30.0, gr[idx], gi[idx])
+        assert_parity(rep)
+        assert np.all(gi >= -1)
