@@ -145,13 +145,21 @@ def dist_setup(n_gpus: int):
 
 
 def barrier_max(x: float, ws: int) -> float:
+    """Maximum of x over the ranks (the slowest rank's time)."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate_rate(units_per_rank: float, seconds: float, ws: int) -> float:
+    """Whole-job throughput of identical replicas: every rank's units over
+    the slowest rank's time."""
+    return ws * units_per_rank / barrier_max(seconds, ws)
 
 
 def barrier(ws: int):
@@ -357,7 +365,7 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_s = barrier_max(sum(step_ms) / 1e3, ws)
     ms = total_s * 1e3 / args.steps
-    value = ws * n_rays * args.steps / total_s / 1e9
+    value = aggregate_rate(n_rays * args.steps, sum(step_ms) / 1e3, ws) / 1e9
     clocks = clk.summary()
 
     # kernel-only time for the roofline: graph = 1 tiny memcpy + 1 kernel
