@@ -81,7 +81,7 @@ fgl_status device_info(DeviceInfo* out) {
 // option defaults
 // ---------------------------------------------------------------------------
 struct Opts {
-  int packet = 64, block = 128, sdepth = 12, bpsm = 0, graph = 0, refill = 32, postpone = 20,
+  int packet = 64, block = 128, sdepth = 8, bpsm = 0, graph = 0, refill = 32, postpone = 20,
       count = 0, tri_mode = 0;
 };
 
@@ -111,7 +111,7 @@ fgl_status resolve_opts(const fgl_batch_opts* o, Opts* r) {
   fgl_status s = device_info(&di);
   if (s != FGL_OK) return s;
   if (stack_smem_bytes(d.block, d.sdepth) > di.smem_optin)
-    return fail(FGL_ERR_INVALID, "block_threads * stack_smem * 8 exceeds shared memory");
+    return fail(FGL_ERR_INVALID, "block_threads * (8 + 24 * stack_smem) bytes exceed shared memory");
   *r = d;
   return FGL_OK;
 }
@@ -381,7 +381,7 @@ fgl_status fgl_scene_build(const float* verts, int64_t nv, const int32_t* tris, 
   *out = nullptr;
   if (!verts || !tris) return fail(FGL_ERR_INVALID, "null vertex or triangle pointer");
   if (nv < 1 || nt < 1) return fail(FGL_ERR_INVALID, "mesh needs at least one vertex and triangle");
-  int width = 8, bins = 32, threads = 0, upload = 1;
+  int width = 4, bins = 32, threads = 0, upload = 1;
   if (opts) {
     if (opts->width) width = opts->width;
     if (opts->sah_bins) bins = opts->sah_bins;

@@ -184,9 +184,13 @@ struct BinaryBuilder {
 
 // Give each child the octant code (bit a: 1 = positive side along axis a,
 // relative to the parent's centre) that best matches its position, greedily
-// by decreasing alignment; codes within a node are distinct.
-void assign_codes(const std::vector<Box>& kids, const Box& parent, std::vector<int>& code) {
+// by decreasing alignment; codes within a node are distinct.  Width 8 uses
+// the three axes (8 codes), width 4 the horizontal axes x and y (4 codes), so
+// that the code is also the child's slot in the node record.
+void assign_codes(const std::vector<Box>& kids, const Box& parent, int width,
+                  std::vector<int>& code) {
   int n = (int)kids.size();
+  const int n_codes = width, axes = width == 8 ? 3 : 2;
   double pc[3];
   for (int a = 0; a < 3; ++a) pc[a] = 0.5 * ((double)parent.lo[a] + parent.hi[a]);
   struct Cand {
@@ -195,9 +199,9 @@ void assign_codes(const std::vector<Box>& kids, const Box& parent, std::vector<i
   };
   std::vector<Cand> cands;
   for (int k = 0; k < n; ++k) {
-    for (int c = 0; c < 8; ++c) {
+    for (int c = 0; c < n_codes; ++c) {
       double s = 0;
-      for (int a = 0; a < 3; ++a) {
+      for (int a = 0; a < axes; ++a) {
         double off = 0.5 * ((double)kids[k].lo[a] + kids[k].hi[a]) - pc[a];
         s += ((c >> a) & 1) ? off : -off;
       }
@@ -324,8 +328,8 @@ int build_bvh(const float* V, int64_t nv, const int32_t* T, int64_t nt, int widt
     std::vector<Box> kb(n);
     for (int i = 0; i < n; ++i) kb[i] = bn[kids[i]].box;
     std::vector<int> code;
-    assign_codes(kb, bn[b].box, code);
-    // positions in increasing code
+    assign_codes(kb, bn[b].box, W, code);
+    // children in increasing code; each child sits in the slot of its code
     std::vector<int> pos(n);
     for (int i = 0; i < n; ++i) pos[i] = i;
     std::sort(pos.begin(), pos.end(), [&](int x, int y) { return code[x] < code[y]; });
@@ -342,13 +346,13 @@ int build_bvh(const float* V, int64_t nv, const int32_t* T, int64_t nt, int widt
       bool inner = c.count > kMaxLeafTris;
       if (inner) {
         imask |= 1u << code[i];
-        meta[j] = (uint8_t)((1u << 5) | (24u + (uint32_t)code[i]));
+        meta[code[i]] = (uint8_t)((1u << 5) | (24u + (uint32_t)code[i]));
         wsrc.push_back(kids[i]);
         wdepth.push_back(wdepth[w] + 1);
         max_depth = std::max(max_depth, wdepth[w] + 1);
       } else {
         int cnt = c.count;
-        meta[j] = (uint8_t)((((1u << cnt) - 1u) << 5) | (uint32_t)tri_off);
+        meta[code[i]] = (uint8_t)((((1u << cnt) - 1u) << 5) | (uint32_t)tri_off);
         for (int t = 0; t < cnt; ++t) {
           int32_t k = idx[c.first + t];
           for (int v = 0; v < 3; ++v) {
@@ -410,8 +414,8 @@ int build_bvh(const float* V, int64_t nv, const int32_t* T, int64_t nt, int widt
           while (qh <= 255 && (double)decode((uint8_t)std::min(qh, 255.0), scale, pa) < ht) qh += 1.0;
           if (qh > 255) ok = false;
           if (!ok) break;
-          q[a][j] = (uint8_t)ql;
-          q[3 + a][j] = (uint8_t)qh;
+          q[a][code[i]] = (uint8_t)ql;
+          q[3 + a][code[i]] = (uint8_t)qh;
         }
         if (ok) break;
       }

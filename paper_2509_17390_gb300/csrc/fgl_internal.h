@@ -39,12 +39,14 @@ namespace fgl {
 // grown by `margin` plus one quantum 2^(e-127) on every side, and verifies the
 // decoded boxes with exactly that arithmetic.
 //
+// Every child sits in the slot equal to its octant code c (width 8: bits
+// x, y, z; width 4: bits x, y), so slots of a partly filled node may be empty.
 // Internal children of a node are stored contiguously from child_base in
-// increasing octant code; child index = child_base + popc(imask & ((1<<c)-1)).
-// A ray with direction-sign bits `oct` (bit a set when d_a < 0) visits
-// children in increasing (c ^ oct), which approximates near-to-far order
-// because the builder gives each child the code of the octant it sits in
-// relative to its siblings.
+// increasing code; child index = child_base + popc(imask & ((1<<c)-1)).
+// A ray with direction-sign bits `oct` (bit a set when d_a < 0; only x, y for
+// width 4) visits children in increasing (c ^ oct), which approximates
+// near-to-far order because the builder gives each child the code of the
+// octant it sits in relative to its siblings.
 // ---------------------------------------------------------------------------
 constexpr int kMaxLeafTris = 3;
 constexpr int kMaxNodeTris = 24;

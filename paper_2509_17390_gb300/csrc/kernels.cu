@@ -41,24 +41,28 @@ __device__ __forceinline__ int postpone_threshold(int pct) {
 }
 
 // Dynamic shared memory: one 64-bit hit key per thread (pooled leaf tests
-// merge into these), then the [sdepth][blockDim] stack array.
+// merge into these), then the [sdepth][blockDim] stack arrays of groups
+// (8 B) and of child entry distances (16 B).
 struct Smem {
   unsigned long long* keys;  // this warp's 32 keys
-  uint2* ss;                 // this thread's stack column
+  uint2* ss;                 // this thread's group column
+  uint4* sq;                 // this thread's entry-distance column
 };
-__device__ __forceinline__ Smem smem_layout() {
-  extern __shared__ unsigned long long smem_u64[];
+__device__ __forceinline__ Smem smem_layout(int sdepth) {
+  extern __shared__ __align__(16) unsigned long long smem_u64[];
   Smem m;
   m.keys = smem_u64 + (threadIdx.x & ~31u);
-  m.ss = reinterpret_cast<uint2*>(smem_u64 + blockDim.x) + threadIdx.x;
+  uint2* ss0 = reinterpret_cast<uint2*>(smem_u64 + blockDim.x);
+  m.ss = ss0 + threadIdx.x;
+  m.sq = reinterpret_cast<uint4*>(ss0 + (size_t)sdepth * blockDim.x) + threadIdx.x;
   return m;
 }
 
 template <int W, bool COUNT>
-__global__ void __launch_bounds__(512) k_plain(const ItemDesc it, int sdepth, int tri_mode,
+__global__ void __maxnreg__(72) k_plain(const ItemDesc it, int sdepth, int tri_mode,
                                                int postpone_pct) {
   const unsigned FULL = 0xFFFFFFFFu;
-  const Smem sm = smem_layout();
+  const Smem sm = smem_layout(sdepth);
   const int lane = threadIdx.x & 31;
   const int64_t total = (int64_t)it.n_env * it.n_rays;
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -79,24 +83,26 @@ __global__ void __launch_bounds__(512) k_plain(const ItemDesc it, int sdepth, in
     tr.start(it.nodes, it.tris, it.max_range);
   }
   uint2 ls[kStackLocal];
+  uint4 lq[kStackLocal];
+  const dev::StackRefs st{sm.ss, sm.sq, ls, lq, (int)blockDim.x, sdepth};
   if (tri_mode != 1) {
     while (__any_sync(FULL, !done)) {
       bool ok = true;
-      if (!done) ok = tr.descend(sm.ss, blockDim.x, sdepth, ls);
+      if (!done) ok = tr.descend(st);
       dev::tri_phase_warp(tr, sm.keys, lane);
       if (!done) {
         if (!ok) {
           atomicOr(&g_status, 1u);
           done = true;
         } else {
-          done = tr.finish(sm.ss, blockDim.x, sdepth, ls);
+          done = tr.finish(st);
         }
       }
     }
   } else if (!done) {
     for (;;) {
       const int pl = postpone_threshold(postpone_pct);
-      if (tr.step(sm.ss, blockDim.x, sdepth, ls, pl, &g_status)) break;
+      if (tr.step(st, pl, &g_status)) break;
     }
   }
   if (gid < total) {
@@ -111,16 +117,18 @@ __global__ void __launch_bounds__(512) k_plain(const ItemDesc it, int sdepth, in
 }
 
 template <int W, bool COUNT>
-__global__ void __launch_bounds__(512) k_persistent(BatchHeader* __restrict__ hdr,
+__global__ void __maxnreg__(72) k_persistent(BatchHeader* __restrict__ hdr,
                                                     const ItemDesc* __restrict__ items, int sdepth,
                                                     int refill_min, int tri_mode, int postpone_pct) {
   const unsigned FULL = 0xFFFFFFFFu;
-  const Smem sm = smem_layout();
+  const Smem sm = smem_layout(sdepth);
   const int lane = threadIdx.x & 31;
   const int64_t n_packets = hdr->n_packets;
   const int n_items = hdr->n_items;
   const int P = hdr->packet_rays;
   uint2 ls[kStackLocal];
+  uint4 lq[kStackLocal];
+  const dev::StackRefs st{sm.ss, sm.sq, ls, lq, (int)blockDim.x, sdepth};
 
   // warp-uniform packet cursor
   int pk_item = 0, pk_env = 0, pk_next = 0, pk_end = 0;
@@ -191,19 +199,19 @@ __global__ void __launch_bounds__(512) k_persistent(BatchHeader* __restrict__ hd
     bool fin = false;
     if (tri_mode != 1) {
       bool ok = true;
-      if (active) ok = tr.descend(sm.ss, blockDim.x, sdepth, ls);
+      if (active) ok = tr.descend(st);
       dev::tri_phase_warp(tr, sm.keys, lane);
       if (active) {
         if (!ok) {
           atomicOr(&g_status, 1u);
           fin = true;
         } else {
-          fin = tr.finish(sm.ss, blockDim.x, sdepth, ls);
+          fin = tr.finish(st);
         }
       }
     } else if (active) {
       const int pl = postpone_pct > 0 ? (__popc(act) * postpone_pct + 99) / 100 : 0;
-      fin = tr.step(sm.ss, blockDim.x, sdepth, ls, pl, &g_status);
+      fin = tr.step(st, pl, &g_status);
     }
     if (fin) {
       float rg;
@@ -259,7 +267,8 @@ void* pick_persistent(int W, bool count) {
 }  // namespace
 
 size_t stack_smem_bytes(int block, int sdepth) {
-  return (size_t)block * sizeof(unsigned long long) + (size_t)block * (size_t)sdepth * sizeof(uint2);
+  return (size_t)block * sizeof(unsigned long long) +
+         (size_t)block * (size_t)sdepth * (sizeof(uint2) + sizeof(uint4));
 }
 
 cudaError_t launch_plain(int W, bool count, const ItemDesc& it, int block, int sdepth,

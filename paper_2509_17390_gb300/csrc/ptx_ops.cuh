@@ -25,6 +25,21 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return r;
 }
 
+// Two non-negative floats as halves rounded toward zero (never above the
+// float), packed (lo in bits 0-15, hi in bits 16-31).
+__device__ __forceinline__ uint32_t pack_half2_rz(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+// A non-negative float as a half rounded toward +infinity (never below it),
+// in the low 16 bits.  Non-negative halves order like their bit patterns.
+__device__ __forceinline__ uint32_t half_rp(float x) {
+  unsigned short h;
+  asm("cvt.rp.f16.f32 %0, %1;" : "=h"(h) : "f"(x));
+  return (uint32_t)h;
+}
+
 // Packed pair of floats (lo, hi) in one 64-bit register pair.
 __device__ __forceinline__ uint64_t pack2f(float lo, float hi) {
   uint64_t r;

@@ -147,10 +147,12 @@ __device__ __forceinline__ float tri_hit(const Ray& r, float4 a, float4 b, float
 // most half a quantum, which the builder covers by growing every child box
 // one extra quantum.  The near and far planes of an axis go through one
 // packed f32x2 FMA.  Returns the node group (child_base, pending-child bits
-// << 24 | imask) and the triangle group (tri_base, leaf triangle bits).
+// << 24 | imask), the triangle group (tri_base, leaf triangle bits) and
+// every child's entry distance as a half rounded toward zero (tq, by slot).
 template <int W>
 __device__ __forceinline__ void intersect_node(const Ray& r, const uint4* __restrict__ nd,
-                                               float tmax, uint2& ng, uint2& tg) {
+                                               float tmax, uint32_t oct_w, uint2& ng, uint2& tg,
+                                               uint4& tq) {
   const uint4 h0 = ldg4(nd), h1 = ldg4(nd + 1);
   uint32_t lox[2], loy[2], loz[2], hix[2], hiy[2], hiz[2];
   if (W == 8) {
@@ -182,10 +184,11 @@ __device__ __forceinline__ void intersect_node(const Ray& r, const uint4* __rest
   for (int w = 0; w < (W + 3) / 4; ++w) {
     const uint32_t mw = w == 0 ? h1.z : h1.w;
     const uint32_t inner = (mw & (mw << 1)) & 0x10101010u;  // bytes 24..31
-    idx_w[w] = (mw & 0x1F1F1F1Fu) ^ ((inner >> 4) * r.oct);
+    idx_w[w] = (mw & 0x1F1F1F1Fu) ^ ((inner >> 4) * oct_w);
     cnt_w[w] = (mw >> 5) & 0x07070707u;
   }
   uint32_t hits = 0;
+  float tn_all[W];
 #pragma unroll
   for (int i = 0; i < W; ++i) {
     const int w = i >> 2;
@@ -199,30 +202,60 @@ __device__ __forceinline__ void intersect_node(const Ray& r, const uint4* __rest
     unpack2f(ffma2(pack2f(byte_magic(nzw, s), byte_magic(fzw, s)), S2z, B2z), tnz, tfz);
     const float tn = max3f(tnx, tny, fmaxf(tnz, 0.f));
     const float tf = min3f(tfx, tfy, fminf(tfz, tmax));
+    tn_all[i] = tn;
     const uint32_t pos = __byte_perm(idx_w[w], 0u, 0x4440u | s);
     const uint32_t cb = __byte_perm(cnt_w[w], 0u, 0x4440u | s);
     if (tn <= tf) hits |= cb << pos;
   }
   ng = make_uint2(h1.x, (hits & 0xFF000000u) | (e >> 24));
   tg = make_uint2(h1.y, hits & 0x00FFFFFFu);
+  // entry distance of every child slot (= its code) as halves, rounded down
+  tq.x = pack_half2_rz(tn_all[0], tn_all[1]);
+  tq.y = pack_half2_rz(tn_all[2], tn_all[3]);
+  if (W == 8) {
+    tq.z = pack_half2_rz(tn_all[4 % W], tn_all[5 % W]);
+    tq.w = pack_half2_rz(tn_all[6 % W], tn_all[7 % W]);
+  } else {
+    tq.z = tq.w = 0u;
+  }
 }
 
-// Per-thread traversal state and stack.  The stack's first `smem_depth`
-// entries live in shared memory (column `threadIdx.x` of a
-// [smem_depth][blockDim.x] array, so a warp's accesses are conflict-free);
-// deeper entries go to a local-memory array.
+// Entry distance (half bits) recorded for the child in slot c of a group.
+__device__ __forceinline__ uint32_t half_at(const uint4& q, uint32_t c) {
+  const uint32_t w = (c & 4u) ? ((c & 2u) ? q.w : q.z) : ((c & 2u) ? q.y : q.x);
+  return (c & 1u) ? (w >> 16) : (w & 0xFFFFu);
+}
+
+// Per-thread traversal state and stack.  A stack entry is a group (64 bits)
+// plus the entry distances of its children (128 bits, see intersect_node).
+// The stack's first `smem_depth` entries live in shared memory (columns
+// `threadIdx.x` of [smem_depth][blockDim.x] arrays, so a warp's accesses are
+// conflict-free); deeper entries go to local-memory arrays.
 //
 // One traversal step is: descend() -- visit the nearest pending child of the
 // current node group, leaving the visited node's hit leaf triangles in `tg`
 // -- then the leaf triangle tests, either lane by lane (tri_serial) or pooled
-// across the warp (tri_phase_warp), then finish() -- pop the next node group
-// when the current one is exhausted.
+// across the warp (tri_phase_warp), then finish() -- pop the next group when
+// the current one is exhausted.  A pending child whose recorded entry
+// distance already exceeds the best hit is dropped without fetching it: the
+// same cull the node test applies, with the newer best t.
+struct StackRefs {
+  uint2* ss;     // shared: group entries, stride `stride`
+  uint4* sq;     // shared: entry distances, stride `stride`
+  uint2* ls;     // local spill
+  uint4* lq;
+  int stride;
+  int sdepth;
+};
+
 template <int W, bool COUNT>
 struct Tracer {
   Ray r;
   float best_t;
   int32_t best_id;
   uint2 ng, tg;
+  uint4 tq;        // entry distances of the current node group's children
+  uint32_t ow;     // octant bits used for child order (x, y, z; x, y for width 4)
   int sp;
   const uint4* __restrict__ nodes;
   const float4* __restrict__ tris;
@@ -233,43 +266,61 @@ struct Tracer {
     tris = (const float4*)tri_ptr;
     best_t = max_range;
     best_id = kNoHit;
-    // root group: one internal child (the root node, code 0)
-    ng = make_uint2(0u, (1u << (24 + r.oct)) | 1u);
+    ow = W == 8 ? r.oct : (r.oct & 3u);
+    // root group: one internal child (the root node, code 0, entry 0)
+    ng = make_uint2(0u, (1u << (24 + ow)) | 1u);
     tg = make_uint2(0u, 0u);
+    tq = make_uint4(0u, 0u, 0u, 0u);
     sp = 0;
     if (COUNT) n_nodes = n_tris = 0;
   }
 
-  __device__ __forceinline__ bool push(uint2 v, uint2* ss, int stride, int sdepth, uint2* ls) {
-    if (sp < sdepth) {
-      ss[sp * stride] = v;
+  __device__ __forceinline__ bool push(uint2 v, uint4 q, const StackRefs& st) {
+    if (sp < st.sdepth) {
+      st.ss[sp * st.stride] = v;
+      st.sq[sp * st.stride] = q;
     } else {
-      int li = sp - sdepth;
+      int li = sp - st.sdepth;
       if (li >= kStackLocal) return false;
-      ls[li] = v;
+      st.ls[li] = v;
+      st.lq[li] = q;
     }
     ++sp;
     return true;
   }
-  __device__ __forceinline__ uint2 pop(uint2* ss, int stride, int sdepth, uint2* ls) {
+  __device__ __forceinline__ void pop(const StackRefs& st) {
     --sp;
-    return sp < sdepth ? ss[sp * stride] : ls[sp - sdepth];
+    if (sp < st.sdepth) {
+      ng = st.ss[sp * st.stride];
+      tq = st.sq[sp * st.stride];
+    } else {
+      ng = st.ls[sp - st.sdepth];
+      tq = st.lq[sp - st.sdepth];
+    }
   }
 
-  // Descend into the nearest pending child of the current node group (the
-  // remaining siblings go onto the stack), or take a popped triangle group.
-  // Returns false on stack overflow (the ray is then abandoned).
-  __device__ __forceinline__ bool descend(uint2* ss, int stride, int sdepth, uint2* ls) {
+  // Descend into the nearest pending child of the current node group whose
+  // recorded entry is not beyond the best hit (the remaining siblings go onto
+  // the stack), or take a popped triangle group.  Returns false on stack
+  // overflow (the ray is then abandoned).
+  __device__ __forceinline__ bool descend(const StackRefs& st) {
     if (ng.y & 0xFF000000u) {
-      const uint32_t pos = __ffs(ng.y >> 24) - 1;
-      const uint32_t code = pos ^ r.oct;
-      ng.y &= ~(1u << (24 + pos));
-      const uint32_t child = ng.x + __popc((ng.y & 0xFFu) & ((1u << code) - 1u));
-      if (ng.y & 0xFF000000u) {
-        if (!push(ng, ss, stride, sdepth, ls)) return false;
-      }
-      intersect_node<W>(r, nodes + (size_t)child * (node_stride(W) / 16), best_t, ng, tg);
-      if (COUNT) ++n_nodes;
+      const uint32_t hb = half_rp(best_t);
+      do {
+        const uint32_t pos = __ffs(ng.y >> 24) - 1;
+        const uint32_t code = pos ^ ow;
+        ng.y &= ~(1u << (24 + pos));
+        if (half_at(tq, code) > hb) continue;  // entirely beyond the best hit
+        const uint32_t child = ng.x + __popc((ng.y & 0xFFu) & ((1u << code) - 1u));
+        if (ng.y & 0xFF000000u) {
+          if (!push(ng, tq, st)) return false;
+        }
+        intersect_node<W>(r, nodes + (size_t)child * (node_stride(W) / 16), best_t, ow, ng, tg, tq);
+        if (COUNT) ++n_nodes;
+        return true;
+      } while (ng.y & 0xFF000000u);
+      ng = make_uint2(0u, 0u);  // every remaining child was beyond the best hit
+      tg = make_uint2(0u, 0u);
     } else {
       tg = ng;
       ng = make_uint2(0u, 0u);
@@ -287,12 +338,11 @@ struct Tracer {
   // Lane-serial leaf tests; when fewer than `postpone_lanes` lanes of the
   // warp are testing triangles and this lane still has nodes to visit, its
   // triangle group is pushed and tested later.  Returns false on overflow.
-  __device__ __forceinline__ bool tri_serial(uint2* ss, int stride, int sdepth, uint2* ls,
-                                             int postpone_lanes) {
+  __device__ __forceinline__ bool tri_serial(const StackRefs& st, int postpone_lanes) {
     while (tg.y) {
       if (postpone_lanes > 0 && (ng.y & 0xFF000000u)) {
         if (__popc(__activemask()) < postpone_lanes) {
-          if (!push(tg, ss, stride, sdepth, ls)) return false;
+          if (!push(tg, make_uint4(0u, 0u, 0u, 0u), st)) return false;
           tg.y = 0;
           break;
         }
@@ -309,23 +359,22 @@ struct Tracer {
 
   // After the leaf tests: pop the next group once the current node group has
   // no pending child.  Returns true when the ray is finished.
-  __device__ __forceinline__ bool finish(uint2* ss, int stride, int sdepth, uint2* ls) {
+  __device__ __forceinline__ bool finish(const StackRefs& st) {
     if (!(ng.y & 0xFF000000u)) {
       if (sp == 0) return true;
-      ng = pop(ss, stride, sdepth, ls);
+      pop(st);
     }
     return false;
   }
 
   // Lane-serial step (descend + tri_serial + finish).  Returns true when the
   // ray is finished.
-  __device__ __forceinline__ bool step(uint2* ss, int stride, int sdepth, uint2* ls,
-                                       int postpone_lanes, unsigned* status) {
-    if (!descend(ss, stride, sdepth, ls) || !tri_serial(ss, stride, sdepth, ls, postpone_lanes)) {
+  __device__ __forceinline__ bool step(const StackRefs& st, int postpone_lanes, unsigned* status) {
+    if (!descend(st) || !tri_serial(st, postpone_lanes)) {
       atomicOr(status, 1u);
       return true;
     }
-    return finish(ss, stride, sdepth, ls);
+    return finish(st);
   }
 
   __device__ __forceinline__ void result(float& range, int32_t& id) const {
