@@ -280,7 +280,7 @@ def main():
     ap.add_argument("--sdepth", type=int, default=0)
     ap.add_argument("--refill", type=int, default=0)
     ap.add_argument("--postpone", type=int, default=0)
-    ap.add_argument("--width", type=int, default=4)
+    ap.add_argument("--width", type=int, default=8)
     ap.add_argument("--tri", type=int, default=0)
     ap.add_argument("--tile", type=str, default="")
     ap.add_argument("--workload", default="walk", choices=["walk", "hetero", "serve"])

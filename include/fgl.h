@@ -66,7 +66,7 @@ typedef struct fgl_sensor_s* fgl_sensor;
 /* ------------------------------------------------------------------------ */
 
 typedef struct {
-  int32_t width;      /* children per BVH node: 4 or 8 (0 = 4) */
+  int32_t width;      /* children per BVH node: 4 or 8 (0 = 8) */
   int32_t sah_bins;   /* binned-SAH bins per axis (0 = 32) */
   int32_t n_threads;  /* host build threads (0 = all cores) */
   int32_t upload;     /* 1 = upload to the current CUDA device (default when
@@ -160,9 +160,9 @@ typedef struct {
 } fgl_cast_item;
 
 typedef struct {
-  int32_t packet_rays;    /* rays per work packet (0 = 64; multiple of 32) */
+  int32_t packet_rays;    /* rays per work packet (0 = 32; multiple of 32) */
   int32_t block_threads;  /* threads per block (0 = 128; multiple of 32, <= 512) */
-  int32_t stack_smem;     /* traversal stack entries kept in shared memory (0 = 12) */
+  int32_t stack_smem;     /* traversal stack entries kept in shared memory (0 = 8) */
   int32_t blocks_per_sm;  /* persistent blocks per SM (0 = as many as fit) */
   int32_t use_graph;      /* 1 = capture the launch sequence in a CUDA graph and
                              replay it while the item layout is unchanged */

@@ -81,7 +81,7 @@ fgl_status device_info(DeviceInfo* out) {
 // option defaults
 // ---------------------------------------------------------------------------
 struct Opts {
-  int packet = 64, block = 128, sdepth = 8, bpsm = 0, graph = 0, refill = 32, postpone = 20,
+  int packet = 32, block = 128, sdepth = 8, bpsm = 0, graph = 0, refill = 32, postpone = 20,
       count = 0, tri_mode = 0;
 };
 
@@ -110,8 +110,8 @@ fgl_status resolve_opts(const fgl_batch_opts* o, Opts* r) {
   DeviceInfo di;
   fgl_status s = device_info(&di);
   if (s != FGL_OK) return s;
-  if (stack_smem_bytes(d.block, d.sdepth) > di.smem_optin)
-    return fail(FGL_ERR_INVALID, "block_threads * (8 + 24 * stack_smem) bytes exceed shared memory");
+  if (stack_smem_bytes(8, d.block, d.sdepth) > di.smem_optin)
+    return fail(FGL_ERR_INVALID, "block_threads * (8 + 24 * stack_smem) bytes (the width-8 stack) exceed shared memory");
   *r = d;
   return FGL_OK;
 }
@@ -381,7 +381,7 @@ fgl_status fgl_scene_build(const float* verts, int64_t nv, const int32_t* tris, 
   *out = nullptr;
   if (!verts || !tris) return fail(FGL_ERR_INVALID, "null vertex or triangle pointer");
   if (nv < 1 || nt < 1) return fail(FGL_ERR_INVALID, "mesh needs at least one vertex and triangle");
-  int width = 4, bins = 32, threads = 0, upload = 1;
+  int width = 8, bins = 32, threads = 0, upload = 1;
   if (opts) {
     if (opts->width) width = opts->width;
     if (opts->sah_bins) bins = opts->sah_bins;
@@ -736,7 +736,7 @@ fgl_status fgl_autotune(const fgl_cast_item* items, int32_t n_items, const fgl_t
   };
   fgl_batch_opts cur = *best;
   // start from the defaults explicitly so that every dimension has a value
-  if (!cur.packet_rays) cur.packet_rays = 64;
+  if (!cur.packet_rays) cur.packet_rays = 32;
   if (!cur.block_threads) cur.block_threads = 128;
   if (!cur.stack_smem) cur.stack_smem = 12;
   if (!cur.refill_min) cur.refill_min = 32;

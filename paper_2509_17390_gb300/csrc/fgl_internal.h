@@ -43,10 +43,10 @@ namespace fgl {
 // x, y, z; width 4: bits x, y), so slots of a partly filled node may be empty.
 // Internal children of a node are stored contiguously from child_base in
 // increasing code; child index = child_base + popc(imask & ((1<<c)-1)).
-// A ray with direction-sign bits `oct` (bit a set when d_a < 0; only x, y for
-// width 4) visits children in increasing (c ^ oct), which approximates
-// near-to-far order because the builder gives each child the code of the
-// octant it sits in relative to its siblings.
+// The traversal visits the hit children of a node in increasing entry
+// distance (ties: lower slot first), carrying each child's entry distance as
+// a 16-bit key so that a child found to lie beyond a newer best hit is never
+// fetched.
 // ---------------------------------------------------------------------------
 constexpr int kMaxLeafTris = 3;
 constexpr int kMaxNodeTris = 24;

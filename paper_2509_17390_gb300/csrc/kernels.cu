@@ -42,27 +42,31 @@ __device__ __forceinline__ int postpone_threshold(int pct) {
 
 // Dynamic shared memory: one 64-bit hit key per thread (pooled leaf tests
 // merge into these), then the [sdepth][blockDim] stack arrays of groups
-// (8 B) and of child entry distances (16 B).
+// (8 B) and of child keys (2 B per child).
+template <int W>
 struct Smem {
-  unsigned long long* keys;  // this warp's 32 keys
+  using Keys = typename dev::KeyWords<W>::T;
+  unsigned long long* keys;  // this warp's 32 hit keys
   uint2* ss;                 // this thread's group column
-  uint4* sq;                 // this thread's entry-distance column
+  Keys* sq;                  // this thread's child-key column
 };
-__device__ __forceinline__ Smem smem_layout(int sdepth) {
+template <int W>
+__device__ __forceinline__ Smem<W> smem_layout(int sdepth) {
   extern __shared__ __align__(16) unsigned long long smem_u64[];
-  Smem m;
+  Smem<W> m;
   m.keys = smem_u64 + (threadIdx.x & ~31u);
   uint2* ss0 = reinterpret_cast<uint2*>(smem_u64 + blockDim.x);
   m.ss = ss0 + threadIdx.x;
-  m.sq = reinterpret_cast<uint4*>(ss0 + (size_t)sdepth * blockDim.x) + threadIdx.x;
+  m.sq = reinterpret_cast<typename Smem<W>::Keys*>(ss0 + (size_t)sdepth * blockDim.x) + threadIdx.x;
   return m;
 }
 
 template <int W, bool COUNT>
 __global__ void __maxnreg__(72) k_plain(const ItemDesc it, int sdepth, int tri_mode,
                                                int postpone_pct) {
+  using Keys = typename dev::KeyWords<W>::T;
   const unsigned FULL = 0xFFFFFFFFu;
-  const Smem sm = smem_layout(sdepth);
+  const Smem<W> sm = smem_layout<W>(sdepth);
   const int lane = threadIdx.x & 31;
   const int64_t total = (int64_t)it.n_env * it.n_rays;
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -83,8 +87,8 @@ __global__ void __maxnreg__(72) k_plain(const ItemDesc it, int sdepth, int tri_m
     tr.start(it.nodes, it.tris, it.max_range);
   }
   uint2 ls[kStackLocal];
-  uint4 lq[kStackLocal];
-  const dev::StackRefs st{sm.ss, sm.sq, ls, lq, (int)blockDim.x, sdepth};
+  Keys lq[kStackLocal];
+  const dev::StackRefs<Keys> st{sm.ss, sm.sq, ls, lq, (int)blockDim.x, sdepth};
   if (tri_mode != 1) {
     while (__any_sync(FULL, !done)) {
       bool ok = true;
@@ -120,15 +124,16 @@ template <int W, bool COUNT>
 __global__ void __maxnreg__(72) k_persistent(BatchHeader* __restrict__ hdr,
                                                     const ItemDesc* __restrict__ items, int sdepth,
                                                     int refill_min, int tri_mode, int postpone_pct) {
+  using Keys = typename dev::KeyWords<W>::T;
   const unsigned FULL = 0xFFFFFFFFu;
-  const Smem sm = smem_layout(sdepth);
+  const Smem<W> sm = smem_layout<W>(sdepth);
   const int lane = threadIdx.x & 31;
   const int64_t n_packets = hdr->n_packets;
   const int n_items = hdr->n_items;
   const int P = hdr->packet_rays;
   uint2 ls[kStackLocal];
-  uint4 lq[kStackLocal];
-  const dev::StackRefs st{sm.ss, sm.sq, ls, lq, (int)blockDim.x, sdepth};
+  Keys lq[kStackLocal];
+  const dev::StackRefs<Keys> st{sm.ss, sm.sq, ls, lq, (int)blockDim.x, sdepth};
 
   // warp-uniform packet cursor
   int pk_item = 0, pk_env = 0, pk_next = 0, pk_end = 0;
@@ -182,7 +187,7 @@ __global__ void __maxnreg__(72) k_persistent(BatchHeader* __restrict__ hdr,
             c_tris += tr.n_tris;
           }
           tr.start(it.nodes, it.tris, it.max_range);
-                const int64_t o = (int64_t)pk_env * it.n_rays + __float_as_int(ds.w);
+          const int64_t o = (int64_t)pk_env * it.n_rays + __float_as_int(ds.w);
           out_r = it.out_range + o;
           out_t = it.out_tri + o;
           active = true;
@@ -266,9 +271,9 @@ void* pick_persistent(int W, bool count) {
 
 }  // namespace
 
-size_t stack_smem_bytes(int block, int sdepth) {
+size_t stack_smem_bytes(int W, int block, int sdepth) {
   return (size_t)block * sizeof(unsigned long long) +
-         (size_t)block * (size_t)sdepth * (sizeof(uint2) + sizeof(uint4));
+         (size_t)block * (size_t)sdepth * (sizeof(uint2) + 2 * (size_t)W);
 }
 
 cudaError_t launch_plain(int W, bool count, const ItemDesc& it, int block, int sdepth,
@@ -276,7 +281,7 @@ cudaError_t launch_plain(int W, bool count, const ItemDesc& it, int block, int s
   const int64_t total = (int64_t)it.n_env * it.n_rays;
   if (total == 0) return cudaSuccess;
   const int64_t grid = (total + block - 1) / block;
-  const size_t smem = stack_smem_bytes(block, sdepth);
+  const size_t smem = stack_smem_bytes(W, block, sdepth);
   void* fn = pick_plain(W, count);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -289,7 +294,7 @@ cudaError_t launch_plain(int W, bool count, const ItemDesc& it, int block, int s
 
 int persistent_blocks_per_sm(int W, bool count, int block, int sdepth) {
   void* fn = pick_persistent(W, count);
-  const size_t smem = stack_smem_bytes(block, sdepth);
+  const size_t smem = stack_smem_bytes(W, block, sdepth);
   if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, block, smem) != cudaSuccess) return 1;
@@ -299,7 +304,7 @@ int persistent_blocks_per_sm(int W, bool count, int block, int sdepth) {
 cudaError_t launch_persistent(int W, bool count, void* scratch, int grid, int block, int sdepth,
                               int refill_min, int tri_mode, int postpone_pct, cudaStream_t s) {
   void* fn = pick_persistent(W, count);
-  const size_t smem = stack_smem_bytes(block, sdepth);
+  const size_t smem = stack_smem_bytes(W, block, sdepth);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -9,7 +9,7 @@ namespace fgl {
 
 // Dynamic shared memory of one block: a 64-bit hit key per thread plus the
 // shared part of the traversal stacks.
-size_t stack_smem_bytes(int block, int sdepth);
+size_t stack_smem_bytes(int W, int block, int sdepth);
 
 // One thread per ray of one item (grid = ceil(n_env * n_rays / block)).
 // tri_mode 0: warp-pooled leaf tests; 1: lane-serial with postponing.

@@ -40,6 +40,21 @@ __device__ __forceinline__ uint32_t half_rp(float x) {
   return (uint32_t)h;
 }
 
+// Element-wise minimum of two pairs of unsigned 16-bit integers.
+__device__ __forceinline__ uint32_t min_u16x2(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm("min.u16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+
+// Byte permute in sign-replicating form: each selector nibble 8 | b gives
+// byte b's most significant bit repeated over the 8 bits of the result byte.
+__device__ __forceinline__ uint32_t prmt_sign(uint32_t x, uint32_t sel) {
+  uint32_t r;
+  asm("prmt.b32 %0, %1, 0, %2;" : "=r"(r) : "r"(x), "r"(sel));
+  return r;
+}
+
 // Packed pair of floats (lo, hi) in one 64-bit register pair.
 __device__ __forceinline__ uint64_t pack2f(float lo, float hi) {
   uint64_t r;

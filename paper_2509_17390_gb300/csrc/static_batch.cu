@@ -103,7 +103,7 @@ extern "C" fgl_status fgl_cast_batched_static(const fgl_cast_item* items, int32_
   if (n_items > 0 && !items) return err(FGL_ERR_INVALID, "items is null");
 
   // launch options (same meaning and defaults as fgl_cast_batched; use_graph is ignored)
-  int packet = 64, block = 128, sdepth = 8, bpsm = 0, refill = 32, postpone = 20, count = 0,
+  int packet = 32, block = 128, sdepth = 8, bpsm = 0, refill = 32, postpone = 20, count = 0,
       tri_mode = 0;
   if (opts) {
     if (opts->packet_rays) packet = opts->packet_rays;
@@ -176,8 +176,8 @@ extern "C" fgl_status fgl_cast_batched_static(const fgl_cast_item* items, int32_
     return cuda_err(e);
   if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
     return cuda_err(e);
-  if (stack_smem_bytes(block, sdepth) > (size_t)optin)
-    return err(FGL_ERR_INVALID, "block_threads * (8 + 24 * stack_smem) bytes exceed shared memory");
+  if (stack_smem_bytes(8, block, sdepth) > (size_t)optin)
+    return err(FGL_ERR_INVALID, "block_threads * (8 + 24 * stack_smem) bytes (the width-8 stack) exceed shared memory");
 
   k_static_table<<<1, 256, 0, s>>>(img, (uint4*)scratch);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_err(e);

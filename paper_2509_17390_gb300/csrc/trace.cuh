@@ -139,6 +139,55 @@ __device__ __forceinline__ float tri_hit(const Ray& r, float4 a, float4 b, float
   return __fdiv_rn(T, det);
 }
 
+// Child keys of a node group: one 16-bit key per child slot, two per 32-bit
+// word (slot 2k in the low half of word k).  The key of a child still to be
+// visited is its entry distance as a half rounded toward zero, with the low
+// log2(W) bits replaced by the slot number; every other slot holds 0xFFFF.
+// Non-negative halves order like their bit patterns, so the smallest key is
+// the nearest pending child (ties go to the lower slot), and clearing low
+// bits keeps a key at or below the true entry distance.
+template <int W>
+struct KeyWords;
+template <>
+struct KeyWords<4> {
+  using T = uint2;
+};
+template <>
+struct KeyWords<8> {
+  using T = uint4;
+};
+
+__device__ __forceinline__ uint32_t key_min(const uint2& k) {
+  const uint32_t m = min_u16x2(k.x, k.y);
+  return min(m & 0xFFFFu, m >> 16);
+}
+__device__ __forceinline__ uint32_t key_min(const uint4& k) {
+  const uint32_t m = min_u16x2(min_u16x2(k.x, k.y), min_u16x2(k.z, k.w));
+  return min(m & 0xFFFFu, m >> 16);
+}
+// Mark slot `c` visited.
+__device__ __forceinline__ void key_clear(uint2& k, uint32_t c) {
+  const uint32_t h = 0xFFFFu << ((c & 1u) << 4);
+  if (c & 2u) k.y |= h;
+  else k.x |= h;
+}
+__device__ __forceinline__ void key_clear(uint4& k, uint32_t c) {
+  const uint32_t h = 0xFFFFu << ((c & 1u) << 4);
+  const uint32_t w = c >> 1;
+  k.x |= w == 0u ? h : 0u;
+  k.y |= w == 1u ? h : 0u;
+  k.z |= w == 2u ? h : 0u;
+  k.w |= w == 3u ? h : 0u;
+}
+__device__ __forceinline__ bool key_any(const uint2& k) { return (k.x & k.y) != 0xFFFFFFFFu; }
+__device__ __forceinline__ bool key_any(const uint4& k) {
+  return (k.x & k.y & k.z & k.w) != 0xFFFFFFFFu;
+}
+
+// Bit 31 of a group's second word: a node group with children left to visit
+// (triangle groups use bits 0-23 only).
+constexpr uint32_t kGroupPending = 0x80000000u;
+
 // Slab test of the W children of one quantized node.  A child box plane is
 // p + q * 2^e along each axis, so its ray parameter is q * S + B with
 // S = 2^e * inv_d and B = (p - o) * inv_d.  The byte q is read as the float
@@ -146,13 +195,13 @@ __device__ __forceinline__ float tri_hit(const Ray& r, float4 a, float4 b, float
 // node: t = fma(2^23 + q, S, B - 2^23 * S).  Rounding B - 2^23 * S costs at
 // most half a quantum, which the builder covers by growing every child box
 // one extra quantum.  The near and far planes of an axis go through one
-// packed f32x2 FMA.  Returns the node group (child_base, pending-child bits
-// << 24 | imask), the triangle group (tri_base, leaf triangle bits) and
-// every child's entry distance as a half rounded toward zero (tq, by slot).
+// packed f32x2 FMA.  Returns the node group (child_base, pending flag |
+// imask), the triangle group (tri_base, leaf triangle bits) and the keys of
+// the hit internal children.
 template <int W>
 __device__ __forceinline__ void intersect_node(const Ray& r, const uint4* __restrict__ nd,
-                                               float tmax, uint32_t oct_w, uint2& ng, uint2& tg,
-                                               uint4& tq) {
+                                               float tmax, uint2& ng, uint2& tg,
+                                               typename KeyWords<W>::T& kq) {
   const uint4 h0 = ldg4(nd), h1 = ldg4(nd + 1);
   uint32_t lox[2], loy[2], loz[2], hix[2], hiy[2], hiz[2];
   if (W == 8) {
@@ -177,14 +226,13 @@ __device__ __forceinline__ void intersect_node(const Ray& r, const uint4* __rest
   const uint64_t B2x = pack2f(Bx, Bx), B2y = pack2f(By, By), B2z = pack2f(Bz, Bz);
   const bool fx = r.oct & 1u, fy = r.oct & 2u, fz = r.oct & 4u;
   // Per 4-child meta word, byte-parallel: bit position of each child's first
-  // hit bit (internal children: 24 + (code ^ oct); leaves: triangle offset)
-  // and its bit count (unary triangle count; 1 for an internal child).
+  // hit bit (internal children: 24 + slot; leaves: triangle offset) and its
+  // bit count (unary triangle count; 1 for an internal child).
   uint32_t idx_w[2], cnt_w[2];
 #pragma unroll
   for (int w = 0; w < (W + 3) / 4; ++w) {
     const uint32_t mw = w == 0 ? h1.z : h1.w;
-    const uint32_t inner = (mw & (mw << 1)) & 0x10101010u;  // bytes 24..31
-    idx_w[w] = (mw & 0x1F1F1F1Fu) ^ ((inner >> 4) * oct_w);
+    idx_w[w] = mw & 0x1F1F1F1Fu;
     cnt_w[w] = (mw >> 5) & 0x07070707u;
   }
   uint32_t hits = 0;
@@ -207,55 +255,54 @@ __device__ __forceinline__ void intersect_node(const Ray& r, const uint4* __rest
     const uint32_t cb = __byte_perm(cnt_w[w], 0u, 0x4440u | s);
     if (tn <= tf) hits |= cb << pos;
   }
-  ng = make_uint2(h1.x, (hits & 0xFF000000u) | (e >> 24));
+  const uint32_t v = hits >> 24;  // hit internal children, by slot
+  ng = make_uint2(h1.x, (v ? kGroupPending : 0u) | (e >> 24));
   tg = make_uint2(h1.y, hits & 0x00FFFFFFu);
-  // entry distance of every child slot (= its code) as halves, rounded down
-  tq.x = pack_half2_rz(tn_all[0], tn_all[1]);
-  tq.y = pack_half2_rz(tn_all[2], tn_all[3]);
-  if (W == 8) {
-    tq.z = pack_half2_rz(tn_all[4 % W], tn_all[5 % W]);
-    tq.w = pack_half2_rz(tn_all[6 % W], tn_all[7 % W]);
-  } else {
-    tq.z = tq.w = 0u;
+  // Keys: bit 8j+7 of t0 (t1) is set when slot j (4+j) is NOT a hit internal
+  // child; a sign-replicating byte permute widens it to the slot's 16 bits.
+  constexpr uint32_t KM = W == 8 ? 0xFFF8FFF8u : 0xFFFCFFFCu;
+  const uint32_t t0 = ~((v & 0xFu) * 0x10204080u);
+  kq.x = (pack_half2_rz(tn_all[0], tn_all[1]) & KM) | 0x00010000u | prmt_sign(t0, 0x9988u);
+  kq.y = (pack_half2_rz(tn_all[2], tn_all[3]) & KM) | 0x00030002u | prmt_sign(t0, 0xBBAAu);
+  if constexpr (W == 8) {
+    const uint32_t t1 = ~((v >> 4) * 0x10204080u);
+    kq.z = (pack_half2_rz(tn_all[4 % W], tn_all[5 % W]) & KM) | 0x00050004u | prmt_sign(t1, 0x9988u);
+    kq.w = (pack_half2_rz(tn_all[6 % W], tn_all[7 % W]) & KM) | 0x00070006u | prmt_sign(t1, 0xBBAAu);
   }
 }
 
-// Entry distance (half bits) recorded for the child in slot c of a group.
-__device__ __forceinline__ uint32_t half_at(const uint4& q, uint32_t c) {
-  const uint32_t w = (c & 4u) ? ((c & 2u) ? q.w : q.z) : ((c & 2u) ? q.y : q.x);
-  return (c & 1u) ? (w >> 16) : (w & 0xFFFFu);
-}
-
-// Per-thread traversal state and stack.  A stack entry is a group (64 bits)
-// plus the entry distances of its children (128 bits, see intersect_node).
-// The stack's first `smem_depth` entries live in shared memory (columns
-// `threadIdx.x` of [smem_depth][blockDim.x] arrays, so a warp's accesses are
-// conflict-free); deeper entries go to local-memory arrays.
+// Per-thread traversal state and stack.  A stack entry is a node group
+// (64 bits) plus its child keys (32 bits per two children), or a postponed
+// triangle group.  The stack's first `sdepth` entries live in shared memory
+// (columns `threadIdx.x` of [sdepth][blockDim.x] arrays, so a warp's
+// accesses are conflict-free); deeper entries go to local-memory arrays.
 //
 // One traversal step is: descend() -- visit the nearest pending child of the
 // current node group, leaving the visited node's hit leaf triangles in `tg`
 // -- then the leaf triangle tests, either lane by lane (tri_serial) or pooled
 // across the warp (tri_phase_warp), then finish() -- pop the next group when
-// the current one is exhausted.  A pending child whose recorded entry
-// distance already exceeds the best hit is dropped without fetching it: the
-// same cull the node test applies, with the newer best t.
+// the current one is exhausted.  Children are visited in order of their
+// entry distance; when the nearest pending child already starts beyond the
+// best hit, so do the others, and the group is dropped without fetching any
+// of them -- the same cull the node test applies, with the newer best t.
+template <class K>
 struct StackRefs {
-  uint2* ss;     // shared: group entries, stride `stride`
-  uint4* sq;     // shared: entry distances, stride `stride`
-  uint2* ls;     // local spill
-  uint4* lq;
+  uint2* ss;  // shared: groups, stride `stride`
+  K* sq;      // shared: child keys, stride `stride`
+  uint2* ls;  // local spill
+  K* lq;
   int stride;
   int sdepth;
 };
 
 template <int W, bool COUNT>
 struct Tracer {
+  using Keys = typename KeyWords<W>::T;
   Ray r;
   float best_t;
   int32_t best_id;
   uint2 ng, tg;
-  uint4 tq;        // entry distances of the current node group's children
-  uint32_t ow;     // octant bits used for child order (x, y, z; x, y for width 4)
+  Keys kq;  // keys of the current node group's children
   int sp;
   const uint4* __restrict__ nodes;
   const float4* __restrict__ tris;
@@ -266,16 +313,17 @@ struct Tracer {
     tris = (const float4*)tri_ptr;
     best_t = max_range;
     best_id = kNoHit;
-    ow = W == 8 ? r.oct : (r.oct & 3u);
-    // root group: one internal child (the root node, code 0, entry 0)
-    ng = make_uint2(0u, (1u << (24 + ow)) | 1u);
+    // root group: one internal child in slot 0 (the root node), entry 0
+    ng = make_uint2(0u, kGroupPending | 1u);
     tg = make_uint2(0u, 0u);
-    tq = make_uint4(0u, 0u, 0u, 0u);
+    kq.x = 0xFFFF0000u;
+    kq.y = 0xFFFFFFFFu;
+    if constexpr (W == 8) kq.z = kq.w = 0xFFFFFFFFu;
     sp = 0;
     if (COUNT) n_nodes = n_tris = 0;
   }
 
-  __device__ __forceinline__ bool push(uint2 v, uint4 q, const StackRefs& st) {
+  __device__ __forceinline__ bool push(uint2 v, const Keys& q, const StackRefs<Keys>& st) {
     if (sp < st.sdepth) {
       st.ss[sp * st.stride] = v;
       st.sq[sp * st.stride] = q;
@@ -288,39 +336,37 @@ struct Tracer {
     ++sp;
     return true;
   }
-  __device__ __forceinline__ void pop(const StackRefs& st) {
+  __device__ __forceinline__ void pop(const StackRefs<Keys>& st) {
     --sp;
     if (sp < st.sdepth) {
       ng = st.ss[sp * st.stride];
-      tq = st.sq[sp * st.stride];
+      kq = st.sq[sp * st.stride];
     } else {
       ng = st.ls[sp - st.sdepth];
-      tq = st.lq[sp - st.sdepth];
+      kq = st.lq[sp - st.sdepth];
     }
   }
 
-  // Descend into the nearest pending child of the current node group whose
-  // recorded entry is not beyond the best hit (the remaining siblings go onto
-  // the stack), or take a popped triangle group.  Returns false on stack
-  // overflow (the ray is then abandoned).
-  __device__ __forceinline__ bool descend(const StackRefs& st) {
-    if (ng.y & 0xFF000000u) {
-      const uint32_t hb = half_rp(best_t);
-      do {
-        const uint32_t pos = __ffs(ng.y >> 24) - 1;
-        const uint32_t code = pos ^ ow;
-        ng.y &= ~(1u << (24 + pos));
-        if (half_at(tq, code) > hb) continue;  // entirely beyond the best hit
-        const uint32_t child = ng.x + __popc((ng.y & 0xFFu) & ((1u << code) - 1u));
-        if (ng.y & 0xFF000000u) {
-          if (!push(ng, tq, st)) return false;
-        }
-        intersect_node<W>(r, nodes + (size_t)child * (node_stride(W) / 16), best_t, ow, ng, tg, tq);
-        if (COUNT) ++n_nodes;
+  // Descend into the nearest pending child of the current node group (the
+  // group goes onto the stack while it has children left), or take a popped
+  // triangle group.  Returns false on stack overflow (the ray is then
+  // abandoned).
+  __device__ __forceinline__ bool descend(const StackRefs<Keys>& st) {
+    if (ng.y & kGroupPending) {
+      const uint32_t key = key_min(kq);
+      if ((key & (0xFFFFu ^ (W - 1))) > half_rp(best_t)) {
+        ng = make_uint2(0u, 0u);  // every remaining child starts beyond the best hit
+        tg = make_uint2(0u, 0u);
         return true;
-      } while (ng.y & 0xFF000000u);
-      ng = make_uint2(0u, 0u);  // every remaining child was beyond the best hit
-      tg = make_uint2(0u, 0u);
+      }
+      const uint32_t code = key & (W - 1);
+      key_clear(kq, code);
+      const uint32_t child = ng.x + __popc(ng.y & ((1u << code) - 1u) & 0xFFu);
+      if (key_any(kq)) {
+        if (!push(ng, kq, st)) return false;
+      }
+      intersect_node<W>(r, nodes + (size_t)child * (node_stride(W) / 16), best_t, ng, tg, kq);
+      if (COUNT) ++n_nodes;
     } else {
       tg = ng;
       ng = make_uint2(0u, 0u);
@@ -338,11 +384,14 @@ struct Tracer {
   // Lane-serial leaf tests; when fewer than `postpone_lanes` lanes of the
   // warp are testing triangles and this lane still has nodes to visit, its
   // triangle group is pushed and tested later.  Returns false on overflow.
-  __device__ __forceinline__ bool tri_serial(const StackRefs& st, int postpone_lanes) {
+  __device__ __forceinline__ bool tri_serial(const StackRefs<Keys>& st, int postpone_lanes) {
     while (tg.y) {
-      if (postpone_lanes > 0 && (ng.y & 0xFF000000u)) {
+      if (postpone_lanes > 0 && (ng.y & kGroupPending)) {
         if (__popc(__activemask()) < postpone_lanes) {
-          if (!push(tg, make_uint4(0u, 0u, 0u, 0u), st)) return false;
+          Keys none;
+          none.x = none.y = 0xFFFFFFFFu;
+          if constexpr (W == 8) none.z = none.w = 0xFFFFFFFFu;
+          if (!push(tg, none, st)) return false;
           tg.y = 0;
           break;
         }
@@ -359,8 +408,8 @@ struct Tracer {
 
   // After the leaf tests: pop the next group once the current node group has
   // no pending child.  Returns true when the ray is finished.
-  __device__ __forceinline__ bool finish(const StackRefs& st) {
-    if (!(ng.y & 0xFF000000u)) {
+  __device__ __forceinline__ bool finish(const StackRefs<Keys>& st) {
+    if (!(ng.y & kGroupPending)) {
       if (sp == 0) return true;
       pop(st);
     }
@@ -369,7 +418,8 @@ struct Tracer {
 
   // Lane-serial step (descend + tri_serial + finish).  Returns true when the
   // ray is finished.
-  __device__ __forceinline__ bool step(const StackRefs& st, int postpone_lanes, unsigned* status) {
+  __device__ __forceinline__ bool step(const StackRefs<Keys>& st, int postpone_lanes,
+                                       unsigned* status) {
     if (!descend(st) || !tri_serial(st, postpone_lanes)) {
       atomicOr(status, 1u);
       return true;
