@@ -79,7 +79,7 @@ typedef struct {
   int64_t node_bytes;   /* bytes of the node array (node_stride * n_nodes) */
   int64_t tri_bytes;    /* bytes of the leaf triangle array (48 * n_tris) */
   int32_t width;        /* children per node */
-  int32_t node_stride;  /* bytes per node record (80 for width 8, 64 for 4) */
+  int32_t node_stride;  /* bytes per node record (112 for width 8, 64 for 4) */
   int32_t depth;        /* levels of the wide tree (root = 1) */
   int32_t resident;     /* 1 when the arrays are on the device */
   double sah_cost;      /* SAH cost of the wide tree (node visits + tri tests, area-weighted) */

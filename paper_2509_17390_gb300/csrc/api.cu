@@ -142,6 +142,7 @@ ItemDesc make_desc(const fgl_cast_item& it) {
   d.n_env = it.n_env;
   d.n_rays = it.sensor->n_rays;
   d.max_range = it.max_range;
+  d.width = it.scene->bvh.width;
   return d;
 }
 
@@ -788,6 +789,7 @@ fgl_status fgl_sync(fgl_stream stream) {
   FGL_CUDA(cudaGetLastError());
   unsigned st = 0;
   FGL_CUDA(read_and_clear_status(&st));
+  if (st & 2u) return fail(FGL_ERR_DEVICE, "a kernel was handed an item of another BVH width");
   if (st) return fail(FGL_ERR_DEVICE, "traversal stack overflow in a kernel");
   return FGL_OK;
 }

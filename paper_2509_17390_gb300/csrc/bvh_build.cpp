@@ -5,7 +5,7 @@
 // "GPU-accelerated ray-casting"; Sec. IV-A for the LBVH routine).  Here the
 // tree is built once per scene on the host with the surface-area heuristic,
 // which gives fewer node visits per ray (the N_nodes term of eq. cost(r_j)),
-// and stored as compressed wide nodes so that one 80-byte read tests eight
+// and stored as compressed wide nodes so that one 112-byte read tests eight
 // children (the "memory layout" point at the end of Sec. IV-C).
 //
 // Compiled without FMA contraction; the one fused operation the traversal
@@ -400,7 +400,7 @@ int build_bvh(const float* V, int64_t nv, const int32_t* T, int64_t nt, int widt
     uint32_t imask = 0;
     int32_t child_base = (int32_t)wsrc.size();
     int64_t tri_base = (int64_t)(otris.size() / kTriFloats);
-    uint8_t meta[8] = {0};
+    uint32_t hb[8] = {0};
     int tri_off = 0;
     for (int j = 0; j < n; ++j) {
       int i = pos[j];
@@ -408,13 +408,13 @@ int build_bvh(const float* V, int64_t nv, const int32_t* T, int64_t nt, int widt
       bool inner = !dp.leaf[kids[i]];
       if (inner) {
         imask |= 1u << code[i];
-        meta[code[i]] = (uint8_t)((1u << 5) | (24u + (uint32_t)code[i]));
+        hb[code[i]] = 1u << (24 + code[i]);
         wsrc.push_back(kids[i]);
         wdepth.push_back(wdepth[w] + 1);
         max_depth = std::max(max_depth, wdepth[w] + 1);
       } else {
         int cnt = c.count;
-        meta[code[i]] = (uint8_t)((((1u << cnt) - 1u) << 5) | (uint32_t)tri_off);
+        hb[code[i]] = ((1u << cnt) - 1u) << tri_off;
         for (int t = 0; t < cnt; ++t) {
           int32_t k = idx[c.first + t];
           for (int v = 0; v < 3; ++v) {
@@ -496,8 +496,8 @@ int build_bvh(const float* V, int64_t nv, const int32_t* T, int64_t nt, int widt
     uint32_t cb = (uint32_t)child_base, tb = (uint32_t)tri_base;
     std::memcpy(rec + 16, &cb, 4);
     std::memcpy(rec + 20, &tb, 4);
-    std::memcpy(rec + 24, meta, W);
-    for (int r = 0; r < 6; ++r) std::memcpy(rec + 32 + r * W, q[r], W);
+    std::memcpy(rec + node_hb_offset(W), hb, 4 * W);
+    for (int r = 0; r < 6; ++r) std::memcpy(rec + node_q_offset(W) + r * W, q[r], W);
   }
 
   if (max_depth > kMaxWideDepth) {
@@ -553,21 +553,25 @@ int64_t verify_bvh(const HostBVH& b, std::string* first_error) {
     Box all;
     all.reset();
     for (int j = 0; j < W; ++j) {
-      uint8_t mt = rec[24 + j];
-      if (mt == 0) continue;
+      uint32_t hbj;
+      std::memcpy(&hbj, rec + node_hb_offset(W) + 4 * j, 4);
+      if (hbj == 0) continue;
       Box cbx;
       cbx.reset();
-      if ((mt & 0x18) == 0x18) {
-        int c = (mt & 31) - 24;
-        if (!((imask >> c) & 1u)) fail("meta/imask mismatch at node " + std::to_string(ni));
-        int64_t child = (int64_t)cbase + __builtin_popcount(imask & ((1u << c) - 1u));
+      if (hbj >> 24) {
+        if (hbj != (1u << (24 + j)) || !((imask >> j) & 1u))
+          fail("hit bits / imask mismatch at node " + std::to_string(ni));
+        int64_t child = (int64_t)cbase + __builtin_popcount(imask & ((1u << j) - 1u));
         if (child <= ni || child >= N) {
           fail("child index out of range at node " + std::to_string(ni));
           continue;
         }
         cbx = content[child];
       } else {
-        int off = mt & 31, cnt = __builtin_popcount(mt >> 5);
+        const int off = __builtin_ctz(hbj), cnt = __builtin_popcount(hbj);
+        if ((imask >> j) & 1u) fail("leaf slot marked internal at node " + std::to_string(ni));
+        if (cnt > kMaxLeafTris || (hbj >> off) != (1u << cnt) - 1u)
+          fail("leaf hit bits not a short contiguous run at node " + std::to_string(ni));
         for (int t = 0; t < cnt; ++t) {
           int64_t ti = (int64_t)tbase + off + t;
           if (ti >= b.n_tris) {
@@ -587,8 +591,8 @@ int64_t verify_bvh(const HostBVH& b, std::string* first_error) {
         }
       }
       for (int a = 0; a < 3; ++a) {
-        float dlo = decode(rec[32 + a * W + j], scale[a], p[a]);
-        float dhi = decode(rec[32 + (3 + a) * W + j], scale[a], p[a]);
+        float dlo = decode(rec[node_q_offset(W) + a * W + j], scale[a], p[a]);
+        float dhi = decode(rec[node_q_offset(W) + (3 + a) * W + j], scale[a], p[a]);
         const double g = m + (double)scale[a];  // margin plus one quantum
         if (!((double)dlo <= (double)cbx.lo[a] - g) || !((double)dhi >= (double)cbx.hi[a] + g))
           fail("child box does not contain its content (node " + std::to_string(ni) + ", pos " +

@@ -23,16 +23,20 @@ namespace fgl {
 //                          e* = biased float exponent of the per-axis scale
 //                          2^(e-127); imask bit c set when the child with
 //                          octant code c is an internal node
-//   bytes 16..31 : uint32 child_base         node index of the first internal child
+//   bytes 16..23 : uint32 child_base         node index of the first internal child
 //                  uint32 tri_base           index of the node's first leaf triangle
-//                  uint8  meta[W] (+pad)     per child position:
-//                     0                       empty position
-//                     0b001_11ccc             internal child with octant code ccc
-//                     0bNNN_ooooo (ooooo<24)  leaf: NNN = unary triangle count
-//                                             (001, 011, 111), ooooo = offset of
-//                                             its first triangle from tri_base
-//   bytes 32..   : uint8 q[6][W]             child boxes in units of the scale:
+//   hit bits     : uint32 hb[W]              per child slot, the bits a hit on that
+//                                             child contributes to the traversal's
+//                                             group words: internal child in slot c:
+//                                             1 << (24 + c); leaf: NNN << off, NNN =
+//                                             unary triangle count (1, 3, 7), off =
+//                                             offset of its first triangle from
+//                                             tri_base (off + count <= 24); empty: 0
+//   quantized    : uint8 q[6][W]             child boxes in units of the scale:
 //                                             lo_x, lo_y, lo_z, hi_x, hi_y, hi_z
+//
+//   width 8 (112 B): hb at bytes 80..111, q at 32..79, bytes 24..31 zero
+//   width 4 ( 64 B): hb at bytes 24..39, q at 40..63
 //
 // Decoding a box coordinate is fmaf(q, 2^(e-127), p) in float32; the builder
 // rounds outward so that every decoded child box contains the child's content
@@ -51,7 +55,9 @@ namespace fgl {
 constexpr int kMaxLeafTris = 3;
 constexpr int kMaxNodeTris = 24;
 
-FGL_HD constexpr int node_stride(int width) { return width == 8 ? 80 : 64; }
+FGL_HD constexpr int node_stride(int width) { return width == 8 ? 112 : 64; }
+FGL_HD constexpr int node_hb_offset(int width) { return width == 8 ? 80 : 24; }
+FGL_HD constexpr int node_q_offset(int width) { return width == 8 ? 32 : 40; }
 
 // Leaf triangle record: 3 x float4 = 48 bytes
 //   {v0.x, v0.y, v0.z, id as int bits}, {v1.xyz, 0}, {v2.xyz, 0}
@@ -100,7 +106,8 @@ struct alignas(16) ItemDesc {
   int32_t n_rays;
   int32_t pk_per_env;    // packets per environment
   float max_range;
-  int32_t pad[2];
+  int32_t width;         // BVH width of `nodes`; a kernel for another width skips the item
+  int32_t pad;
 };
 static_assert(sizeof(ItemDesc) == 80, "ItemDesc layout");
 

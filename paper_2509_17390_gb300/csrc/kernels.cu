@@ -16,7 +16,7 @@
 
 namespace fgl {
 
-__device__ unsigned int g_status;
+__device__ unsigned int g_status;  // bit 0: stack overflow; bit 1: item of another width
 __device__ unsigned long long g_counters[3];  // rays, node visits, triangle tests
 
 namespace {
@@ -68,6 +68,10 @@ __global__ void __maxnreg__(72) k_plain(const ItemDesc it, int sdepth, int tri_m
   const unsigned FULL = 0xFFFFFFFFu;
   const Smem<W> sm = smem_layout<W>(sdepth);
   const int lane = threadIdx.x & 31;
+  if (it.width != W) {  // never read nodes laid out for another width
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&g_status, 2u);
+    return;
+  }
   const int64_t total = (int64_t)it.n_env * it.n_rays;
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool done = gid >= total;
@@ -173,6 +177,11 @@ __global__ void __maxnreg__(72) k_persistent(BatchHeader* __restrict__ hdr,
           const int chunk = (int)(local - (int64_t)pk_env * ppe);
           pk_next = chunk * P;
           pk_end = min(pk_next + P, items[lo].n_rays);
+        }
+        if (items[pk_item].width != W) {  // never read nodes laid out for another width
+          if (lane == 0) atomicOr(&g_status, 2u);
+          pk_next = pk_end;
+          continue;
         }
         const int avail = pk_end - pk_next;
         const int rank = __popc(idle & ((1u << lane) - 1u));

@@ -195,7 +195,8 @@ constexpr uint32_t kGroupPending = 0x80000000u;
 // node: t = fma(2^23 + q, S, B - 2^23 * S).  Rounding B - 2^23 * S costs at
 // most half a quantum, which the builder covers by growing every child box
 // one extra quantum.  The near and far planes of an axis go through one
-// packed f32x2 FMA.  Returns the node group (child_base, pending flag |
+// packed f32x2 FMA.  A hit child contributes its precomputed hit bits (its
+// leaf triangles' bits, or bit 24 + slot for an internal child).  Returns the node group (child_base, pending flag |
 // imask), the triangle group (tri_base, leaf triangle bits) and the keys of
 // the hit internal children.
 template <int W>
@@ -203,16 +204,20 @@ __device__ __forceinline__ void intersect_node(const Ray& r, const uint4* __rest
                                                float tmax, uint2& ng, uint2& tg,
                                                typename KeyWords<W>::T& kq) {
   const uint4 h0 = ldg4(nd), h1 = ldg4(nd + 1);
-  uint32_t lox[2], loy[2], loz[2], hix[2], hiy[2], hiz[2];
+  uint32_t lox[2], loy[2], loz[2], hix[2], hiy[2], hiz[2], hb[W];
   if (W == 8) {
     const uint4 q0 = ldg4(nd + 2), q1 = ldg4(nd + 3), q2 = ldg4(nd + 4);
+    const uint4 m0 = ldg4(nd + 5), m1 = ldg4(nd + 6);
     lox[0] = q0.x; lox[1] = q0.y; loy[0] = q0.z; loy[1] = q0.w;
     loz[0] = q1.x; loz[1] = q1.y; hix[0] = q1.z; hix[1] = q1.w;
     hiy[0] = q2.x; hiy[1] = q2.y; hiz[0] = q2.z; hiz[1] = q2.w;
+    hb[0] = m0.x; hb[1] = m0.y; hb[2] = m0.z; hb[3] = m0.w;
+    hb[4 % W] = m1.x; hb[5 % W] = m1.y; hb[6 % W] = m1.z; hb[7 % W] = m1.w;
   } else {
     const uint4 q0 = ldg4(nd + 2), q1 = ldg4(nd + 3);
-    lox[0] = q0.x; loy[0] = q0.y; loz[0] = q0.z; hix[0] = q0.w;
-    hiy[0] = q1.x; hiz[0] = q1.y;
+    hb[0] = h1.z; hb[1] = h1.w; hb[2] = q0.x; hb[3 % W] = q0.y;
+    lox[0] = q0.z; loy[0] = q0.w; loz[0] = q1.x; hix[0] = q1.y;
+    hiy[0] = q1.z; hiz[0] = q1.w;
     lox[1] = loy[1] = loz[1] = hix[1] = hiy[1] = hiz[1] = 0;
   }
   const uint32_t e = h0.w;
@@ -225,16 +230,6 @@ __device__ __forceinline__ void intersect_node(const Ray& r, const uint4* __rest
   const uint64_t S2x = pack2f(Sx, Sx), S2y = pack2f(Sy, Sy), S2z = pack2f(Sz, Sz);
   const uint64_t B2x = pack2f(Bx, Bx), B2y = pack2f(By, By), B2z = pack2f(Bz, Bz);
   const bool fx = r.oct & 1u, fy = r.oct & 2u, fz = r.oct & 4u;
-  // Per 4-child meta word, byte-parallel: bit position of each child's first
-  // hit bit (internal children: 24 + slot; leaves: triangle offset) and its
-  // bit count (unary triangle count; 1 for an internal child).
-  uint32_t idx_w[2], cnt_w[2];
-#pragma unroll
-  for (int w = 0; w < (W + 3) / 4; ++w) {
-    const uint32_t mw = w == 0 ? h1.z : h1.w;
-    idx_w[w] = mw & 0x1F1F1F1Fu;
-    cnt_w[w] = (mw >> 5) & 0x07070707u;
-  }
   uint32_t hits = 0;
   float tn_all[W];
 #pragma unroll
@@ -251,9 +246,7 @@ __device__ __forceinline__ void intersect_node(const Ray& r, const uint4* __rest
     const float tn = max3f(tnx, tny, fmaxf(tnz, 0.f));
     const float tf = min3f(tfx, tfy, fminf(tfz, tmax));
     tn_all[i] = tn;
-    const uint32_t pos = __byte_perm(idx_w[w], 0u, 0x4440u | s);
-    const uint32_t cb = __byte_perm(cnt_w[w], 0u, 0x4440u | s);
-    if (tn <= tf) hits |= cb << pos;
+    if (tn <= tf) hits |= hb[i];
   }
   const uint32_t v = hits >> 24;  // hit internal children, by slot
   ng = make_uint2(h1.x, (v ? kGroupPending : 0u) | (e >> 24));
@@ -406,14 +399,19 @@ struct Tracer {
     return true;
   }
 
-  // After the leaf tests: pop the next group once the current node group has
-  // no pending child.  Returns true when the ray is finished.
+  // After the leaf tests: once the current node group has no pending child,
+  // pop until a group with a child not beyond the best hit (or a postponed
+  // triangle group) is on top; dead groups cost a shared-memory load each
+  // instead of a traversal step.  Returns true when the ray is finished.
   __device__ __forceinline__ bool finish(const StackRefs<Keys>& st) {
-    if (!(ng.y & kGroupPending)) {
+    if (ng.y & kGroupPending) return false;
+    const uint32_t hb = half_rp(best_t);
+    for (;;) {
       if (sp == 0) return true;
       pop(st);
+      if (!(ng.y & kGroupPending)) return false;
+      if ((key_min(kq) & (0xFFFFu ^ (W - 1))) <= hb) return false;
     }
-    return false;
   }
 
   // Lane-serial step (descend + tri_serial + finish).  Returns true when the

@@ -44,7 +44,9 @@ def test_header_compiles_as_c(tmp_path):
 # host builder
 # ---------------------------------------------------------------------------
 def decode_nodes(nodes: np.ndarray, width: int):
-    S = 80 if width == 8 else 64
+    """Node records as laid out by the builder: width 8 in 112 B (hit bits at
+    80, quantized planes at 32), width 4 in 64 B (hit bits at 24, planes at 40)."""
+    S, HB, Q = (112, 80, 32) if width == 8 else (64, 24, 40)
     rec = nodes.reshape(-1, S)
     p = rec[:, 0:12].copy().view(np.float32)
     packed = rec[:, 12:16].copy().view(np.uint32)[:, 0]
@@ -52,11 +54,11 @@ def decode_nodes(nodes: np.ndarray, width: int):
     scale = (e << 23).view(np.float32)
     imask = packed >> 24
     base = rec[:, 16:24].copy().view(np.uint32)
-    meta = rec[:, 24:24 + width]
-    q = rec[:, 32:32 + 6 * width].reshape(-1, 6, width).astype(np.float32)
+    hb = rec[:, HB:HB + 4 * width].copy().view(np.uint32)
+    q = rec[:, Q:Q + 6 * width].reshape(-1, 6, width).astype(np.float32)
     lo = (q[:, 0:3] * scale[:, :, None]).astype(np.float32) + p[:, :, None]   # q*2^e is exact
     hi = (q[:, 3:6] * scale[:, :, None]).astype(np.float32) + p[:, :, None]
-    return dict(p=p, imask=imask, child_base=base[:, 0], tri_base=base[:, 1], meta=meta, lo=lo, hi=hi,
+    return dict(p=p, imask=imask, child_base=base[:, 0], tri_base=base[:, 1], hb=hb, lo=lo, hi=hi,
                 scale=scale)
 
 
@@ -76,18 +78,20 @@ def check_tree(v, t, width):
     chi = np.full((N, 3), -np.inf)
     for ni in range(N - 1, -1, -1):
         for j in range(width):
-            mt = int(D["meta"][ni, j])
-            if mt == 0:
+            hb = int(D["hb"][ni, j])
+            if hb == 0:
                 continue
-            if (mt & 0x18) == 0x18:
-                c = (mt & 31) - 24
-                assert (D["imask"][ni] >> c) & 1
-                child = int(D["child_base"][ni]) + bin(int(D["imask"][ni]) & ((1 << c) - 1)).count("1")
+            if hb >> 24:
+                assert hb == 1 << (24 + j)                             # internal child: bit 24 + slot
+                assert (D["imask"][ni] >> j) & 1
+                child = int(D["child_base"][ni]) + bin(int(D["imask"][ni]) & ((1 << j) - 1)).count("1")
                 assert ni < child < N
                 lo, hi = clo[child], chi[child]
             else:
-                off, cnt = mt & 31, bin(mt >> 5).count("1")
-                assert 1 <= cnt <= 3
+                assert not (D["imask"][ni] >> j) & 1
+                off = (hb & -hb).bit_length() - 1
+                cnt = bin(hb).count("1")
+                assert 1 <= cnt <= 3 and hb >> off == (1 << cnt) - 1   # a short contiguous run
                 k = int(D["tri_base"][ni]) + off
                 pts = tv[k:k + cnt].reshape(-1, 3).astype(np.float64)
                 lo, hi = pts.min(0), pts.max(0)
@@ -104,7 +108,7 @@ def check_tree(v, t, width):
 def test_builder_boxes_conservative_tiny_room(width):
     v, t, _ = synth.tiny_room_scene(1)
     st = check_tree(v, t, width)
-    assert st["width"] == width and st["node_stride"] == (80 if width == 8 else 64)
+    assert st["width"] == width and st["node_stride"] == (112 if width == 8 else 64)
 
 
 @pytest.mark.parametrize("width", [8, 4])

@@ -186,6 +186,25 @@ def test_batched_variants_bitwise_and_equal_plain(indoor, indoor_scenes, tiny):
                 assert np.array_equal(pr, br) and np.array_equal(pi, bi), (packet, block, sdepth)
 
 
+def test_graph_replay_after_scene_rebuilt_at_other_width(indoor, indoor_scenes):
+    """A captured graph is never replayed for a scene of another BVH width,
+    even when the new scene's buffers land at the freed scene's addresses:
+    the item records carry the width, so the graph's key changes."""
+    w = indoor
+    P = synth.sample_free_pose(np.random.default_rng(11), w.obstacles, 4)
+    s = fgl.Sensor.from_table(synth.grid_sensor(16, -15, 15, 360))
+    ref = run_plain(indoor_scenes[8], s, P, 120.0)
+    assert all(np.array_equal(a, b) for a, b in zip(ref, run_plain(indoor_scenes[4], s, P, 120.0)))
+    stream = torch.cuda.Stream()
+    opts = fgl.BatchOpts(use_graph=1)
+    for W in (8, 4, 8, 4):
+        sc = fgl.Scene(w.verts, w.tris, width=W)
+        for rep in range(2):
+            (r, i), = run_batched([(sc, s, P, 120.0)], opts, stream=stream)
+            assert np.array_equal(r, ref[0]) and np.array_equal(i, ref[1]), (W, rep)
+        sc.close()
+
+
 # ---------------------------------------------------------------------------
 # edge cases
 # ---------------------------------------------------------------------------
