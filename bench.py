@@ -14,7 +14,11 @@ Printed JSON line (rank 0):
                    buffers (poses H2D and ranges+ids D2H inside the timed region)
   per_env_launch   the plain form: one fgl_cast launch per environment
   roofline         algorithmic node+triangle+I/O bytes per launch / kernel time
-                   against the measured HBM copy bandwidth
+                   against the measured HBM copy bandwidth (the cost model of
+                   eq. cost(r_j) as bytes; the kernel is served from L1/L2)
+  roofline_issue   warp instructions per ray (ncu, same sources) x rays / kernel
+                   time against 4 warp instructions per SM per cycle: the
+                   kernel's actual limiter
   cpu_baseline     the FP64 oracle on the host cores over a bounded sample
 
 --impl reference times the FP64 CPU oracle (the only reference this method
@@ -62,17 +66,23 @@ def read_peaks():
         return 6800.0, "fallback"
 
 
-def read_traffic(name: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources."""
+def read_profile(name: str, field: str):
+    """A per-launch figure from the committed ncu summary (profiles/traffic.json),
+    if it was taken on the current kernel sources."""
     try:
         d = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
         e = d.get(name)
-        if e and e.get("kernel_hash") == kernel_hash():
-            return float(e["dram_bytes_per_launch"])
+        if e and e.get("kernel_hash") == kernel_hash() and e.get(field) is not None:
+            return float(e[field])
     except Exception:
         pass
     return None
+
+
+def read_traffic(name: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources."""
+    return read_profile(name, "dram_bytes_per_launch")
 
 
 class ClockSampler:
@@ -377,6 +387,19 @@ def main():
                 "peak_source": peak_kind, "bytes_per_ray": round(b_ray, 1),
                 "node_visits_per_ray": round(c_nodes / max(1, c_rays), 2),
                 "tri_tests_per_ray": round(c_tris / max(1, c_rays), 2)}
+    # instruction issue, the kernel's actual limiter: warp instructions per ray
+    # (ncu, same kernel sources) x rays / kernel time, against 4 warp
+    # instructions per SM per cycle at the SM clock sampled during the run
+    ipr = read_profile("k_persistent", "warp_inst_per_ray")
+    roofline_issue = None
+    if ipr is not None:
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = (clocks or {}).get("sm_mhz") or (clocks or {}).get("sm_max_mhz") or 2070.0
+        ipeak = 4.0 * sms * mhz * 1e6 / 1e9
+        iach = ipr * n_rays / (kern_ms / 1e3) / 1e9
+        roofline_issue = {"bound": "issue", "achieved": round(iach, 1), "peak": round(ipeak, 1),
+                          "unit": "G warp-inst/s", "frac": round(iach / ipeak, 4),
+                          "warp_inst_per_ray": ipr, "peak_basis": f"4 x {sms} SMs x {mhz:.0f} MHz"}
 
     # per-env launch (plain form): one fgl_cast per environment
     per_env = None
@@ -456,7 +479,7 @@ def main():
                        "between timed steps (256 MiB write)", "bvh_width": st["width"],
                        "opts": opts.as_dict(), "scene_tris": st["n_tris"],
                        "rays_per_step": n_rays, "frames_per_s": round(ws * n_env / (ms / 1e3), 1)},
-            "gpu_launches": args.steps, "roofline": roofline, "e2e": e2e,
+            "gpu_launches": args.steps, "roofline": roofline, "roofline_issue": roofline_issue, "e2e": e2e,
             "per_env_launch": per_env, "served": served, "cpu_baseline": cpu, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

@@ -141,7 +141,8 @@ fgl_status fgl_sensor_dirs(fgl_sensor sensor, float* out_dirs);
 /* ------------------------------------------------------------------------ */
 
 /* Plain form: one kernel launch, one thread per ray, over n_env poses of one
- * sensor against one scene.
+ * sensor against one scene, with t_min = 0 (a min_range needs the batched
+ * form).
  *   poses:     device float32 [n_env][3][4]
  *   out_range: device float32 [n_env * n_rays]; out_tri: device int32, same.
  * n_env == 0 is a no-op.  Errors: FGL_ERR_INVALID (null handle/pointer,
@@ -149,14 +150,20 @@ fgl_status fgl_sensor_dirs(fgl_sensor sensor, float* out_dirs);
 fgl_status fgl_cast(fgl_scene scene, fgl_sensor sensor, const float* poses, int32_t n_env,
                     float max_range, float* out_range, int32_t* out_tri, fgl_stream stream);
 
+/* One batched work item.  The return of each ray is its nearest mesh
+ * intersection with t in [min_range, max_range] (eq. t_j*: intersections
+ * outside the sensor's [t_min, t_max] are discarded), t > 0 always; a
+ * surface nearer than min_range is passed through, so the ray may return a
+ * farther surface behind it.  No intersection -> (max_range, -1). */
 typedef struct {
   fgl_scene scene;
   fgl_sensor sensor;
   const float* poses;   /* device float32 [n_env][3][4] */
   int32_t n_env;
-  float max_range;
+  float max_range;      /* t_max: finite, > 0 */
   float* out_range;     /* device float32 [n_env * n_rays] */
   int32_t* out_tri;     /* device int32  [n_env * n_rays] */
+  float min_range;      /* t_min: finite, 0 <= min_range < max_range (0 = none) */
 } fgl_cast_item;
 
 typedef struct {
@@ -291,6 +298,7 @@ typedef struct {
   const float* poses;        /* host float32 [n_env][3][4]; copied by submit */
   float* out_range;          /* host float32 [n_env * n_rays]; page-locked is fastest */
   int32_t* out_tri;          /* host int32  [n_env * n_rays] */
+  float min_range;           /* t_min, as in fgl_cast_item (0 = none) */
 } fgl_request;
 
 typedef struct {

@@ -54,8 +54,8 @@ def lib():
             L.orc_scene_free.argtypes = [P]
             L.orc_scene_depth.argtypes = [P]
             L.orc_scene_depth.restype = I32
-            L.orc_cast.argtypes = [P, P, P, I64, D, I32, P, P, P]
-            L.orc_validate.argtypes = [P, P, P, I64, D, P, P, I32, P]
+            L.orc_cast.argtypes = [P, P, P, I64, D, D, I32, P, P, P]
+            L.orc_validate.argtypes = [P, P, P, I64, D, D, P, P, I32, P]
             L.orc_tri_test.argtypes = [P, P, P, P, P, P]
             L.orc_tri_test.restype = I32
             _lib = L
@@ -117,26 +117,27 @@ class Scene:
         return lib().orc_scene_depth(self._h)
 
     def cast(self, o: np.ndarray, d: np.ndarray, max_range: float, flags: bool = True,
-             nthreads: int = 0):
-        """Nearest hit (eq. t_j*): (range f64, id i32, flags u8 or None)."""
+             nthreads: int = 0, min_range: float = 0.0):
+        """Nearest hit (eq. t_j*) among intersections with t > 0 and
+        min_range <= t <= max_range: (range f64, id i32, flags u8 or None)."""
         o = np.ascontiguousarray(o, np.float32).reshape(-1, 3)
         d = np.ascontiguousarray(d, np.float32).reshape(-1, 3)
         n = len(o)
         t = np.empty(n, np.float64)
         ids = np.empty(n, np.int32)
         fl = np.empty(n, np.uint8) if flags else None
-        lib().orc_cast(self._h, _ptr(o), _ptr(d), n, float(max_range), int(nthreads), _ptr(t),
+        lib().orc_cast(self._h, _ptr(o), _ptr(d), n, float(min_range), float(max_range), int(nthreads), _ptr(t),
                        _ptr(ids), _ptr(fl) if flags else None)
         return t, ids, fl
 
-    def validate(self, o, d, max_range, rng, ids, nthreads: int = 0) -> np.ndarray:
+    def validate(self, o, d, max_range, rng, ids, nthreads: int = 0, min_range: float = 0.0) -> np.ndarray:
         """Per ray: is (range, id) an acceptable FP32 answer?  (bool array)"""
         o = np.ascontiguousarray(o, np.float32).reshape(-1, 3)
         d = np.ascontiguousarray(d, np.float32).reshape(-1, 3)
         r = np.ascontiguousarray(rng, np.float32)
         i = np.ascontiguousarray(ids, np.int32)
         ok = np.empty(len(o), np.uint8)
-        lib().orc_validate(self._h, _ptr(o), _ptr(d), len(o), float(max_range), _ptr(r), _ptr(i),
+        lib().orc_validate(self._h, _ptr(o), _ptr(d), len(o), float(min_range), float(max_range), _ptr(r), _ptr(i),
                            int(nthreads), _ptr(ok))
         return ok.astype(bool)
 

@@ -9,7 +9,8 @@
 //     x_s = t_s (the pose translation) and d_j = R_s applied to the beam's
 //     sensor-frame unit direction (orc_sensor_dirs, orc_world_rays);
 //   * the LiDAR return, eq. t_j*: the smallest ray parameter at which the ray
-//     meets any mesh triangle, over (t_min, t_max] = (0, max_range]
+//     meets any mesh triangle, among intersections with t inside the sensor's
+//     range [t_min, t_max] = [min_range, max_range], and always t > 0
 //     (orc_cast).  Ties in t go to the smaller triangle id; a miss is reported
 //     as (max_range, -1).
 // The paper traverses a BVH pruned by the best-so-far t (Sec. IV-C, "GPU-
@@ -30,8 +31,9 @@
 //          ray parameter in [-1e-4, t* + tol(t*)], with L_k the largest
 //          distance from the ray origin to that triangle's vertices;
 //   TIE  : another triangle is hit within tol(t*) of the nearest hit;
-//   RANGE: a triangle is hit at |t| <= 1e-4 or within tol(max_range) of
-//          max_range, inside the same window;
+//   RANGE: a triangle is hit at |t| <= 1e-4, or within tol(max_range) of
+//          max_range, or (min_range > 0) within tol(min_range) of
+//          min_range, inside the same window;
 // where tol(x) = 1e-4 + 1e-6 * x (metres, unit-length rays).
 //
 // Build: g++ -O2 -std=c++17 -ffp-contract=off -fPIC -shared -pthread.
@@ -251,14 +253,14 @@ void bvh_visit(const Scene& s, V3 o, V3 d, double t0, double t1, double grow_rel
   }
 }
 
-// Nearest hit over (0, max_range], ties to the smaller id.
-void nearest(const Scene& s, V3 o, V3 d, double R, double* out_t, int32_t* out_id) {
+// Nearest hit with t > 0 and Rmin <= t <= R, ties to the smaller id.
+void nearest(const Scene& s, V3 o, V3 d, double Rmin, double R, double* out_t, int32_t* out_id) {
   double bt = std::numeric_limits<double>::infinity();
   int64_t bid = -1;
   auto consider = [&](int64_t k) {
     double t;
     if (!tri_test(o, d, s.vert(k, 0), s.vert(k, 1), s.vert(k, 2), &t)) return;
-    if (!(t > 0.0) || !(t <= R)) return;
+    if (!(t > 0.0) || !(t >= Rmin) || !(t <= R)) return;
     if (t < bt || (t == bt && k < bid)) {
       bt = t;
       bid = k;
@@ -325,7 +327,7 @@ inline bool near_edge(const Scene& s, int64_t k, V3 o, V3 d, double tw0, double 
   return false;
 }
 
-uint8_t flags_for(const Scene& s, V3 o, V3 d, double R, double t_star, int32_t id_star) {
+uint8_t flags_for(const Scene& s, V3 o, V3 d, double Rmin, double R, double t_star, int32_t id_star) {
   double tw0 = -kAbsTol;
   double tw1 = t_star + tol(t_star);
   uint8_t fl = 0;
@@ -335,7 +337,9 @@ uint8_t flags_for(const Scene& s, V3 o, V3 d, double R, double t_star, int32_t i
     if (tri_test(o, d, s.vert(k, 0), s.vert(k, 1), s.vert(k, 2), &t)) {
       if (t >= tw0 && t <= tw1) {
         if (std::fabs(t) <= kAbsTol || std::fabs(t - R) <= tol(R)) fl |= FLAG_RANGE;
-        if (id_star >= 0 && k != id_star && t > 0.0 && t <= R && std::fabs(t - t_star) <= tol(t_star))
+        if (Rmin > 0.0 && std::fabs(t - Rmin) <= tol(Rmin)) fl |= FLAG_RANGE;
+        if (id_star >= 0 && k != id_star && t > 0.0 && t >= Rmin && t <= R &&
+            std::fabs(t - t_star) <= tol(t_star))
           fl |= FLAG_TIE;
       }
     }
@@ -350,17 +354,20 @@ uint8_t flags_for(const Scene& s, V3 o, V3 d, double R, double t_star, int32_t i
 
 // Is (range, id) an acceptable FP32 answer for this ray?  Accepted when
 //  * id >= 0: triangle id's plane is crossed within tol of `range`, the
-//    crossing lies in (0 - 1e-4, R + tol(R)], and the ray meets the triangle
-//    or passes within 1e-6 L of its boundary; a miss must report range == R;
-//  * every triangle the FP64 test hits at t in (1e-4, range - tol(range))
-//    (or (1e-4, R - tol(R)) for a miss) is an edge-grazing one.
-bool validate_one(const Scene& s, V3 o, V3 d, double R, double range, int32_t id) {
+//    crossing lies in [Rmin - tol(Rmin), R + tol(R)] (from -1e-4 when
+//    Rmin = 0), and the ray meets the triangle or passes within 1e-6 L of its
+//    boundary; a miss must report range == R;
+//  * every triangle the FP64 test hits at t in (lo, range - tol(range)) (or
+//    (lo, R - tol(R)) for a miss), lo = max(1e-4, Rmin + tol(Rmin)) (1e-4
+//    when Rmin = 0), is an edge-grazing one.
+bool validate_one(const Scene& s, V3 o, V3 d, double Rmin, double R, double range, int32_t id) {
   if (id >= s.nt || id < -1) return false;
   double lim;
   if (id >= 0) {
     double tg = plane_t(o, d, s.vert(id, 0), s.vert(id, 1), s.vert(id, 2));
     if (!(std::fabs(tg - range) <= tol(tg))) return false;
-    if (!(tg >= -kAbsTol && tg <= R + tol(R))) return false;
+    const double tlo = Rmin > 0.0 ? Rmin - tol(Rmin) : -kAbsTol;
+    if (!(tg >= tlo && tg <= R + tol(R))) return false;
     double t;
     bool inside = tri_test(o, d, s.vert(id, 0), s.vert(id, 1), s.vert(id, 2), &t);
     if (!inside && !near_edge(s, id, o, d, tg - tol(tg), tg + tol(tg))) return false;
@@ -369,16 +376,17 @@ bool validate_one(const Scene& s, V3 o, V3 d, double R, double range, int32_t id
     if (range != R) return false;
     lim = R - tol(R);
   }
+  const double lo = Rmin > 0.0 ? std::max(kAbsTol, Rmin + tol(Rmin)) : kAbsTol;
   bool ok = true;
   auto visit = [&](int64_t k) {
     if (!ok) return;
     double t;
     if (!tri_test(o, d, s.vert(k, 0), s.vert(k, 1), s.vert(k, 2), &t)) return;
-    if (t > kAbsTol && t < lim) {
+    if (t > lo && t < lim) {
       if (!near_edge(s, k, o, d, t - tol(t), t + tol(t))) ok = false;
     }
   };
-  if (lim > kAbsTol) {
+  if (lim > lo) {
     if (!s.use_bvh) {
       for (int64_t k = 0; k < s.nt; ++k) visit(k);
     } else {
@@ -417,7 +425,7 @@ inline V3 ld3(const float* p, int64_t i) { return {(double)p[3 * i], (double)p[3
 
 extern "C" {
 
-int orc_version(void) { return 1; }
+int orc_version(void) { return 2; }
 
 // Sensor-frame unit directions (eq. r_j, d_j in S^2): from per-ray elevation
 // and azimuth (radians, float32), d = (cos el cos az, cos el sin az, sin el)
@@ -479,28 +487,31 @@ void orc_scene_free(void* h) { delete static_cast<Scene*>(h); }
 int orc_scene_depth(void* h) { return static_cast<Scene*>(h)->depth; }
 
 // Nearest hit per ray (eq. t_j*) plus ambiguity flags.  o, d: float32 [n][3].
+// Accepted hits: t > 0 and min_range <= t <= max_range.
 // out_t: FP64 range (= max_range on a miss), out_id: triangle id or -1,
 // out_flags: EDGE|TIE|RANGE bits (may be NULL to skip the flag pass).
-void orc_cast(void* h, const float* o, const float* d, int64_t n, double max_range, int nthreads,
-              double* out_t, int32_t* out_id, uint8_t* out_flags) {
+void orc_cast(void* h, const float* o, const float* d, int64_t n, double min_range,
+              double max_range, int nthreads, double* out_t, int32_t* out_id, uint8_t* out_flags) {
   const Scene& s = *static_cast<Scene*>(h);
   parallel_for(n, nthreads, [&](int64_t i) {
     V3 oo = ld3(o, i), dd = ld3(d, i);
     double t;
     int32_t id;
-    nearest(s, oo, dd, max_range, &t, &id);
+    nearest(s, oo, dd, min_range, max_range, &t, &id);
     out_t[i] = t;
     out_id[i] = id;
-    if (out_flags) out_flags[i] = flags_for(s, oo, dd, max_range, t, id);
+    if (out_flags) out_flags[i] = flags_for(s, oo, dd, min_range, max_range, t, id);
   });
 }
 
 // Plausibility of a candidate answer per ray (see validate_one).
-void orc_validate(void* h, const float* o, const float* d, int64_t n, double max_range,
-                  const float* range, const int32_t* id, int nthreads, uint8_t* out_ok) {
+void orc_validate(void* h, const float* o, const float* d, int64_t n, double min_range,
+                  double max_range, const float* range, const int32_t* id, int nthreads,
+                  uint8_t* out_ok) {
   const Scene& s = *static_cast<Scene*>(h);
   parallel_for(n, nthreads, [&](int64_t i) {
-    out_ok[i] = validate_one(s, ld3(o, i), ld3(d, i), max_range, (double)range[i], id[i]) ? 1 : 0;
+    out_ok[i] = validate_one(s, ld3(o, i), ld3(d, i), min_range, max_range, (double)range[i], id[i])
+                    ? 1 : 0;
   });
 }
 

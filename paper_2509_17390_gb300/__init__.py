@@ -50,7 +50,7 @@ class SceneStats(ctypes.Structure):
 
 class CastItem(ctypes.Structure):
     _fields_ = [("scene", P), ("sensor", P), ("poses", P), ("n_env", I32), ("max_range", F32),
-                ("out_range", P), ("out_tri", P)]
+                ("out_range", P), ("out_tri", P), ("min_range", F32)]
 
 
 class BatchOpts(ctypes.Structure):
@@ -282,15 +282,17 @@ def cast_opts(scene: Scene, sensor: Sensor, poses, max_range: float, opts: Batch
 
 
 def make_items(items: Sequence[tuple]):
-    """items: (scene, sensor, poses, max_range, out_range, out_tri) tuples with
-    torch CUDA tensors; returns the ctypes array."""
+    """items: (scene, sensor, poses, max_range, out_range, out_tri[, min_range])
+    tuples with torch CUDA tensors; returns the ctypes array."""
     arr = (CastItem * max(1, len(items)))()
-    for i, (sc, se, poses, rmax, orng, otri) in enumerate(items):
+    for i, item in enumerate(items):
+        sc, se, poses, rmax, orng, otri = item[:6]
+        rmin = float(item[6]) if len(item) > 6 else 0.0
         n_env = poses.shape[0] if poses.dim() == 3 else poses.numel() // 12
         n = n_env * se.n_rays
         arr[i] = CastItem(sc.handle, se.handle, _dev_ptr(poses, "float32", n_env * 12, "poses"),
                           n_env, float(rmax), _dev_ptr(orng, "float32", n, "out_range"),
-                          _dev_ptr(otri, "int32", n, "out_tri"))
+                          _dev_ptr(otri, "int32", n, "out_tri"), rmin)
     return arr
 
 
@@ -339,10 +341,12 @@ def cast_batched_host(items: Sequence[tuple], opts: Optional[BatchOpts] = None, 
     """End-to-end batched form (fgl_cast_batched_host): poses and outputs are
     host tensors/arrays (page-locked for full speed); blocks until done."""
     arr = (CastItem * max(1, len(items)))()
-    for i, (sc, se, poses, rmax, orng, otri) in enumerate(items):
+    for i, item in enumerate(items):
+        sc, se, poses, rmax, orng, otri = item[:6]
+        rmin = float(item[6]) if len(item) > 6 else 0.0
         n_env = int(np.prod(poses.shape)) // 12
         arr[i] = CastItem(sc.handle, se.handle, _host_ptr(poses), n_env, float(rmax),
-                          _host_ptr(orng), _host_ptr(otri))
+                          _host_ptr(orng), _host_ptr(otri), rmin)
     _check(lib().fgl_cast_batched_host(arr, len(items), ctypes.byref(opts) if opts else None,
                                        _stream_handle(stream)))
 
@@ -394,7 +398,7 @@ class ServerOpts(ctypes.Structure):
 
 class Request(ctypes.Structure):
     _fields_ = [("scene_id", I32), ("sensor_id", I32), ("n_env", I32), ("max_range", F32),
-                ("poses", P), ("out_range", P), ("out_tri", P)]
+                ("poses", P), ("out_range", P), ("out_tri", P), ("min_range", F32)]
 
 
 class RequestInfo(ctypes.Structure):
@@ -432,11 +436,12 @@ class Server:
         self._keep.append(sensor)
         return i.value
 
-    def submit(self, scene_id: int, sensor_id: int, poses, max_range: float, out_range, out_tri) -> int:
+    def submit(self, scene_id: int, sensor_id: int, poses, max_range: float, out_range, out_tri,
+               min_range: float = 0.0) -> int:
         """poses: host float32 [n_env,3,4]; outputs: host arrays/tensors."""
         n_env = int(np.prod(poses.shape)) // 12
         r = Request(scene_id, sensor_id, n_env, float(max_range), _host_ptr(poses),
-                    _host_ptr(out_range), _host_ptr(out_tri))
+                    _host_ptr(out_range), _host_ptr(out_tri), float(min_range))
         t = I64()
         _check(lib().fgl_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
         return t.value

@@ -122,6 +122,8 @@ fgl_status check_item(const fgl_cast_item& it, int idx) {
   if (it.n_env < 0) return fail(FGL_ERR_INVALID, w + "n_env < 0");
   if (!(std::isfinite(it.max_range) && it.max_range > 0.f))
     return fail(FGL_ERR_INVALID, w + "max_range must be finite and > 0");
+  if (!(it.min_range >= 0.f && it.min_range < it.max_range))
+    return fail(FGL_ERR_INVALID, w + "min_range must satisfy 0 <= min_range < max_range");
   if (it.n_env > 0 && (!it.poses || !it.out_range || !it.out_tri))
     return fail(FGL_ERR_INVALID, w + "null poses or output pointer");
   if (!it.scene->d_nodes) return fail(FGL_ERR_INVALID, w + "scene is not resident on the device");
@@ -143,6 +145,7 @@ ItemDesc make_desc(const fgl_cast_item& it) {
   d.n_rays = it.sensor->n_rays;
   d.max_range = it.max_range;
   d.width = it.scene->bvh.width;
+  d.min_range = it.min_range;
   return d;
 }
 
@@ -357,6 +360,8 @@ const char* static_item_desc(const fgl_cast_item& it, ItemDesc* d, int* width) {
   if (it.n_env < 0) return "n_env < 0 in an item";
   if (!(std::isfinite(it.max_range) && it.max_range > 0.f))
     return "max_range must be finite and > 0";
+  if (!(it.min_range >= 0.f && it.min_range < it.max_range))
+    return "min_range must satisfy 0 <= min_range < max_range";
   if (it.n_env > 0 && (!it.poses || !it.out_range || !it.out_tri))
     return "null poses or output pointer in an item";
   if (!it.scene->d_nodes) return "scene is not resident on the device";

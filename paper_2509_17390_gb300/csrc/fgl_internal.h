@@ -107,7 +107,7 @@ struct alignas(16) ItemDesc {
   int32_t pk_per_env;    // packets per environment
   float max_range;
   int32_t width;         // BVH width of `nodes`; a kernel for another width skips the item
-  int32_t pad;
+  float min_range;       // t_min: hits nearer than this are discarded
 };
 static_assert(sizeof(ItemDesc) == 80, "ItemDesc layout");
 

@@ -88,7 +88,7 @@ __global__ void __maxnreg__(72) k_plain(const ItemDesc it, int sdepth, int tri_m
     float ox, oy, oz, dx, dy, dz;
     dev::world_ray(it.poses + 12 * (int64_t)env, ds, ox, oy, oz, dx, dy, dz);
     dev::setup_ray(tr.r, ox, oy, oz, dx, dy, dz);
-    tr.start(it.nodes, it.tris, it.max_range);
+    tr.start(it.nodes, it.tris, it.min_range, it.max_range);
   }
   uint2 ls[kStackLocal];
   Keys lq[kStackLocal];
@@ -195,7 +195,7 @@ __global__ void __maxnreg__(72) k_persistent(BatchHeader* __restrict__ hdr,
             c_nodes += tr.n_nodes;
             c_tris += tr.n_tris;
           }
-          tr.start(it.nodes, it.tris, it.max_range);
+          tr.start(it.nodes, it.tris, it.min_range, it.max_range);
           const int64_t o = (int64_t)pk_env * it.n_rays + __float_as_int(ds.w);
           out_r = it.out_range + o;
           out_t = it.out_tri + o;

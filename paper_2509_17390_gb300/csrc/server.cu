@@ -297,6 +297,7 @@ void worker_main(fgl_server_s* Sp) {
         it.poses = q.d_poses + (size_t)q.env_next * 12;
         it.n_env = chunk;
         it.max_range = q.r.max_range;
+        it.min_range = q.r.min_range;
         it.out_range = q.d_range + (size_t)q.env_next * q.n_rays;
         it.out_tri = q.d_tri + (size_t)q.env_next * q.n_rays;
         items.push_back(it);
@@ -317,6 +318,7 @@ void worker_main(fgl_server_s* Sp) {
           it.poses = q.d_poses + (size_t)e * 12;
           it.n_env = 1;
           it.max_range = q.r.max_range;
+          it.min_range = q.r.min_range;
           it.out_range = q.d_range + (size_t)e * q.n_rays;
           it.out_tri = q.d_tri + (size_t)e * q.n_rays;
           items.push_back(it);
@@ -350,8 +352,10 @@ void worker_main(fgl_server_s* Sp) {
       status = fgl_cast_batched(items.data(), (int32_t)items.size(), &S.o.opts, S.compute);
     } else {
       for (const fgl_cast_item& it : items) {
-        status = fgl_cast(it.scene, it.sensor, it.poses, 1, it.max_range, it.out_range, it.out_tri,
-                          S.compute);
+        status = it.min_range > 0.f
+                     ? fgl_cast_batched(&it, 1, &S.o.opts, S.compute)
+                     : fgl_cast(it.scene, it.sensor, it.poses, 1, it.max_range, it.out_range,
+                                it.out_tri, S.compute);
         if (status != FGL_OK) break;
       }
     }
@@ -499,6 +503,8 @@ fgl_status fgl_server_submit(fgl_server S, const fgl_request* r, int64_t* ticket
     if (!r->poses || !r->out_range || !r->out_tri) return set_err(FGL_ERR_INVALID, "null buffer");
     if (!(std::isfinite(r->max_range) && r->max_range > 0.f))
       return set_err(FGL_ERR_INVALID, "max_range must be finite and > 0");
+    if (!(r->min_range >= 0.f && r->min_range < r->max_range))
+      return set_err(FGL_ERR_INVALID, "min_range must satisfy 0 <= min_range < max_range");
     q->bytes = request_bytes(r->n_env, q->n_rays);
     if (q->bytes + S->scenes[r->scene_id].bytes > S->o.hbm_budget_bytes) {
       ++S->rejected;

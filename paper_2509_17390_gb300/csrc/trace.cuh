@@ -201,7 +201,7 @@ constexpr uint32_t kGroupPending = 0x80000000u;
 // the hit internal children.
 template <int W>
 __device__ __forceinline__ void intersect_node(const Ray& r, const uint4* __restrict__ nd,
-                                               float tmax, uint2& ng, uint2& tg,
+                                               float tmin, float tmax, uint2& ng, uint2& tg,
                                                typename KeyWords<W>::T& kq) {
   const uint4 h0 = ldg4(nd), h1 = ldg4(nd + 1);
   uint32_t lox[2], loy[2], loz[2], hix[2], hiy[2], hiz[2], hb[W];
@@ -243,7 +243,7 @@ __device__ __forceinline__ void intersect_node(const Ray& r, const uint4* __rest
     unpack2f(ffma2(pack2f(byte_magic(nxw, s), byte_magic(fxw, s)), S2x, B2x), tnx, tfx);
     unpack2f(ffma2(pack2f(byte_magic(nyw, s), byte_magic(fyw, s)), S2y, B2y), tny, tfy);
     unpack2f(ffma2(pack2f(byte_magic(nzw, s), byte_magic(fzw, s)), S2z, B2z), tnz, tfz);
-    const float tn = max3f(tnx, tny, fmaxf(tnz, 0.f));
+    const float tn = max3f(tnx, tny, fmaxf(tnz, tmin));
     const float tf = min3f(tfx, tfy, fminf(tfz, tmax));
     tn_all[i] = tn;
     if (tn <= tf) hits |= hb[i];
@@ -292,6 +292,7 @@ template <int W, bool COUNT>
 struct Tracer {
   using Keys = typename KeyWords<W>::T;
   Ray r;
+  float tmin;      // t_min of eq. t_j*: hits nearer than this are discarded
   float best_t;
   int32_t best_id;
   uint2 ng, tg;
@@ -301,9 +302,11 @@ struct Tracer {
   const float4* __restrict__ tris;
   uint32_t n_nodes, n_tris;
 
-  __device__ __forceinline__ void start(const void* node_ptr, const void* tri_ptr, float max_range) {
+  __device__ __forceinline__ void start(const void* node_ptr, const void* tri_ptr, float min_range,
+                                        float max_range) {
     nodes = (const uint4*)node_ptr;
     tris = (const float4*)tri_ptr;
+    tmin = min_range;
     best_t = max_range;
     best_id = kNoHit;
     // root group: one internal child in slot 0 (the root node), entry 0
@@ -358,7 +361,7 @@ struct Tracer {
       if (key_any(kq)) {
         if (!push(ng, kq, st)) return false;
       }
-      intersect_node<W>(r, nodes + (size_t)child * (node_stride(W) / 16), best_t, ng, tg, kq);
+      intersect_node<W>(r, nodes + (size_t)child * (node_stride(W) / 16), tmin, best_t, ng, tg, kq);
       if (COUNT) ++n_nodes;
     } else {
       tg = ng;
@@ -368,7 +371,7 @@ struct Tracer {
   }
 
   __device__ __forceinline__ void consider(float t, int32_t id) {
-    if (t > 0.f && (t < best_t || (t == best_t && id < best_id))) {
+    if (t > 0.f && t >= tmin && (t < best_t || (t == best_t && id < best_id))) {
       best_t = t;
       best_id = id;
     }
@@ -500,6 +503,7 @@ __device__ __forceinline__ void tri_phase_warp(Tracer<W, COUNT>& tr, unsigned lo
     q.Sz = __shfl_sync(FULL, tr.r.Sz, owner);
     q.k = __shfl_sync(FULL, tr.r.k, owner);
     const float o_best = __shfl_sync(FULL, tr.best_t, owner);
+    const float o_tmin = __shfl_sync(FULL, tr.tmin, owner);
     if (p < total) {
       const uint32_t k = (uint32_t)(p - (o_incl - o_cnt));
       const uint32_t pos = nth_set_bit(o_bits, k);
@@ -507,7 +511,7 @@ __device__ __forceinline__ void tri_phase_warp(Tracer<W, COUNT>& tr, unsigned lo
       const float4 a = ldg4f(tp), bb = ldg4f(tp + 1), c = ldg4f(tp + 2);
       if (COUNT) ++tr.n_tris;
       const float t = tri_hit(q, a, bb, c, o_best);
-      if (t > 0.f) atomicMin(&keys[owner], hit_key(t, __float_as_int(a.w)));
+      if (t > 0.f && t >= o_tmin) atomicMin(&keys[owner], hit_key(t, __float_as_int(a.w)));
     }
   }
   __syncwarp();

@@ -5,17 +5,18 @@ import numpy as np
 import oracle
 
 
-def parity_report(osc: "oracle.Scene", o, d, max_range, gpu_range, gpu_id):
+def parity_report(osc: "oracle.Scene", o, d, max_range, gpu_range, gpu_id, min_range=0.0):
     """Compare GPU (range, id) per ray with the oracle under the tolerance
     contract; flagged rays must still pass the oracle's plausibility check."""
     gr = np.asarray(gpu_range, np.float32)
     gi = np.asarray(gpu_id, np.int32)
-    r_o, i_o, fl = osc.cast(o, d, max_range)
+    r_o, i_o, fl = osc.cast(o, d, max_range, min_range=min_range)
     bad, checked = oracle.compare(gr, gi, r_o, i_o, fl, max_range)
     flagged = fl != 0
     invalid = 0
     if flagged.any():
-        ok = osc.validate(o[flagged], d[flagged], max_range, gr[flagged], gi[flagged])
+        ok = osc.validate(o[flagged], d[flagged], max_range, gr[flagged], gi[flagged],
+                          min_range=min_range)
         invalid = int((~ok).sum())
     return {
         "n": len(gr),

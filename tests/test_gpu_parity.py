@@ -57,14 +57,15 @@ def run_plain(scene, sensor, P, max_range, opts=None):
 
 
 def run_batched(items_np, opts=None, stream=None):
-    """items_np: (scene, sensor, poses np, max_range)."""
+    """items_np: (scene, sensor, poses np, max_range[, min_range])."""
     items, outs = [], []
-    for sc, se, P, R in items_np:
+    for it in items_np:
+        sc, se, P, R = it[:4]
         poses = torch.from_numpy(np.ascontiguousarray(P, np.float32)).cuda()
         n = P.shape[0] * se.n_rays
         r = torch.full((n,), -7.0, dtype=torch.float32, device="cuda")
         i = torch.full((n,), -7, dtype=torch.int32, device="cuda")
-        items.append((sc, se, poses, R, r, i))
+        items.append((sc, se, poses, R, r, i) + tuple(it[4:]))
         outs.append((r, i))
     fgl.cast_batched(items, opts, stream=stream)
     fgl.sync(stream)
@@ -132,6 +133,28 @@ def test_indoor_random_poses_and_short_range(indoor, indoor_scenes, indoor_oracl
         assert_parity(rep)
         if R < 1:
             assert rep["hits"] < rep["n"]
+
+
+@pytest.mark.parametrize("width", [8, 4])
+def test_min_range_vs_oracle(indoor, indoor_scenes, indoor_oracle, width):
+    """t_min of eq. t_j*: nearer surfaces are passed through (the two-sided
+    test then returns the back of a thin object or the next surface)."""
+    w = indoor
+    P = synth.sample_free_pose(np.random.default_rng(41), w.obstacles, 6, upright=False)
+    tab = synth.grid_sensor(16, -15, 15, 360)
+    se = fgl.Sensor.from_table(tab)
+    o, d = oracle.world_rays(oracle.sensor_dirs(tab.elev, tab.azim), P)
+    mins = (0.4, 1.5, 4.0)
+    outs = run_batched([(indoor_scenes[width], se, P, 120.0, m) for m in mins])
+    plain, _ = run_plain(indoor_scenes[width], se, P, 120.0)
+    for m, (gr, gi) in zip(mins, outs):
+        rep = parity_report(indoor_oracle, o, d, 120.0, gr, gi, min_range=m)
+        assert_parity(rep)
+        assert np.all(gr[gi >= 0] >= np.float32(m))
+        assert np.any(gr > plain)                  # some nearer surfaces were skipped
+    # one item alone gives the same bits as inside the mixed batch
+    (gr1, gi1), = run_batched([(indoor_scenes[width], se, P, 120.0, mins[1])])
+    assert np.array_equal(gr1, outs[1][0]) and np.array_equal(gi1, outs[1][1])
 
 
 # ---------------------------------------------------------------------------

@@ -22,7 +22,7 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 # ---------------------------------------------------------------------------
 # independent brute force: Moller & Trumbore (1997), FP64, vectorised numpy
 # ---------------------------------------------------------------------------
-def mt_nearest(verts, tris, o, d, max_range):
+def mt_nearest(verts, tris, o, d, max_range, min_range=0.0):
     v = verts.astype(np.float64)[tris.astype(np.int64)]          # [nt,3,3]
     o = o.astype(np.float64)
     d = d.astype(np.float64)
@@ -40,7 +40,7 @@ def mt_nearest(verts, tris, o, d, max_range):
         q = np.cross(s, e1)
         w = np.einsum("j,ij->i", d[i], q) * inv
         t = np.einsum("ij,ij->i", e2, q) * inv
-        hit = ok & (u >= 0) & (w >= 0) & (u + w <= 1) & (t > 0) & (t <= max_range)
+        hit = ok & (u >= 0) & (w >= 0) & (u + w <= 1) & (t > 0) & (t >= min_range) & (t <= max_range)
         if hit.any():
             tt = np.where(hit, t, np.inf)
             m = tt.min()
@@ -204,6 +204,69 @@ def test_bvh_bit_identical_to_brute_force(seed):
     b = oracle.Scene(v, t, bvh=True).cast(o, d, 25.0)
     for x, y in zip(a, b):
         assert np.array_equal(x, y)
+
+
+# ---------------------------------------------------------------------------
+# minimum range t_min (eq. t_j*: intersections outside [t_min, t_max] are
+# discarded; a surface nearer than t_min is passed through)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("bvh", [False, True])
+def test_min_range_closed_form_box(bvh):
+    """Rays along +x from x = -1 through the closed box [0,1]^3: entry face at
+    t = 1, exit face at t = 2.  t_min <= 1 returns the entry face (t_min = 1
+    inclusive), 1 < t_min <= 2 the exit face, t_min > 2 a miss."""
+    v, t = synth.aabb_box((0.0, 0.0, 0.0), (1.0, 1.0, 1.0), 2)
+    sc = oracle.Scene(v, t, bvh=bvh)
+    rng = np.random.default_rng(5)
+    yz = rng.uniform(0.05, 0.95, (200, 2))
+    o = np.concatenate([np.full((200, 1), -1.0), yz], 1).astype(np.float32)
+    d = np.tile(np.array([[1.0, 0.0, 0.0]], np.float32), (200, 1))
+    for tmin, want, plane in ((0.0, 1.0, 0.0), (0.5, 1.0, 0.0), (1.0, 1.0, 0.0), (1.5, 2.0, 1.0),
+                              (2.0, 2.0, 1.0), (2.5, None, None)):
+        r, ids, fl = sc.cast(o, d, 10.0, min_range=tmin)
+        if want is None:
+            assert np.all(ids == -1) and np.all(r == 10.0)
+            continue
+        assert np.all(r == want), tmin
+        assert np.all(v[t[ids]][:, :, 0] == plane), tmin               # the hit lies on that face
+        if tmin == want:
+            assert np.all(fl & oracle.FLAG_RANGE)                      # hit exactly at t_min
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_min_range_bvh_equals_brute_force_and_moller_trumbore(seed):
+    rng = np.random.default_rng(300 + seed)
+    v, t = random_soup(rng, 600, size_lo=0.05, size_hi=1.5)
+    o, d = random_rays(rng, 500)
+    for tmin in (0.0, 0.7, 3.0):
+        a = oracle.Scene(v, t, bvh=False).cast(o, d, 25.0, min_range=tmin)
+        b = oracle.Scene(v, t, bvh=True).cast(o, d, 25.0, min_range=tmin)
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+        r, ids, fl = a
+        mr, mi = mt_nearest(v, t, o, d, 25.0, min_range=tmin)
+        unflagged = fl == 0
+        assert np.array_equal(ids[unflagged], mi[unflagged]), tmin
+        np.testing.assert_allclose(r[unflagged], mr[unflagged], rtol=1e-9, atol=1e-12)
+        if tmin > 0:
+            assert np.all(r[ids >= 0] >= tmin)
+            # without t_min the same rays return something at least as near
+            r0, i0, _ = oracle.Scene(v, t, bvh=True).cast(o, d, 25.0)
+            assert np.all(r0 <= r)
+
+
+def test_min_range_validator():
+    """The plausibility check honours t_min: the exit face is a valid answer
+    for t_min between the faces, the entry face is not."""
+    v, t = synth.aabb_box((0.0, 0.0, 0.0), (1.0, 1.0, 1.0), 1)
+    sc = oracle.Scene(v, t)
+    o = np.array([[-1.0, 0.3, 0.6]], np.float32)
+    d = np.array([[1.0, 0.0, 0.0]], np.float32)
+    r, ids, _ = sc.cast(o, d, 10.0, min_range=1.5)
+    r0, i0, _ = sc.cast(o, d, 10.0)
+    assert sc.validate(o, d, 10.0, r.astype(np.float32), ids, min_range=1.5)[0]
+    assert not sc.validate(o, d, 10.0, r0.astype(np.float32), i0, min_range=1.5)[0]
+    assert not sc.validate(o, d, 10.0, r.astype(np.float32), ids)[0]        # skipped the entry face
 
 
 def test_bvh_bit_identical_on_tiny_room_workload():
