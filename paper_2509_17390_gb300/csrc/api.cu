@@ -186,6 +186,7 @@ BatchCtx* get_ctx(cudaStream_t s) {
 
 struct Group {
   int W;
+  bool tmin = false;  // some item has min_range > 0
   std::vector<ItemDesc> items;
   int64_t n_packets = 0;
 };
@@ -205,6 +206,7 @@ void build_table(const fgl_cast_item* items, int n, int P, std::vector<Group>& g
       d.pk_per_env = (d.n_rays + P - 1) / P;
       d.pk_begin = g.n_packets;
       g.n_packets += (int64_t)d.pk_per_env * d.n_env;
+      g.tmin = g.tmin || d.min_range > 0.f;
       g.items.push_back(d);
     }
     if (!g.items.empty()) groups.push_back(std::move(g));
@@ -230,11 +232,11 @@ struct LaunchCfg {
   int grid = 0;
 };
 
-fgl_status grid_for(int W, const Opts& o, int* grid) {
+fgl_status grid_for(int W, bool tmin, const Opts& o, int* grid) {
   DeviceInfo di;
   fgl_status s = device_info(&di);
   if (s != FGL_OK) return s;
-  int bpsm = o.bpsm ? o.bpsm : persistent_blocks_per_sm(W, o.count != 0, o.block, o.sdepth);
+  int bpsm = o.bpsm ? o.bpsm : persistent_blocks_per_sm(W, o.count != 0, tmin, o.block, o.sdepth);
   *grid = std::max(1, di.sm_count * bpsm);
   return FGL_OK;
 }
@@ -247,9 +249,10 @@ fgl_status enqueue_batch(BatchCtx& c, const std::vector<Group>& groups,
   FGL_CUDA(cudaMemcpyAsync(c.d_scratch, c.h_staging, c.table_bytes, cudaMemcpyHostToDevice, s));
   for (size_t g = 0; g < groups.size(); ++g) {
     int grid = 0;
-    fgl_status st = grid_for(groups[g].W, o, &grid);
+    fgl_status st = grid_for(groups[g].W, groups[g].tmin, o, &grid);
     if (st != FGL_OK) return st;
-    FGL_CUDA(launch_persistent(groups[g].W, o.count != 0, (char*)c.d_scratch + offsets[g], grid,
+    FGL_CUDA(launch_persistent(groups[g].W, o.count != 0, groups[g].tmin,
+                               (char*)c.d_scratch + offsets[g], grid,
                                o.block, o.sdepth, o.refill, o.tri_mode, o.postpone, s));
   }
   return FGL_OK;
@@ -266,7 +269,7 @@ fgl_status run_batched(const fgl_cast_item* items, int n, const Opts& o, cudaStr
   // warm the occupancy query (sets kernel attributes) outside any capture
   for (const Group& g : groups) {
     int grid;
-    fgl_status st = grid_for(g.W, o, &grid);
+    fgl_status st = grid_for(g.W, g.tmin, o, &grid);
     if (st != FGL_OK) return st;
   }
   if (!c.staged) FGL_CUDA(cudaEventCreateWithFlags(&c.staged, cudaEventDisableTiming));

@@ -124,7 +124,7 @@ __global__ void __maxnreg__(72) k_plain(const ItemDesc it, int sdepth, int tri_m
   if (COUNT) flush_counters<COUNT>(gid < total ? 1u : 0u, tr.n_nodes, tr.n_tris);
 }
 
-template <int W, bool COUNT>
+template <int W, bool COUNT, bool TMIN>
 __global__ void __maxnreg__(72) k_persistent(BatchHeader* __restrict__ hdr,
                                                     const ItemDesc* __restrict__ items, int sdepth,
                                                     int refill_min, int tri_mode, int postpone_pct) {
@@ -143,7 +143,7 @@ __global__ void __maxnreg__(72) k_persistent(BatchHeader* __restrict__ hdr,
   int pk_item = 0, pk_env = 0, pk_next = 0, pk_end = 0;
   bool drained = false;
   // lane state
-  dev::Tracer<W, COUNT> tr;
+  dev::Tracer<W, COUNT, TMIN> tr;
   tr.tg = make_uint2(0u, 0u);
   tr.ng = make_uint2(0u, 0u);
   if (COUNT) tr.n_nodes = tr.n_tris = 0;
@@ -264,18 +264,22 @@ template <int W, bool COUNT>
 void* plain_fn() {
   return (void*)k_plain<W, COUNT>;
 }
-template <int W, bool COUNT>
+template <int W, bool COUNT, bool TMIN>
 void* persistent_fn() {
-  return (void*)k_persistent<W, COUNT>;
+  return (void*)k_persistent<W, COUNT, TMIN>;
 }
 
 void* pick_plain(int W, bool count) {
   if (W == 8) return count ? plain_fn<8, true>() : plain_fn<8, false>();
   return count ? plain_fn<4, true>() : plain_fn<4, false>();
 }
-void* pick_persistent(int W, bool count) {
-  if (W == 8) return count ? persistent_fn<8, true>() : persistent_fn<8, false>();
-  return count ? persistent_fn<4, true>() : persistent_fn<4, false>();
+template <int W>
+void* pick_persistent_w(bool count, bool tmin) {
+  if (tmin) return count ? persistent_fn<W, true, true>() : persistent_fn<W, false, true>();
+  return count ? persistent_fn<W, true, false>() : persistent_fn<W, false, false>();
+}
+void* pick_persistent(int W, bool count, bool tmin) {
+  return W == 8 ? pick_persistent_w<8>(count, tmin) : pick_persistent_w<4>(count, tmin);
 }
 
 }  // namespace
@@ -301,8 +305,8 @@ cudaError_t launch_plain(int W, bool count, const ItemDesc& it, int block, int s
   return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(block), args, smem, s);
 }
 
-int persistent_blocks_per_sm(int W, bool count, int block, int sdepth) {
-  void* fn = pick_persistent(W, count);
+int persistent_blocks_per_sm(int W, bool count, bool tmin, int block, int sdepth) {
+  void* fn = pick_persistent(W, count, tmin);
   const size_t smem = stack_smem_bytes(W, block, sdepth);
   if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int n = 0;
@@ -310,9 +314,10 @@ int persistent_blocks_per_sm(int W, bool count, int block, int sdepth) {
   return n > 0 ? n : 1;
 }
 
-cudaError_t launch_persistent(int W, bool count, void* scratch, int grid, int block, int sdepth,
-                              int refill_min, int tri_mode, int postpone_pct, cudaStream_t s) {
-  void* fn = pick_persistent(W, count);
+cudaError_t launch_persistent(int W, bool count, bool tmin, void* scratch, int grid, int block,
+                              int sdepth, int refill_min, int tri_mode, int postpone_pct,
+                              cudaStream_t s) {
+  void* fn = pick_persistent(W, count, tmin);
   const size_t smem = stack_smem_bytes(W, block, sdepth);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -17,12 +17,15 @@ cudaError_t launch_plain(int W, bool count, const ItemDesc& it, int block, int s
                          int tri_mode, int postpone_pct, cudaStream_t s);
 
 // Resident blocks per SM of the persistent kernel for this configuration.
-int persistent_blocks_per_sm(int W, bool count, int block, int sdepth);
+int persistent_blocks_per_sm(int W, bool count, bool tmin, int block, int sdepth);
 
 // Persistent kernel over the work queue in `scratch`: a BatchHeader
-// followed by n_items ItemDesc records (device memory).
-cudaError_t launch_persistent(int W, bool count, void* scratch, int grid, int block, int sdepth,
-                              int refill_min, int tri_mode, int postpone_pct, cudaStream_t s);
+// followed by n_items ItemDesc records (device memory).  tmin selects the
+// instantiation that honours ItemDesc::min_range (needed when any item of
+// the group has min_range > 0; otherwise min_range is taken as 0).
+cudaError_t launch_persistent(int W, bool count, bool tmin, void* scratch, int grid, int block,
+                              int sdepth, int refill_min, int tri_mode, int postpone_pct,
+                              cudaStream_t s);
 
 // Debug export of world rays (beam order).
 cudaError_t launch_world_rays(const void* dirs, const float* poses, int n_env, int n_rays,

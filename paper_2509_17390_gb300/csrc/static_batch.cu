@@ -130,6 +130,7 @@ extern "C" fgl_status fgl_cast_batched_static(const fgl_cast_item* items, int32_
   img.n_words = 0;
   size_t group_off[kMaxGroups] = {0, 0};
   int group_w[kMaxGroups] = {0, 0};
+  bool group_tmin[kMaxGroups] = {false, false};
   int n_groups = 0;
   size_t used = 0;
   for (int W : {8, 4}) {
@@ -139,6 +140,7 @@ extern "C" fgl_status fgl_cast_batched_static(const fgl_cast_item* items, int32_
     size_t off = used + sizeof(BatchHeader);
     int n_in = 0;
     int64_t packets = 0;
+    bool tmin = false;
     for (int i = 0; i < n_items; ++i) {
       ItemDesc d;
       int width = 0;
@@ -148,6 +150,7 @@ extern "C" fgl_status fgl_cast_batched_static(const fgl_cast_item* items, int32_
       d.pk_per_env = (d.n_rays + packet - 1) / packet;
       d.pk_begin = packets;
       packets += (int64_t)d.pk_per_env * d.n_env;
+      tmin = tmin || d.min_range > 0.f;
       std::memcpy((char*)img.words + off, &d, sizeof(d));
       off += sizeof(d);
       ++n_in;
@@ -160,6 +163,7 @@ extern "C" fgl_status fgl_cast_batched_static(const fgl_cast_item* items, int32_
     std::memcpy((char*)img.words + hdr_off, &h, sizeof(h));
     group_off[n_groups] = hdr_off;
     group_w[n_groups] = W;
+    group_tmin[n_groups] = tmin;
     ++n_groups;
     used = off;
   }
@@ -182,9 +186,10 @@ extern "C" fgl_status fgl_cast_batched_static(const fgl_cast_item* items, int32_
   k_static_table<<<1, 256, 0, s>>>(img, (uint4*)scratch);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_err(e);
   for (int g = 0; g < n_groups; ++g) {
-    const int per_sm = bpsm ? bpsm : persistent_blocks_per_sm(group_w[g], count != 0, block, sdepth);
+    const int per_sm =
+        bpsm ? bpsm : persistent_blocks_per_sm(group_w[g], count != 0, group_tmin[g], block, sdepth);
     const int grid = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
-    e = launch_persistent(group_w[g], count != 0, (char*)scratch + group_off[g], grid, block,
+    e = launch_persistent(group_w[g], count != 0, group_tmin[g], (char*)scratch + group_off[g], grid, block,
                           sdepth, refill, tri_mode, postpone, s);
     if (e != cudaSuccess) return cuda_err(e);
   }

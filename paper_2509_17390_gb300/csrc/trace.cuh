@@ -288,11 +288,14 @@ struct StackRefs {
   int sdepth;
 };
 
-template <int W, bool COUNT>
+// TMIN: the rays may have a minimum range t_min > 0 (eq. t_j*: hits nearer
+// than it are discarded); without it t_min is the constant 0 and costs no
+// register.
+template <int W, bool COUNT, bool TMIN = false>
 struct Tracer {
   using Keys = typename KeyWords<W>::T;
   Ray r;
-  float tmin;      // t_min of eq. t_j*: hits nearer than this are discarded
+  float tmin_;     // t_min (used when TMIN)
   float best_t;
   int32_t best_id;
   uint2 ng, tg;
@@ -306,7 +309,7 @@ struct Tracer {
                                         float max_range) {
     nodes = (const uint4*)node_ptr;
     tris = (const float4*)tri_ptr;
-    tmin = min_range;
+    tmin_ = TMIN ? min_range : 0.f;
     best_t = max_range;
     best_id = kNoHit;
     // root group: one internal child in slot 0 (the root node), entry 0
@@ -318,6 +321,8 @@ struct Tracer {
     sp = 0;
     if (COUNT) n_nodes = n_tris = 0;
   }
+
+  __device__ __forceinline__ float tmin() const { return TMIN ? tmin_ : 0.f; }
 
   __device__ __forceinline__ bool push(uint2 v, const Keys& q, const StackRefs<Keys>& st) {
     if (sp < st.sdepth) {
@@ -361,7 +366,7 @@ struct Tracer {
       if (key_any(kq)) {
         if (!push(ng, kq, st)) return false;
       }
-      intersect_node<W>(r, nodes + (size_t)child * (node_stride(W) / 16), tmin, best_t, ng, tg, kq);
+      intersect_node<W>(r, nodes + (size_t)child * (node_stride(W) / 16), tmin(), best_t, ng, tg, kq);
       if (COUNT) ++n_nodes;
     } else {
       tg = ng;
@@ -371,7 +376,7 @@ struct Tracer {
   }
 
   __device__ __forceinline__ void consider(float t, int32_t id) {
-    if (t > 0.f && t >= tmin && (t < best_t || (t == best_t && id < best_id))) {
+    if (t > 0.f && t >= tmin() && (t < best_t || (t == best_t && id < best_id))) {
       best_t = t;
       best_id = id;
     }
@@ -462,8 +467,8 @@ __device__ __forceinline__ unsigned long long hit_key(float t, int32_t id) {
 // shared-memory key -- the same lexicographic minimum as the lane-serial
 // path.  All 32 lanes of the warp must call this together; lanes without a
 // ray simply have no triangles.  `keys` points at the warp's 32 slots.
-template <int W, bool COUNT>
-__device__ __forceinline__ void tri_phase_warp(Tracer<W, COUNT>& tr, unsigned long long* keys,
+template <int W, bool COUNT, bool TMIN>
+__device__ __forceinline__ void tri_phase_warp(Tracer<W, COUNT, TMIN>& tr, unsigned long long* keys,
                                                int lane) {
   const unsigned FULL = 0xFFFFFFFFu;
   const uint32_t bits = tr.tg.y & 0x00FFFFFFu;
@@ -503,7 +508,7 @@ __device__ __forceinline__ void tri_phase_warp(Tracer<W, COUNT>& tr, unsigned lo
     q.Sz = __shfl_sync(FULL, tr.r.Sz, owner);
     q.k = __shfl_sync(FULL, tr.r.k, owner);
     const float o_best = __shfl_sync(FULL, tr.best_t, owner);
-    const float o_tmin = __shfl_sync(FULL, tr.tmin, owner);
+    const float o_tmin = TMIN ? __shfl_sync(FULL, tr.tmin_, owner) : 0.f;
     if (p < total) {
       const uint32_t k = (uint32_t)(p - (o_incl - o_cnt));
       const uint32_t pos = nth_set_bit(o_bits, k);
