@@ -1,11 +1,12 @@
-"""FP64 CPU oracle for first-hit LiDAR ray casting (paper Sec. IV-C).
+"""FP64 CPU oracle for first-hit LiDAR ray casting (paper Sec. IV-C) and for
+the Gaussian-to-occupancy conversion (Sec. IV-A).
 
 TEST INFRASTRUCTURE ONLY: imported by tests/, ``__graft_entry__.smoke()`` and
 the CPU-baseline leg of ``bench.py``; never by the library it checks.  It
 shares no code with ``paper_2509_17390_gb300``.
 
-The C++ source (``oracle.cpp``) is compiled on first use (or by
-``build()``) with ``-ffp-contract=off`` into ``oracle/_build/liboracle.so``.
+The C++ sources (``oracle.cpp``, ``density.cpp``) are compiled on first use
+(or by ``build()``) with ``-ffp-contract=off`` into ``oracle/_build/liboracle.so``.
 """
 
 from __future__ import annotations
@@ -19,6 +20,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.cpp")
+_SRC_DENSITY = os.path.join(_HERE, "density.cpp")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
@@ -30,10 +32,11 @@ FLAG_EDGE, FLAG_TIE, FLAG_RANGE = 1, 2, 4
 def build(force: bool = False) -> str:
     """Compile liboracle.so (g++, FP64, no FMA contraction)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_DENSITY))
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-               "-shared", "-pthread", _SRC, "-o", tmp]
+               "-shared", "-pthread", _SRC, _SRC_DENSITY, "-o", tmp]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -58,6 +61,9 @@ def lib():
             L.orc_validate.argtypes = [P, P, P, I64, D, D, P, P, I32, P]
             L.orc_tri_test.argtypes = [P, P, P, P, P, P]
             L.orc_tri_test.restype = I32
+            L.orc_gauss_tile_ranges.argtypes = [P, P, P, I64, P, ctypes.c_float, I32, P]
+            L.orc_density.argtypes = [P, P, P, P, I64, P, ctypes.c_float, P, I32, I32, P, P]
+            L.orc_occupancy.argtypes = [P, P, D, P, P]
             _lib = L
     return _lib
 
@@ -168,3 +174,54 @@ def compare(range_gpu, id_gpu, range_orc, id_orc, flags, max_range):
     bad |= checked & hit_o & hit_g & (np.abs(rg - ro) > tolr)
     bad |= checked & ~hit_o & ~hit_g & (rg != np.float32(max_range))
     return bad, checked
+
+
+# ---------------------------------------------------------------------------
+# Gaussian-to-occupancy (paper Sec. IV-A)
+# ---------------------------------------------------------------------------
+def _f32(a, cols):
+    return np.ascontiguousarray(a, np.float32).reshape(-1, cols) if cols else np.ascontiguousarray(a, np.float32).reshape(-1)
+
+
+def gauss_tile_ranges(mu, scale, quat, origin, h, B):
+    """Candidate tile ranges [n, 6] (lo xyz, hi xyz; inclusive, unclamped)."""
+    mu, scale, quat = _f32(mu, 3), _f32(scale, 3), _f32(quat, 4)
+    o = np.ascontiguousarray(origin, np.float32)
+    out = np.empty((len(mu), 6), np.int32)
+    lib().orc_gauss_tile_ranges(_ptr(mu), _ptr(scale), _ptr(quat), len(mu), _ptr(o), float(h), int(B),
+                                _ptr(out))
+    return out
+
+
+def density(mu, scale, quat, alpha, origin, h, dims, B, nthreads: int = 0):
+    """Eq. D(v) over the grid (FP64) and A(v) = sum of alpha^2 over the
+    candidates of v's tile; both shaped [nz, ny, nx]."""
+    mu, scale, quat, alpha = _f32(mu, 3), _f32(scale, 3), _f32(quat, 4), _f32(alpha, 0)
+    o = np.ascontiguousarray(origin, np.float32)
+    dm = np.ascontiguousarray(dims, np.int32)
+    nx, ny, nz = (int(x) for x in dims)
+    D = np.empty((nz, ny, nx), np.float64)
+    A = np.empty((nz, ny, nx), np.float64)
+    lib().orc_density(_ptr(mu), _ptr(scale), _ptr(quat), _ptr(alpha), len(mu), _ptr(o), float(h),
+                      _ptr(dm), int(B), int(nthreads), _ptr(D), _ptr(A))
+    return D, A
+
+
+def occupancy(D, theta):
+    """Eqs. V_occ and Surf from a density grid [nz, ny, nx]: (occ u8, surf u8)."""
+    D = np.ascontiguousarray(D, np.float64)
+    nz, ny, nx = D.shape
+    dm = np.array([nx, ny, nz], np.int32)
+    occ = np.empty(D.shape, np.uint8)
+    surf = np.empty(D.shape, np.uint8)
+    lib().orc_occupancy(_ptr(D), _ptr(dm), float(theta), _ptr(occ), _ptr(surf))
+    return occ, surf
+
+
+def density_tolerance(D, A):
+    """Per-voxel tolerance of a float32 implementation of eq. D(v): each term
+    alpha^2 exp(-q/2) carries an error of at most alpha^2 * 3e-5 (float32
+    voxel-to-mean offsets within 5e-7 m at coordinates up to 10 m, scales of
+    at least 1 cm: |dq| <= 1e-4 sqrt(q), and max_q exp(-q/2) sqrt(q)/2 < 0.43,
+    plus the exponential's own error), and the float32 sum adds 1e-6 relative."""
+    return 3e-5 * np.asarray(A) + 1e-6 * np.abs(np.asarray(D)) + 1e-9
