@@ -264,6 +264,65 @@ fgl_status fgl_world_rays(fgl_sensor sensor, const float* poses, int32_t n_env, 
                           float* out_d, fgl_stream stream);
 
 /* ------------------------------------------------------------------------ */
+/* Gaussian-to-occupancy conversion (paper Sec. IV-A)                        */
+/* ------------------------------------------------------------------------ */
+
+/* 3D Gaussians (device pointers; the caller owns them). */
+typedef struct {
+  const float* mu;       /* [n][3] means */
+  const float* scale;    /* [n][3] standard deviations along the Gaussian's own axes */
+  const float* quat;     /* [n][4] rotation (w, x, y, z), any nonzero norm */
+  const float* opacity;  /* [n] alpha */
+  int64_t n;             /* < 2^32 */
+} fgl_gaussians;
+
+/* Isotropic voxel grid: voxel (i, j, k) has centre
+ * origin + ((i + 1/2) h, (j + 1/2) h, (k + 1/2) h) and linear index
+ * (k * dims[1] + j) * dims[0] + i.  Tiles are tile^3 voxels, tile (a, b, c)
+ * holding voxels [a*tile, a*tile + tile) x ... (partial at the far faces). */
+typedef struct {
+  float origin[3];
+  float h;               /* voxel edge, finite and > 0 */
+  int32_t dims[3];       /* >= 1 each */
+  int32_t tile;          /* 4 or 8 (0 = 8) */
+} fgl_grid;
+
+typedef struct {
+  int64_t n_pairs;       /* (Gaussian, tile) candidate pairs */
+  int64_t n_tiles;
+  int64_t n_voxels;
+} fgl_density_stats;
+
+/* Eq. D(v) on the grid, then eqs. V_occ, Int and Surf:
+ *   D(v) = sum over the candidates G of v's tile of
+ *          alpha_G^2 exp(-1/2 (v - mu_G)^T Sigma_G^-1 (v - mu_G)),
+ *   Sigma = R diag(scale^2) R^T, R the rotation of the normalised quaternion;
+ *   V_occ = D > theta; Int = V_occ at the voxel and its 6 face neighbours
+ *   (outside the grid counts as empty); Surf = V_occ and not Int.
+ * Candidates of a tile (eq. C_tile): the Gaussians whose axis-aligned box of
+ * the 3-sigma ellipsoid meets the tile.  That integer decision is taken in
+ * float32 with this exact operation sequence (round to nearest, no FMA):
+ *   n = sqrt(((w*w + x*x) + y*y) + z*z); w, x, y, z /= n;
+ *   R = [[1-2(yy+zz), 2(xy-wz), 2(xz+wy)], [2(xy+wz), 1-2(xx+zz), 2(yz-wx)],
+ *        [2(xz-wy), 2(yz+wx), 1-2(xx+yy)]]   (xx = x*x, wz = w*z, ...);
+ *   var_a = ((R_a0*s0)^2 + (R_a1*s1)^2) + (R_a2*s2)^2;  e_a = 3 * sqrt(var_a);
+ *   cell = float(tile) * h;
+ *   lo_a = floor(((mu_a - e_a) - origin_a) / cell), hi_a likewise with + e_a,
+ *   both clamped to [-2^30, 2^30];
+ * tile (a, b, c) is a candidate iff lo <= (a, b, c) <= hi per axis.  A
+ * Gaussian with a non-finite mean or scale, a scale <= 0 or a zero quaternion
+ * is nobody's candidate.  Each voxel sums its tile's candidates in increasing
+ * Gaussian index (float32; the results are deterministic).
+ *   out_density: device float32 [n_voxels] (required);
+ *   out_occ / out_surf: device uint8 [n_voxels] (0/1), either may be NULL.
+ * The call synchronises `stream` once (to size the pair buffers, cached per
+ * stream); the rest is asynchronous.  Errors: FGL_ERR_INVALID (bad grid,
+ * tile, null pointers, more than 2^31 - 1 pairs), FGL_ERR_CUDA. */
+fgl_status fgl_gaussian_density(const fgl_gaussians* gaussians, const fgl_grid* grid, float theta,
+                                float* out_density, uint8_t* out_occ, uint8_t* out_surf,
+                                fgl_density_stats* stats, fgl_stream stream);
+
+/* ------------------------------------------------------------------------ */
 /* Serving: continuous batching of scan requests                             */
 /* ------------------------------------------------------------------------ */
 /* The paper batches thousands of environments on one GPU (Sec. IV-C; Table

@@ -19,7 +19,8 @@ import numpy as np
 from . import build_native
 
 __all__ = ["Scene", "Sensor", "BatchOpts", "cast", "cast_opts", "cast_batched",
-           "cast_batched_host", "cast_batched_static", "autotune", "TuneOpts", "world_rays", "sync", "work_counters", "FglError", "lib"]
+           "cast_batched_host", "cast_batched_static", "autotune", "TuneOpts", "world_rays", "sync", "work_counters", "FglError", "lib",
+           "gaussian_density", "Gaussians", "Grid"]
 
 FGL_OK, FGL_ERR_INVALID, FGL_ERR_OOM, FGL_ERR_CUDA = 0, 1, 2, 3
 FGL_ERR_BUDGET, FGL_ERR_TIMEOUT, FGL_ERR_CANCELLED, FGL_ERR_DEVICE = 4, 5, 6, 7
@@ -107,6 +108,7 @@ def lib():
                 "fgl_sync": ([P], I32),
                 "fgl_work_counters": ([P, P, P], I32),
                 "fgl_world_rays": ([P, P, I32, P, P, P], I32),
+                "fgl_gaussian_density": ([P, P, F32, P, P, P, P, P], I32),
                 "fgl_last_error": ([], ctypes.c_char_p),
                 "fgl_version": ([], I32),
             }
@@ -379,6 +381,51 @@ def world_rays(sensor: Sensor, poses, stream=None):
 def sync(stream=None):
     """Wait for the stream and surface asynchronous / device-side errors."""
     _check(lib().fgl_sync(_stream_handle(stream)))
+
+
+class Gaussians(ctypes.Structure):
+    _fields_ = [("mu", P), ("scale", P), ("quat", P), ("opacity", P), ("n", I64)]
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("origin", F32 * 3), ("h", F32), ("dims", I32 * 3), ("tile", I32)]
+
+
+class DensityStats(ctypes.Structure):
+    _fields_ = [("n_pairs", I64), ("n_tiles", I64), ("n_voxels", I64)]
+
+
+def gaussian_density(mu, scale, quat, opacity, origin, h: float, dims, theta: float = 0.5,
+                     tile: int = 0, out_density=None, out_occ=None, out_surf=None, stream=None,
+                     masks: bool = True):
+    """Gaussian-to-occupancy conversion (fgl_gaussian_density, paper Sec.
+    IV-A) on torch CUDA tensors: mu/scale [n,3], quat [n,4] (w,x,y,z),
+    opacity [n].  Returns (density [nz,ny,nx] f32, occ u8, surf u8, stats);
+    occ and surf are None when masks=False."""
+    import torch
+    n = int(mu.shape[0]) if mu.dim() > 1 else mu.numel() // 3
+    nx, ny, nz = (int(d) for d in dims)
+    nv = nx * ny * nz
+    dev = mu.device
+    if out_density is None:
+        out_density = torch.empty((nz, ny, nx), dtype=torch.float32, device=dev)
+    if masks and out_occ is None:
+        out_occ = torch.empty((nz, ny, nx), dtype=torch.uint8, device=dev)
+    if masks and out_surf is None:
+        out_surf = torch.empty((nz, ny, nx), dtype=torch.uint8, device=dev)
+    gs = Gaussians(_dev_ptr(mu, "float32", 3 * n, "mu") if n else None,
+                   _dev_ptr(scale, "float32", 3 * n, "scale") if n else None,
+                   _dev_ptr(quat, "float32", 4 * n, "quat") if n else None,
+                   _dev_ptr(opacity, "float32", n, "opacity") if n else None, n)
+    g = Grid((F32 * 3)(*[float(x) for x in origin]), float(h), (I32 * 3)(nx, ny, nz), int(tile))
+    st = DensityStats()
+    _check(lib().fgl_gaussian_density(ctypes.byref(gs), ctypes.byref(g), float(theta),
+                                      _dev_ptr(out_density, "float32", nv, "out_density"),
+                                      _dev_ptr(out_occ, "uint8", nv, "out_occ") if masks else None,
+                                      _dev_ptr(out_surf, "uint8", nv, "out_surf") if masks else None,
+                                      ctypes.byref(st), _stream_handle(stream)))
+    return out_density, out_occ, out_surf, {"n_pairs": st.n_pairs, "n_tiles": st.n_tiles,
+                                            "n_voxels": st.n_voxels}
 
 
 def work_counters():

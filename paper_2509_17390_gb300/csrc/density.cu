@@ -1,0 +1,605 @@
+// Gaussian-to-occupancy conversion (paper Sec. IV-A): eq. D(v) on a voxel
+// grid, restricted per tile to the tile's candidate Gaussians (eq. C_tile),
+// then eqs. V_occ, Int and Surf.
+//
+// Pipeline (all on the caller's stream; one host synchronisation to size the
+// pair buffers):
+//   k_gauss_prep   per Gaussian: validity, the float32 candidate tile range
+//                  (the exact operation sequence of fgl.h), the count of
+//                  covered tiles, and the density parameters (mean, alpha^2,
+//                  the inverse covariance pre-scaled for exp2);
+//   scan           exclusive prefix sum of the counts -> pair offsets;
+//   k_emit         (tile, Gaussian) pairs, in Gaussian order;
+//   radix sort     stable LSD sort of the pairs by tile (8-bit digits), so
+//                  every tile's candidates end up in increasing Gaussian
+//                  index and the float32 sums are deterministic;
+//   k_tile_bounds  begin/end of every tile's candidate run;
+//   k_density<B>   one block per tile: candidates staged in shared memory in
+//                  chunks, each thread accumulates its voxels over them;
+//   k_occ_surf     D > theta and the 6-neighbour surface test.
+//
+// The paper finds the candidates of a tile with an LBVH query over Gaussian
+// AABBs (Karras); binning each Gaussian to the tiles its AABB covers gives
+// the same candidate sets without building or traversing a tree.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "fgl.h"
+#include "fgl_internal.h"
+#include "ptx_ops.cuh"
+
+namespace fgl {
+void record_error(int status, const char* msg);
+}  // namespace fgl
+
+using namespace fgl;
+
+namespace {
+
+constexpr float kHalfLog2e = 0.72134752044448170368f;  // log2(e) / 2
+
+// Density parameters of one Gaussian, 48 bytes:
+//   a = (mu_x, mu_y, mu_z, alpha^2)
+//   b = (M00, M11, M22, M01), c = (M02, M12, valid, 0), M = -(log2 e / 2) * 2^[a!=b] Sigma^-1
+// so that alpha^2 * exp(-q/2) = alpha^2 * exp2(M00 dx^2 + M11 dy^2 + M22 dz^2
+//                                               + M01 dx dy + M02 dx dz + M12 dy dz).
+struct GaussParams {
+  float4 a, b, c;
+};
+
+struct TileRange {
+  int lo[3], hi[3];
+};
+
+// Candidate tile range in float32, the operation sequence of fgl.h (no FMA).
+__device__ __forceinline__ bool tile_range(const float* mu, const float* s, const float* q,
+                                           const float o[3], float cell, int ntiles[3],
+                                           TileRange& t, float R[3][3]) {
+  for (int a = 0; a < 3; ++a)
+    if (!isfinite(mu[a]) || !isfinite(s[a]) || !(s[a] > 0.0f)) return false;
+  float w = q[0], x = q[1], y = q[2], z = q[3];
+  float n2 = __fadd_rn(__fmul_rn(w, w), __fmul_rn(x, x));
+  n2 = __fadd_rn(n2, __fmul_rn(y, y));
+  n2 = __fadd_rn(n2, __fmul_rn(z, z));
+  if (!(n2 > 0.0f) || !isfinite(n2)) return false;
+  const float n = __fsqrt_rn(n2);
+  w = __fdiv_rn(w, n);
+  x = __fdiv_rn(x, n);
+  y = __fdiv_rn(y, n);
+  z = __fdiv_rn(z, n);
+  const float xx = __fmul_rn(x, x), yy = __fmul_rn(y, y), zz = __fmul_rn(z, z);
+  const float xy = __fmul_rn(x, y), xz = __fmul_rn(x, z), yz = __fmul_rn(y, z);
+  const float wx = __fmul_rn(w, x), wy = __fmul_rn(w, y), wz = __fmul_rn(w, z);
+  R[0][0] = __fsub_rn(1.0f, __fmul_rn(2.0f, __fadd_rn(yy, zz)));
+  R[0][1] = __fmul_rn(2.0f, __fsub_rn(xy, wz));
+  R[0][2] = __fmul_rn(2.0f, __fadd_rn(xz, wy));
+  R[1][0] = __fmul_rn(2.0f, __fadd_rn(xy, wz));
+  R[1][1] = __fsub_rn(1.0f, __fmul_rn(2.0f, __fadd_rn(xx, zz)));
+  R[1][2] = __fmul_rn(2.0f, __fsub_rn(yz, wx));
+  R[2][0] = __fmul_rn(2.0f, __fsub_rn(xz, wy));
+  R[2][1] = __fmul_rn(2.0f, __fadd_rn(yz, wx));
+  R[2][2] = __fsub_rn(1.0f, __fmul_rn(2.0f, __fadd_rn(xx, yy)));
+  for (int a = 0; a < 3; ++a) {
+    const float p0 = __fmul_rn(R[a][0], s[0]), p1 = __fmul_rn(R[a][1], s[1]),
+                p2 = __fmul_rn(R[a][2], s[2]);
+    float v = __fadd_rn(__fmul_rn(p0, p0), __fmul_rn(p1, p1));
+    v = __fadd_rn(v, __fmul_rn(p2, p2));
+    const float e = __fmul_rn(3.0f, __fsqrt_rn(v));
+    const float lo = __fsub_rn(__fsub_rn(mu[a], e), o[a]);
+    const float hi = __fsub_rn(__fadd_rn(mu[a], e), o[a]);
+    const float flo = fminf(fmaxf(floorf(__fdiv_rn(lo, cell)), -1073741824.0f), 1073741824.0f);
+    const float fhi = fminf(fmaxf(floorf(__fdiv_rn(hi, cell)), -1073741824.0f), 1073741824.0f);
+    t.lo[a] = max((int)flo, 0);
+    t.hi[a] = min((int)fhi, ntiles[a] - 1);
+    if (t.lo[a] > t.hi[a]) return false;
+  }
+  return true;
+}
+
+struct GridArgs {
+  float o[3];
+  float h;
+  float cell;
+  int dims[3];
+  int ntiles[3];
+};
+
+__global__ void k_gauss_prep(const float* __restrict__ mu, const float* __restrict__ scale,
+                             const float* __restrict__ quat, const float* __restrict__ alpha,
+                             int64_t n, GridArgs g, GaussParams* __restrict__ params,
+                             int4* __restrict__ ranges, unsigned long long* __restrict__ counts) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float m[3], s[3], q[4];
+  for (int a = 0; a < 3; ++a) {
+    m[a] = mu[3 * i + a];
+    s[a] = scale[3 * i + a];
+  }
+  for (int a = 0; a < 4; ++a) q[a] = quat[4 * i + a];
+  TileRange t;
+  float R[3][3];
+  const bool ok = tile_range(m, s, q, g.o, g.cell, g.ntiles, t, R);
+  GaussParams P;
+  P.a = make_float4(m[0], m[1], m[2], 0.f);
+  P.b = make_float4(0.f, 0.f, 0.f, 0.f);
+  P.c = make_float4(0.f, 0.f, 0.f, 0.f);
+  unsigned long long cnt = 0;
+  int4 r0 = make_int4(0, 0, 0, 0), r1 = make_int4(-1, -1, -1, 0);
+  if (ok) {
+    const float al = alpha[i];
+    P.a.w = al * al;
+    // Sigma^-1 = R diag(1/s^2) R^T, times -(log2 e)/2, off-diagonals doubled
+    const float i0 = 1.0f / (s[0] * s[0]), i1 = 1.0f / (s[1] * s[1]), i2 = 1.0f / (s[2] * s[2]);
+    float M[3][3];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b)
+        M[a][b] = R[a][0] * R[b][0] * i0 + R[a][1] * R[b][1] * i1 + R[a][2] * R[b][2] * i2;
+    const float k = -kHalfLog2e;
+    P.b = make_float4(k * M[0][0], k * M[1][1], k * M[2][2], 2.f * k * M[0][1]);
+    P.c = make_float4(2.f * k * M[0][2], 2.f * k * M[1][2], 1.f, 0.f);
+    cnt = (unsigned long long)(t.hi[0] - t.lo[0] + 1) * (t.hi[1] - t.lo[1] + 1) *
+          (t.hi[2] - t.lo[2] + 1);
+    r0 = make_int4(t.lo[0], t.lo[1], t.lo[2], 0);
+    r1 = make_int4(t.hi[0], t.hi[1], t.hi[2], 0);
+  }
+  params[i] = P;
+  ranges[2 * i] = r0;
+  ranges[2 * i + 1] = r1;
+  counts[i] = cnt;
+}
+
+// ---------------------------------------------------------------------------
+// exclusive scan (in place), 2048 items per block, recursive over block sums
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void k_scan_blocks(T* __restrict__ x, int64_t n, T* __restrict__ sums) {
+  __shared__ T warp_tot[32];
+  const int64_t base = (int64_t)blockIdx.x * 2048;
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  const int64_t i0 = base + 2 * t;
+  T a = i0 < n ? x[i0] : T(0);
+  T b = i0 + 1 < n ? x[i0 + 1] : T(0);
+  T v = a + b;  // inclusive warp scan of pair sums
+  T incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T u = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= o) incl += u;
+  }
+  if (lane == 31) warp_tot[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    T w = warp_tot[lane];
+    T wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      T u = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+      if (lane >= o) wi += u;
+    }
+    warp_tot[lane] = wi - w;  // exclusive warp offsets
+    if (lane == 31 && sums) sums[blockIdx.x] = wi;
+  }
+  __syncthreads();
+  const T excl = warp_tot[wid] + incl - v;
+  if (i0 < n) x[i0] = excl;
+  if (i0 + 1 < n) x[i0 + 1] = excl + a;
+}
+
+template <class T>
+__global__ void k_scan_add(T* __restrict__ x, int64_t n, const T* __restrict__ sums) {
+  const int64_t i = (int64_t)blockIdx.x * 2048 + threadIdx.x;
+  const T add = sums[blockIdx.x];
+  if (i < n) x[i] += add;
+  if (i + 1024 < n) x[i + 1024] += add;
+}
+
+// ---------------------------------------------------------------------------
+// pairs, stable radix sort by tile, tile bounds
+// ---------------------------------------------------------------------------
+__global__ void k_emit(const int4* __restrict__ ranges, const unsigned long long* __restrict__ offs,
+                       int64_t n, GridArgs g, uint32_t* __restrict__ keys,
+                       uint32_t* __restrict__ vals) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int4 lo = ranges[2 * i], hi = ranges[2 * i + 1];
+  uint64_t p = offs[i];
+  for (int c = lo.z; c <= hi.z; ++c)
+    for (int b = lo.y; b <= hi.y; ++b)
+      for (int a = lo.x; a <= hi.x; ++a) {
+        keys[p] = (uint32_t)((c * g.ntiles[1] + b) * g.ntiles[0] + a);
+        vals[p] = (uint32_t)i;
+        ++p;
+      }
+}
+
+constexpr int kSortThreads = 256;
+constexpr int kSortRounds = 16;  // items per block = 256 * 16
+
+__global__ void k_radix_hist(const uint32_t* __restrict__ keys, int64_t n, int shift,
+                             uint32_t* __restrict__ hist, int nblocks) {
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * (kSortThreads * kSortRounds);
+  for (int r = 0; r < kSortRounds; ++r) {
+    const int64_t i = base + r * kSortThreads + threadIdx.x;
+    if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+// Stable scatter: within a block, items are ranked in index order (round,
+// then thread); across blocks, the scanned histogram orders them.
+__global__ void k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                int64_t n, int shift, const uint32_t* __restrict__ offs,
+                                int nblocks, uint32_t* __restrict__ kout,
+                                uint32_t* __restrict__ vout) {
+  __shared__ uint32_t base_off[256];
+  __shared__ uint32_t running[256];
+  __shared__ uint32_t wcnt[kSortThreads / 32][256];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  base_off[t] = offs[(int64_t)t * nblocks + blockIdx.x];
+  running[t] = 0;
+  for (int k = 0; k < kSortThreads / 32; ++k) wcnt[k][t] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * (kSortThreads * kSortRounds);
+  const unsigned lt = (1u << lane) - 1u;
+  for (int r = 0; r < kSortRounds; ++r) {
+    const int64_t i = base + r * kSortThreads + t;
+    const bool valid = i < n;
+    uint32_t key = 0, val = 0, d = 256;
+    if (valid) {
+      key = kin[i];
+      val = vin[i];
+      d = (key >> shift) & 255u;
+    }
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
+    const uint32_t rank = __popc(peers & lt);
+    if (valid && rank == 0) wcnt[w][d] = __popc(peers);
+    __syncthreads();
+    if (valid) {
+      uint32_t pre = 0;
+      for (int k = 0; k < w; ++k) pre += wcnt[k][d];
+      const uint32_t pos = base_off[d] + running[d] + pre + rank;
+      kout[pos] = key;
+      vout[pos] = val;
+    }
+    __syncthreads();
+    uint32_t tot = 0;
+    for (int k = 0; k < kSortThreads / 32; ++k) {
+      tot += wcnt[k][t];
+      wcnt[k][t] = 0;
+    }
+    running[t] += tot;
+    __syncthreads();
+  }
+}
+
+__global__ void k_tile_bounds(const uint32_t* __restrict__ keys, int64_t n,
+                              uint32_t* __restrict__ begin, uint32_t* __restrict__ end) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t k = keys[i];
+  if (i == 0 || keys[i - 1] != k) begin[k] = (uint32_t)i;
+  if (i == n - 1 || keys[i + 1] != k) end[k] = (uint32_t)(i + 1);
+}
+
+// ---------------------------------------------------------------------------
+// density: one block per tile of B^3 voxels; each thread owns VX voxels of
+// one x-row (they share the y/z part of the quadratic form)
+// ---------------------------------------------------------------------------
+template <int B>
+struct DensityCfg {
+  static constexpr int VX = B >= 8 ? 4 : 2;           // voxels per thread along x
+  static constexpr int THREADS = B * B * B / VX;       // 128 for B = 8, 32 for B = 4
+  static constexpr int CHUNK = 256;                    // candidates staged per pass
+};
+
+template <int B>
+__global__ void __launch_bounds__(DensityCfg<B>::THREADS)
+    k_density(const GaussParams* __restrict__ params, const uint32_t* __restrict__ cand,
+              const uint32_t* __restrict__ begin, const uint32_t* __restrict__ end, GridArgs g,
+              float* __restrict__ out) {
+  using C = DensityCfg<B>;
+  __shared__ float4 sa[C::CHUNK];  // (tile origin - mu) as float, alpha^2
+  __shared__ float4 sb[C::CHUNK];
+  __shared__ float2 sc[C::CHUNK];
+  const int tile = blockIdx.x;
+  const int tx = tile % g.ntiles[0], ty = (tile / g.ntiles[0]) % g.ntiles[1],
+            tz = tile / (g.ntiles[0] * g.ntiles[1]);
+  const uint32_t b0 = begin[tile], b1 = end[tile];
+  // thread -> voxels (x0 .. x0+VX-1, y, z) inside the tile
+  const int t = threadIdx.x;
+  const int xg = t % (B / C::VX), y = (t / (B / C::VX)) % B, z = t / ((B / C::VX) * B);
+  const int x0 = xg * C::VX;
+  float ox[C::VX];
+#pragma unroll
+  for (int v = 0; v < C::VX; ++v) ox[v] = ((float)(x0 + v) + 0.5f) * g.h;
+  const float oy = ((float)y + 0.5f) * g.h, oz = ((float)z + 0.5f) * g.h;
+  // tile corner in FP64 (the offsets to the means are formed there, then
+  // rounded once: |tile corner - mu| is small, so the float offset is accurate)
+  const double cx = (double)g.o[0] + (double)(tx * B) * (double)g.h;
+  const double cy = (double)g.o[1] + (double)(ty * B) * (double)g.h;
+  const double cz = (double)g.o[2] + (double)(tz * B) * (double)g.h;
+  float acc[C::VX];
+#pragma unroll
+  for (int v = 0; v < C::VX; ++v) acc[v] = 0.f;
+  for (uint32_t c0 = b0; c0 < b1; c0 += C::CHUNK) {
+    const uint32_t m = min((uint32_t)C::CHUNK, b1 - c0);
+    __syncthreads();
+    for (uint32_t k = t; k < m; k += C::THREADS) {
+      const GaussParams P = params[cand[c0 + k]];
+      sa[k] = make_float4((float)(cx - (double)P.a.x), (float)(cy - (double)P.a.y),
+                          (float)(cz - (double)P.a.z), P.a.w);
+      sb[k] = P.b;
+      sc[k] = make_float2(P.c.x, P.c.y);
+    }
+    __syncthreads();
+    for (uint32_t k = 0; k < m; ++k) {
+      const float4 A = sa[k];
+      const float4 M = sb[k];
+      const float2 N = sc[k];
+      const float dy = A.y + oy, dz = A.z + oz;
+      // y/z part: M11 dy^2 + M22 dz^2 + M12 dy dz, and the x coefficient M01 dy + M02 dz
+      const float syz = fmaf(fmaf(M.y, dy, N.y * dz), dy, M.z * dz * dz);
+      const float bx = fmaf(M.w, dy, N.x * dz);
+#pragma unroll
+      for (int v = 0; v < C::VX; ++v) {
+        const float dx = A.x + ox[v];
+        const float e = fmaf(fmaf(M.x, dx, bx), dx, syz);  // <= 0
+        acc[v] = fmaf(A.w, dev::ex2_approx(e), acc[v]);
+      }
+    }
+  }
+  const int gx = tx * B + x0, gy = ty * B + y, gz = tz * B + z;
+  if (gy < g.dims[1] && gz < g.dims[2]) {
+    float* row = out + ((int64_t)gz * g.dims[1] + gy) * g.dims[0];
+#pragma unroll
+    for (int v = 0; v < C::VX; ++v)
+      if (gx + v < g.dims[0]) row[gx + v] = acc[v];
+  }
+}
+
+__global__ void k_occ_surf(const float* __restrict__ D, GridArgs g, float theta,
+                           uint8_t* __restrict__ occ, uint8_t* __restrict__ surf) {
+  const int64_t n = (int64_t)g.dims[0] * g.dims[1] * g.dims[2];
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int nx = g.dims[0], ny = g.dims[1], nz = g.dims[2];
+  const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((int64_t)nx * ny));
+  const bool o = D[i] > theta;
+  bool interior = o;
+  if (interior) interior = x > 0 && D[i - 1] > theta;
+  if (interior) interior = x + 1 < nx && D[i + 1] > theta;
+  if (interior) interior = y > 0 && D[i - nx] > theta;
+  if (interior) interior = y + 1 < ny && D[i + nx] > theta;
+  if (interior) interior = z > 0 && D[i - (int64_t)nx * ny] > theta;
+  if (interior) interior = z + 1 < nz && D[i + (int64_t)nx * ny] > theta;
+  if (occ) occ[i] = o ? 1 : 0;
+  if (surf) surf[i] = (o && !interior) ? 1 : 0;
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct Scratch {
+  int device = -1;
+  void* params = nullptr;
+  size_t params_cap = 0;
+  void* ranges = nullptr;
+  size_t ranges_cap = 0;
+  void* counts = nullptr;
+  size_t counts_cap = 0;
+  void* sums = nullptr;
+  size_t sums_cap = 0;
+  void* pairs = nullptr;  // keys, vals, keys', vals'
+  size_t pairs_cap = 0;
+  void* hist = nullptr;
+  size_t hist_cap = 0;
+  void* bounds = nullptr;
+  size_t bounds_cap = 0;
+  std::mutex mu;
+};
+std::mutex g_scr_mu;
+std::unordered_map<uint64_t, std::unique_ptr<Scratch>> g_scr;
+
+Scratch* get_scratch(cudaStream_t s) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const uint64_t key = (uint64_t)(uintptr_t)s ^ ((uint64_t)dev << 56);
+  std::lock_guard<std::mutex> lk(g_scr_mu);
+  auto& p = g_scr[key];
+  if (!p) {
+    p.reset(new Scratch());
+    p->device = dev;
+  }
+  return p.get();
+}
+
+// grow a device buffer (contents not preserved); synchronises the stream first
+cudaError_t ensure(void** buf, size_t* cap, size_t bytes, cudaStream_t s) {
+  if (bytes <= *cap) return cudaSuccess;
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  if (*buf) cudaFree(*buf);
+  *buf = nullptr;
+  *cap = 0;
+  const size_t nb = std::max<size_t>(bytes + bytes / 4, 1 << 16);
+  e = cudaMalloc(buf, nb);
+  if (e != cudaSuccess) {
+    *buf = nullptr;
+    return e;
+  }
+  *cap = nb;
+  return cudaSuccess;
+}
+
+fgl_status err(int status, const std::string& msg) {
+  record_error(status, msg.c_str());
+  return (fgl_status)status;
+}
+
+fgl_status cuda_err(cudaError_t e, const char* what) {
+  return err(FGL_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define DCUDA(call)                                   \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return cuda_err(e_, #call); \
+  } while (0)
+
+// exclusive scan of n values in place; `tmp` holds the per-level block sums
+template <class T>
+cudaError_t scan_exclusive(T* x, int64_t n, T* tmp, size_t tmp_elems, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t nb = (n + 2047) / 2048;
+  if (nb == 1) {
+    k_scan_blocks<T><<<1, 1024, 0, s>>>(x, n, (T*)nullptr);
+    return cudaGetLastError();
+  }
+  if ((size_t)nb > tmp_elems) return cudaErrorInvalidValue;
+  k_scan_blocks<T><<<(unsigned)nb, 1024, 0, s>>>(x, n, tmp);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = scan_exclusive<T>(tmp, nb, tmp + nb, tmp_elems - nb, s);
+  if (e != cudaSuccess) return e;
+  k_scan_add<T><<<(unsigned)nb, 1024, 0, s>>>(x, n, tmp);
+  return cudaGetLastError();
+}
+
+// block sums needed by scan_exclusive over n values, all levels
+size_t scan_tmp_elems(int64_t n) {
+  size_t t = 0;
+  while (n > 2048) {
+    n = (n + 2047) / 2048;
+    t += (size_t)n;
+  }
+  return t + 1;
+}
+
+}  // namespace
+
+extern "C" fgl_status fgl_gaussian_density(const fgl_gaussians* gs, const fgl_grid* grid,
+                                           float theta, float* out_density, uint8_t* out_occ,
+                                           uint8_t* out_surf, fgl_density_stats* stats,
+                                           fgl_stream stream) {
+  if (!gs || !grid) return err(FGL_ERR_INVALID, "null gaussians or grid");
+  if (gs->n < 0) return err(FGL_ERR_INVALID, "n < 0");
+  if (gs->n > 0 && (!gs->mu || !gs->scale || !gs->quat || !gs->opacity))
+    return err(FGL_ERR_INVALID, "null Gaussian parameter pointer");
+  if (gs->n >= ((int64_t)1 << 32)) return err(FGL_ERR_INVALID, "too many Gaussians (max 2^32 - 1)");
+  if (!out_density) return err(FGL_ERR_INVALID, "out_density is null");
+  const int B = grid->tile ? grid->tile : 8;
+  if (B != 4 && B != 8) return err(FGL_ERR_INVALID, "tile must be 4 or 8");
+  if (!(std::isfinite(grid->h) && grid->h > 0.f)) return err(FGL_ERR_INVALID, "h must be finite and > 0");
+  for (int a = 0; a < 3; ++a) {
+    if (grid->dims[a] < 1) return err(FGL_ERR_INVALID, "grid dims must be >= 1");
+    if (!std::isfinite(grid->origin[a])) return err(FGL_ERR_INVALID, "grid origin must be finite");
+  }
+  if (!std::isfinite(theta)) return err(FGL_ERR_INVALID, "theta must be finite");
+  GridArgs g;
+  for (int a = 0; a < 3; ++a) {
+    g.o[a] = grid->origin[a];
+    g.dims[a] = grid->dims[a];
+    g.ntiles[a] = (grid->dims[a] + B - 1) / B;
+  }
+  g.h = grid->h;
+  g.cell = (float)B * grid->h;
+  const int64_t n_vox = (int64_t)g.dims[0] * g.dims[1] * g.dims[2];
+  const int64_t n_tiles = (int64_t)g.ntiles[0] * g.ntiles[1] * g.ntiles[2];
+  if (n_tiles >= ((int64_t)1 << 31)) return err(FGL_ERR_INVALID, "grid has too many tiles");
+  cudaStream_t s = (cudaStream_t)stream;
+  Scratch& S = *get_scratch(s);
+  std::lock_guard<std::mutex> lk(S.mu);
+  const int64_t n = gs->n;
+
+  // tile bounds (begin, end) start empty
+  DCUDA(ensure(&S.bounds, &S.bounds_cap, (size_t)n_tiles * 2 * sizeof(uint32_t), s));
+  uint32_t* begin = (uint32_t*)S.bounds;
+  uint32_t* end = begin + n_tiles;
+  DCUDA(cudaMemsetAsync(begin, 0, (size_t)n_tiles * 2 * sizeof(uint32_t), s));
+
+  uint64_t n_pairs = 0;
+  if (n > 0) {
+    DCUDA(ensure(&S.params, &S.params_cap, (size_t)n * sizeof(GaussParams), s));
+    DCUDA(ensure(&S.ranges, &S.ranges_cap, (size_t)n * 2 * sizeof(int4), s));
+    DCUDA(ensure(&S.counts, &S.counts_cap, (size_t)(n + 1) * sizeof(unsigned long long), s));
+    const size_t tmp_g = scan_tmp_elems(n + 1);
+    DCUDA(ensure(&S.sums, &S.sums_cap, tmp_g * sizeof(unsigned long long), s));
+    GaussParams* params = (GaussParams*)S.params;
+    int4* ranges = (int4*)S.ranges;
+    unsigned long long* counts = (unsigned long long*)S.counts;
+    const unsigned gb = (unsigned)((n + 255) / 256);
+    k_gauss_prep<<<gb, 256, 0, s>>>(gs->mu, gs->scale, gs->quat, gs->opacity, n, g, params, ranges,
+                                    counts);
+    DCUDA(cudaGetLastError());
+    DCUDA(cudaMemsetAsync(counts + n, 0, sizeof(unsigned long long), s));
+    DCUDA(scan_exclusive<unsigned long long>(counts, n + 1, (unsigned long long*)S.sums, tmp_g, s));
+    DCUDA(cudaMemcpyAsync(&n_pairs, counts + n, sizeof(n_pairs), cudaMemcpyDeviceToHost, s));
+    DCUDA(cudaStreamSynchronize(s));
+    if (n_pairs >= ((uint64_t)1 << 31))
+      return err(FGL_ERR_INVALID, "too many (Gaussian, tile) pairs (max 2^31 - 1): use a larger tile or voxel");
+  }
+  if (n_pairs > 0) {
+    DCUDA(ensure(&S.pairs, &S.pairs_cap, (size_t)n_pairs * 4 * sizeof(uint32_t), s));
+    uint32_t* k0 = (uint32_t*)S.pairs;
+    uint32_t* v0 = k0 + n_pairs;
+    uint32_t* k1 = v0 + n_pairs;
+    uint32_t* v1 = k1 + n_pairs;
+    const unsigned gb = (unsigned)((n + 255) / 256);
+    k_emit<<<gb, 256, 0, s>>>((const int4*)S.ranges, (const unsigned long long*)S.counts, n, g, k0,
+                              v0);
+    DCUDA(cudaGetLastError());
+    // stable LSD radix sort by tile id
+    int bits = 1;
+    while (((int64_t)1 << bits) < n_tiles) ++bits;
+    const int items = kSortThreads * kSortRounds;
+    const int nblocks = (int)((n_pairs + items - 1) / items);
+    const int64_t nh = (int64_t)256 * nblocks;
+    const size_t tmp_h = scan_tmp_elems(nh);
+    DCUDA(ensure(&S.hist, &S.hist_cap, (size_t)(nh + tmp_h) * sizeof(uint32_t), s));
+    uint32_t* hist = (uint32_t*)S.hist;
+    for (int shift = 0; shift < bits; shift += 8) {
+      k_radix_hist<<<nblocks, kSortThreads, 0, s>>>(k0, (int64_t)n_pairs, shift, hist, nblocks);
+      DCUDA(cudaGetLastError());
+      DCUDA(scan_exclusive<uint32_t>(hist, nh, hist + nh, tmp_h, s));
+      k_radix_scatter<<<nblocks, kSortThreads, 0, s>>>(k0, v0, (int64_t)n_pairs, shift, hist,
+                                                      nblocks, k1, v1);
+      DCUDA(cudaGetLastError());
+      std::swap(k0, k1);
+      std::swap(v0, v1);
+    }
+    k_tile_bounds<<<(unsigned)((n_pairs + 255) / 256), 256, 0, s>>>(k0, (int64_t)n_pairs, begin,
+                                                                     end);
+    DCUDA(cudaGetLastError());
+    if (B == 8)
+      k_density<8><<<(unsigned)n_tiles, DensityCfg<8>::THREADS, 0, s>>>(
+          (const GaussParams*)S.params, v0, begin, end, g, out_density);
+    else
+      k_density<4><<<(unsigned)n_tiles, DensityCfg<4>::THREADS, 0, s>>>(
+          (const GaussParams*)S.params, v0, begin, end, g, out_density);
+    DCUDA(cudaGetLastError());
+  } else {
+    DCUDA(cudaMemsetAsync(out_density, 0, (size_t)n_vox * sizeof(float), s));
+  }
+  if (out_occ || out_surf) {
+    k_occ_surf<<<(unsigned)((n_vox + 255) / 256), 256, 0, s>>>(out_density, g, theta, out_occ,
+                                                               out_surf);
+    DCUDA(cudaGetLastError());
+  }
+  if (stats) {
+    stats->n_pairs = (int64_t)n_pairs;
+    stats->n_tiles = n_tiles;
+    stats->n_voxels = n_vox;
+  }
+  return FGL_OK;
+}

@@ -40,6 +40,14 @@ __device__ __forceinline__ uint32_t half_rp(float x) {
   return (uint32_t)h;
 }
 
+// 2^x, approximate (relative error about 2^-22); results below the smallest
+// normal float are flushed to zero.
+__device__ __forceinline__ float ex2_approx(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // Element-wise minimum of two pairs of unsigned 16-bit integers.
 __device__ __forceinline__ uint32_t min_u16x2(uint32_t a, uint32_t b) {
   uint32_t r;
