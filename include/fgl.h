@@ -288,9 +288,14 @@ typedef struct {
 } fgl_grid;
 
 typedef struct {
-  int64_t n_pairs;       /* (Gaussian, tile) candidate pairs */
-  int64_t n_tiles;
-  int64_t n_voxels;
+  int32_t timing;        /* in: 1 = time the call with CUDA events on `stream` (it then
+                            synchronises the stream again before returning) */
+  int64_t n_pairs;       /* out: (Gaussian, tile) candidate pairs */
+  int64_t n_tiles;       /* out */
+  int64_t n_voxels;      /* out */
+  float ms_total;        /* out (timing): first to last launch of the call */
+  float ms_density;      /* out (timing): the density kernel alone */
+  int32_t n_launches;    /* out: kernels the call launched */
 } fgl_density_stats;
 
 /* Eq. D(v) on the grid, then eqs. V_occ, Int and Surf:
@@ -314,7 +319,8 @@ typedef struct {
  * is nobody's candidate.  Each voxel sums its tile's candidates in increasing
  * Gaussian index (float32; the results are deterministic).
  *   out_density: device float32 [n_voxels] (required);
- *   out_occ / out_surf: device uint8 [n_voxels] (0/1), either may be NULL.
+ *   out_occ / out_surf: device uint8 [n_voxels] (0/1), either may be NULL;
+ *   stats: may be NULL (see fgl_density_stats for its one input field).
  * The call synchronises `stream` once (to size the pair buffers, cached per
  * stream); the rest is asynchronous.  Errors: FGL_ERR_INVALID (bad grid,
  * tile, null pointers, more than 2^31 - 1 pairs), FGL_ERR_CUDA. */

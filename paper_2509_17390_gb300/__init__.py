@@ -392,12 +392,13 @@ class Grid(ctypes.Structure):
 
 
 class DensityStats(ctypes.Structure):
-    _fields_ = [("n_pairs", I64), ("n_tiles", I64), ("n_voxels", I64)]
+    _fields_ = [("timing", I32), ("n_pairs", I64), ("n_tiles", I64), ("n_voxels", I64),
+                ("ms_total", F32), ("ms_density", F32), ("n_launches", I32)]
 
 
 def gaussian_density(mu, scale, quat, opacity, origin, h: float, dims, theta: float = 0.5,
                      tile: int = 0, out_density=None, out_occ=None, out_surf=None, stream=None,
-                     masks: bool = True):
+                     masks: bool = True, timing: bool = False):
     """Gaussian-to-occupancy conversion (fgl_gaussian_density, paper Sec.
     IV-A) on torch CUDA tensors: mu/scale [n,3], quat [n,4] (w,x,y,z),
     opacity [n].  Returns (density [nz,ny,nx] f32, occ u8, surf u8, stats);
@@ -419,13 +420,16 @@ def gaussian_density(mu, scale, quat, opacity, origin, h: float, dims, theta: fl
                    _dev_ptr(opacity, "float32", n, "opacity") if n else None, n)
     g = Grid((F32 * 3)(*[float(x) for x in origin]), float(h), (I32 * 3)(nx, ny, nz), int(tile))
     st = DensityStats()
+    st.timing = 1 if timing else 0
     _check(lib().fgl_gaussian_density(ctypes.byref(gs), ctypes.byref(g), float(theta),
                                       _dev_ptr(out_density, "float32", nv, "out_density"),
                                       _dev_ptr(out_occ, "uint8", nv, "out_occ") if masks else None,
                                       _dev_ptr(out_surf, "uint8", nv, "out_surf") if masks else None,
                                       ctypes.byref(st), _stream_handle(stream)))
     return out_density, out_occ, out_surf, {"n_pairs": st.n_pairs, "n_tiles": st.n_tiles,
-                                            "n_voxels": st.n_voxels}
+                                            "n_voxels": st.n_voxels, "ms_total": st.ms_total,
+                                            "ms_density": st.ms_density,
+                                            "n_launches": st.n_launches}
 
 
 def work_counters():

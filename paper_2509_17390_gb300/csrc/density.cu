@@ -15,7 +15,8 @@
 //                  index and the float32 sums are deterministic;
 //   k_tile_bounds  begin/end of every tile's candidate run;
 //   k_density<B>   one block per tile: candidates staged in shared memory in
-//                  chunks, each thread accumulates its voxels over them;
+//                  chunks, each thread accumulates one x-row of voxels over
+//                  them in packed f32x2 arithmetic (one ex2 per evaluation);
 //   k_occ_surf     D > theta and the 6-neighbour surface test.
 //
 // The paper finds the candidates of a tile with an LBVH query over Gaussian
@@ -236,50 +237,58 @@ __global__ void k_radix_hist(const uint32_t* __restrict__ keys, int64_t n, int s
   hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
 }
 
-// Stable scatter: within a block, items are ranked in index order (round,
-// then thread); across blocks, the scanned histogram orders them.
+// Stable scatter.  Each warp owns a contiguous run of kSortRounds * 32 items
+// (warp w of the block: items [w*R*32, (w+1)*R*32) of the block's slice), so
+// index order is (warp, round, lane).  Pass 1 counts each warp's digits with
+// __match_any_sync; one block barrier turns those counts into per-warp bases;
+// pass 2 ranks every item inside its warp (earlier rounds, then lower lanes
+// in the same round) and writes it out.
 __global__ void k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                                 int64_t n, int shift, const uint32_t* __restrict__ offs,
                                 int nblocks, uint32_t* __restrict__ kout,
                                 uint32_t* __restrict__ vout) {
-  __shared__ uint32_t base_off[256];
-  __shared__ uint32_t running[256];
-  __shared__ uint32_t wcnt[kSortThreads / 32][256];
+  constexpr int NW = kSortThreads / 32;
+  __shared__ uint32_t wbase[NW][256];  // digit counts, then per-warp base offsets
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  base_off[t] = offs[(int64_t)t * nblocks + blockIdx.x];
-  running[t] = 0;
-  for (int k = 0; k < kSortThreads / 32; ++k) wcnt[k][t] = 0;
+  for (int k = 0; k < NW; ++k) wbase[k][t] = 0;
   __syncthreads();
-  const int64_t base = (int64_t)blockIdx.x * (kSortThreads * kSortRounds);
+  const int64_t base = (int64_t)blockIdx.x * (kSortThreads * kSortRounds) +
+                       (int64_t)w * (32 * kSortRounds);
   const unsigned lt = (1u << lane) - 1u;
+  uint32_t key[kSortRounds];
+#pragma unroll
   for (int r = 0; r < kSortRounds; ++r) {
-    const int64_t i = base + r * kSortThreads + t;
-    const bool valid = i < n;
-    uint32_t key = 0, val = 0, d = 256;
-    if (valid) {
-      key = kin[i];
-      val = vin[i];
-      d = (key >> shift) & 255u;
-    }
+    const int64_t i = base + r * 32 + lane;
+    key[r] = i < n ? kin[i] : 0xFFFFFFFFu;
+    const uint32_t d = i < n ? (key[r] >> shift) & 255u : 256u;
     const unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
-    const uint32_t rank = __popc(peers & lt);
-    if (valid && rank == 0) wcnt[w][d] = __popc(peers);
-    __syncthreads();
-    if (valid) {
-      uint32_t pre = 0;
-      for (int k = 0; k < w; ++k) pre += wcnt[k][d];
-      const uint32_t pos = base_off[d] + running[d] + pre + rank;
-      kout[pos] = key;
-      vout[pos] = val;
+    if (d < 256u && __popc(peers & lt) == 0) wbase[w][d] += __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  {
+    // thread t = digit t: exclusive prefix over warps, plus the block's global offset
+    uint32_t run = offs[(int64_t)t * nblocks + blockIdx.x];
+    for (int k = 0; k < NW; ++k) {
+      const uint32_t c = wbase[k][t];
+      wbase[k][t] = run;
+      run += c;
     }
-    __syncthreads();
-    uint32_t tot = 0;
-    for (int k = 0; k < kSortThreads / 32; ++k) {
-      tot += wcnt[k][t];
-      wcnt[k][t] = 0;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kSortRounds; ++r) {
+    const int64_t i = base + r * 32 + lane;
+    const uint32_t d = i < n ? (key[r] >> shift) & 255u : 256u;
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
+    if (d < 256u) {
+      const uint32_t pos = wbase[w][d] + __popc(peers & lt);
+      kout[pos] = key[r];
+      vout[pos] = vin[i];
     }
-    running[t] += tot;
-    __syncthreads();
+    __syncwarp();
+    if (d < 256u && __popc(peers & lt) == 0) wbase[w][d] += __popc(peers);
+    __syncwarp();
   }
 }
 
@@ -293,15 +302,21 @@ __global__ void k_tile_bounds(const uint32_t* __restrict__ keys, int64_t n,
 }
 
 // ---------------------------------------------------------------------------
-// density: one block per tile of B^3 voxels; each thread owns VX voxels of
-// one x-row (they share the y/z part of the quadratic form)
+// density: one block per tile of B^3 voxels; each thread owns one x-row of
+// the tile (B voxels sharing the y/z part of the quadratic form) and works on
+// voxel pairs with packed f32x2 arithmetic
 // ---------------------------------------------------------------------------
 template <int B>
 struct DensityCfg {
-  static constexpr int VX = B >= 8 ? 4 : 2;           // voxels per thread along x
-  static constexpr int THREADS = B * B * B / VX;       // 128 for B = 8, 32 for B = 4
-  static constexpr int CHUNK = 256;                    // candidates staged per pass
+  static constexpr int THREADS = B * B;  // one x-row each: 64 for B = 8, 16 for B = 4
+  static constexpr int CHUNK = 128;      // candidates staged per pass
 };
+
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
 
 template <int B>
 __global__ void __launch_bounds__(DensityCfg<B>::THREADS)
@@ -309,62 +324,71 @@ __global__ void __launch_bounds__(DensityCfg<B>::THREADS)
               const uint32_t* __restrict__ begin, const uint32_t* __restrict__ end, GridArgs g,
               float* __restrict__ out) {
   using C = DensityCfg<B>;
-  __shared__ float4 sa[C::CHUNK];  // (tile origin - mu) as float, alpha^2
-  __shared__ float4 sb[C::CHUNK];
-  __shared__ float2 sc[C::CHUNK];
+  // staged candidate k:  s0 = (dX, dX, M00, M00), s1 = (a2, a2, dY, dZ),
+  // s2 = (M11, M22, M01, M02), s3 = M12, with (dX, dY, dZ) = tile corner - mu
+  __shared__ float4 s0[C::CHUNK], s1[C::CHUNK], s2[C::CHUNK];
+  __shared__ float s3[C::CHUNK];
   const int tile = blockIdx.x;
   const int tx = tile % g.ntiles[0], ty = (tile / g.ntiles[0]) % g.ntiles[1],
             tz = tile / (g.ntiles[0] * g.ntiles[1]);
   const uint32_t b0 = begin[tile], b1 = end[tile];
-  // thread -> voxels (x0 .. x0+VX-1, y, z) inside the tile
   const int t = threadIdx.x;
-  const int xg = t % (B / C::VX), y = (t / (B / C::VX)) % B, z = t / ((B / C::VX) * B);
-  const int x0 = xg * C::VX;
-  float ox[C::VX];
+  const int y = t % B, z = t / B;
+  uint64_t ox2[B / 2];
 #pragma unroll
-  for (int v = 0; v < C::VX; ++v) ox[v] = ((float)(x0 + v) + 0.5f) * g.h;
+  for (int p = 0; p < B / 2; ++p)
+    ox2[p] = dev::pack2f(((float)(2 * p) + 0.5f) * g.h, ((float)(2 * p + 1) + 0.5f) * g.h);
   const float oy = ((float)y + 0.5f) * g.h, oz = ((float)z + 0.5f) * g.h;
   // tile corner in FP64 (the offsets to the means are formed there, then
   // rounded once: |tile corner - mu| is small, so the float offset is accurate)
   const double cx = (double)g.o[0] + (double)(tx * B) * (double)g.h;
   const double cy = (double)g.o[1] + (double)(ty * B) * (double)g.h;
   const double cz = (double)g.o[2] + (double)(tz * B) * (double)g.h;
-  float acc[C::VX];
+  uint64_t acc2[B / 2];
 #pragma unroll
-  for (int v = 0; v < C::VX; ++v) acc[v] = 0.f;
+  for (int p = 0; p < B / 2; ++p) acc2[p] = 0ull;
   for (uint32_t c0 = b0; c0 < b1; c0 += C::CHUNK) {
     const uint32_t m = min((uint32_t)C::CHUNK, b1 - c0);
     __syncthreads();
     for (uint32_t k = t; k < m; k += C::THREADS) {
       const GaussParams P = params[cand[c0 + k]];
-      sa[k] = make_float4((float)(cx - (double)P.a.x), (float)(cy - (double)P.a.y),
-                          (float)(cz - (double)P.a.z), P.a.w);
-      sb[k] = P.b;
-      sc[k] = make_float2(P.c.x, P.c.y);
+      const float dX = (float)(cx - (double)P.a.x);
+      s0[k] = make_float4(dX, dX, P.b.x, P.b.x);
+      s1[k] = make_float4(P.a.w, P.a.w, (float)(cy - (double)P.a.y), (float)(cz - (double)P.a.z));
+      s2[k] = make_float4(P.b.y, P.b.z, P.b.w, P.c.x);
+      s3[k] = P.c.y;
     }
     __syncthreads();
     for (uint32_t k = 0; k < m; ++k) {
-      const float4 A = sa[k];
-      const float4 M = sb[k];
-      const float2 N = sc[k];
-      const float dy = A.y + oy, dz = A.z + oz;
-      // y/z part: M11 dy^2 + M22 dz^2 + M12 dy dz, and the x coefficient M01 dy + M02 dz
-      const float syz = fmaf(fmaf(M.y, dy, N.y * dz), dy, M.z * dz * dz);
-      const float bx = fmaf(M.w, dy, N.x * dz);
+      const float4 A = s0[k], W = s1[k], M = s2[k];
+      const float m12 = s3[k];
+      const float dy = W.z + oy, dz = W.w + oz;
+      // y/z part M11 dy^2 + M12 dy dz + M22 dz^2 and x coefficient M01 dy + M02 dz
+      const float syz = fmaf(fmaf(M.x, dy, m12 * dz), dy, (M.y * dz) * dz);
+      const float bx = fmaf(M.z, dy, M.w * dz);
+      const uint64_t dX2 = dev::pack2f(A.x, A.y), M002 = dev::pack2f(A.z, A.w);
+      const uint64_t a22 = dev::pack2f(W.x, W.y);
+      const uint64_t bx2 = dev::pack2f(bx, bx), syz2 = dev::pack2f(syz, syz);
 #pragma unroll
-      for (int v = 0; v < C::VX; ++v) {
-        const float dx = A.x + ox[v];
-        const float e = fmaf(fmaf(M.x, dx, bx), dx, syz);  // <= 0
-        acc[v] = fmaf(A.w, dev::ex2_approx(e), acc[v]);
+      for (int p = 0; p < B / 2; ++p) {
+        const uint64_t dx2 = add2(dX2, ox2[p]);
+        const uint64_t q2 = dev::ffma2(dev::ffma2(M002, dx2, bx2), dx2, syz2);  // <= 0
+        float q0, q1;
+        dev::unpack2f(q2, q0, q1);
+        acc2[p] = dev::ffma2(a22, dev::pack2f(dev::ex2_approx(q0), dev::ex2_approx(q1)), acc2[p]);
       }
     }
   }
-  const int gx = tx * B + x0, gy = ty * B + y, gz = tz * B + z;
+  const int gx = tx * B, gy = ty * B + y, gz = tz * B + z;
   if (gy < g.dims[1] && gz < g.dims[2]) {
     float* row = out + ((int64_t)gz * g.dims[1] + gy) * g.dims[0];
 #pragma unroll
-    for (int v = 0; v < C::VX; ++v)
-      if (gx + v < g.dims[0]) row[gx + v] = acc[v];
+    for (int p = 0; p < B / 2; ++p) {
+      float a0, a1;
+      dev::unpack2f(acc2[p], a0, a1);
+      if (gx + 2 * p < g.dims[0]) row[gx + 2 * p] = a0;
+      if (gx + 2 * p + 1 < g.dims[0]) row[gx + 2 * p + 1] = a1;
+    }
   }
 }
 
@@ -406,6 +430,7 @@ struct Scratch {
   size_t hist_cap = 0;
   void* bounds = nullptr;
   size_t bounds_cap = 0;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   std::mutex mu;
 };
 std::mutex g_scr_mu;
@@ -459,20 +484,24 @@ fgl_status cuda_err(cudaError_t e, const char* what) {
 
 // exclusive scan of n values in place; `tmp` holds the per-level block sums
 template <class T>
-cudaError_t scan_exclusive(T* x, int64_t n, T* tmp, size_t tmp_elems, cudaStream_t s) {
+cudaError_t scan_exclusive(T* x, int64_t n, T* tmp, size_t tmp_elems, cudaStream_t s,
+                           int* launches) {
   if (n <= 0) return cudaSuccess;
   const int64_t nb = (n + 2047) / 2048;
   if (nb == 1) {
     k_scan_blocks<T><<<1, 1024, 0, s>>>(x, n, (T*)nullptr);
+    ++*launches;
     return cudaGetLastError();
   }
   if ((size_t)nb > tmp_elems) return cudaErrorInvalidValue;
   k_scan_blocks<T><<<(unsigned)nb, 1024, 0, s>>>(x, n, tmp);
+  ++*launches;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  e = scan_exclusive<T>(tmp, nb, tmp + nb, tmp_elems - nb, s);
+  e = scan_exclusive<T>(tmp, nb, tmp + nb, tmp_elems - nb, s, launches);
   if (e != cudaSuccess) return e;
   k_scan_add<T><<<(unsigned)nb, 1024, 0, s>>>(x, n, tmp);
+  ++*launches;
   return cudaGetLastError();
 }
 
@@ -521,6 +550,12 @@ extern "C" fgl_status fgl_gaussian_density(const fgl_gaussians* gs, const fgl_gr
   Scratch& S = *get_scratch(s);
   std::lock_guard<std::mutex> lk(S.mu);
   const int64_t n = gs->n;
+  const bool timing = stats && stats->timing == 1;
+  int launches = 0;
+  if (timing && !S.ev[0]) {
+    for (int k = 0; k < 4; ++k) DCUDA(cudaEventCreate(&S.ev[k]));
+  }
+  if (timing) DCUDA(cudaEventRecord(S.ev[0], s));
 
   // tile bounds (begin, end) start empty
   DCUDA(ensure(&S.bounds, &S.bounds_cap, (size_t)n_tiles * 2 * sizeof(uint32_t), s));
@@ -541,9 +576,11 @@ extern "C" fgl_status fgl_gaussian_density(const fgl_gaussians* gs, const fgl_gr
     const unsigned gb = (unsigned)((n + 255) / 256);
     k_gauss_prep<<<gb, 256, 0, s>>>(gs->mu, gs->scale, gs->quat, gs->opacity, n, g, params, ranges,
                                     counts);
+    ++launches;
     DCUDA(cudaGetLastError());
     DCUDA(cudaMemsetAsync(counts + n, 0, sizeof(unsigned long long), s));
-    DCUDA(scan_exclusive<unsigned long long>(counts, n + 1, (unsigned long long*)S.sums, tmp_g, s));
+    DCUDA(scan_exclusive<unsigned long long>(counts, n + 1, (unsigned long long*)S.sums, tmp_g, s,
+                                             &launches));
     DCUDA(cudaMemcpyAsync(&n_pairs, counts + n, sizeof(n_pairs), cudaMemcpyDeviceToHost, s));
     DCUDA(cudaStreamSynchronize(s));
     if (n_pairs >= ((uint64_t)1 << 31))
@@ -558,6 +595,7 @@ extern "C" fgl_status fgl_gaussian_density(const fgl_gaussians* gs, const fgl_gr
     const unsigned gb = (unsigned)((n + 255) / 256);
     k_emit<<<gb, 256, 0, s>>>((const int4*)S.ranges, (const unsigned long long*)S.counts, n, g, k0,
                               v0);
+    ++launches;
     DCUDA(cudaGetLastError());
     // stable LSD radix sort by tile id
     int bits = 1;
@@ -570,36 +608,51 @@ extern "C" fgl_status fgl_gaussian_density(const fgl_gaussians* gs, const fgl_gr
     uint32_t* hist = (uint32_t*)S.hist;
     for (int shift = 0; shift < bits; shift += 8) {
       k_radix_hist<<<nblocks, kSortThreads, 0, s>>>(k0, (int64_t)n_pairs, shift, hist, nblocks);
+      ++launches;
       DCUDA(cudaGetLastError());
-      DCUDA(scan_exclusive<uint32_t>(hist, nh, hist + nh, tmp_h, s));
+      DCUDA(scan_exclusive<uint32_t>(hist, nh, hist + nh, tmp_h, s, &launches));
       k_radix_scatter<<<nblocks, kSortThreads, 0, s>>>(k0, v0, (int64_t)n_pairs, shift, hist,
                                                       nblocks, k1, v1);
+      ++launches;
       DCUDA(cudaGetLastError());
       std::swap(k0, k1);
       std::swap(v0, v1);
     }
     k_tile_bounds<<<(unsigned)((n_pairs + 255) / 256), 256, 0, s>>>(k0, (int64_t)n_pairs, begin,
                                                                      end);
+    ++launches;
     DCUDA(cudaGetLastError());
+    if (timing) DCUDA(cudaEventRecord(S.ev[1], s));
     if (B == 8)
       k_density<8><<<(unsigned)n_tiles, DensityCfg<8>::THREADS, 0, s>>>(
           (const GaussParams*)S.params, v0, begin, end, g, out_density);
     else
       k_density<4><<<(unsigned)n_tiles, DensityCfg<4>::THREADS, 0, s>>>(
           (const GaussParams*)S.params, v0, begin, end, g, out_density);
+    ++launches;
     DCUDA(cudaGetLastError());
+    if (timing) DCUDA(cudaEventRecord(S.ev[2], s));
   } else {
     DCUDA(cudaMemsetAsync(out_density, 0, (size_t)n_vox * sizeof(float), s));
   }
   if (out_occ || out_surf) {
     k_occ_surf<<<(unsigned)((n_vox + 255) / 256), 256, 0, s>>>(out_density, g, theta, out_occ,
                                                                out_surf);
+    ++launches;
     DCUDA(cudaGetLastError());
   }
   if (stats) {
     stats->n_pairs = (int64_t)n_pairs;
     stats->n_tiles = n_tiles;
     stats->n_voxels = n_vox;
+    stats->ms_total = stats->ms_density = 0.f;
+    stats->n_launches = launches;
+  }
+  if (timing) {
+    DCUDA(cudaEventRecord(S.ev[3], s));
+    DCUDA(cudaEventSynchronize(S.ev[3]));
+    DCUDA(cudaEventElapsedTime(&stats->ms_total, S.ev[0], S.ev[3]));
+    if (n_pairs > 0) DCUDA(cudaEventElapsedTime(&stats->ms_density, S.ev[1], S.ev[2]));
   }
   return FGL_OK;
 }
