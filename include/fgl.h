@@ -154,7 +154,14 @@ fgl_status fgl_cast(fgl_scene scene, fgl_sensor sensor, const float* poses, int3
  * intersection with t in [min_range, max_range] (eq. t_j*: intersections
  * outside the sensor's [t_min, t_max] are discarded), t > 0 always; a
  * surface nearer than min_range is passed through, so the ray may return a
- * farther surface behind it.  No intersection -> (max_range, -1). */
+ * farther surface behind it.  No intersection -> (max_range, -1).
+ * With instances, the environment's mesh is the scene plus every instance
+ * moved by its pose: each instance is cast in its own frame with the ray
+ *   u = o - t_k;  o'_i = ((R_0i u_0 + R_1i u_1) + R_2i u_2),
+ *   d'_i = ((R_0i d_0 + R_1i d_1) + R_2i d_2)   (float32, no FMA),
+ * which keeps the ray parameter t of a rigid motion; the return is the
+ * nearest over the scene and the instances, ties going to the scene, then to
+ * the lower instance index. */
 typedef struct {
   fgl_scene scene;
   fgl_sensor sensor;
@@ -164,6 +171,18 @@ typedef struct {
   float* out_range;     /* device float32 [n_env * n_rays] */
   int32_t* out_tri;     /* device int32  [n_env * n_rays] */
   float min_range;      /* t_min: finite, 0 <= min_range < max_range (0 = none) */
+  /* Optional (zero-initialise to leave unused): */
+  float* out_points;    /* device float32 [n_env * n_rays][3]: the world-frame return
+                           point o + t d, each coordinate o_i + (t * d_i) rounded twice;
+                           NaN for a miss */
+  int32_t n_instances;  /* rigid instances per environment (0 = none) */
+  const fgl_scene* instances;   /* host array [n_instances]: meshes in their own frames
+                                   (any BVH width; resident on the device) */
+  const float* instance_poses;  /* device float32 [n_env][n_instances][3][4]: world-from-local
+                                   [R | t] of instance k in environment e, R orthonormal */
+  int32_t* out_instance;        /* device int32 [n_env * n_rays]: k when the return lies on
+                                   instance k (out_tri is then its triangle), -1 otherwise;
+                                   may be NULL */
 } fgl_cast_item;
 
 typedef struct {

@@ -61,6 +61,7 @@ def lib():
             L.orc_validate.argtypes = [P, P, P, I64, D, D, P, P, I32, P]
             L.orc_tri_test.argtypes = [P, P, P, P, P, P]
             L.orc_tri_test.restype = I32
+            L.orc_instance_rays.argtypes = [P, P, P, I64, P, P]
             L.orc_gauss_tile_ranges.argtypes = [P, P, P, I64, P, ctypes.c_float, I32, P]
             L.orc_density.argtypes = [P, P, P, P, I64, P, ctypes.c_float, P, I32, I32, P, P]
             L.orc_occupancy.argtypes = [P, P, D, P, P]
@@ -98,6 +99,49 @@ def tri_test(o, d, v0, v1, v2):
     t = np.zeros(1, np.float64)
     hit = lib().orc_tri_test(*[_ptr(a) for a in args], _ptr(t))
     return float(t[0]) if hit else None
+
+
+def instance_rays(o: np.ndarray, d: np.ndarray, poses: np.ndarray):
+    """Rays moved into instance frames (float32, the fixed sequence of the C
+    source): poses is world-from-local [R | t] per ray, [n, 3, 4] or [n, 12]."""
+    o = np.ascontiguousarray(o, np.float32).reshape(-1, 3)
+    d = np.ascontiguousarray(d, np.float32).reshape(-1, 3)
+    P = np.ascontiguousarray(poses, np.float32).reshape(-1, 12)
+    oo = np.empty_like(o)
+    dd = np.empty_like(d)
+    lib().orc_instance_rays(_ptr(o), _ptr(d), _ptr(P), len(o), _ptr(oo), _ptr(dd))
+    return oo, dd
+
+
+def cast_with_instances(static: "Scene", instances, o, d, inst_poses, n_rays, max_range,
+                        min_range: float = 0.0):
+    """Eq. t_j* over a scene plus per-environment rigid instances.
+
+    inst_poses: [n_env, n_inst, 3, 4] world-from-local; rays env-major
+    (n_env * n_rays).  Each instance is cast in its own frame (instance_rays);
+    the return is the nearest, ties going to the scene, then to the lower
+    instance.  Returns (range f64, tri id, instance (-1 = scene), flags): the
+    flags of every part are combined (an ambiguity in any part may decide the
+    nearest), and a ray is also TIE-flagged when two parts return within tol
+    of each other."""
+    r, i, fl = static.cast(o, d, max_range, min_range=min_range)
+    inst = np.full(len(r), -1, np.int32)
+    r = r.copy()
+    i = i.copy()
+    fl = fl.copy()
+    P = np.asarray(inst_poses, np.float32)
+    for k, sc in enumerate(instances):
+        pk = np.repeat(P[:, k].reshape(-1, 12), n_rays, axis=0)
+        lo, ld = instance_rays(o, d, pk)
+        rk, ik, fk = sc.cast(lo, ld, max_range, min_range=min_range)
+        hit_k = ik >= 0
+        close = hit_k & (i >= 0) & (np.abs(rk - r) <= 1e-4 + 1e-6 * np.abs(r))
+        take = hit_k & ((i < 0) | (rk < r))
+        fl = fl | fk | np.where(close, FLAG_TIE, 0).astype(np.uint8)
+        r = np.where(take, rk, r)
+        i = np.where(take, ik, i)
+        inst = np.where(take, k, inst).astype(np.int32)
+    return r, i, inst, fl
 
 
 class Scene:

@@ -463,6 +463,28 @@ void orc_world_rays(const float* dirs, int64_t n_rays, const float* poses, int64
   }
 }
 
+// A ray moved into the frame of a rigidly posed instance (world-from-local
+// pose [R | t], float32 [12] per ray): u = o - t, o'_i = ((R_0i u_0 + R_1i u_1)
+// + R_2i u_2), d'_i the same with d, every product and sum rounded to float32
+// (no FMA).  A rigid motion keeps the ray parameter, so a hit at t in the
+// instance frame is a hit at t in the world.
+void orc_instance_rays(const float* o, const float* d, const float* pose, int64_t n, float* out_o,
+                       float* out_d) {
+  for (int64_t r = 0; r < n; ++r) {
+    const float* P = pose + 12 * r;
+    const float u[3] = {o[3 * r] - P[3], o[3 * r + 1] - P[7], o[3 * r + 2] - P[11]};
+    const float* dd = d + 3 * r;
+    for (int i = 0; i < 3; ++i) {
+      float a0 = P[i] * u[0], a1 = P[4 + i] * u[1], a2 = P[8 + i] * u[2];
+      float s01 = a0 + a1;
+      out_o[3 * r + i] = s01 + a2;
+      float b0 = P[i] * dd[0], b1 = P[4 + i] * dd[1], b2 = P[8 + i] * dd[2];
+      float t01 = b0 + b1;
+      out_d[3 * r + i] = t01 + b2;
+    }
+  }
+}
+
 // Scene: vertices float32 [nv][3], triangles int32 [nt][3].  use_bvh selects
 // the median-split BVH (1) or the brute-force loop (0).  Returns NULL on
 // invalid input (vertex id out of range, non-finite vertex).

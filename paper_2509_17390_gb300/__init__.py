@@ -51,7 +51,8 @@ class SceneStats(ctypes.Structure):
 
 class CastItem(ctypes.Structure):
     _fields_ = [("scene", P), ("sensor", P), ("poses", P), ("n_env", I32), ("max_range", F32),
-                ("out_range", P), ("out_tri", P), ("min_range", F32)]
+                ("out_range", P), ("out_tri", P), ("min_range", F32), ("out_points", P),
+                ("n_instances", I32), ("instances", P), ("instance_poses", P), ("out_instance", P)]
 
 
 class BatchOpts(ctypes.Structure):
@@ -284,17 +285,36 @@ def cast_opts(scene: Scene, sensor: Sensor, poses, max_range: float, opts: Batch
 
 
 def make_items(items: Sequence[tuple]):
-    """items: (scene, sensor, poses, max_range, out_range, out_tri[, min_range])
-    tuples with torch CUDA tensors; returns the ctypes array."""
+    """items: (scene, sensor, poses, max_range, out_range, out_tri[, min_range
+    [, extras]]) tuples with torch CUDA tensors, extras a dict with any of
+    "points" (out [n, 3] float32), "instances" (list of Scene), "instance_poses"
+    ([n_env, n_instances, 3, 4] float32) and "out_instance" ([n] int32).
+    Returns the ctypes array (it keeps the instance handle arrays alive)."""
     arr = (CastItem * max(1, len(items)))()
+    keep = []
     for i, item in enumerate(items):
         sc, se, poses, rmax, orng, otri = item[:6]
-        rmin = float(item[6]) if len(item) > 6 else 0.0
+        rmin = float(item[6]) if len(item) > 6 and item[6] is not None else 0.0
+        ex = item[7] if len(item) > 7 and item[7] else {}
         n_env = poses.shape[0] if poses.dim() == 3 else poses.numel() // 12
         n = n_env * se.n_rays
-        arr[i] = CastItem(sc.handle, se.handle, _dev_ptr(poses, "float32", n_env * 12, "poses"),
-                          n_env, float(rmax), _dev_ptr(orng, "float32", n, "out_range"),
-                          _dev_ptr(otri, "int32", n, "out_tri"), rmin)
+        c = CastItem(sc.handle, se.handle, _dev_ptr(poses, "float32", n_env * 12, "poses"),
+                     n_env, float(rmax), _dev_ptr(orng, "float32", n, "out_range"),
+                     _dev_ptr(otri, "int32", n, "out_tri"), rmin)
+        if ex.get("points") is not None:
+            c.out_points = _dev_ptr(ex["points"], "float32", 3 * n, "points")
+        insts = ex.get("instances") or []
+        if insts:
+            h = (P * len(insts))(*[x.handle for x in insts])
+            keep.append(h)
+            c.n_instances = len(insts)
+            c.instances = ctypes.cast(h, P)
+            c.instance_poses = _dev_ptr(ex["instance_poses"], "float32", n_env * len(insts) * 12,
+                                        "instance_poses")
+        if ex.get("out_instance") is not None:
+            c.out_instance = _dev_ptr(ex["out_instance"], "int32", n, "out_instance")
+        arr[i] = c
+    arr._keep = keep
     return arr
 
 

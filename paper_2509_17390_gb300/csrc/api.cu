@@ -129,8 +129,22 @@ fgl_status check_item(const fgl_cast_item& it, int idx) {
   if (!it.scene->d_nodes) return fail(FGL_ERR_INVALID, w + "scene is not resident on the device");
   if ((int64_t)it.n_env * it.sensor->n_rays > ((int64_t)1 << 40))
     return fail(FGL_ERR_INVALID, w + "too many rays");
+  if (it.n_instances < 0 || it.n_instances > 4096)
+    return fail(FGL_ERR_INVALID, w + "n_instances must be in [0, 4096]");
+  if (it.n_instances > 0) {
+    if (!it.instances) return fail(FGL_ERR_INVALID, w + "instances is null");
+    if (it.n_env > 0 && !it.instance_poses) return fail(FGL_ERR_INVALID, w + "instance_poses is null");
+    for (int k = 0; k < it.n_instances; ++k) {
+      if (!it.instances[k]) return fail(FGL_ERR_INVALID, w + "null instance scene");
+      if (!it.instances[k]->d_nodes)
+        return fail(FGL_ERR_INVALID, w + "instance scene is not resident on the device");
+    }
+  }
   return FGL_OK;
 }
+
+// Items with instances or point output need launches beyond the scene pass.
+bool has_extras(const fgl_cast_item& it) { return it.n_instances > 0 || it.out_points; }
 
 ItemDesc make_desc(const fgl_cast_item& it) {
   ItemDesc d;
@@ -245,7 +259,8 @@ fgl_status grid_for(int W, bool tmin, const Opts& o, int* grid) {
 // (host may rewrite the pinned table once it has fired) is recorded by the
 // caller outside any graph capture.
 fgl_status enqueue_batch(BatchCtx& c, const std::vector<Group>& groups,
-                         const std::vector<size_t>& offsets, const Opts& o, cudaStream_t s) {
+                         const std::vector<size_t>& offsets, const Opts& o,
+                         const fgl_cast_item* items, int n, cudaStream_t s) {
   FGL_CUDA(cudaMemcpyAsync(c.d_scratch, c.h_staging, c.table_bytes, cudaMemcpyHostToDevice, s));
   for (size_t g = 0; g < groups.size(); ++g) {
     int grid = 0;
@@ -255,7 +270,57 @@ fgl_status enqueue_batch(BatchCtx& c, const std::vector<Group>& groups,
                                (char*)c.d_scratch + offsets[g], grid,
                                o.block, o.sdepth, o.refill, o.tri_mode, o.postpone, s));
   }
+  // instance passes, then return points, item by item
+  for (int i = 0; i < n; ++i) {
+    const fgl_cast_item& it = items[i];
+    if (it.n_env == 0 || !has_extras(it)) continue;
+    const ItemDesc d = make_desc(it);
+    for (int k = 0; k < it.n_instances; ++k) {
+      const fgl_scene is = it.instances[k];
+      InstancePass a;
+      a.dirs = d.dirs;
+      a.poses = d.poses;
+      a.n_env = d.n_env;
+      a.n_rays = d.n_rays;
+      a.nodes = is->d_nodes;
+      a.tris = is->d_tris;
+      a.width = is->bvh.width;
+      a.n_inst = it.n_instances;
+      a.k = k;
+      a.inst_poses = it.instance_poses;
+      a.min_range = it.min_range;
+      a.out_range = it.out_range;
+      a.out_tri = it.out_tri;
+      a.out_inst = it.out_instance;
+      FGL_CUDA(launch_instance_pass(a, it.min_range > 0.f, 128, o.sdepth, s));
+    }
+    if (it.n_instances == 0 && it.out_instance)
+      FGL_CUDA(cudaMemsetAsync(it.out_instance, 0xFF, (size_t)d.n_env * d.n_rays * sizeof(int32_t), s));
+    if (it.out_points) FGL_CUDA(launch_points(d, it.out_points, s));
+  }
   return FGL_OK;
+}
+
+// Bytes of the launches beyond the work-queue table (they are baked into a
+// captured graph, so they are part of its key).
+void extras_key(const fgl_cast_item* items, int n, std::vector<uint8_t>& key) {
+  auto put = [&](const void* p, size_t b) {
+    key.insert(key.end(), (const uint8_t*)p, (const uint8_t*)p + b);
+  };
+  for (int i = 0; i < n; ++i) {
+    const fgl_cast_item& it = items[i];
+    if (!has_extras(it)) continue;
+    put(&i, sizeof(i));
+    put(&it.out_points, sizeof(it.out_points));
+    put(&it.n_instances, sizeof(it.n_instances));
+    put(&it.instance_poses, sizeof(it.instance_poses));
+    put(&it.out_instance, sizeof(it.out_instance));
+    for (int k = 0; k < it.n_instances; ++k) {
+      put(&it.instances[k]->d_nodes, sizeof(void*));
+      put(&it.instances[k]->d_tris, sizeof(void*));
+      put(&it.instances[k]->bvh.width, sizeof(int));
+    }
+  }
 }
 
 fgl_status run_batched(const fgl_cast_item* items, int n, const Opts& o, cudaStream_t s) {
@@ -312,7 +377,7 @@ fgl_status run_batched(const fgl_cast_item* items, int n, const Opts& o, cudaStr
     c.table_bytes = table.size();
   }
   if (!o.graph) {
-    fgl_status st = enqueue_batch(c, groups, offsets, o, s);
+    fgl_status st = enqueue_batch(c, groups, offsets, o, items, n, s);
     if (st != FGL_OK) return st;
     FGL_CUDA(cudaEventRecord(c.staged, s));
     return FGL_OK;
@@ -323,6 +388,7 @@ fgl_status run_batched(const fgl_cast_item* items, int n, const Opts& o, cudaStr
   const int cfg[9] = {o.packet, o.block, o.sdepth, o.bpsm, o.refill, o.postpone, o.count,
                       o.tri_mode, (int)(uintptr_t)c.d_scratch};
   key.insert(key.end(), (const uint8_t*)cfg, (const uint8_t*)cfg + sizeof(cfg));
+  extras_key(items, n, key);
   if (realloc || !c.gexec || key != c.gkey) {
     if (c.gexec) {
       cudaGraphExecDestroy(c.gexec);
@@ -331,7 +397,7 @@ fgl_status run_batched(const fgl_cast_item* items, int n, const Opts& o, cudaStr
     if (s == nullptr) return fail(FGL_ERR_INVALID, "use_graph needs a non-default stream");
     cudaGraph_t graph = nullptr;
     FGL_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    fgl_status st = enqueue_batch(c, groups, offsets, o, s);
+    fgl_status st = enqueue_batch(c, groups, offsets, o, items, n, s);
     cudaError_t e = cudaStreamEndCapture(s, &graph);
     if (st != FGL_OK) {
       if (graph) cudaGraphDestroy(graph);
@@ -369,6 +435,8 @@ const char* static_item_desc(const fgl_cast_item& it, ItemDesc* d, int* width) {
     return "null poses or output pointer in an item";
   if (!it.scene->d_nodes) return "scene is not resident on the device";
   if ((int64_t)it.n_env * it.sensor->n_rays > ((int64_t)1 << 40)) return "too many rays in an item";
+  if (it.n_instances != 0 || it.out_points || it.out_instance)
+    return "instances and return points need fgl_cast_batched";
   *d = make_desc(it);
   *width = it.scene->bvh.width;
   return nullptr;
@@ -638,6 +706,9 @@ fgl_status fgl_cast_batched_host(const fgl_cast_item* items, int32_t n_items,
   for (int i = 0; i < n_items; ++i) {
     fgl_status st = check_item(items[i], i);
     if (st != FGL_OK) return st;
+    if (has_extras(items[i]) || items[i].out_instance)
+      return fail(FGL_ERR_INVALID, "item " + std::to_string(i) +
+                                       ": instances and return points need fgl_cast_batched");
   }
   Opts o;
   fgl_status st = resolve_opts(opts, &o);

@@ -204,20 +204,40 @@ __global__ void k_scan_add(T* __restrict__ x, int64_t n, const T* __restrict__ s
 // ---------------------------------------------------------------------------
 // pairs, stable radix sort by tile, tile bounds
 // ---------------------------------------------------------------------------
+// One warp per 32 consecutive Gaussians: the warp writes each Gaussian's
+// pairs in turn with its 32 lanes, so the stores are contiguous and a
+// Gaussian covering many tiles does not hold up its neighbours.
 __global__ void k_emit(const int4* __restrict__ ranges, const unsigned long long* __restrict__ offs,
                        int64_t n, GridArgs g, uint32_t* __restrict__ keys,
                        uint32_t* __restrict__ vals) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int4 lo = ranges[2 * i], hi = ranges[2 * i + 1];
-  uint64_t p = offs[i];
-  for (int c = lo.z; c <= hi.z; ++c)
-    for (int b = lo.y; b <= hi.y; ++b)
-      for (int a = lo.x; a <= hi.x; ++a) {
-        keys[p] = (uint32_t)((c * g.ntiles[1] + b) * g.ntiles[0] + a);
-        vals[p] = (uint32_t)i;
-        ++p;
-      }
+  const int lane = threadIdx.x & 31;
+  const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane);
+  if (g0 >= n) return;
+  const int64_t mine = g0 + lane;
+  int4 lo = make_int4(0, 0, 0, 0), hi = make_int4(-1, -1, -1, 0);
+  unsigned long long off = 0;
+  if (mine < n) {
+    lo = ranges[2 * mine];
+    hi = ranges[2 * mine + 1];
+    off = offs[mine];
+  }
+  for (int j = 0; j < 32; ++j) {
+    const int lx = __shfl_sync(0xFFFFFFFFu, lo.x, j), ly = __shfl_sync(0xFFFFFFFFu, lo.y, j),
+              lz = __shfl_sync(0xFFFFFFFFu, lo.z, j);
+    const int ex = __shfl_sync(0xFFFFFFFFu, hi.x, j) - lx + 1;
+    const int ey = __shfl_sync(0xFFFFFFFFu, hi.y, j) - ly + 1;
+    const int ez = __shfl_sync(0xFFFFFFFFu, hi.z, j) - lz + 1;
+    const unsigned long long o = __shfl_sync(0xFFFFFFFFu, off, j);
+    if (ex <= 0 || ey <= 0 || ez <= 0) continue;  // no tiles (also past the end)
+    const int cnt = ex * ey * ez;
+    const uint32_t gid = (uint32_t)(g0 + j);
+    for (int p = lane; p < cnt; p += 32) {
+      const int a = p % ex, r = p / ex;
+      const int b = r % ey, c = r / ey;
+      keys[o + p] = (uint32_t)(((lz + c) * g.ntiles[1] + (ly + b)) * g.ntiles[0] + (lx + a));
+      vals[o + p] = gid;
+    }
+  }
 }
 
 constexpr int kSortThreads = 256;
@@ -255,12 +275,9 @@ __global__ void k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t
   const int64_t base = (int64_t)blockIdx.x * (kSortThreads * kSortRounds) +
                        (int64_t)w * (32 * kSortRounds);
   const unsigned lt = (1u << lane) - 1u;
-  uint32_t key[kSortRounds];
-#pragma unroll
   for (int r = 0; r < kSortRounds; ++r) {
     const int64_t i = base + r * 32 + lane;
-    key[r] = i < n ? kin[i] : 0xFFFFFFFFu;
-    const uint32_t d = i < n ? (key[r] >> shift) & 255u : 256u;
+    const uint32_t d = i < n ? (kin[i] >> shift) & 255u : 256u;
     const unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
     if (d < 256u && __popc(peers & lt) == 0) wbase[w][d] += __popc(peers);
     __syncwarp();
@@ -276,14 +293,14 @@ __global__ void k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t
     }
   }
   __syncthreads();
-#pragma unroll
   for (int r = 0; r < kSortRounds; ++r) {
     const int64_t i = base + r * 32 + lane;
-    const uint32_t d = i < n ? (key[r] >> shift) & 255u : 256u;
+    const uint32_t key = i < n ? kin[i] : 0u;
+    const uint32_t d = i < n ? (key >> shift) & 255u : 256u;
     const unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
     if (d < 256u) {
       const uint32_t pos = wbase[w][d] + __popc(peers & lt);
-      kout[pos] = key[r];
+      kout[pos] = key;
       vout[pos] = vin[i];
     }
     __syncwarp();

@@ -111,6 +111,24 @@ struct alignas(16) ItemDesc {
 };
 static_assert(sizeof(ItemDesc) == 80, "ItemDesc layout");
 
+// One instance pass: cast the rays of an item against instance k of each
+// environment (its BVH in its own frame, its pose per environment), keeping
+// the nearer of that and the return already in the outputs.
+struct InstancePass {
+  const void* dirs;         // float4 per ray, tile order
+  const float* poses;       // [n_env][12] sensor poses
+  int32_t n_env, n_rays;
+  const void* nodes;        // the instance's BVH
+  const void* tris;
+  int32_t width;
+  int32_t n_inst, k;
+  const float* inst_poses;  // [n_env][n_inst][12] world-from-local
+  float min_range;
+  float* out_range;
+  int32_t* out_tri;
+  int32_t* out_inst;        // may be null
+};
+
 struct alignas(16) BatchHeader {
   unsigned long long head;   // next packet to hand out (atomic)
   int64_t n_packets;

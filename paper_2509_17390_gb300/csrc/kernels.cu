@@ -240,6 +240,103 @@ __global__ void __maxnreg__(72) k_persistent(BatchHeader* __restrict__ hdr,
   if (COUNT) flush_counters<COUNT>(c_rays, c_nodes + tr.n_nodes, c_tris + tr.n_tris);
 }
 
+// Second pass over one item for instance k: every ray, moved into the
+// instance's frame by the inverse of its rigid pose (the float32 sequence of
+// fgl.h), is cast against the instance's BVH, pruned by the return found so
+// far, and replaces it only when strictly nearer (ties stay with the scene
+// and with lower instances).
+template <int W, bool TMIN>
+__global__ void __maxnreg__(72) k_instance_pass(const InstancePass a, int sdepth) {
+  using Keys = typename dev::KeyWords<W>::T;
+  const unsigned FULL = 0xFFFFFFFFu;
+  const Smem<W> sm = smem_layout<W>(sdepth);
+  const int lane = threadIdx.x & 31;
+  if (a.width != W) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&g_status, 2u);
+    return;
+  }
+  const int64_t total = (int64_t)a.n_env * a.n_rays;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool done = gid >= total;
+  int64_t o_idx = 0;
+  float cur_t = 0.f;
+  int32_t cur_id = -1;
+  dev::Tracer<W, false, TMIN> tr;
+  tr.tg = make_uint2(0u, 0u);
+  tr.ng = make_uint2(0u, 0u);
+  if (!done) {
+    const int env = (int)(gid / a.n_rays);
+    const int j = (int)(gid - (int64_t)env * a.n_rays);
+    const float4 ds = __ldg((const float4*)a.dirs + j);
+    o_idx = (int64_t)env * a.n_rays + __float_as_int(ds.w);
+    float ox, oy, oz, dx, dy, dz;
+    dev::world_ray(a.poses + 12 * (int64_t)env, ds, ox, oy, oz, dx, dy, dz);
+    const float* P = a.inst_poses + 12 * ((int64_t)env * a.n_inst + a.k);
+    float R[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) R[i] = __ldg(P + i);
+    const float u0 = __fsub_rn(ox, R[3]), u1 = __fsub_rn(oy, R[7]), u2 = __fsub_rn(oz, R[11]);
+    // o' = R^T u, d' = R^T d: column i of R against (u0, u1, u2)
+    float lo[3], ld[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      lo[i] = __fadd_rn(__fadd_rn(__fmul_rn(R[i], u0), __fmul_rn(R[4 + i], u1)), __fmul_rn(R[8 + i], u2));
+      ld[i] = __fadd_rn(__fadd_rn(__fmul_rn(R[i], dx), __fmul_rn(R[4 + i], dy)), __fmul_rn(R[8 + i], dz));
+    }
+    cur_t = a.out_range[o_idx];
+    cur_id = a.out_tri[o_idx];
+    dev::setup_ray(tr.r, lo[0], lo[1], lo[2], ld[0], ld[1], ld[2]);
+    tr.start(a.nodes, a.tris, a.min_range, cur_t);
+  }
+  uint2 ls[kStackLocal];
+  Keys lq[kStackLocal];
+  const dev::StackRefs<Keys> st{sm.ss, sm.sq, ls, lq, (int)blockDim.x, sdepth};
+  while (__any_sync(FULL, !done)) {
+    bool ok = true;
+    if (!done) ok = tr.descend(st);
+    dev::tri_phase_warp(tr, sm.keys, lane);
+    if (!done) {
+      if (!ok) {
+        atomicOr(&g_status, 1u);
+        done = true;
+      } else {
+        done = tr.finish(st);
+      }
+    }
+  }
+  if (gid < total) {
+    const bool take = tr.best_id != dev::kNoHit && (cur_id < 0 || tr.best_t < cur_t);
+    if (take) {
+      a.out_range[o_idx] = tr.best_t;
+      a.out_tri[o_idx] = tr.best_id;
+      if (a.out_inst) a.out_inst[o_idx] = a.k;
+    } else if (a.k == 0 && a.out_inst) {
+      a.out_inst[o_idx] = -1;
+    }
+  }
+}
+
+// World-frame return points: p_i = o_i + (t * d_i) (two roundings), NaN on a miss.
+__global__ void k_points(const float4* __restrict__ dirs, const float* __restrict__ poses,
+                         int n_env, int n_rays, const float* __restrict__ range,
+                         const int32_t* __restrict__ tri, float* __restrict__ out) {
+  const int64_t total = (int64_t)n_env * n_rays;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= total) return;
+  const int env = (int)(gid / n_rays);
+  const int j = (int)(gid - (int64_t)env * n_rays);
+  const float4 ds = __ldg(dirs + j);
+  const int64_t o = (int64_t)env * n_rays + __float_as_int(ds.w);
+  float ox, oy, oz, dx, dy, dz;
+  dev::world_ray(poses + 12 * (int64_t)env, ds, ox, oy, oz, dx, dy, dz);
+  const float t = range[o];
+  const bool hit = tri[o] >= 0;
+  const float nan = __int_as_float(0x7FC00000);
+  out[3 * o + 0] = hit ? __fadd_rn(ox, __fmul_rn(t, dx)) : nan;
+  out[3 * o + 1] = hit ? __fadd_rn(oy, __fmul_rn(t, dy)) : nan;
+  out[3 * o + 2] = hit ? __fadd_rn(oz, __fmul_rn(t, dz)) : nan;
+}
+
 __global__ void k_world_rays(const float4* __restrict__ dirs, const float* __restrict__ poses,
                              int n_env, int n_rays, float* __restrict__ out_o,
                              float* __restrict__ out_d) {
@@ -327,6 +424,31 @@ cudaError_t launch_persistent(int W, bool count, bool tmin, void* scratch, int g
   const ItemDesc* items = (const ItemDesc*)((char*)scratch + sizeof(BatchHeader));
   void* args[] = {&hdr, &items, &sdepth, &refill_min, &tri_mode, &postpone_pct};
   return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, s);
+}
+
+cudaError_t launch_instance_pass(const InstancePass& a, bool tmin, int block, int sdepth,
+                                 cudaStream_t s) {
+  const int64_t total = (int64_t)a.n_env * a.n_rays;
+  if (total == 0) return cudaSuccess;
+  void* fn;
+  if (a.width == 8) fn = tmin ? (void*)k_instance_pass<8, true> : (void*)k_instance_pass<8, false>;
+  else fn = tmin ? (void*)k_instance_pass<4, true> : (void*)k_instance_pass<4, false>;
+  const size_t smem = stack_smem_bytes(a.width, block, sdepth);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  InstancePass arg = a;
+  void* args[] = {&arg, &sdepth};
+  return cudaLaunchKernel(fn, dim3((unsigned)((total + block - 1) / block)), dim3(block), args, smem, s);
+}
+
+cudaError_t launch_points(const ItemDesc& it, float* out, cudaStream_t s) {
+  const int64_t total = (int64_t)it.n_env * it.n_rays;
+  if (total == 0) return cudaSuccess;
+  k_points<<<(unsigned)((total + 255) / 256), 256, 0, s>>>((const float4*)it.dirs, it.poses, it.n_env,
+                                                          it.n_rays, it.out_range, it.out_tri, out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_world_rays(const void* dirs, const float* poses, int n_env, int n_rays,

@@ -27,6 +27,14 @@ cudaError_t launch_persistent(int W, bool count, bool tmin, void* scratch, int g
                               int sdepth, int refill_min, int tri_mode, int postpone_pct,
                               cudaStream_t s);
 
+// Instance pass (see InstancePass in fgl_internal.h): one launch per item
+// and instance, after the scene pass.
+cudaError_t launch_instance_pass(const InstancePass& a, bool tmin, int block, int sdepth,
+                                 cudaStream_t s);
+
+// World-frame return points of one item, after its scene and instance passes.
+cudaError_t launch_points(const ItemDesc& it, float* out, cudaStream_t s);
+
 // Debug export of world rays (beam order).
 cudaError_t launch_world_rays(const void* dirs, const float* poses, int n_env, int n_rays,
                               float* out_o, float* out_d, cudaStream_t s);

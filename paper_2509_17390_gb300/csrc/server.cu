@@ -291,7 +291,7 @@ void worker_main(fgl_server_s* Sp) {
         if (q.cancel || q.env_next >= q.r.n_env || budget <= 0) continue;
         int64_t fit = budget / std::max<int32_t>(1, q.n_rays);
         int32_t chunk = (int32_t)std::min<int64_t>(q.r.n_env - q.env_next, std::max<int64_t>(1, fit));
-        fgl_cast_item it;
+        fgl_cast_item it{};
         it.scene = S.scenes[q.r.scene_id].scene;
         it.sensor = S.sensors[q.r.sensor_id].sensor;
         it.poses = q.d_poses + (size_t)q.env_next * 12;
@@ -312,7 +312,7 @@ void worker_main(fgl_server_s* Sp) {
         Request& q = *S.reqs[tk];
         if (q.cancel || q.env_next >= q.r.n_env) continue;
         for (int32_t e = 0; e < q.r.n_env; ++e) {
-          fgl_cast_item it;
+          fgl_cast_item it{};
           it.scene = S.scenes[q.r.scene_id].scene;
           it.sensor = S.sensors[q.r.sensor_id].sensor;
           it.poses = q.d_poses + (size_t)e * 12;

@@ -476,3 +476,70 @@ def test_validate_accepts_oracle_and_rejects_mistakes():
     assert box.any()
     far_r, far_i, _ = oracle.Scene(v[:8], t[:12]).cast(o[box], d[box], 100.0)
     assert not sc.validate(o[box], d[box], 100.0, far_r.astype(np.float32), far_i).any()
+
+
+# ---------------------------------------------------------------------------
+# per-environment rigid instances
+# ---------------------------------------------------------------------------
+def _rot_z(deg):
+    a = np.deg2rad(deg)
+    return np.array([[np.cos(a), -np.sin(a), 0], [np.sin(a), np.cos(a), 0], [0, 0, 1.0]])
+
+
+def test_instance_rays_identity_and_closed_form():
+    rng = np.random.default_rng(21)
+    o, d = random_rays(rng, 50)
+    P = np.tile(np.hstack([np.eye(3), np.zeros((3, 1))]).reshape(1, 12), (50, 1)).astype(np.float32)
+    lo, ld = oracle.instance_rays(o, d, P)
+    assert np.array_equal(lo, o) and np.array_equal(ld, d)
+    # a unit box turned 90 degrees about z and moved to (5, 2, 0): rays along +x at height 0.5
+    v, t = synth.aabb_box((0, 0, 0), (1, 1, 1), 1)
+    box = oracle.Scene(v, t, bvh=False)
+    pose = np.hstack([np.round(_rot_z(90), 12), [[5.0], [2.0], [0.0]]]).astype(np.float32)
+    # in the world the box occupies x in [4, 5], y in [2, 3]
+    o = np.array([[0.0, 2.25, 0.5], [0.0, 2.75, 0.25], [0.0, 3.5, 0.5]], np.float32)
+    d = np.tile(np.array([[1.0, 0.0, 0.0]], np.float32), (3, 1))
+    lo, ld = oracle.instance_rays(o, d, np.tile(pose.reshape(1, 12), (3, 1)))
+    r, ids, _ = box.cast(lo, ld, 100.0)
+    assert r[0] == 4.0 and r[1] == 4.0 and ids[2] == -1
+
+
+def test_instances_match_the_union_mesh_moved_in_fp64():
+    """Casting each instance in its own frame agrees with casting one mesh
+    made of the scene and the instances' vertices moved into the world."""
+    rng = np.random.default_rng(22)
+    vs, ts, obs = synth.tiny_room_scene(3)
+    uv, ut = synth.icosphere_unit(2)
+    sphere_v, sphere_t = (0.4 * uv).astype(np.float32), ut
+    box_v, box_t = synth.aabb_box((-0.3, -0.2, -0.25), (0.3, 0.2, 0.25), 2)
+    inst_mesh = [(sphere_v, sphere_t), (box_v, box_t)]
+    n_env, R = 3, 100.0
+    P = synth.sample_free_pose(rng, obs, n_env)
+    tab = synth.grid_sensor(8, -10, 10, 90)
+    dirs = oracle.sensor_dirs(tab.elev, tab.azim)
+    o, d = oracle.world_rays(dirs, P)
+    IP = np.zeros((n_env, 2, 3, 4), np.float32)
+    for e in range(n_env):
+        for k in range(2):
+            IP[e, k, :, :3] = _rot_z(rng.uniform(0, 360))
+            IP[e, k, :, 3] = P[e, :, 3] + rng.uniform(-2, 2, 3) * [1, 1, 0.3] + [0, 0, 0.2]
+    r, ids, inst, fl = oracle.cast_with_instances(oracle.Scene(vs, ts), [oracle.Scene(*m) for m in inst_mesh],
+                                                  o, d, IP, tab.n_rays, R)
+    assert (inst >= 0).sum() > 20                           # the instances are seen
+    for e in range(n_env):
+        parts_v, parts_t, base, offs = [vs.astype(np.float64)], [ts], len(vs), [0]
+        for k, (mv, mt) in enumerate(inst_mesh):
+            wv = mv.astype(np.float64) @ IP[e, k, :, :3].astype(np.float64).T + IP[e, k, :, 3]
+            parts_v.append(wv)
+            parts_t.append(mt + base)
+            offs.append(len(ts) + sum(len(x[1]) for x in inst_mesh[:k]))
+            base += len(mv)
+        U = oracle.Scene(np.concatenate(parts_v).astype(np.float32), np.concatenate(parts_t), bvh=False)
+        sl = slice(e * tab.n_rays, (e + 1) * tab.n_rays)
+        ru, iu, fu = U.cast(o[sl], d[sl], R)
+        ok = (fl[sl] == 0) & (fu == 0)
+        # world vertices rounded to float32 move surfaces by ~1e-7 m
+        np.testing.assert_allclose(r[sl][ok], ru[ok], rtol=1e-5, atol=1e-5)
+        gi = np.where(inst[sl] < 0, ids[sl], np.array(offs)[inst[sl] + 1] + ids[sl])
+        gi = np.where(ids[sl] < 0, -1, gi)
+        assert np.mean(gi[ok] == iu[ok]) > 0.999
