@@ -294,7 +294,7 @@ def main():
     ap.add_argument("--tri", type=int, default=0)
     ap.add_argument("--tile", type=str, default="")
     ap.add_argument("--workload", default="walk",
-                    choices=["walk", "hetero", "serve", "occupancy", "walk_instances"])
+                    choices=["walk", "hetero", "serve", "occupancy", "walk_instances", "lbvh"])
     ap.add_argument("--no-serve", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -313,6 +313,8 @@ def main():
         return run_occupancy(args)
     if args.workload == "walk_instances":
         return run_walk_instances(args)
+    if args.workload == "lbvh":
+        return run_lbvh(args)
 
     import torch
     import paper_2509_17390_gb300 as fgl
@@ -685,6 +687,100 @@ def run_walk_instances(args):
                            "l2": "flushed between timed steps (256 MiB write)"},
                 "without_instances_ms_per_step": round(tot0 * 1e3 / args.steps, 3),
                 "gpu_launches": args.steps * (1 + K + 1), "clocks": clocks}
+        print(json.dumps(line), flush=True)
+
+
+def run_lbvh(args):
+    """The paper's route on the batched walk: a triangle LBVH built on the GPU
+    and cast one thread per beam, against the host-built wide SAH BVH and its
+    persistent batched kernel; plus a dynamic-scene step (every vertex moved,
+    the LBVH rebuilt, then cast)."""
+    import torch
+    import paper_2509_17390_gb300 as fgl
+    from synth import workloads
+    ws, rank, local = dist_setup(args.gpus)
+    n_steps = args.warmup + args.steps
+    w = workloads.batched_walk(2, n_env=args.n_env, n_steps=min(n_steps, 100))
+    n_env, S = args.n_env, w.poses.shape[0]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.Stream(device=dev)
+    vd = torch.from_numpy(w.verts).to(dev)
+    td = torch.from_numpy(w.tris).to(dev)
+    # builds: GPU LBVH (synchronised, median of 5) vs host SAH + collapse
+    lb = fgl.Lbvh(vd, td, stream=stream)
+    bms = []
+    for _ in range(5):
+        lb.rebuild(vd, td, stream=stream)
+        bms.append(lb.stats()["build_ms"])
+    wide = fgl.Scene(w.verts, w.tris, width=args.width)
+    sensor = fgl.Sensor.from_table(w.sensor)
+    n_rays = n_env * sensor.n_rays
+    walk_d = torch.from_numpy(w.poses).to(dev)
+    pose = torch.empty((n_env, 3, 4), dtype=torch.float32, device=dev)
+    out_r = torch.empty(n_rays, dtype=torch.float32, device=dev)
+    out_i = torch.empty(n_rays, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    opts = fgl.BatchOpts(use_graph=1)
+    items = [(wide, sensor, pose, w.max_range, out_r, out_i)]
+    arr = fgl.make_items(items)
+    shift = torch.tensor([0.0, 0.0, 0.0], device=dev)
+
+    def cast_lbvh(s):
+        with torch.cuda.stream(stream):
+            pose.copy_(walk_d[s % S])
+        lb.cast(sensor, pose, w.max_range, out_range=out_r, out_tri=out_i, stream=stream)
+
+    def cast_wide(s):
+        with torch.cuda.stream(stream):
+            pose.copy_(walk_d[s % S])
+        fgl.cast_batched(items, opts, stream=stream, arr=arr)
+
+    def dynamic(s):
+        with torch.cuda.stream(stream):
+            pose.copy_(walk_d[s % S])
+            vd.add_(0.001)                      # every vertex moves
+        lb.rebuild(vd, td, stream=stream)
+        lb.cast(sensor, pose, w.max_range, out_range=out_r, out_tri=out_i, stream=stream)
+
+    def timed(fn):
+        for k in range(args.warmup):
+            fn(k)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        barrier(ws)
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(k & 0xFF)
+                ev[k][0].record(stream)
+            fn(args.warmup + k)
+            with torch.cuda.stream(stream):
+                ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        return barrier_max(sum(a.elapsed_time(b) for a, b in ev) / 1e3, ws)
+
+    with ClockSampler(local) as clk:
+        t_lbvh = timed(cast_lbvh)
+    clocks = clk.summary()
+    t_wide = timed(cast_wide)
+    t_dyn = timed(dynamic)
+    if rank == 0:
+        line = {"metric": "Grays/s @4096 envs x 1M tris, GPU-built triangle LBVH cast one thread per beam",
+                "value": round(ws * n_rays * args.steps / t_lbvh / 1e9, 4), "unit": UNIT, "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(t_lbvh * 1e3 / args.steps, 3), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "batched_walk (4096 envs x 5760 rays, 1,000,300 tris)",
+                           "l2": "flushed between timed steps (256 MiB write)"},
+                "lbvh_build_ms_median": round(float(np.median(bms)), 2),
+                "lbvh_depth": lb.stats()["depth"],
+                "wide_sah_build_ms_host": round(wide.stats()["build_ms"], 1),
+                "wide_batched": {"value": round(ws * n_rays * args.steps / t_wide / 1e9, 4), "unit": UNIT,
+                                 "ms_per_step": round(t_wide * 1e3 / args.steps, 3)},
+                "dynamic_rebuild_and_cast": {"ms_per_step": round(t_dyn * 1e3 / args.steps, 3),
+                                             "value": round(ws * n_rays * args.steps / t_dyn / 1e9, 4),
+                                             "unit": UNIT},
+                "gpu_launches": args.steps, "clocks": clocks}
         print(json.dumps(line), flush=True)
 
 

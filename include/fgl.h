@@ -283,6 +283,49 @@ fgl_status fgl_world_rays(fgl_sensor sensor, const float* poses, int32_t n_env, 
                           float* out_d, fgl_stream stream);
 
 /* ------------------------------------------------------------------------ */
+/* Triangle LBVH built on the GPU (paper Sec. IV-C with the LBVH routine of  */
+/* Sec. IV-A): for meshes that change every frame, and the paper's one-      */
+/* thread-per-beam traversal                                                 */
+/* ------------------------------------------------------------------------ */
+
+typedef struct fgl_lbvh_s* fgl_lbvh;
+
+typedef struct {
+  int64_t n_tris;
+  int64_t n_nodes;          /* internal nodes (n_tris - 1); leaves hold one triangle */
+  int32_t depth;            /* levels of the binary tree (root = 1) */
+  int32_t overflow;         /* 1 when a cast's traversal stack overflowed (returns then wrong) */
+  float build_ms;           /* host-observed build time of the last build, synchronised */
+  float margin;             /* outward margin of every leaf box (metres) */
+  float centroid_lo[3];     /* the box the Morton codes quantise (triangle centroids) */
+  float centroid_hi[3];
+} fgl_lbvh_stats;
+
+/* Build (or, with *out already set, rebuild in place) a triangle LBVH on the
+ * GPU from DEVICE arrays: verts float32 [nv][3], tris int32 [nt][3].
+ * Morton codes (eqs. u_i, m_i: 10 bits per axis of the centroid in the box of
+ * all centroids), a stable radix sort, the hierarchy from longest common
+ * prefixes (eq. LCP; equal codes ordered by position), then node boxes bottom
+ * up; leaf boxes are grown by 2^-17 max(1, max |coord|).  Synchronises
+ * `stream` at the end.  Errors: FGL_ERR_INVALID (empty mesh, nt >= 2^30, a
+ * vertex id out of range or a non-finite vertex), FGL_ERR_OOM, FGL_ERR_CUDA. */
+fgl_status fgl_lbvh_build(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
+                          fgl_stream stream, fgl_lbvh* out);
+fgl_status fgl_lbvh_destroy(fgl_lbvh lbvh);
+fgl_status fgl_lbvh_get_stats(fgl_lbvh lbvh, fgl_lbvh_stats* out);
+/* Host copies of the nodes (64 B each: both child boxes as floats, then int32
+ * left, right, parent, 0; a reference < 0 is ~leaf) and the triangles in
+ * Morton order (48 B each, as the wide BVH's leaf records). */
+fgl_status fgl_lbvh_export(fgl_lbvh lbvh, void* nodes, int64_t node_bytes, void* tris,
+                           int64_t tri_bytes);
+/* eq. t_j* over an LBVH, one thread per beam (the paper's form): the same
+ * returns, bit for bit, as fgl_cast on a wide BVH of the same mesh (same
+ * triangle test and (t, id) rule), t in [min_range, max_range]. */
+fgl_status fgl_cast_lbvh(fgl_lbvh lbvh, fgl_sensor sensor, const float* poses, int32_t n_env,
+                         float min_range, float max_range, float* out_range, int32_t* out_tri,
+                         fgl_stream stream);
+
+/* ------------------------------------------------------------------------ */
 /* Gaussian-to-occupancy conversion (paper Sec. IV-A)                        */
 /* ------------------------------------------------------------------------ */
 

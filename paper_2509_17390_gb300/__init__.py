@@ -20,7 +20,7 @@ from . import build_native
 
 __all__ = ["Scene", "Sensor", "BatchOpts", "cast", "cast_opts", "cast_batched",
            "cast_batched_host", "cast_batched_static", "autotune", "TuneOpts", "world_rays", "sync", "work_counters", "FglError", "lib",
-           "gaussian_density", "Gaussians", "Grid"]
+           "gaussian_density", "Gaussians", "Grid", "Lbvh"]
 
 FGL_OK, FGL_ERR_INVALID, FGL_ERR_OOM, FGL_ERR_CUDA = 0, 1, 2, 3
 FGL_ERR_BUDGET, FGL_ERR_TIMEOUT, FGL_ERR_CANCELLED, FGL_ERR_DEVICE = 4, 5, 6, 7
@@ -110,6 +110,11 @@ def lib():
                 "fgl_work_counters": ([P, P, P], I32),
                 "fgl_world_rays": ([P, P, I32, P, P, P], I32),
                 "fgl_gaussian_density": ([P, P, F32, P, P, P, P, P], I32),
+                "fgl_lbvh_build": ([P, I64, P, I64, P, P], I32),
+                "fgl_lbvh_destroy": ([P], I32),
+                "fgl_lbvh_get_stats": ([P, P], I32),
+                "fgl_lbvh_export": ([P, P, I64, P, I64], I32),
+                "fgl_cast_lbvh": ([P, P, P, I32, F32, F32, P, P, P], I32),
                 "fgl_last_error": ([], ctypes.c_char_p),
                 "fgl_version": ([], I32),
             }
@@ -401,6 +406,72 @@ def world_rays(sensor: Sensor, poses, stream=None):
 def sync(stream=None):
     """Wait for the stream and surface asynchronous / device-side errors."""
     _check(lib().fgl_sync(_stream_handle(stream)))
+
+
+class LbvhStats(ctypes.Structure):
+    _fields_ = [("n_tris", I64), ("n_nodes", I64), ("depth", I32), ("overflow", I32),
+                ("build_ms", F32), ("margin", F32), ("centroid_lo", F32 * 3), ("centroid_hi", F32 * 3)]
+
+
+class Lbvh:
+    """A triangle LBVH built on the GPU from CUDA tensors (fgl_lbvh_build):
+    verts float32 [nv, 3], tris int32 [nt, 3].  rebuild() refits it to moved
+    vertices (a full rebuild into the same buffers)."""
+
+    def __init__(self, verts, tris, stream=None):
+        self._h = P()
+        self._nt = 0
+        self.rebuild(verts, tris, stream)
+
+    def rebuild(self, verts, tris, stream=None):
+        nv = verts.numel() // 3
+        nt = tris.numel() // 3
+        _check(lib().fgl_lbvh_build(_dev_ptr(verts, "float32", 3 * nv, "verts"), nv,
+                                    _dev_ptr(tris, "int32", 3 * nt, "tris"), nt,
+                                    _stream_handle(stream), ctypes.byref(self._h)))
+        self._nt = nt
+
+    @property
+    def handle(self):
+        return self._h
+
+    def stats(self) -> dict:
+        st = LbvhStats()
+        _check(lib().fgl_lbvh_get_stats(self._h, ctypes.byref(st)))
+        return {"n_tris": st.n_tris, "n_nodes": st.n_nodes, "depth": st.depth, "overflow": st.overflow,
+                "build_ms": st.build_ms, "margin": st.margin,
+                "centroid_lo": list(st.centroid_lo), "centroid_hi": list(st.centroid_hi)}
+
+    def export(self):
+        """(nodes uint8 [n_nodes*64], tris float32 [nt, 12]) host copies."""
+        n_nodes = max(0, self._nt - 1)
+        nodes = np.empty(n_nodes * 64, np.uint8)
+        tris = np.empty((self._nt, 12), np.float32)
+        _check(lib().fgl_lbvh_export(self._h, _np_ptr(nodes), nodes.nbytes, _np_ptr(tris), tris.nbytes))
+        return nodes, tris
+
+    def cast(self, sensor: "Sensor", poses, max_range: float, min_range: float = 0.0,
+             out_range=None, out_tri=None, stream=None):
+        """eq. t_j* over the LBVH, one thread per beam (fgl_cast_lbvh)."""
+        n_env = poses.shape[0] if poses.dim() == 3 else poses.numel() // 12
+        n = n_env * sensor.n_rays
+        out_range, out_tri = _outputs(n, poses.device, out_range, out_tri)
+        _check(lib().fgl_cast_lbvh(self._h, sensor.handle, _dev_ptr(poses, "float32", n_env * 12, "poses"),
+                                   n_env, float(min_range), float(max_range),
+                                   _dev_ptr(out_range, "float32", n, "out_range"),
+                                   _dev_ptr(out_tri, "int32", n, "out_tri"), _stream_handle(stream)))
+        return out_range, out_tri
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fgl_lbvh_destroy(self._h)
+            self._h = P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Gaussians(ctypes.Structure):

@@ -684,6 +684,23 @@ fgl_status fgl_cast_opts(fgl_scene scene, fgl_sensor sensor, const float* poses,
   return FGL_OK;
 }
 
+fgl_status fgl_cast_lbvh(fgl_lbvh lbvh, fgl_sensor sensor, const float* poses, int32_t n_env,
+                         float min_range, float max_range, float* out_range, int32_t* out_tri,
+                         fgl_stream stream) {
+  if (!lbvh || !sensor) return fail(FGL_ERR_INVALID, "null LBVH or sensor");
+  if (n_env < 0) return fail(FGL_ERR_INVALID, "n_env < 0");
+  if (!(std::isfinite(max_range) && max_range > 0.f))
+    return fail(FGL_ERR_INVALID, "max_range must be finite and > 0");
+  if (!(min_range >= 0.f && min_range < max_range))
+    return fail(FGL_ERR_INVALID, "min_range must satisfy 0 <= min_range < max_range");
+  if (n_env > 0 && (!poses || !out_range || !out_tri))
+    return fail(FGL_ERR_INVALID, "null poses or output pointer");
+  if (n_env == 0) return FGL_OK;
+  FGL_CUDA(launch_lbvh_cast(lbvh, sensor->d_dirs, poses, n_env, sensor->n_rays, min_range, max_range,
+                            out_range, out_tri, (cudaStream_t)stream));
+  return FGL_OK;
+}
+
 fgl_status fgl_cast_batched(const fgl_cast_item* items, int32_t n_items, const fgl_batch_opts* opts,
                             fgl_stream stream) {
   if (n_items < 0) return fail(FGL_ERR_INVALID, "n_items < 0");

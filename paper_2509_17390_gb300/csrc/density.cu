@@ -8,9 +8,9 @@
 //                  (the exact operation sequence of fgl.h), the count of
 //                  covered tiles, and the density parameters (mean, alpha^2,
 //                  the inverse covariance pre-scaled for exp2);
-//   scan           exclusive prefix sum of the counts -> pair offsets;
+//   scan           exclusive prefix sum of the counts -> pair offsets (sort.cu);
 //   k_emit         (tile, Gaussian) pairs, in Gaussian order;
-//   radix sort     stable LSD sort of the pairs by tile (8-bit digits), so
+//   radix sort     stable LSD sort of the pairs by tile (8-bit digits, sort.cu), so
 //                  every tile's candidates end up in increasing Gaussian
 //                  index and the float32 sums are deterministic;
 //   k_tile_bounds  begin/end of every tile's candidate run;
@@ -35,6 +35,7 @@
 #include "fgl.h"
 #include "fgl_internal.h"
 #include "ptx_ops.cuh"
+#include "sort.h"
 
 namespace fgl {
 void record_error(int status, const char* msg);
@@ -157,51 +158,6 @@ __global__ void k_gauss_prep(const float* __restrict__ mu, const float* __restri
 }
 
 // ---------------------------------------------------------------------------
-// exclusive scan (in place), 2048 items per block, recursive over block sums
-// ---------------------------------------------------------------------------
-template <class T>
-__global__ void k_scan_blocks(T* __restrict__ x, int64_t n, T* __restrict__ sums) {
-  __shared__ T warp_tot[32];
-  const int64_t base = (int64_t)blockIdx.x * 2048;
-  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-  const int64_t i0 = base + 2 * t;
-  T a = i0 < n ? x[i0] : T(0);
-  T b = i0 + 1 < n ? x[i0 + 1] : T(0);
-  T v = a + b;  // inclusive warp scan of pair sums
-  T incl = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    T u = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-    if (lane >= o) incl += u;
-  }
-  if (lane == 31) warp_tot[wid] = incl;
-  __syncthreads();
-  if (wid == 0) {
-    T w = warp_tot[lane];
-    T wi = w;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      T u = __shfl_up_sync(0xFFFFFFFFu, wi, o);
-      if (lane >= o) wi += u;
-    }
-    warp_tot[lane] = wi - w;  // exclusive warp offsets
-    if (lane == 31 && sums) sums[blockIdx.x] = wi;
-  }
-  __syncthreads();
-  const T excl = warp_tot[wid] + incl - v;
-  if (i0 < n) x[i0] = excl;
-  if (i0 + 1 < n) x[i0 + 1] = excl + a;
-}
-
-template <class T>
-__global__ void k_scan_add(T* __restrict__ x, int64_t n, const T* __restrict__ sums) {
-  const int64_t i = (int64_t)blockIdx.x * 2048 + threadIdx.x;
-  const T add = sums[blockIdx.x];
-  if (i < n) x[i] += add;
-  if (i + 1024 < n) x[i + 1024] += add;
-}
-
-// ---------------------------------------------------------------------------
 // pairs, stable radix sort by tile, tile bounds
 // ---------------------------------------------------------------------------
 // One warp per 32 consecutive Gaussians: the warp writes each Gaussian's
@@ -237,75 +193,6 @@ __global__ void k_emit(const int4* __restrict__ ranges, const unsigned long long
       keys[o + p] = (uint32_t)(((lz + c) * g.ntiles[1] + (ly + b)) * g.ntiles[0] + (lx + a));
       vals[o + p] = gid;
     }
-  }
-}
-
-constexpr int kSortThreads = 256;
-constexpr int kSortRounds = 16;  // items per block = 256 * 16
-
-__global__ void k_radix_hist(const uint32_t* __restrict__ keys, int64_t n, int shift,
-                             uint32_t* __restrict__ hist, int nblocks) {
-  __shared__ uint32_t h[256];
-  h[threadIdx.x] = 0;
-  __syncthreads();
-  const int64_t base = (int64_t)blockIdx.x * (kSortThreads * kSortRounds);
-  for (int r = 0; r < kSortRounds; ++r) {
-    const int64_t i = base + r * kSortThreads + threadIdx.x;
-    if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
-  }
-  __syncthreads();
-  hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
-}
-
-// Stable scatter.  Each warp owns a contiguous run of kSortRounds * 32 items
-// (warp w of the block: items [w*R*32, (w+1)*R*32) of the block's slice), so
-// index order is (warp, round, lane).  Pass 1 counts each warp's digits with
-// __match_any_sync; one block barrier turns those counts into per-warp bases;
-// pass 2 ranks every item inside its warp (earlier rounds, then lower lanes
-// in the same round) and writes it out.
-__global__ void k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
-                                int64_t n, int shift, const uint32_t* __restrict__ offs,
-                                int nblocks, uint32_t* __restrict__ kout,
-                                uint32_t* __restrict__ vout) {
-  constexpr int NW = kSortThreads / 32;
-  __shared__ uint32_t wbase[NW][256];  // digit counts, then per-warp base offsets
-  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  for (int k = 0; k < NW; ++k) wbase[k][t] = 0;
-  __syncthreads();
-  const int64_t base = (int64_t)blockIdx.x * (kSortThreads * kSortRounds) +
-                       (int64_t)w * (32 * kSortRounds);
-  const unsigned lt = (1u << lane) - 1u;
-  for (int r = 0; r < kSortRounds; ++r) {
-    const int64_t i = base + r * 32 + lane;
-    const uint32_t d = i < n ? (kin[i] >> shift) & 255u : 256u;
-    const unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
-    if (d < 256u && __popc(peers & lt) == 0) wbase[w][d] += __popc(peers);
-    __syncwarp();
-  }
-  __syncthreads();
-  {
-    // thread t = digit t: exclusive prefix over warps, plus the block's global offset
-    uint32_t run = offs[(int64_t)t * nblocks + blockIdx.x];
-    for (int k = 0; k < NW; ++k) {
-      const uint32_t c = wbase[k][t];
-      wbase[k][t] = run;
-      run += c;
-    }
-  }
-  __syncthreads();
-  for (int r = 0; r < kSortRounds; ++r) {
-    const int64_t i = base + r * 32 + lane;
-    const uint32_t key = i < n ? kin[i] : 0u;
-    const uint32_t d = i < n ? (key >> shift) & 255u : 256u;
-    const unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
-    if (d < 256u) {
-      const uint32_t pos = wbase[w][d] + __popc(peers & lt);
-      kout[pos] = key;
-      vout[pos] = vin[i];
-    }
-    __syncwarp();
-    if (d < 256u && __popc(peers & lt) == 0) wbase[w][d] += __popc(peers);
-    __syncwarp();
   }
 }
 
@@ -499,39 +386,6 @@ fgl_status cuda_err(cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_err(e_, #call); \
   } while (0)
 
-// exclusive scan of n values in place; `tmp` holds the per-level block sums
-template <class T>
-cudaError_t scan_exclusive(T* x, int64_t n, T* tmp, size_t tmp_elems, cudaStream_t s,
-                           int* launches) {
-  if (n <= 0) return cudaSuccess;
-  const int64_t nb = (n + 2047) / 2048;
-  if (nb == 1) {
-    k_scan_blocks<T><<<1, 1024, 0, s>>>(x, n, (T*)nullptr);
-    ++*launches;
-    return cudaGetLastError();
-  }
-  if ((size_t)nb > tmp_elems) return cudaErrorInvalidValue;
-  k_scan_blocks<T><<<(unsigned)nb, 1024, 0, s>>>(x, n, tmp);
-  ++*launches;
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  e = scan_exclusive<T>(tmp, nb, tmp + nb, tmp_elems - nb, s, launches);
-  if (e != cudaSuccess) return e;
-  k_scan_add<T><<<(unsigned)nb, 1024, 0, s>>>(x, n, tmp);
-  ++*launches;
-  return cudaGetLastError();
-}
-
-// block sums needed by scan_exclusive over n values, all levels
-size_t scan_tmp_elems(int64_t n) {
-  size_t t = 0;
-  while (n > 2048) {
-    n = (n + 2047) / 2048;
-    t += (size_t)n;
-  }
-  return t + 1;
-}
-
 }  // namespace
 
 extern "C" fgl_status fgl_gaussian_density(const fgl_gaussians* gs, const fgl_grid* grid,
@@ -596,8 +450,7 @@ extern "C" fgl_status fgl_gaussian_density(const fgl_gaussians* gs, const fgl_gr
     ++launches;
     DCUDA(cudaGetLastError());
     DCUDA(cudaMemsetAsync(counts + n, 0, sizeof(unsigned long long), s));
-    DCUDA(scan_exclusive<unsigned long long>(counts, n + 1, (unsigned long long*)S.sums, tmp_g, s,
-                                             &launches));
+    DCUDA(scan_exclusive_u64(counts, n + 1, (unsigned long long*)S.sums, tmp_g, s, &launches));
     DCUDA(cudaMemcpyAsync(&n_pairs, counts + n, sizeof(n_pairs), cudaMemcpyDeviceToHost, s));
     DCUDA(cudaStreamSynchronize(s));
     if (n_pairs >= ((uint64_t)1 << 31))
@@ -617,23 +470,13 @@ extern "C" fgl_status fgl_gaussian_density(const fgl_gaussians* gs, const fgl_gr
     // stable LSD radix sort by tile id
     int bits = 1;
     while (((int64_t)1 << bits) < n_tiles) ++bits;
-    const int items = kSortThreads * kSortRounds;
-    const int nblocks = (int)((n_pairs + items - 1) / items);
-    const int64_t nh = (int64_t)256 * nblocks;
-    const size_t tmp_h = scan_tmp_elems(nh);
-    DCUDA(ensure(&S.hist, &S.hist_cap, (size_t)(nh + tmp_h) * sizeof(uint32_t), s));
-    uint32_t* hist = (uint32_t*)S.hist;
-    for (int shift = 0; shift < bits; shift += 8) {
-      k_radix_hist<<<nblocks, kSortThreads, 0, s>>>(k0, (int64_t)n_pairs, shift, hist, nblocks);
-      ++launches;
-      DCUDA(cudaGetLastError());
-      DCUDA(scan_exclusive<uint32_t>(hist, nh, hist + nh, tmp_h, s, &launches));
-      k_radix_scatter<<<nblocks, kSortThreads, 0, s>>>(k0, v0, (int64_t)n_pairs, shift, hist,
-                                                      nblocks, k1, v1);
-      ++launches;
-      DCUDA(cudaGetLastError());
-      std::swap(k0, k1);
-      std::swap(v0, v1);
+    DCUDA(ensure(&S.hist, &S.hist_cap, radix_sort_tmp_elems((int64_t)n_pairs) * sizeof(uint32_t), s));
+    bool second = false;
+    DCUDA(radix_sort_pairs(k0, v0, k1, v1, (int64_t)n_pairs, bits, (uint32_t*)S.hist, s, &launches,
+                           &second));
+    if (second) {
+      k0 = k1;
+      v0 = v1;
     }
     k_tile_bounds<<<(unsigned)((n_pairs + 255) / 256), 256, 0, s>>>(k0, (int64_t)n_pairs, begin,
                                                                      end);

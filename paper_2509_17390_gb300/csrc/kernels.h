@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include "fgl.h"
 #include "fgl_internal.h"
 
 namespace fgl {
@@ -34,6 +35,11 @@ cudaError_t launch_instance_pass(const InstancePass& a, bool tmin, int block, in
 
 // World-frame return points of one item, after its scene and instance passes.
 cudaError_t launch_points(const ItemDesc& it, float* out, cudaStream_t s);
+
+// One-thread-per-ray cast over a GPU-built triangle LBVH (lbvh.cu).
+cudaError_t launch_lbvh_cast(const fgl_lbvh_s* L, const void* dirs, const float* poses, int n_env,
+                             int n_rays, float min_range, float max_range, float* out_range,
+                             int32_t* out_tri, cudaStream_t s);
 
 // Debug export of world rays (beam order).
 cudaError_t launch_world_rays(const void* dirs, const float* poses, int n_env, int n_rays,
