@@ -1,11 +1,12 @@
-"""FP64 CPU oracle for first-hit LiDAR ray casting (paper Sec. IV-C) and for
-the Gaussian-to-occupancy conversion (Sec. IV-A).
+"""FP64 CPU oracle for first-hit LiDAR ray casting (paper Sec. IV-C), for
+the Gaussian-to-occupancy conversion (Sec. IV-A) and for the mesh
+reconstruction steps (Sec. IV-B: denoising, narrow-band TSDF, isosurface).
 
 TEST INFRASTRUCTURE ONLY: imported by tests/, ``__graft_entry__.smoke()`` and
 the CPU-baseline leg of ``bench.py``; never by the library it checks.  It
 shares no code with ``paper_2509_17390_gb300``.
 
-The C++ sources (``oracle.cpp``, ``density.cpp``) are compiled on first use
+The C++ sources (``oracle.cpp``, ``density.cpp``, ``tsdf.cpp``) are compiled on first use
 (or by ``build()``) with ``-ffp-contract=off`` into ``oracle/_build/liboracle.so``.
 """
 
@@ -21,6 +22,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.cpp")
 _SRC_DENSITY = os.path.join(_HERE, "density.cpp")
+_SRC_TSDF = os.path.join(_HERE, "tsdf.cpp")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
@@ -32,11 +34,11 @@ FLAG_EDGE, FLAG_TIE, FLAG_RANGE = 1, 2, 4
 def build(force: bool = False) -> str:
     """Compile liboracle.so (g++, FP64, no FMA contraction)."""
     os.makedirs(_BUILD, exist_ok=True)
-    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_DENSITY))
+    newest = max(os.path.getmtime(f) for f in (_SRC, _SRC_DENSITY, _SRC_TSDF))
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-               "-shared", "-pthread", _SRC, _SRC_DENSITY, "-o", tmp]
+               "-shared", "-pthread", _SRC, _SRC_DENSITY, _SRC_TSDF, "-o", tmp]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -65,6 +67,13 @@ def lib():
             L.orc_gauss_tile_ranges.argtypes = [P, P, P, I64, P, ctypes.c_float, I32, P]
             L.orc_density.argtypes = [P, P, P, P, I64, P, ctypes.c_float, P, I32, I32, P, P]
             L.orc_occupancy.argtypes = [P, P, D, P, P]
+            F = ctypes.c_float
+            L.orc_blur.argtypes = [P, I64, I64, I64, D, I32, P]
+            L.orc_outside.argtypes = [P, I64, I64, I64, P]
+            L.orc_shell.argtypes = [P, I64, I64, I64, I32, P]
+            L.orc_tsdf.argtypes = [P, P, I64, F, F, P]
+            L.orc_marching_tets.argtypes = [P, I64, I64, I64, P, F, F, I32, I32, P, P, P, P, P]
+            L.orc_tsdf_free.argtypes = [P]
             _lib = L
     return _lib
 
@@ -269,3 +278,129 @@ def density_tolerance(D, A):
     at least 1 cm: |dq| <= 1e-4 sqrt(q), and max_q exp(-q/2) sqrt(q)/2 < 0.43,
     plus the exponential's own error), and the float32 sum adds 1e-6 relative."""
     return 3e-5 * np.asarray(A) + 1e-6 * np.abs(np.asarray(D)) + 1e-9
+
+
+# ---------------------------------------------------------------------------
+# Mesh reconstruction (Sec. IV-B)
+# ---------------------------------------------------------------------------
+
+def blur_radius(sigma_vox: float) -> int:
+    """Taps of the eq. V' kernel on each side: ceil(3 sigma) (sigma in voxels)."""
+    return int(np.ceil(3.0 * float(sigma_vox)))
+
+
+def blur(V, sigma_vox: float, radius: int | None = None):
+    """Eq. V': the normalised Gaussian of sigma_vox voxels (radius taps a side,
+    default ceil(3 sigma)) over a binary grid [nz, ny, nx], 0 outside; FP64."""
+    V = np.ascontiguousarray(V, np.uint8)
+    nz, ny, nx = V.shape
+    R = blur_radius(sigma_vox) if radius is None else int(radius)
+    out = np.empty(V.shape, np.float64)
+    rc = lib().orc_blur(_ptr(V), nx, ny, nz, float(sigma_vox), R, _ptr(out))
+    if rc:
+        raise ValueError("orc_blur: bad arguments")
+    return out
+
+
+def rethreshold(Vp, mode: str, value: float):
+    """Eq. rethresh: V~ = [V' >= tau] (mode "fixed", value tau) or
+    [V' >= Quantile_q(V')] (mode "quantile", value q), the quantile being the
+    order statistic of rank floor(q (N - 1)) in ascending order.  Returns
+    (V~ u8, threshold)."""
+    Vp = np.asarray(Vp)
+    if mode == "fixed":
+        thr = float(value)
+    elif mode == "quantile":
+        flat = np.sort(Vp.ravel())
+        thr = float(flat[int(np.floor(float(value) * (flat.size - 1)))])
+    else:
+        raise ValueError(mode)
+    return (Vp >= thr).astype(np.uint8), thr
+
+
+def outside(V):
+    """Sign of eq. phi: 1 where the flood fill over free voxels from the padded
+    frame reaches, else 0 ([nz, ny, nx] u8)."""
+    V = np.ascontiguousarray(V, np.uint8)
+    nz, ny, nx = V.shape
+    out = np.empty(V.shape, np.uint8)
+    if lib().orc_outside(_ptr(V), nx, ny, nz, _ptr(out)):
+        raise ValueError("orc_outside: bad arguments")
+    return out
+
+
+def shell(V, L: int):
+    """First-arrival shell index p(x) from eq. S_0, shells up to L; 255 beyond."""
+    V = np.ascontiguousarray(V, np.uint8)
+    nz, ny, nx = V.shape
+    p = np.empty(V.shape, np.uint8)
+    if lib().orc_shell(_ptr(V), nx, ny, nz, int(L), _ptr(p)):
+        raise ValueError("orc_shell: bad arguments")
+    return p
+
+
+def band_layers(h: float, r: float) -> int:
+    """Shells needed for the band: ceil(r / h) (a voxel first reached later has
+    (p + 1/2) h > r and is clipped anyway)."""
+    return int(np.ceil(np.float64(np.float32(r)) / np.float64(np.float32(h))))
+
+
+def tsdf(V, h: float, r: float):
+    """Eq. phi = clip(s (p + 1/2) h, -r, r) for a surface grid V [nz, ny, nx];
+    returns (phi f32, outside u8, p u8)."""
+    V = np.ascontiguousarray(V, np.uint8)
+    L = min(band_layers(h, r), 254)
+    out = outside(V)
+    p = shell(V, L)
+    phi = np.empty(V.shape, np.float32)
+    if lib().orc_tsdf(_ptr(out), _ptr(p), V.size, float(h), float(r), _ptr(phi)):
+        raise ValueError("orc_tsdf: bad arguments")
+    return phi, out, p
+
+
+def marching_tets(phi, origin, h: float, iso: float = 0.0, step: int = 1, normals: bool = False):
+    """The phi = iso level set by marching tetrahedra (canonical vertex and
+    triangle order, normals towards phi >= iso).  Returns (verts f32 [nv, 3],
+    tris i32 [nt, 3], normals f32 [nv, 3] or None)."""
+    phi = np.ascontiguousarray(phi, np.float32)
+    nz, ny, nx = phi.shape
+    o = np.ascontiguousarray(origin, np.float32)
+    pv, pt, pn = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    nv, nt = ctypes.c_int64(), ctypes.c_int64()
+    L = lib()
+    rc = L.orc_marching_tets(_ptr(phi), nx, ny, nz, _ptr(o), float(h), float(iso), int(step),
+                             int(bool(normals)), ctypes.byref(pv), ctypes.byref(nv), ctypes.byref(pt),
+                             ctypes.byref(nt), ctypes.byref(pn) if normals else None)
+    if rc:
+        raise ValueError("orc_marching_tets: bad arguments")
+    try:
+        verts = np.ctypeslib.as_array(ctypes.cast(pv, ctypes.POINTER(ctypes.c_float)),
+                                      (max(nv.value, 1) * 3,))[:nv.value * 3].reshape(-1, 3).copy()
+        tris = np.ctypeslib.as_array(ctypes.cast(pt, ctypes.POINTER(ctypes.c_int32)),
+                                     (max(nt.value, 1) * 3,))[:nt.value * 3].reshape(-1, 3).copy()
+        nrm = None
+        if normals:
+            nrm = np.ctypeslib.as_array(ctypes.cast(pn, ctypes.POINTER(ctypes.c_float)),
+                                        (max(nv.value, 1) * 3,))[:nv.value * 3].reshape(-1, 3).copy()
+    finally:
+        L.orc_tsdf_free(pv)
+        L.orc_tsdf_free(pt)
+        if normals:
+            L.orc_tsdf_free(pn)
+    return verts, tris, nrm
+
+
+def blur_tolerance(radius: int) -> float:
+    """Absolute tolerance of a float32 eq. V' (values in [0, 1]): three passes
+    of 2R + 1 float32 products and sums, each within 2^-24 relative, on
+    partial sums at most 1, plus the weights' own float32 rounding."""
+    return 4.0 * 3 * (2 * radius + 2) * 2.0 ** -24
+
+
+def vertex_tolerance(verts, h: float) -> float:
+    """Absolute tolerance on a float32 marching-tetrahedra vertex: the voxel
+    centre (o + (i + 1/2) h) and the step along the edge each round a few
+    times at the coordinate's magnitude; tau's own float32 error moves the
+    vertex by at most 4 ulp of h."""
+    mag = float(np.max(np.abs(verts))) if len(verts) else 1.0
+    return 8 * 2.0 ** -24 * max(mag, 1.0) + 8 * 2.0 ** -24 * float(h)
