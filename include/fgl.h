@@ -55,7 +55,8 @@ typedef enum {
   FGL_ERR_BUDGET = 4,    /* serving: request larger than the HBM budget */
   FGL_ERR_TIMEOUT = 5,   /* serving: wait timed out */
   FGL_ERR_CANCELLED = 6, /* serving: request cancelled */
-  FGL_ERR_DEVICE = 7     /* a kernel reported an error (traversal stack overflow) */
+  FGL_ERR_DEVICE = 7,    /* a kernel reported an error (traversal stack overflow) */
+  FGL_ERR_CAPACITY = 8   /* output buffers too small; the needed counts are reported */
 } fgl_status;
 
 typedef struct fgl_scene_s* fgl_scene;
@@ -389,6 +390,96 @@ typedef struct {
 fgl_status fgl_gaussian_density(const fgl_gaussians* gaussians, const fgl_grid* grid, float theta,
                                 float* out_density, uint8_t* out_occ, uint8_t* out_surf,
                                 fgl_density_stats* stats, fgl_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* Mesh reconstruction (Sec. IV-B)                                           */
+/* ------------------------------------------------------------------------ */
+/* The steps between the surface-only occupancy (fgl_gaussian_density's
+ * out_surf) and a triangle mesh: binary denoising and re-thresholding, the
+ * narrow-band TSDF and its level set.  Grids are fgl_grid (tile ignored);
+ * every voxel array is [dims[2]][dims[1]][dims[0]] contiguous device memory.
+ * The voxel spacing is isotropic, so the paper's v_min is h.  Each call keeps
+ * grow-only scratch per stream. */
+
+/* Eq. V' then eq. rethresh:
+ *   V'(x) = sum over k in [-R, R]^3 of w(k_x) w(k_y) w(k_z) V(x + k), V = 0
+ *           outside the grid and 1 where the byte is nonzero,
+ *   w(j)  = exp(-j^2 / (2 s^2)) / sum_{|i| <= R} exp(-i^2 / (2 s^2)),
+ *   s = sigma / h voxels, R = ceil(3 s) (at most 32);
+ *   mask  = V' >= tau (mode 0, value = tau), or V' >= the order statistic of
+ *           V' of rank floor(q (N - 1)) in ascending order (mode 1, value =
+ *           q in [0, 1]; exact, chosen among the float32 V' values).
+ * V' is computed in float32 (weights rounded from FP64, three passes x, y,
+ * z, taps summed in ascending order).
+ *   surf: u8 voxels (in); out_blur: float V' (may be NULL); out_mask: u8 0/1;
+ *   out_threshold: HOST float receiving the threshold used (may be NULL; in
+ *   quantile mode this synchronises the stream).
+ * Errors: FGL_ERR_INVALID (null pointers, bad grid, sigma <= 0 or too large,
+ * mode, non-finite value, q outside [0, 1]), FGL_ERR_CUDA. */
+fgl_status fgl_denoise(const uint8_t* surf, const fgl_grid* grid, float sigma, int32_t mode,
+                       float value, float* out_blur, uint8_t* out_mask, float* out_threshold,
+                       fgl_stream stream);
+
+typedef struct {
+  int32_t timing;        /* in: 1 = time the call with CUDA events (synchronises the stream) */
+  int32_t n_layers;      /* out: shells grown, L = ceil(trunc / h) */
+  int32_t n_launches;    /* out: kernels the call launched */
+  float ms_total;        /* out (timing): first to last launch */
+} fgl_tsdf_stats;
+
+/* The narrow-band TSDF of a surface grid V (nonzero byte = surface voxel):
+ *   sign   s = +1 on the free voxels (V = 0) reached from a one-voxel free
+ *          frame around the grid through face neighbours over free voxels,
+ *          s = -1 elsewhere (surface voxels and enclosed voids);
+ *   shells S_0 = voxels with a face neighbour inside the grid whose V
+ *          differs (eq. S_0); S_m adds the face neighbours of S_{m-1};
+ *          p(x) = first m with x in S_m, for m <= L = ceil(trunc / h);
+ *   phi    = s * min((p + 1/2) h, trunc), and s * trunc where p > L (eq. phi;
+ *          the half voxel places the zero crossing between the two sides of
+ *          S_0 instead of on grid points).
+ * phi is float32 and exact: (p + 1/2) h rounds once.
+ *   out_phi: float [N]; out_outside: u8 s > 0 (may be NULL); out_shell: u8
+ *   p, 255 beyond L (may be NULL); stats may be NULL.
+ * Asynchronous unless stats->timing.  Errors: FGL_ERR_INVALID (null pointers,
+ * bad grid, more than 2^31 - 2 voxels, trunc <= 0, L > 254), FGL_ERR_CUDA,
+ * FGL_ERR_DEVICE (reported by the next call on the stream: a union-find
+ * loop hit its N + 2 step bound, which correct input cannot cause). */
+fgl_status fgl_tsdf(const uint8_t* surf, const fgl_grid* grid, float trunc, float* out_phi,
+                    uint8_t* out_outside, uint8_t* out_shell, fgl_tsdf_stats* stats,
+                    fgl_stream stream);
+
+/* The level set phi = iso by marching tetrahedra on the samples of every
+ * step-th voxel (paper's mc_step); sample (i, j, k) is voxel (i, j, k) * step
+ * with centre origin + ((i step + 1/2) h, ...).  Each cube of eight samples
+ * (corner c = dx + 2 dy + 4 dz) splits into the six tetrahedra (0,1,3,7),
+ * (0,1,5,7), (0,2,3,7), (0,2,6,7), (0,4,5,7), (0,4,6,7); a sample is inside
+ * when phi < iso (NaN counts as outside).  Output order (canonical, so the
+ * mesh is reproducible bit for bit):
+ *   vertices  one per sample edge a -> a + d (d of type t = dx + 2 dy + 4 dz,
+ *             t = 1..7) whose ends disagree, by sample index then t, at
+ *             P(a) + tau (P(a + d) - P(a)), tau = (iso - phi_a) / (phi_b - phi_a);
+ *   triangles by cube (its lowest sample), tetrahedron, then: one corner on
+ *             its own side -> the triangle on its three edges (the others in
+ *             tetrahedron order); two inside (a, b) and two outside (c, d) ->
+ *             (ac, ad, bd), (ac, bd, bc); a triangle whose normal through the
+ *             edge midpoints points against (outside corners - inside corners)
+ *             has its last two vertices swapped: normals face phi >= iso;
+ *   normals   (optional) the central-difference gradient of phi on the sample
+ *             grid (one-sided on the border), (1 - tau) g(a) + tau g(b),
+ *             normalised.
+ * The mesh is watertight wherever the level set stays inside the grid.
+ *   out_verts: float [vert_capacity][3]; out_tris: int32 [tri_capacity][3];
+ *   out_normals: float [vert_capacity][3] or NULL; n_verts, n_tris: HOST,
+ *   receive the counts.  With out_verts, out_tris and out_normals all NULL the
+ *   call only counts.
+ * Synchronises the stream once (to read the counts).  Errors: FGL_ERR_INVALID
+ * (null pointers, bad grid, step < 1, non-finite iso, more than 2^31 - 1
+ * vertices or triangles), FGL_ERR_CAPACITY (counts set, nothing written),
+ * FGL_ERR_CUDA. */
+fgl_status fgl_marching_tets(const float* phi, const fgl_grid* grid, float iso, int32_t step,
+                             float* out_verts, int64_t vert_capacity, int32_t* out_tris,
+                             int64_t tri_capacity, float* out_normals, int64_t* n_verts,
+                             int64_t* n_tris, fgl_stream stream);
 
 /* ------------------------------------------------------------------------ */
 /* Serving: continuous batching of scan requests                             */

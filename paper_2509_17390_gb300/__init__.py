@@ -20,12 +20,14 @@ from . import build_native
 
 __all__ = ["Scene", "Sensor", "BatchOpts", "cast", "cast_opts", "cast_batched",
            "cast_batched_host", "cast_batched_static", "autotune", "TuneOpts", "world_rays", "sync", "work_counters", "FglError", "lib",
-           "gaussian_density", "Gaussians", "Grid", "Lbvh"]
+           "gaussian_density", "Gaussians", "Grid", "Lbvh", "denoise", "tsdf", "marching_tets",
+           "mesh_from_surface", "mesh_from_gaussians"]
 
 FGL_OK, FGL_ERR_INVALID, FGL_ERR_OOM, FGL_ERR_CUDA = 0, 1, 2, 3
 FGL_ERR_BUDGET, FGL_ERR_TIMEOUT, FGL_ERR_CANCELLED, FGL_ERR_DEVICE = 4, 5, 6, 7
+FGL_ERR_CAPACITY = 8
 STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "BUDGET", 5: "TIMEOUT",
-                6: "CANCELLED", 7: "DEVICE"}
+                6: "CANCELLED", 7: "DEVICE", 8: "CAPACITY"}
 
 
 class FglError(RuntimeError):
@@ -115,6 +117,9 @@ def lib():
                 "fgl_lbvh_get_stats": ([P, P], I32),
                 "fgl_lbvh_export": ([P, P, I64, P, I64], I32),
                 "fgl_cast_lbvh": ([P, P, P, I32, F32, F32, P, P, P], I32),
+                "fgl_denoise": ([P, P, F32, I32, F32, P, P, P, P], I32),
+                "fgl_tsdf": ([P, P, F32, P, P, P, P, P], I32),
+                "fgl_marching_tets": ([P, P, F32, I32, P, I64, P, I64, P, P, P, P], I32),
                 "fgl_last_error": ([], ctypes.c_char_p),
                 "fgl_version": ([], I32),
             }
@@ -521,6 +526,125 @@ def gaussian_density(mu, scale, quat, opacity, origin, h: float, dims, theta: fl
                                             "n_voxels": st.n_voxels, "ms_total": st.ms_total,
                                             "ms_density": st.ms_density,
                                             "n_launches": st.n_launches}
+
+
+# ---------------------------------------------------------------------------
+# mesh reconstruction (fgl_denoise, fgl_tsdf, fgl_marching_tets; Sec. IV-B)
+# ---------------------------------------------------------------------------
+class TsdfStats(ctypes.Structure):
+    _fields_ = [("timing", I32), ("n_layers", I32), ("n_launches", I32), ("ms_total", F32)]
+
+
+def _grid_of(shape, origin, h):
+    nz, ny, nx = (int(d) for d in shape)
+    return Grid((F32 * 3)(*[float(x) for x in origin]), float(h), (I32 * 3)(nx, ny, nz), 0), nx * ny * nz
+
+
+def denoise(surf, h: float, sigma: float, tau: float = 0.5, quantile=None, blur: bool = False,
+            stream=None):
+    """Eqs. V' and rethresh (fgl_denoise) on a u8 CUDA grid [nz, ny, nx]:
+    blur by a Gaussian of sigma metres, keep V' >= tau (or V' >= the
+    quantile-q order statistic when quantile is given).  Returns (mask u8,
+    V' f32 or None, threshold used)."""
+    import torch
+    g, n = _grid_of(surf.shape, (0.0, 0.0, 0.0), h)
+    mask = torch.empty(surf.shape, dtype=torch.uint8, device=surf.device)
+    vp = torch.empty(surf.shape, dtype=torch.float32, device=surf.device) if blur else None
+    thr = F32()
+    mode, value = (1, float(quantile)) if quantile is not None else (0, float(tau))
+    _check(lib().fgl_denoise(_dev_ptr(surf, "uint8", n, "surf"), ctypes.byref(g), float(sigma), mode,
+                             value, _dev_ptr(vp, "float32", n, "blur") if blur else None,
+                             _dev_ptr(mask, "uint8", n, "mask"), ctypes.byref(thr),
+                             _stream_handle(stream)))
+    return mask, vp, float(thr.value)
+
+
+def tsdf(surf, h: float, trunc: float, outside: bool = False, shell: bool = False,
+         timing: bool = False, stream=None):
+    """Narrow-band TSDF (fgl_tsdf) of a u8 surface grid [nz, ny, nx]:
+    returns (phi f32, outside u8 or None, shell index u8 or None, stats)."""
+    import torch
+    g, n = _grid_of(surf.shape, (0.0, 0.0, 0.0), h)
+    dev = surf.device
+    phi = torch.empty(surf.shape, dtype=torch.float32, device=dev)
+    out = torch.empty(surf.shape, dtype=torch.uint8, device=dev) if outside else None
+    sh = torch.empty(surf.shape, dtype=torch.uint8, device=dev) if shell else None
+    st = TsdfStats()
+    st.timing = 1 if timing else 0
+    _check(lib().fgl_tsdf(_dev_ptr(surf, "uint8", n, "surf"), ctypes.byref(g), float(trunc),
+                          _dev_ptr(phi, "float32", n, "phi"),
+                          _dev_ptr(out, "uint8", n, "outside") if outside else None,
+                          _dev_ptr(sh, "uint8", n, "shell") if shell else None, ctypes.byref(st),
+                          _stream_handle(stream)))
+    return phi, out, sh, {"n_layers": st.n_layers, "n_launches": st.n_launches,
+                          "ms_total": st.ms_total}
+
+
+def marching_tets(phi, origin, h: float, iso: float = 0.0, step: int = 1, normals: bool = False,
+                  capacity=None, stream=None):
+    """The phi = iso level set (fgl_marching_tets) of a float CUDA grid
+    [nz, ny, nx] whose voxel (i, j, k) has centre origin + (idx + 1/2) h.
+    Returns (verts f32 [nv, 3], tris i32 [nt, 3], normals f32 [nv, 3] or
+    None).  capacity=(verts, tris) sizes the outputs up front; without it the
+    call counts first (a second pass over the grid)."""
+    import torch
+    g, n = _grid_of(phi.shape, origin, h)
+    dev = phi.device
+    nv, nt = I64(), I64()
+    L = lib()
+    pphi = _dev_ptr(phi, "float32", n, "phi")
+    hs = _stream_handle(stream)
+    if capacity is None:
+        _check(L.fgl_marching_tets(pphi, ctypes.byref(g), float(iso), int(step), None, 0, None, 0, None,
+                                   ctypes.byref(nv), ctypes.byref(nt), hs))
+        capacity = (nv.value, nt.value)
+    for _ in range(2):
+        vc, tc = max(int(capacity[0]), 1), max(int(capacity[1]), 1)
+        verts = torch.empty((vc, 3), dtype=torch.float32, device=dev)
+        tris = torch.empty((tc, 3), dtype=torch.int32, device=dev)
+        nrm = torch.empty((vc, 3), dtype=torch.float32, device=dev) if normals else None
+        st = L.fgl_marching_tets(pphi, ctypes.byref(g), float(iso), int(step),
+                                 _dev_ptr(verts, "float32", 3 * vc, "verts"), vc,
+                                 _dev_ptr(tris, "int32", 3 * tc, "tris"), tc,
+                                 _dev_ptr(nrm, "float32", 3 * vc, "normals") if normals else None,
+                                 ctypes.byref(nv), ctypes.byref(nt), hs)
+        if st == FGL_ERR_CAPACITY:
+            capacity = (nv.value, nt.value)
+            continue
+        _check(st)
+        return (verts[:nv.value], tris[:nt.value], nrm[:nv.value] if normals else None)
+    raise FglError(FGL_ERR_CAPACITY, "marching_tets: capacity retry failed")
+
+
+def mesh_from_surface(surf, origin, h: float, trunc: float = 0.06, sigma=None, tau: float = 0.5,
+                      quantile=None, iso: float = 0.0, step: int = 1, normals: bool = False,
+                      capacity=None, stream=None):
+    """Sec. IV-B from a surface grid: optional denoising (sigma metres; the
+    paper leaves sigma and tau open), the narrow-band TSDF of half-width
+    trunc, and its iso level set.  Returns (verts, tris, normals, phi)."""
+    if sigma:
+        surf, _, _ = denoise(surf, h, sigma, tau=tau, quantile=quantile, stream=stream)
+    phi, _, _, _ = tsdf(surf, h, trunc, stream=stream)
+    v, t, nrm = marching_tets(phi, origin, h, iso=iso, step=step, normals=normals, capacity=capacity,
+                              stream=stream)
+    return v, t, nrm, phi
+
+
+def mesh_from_gaussians(mu, scale, quat, opacity, origin, h: float, dims, theta: float = 0.5,
+                        trunc: float = 0.06, sigma="half-voxel", tau: float = 0.5, iso: float = 0.0,
+                        step: int = 1, normals: bool = False, capacity=None, stream=None):
+    """3D Gaussians to a watertight mesh on the GPU (Sec. IV-A then IV-B):
+    density and surface shell (gaussian_density), denoising (default sigma =
+    h / 2 with tau = 1/2: a lone voxel blurs below 1/2 while a one-voxel
+    plane stays at 0.79; sigma=None skips it), TSDF and marching tetrahedra.
+    Returns (verts, tris, normals)."""
+    _, _, surf, _ = gaussian_density(mu, scale, quat, opacity, origin, h, dims, theta=theta,
+                                     stream=stream)
+    if isinstance(sigma, str):
+        sigma = 0.5 * h
+    v, t, nrm, _ = mesh_from_surface(surf, origin, h, trunc=trunc, sigma=sigma, tau=tau, iso=iso,
+                                     step=step, normals=normals, capacity=capacity, stream=stream)
+    return v, t, nrm
 
 
 def work_counters():

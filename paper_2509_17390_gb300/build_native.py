@@ -23,7 +23,8 @@ NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp
 GXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-fno-fast-math", "-pthread",
              "-I" + INCLUDE, "-I" + CSRC]
 
-CU_SOURCES = ["kernels.cu", "api.cu", "static_batch.cu", "server.cu", "density.cu", "sort.cu", "lbvh.cu"]
+CU_SOURCES = ["kernels.cu", "api.cu", "static_batch.cu", "server.cu", "density.cu", "sort.cu", "lbvh.cu",
+              "mesh.cu"]
 CPP_SOURCES = ["bvh_build.cpp"]
 HEADERS = ["fgl_internal.h", "kernels.h", "trace.cuh", "ptx_ops.cuh", "sort.h"]
 

@@ -37,9 +37,6 @@
 #include "ptx_ops.cuh"
 #include "sort.h"
 
-namespace fgl {
-void record_error(int status, const char* msg);
-}  // namespace fgl
 
 using namespace fgl;
 

@@ -14,6 +14,9 @@
 
 namespace fgl {
 
+// Record the calling thread's last error (api.cu); returned by fgl_last_error.
+void record_error(int status, const char* msg);
+
 // ---------------------------------------------------------------------------
 // Wide BVH node record (W children, W in {4, 8}); 16-byte aligned so the
 // traversal reads it with 16-byte vector loads.

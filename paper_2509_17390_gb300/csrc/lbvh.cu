@@ -31,9 +31,6 @@
 #include "sort.h"
 #include "trace.cuh"
 
-namespace fgl {
-void record_error(int status, const char* msg);
-}  // namespace fgl
 
 using namespace fgl;
 

@@ -1,0 +1,975 @@
+// Mesh reconstruction on the GPU (paper Sec. IV-B): binary denoising and
+// re-thresholding (eqs. V', rethresh), the narrow-band TSDF (outside flood
+// fill, shells from S_0, eq. phi) and isosurface extraction by marching
+// tetrahedra.
+//
+// Bit grids.  A binary grid [nz][ny][nx] packs into 32-voxel words along x:
+// word (row = k ny + j, xw) holds voxel x = 32 xw + b in bit b, a row holds
+// mw = ceil(nx / 32) words and the bits past nx are zero.  Shells, signs and
+// marching-tetrahedra corner tests all run on these words, 32 voxels per
+// instruction.
+//
+// fgl_denoise        eq. V' as three separable passes (float32 taps rounded
+//                    from FP64 weights, sums in ascending tap order), then
+//                    eq. rethresh with a fixed tau or the exact order statistic
+//                    of rank floor(q (N - 1)) by a four-pass radix select on
+//                    the float bit patterns (V' >= 0, so they sort as u32).
+// fgl_tsdf           sign: a lock-free union-find over the free voxels with a
+//                    virtual root 0 standing for the padded frame (every free
+//                    voxel on the grid's faces starts linked to it; a link
+//                    always goes from the larger root to the smaller, so the
+//                    frame's component ends under 0); one pass, no flood
+//                    rounds.  Shells: S_0 from word XORs with the six
+//                    neighbours, then L = ceil(r / h) word dilations; p(x) is
+//                    the first mask holding x.  phi = s min((p + 1/2) h, r).
+// fgl_marching_tets  sign bits of the sample grid; per word, the crossing
+//                    edges of the seven types and the triangles of the six
+//                    tetrahedra counted bit-sliced over 32 samples; two
+//                    exclusive scans give every word its vertex and triangle
+//                    offsets; the emit pass writes both in the canonical order
+//                    documented in fgl.h.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+
+#include "fgl.h"
+#include "fgl_internal.h"
+#include "sort.h"
+
+namespace fgl {
+namespace {
+
+struct BitGrid {
+  int32_t nx, ny, nz, mw;
+  __host__ __device__ int64_t rows() const { return (int64_t)ny * nz; }
+  __host__ __device__ int64_t words() const { return rows() * mw; }
+};
+
+BitGrid make_bits(int nx, int ny, int nz) { return BitGrid{nx, ny, nz, (nx + 31) / 32}; }
+
+// bits of word xw that hold voxels (x < nx)
+__device__ __forceinline__ uint32_t valid_bits(const BitGrid& g, int xw) {
+  const int rem = g.nx - 32 * xw;
+  return rem >= 32 ? 0xFFFFFFFFu : ((1u << rem) - 1u);
+}
+
+// bits b of word xw whose voxel x has an x + 1 neighbour in the grid
+__device__ __forceinline__ uint32_t valid_bits_next(const BitGrid& g, int xw) {
+  return (valid_bits(g, xw) >> 1) | (xw + 1 < g.mw ? 0x80000000u : 0u);
+}
+
+// ---------------------------------------------------------------------------
+// packing
+// ---------------------------------------------------------------------------
+
+// one warp per word: bit b = V[row, 32 xw + b] != 0
+__global__ void k_pack_u8(const uint8_t* __restrict__ V, BitGrid g, uint32_t* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t n_warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < g.words(); w += n_warps) {
+    const int64_t row = w / g.mw;
+    const int x = (int)(w - row * g.mw) * 32 + lane;
+    const bool bit = x < g.nx && V[row * g.nx + x] != 0;
+    const uint32_t m = __ballot_sync(0xFFFFFFFFu, bit);
+    if (lane == 0) out[w] = m;
+  }
+}
+
+// one warp per word of the sample grid m (every step-th voxel of the nx x ny
+// voxel grid): bit = phi < iso
+__global__ void k_pack_inside(const float* __restrict__ phi, int nx, int ny, int step, BitGrid m,
+                              float iso, uint32_t* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t n_warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < m.words(); w += n_warps) {
+    const int64_t row = w / m.mw;
+    const int x = (int)(w - row * m.mw) * 32 + lane;
+    const int j = (int)(row % m.ny), k = (int)(row / m.ny);
+    bool bit = false;
+    if (x < m.nx) bit = phi[((int64_t)k * step * ny + (int64_t)j * step) * nx + (int64_t)x * step] < iso;
+    const uint32_t mask = __ballot_sync(0xFFFFFFFFu, bit);
+    if (lane == 0) out[w] = mask;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// eq. V': separable blur and eq. rethresh
+// ---------------------------------------------------------------------------
+constexpr int kMaxTaps = 32;
+
+struct Taps {
+  int R;
+  float w[2 * kMaxTaps + 1];
+};
+
+__device__ __forceinline__ float unit(uint8_t v) { return v ? 1.f : 0.f; }
+__device__ __forceinline__ float unit(float v) { return v; }
+
+// one pass along AXIS (0 = x, 1 = y, 2 = z); grid: x over blockIdx.x, rows
+// strided over blockIdx.y; a nonzero byte counts as 1
+template <int AXIS, class TIn>
+__global__ void k_blur(const TIn* __restrict__ in, float* __restrict__ out, int nx, int ny, int nz,
+                       Taps taps) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= nx) return;
+  const int64_t rows = (int64_t)ny * nz;
+  for (int64_t row = blockIdx.y; row < rows; row += gridDim.y) {
+    const int j = (int)(row % ny), k = (int)(row / ny);
+    const int64_t v = row * nx + x;
+    const int c = AXIS == 0 ? x : AXIS == 1 ? j : k;
+    const int lim = AXIS == 0 ? nx : AXIS == 1 ? ny : nz;
+    const int64_t stride = AXIS == 0 ? 1 : AXIS == 1 ? (int64_t)nx : (int64_t)nx * ny;
+    float s = 0.f;
+    for (int t = -taps.R; t <= taps.R; ++t) {
+      const int cc = c + t;
+      if (cc < 0 || cc >= lim) continue;
+      s += taps.w[t + taps.R] * unit(in[v + t * stride]);
+    }
+    out[v] = s;
+  }
+}
+
+// mask = V' >= threshold (the device value when thr_dev is set)
+__global__ void k_threshold(const float* __restrict__ Vp, int64_t n, float thr,
+                            const uint32_t* __restrict__ thr_dev, uint8_t* __restrict__ mask) {
+  const float t = thr_dev ? __uint_as_float(*thr_dev) : thr;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    mask[i] = Vp[i] >= t ? 1 : 0;
+}
+
+// radix select state: the key bits fixed so far and the rank left among the
+// keys that share them
+struct SelState {
+  uint32_t prefix;
+  uint32_t rank;
+};
+
+__global__ void k_sel_init(SelState* st, uint32_t rank, uint32_t* hist) {
+  if (threadIdx.x == 0) {
+    st->prefix = 0;
+    st->rank = rank;
+  }
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+}
+
+// histogram of digit (key >> shift) & 255 over the keys whose higher bits
+// equal the prefix
+__global__ void k_sel_hist(const uint32_t* __restrict__ keys, int64_t n, int shift,
+                           const SelState* __restrict__ st, uint32_t* __restrict__ hist) {
+  __shared__ uint32_t h[256];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  const uint32_t prefix = st->prefix;
+  const int hi = shift + 8;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t k = keys[i];
+    if (hi < 32 && (k >> hi) != (prefix >> hi)) continue;
+    atomicAdd(&h[(k >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 256; i += blockDim.x)
+    if (h[i]) atomicAdd(&hist[i], h[i]);
+}
+
+// pick the digit that holds the remaining rank; clear the histogram
+__global__ void k_sel_pick(SelState* st, int shift, uint32_t* hist) {
+  if (threadIdx.x == 0) {
+    uint32_t r = st->rank, d = 0;
+    for (; d < 255; ++d) {
+      if (r < hist[d]) break;
+      r -= hist[d];
+    }
+    st->rank = r;
+    st->prefix |= d << shift;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+}
+
+// ---------------------------------------------------------------------------
+// sign: union-find over free voxels (labels v + 1; 0 = the padded frame)
+// ---------------------------------------------------------------------------
+
+// Root of x.  Parents only ever decrease along a path, so the walk ends
+// within `limit` = N + 2 steps; path halving stores an ancestor, which is
+// always a valid parent.
+__device__ __forceinline__ uint32_t uf_find(uint32_t* parent, uint32_t x, uint32_t limit, int* err) {
+  for (uint32_t it = 0; it < limit; ++it) {
+    const uint32_t p = __ldcg(parent + x);
+    if (p == x) return x;
+    const uint32_t gp = __ldcg(parent + p);
+    if (gp != p) __stcg(parent + x, gp);
+    x = gp;
+  }
+  atomicOr(err, 1);
+  return x;
+}
+
+// Link the two roots, the larger under the smaller.  A failed exchange means
+// another thread linked the root first, so the next root is strictly smaller:
+// at most N + 2 rounds.
+__device__ __forceinline__ void uf_unite(uint32_t* parent, uint32_t a, uint32_t b, uint32_t limit,
+                                         int* err) {
+  for (uint32_t it = 0; it < limit; ++it) {
+    a = uf_find(parent, a, limit, err);
+    b = uf_find(parent, b, limit, err);
+    if (a == b) return;
+    if (a < b) {
+      const uint32_t t = a;
+      a = b;
+      b = t;
+    }
+    const uint32_t old = atomicCAS(parent + a, a, b);
+    if (old == a) return;
+  }
+  atomicOr(err, 2);
+}
+
+__device__ __forceinline__ bool bit_at(const uint32_t* __restrict__ bits, const BitGrid& g,
+                                       int64_t row, int x) {
+  return (bits[row * g.mw + (x >> 5)] >> (x & 31)) & 1u;
+}
+
+// parent[v + 1] = 0 for a free voxel on a face of the grid, else v + 1
+__global__ void k_uf_init(const uint32_t* __restrict__ Vb, BitGrid g, uint32_t* __restrict__ parent) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (blockIdx.y == 0 && x == 0) parent[0] = 0;
+  if (x >= g.nx) return;
+  for (int64_t row = blockIdx.y; row < g.rows(); row += gridDim.y) {
+    const int j = (int)(row % g.ny), k = (int)(row / g.ny);
+    const int64_t v = row * g.nx + x;
+    const bool face = x == 0 || j == 0 || k == 0 || x == g.nx - 1 || j == g.ny - 1 || k == g.nz - 1;
+    const bool free_ = !bit_at(Vb, g, row, x);
+    parent[v + 1] = (free_ && face) ? 0u : (uint32_t)(v + 1);
+  }
+}
+
+// every free voxel joins its free -x, -y and -z neighbours
+__global__ void k_uf_merge(const uint32_t* __restrict__ Vb, BitGrid g, uint32_t* parent, int* err) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= g.nx) return;
+  const uint32_t limit = (uint32_t)(g.rows() * g.nx + 2);
+  for (int64_t row = blockIdx.y; row < g.rows(); row += gridDim.y) {
+    if (bit_at(Vb, g, row, x)) continue;
+    const int j = (int)(row % g.ny), k = (int)(row / g.ny);
+    const uint32_t a = (uint32_t)(row * g.nx + x + 1);
+    if (x > 0 && !bit_at(Vb, g, row, x - 1)) uf_unite(parent, a, a - 1, limit, err);
+    if (j > 0 && !bit_at(Vb, g, row - 1, x)) uf_unite(parent, a, a - (uint32_t)g.nx, limit, err);
+    if (k > 0 && !bit_at(Vb, g, row - g.ny, x))
+      uf_unite(parent, a, a - (uint32_t)((int64_t)g.nx * g.ny), limit, err);
+  }
+}
+
+// outside word: free voxels whose root is the frame
+__global__ void k_uf_outside(const uint32_t* __restrict__ Vb, BitGrid g, uint32_t* parent,
+                             uint32_t* __restrict__ Ob, int* err) {
+  const int lane = threadIdx.x & 31;
+  const int64_t n_warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const uint32_t limit = (uint32_t)(g.rows() * g.nx + 2);
+  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < g.words(); w += n_warps) {
+    const int64_t row = w / g.mw;
+    const int x = (int)(w - row * g.mw) * 32 + lane;
+    bool out = false;
+    if (x < g.nx && !((Vb[w] >> lane) & 1u))
+      out = uf_find(parent, (uint32_t)(row * g.nx + x + 1), limit, err) == 0u;
+    const uint32_t m = __ballot_sync(0xFFFFFFFFu, out);
+    if (lane == 0) Ob[w] = m;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// shells
+// ---------------------------------------------------------------------------
+
+// the six neighbour words of word w, as values at bit b of voxel b's neighbour
+struct Nbr {
+  uint32_t xm, xp, ym, yp, zm, zp;
+  bool has_ym, has_yp, has_zm, has_zp;
+};
+
+__device__ __forceinline__ Nbr neighbours(const uint32_t* __restrict__ B, const BitGrid& g, int64_t w) {
+  const int64_t row = w / g.mw;
+  const int xw = (int)(w - row * g.mw);
+  const int j = (int)(row % g.ny), k = (int)(row / g.ny);
+  const uint32_t c = B[w];
+  const uint32_t prev = xw > 0 ? B[w - 1] : 0u, next = xw + 1 < g.mw ? B[w + 1] : 0u;
+  Nbr n;
+  n.xm = (c << 1) | (prev >> 31);
+  n.xp = (c >> 1) | (next << 31);
+  n.has_ym = j > 0;
+  n.has_yp = j + 1 < g.ny;
+  n.has_zm = k > 0;
+  n.has_zp = k + 1 < g.nz;
+  const int64_t plane = (int64_t)g.mw * g.ny;
+  n.ym = n.has_ym ? B[w - g.mw] : 0u;
+  n.yp = n.has_yp ? B[w + g.mw] : 0u;
+  n.zm = n.has_zm ? B[w - plane] : 0u;
+  n.zp = n.has_zp ? B[w + plane] : 0u;
+  return n;
+}
+
+// eq. S_0: a voxel with an in-grid face neighbour of the other value
+__global__ void k_s0(const uint32_t* __restrict__ Vb, BitGrid g, uint32_t* __restrict__ S0) {
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < g.words();
+       w += (int64_t)gridDim.x * blockDim.x) {
+    const int xw = (int)(w % g.mw);
+    const uint32_t c = Vb[w];
+    const Nbr n = neighbours(Vb, g, w);
+    const uint32_t ex_m = xw == 0 ? ~1u : ~0u;
+    uint32_t d = ((c ^ n.xm) & ex_m) | ((c ^ n.xp) & valid_bits_next(g, xw));
+    if (n.has_ym) d |= c ^ n.ym;
+    if (n.has_yp) d |= c ^ n.yp;
+    if (n.has_zm) d |= c ^ n.zm;
+    if (n.has_zp) d |= c ^ n.zp;
+    S0[w] = d & valid_bits(g, xw);
+  }
+}
+
+// one shell: the mask grown by its face neighbours (padding bits stay zero)
+__global__ void k_dilate(const uint32_t* __restrict__ Din, BitGrid g, uint32_t* __restrict__ Dout) {
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < g.words();
+       w += (int64_t)gridDim.x * blockDim.x) {
+    const Nbr n = neighbours(Din, g, w);
+    Dout[w] = (Din[w] | n.xm | n.xp | n.ym | n.yp | n.zm | n.zp) & valid_bits(g, (int)(w % g.mw));
+  }
+}
+
+// eq. phi per voxel from the sign word and the first shell mask holding it
+__global__ void k_phi(const uint32_t* __restrict__ Ob, const uint32_t* __restrict__ D, int L, BitGrid g,
+                      float h, float r, float* __restrict__ phi, uint8_t* __restrict__ out_outside,
+                      uint8_t* __restrict__ out_shell) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= g.nx) return;
+  const int64_t nw = g.words();
+  for (int64_t row = blockIdx.y; row < g.rows(); row += gridDim.y) {
+    const int64_t w = row * g.mw + (x >> 5);
+    const int b = x & 31;
+    int p = 255;
+    for (int m = 0; m <= L; ++m)
+      if ((D[(int64_t)m * nw + w] >> b) & 1u) {
+        p = m;
+        break;
+      }
+    const bool out = (Ob[w] >> b) & 1u;
+    const float delta = p == 255 ? r : fminf(((float)p + 0.5f) * h, r);
+    const int64_t v = row * g.nx + x;
+    phi[v] = out ? delta : -delta;
+    if (out_outside) out_outside[v] = out ? 1 : 0;
+    if (out_shell) out_shell[v] = (uint8_t)p;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// marching tetrahedra
+// ---------------------------------------------------------------------------
+
+// corner word c (c = dx + 2 dy + 4 dz) of the cubes whose lowest sample is in
+// word (j, k, xw): bit b = inside bit of sample (32 xw + b + dx, j + dy, k + dz)
+__device__ __forceinline__ void corner_words(const uint32_t* __restrict__ I, const BitGrid& m, int j,
+                                             int k, int xw, uint32_t C[8]) {
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int jj = j + ((c >> 1) & 1), kk = k + ((c >> 2) & 1);
+    uint32_t lo = 0, hi = 0;
+    if (jj < m.ny && kk < m.nz) {
+      const int64_t w = ((int64_t)kk * m.ny + jj) * m.mw + xw;
+      lo = I[w];
+      if ((c & 1) && xw + 1 < m.mw) hi = I[w + 1];
+    }
+    C[c] = (c & 1) ? ((lo >> 1) | (hi << 31)) : lo;
+  }
+}
+
+// middle corners of the six tetrahedra (0, a, b, 7)
+__constant__ int8_t kTetMid[6][2] = {{1, 3}, {1, 5}, {2, 3}, {2, 6}, {4, 5}, {4, 6}};
+
+__device__ __forceinline__ void crossing_words(const uint32_t C[8], const BitGrid& m, int j, int k,
+                                               int xw, uint32_t X[7]) {
+  const uint32_t v0 = valid_bits(m, xw), v1 = valid_bits_next(m, xw);
+#pragma unroll
+  for (int t = 1; t <= 7; ++t) {
+    uint32_t mask = (t & 1) ? v1 : v0;
+    if (j + ((t >> 1) & 1) >= m.ny || k + ((t >> 2) & 1) >= m.nz) mask = 0;
+    X[t - 1] = (C[0] ^ C[t]) & mask;
+  }
+}
+
+__device__ __forceinline__ uint32_t cube_bits(const BitGrid& m, int j, int k, int xw) {
+  return (j + 1 < m.ny && k + 1 < m.nz) ? valid_bits_next(m, xw) : 0u;
+}
+
+__device__ __forceinline__ uint32_t tri_count(const uint32_t C[8], uint32_t cubes) {
+  uint32_t n = 0;
+#pragma unroll
+  for (int T = 0; T < 6; ++T) {
+    const uint32_t a = C[0], b = C[kTetMid[T][0]], c = C[kTetMid[T][1]], d = C[7];
+    const uint32_t odd = a ^ b ^ c ^ d;
+    const uint32_t two = ~odd & (a | b | c | d) & ~(a & b & c & d);
+    n += __popc(odd & cubes) + 2 * __popc(two & cubes);
+  }
+  return n;
+}
+
+// per word: the seven crossing words and the vertex / triangle counts
+__global__ void k_mt_count(const uint32_t* __restrict__ I, BitGrid m, uint32_t* __restrict__ X,
+                           unsigned long long* __restrict__ cnt_v, unsigned long long* __restrict__ cnt_t) {
+  const int64_t nw = m.words();
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nw;
+       w += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = w / m.mw;
+    const int xw = (int)(w - row * m.mw);
+    const int j = (int)(row % m.ny), k = (int)(row / m.ny);
+    uint32_t C[8], Xw[7];
+    corner_words(I, m, j, k, xw, C);
+    crossing_words(C, m, j, k, xw, Xw);
+    uint32_t nv = 0;
+#pragma unroll
+    for (int t = 0; t < 7; ++t) {
+      X[t * nw + w] = Xw[t];
+      nv += __popc(Xw[t]);
+    }
+    cnt_v[w] = nv;
+    cnt_t[w] = tri_count(C, cube_bits(m, j, k, xw));
+  }
+}
+
+struct EmitArgs {
+  const float* phi;
+  int nx, ny;          // voxel grid (row pitch of phi)
+  int step;
+  BitGrid m;           // sample grid
+  float ox, oy, oz, h, iso;
+  const uint32_t* I;
+  const uint32_t* X;
+  const unsigned long long* base_v;
+  const unsigned long long* base_t;
+  float* verts;
+  int32_t* tris;
+  float* normals;
+};
+
+__device__ __forceinline__ float sample_phi(const EmitArgs& a, int x, int j, int k) {
+  return a.phi[((int64_t)k * a.step * a.ny + (int64_t)j * a.step) * a.nx + (int64_t)x * a.step];
+}
+
+// central-difference gradient of phi on the sample grid (one-sided on the border)
+__device__ void sample_grad(const EmitArgs& a, int x, int j, int k, float g[3]) {
+  const int c[3] = {x, j, k}, lim[3] = {a.m.nx, a.m.ny, a.m.nz};
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    int lo[3] = {x, j, k}, hi[3] = {x, j, k};
+    if (c[ax] > 0) lo[ax] -= 1;
+    if (c[ax] < lim[ax] - 1) hi[ax] += 1;
+    const int span = hi[ax] - lo[ax];
+    g[ax] = span > 0 ? (sample_phi(a, hi[0], hi[1], hi[2]) - sample_phi(a, lo[0], lo[1], lo[2])) /
+                           ((float)(span * a.step) * a.h)
+                     : 0.f;
+  }
+}
+
+__device__ void emit_vertex(const EmitArgs& a, int x, int j, int k, int t, int64_t id) {
+  const int dx = t & 1, dy = (t >> 1) & 1, dz = (t >> 2) & 1;
+  const float fa = sample_phi(a, x, j, k), fb = sample_phi(a, x + dx, j + dy, k + dz);
+  const float tau = (a.iso - fa) / (fb - fa);
+  const float span = (float)a.step * a.h;
+  float p[3] = {a.ox + ((float)(x * a.step) + 0.5f) * a.h, a.oy + ((float)(j * a.step) + 0.5f) * a.h,
+                a.oz + ((float)(k * a.step) + 0.5f) * a.h};
+  if (dx) p[0] += tau * span;
+  if (dy) p[1] += tau * span;
+  if (dz) p[2] += tau * span;
+  a.verts[id * 3 + 0] = p[0];
+  a.verts[id * 3 + 1] = p[1];
+  a.verts[id * 3 + 2] = p[2];
+  if (a.normals) {
+    float ga[3], gb[3], n[3];
+    sample_grad(a, x, j, k, ga);
+    sample_grad(a, x + dx, j + dy, k + dz, gb);
+    float len2 = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      n[c] = (1.f - tau) * ga[c] + tau * gb[c];
+      len2 += n[c] * n[c];
+    }
+    const float len = sqrtf(len2);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) a.normals[id * 3 + c] = len > 0.f ? n[c] / len : 0.f;
+  }
+}
+
+// first vertex id of sample (x, j, k) and the set of its edge types (bit t)
+__device__ __forceinline__ void owner_info(const EmitArgs& a, int x, int j, int k, uint32_t* first,
+                                           uint32_t* types) {
+  const int64_t nw = a.m.words();
+  const int64_t w = ((int64_t)k * a.m.ny + j) * a.m.mw + (x >> 5);
+  const int b = x & 31;
+  const uint32_t below = (1u << b) - 1u;
+  uint32_t f = (uint32_t)a.base_v[w], ty = 0;
+#pragma unroll
+  for (int t = 1; t <= 7; ++t) {
+    const uint32_t xw = __ldg(a.X + (t - 1) * nw + w);
+    f += __popc(xw & below);
+    ty |= ((xw >> b) & 1u) << t;
+  }
+  *first = f;
+  *types = ty;
+}
+
+__device__ __forceinline__ int3 corner_xyz(int c) { return make_int3(c & 1, (c >> 1) & 1, (c >> 2) & 1); }
+
+// one triangle on the edges (p0, q0), (p1, q1), (p2, q2) of a tetrahedron
+// with the given corner set and inside flags; oriented towards the outside
+__device__ __forceinline__ void emit_tri(const EmitArgs& a, const int tet[4], const bool in[4],
+                                         const int e[3][2], const uint32_t first[8],
+                                         const uint32_t types[8], int64_t id) {
+  // doubled edge midpoints (integers) and the inside-to-outside direction
+  int3 mp[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const int3 u = corner_xyz(e[q][0]), v = corner_xyz(e[q][1]);
+    mp[q] = make_int3(u.x + v.x, u.y + v.y, u.z + v.z);
+  }
+  int nin = 0;
+  int3 sin = make_int3(0, 0, 0), sout = make_int3(0, 0, 0);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int3 c = corner_xyz(tet[q]);
+    if (in[q]) {
+      ++nin;
+      sin.x += c.x, sin.y += c.y, sin.z += c.z;
+    } else {
+      sout.x += c.x, sout.y += c.y, sout.z += c.z;
+    }
+  }
+  const int nout = 4 - nin;
+  const int3 G = make_int3(nin * sout.x - nout * sin.x, nin * sout.y - nout * sin.y, nin * sout.z - nout * sin.z);
+  const int3 U = make_int3(mp[1].x - mp[0].x, mp[1].y - mp[0].y, mp[1].z - mp[0].z);
+  const int3 V = make_int3(mp[2].x - mp[0].x, mp[2].y - mp[0].y, mp[2].z - mp[0].z);
+  const int3 N = make_int3(U.y * V.z - U.z * V.y, U.z * V.x - U.x * V.z, U.x * V.y - U.y * V.x);
+  const bool flip = N.x * G.x + N.y * G.y + N.z * G.z < 0;
+  int32_t ids[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const int lo = min(e[q][0], e[q][1]), hi = max(e[q][0], e[q][1]);
+    const int t = hi ^ lo;
+    ids[q] = (int32_t)(first[lo] + __popc(types[lo] & ((1u << t) - 1u)));
+  }
+  a.tris[id * 3 + 0] = ids[0];
+  a.tris[id * 3 + 1] = flip ? ids[2] : ids[1];
+  a.tris[id * 3 + 2] = flip ? ids[1] : ids[2];
+}
+
+__global__ void k_mt_emit(EmitArgs a) {
+  const int64_t nw = a.m.words();
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nw;
+       w += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = w / a.m.mw;
+    const int xw = (int)(w - row * a.m.mw);
+    const int j = (int)(row % a.m.ny), k = (int)(row / a.m.ny);
+    uint32_t Xw[7], any = 0;
+#pragma unroll
+    for (int t = 0; t < 7; ++t) {
+      Xw[t] = a.X[t * nw + w];
+      any |= Xw[t];
+    }
+    // vertices, by sample then type
+    int64_t vid = (int64_t)a.base_v[w];
+    for (uint32_t M = any; M; M &= M - 1) {
+      const int b = __ffs(M) - 1;
+#pragma unroll 1
+      for (int t = 1; t <= 7; ++t)
+        if ((Xw[t - 1] >> b) & 1u) emit_vertex(a, xw * 32 + b, j, k, t, vid++);
+    }
+    // triangles, by cube, tetrahedron, then the documented split
+    const uint32_t cubes = cube_bits(a.m, j, k, xw);
+    if (!cubes) continue;
+    uint32_t C[8];
+    corner_words(a.I, a.m, j, k, xw, C);
+    uint32_t all1 = ~0u, any1 = 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      all1 &= C[c];
+      any1 |= C[c];
+    }
+    int64_t tid = (int64_t)a.base_t[w];
+    for (uint32_t M = cubes & any1 & ~all1; M; M &= M - 1) {
+      const int b = __ffs(M) - 1;
+      const int x = xw * 32 + b;
+      uint32_t first[8], types[8];  // corner 7 owns no edge of its cube
+#pragma unroll 1
+      for (int c = 0; c < 7; ++c)
+        owner_info(a, x + (c & 1), j + ((c >> 1) & 1), k + ((c >> 2) & 1), &first[c], &types[c]);
+#pragma unroll 1
+      for (int T = 0; T < 6; ++T) {
+        const int tet[4] = {0, kTetMid[T][0], kTetMid[T][1], 7};
+        bool in[4];
+        int nin = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          in[q] = (C[tet[q]] >> b) & 1u;
+          nin += in[q];
+        }
+        if (nin == 0 || nin == 4) continue;
+        if (nin & 1) {
+          const bool lone_in = nin == 1;
+          int lone = 0, o[3], no = 0;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (in[q] == lone_in) lone = q;
+            else o[no++] = q;
+          }
+          const int e[3][2] = {{tet[lone], tet[o[0]]}, {tet[lone], tet[o[1]]}, {tet[lone], tet[o[2]]}};
+          emit_tri(a, tet, in, e, first, types, tid++);
+        } else {
+          int ins[2], outs[2], ni = 0, nu = 0;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (in[q]) ins[ni++] = tet[q];
+            else outs[nu++] = tet[q];
+          }
+          const int e1[3][2] = {{ins[0], outs[0]}, {ins[0], outs[1]}, {ins[1], outs[1]}};
+          const int e2[3][2] = {{ins[0], outs[0]}, {ins[1], outs[1]}, {ins[1], outs[0]}};
+          emit_tri(a, tet, in, e1, first, types, tid++);
+          emit_tri(a, tet, in, e2, first, types, tid++);
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct Buf {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+
+struct Scratch {
+  Buf bits_a, bits_b, shells, parent, x_words, cnt_v, cnt_t, scan_tmp, blur_a, blur_b, sel;
+  int* err = nullptr;        // device: union-find limit reached (bit 0 find, bit 1 unite)
+  unsigned long long* host = nullptr;  // pinned: [0..1] counts read back, [2] the error flag
+  cudaEvent_t err_ready = nullptr;     // recorded after the flag's copy to host[2]
+  int pending_err_check = 0;
+  std::mutex mu;
+};
+std::mutex g_scr_mu;
+std::unordered_map<uint64_t, std::unique_ptr<Scratch>> g_scr;
+
+Scratch* get_scratch(cudaStream_t s) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const uint64_t key = (uint64_t)(uintptr_t)s ^ ((uint64_t)dev << 56);
+  std::lock_guard<std::mutex> lk(g_scr_mu);
+  auto& p = g_scr[key];
+  if (!p) p.reset(new Scratch());
+  return p.get();
+}
+
+// grow a device buffer (contents not preserved); synchronises the stream first
+cudaError_t ensure(Buf& b, size_t bytes, cudaStream_t s) {
+  if (bytes <= b.cap) return cudaSuccess;
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.cap = 0;
+  const size_t nb = std::max<size_t>(bytes + bytes / 8, 1 << 16);
+  e = cudaMalloc(&b.p, nb);
+  if (e != cudaSuccess) {
+    b.p = nullptr;
+    return e;
+  }
+  b.cap = nb;
+  return cudaSuccess;
+}
+
+cudaError_t ensure_small(Scratch& S) {
+  if (!S.err) {
+    cudaError_t e = cudaMalloc(&S.err, sizeof(int));
+    if (e != cudaSuccess) return e;
+    e = cudaMemset(S.err, 0, sizeof(int));
+    if (e != cudaSuccess) return e;
+  }
+  if (!S.err_ready) {
+    cudaError_t e = cudaEventCreateWithFlags(&S.err_ready, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+  }
+  if (!S.host) {
+    cudaError_t e = cudaMallocHost(&S.host, 4 * sizeof(unsigned long long));
+    if (e != cudaSuccess) return e;
+    std::memset(S.host, 0, 4 * sizeof(unsigned long long));
+  }
+  return cudaSuccess;
+}
+
+fgl_status err(int status, const std::string& msg) {
+  record_error(status, msg.c_str());
+  return (fgl_status)status;
+}
+
+fgl_status cuda_err(cudaError_t e, const char* what) {
+  return err(FGL_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define MCUDA(call)                                   \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return cuda_err(e_, #call); \
+  } while (0)
+
+fgl_status check_grid(const fgl_grid* g, int64_t* n) {
+  if (!g) return err(FGL_ERR_INVALID, "null grid");
+  if (!(std::isfinite(g->h) && g->h > 0.f)) return err(FGL_ERR_INVALID, "h must be finite and > 0");
+  for (int a = 0; a < 3; ++a) {
+    if (g->dims[a] < 1) return err(FGL_ERR_INVALID, "grid dims must be >= 1");
+    if (!std::isfinite(g->origin[a])) return err(FGL_ERR_INVALID, "grid origin must be finite");
+  }
+  *n = (int64_t)g->dims[0] * g->dims[1] * g->dims[2];
+  if (*n > ((int64_t)1 << 31) - 2) return err(FGL_ERR_INVALID, "grid has more than 2^31 - 2 voxels");
+  return FGL_OK;
+}
+
+// launch shapes: per-voxel kernels take (ceil(nx / 128), min(rows, 65535))
+// blocks of 128; per-word kernels a grid-stride of 256-thread blocks
+dim3 voxel_grid(int nx, int64_t rows) {
+  return dim3((unsigned)((nx + 127) / 128), (unsigned)std::min<int64_t>(rows, 65535));
+}
+unsigned word_blocks(int64_t items, int per_block) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((items + per_block - 1) / per_block, 152 * 64));
+}
+
+// A union-find limit hit by an earlier call on this stream, seen once that
+// call's flag copy has landed (never blocks unless `wait`).  The loops are
+// bounded by N + 2 rounds, so this only reports a fault.
+fgl_status take_device_error(Scratch& S, cudaStream_t s, bool wait) {
+  if (!S.pending_err_check) return FGL_OK;
+  if (wait) {
+    MCUDA(cudaEventSynchronize(S.err_ready));
+  } else if (cudaEventQuery(S.err_ready) != cudaSuccess) {
+    cudaGetLastError();  // clear cudaErrorNotReady
+    return FGL_OK;
+  }
+  S.pending_err_check = 0;
+  if (S.host[2]) {
+    S.host[2] = 0;
+    MCUDA(cudaMemsetAsync(S.err, 0, sizeof(int), s));
+    return err(FGL_ERR_DEVICE, "fgl_tsdf: union-find step limit reached");
+  }
+  return FGL_OK;
+}
+
+}  // namespace
+}  // namespace fgl
+
+using namespace fgl;
+
+extern "C" fgl_status fgl_denoise(const uint8_t* surf, const fgl_grid* grid, float sigma, int32_t mode,
+                                  float value, float* out_blur, uint8_t* out_mask, float* out_threshold,
+                                  fgl_stream stream) {
+  int64_t n = 0;
+  if (fgl_status st = check_grid(grid, &n)) return st;
+  if (!surf || !out_mask) return err(FGL_ERR_INVALID, "null surf or out_mask");
+  if (!(std::isfinite(sigma) && sigma > 0.f)) return err(FGL_ERR_INVALID, "sigma must be finite and > 0");
+  if (mode != 0 && mode != 1) return err(FGL_ERR_INVALID, "mode must be 0 (fixed) or 1 (quantile)");
+  if (!std::isfinite(value)) return err(FGL_ERR_INVALID, "threshold value must be finite");
+  if (mode == 1 && !(value >= 0.f && value <= 1.f)) return err(FGL_ERR_INVALID, "quantile must lie in [0, 1]");
+  const double sv = (double)sigma / (double)grid->h;
+  const double Rd = std::ceil(3.0 * sv);
+  if (Rd > kMaxTaps) return err(FGL_ERR_INVALID, "sigma too large: more than 32 taps a side");
+  Taps taps{};
+  taps.R = (int)Rd;
+  double Z = 0;
+  for (int j = -taps.R; j <= taps.R; ++j) Z += std::exp(-(double)j * j / (2 * sv * sv));
+  for (int j = -taps.R; j <= taps.R; ++j)
+    taps.w[j + taps.R] = (float)(std::exp(-(double)j * j / (2 * sv * sv)) / Z);
+  cudaStream_t s = (cudaStream_t)stream;
+  Scratch& S = *get_scratch(s);
+  std::lock_guard<std::mutex> lk(S.mu);
+  MCUDA(ensure_small(S));
+  const int nx = grid->dims[0], ny = grid->dims[1], nz = grid->dims[2];
+  MCUDA(ensure(S.blur_a, sizeof(float) * n, s));
+  if (!out_blur) MCUDA(ensure(S.blur_b, sizeof(float) * n, s));
+  float* A = (float*)S.blur_a.p;
+  float* B = out_blur ? out_blur : (float*)S.blur_b.p;
+  const dim3 vg = voxel_grid(nx, (int64_t)ny * nz);
+  // x into B, y into A, z into B (the caller's buffer when given)
+  k_blur<0, uint8_t><<<vg, 128, 0, s>>>(surf, B, nx, ny, nz, taps);
+  k_blur<1, float><<<vg, 128, 0, s>>>(B, A, nx, ny, nz, taps);
+  k_blur<2, float><<<vg, 128, 0, s>>>(A, B, nx, ny, nz, taps);
+  MCUDA(cudaGetLastError());
+  const uint32_t* thr_dev = nullptr;
+  if (mode == 1) {
+    MCUDA(ensure(S.sel, sizeof(SelState) + 256 * sizeof(uint32_t), s));
+    SelState* st = (SelState*)S.sel.p;
+    uint32_t* hist = (uint32_t*)((char*)S.sel.p + sizeof(SelState));
+    const uint32_t rank = (uint32_t)std::floor((double)value * (double)(n - 1));
+    k_sel_init<<<1, 256, 0, s>>>(st, rank, hist);
+    for (int shift = 24; shift >= 0; shift -= 8) {
+      k_sel_hist<<<word_blocks(n, 1024), 256, 0, s>>>((const uint32_t*)B, n, shift, st, hist);
+      k_sel_pick<<<1, 256, 0, s>>>(st, shift, hist);
+    }
+    MCUDA(cudaGetLastError());
+    thr_dev = &st->prefix;
+  }
+  k_threshold<<<word_blocks(n, 1024), 256, 0, s>>>(B, n, value, thr_dev, out_mask);
+  MCUDA(cudaGetLastError());
+  if (out_threshold) {
+    if (thr_dev) {
+      uint32_t bits = 0;
+      MCUDA(cudaMemcpyAsync(&bits, thr_dev, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+      MCUDA(cudaStreamSynchronize(s));
+      std::memcpy(out_threshold, &bits, sizeof(float));
+    } else {
+      *out_threshold = value;
+    }
+  }
+  return FGL_OK;
+}
+
+extern "C" fgl_status fgl_tsdf(const uint8_t* surf, const fgl_grid* grid, float trunc, float* out_phi,
+                               uint8_t* out_outside, uint8_t* out_shell, fgl_tsdf_stats* stats,
+                               fgl_stream stream) {
+  int64_t n = 0;
+  if (fgl_status st = check_grid(grid, &n)) return st;
+  if (!surf || !out_phi) return err(FGL_ERR_INVALID, "null surf or out_phi");
+  if (!(std::isfinite(trunc) && trunc > 0.f)) return err(FGL_ERR_INVALID, "trunc must be finite and > 0");
+  const double Ld = std::ceil((double)trunc / (double)grid->h);
+  if (Ld > 254) return err(FGL_ERR_INVALID, "truncation band wider than 254 voxels");
+  const int L = (int)Ld;
+  cudaStream_t s = (cudaStream_t)stream;
+  Scratch& S = *get_scratch(s);
+  std::lock_guard<std::mutex> lk(S.mu);
+  MCUDA(ensure_small(S));
+  if (fgl_status st = take_device_error(S, s, false)) return st;
+  const BitGrid g = make_bits(grid->dims[0], grid->dims[1], grid->dims[2]);
+  const int64_t nw = g.words();
+  MCUDA(ensure(S.bits_a, sizeof(uint32_t) * nw, s));
+  MCUDA(ensure(S.bits_b, sizeof(uint32_t) * nw, s));
+  MCUDA(ensure(S.shells, sizeof(uint32_t) * nw * (L + 1), s));
+  MCUDA(ensure(S.parent, sizeof(uint32_t) * (n + 1), s));
+  uint32_t* Vb = (uint32_t*)S.bits_a.p;
+  uint32_t* Ob = (uint32_t*)S.bits_b.p;
+  uint32_t* D = (uint32_t*)S.shells.p;
+  uint32_t* parent = (uint32_t*)S.parent.p;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  const bool timing = stats && stats->timing;
+  if (timing) {
+    MCUDA(cudaEventCreate(&e0));
+    MCUDA(cudaEventCreate(&e1));
+    MCUDA(cudaEventRecord(e0, s));
+  }
+  int launches = 0;
+  const dim3 vg = voxel_grid(g.nx, g.rows());
+  k_pack_u8<<<word_blocks(nw * 32, 256), 256, 0, s>>>(surf, g, Vb);
+  k_uf_init<<<vg, 128, 0, s>>>(Vb, g, parent);
+  k_uf_merge<<<vg, 128, 0, s>>>(Vb, g, parent, S.err);
+  k_uf_outside<<<word_blocks(nw * 32, 256), 256, 0, s>>>(Vb, g, parent, Ob, S.err);
+  k_s0<<<word_blocks(nw, 256), 256, 0, s>>>(Vb, g, D);
+  launches += 5;
+  for (int m = 1; m <= L; ++m, ++launches)
+    k_dilate<<<word_blocks(nw, 256), 256, 0, s>>>(D + (m - 1) * nw, g, D + m * nw);
+  k_phi<<<vg, 128, 0, s>>>(Ob, D, L, g, grid->h, trunc, out_phi, out_outside, out_shell);
+  ++launches;
+  MCUDA(cudaGetLastError());
+  MCUDA(cudaMemcpyAsync(S.host + 2, S.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MCUDA(cudaEventRecord(S.err_ready, s));
+  S.pending_err_check = 1;
+  if (stats) {
+    stats->n_layers = L;
+    stats->n_launches = launches;
+    stats->ms_total = 0.f;
+  }
+  if (timing) {
+    MCUDA(cudaEventRecord(e1, s));
+    MCUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    stats->ms_total = ms;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (fgl_status st = take_device_error(S, s, true)) return st;
+  }
+  return FGL_OK;
+}
+
+extern "C" fgl_status fgl_marching_tets(const float* phi, const fgl_grid* grid, float iso, int32_t step,
+                                        float* out_verts, int64_t vert_capacity, int32_t* out_tris,
+                                        int64_t tri_capacity, float* out_normals, int64_t* n_verts,
+                                        int64_t* n_tris, fgl_stream stream) {
+  int64_t n = 0;
+  if (fgl_status st = check_grid(grid, &n)) return st;
+  if (!phi || !n_verts || !n_tris) return err(FGL_ERR_INVALID, "null phi or count pointer");
+  if (step < 1) return err(FGL_ERR_INVALID, "step must be >= 1");
+  if (!std::isfinite(iso)) return err(FGL_ERR_INVALID, "iso must be finite");
+  if (vert_capacity < 0 || tri_capacity < 0) return err(FGL_ERR_INVALID, "negative capacity");
+  const bool query = !out_verts && !out_tris && !out_normals;
+  if (!query && (!out_verts || !out_tris)) return err(FGL_ERR_INVALID, "out_verts and out_tris go together");
+  const int nx = grid->dims[0], ny = grid->dims[1], nz = grid->dims[2];
+  const BitGrid m = make_bits((nx - 1) / step + 1, (ny - 1) / step + 1, (nz - 1) / step + 1);
+  const int64_t nw = m.words();
+  cudaStream_t s = (cudaStream_t)stream;
+  Scratch& S = *get_scratch(s);
+  std::lock_guard<std::mutex> lk(S.mu);
+  MCUDA(ensure_small(S));
+  const size_t tmp_elems = scan_tmp_elems(nw + 1);
+  MCUDA(ensure(S.bits_a, sizeof(uint32_t) * nw, s));
+  MCUDA(ensure(S.x_words, sizeof(uint32_t) * nw * 7, s));
+  MCUDA(ensure(S.cnt_v, sizeof(unsigned long long) * (nw + 1), s));
+  MCUDA(ensure(S.cnt_t, sizeof(unsigned long long) * (nw + 1), s));
+  MCUDA(ensure(S.scan_tmp, sizeof(unsigned long long) * tmp_elems, s));
+  uint32_t* I = (uint32_t*)S.bits_a.p;
+  uint32_t* X = (uint32_t*)S.x_words.p;
+  auto* cv = (unsigned long long*)S.cnt_v.p;
+  auto* ct = (unsigned long long*)S.cnt_t.p;
+  auto* tmp = (unsigned long long*)S.scan_tmp.p;
+  int launches = 0;
+  k_pack_inside<<<word_blocks(nw * 32, 256), 256, 0, s>>>(phi, nx, ny, step, m, iso, I);
+  k_mt_count<<<word_blocks(nw, 256), 256, 0, s>>>(I, m, X, cv, ct);
+  MCUDA(cudaGetLastError());
+  MCUDA(cudaMemsetAsync(cv + nw, 0, sizeof(unsigned long long), s));
+  MCUDA(cudaMemsetAsync(ct + nw, 0, sizeof(unsigned long long), s));
+  MCUDA(scan_exclusive_u64(cv, nw + 1, tmp, tmp_elems, s, &launches));
+  MCUDA(scan_exclusive_u64(ct, nw + 1, tmp, tmp_elems, s, &launches));
+  MCUDA(cudaMemcpyAsync(S.host, cv + nw, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  MCUDA(cudaMemcpyAsync(S.host + 1, ct + nw, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  MCUDA(cudaStreamSynchronize(s));
+  const int64_t nv = (int64_t)S.host[0], nt = (int64_t)S.host[1];
+  *n_verts = nv;
+  *n_tris = nt;
+  if (nv >= ((int64_t)1 << 31) || nt >= ((int64_t)1 << 31))
+    return err(FGL_ERR_INVALID, "mesh needs more than 2^31 - 1 vertices or triangles");
+  if (query) return FGL_OK;
+  if (nv > vert_capacity || nt > tri_capacity)
+    return err(FGL_ERR_CAPACITY, "output buffers too small (the counts are in n_verts, n_tris)");
+  if (nv == 0 && nt == 0) return FGL_OK;
+  EmitArgs a{};
+  a.phi = phi;
+  a.nx = nx;
+  a.ny = ny;
+  a.step = step;
+  a.m = m;
+  a.ox = grid->origin[0];
+  a.oy = grid->origin[1];
+  a.oz = grid->origin[2];
+  a.h = grid->h;
+  a.iso = iso;
+  a.I = I;
+  a.X = X;
+  a.base_v = cv;
+  a.base_t = ct;
+  a.verts = out_verts;
+  a.tris = out_tris;
+  a.normals = out_normals;
+  k_mt_emit<<<word_blocks(nw, 128), 128, 0, s>>>(a);
+  MCUDA(cudaGetLastError());
+  return FGL_OK;
+}

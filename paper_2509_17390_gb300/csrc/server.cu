@@ -37,7 +37,7 @@
 #include "fgl.h"
 
 namespace fgl {
-void record_error(int status, const char* msg);
+void record_error(int status, const char* msg);  // api.cu
 }
 
 namespace {

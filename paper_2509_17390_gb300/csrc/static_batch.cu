@@ -26,9 +26,8 @@
 #include "kernels.h"
 
 namespace fgl {
-// Allocation-free item check + descriptor fill, and error recording (api.cu).
+// Allocation-free item check + descriptor fill (api.cu).
 const char* static_item_desc(const fgl_cast_item& it, ItemDesc* d, int* width);
-void record_error(int status, const char* msg);
 }  // namespace fgl
 
 using namespace fgl;

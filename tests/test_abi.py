@@ -177,3 +177,36 @@ def test_cast_argument_validation_without_gpu():
     el[2] = np.inf
     assert L.fgl_sensor_create(el.ctypes.data, el.ctypes.data, 6, 1, 6, 0, 0,
                                ctypes.byref(out)) == fgl.FGL_ERR_INVALID
+
+
+def test_mesh_argument_validation_without_gpu():
+    """fgl_denoise / fgl_tsdf / fgl_marching_tets reject bad arguments before
+    any CUDA call."""
+    L = fgl.lib()
+    F, I = ctypes.c_float, ctypes.c_int32
+    good = fgl.Grid((F * 3)(0, 0, 0), 0.1, (I * 3)(4, 4, 4), 0)
+    bad_dims = fgl.Grid((F * 3)(0, 0, 0), 0.1, (I * 3)(4, 0, 4), 0)
+    bad_h = fgl.Grid((F * 3)(0, 0, 0), float("nan"), (I * 3)(4, 4, 4), 0)
+    huge = fgl.Grid((F * 3)(0, 0, 0), 0.1, (I * 3)(2048, 2048, 1024), 0)
+    fake = ctypes.c_void_p(16)                      # never dereferenced: rejected first
+    nv, nt = ctypes.c_int64(), ctypes.c_int64()
+    E = fgl.FGL_ERR_INVALID
+    assert L.fgl_tsdf(None, ctypes.byref(good), 0.1, fake, None, None, None, None) == E
+    assert L.fgl_tsdf(fake, ctypes.byref(bad_dims), 0.1, fake, None, None, None, None) == E
+    assert L.fgl_tsdf(fake, ctypes.byref(bad_h), 0.1, fake, None, None, None, None) == E
+    assert L.fgl_tsdf(fake, ctypes.byref(good), 0.0, fake, None, None, None, None) == E
+    assert L.fgl_tsdf(fake, ctypes.byref(good), 26.0, fake, None, None, None, None) == E   # 260 shells
+    assert L.fgl_tsdf(fake, ctypes.byref(huge), 0.1, fake, None, None, None, None) == E
+    assert L.fgl_denoise(fake, ctypes.byref(good), 0.0, 0, 0.5, None, fake, None, None) == E
+    assert L.fgl_denoise(fake, ctypes.byref(good), 0.1, 2, 0.5, None, fake, None, None) == E
+    assert L.fgl_denoise(fake, ctypes.byref(good), 0.1, 1, 1.5, None, fake, None, None) == E
+    assert L.fgl_denoise(fake, ctypes.byref(good), 5.0, 0, 0.5, None, fake, None, None) == E  # 150 taps
+    assert L.fgl_denoise(fake, ctypes.byref(good), 0.1, 0, 0.5, None, None, None, None) == E
+    assert L.fgl_marching_tets(fake, ctypes.byref(good), 0.0, 0, None, 0, None, 0, None,
+                               ctypes.byref(nv), ctypes.byref(nt), None) == E
+    assert L.fgl_marching_tets(fake, ctypes.byref(good), float("inf"), 1, None, 0, None, 0, None,
+                               ctypes.byref(nv), ctypes.byref(nt), None) == E
+    assert L.fgl_marching_tets(fake, ctypes.byref(good), 0.0, 1, fake, 4, None, 4, None,
+                               ctypes.byref(nv), ctypes.byref(nt), None) == E
+    assert L.fgl_marching_tets(None, ctypes.byref(good), 0.0, 1, None, 0, None, 0, None,
+                               ctypes.byref(nv), ctypes.byref(nt), None) == E

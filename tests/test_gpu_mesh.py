@@ -1,0 +1,235 @@
+"""GPU parity of the mesh-reconstruction steps (paper Sec. IV-B) against the
+FP64 oracle, through the C-ABI.
+
+Contract:
+  * TSDF (fgl_tsdf): sign, shell index and phi bit-exact (integer decisions;
+    phi = s min((p + 1/2) h, r) rounds once on both sides);
+  * denoise (fgl_denoise): |V'_gpu - V'_oracle| <= oracle.blur_tolerance(R);
+    the mask equal wherever V'_oracle is farther than that from the
+    threshold; the quantile threshold is exactly the order statistic of the
+    GPU's own float32 V';
+  * marching tetrahedra (fgl_marching_tets): vertex and triangle counts and
+    every triangle's vertex ids exact (the inside test phi < iso is exact and
+    the order canonical); vertices within oracle.vertex_tolerance; normals
+    within 1e-4 where the gradient is not tiny.
+"""
+
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+fgl = pytest.importorskip("paper_2509_17390_gb300")
+
+
+def cu(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def random_binary(rng, shape, p):
+    return (rng.random(shape) < p).astype(np.uint8)
+
+
+def hollow_sphere(n, c, r0, r1):
+    z, y, x = np.indices(n)
+    d = np.sqrt((x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2)
+    return ((d >= r0) & (d < r1)).astype(np.uint8)
+
+
+# -- TSDF -----------------------------------------------------------------------
+
+TSDF_CASES = [((23, 17, 70), 0.2, 0.02, 0.05), ((9, 40, 33), 0.45, 0.03, 0.09),
+              ((30, 31, 65), 0.05, 0.015, 0.06), ((1, 1, 1), 0.5, 0.1, 0.1), ((1, 5, 1), 0.5, 0.1, 0.25),
+              ((7, 1, 97), 0.3, 0.01, 0.035)]
+
+
+@pytest.mark.parametrize("shape,p,h,r", TSDF_CASES)
+def test_tsdf_bit_exact(shape, p, h, r):
+    rng = np.random.default_rng(sum(shape))
+    V = random_binary(rng, shape, p)
+    phi, out, sh, st = fgl.tsdf(cu(V), h, r, outside=True, shell=True, timing=True)
+    phi_o, out_o, p_o = oracle.tsdf(V, h, r)
+    assert np.array_equal(out.cpu().numpy(), out_o)
+    assert np.array_equal(sh.cpu().numpy(), p_o)
+    assert np.array_equal(phi.cpu().numpy().view(np.uint32), phi_o.view(np.uint32))
+    assert st["n_layers"] == oracle.band_layers(h, r) and st["ms_total"] > 0
+
+
+def test_tsdf_cavities_and_degenerate_grids():
+    V = hollow_sphere((40, 36, 45), (22.3, 17.6, 20.1), 9.0, 10.5)
+    V[2:6, 2:6, 2:6] = 1
+    V[3:5, 3:5, 3:5] = 0                                     # a tiny closed box: second cavity
+    for grid in (V, np.ones((5, 6, 7), np.uint8), np.zeros((5, 6, 7), np.uint8)):
+        phi, out, sh, _ = fgl.tsdf(cu(grid), 0.02, 0.07, outside=True, shell=True)
+        phi_o, out_o, p_o = oracle.tsdf(grid, 0.02, 0.07)
+        assert np.array_equal(out.cpu().numpy(), out_o)
+        assert np.array_equal(sh.cpu().numpy(), p_o)
+        assert np.array_equal(phi.cpu().numpy(), phi_o)
+    o = fgl.tsdf(cu(V), 0.02, 0.07, outside=True)[1].cpu().numpy()
+    assert o[20, 17, 22] == 0 and o[4, 4, 4] == 0 and o[0, 0, 0] == 1
+
+
+def test_tsdf_large_grid_vs_oracle():
+    """A 160 x 150 x 170 grid (4.1 M voxels, 5 words a row) of thin shells,
+    slabs and noise: bit-exact."""
+    rng = np.random.default_rng(77)
+    shape = (170, 150, 160)
+    V = hollow_sphere(shape, (80.2, 75.5, 85.3), 50.0, 51.5)
+    V |= hollow_sphere(shape, (40.0, 40.0, 40.0), 20.0, 21.0)
+    V[:, 100:102, :] |= 1
+    V |= random_binary(rng, shape, 0.002)
+    phi, out, sh, _ = fgl.tsdf(cu(V), 0.015, 0.06, outside=True, shell=True)
+    phi_o, out_o, p_o = oracle.tsdf(V, 0.015, 0.06)
+    assert np.array_equal(out.cpu().numpy(), out_o)
+    assert np.array_equal(sh.cpu().numpy(), p_o)
+    assert np.array_equal(phi.cpu().numpy(), phi_o)
+
+
+# -- denoise ----------------------------------------------------------------------
+
+@pytest.mark.parametrize("shape,sigma_vox", [((21, 30, 47), 0.5), ((12, 13, 70), 1.3), ((5, 4, 3), 2.0)])
+def test_denoise_fixed_threshold(shape, sigma_vox):
+    rng = np.random.default_rng(int(sigma_vox * 10))
+    V = random_binary(rng, shape, 0.2)
+    V[V.shape[0] // 2] = 1                                   # a plane that survives
+    h = 0.02
+    sigma = np.float32(sigma_vox * h)
+    mask, vp, thr = fgl.denoise(cu(V), h, float(sigma), tau=0.3, blur=True)
+    sv = np.float64(sigma) / np.float64(np.float32(h))
+    R = oracle.blur_radius(sv)
+    vp_o = oracle.blur(V, sv, R)
+    tol = oracle.blur_tolerance(R)
+    err = np.abs(vp.cpu().numpy().astype(np.float64) - vp_o)
+    assert err.max() <= tol, (err.max(), tol)
+    m_o, _ = oracle.rethreshold(vp_o, "fixed", 0.3)
+    clear = np.abs(vp_o - np.float32(0.3)) > tol
+    assert np.array_equal(mask.cpu().numpy()[clear], m_o[clear]) and thr == np.float32(0.3)
+    # the mask follows from the GPU's own V' exactly
+    assert np.array_equal(mask.cpu().numpy(), (vp.cpu().numpy() >= np.float32(0.3)).astype(np.uint8))
+
+
+@pytest.mark.parametrize("q", [0.0, 0.37, 0.9, 1.0])
+def test_denoise_quantile_is_the_exact_order_statistic(q):
+    rng = np.random.default_rng(5)
+    V = random_binary(rng, (19, 23, 41), 0.3)
+    mask, vp, thr = fgl.denoise(cu(V), 0.01, 0.012, quantile=q, blur=True)
+    g = vp.cpu().numpy()
+    m_own, thr_own = oracle.rethreshold(g, "quantile", q)
+    assert np.float32(thr) == np.float32(thr_own)
+    assert np.array_equal(mask.cpu().numpy(), m_own)
+    # and within the blur tolerance of the oracle's FP64 quantile
+    sv = np.float64(np.float32(0.012)) / np.float64(np.float32(0.01))
+    _, thr_o = oracle.rethreshold(oracle.blur(V, sv), "quantile", q)
+    assert abs(thr - thr_o) <= oracle.blur_tolerance(oracle.blur_radius(sv))
+
+
+# -- marching tetrahedra ----------------------------------------------------------
+
+def check_mt(phi, origin, h, iso=0.0, step=1, normals=True):
+    v, t, n = fgl.marching_tets(cu(phi), origin, h, iso=iso, step=step, normals=normals)
+    vo, to, no = oracle.marching_tets(phi, origin, h, iso=iso, step=step, normals=normals)
+    v, t = v.cpu().numpy(), t.cpu().numpy()
+    assert v.shape == vo.shape and t.shape == to.shape
+    assert np.array_equal(t, to)
+    if len(v):
+        assert np.max(np.abs(v - vo)) <= oracle.vertex_tolerance(vo, h * step)
+    if normals and len(v):
+        n = n.cpu().numpy()
+        ok = np.linalg.norm(no, axis=1) > 0.5                   # unit where the oracle's gradient is nonzero
+        assert np.max(np.abs(n[ok] - no[ok]), initial=0) < 1e-4
+    return v, t
+
+
+def sphere_phi(shape, h, c, R):
+    z, y, x = np.indices(shape)
+    P = np.stack([x, y, z], -1) * h + h / 2
+    return (np.linalg.norm(P - c, axis=-1) - R).astype(np.float32)
+
+
+@pytest.mark.parametrize("step", [1, 2, 3])
+def test_marching_tets_tsdf_field(step):
+    V = hollow_sphere((41, 38, 70), (35.2, 19.1, 20.4), 11.0, 12.5)
+    V[10:14, :, :] = 1
+    phi, _, _ = oracle.tsdf(V, 0.02, 0.06)
+    v, t = check_mt(phi, (-0.3, 0.1, 0.25), 0.02, step=step)
+    assert len(t) > 100
+
+
+@pytest.mark.parametrize("iso", [0.0, 0.013, -0.2])
+def test_marching_tets_random_and_analytic_fields(iso):
+    rng = np.random.default_rng(9)
+    check_mt(rng.standard_normal((13, 9, 40)).astype(np.float32), (0.0, 0.0, 0.0), 0.1, iso=iso)
+    check_mt(sphere_phi((36, 40, 66), 0.03, np.array([1.0, 0.6, 0.55]), 0.45), (0.0, 0.0, 0.0), 0.03,
+             iso=iso)
+
+
+def test_marching_tets_edge_cases_and_capacity():
+    # no crossing, a single sample, one row, a degenerate thin grid
+    for phi in (np.ones((4, 5, 6), np.float32), np.ones((1, 1, 1), np.float32),
+                np.linspace(-1, 1, 70, dtype=np.float32).reshape(1, 1, 70),
+                np.random.default_rng(1).standard_normal((2, 1, 33)).astype(np.float32)):
+        check_mt(phi, (0.0, 0.0, 0.0), 0.5, normals=False)
+    # undersized buffers through the C-ABI: FGL_ERR_CAPACITY with the counts
+    phi = sphere_phi((20, 20, 20), 0.1, np.array([1.0, 1.0, 1.0]), 0.6)
+    d = cu(phi)
+    vo, to, _ = oracle.marching_tets(phi, (0, 0, 0), 0.1)
+    g = fgl.Grid((ctypes.c_float * 3)(0, 0, 0), 0.1, (ctypes.c_int32 * 3)(20, 20, 20), 0)
+    vb = torch.empty((4, 3), dtype=torch.float32, device="cuda")
+    tb = torch.empty((4, 3), dtype=torch.int32, device="cuda")
+    nv, nt = ctypes.c_int64(), ctypes.c_int64()
+    st = fgl.lib().fgl_marching_tets(ctypes.c_void_p(d.data_ptr()), ctypes.byref(g), 0.0, 1,
+                                     ctypes.c_void_p(vb.data_ptr()), 4, ctypes.c_void_p(tb.data_ptr()), 4,
+                                     None, ctypes.byref(nv), ctypes.byref(nt), None)
+    assert st == fgl.FGL_ERR_CAPACITY and (nv.value, nt.value) == (len(vo), len(to))
+    v, t, _ = fgl.marching_tets(d, (0, 0, 0), 0.1, capacity=(10, 10))   # retried at the counts
+    assert np.array_equal(t.cpu().numpy(), to)
+    with pytest.raises(fgl.FglError):
+        fgl.marching_tets(d, (0, 0, 0), 0.1, step=0)
+
+
+# -- the GPU pipeline: Gaussians -> mesh -------------------------------------------
+
+def edge_stats(tris):
+    e = np.concatenate([tris[:, [0, 1]], tris[:, [1, 2]], tris[:, [2, 0]]])
+    _, cu_ = np.unique(np.sort(e, axis=1), axis=0, return_counts=True)
+    _, cd = np.unique(e, axis=0, return_counts=True)
+    return bool(np.all(cu_ == 2)), bool(np.all(cd == 1))
+
+
+def test_pipeline_from_gaussians_matches_oracle_steps():
+    """Gaussians on a small open-topped room: the GPU's surface grid goes
+    through the oracle's blur (within tolerance, mask equal away from the
+    threshold), then the GPU's mask through the oracle's TSDF and marching
+    tetrahedra, which the GPU pipeline's mesh matches exactly; the mesh is
+    closed and consistently oriented."""
+    from synth import gaussians
+    gs = gaussians.gaussian_room(12, (2.0, 1.5, 1.0), 40_000, 1, 1)
+    h = 0.04
+    origin = (-0.6, -0.6, -0.6)                              # 3 sigma of the largest Gaussian
+    dims = (int(np.ceil(3.2 / h)), int(np.ceil(2.7 / h)), int(np.ceil(2.2 / h)))
+    t = lambda a: cu(a)
+    D, occ, surf, _ = fgl.gaussian_density(t(gs.mu), t(gs.scale), t(gs.quat), t(gs.alpha), origin, h, dims)
+    S = surf.cpu().numpy()
+    mask, vp, _ = fgl.denoise(surf, h, 0.5 * h, tau=0.5, blur=True)
+    sv = np.float64(np.float32(0.5 * h)) / np.float64(np.float32(h))
+    vp_o = oracle.blur(S, sv)
+    tol = oracle.blur_tolerance(oracle.blur_radius(sv))
+    assert np.abs(vp.cpu().numpy() - vp_o).max() <= tol
+    M = mask.cpu().numpy()
+    clear = np.abs(vp_o - 0.5) > tol
+    assert np.array_equal(M[clear], oracle.rethreshold(vp_o, "fixed", 0.5)[0][clear])
+    # downstream of the GPU's own mask the steps are exact
+    phi_o, _, _ = oracle.tsdf(M, h, 0.06)
+    vo, to, _ = oracle.marching_tets(phi_o, origin, h)
+    v, tr, _ = fgl.mesh_from_gaussians(t(gs.mu), t(gs.scale), t(gs.quat), t(gs.alpha), origin, h, dims,
+                                       trunc=0.06)
+    tr = tr.cpu().numpy()
+    assert np.array_equal(tr, to)
+    assert np.max(np.abs(v.cpu().numpy() - vo)) <= oracle.vertex_tolerance(vo, h)
+    closed, oriented = edge_stats(tr)
+    assert closed and oriented and len(tr) > 10_000
