@@ -293,23 +293,39 @@ __global__ void __launch_bounds__(DensityCfg<B>::THREADS)
   }
 }
 
+// eqs. V_occ, Int, Surf: x over blockIdx.x, rows (y, z) strided over
+// blockIdx.y with (y, z) stepped without a division per row; an occupied
+// voxel loads its six neighbours at once
 __global__ void k_occ_surf(const float* __restrict__ D, GridArgs g, float theta,
                            uint8_t* __restrict__ occ, uint8_t* __restrict__ surf) {
-  const int64_t n = (int64_t)g.dims[0] * g.dims[1] * g.dims[2];
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
   const int nx = g.dims[0], ny = g.dims[1], nz = g.dims[2];
-  const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((int64_t)nx * ny));
-  const bool o = D[i] > theta;
-  bool interior = o;
-  if (interior) interior = x > 0 && D[i - 1] > theta;
-  if (interior) interior = x + 1 < nx && D[i + 1] > theta;
-  if (interior) interior = y > 0 && D[i - nx] > theta;
-  if (interior) interior = y + 1 < ny && D[i + nx] > theta;
-  if (interior) interior = z > 0 && D[i - (int64_t)nx * ny] > theta;
-  if (interior) interior = z + 1 < nz && D[i + (int64_t)nx * ny] > theta;
-  if (occ) occ[i] = o ? 1 : 0;
-  if (surf) surf[i] = (o && !interior) ? 1 : 0;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= nx) return;
+  const int64_t rows = (int64_t)ny * nz, plane = (int64_t)nx * ny;
+  int y = (int)(blockIdx.y % ny), z = (int)(blockIdx.y / ny);
+  const int dy = (int)(gridDim.y % ny), dz = (int)(gridDim.y / ny);
+  for (int64_t row = blockIdx.y; row < rows; row += gridDim.y) {
+    const int64_t i = row * nx + x;
+    const bool o = D[i] > theta;
+    bool interior = false;
+    if (o) {
+      const bool xm = x > 0 && D[i - 1] > theta;
+      const bool xp = x + 1 < nx && D[i + 1] > theta;
+      const bool ym = y > 0 && D[i - nx] > theta;
+      const bool yp = y + 1 < ny && D[i + nx] > theta;
+      const bool zm = z > 0 && D[i - plane] > theta;
+      const bool zp = z + 1 < nz && D[i + plane] > theta;
+      interior = xm && xp && ym && yp && zm && zp;
+    }
+    if (occ) occ[i] = o ? 1 : 0;
+    if (surf) surf[i] = (o && !interior) ? 1 : 0;
+    y += dy;
+    z += dz;
+    if (y >= ny) {
+      y -= ny;
+      ++z;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -493,8 +509,10 @@ extern "C" fgl_status fgl_gaussian_density(const fgl_gaussians* gs, const fgl_gr
     DCUDA(cudaMemsetAsync(out_density, 0, (size_t)n_vox * sizeof(float), s));
   }
   if (out_occ || out_surf) {
-    k_occ_surf<<<(unsigned)((n_vox + 255) / 256), 256, 0, s>>>(out_density, g, theta, out_occ,
-                                                               out_surf);
+    const int bx = (grid->dims[0] + 127) / 128;
+    const int64_t rows = (int64_t)grid->dims[1] * grid->dims[2];
+    const dim3 og((unsigned)bx, (unsigned)std::max<int64_t>(1, std::min<int64_t>(rows, 4096 / bx)));
+    k_occ_surf<<<og, 128, 0, s>>>(out_density, g, theta, out_occ, out_surf);
     ++launches;
     DCUDA(cudaGetLastError());
   }

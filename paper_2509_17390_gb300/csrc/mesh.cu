@@ -14,12 +14,13 @@
 //                    eq. rethresh with a fixed tau or the exact order statistic
 //                    of rank floor(q (N - 1)) by a four-pass radix select on
 //                    the float bit patterns (V' >= 0, so they sort as u32).
-// fgl_tsdf           sign: a lock-free union-find over the free voxels with a
-//                    virtual root 0 standing for the padded frame (every free
-//                    voxel on the grid's faces starts linked to it; a link
-//                    always goes from the larger root to the smaller, so the
-//                    frame's component ends under 0); one pass, no flood
-//                    rounds.  Shells: S_0 from word XORs with the six
+// fgl_tsdf           sign: a lock-free union-find over the free x-runs of the
+//                    rows with a virtual root 0 standing for the padded frame
+//                    (every run touching the grid's faces starts linked to
+//                    it; a link always goes from the larger root to the
+//                    smaller, so the frame's component ends under 0): runs of
+//                    adjacent rows that overlap are united once per overlap
+//                    segment, a warp per row; no flood rounds.  Shells: S_0 from word XORs with the six
 //                    neighbours, then L = ceil(r / h) word dilations; p(x) is
 //                    the first mask holding x.  phi = s min((p + 1/2) h, r).
 // fgl_marching_tets  sign bits of the sample grid; per word, the crossing
@@ -69,35 +70,70 @@ __device__ __forceinline__ uint32_t valid_bits_next(const BitGrid& g, int xw) {
 // packing
 // ---------------------------------------------------------------------------
 
-// one warp per word: bit b = V[row, 32 xw + b] != 0
+constexpr int kPackWords = 8;  // words per warp step (independent loads in flight)
+
+// one warp per row, kPackWords words a step: bit b of word xw = V[row, 32 xw + b] != 0
 __global__ void k_pack_u8(const uint8_t* __restrict__ V, BitGrid g, uint32_t* __restrict__ out) {
   const int lane = threadIdx.x & 31;
   const int64_t n_warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < g.words(); w += n_warps) {
-    const int64_t row = w / g.mw;
-    const int x = (int)(w - row * g.mw) * 32 + lane;
-    const bool bit = x < g.nx && V[row * g.nx + x] != 0;
-    const uint32_t m = __ballot_sync(0xFFFFFFFFu, bit);
-    if (lane == 0) out[w] = m;
+  for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < g.rows(); row += n_warps) {
+    const uint8_t* src = V + row * g.nx;
+    uint32_t* dst = out + row * g.mw;
+    for (int xw0 = 0; xw0 < g.mw; xw0 += kPackWords) {
+      uint32_t mine = 0;
+#pragma unroll
+      for (int u = 0; u < kPackWords; ++u) {
+        const int x = (xw0 + u) * 32 + lane;
+        const uint32_t m = __ballot_sync(0xFFFFFFFFu, x < g.nx && src[x] != 0);
+        if (lane == u) mine = m;
+      }
+      if (lane < kPackWords && xw0 + lane < g.mw) dst[xw0 + lane] = mine;
+    }
   }
 }
 
-// one warp per word of the sample grid m (every step-th voxel of the nx x ny
-// voxel grid): bit = phi < iso
+// the same on the sample grid m (every step-th voxel of the nx x ny voxel
+// grid): bit = phi < iso
 __global__ void k_pack_inside(const float* __restrict__ phi, int nx, int ny, int step, BitGrid m,
                               float iso, uint32_t* __restrict__ out) {
   const int lane = threadIdx.x & 31;
   const int64_t n_warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < m.words(); w += n_warps) {
-    const int64_t row = w / m.mw;
-    const int x = (int)(w - row * m.mw) * 32 + lane;
-    const int j = (int)(row % m.ny), k = (int)(row / m.ny);
-    bool bit = false;
-    if (x < m.nx) bit = phi[((int64_t)k * step * ny + (int64_t)j * step) * nx + (int64_t)x * step] < iso;
-    const uint32_t mask = __ballot_sync(0xFFFFFFFFu, bit);
-    if (lane == 0) out[w] = mask;
+  for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < m.rows(); row += n_warps) {
+    const int j = (int)((uint32_t)row % (uint32_t)m.ny), k = (int)((uint32_t)row / (uint32_t)m.ny);
+    const float* src = phi + ((int64_t)k * step * ny + (int64_t)j * step) * nx;
+    uint32_t* dst = out + row * m.mw;
+    for (int xw0 = 0; xw0 < m.mw; xw0 += kPackWords) {
+      uint32_t mine = 0;
+#pragma unroll
+      for (int u = 0; u < kPackWords; ++u) {
+        const int x = (xw0 + u) * 32 + lane;
+        const uint32_t mk = __ballot_sync(0xFFFFFFFFu, x < m.nx && src[(int64_t)x * step] < iso);
+        if (lane == u) mine = mk;
+      }
+      if (lane < kPackWords && xw0 + lane < m.mw) dst[xw0 + lane] = mine;
+    }
   }
 }
+
+// rows row0, row0 + stride, ... of a grid with ny rows a plane, as (j, k)
+// without a division per row
+struct RowWalk {
+  int j, k, dj, dk, ny;
+  __device__ RowWalk(int64_t row0, int64_t stride, int ny_) : ny(ny_) {
+    j = (int)(row0 % ny_);
+    k = (int)(row0 / ny_);
+    dj = (int)(stride % ny_);
+    dk = (int)(stride / ny_);
+  }
+  __device__ __forceinline__ void next() {
+    j += dj;
+    k += dk;
+    if (j >= ny) {
+      j -= ny;
+      ++k;
+    }
+  }
+};
 
 // ---------------------------------------------------------------------------
 // eq. V': separable blur and eq. rethresh
@@ -120,8 +156,9 @@ __global__ void k_blur(const TIn* __restrict__ in, float* __restrict__ out, int 
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= nx) return;
   const int64_t rows = (int64_t)ny * nz;
-  for (int64_t row = blockIdx.y; row < rows; row += gridDim.y) {
-    const int j = (int)(row % ny), k = (int)(row / ny);
+  RowWalk rw(blockIdx.y, gridDim.y, ny);
+  for (int64_t row = blockIdx.y; row < rows; row += gridDim.y, rw.next()) {
+    const int j = rw.j, k = rw.k;
     const int64_t v = row * nx + x;
     const int c = AXIS == 0 ? x : AXIS == 1 ? j : k;
     const int lim = AXIS == 0 ? nx : AXIS == 1 ? ny : nz;
@@ -133,6 +170,105 @@ __global__ void k_blur(const TIn* __restrict__ in, float* __restrict__ out, int 
       s += taps.w[t + taps.R] * unit(in[v + t * stride]);
     }
     out[v] = s;
+  }
+}
+
+// Fused eq. V' for R <= 4: one block per 32 x 8 x 8 output tile stages the
+// input with a halo of R in shared memory as 0/1 bytes, then the x, y and z
+// passes run in shared memory and the tile writes V' (when asked) and the
+// fixed-threshold mask (when asked).  Taps sum in the same ascending order
+// as k_blur; a tap outside the grid adds w * 0, which leaves the sum bitwise
+// unchanged, so both paths agree bit for bit.
+constexpr int kBTX = 32, kBTY = 8, kBTZ = 8;
+
+template <int R>
+constexpr size_t fused_blur_smem() {
+  return ((size_t)(kBTX + 2 * R) * (kBTY + 2 * R) * (kBTZ + 2 * R) + 15) / 16 * 16 +
+         sizeof(float) * ((size_t)kBTX * (kBTY + 2 * R) * (kBTZ + 2 * R) + (size_t)kBTX * kBTY * (kBTZ + 2 * R));
+}
+
+template <int R>
+__global__ void __launch_bounds__(256) k_blur_fused(const uint8_t* __restrict__ in, int nx, int ny, int nz,
+                                                    Taps taps, float thr, float* __restrict__ out_blur,
+                                                    uint8_t* __restrict__ out_mask) {
+  constexpr int EX = kBTX + 2 * R, EY = kBTY + 2 * R, EZ = kBTZ + 2 * R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint8_t* s_in = smem_raw;
+  float* s_x = (float*)(smem_raw + ((size_t)EX * EY * EZ + 15) / 16 * 16);  // [EZ][EY][kBTX]
+  float* s_y = s_x + kBTX * EY * EZ;                                        // [EZ][kBTY][kBTX]
+  const int x0 = blockIdx.x * kBTX, y0 = blockIdx.y * kBTY, z0 = blockIdx.z * kBTZ;
+  const int tid = threadIdx.x;
+  constexpr int kIn = EX * EY * EZ, kLoads = (kIn + 255) / 256;
+  uint8_t v[kLoads];  // every load issued before the first shared store: one memory latency
+#pragma unroll
+  for (int u = 0; u < kLoads; ++u) {
+    const int i = tid + 256 * u;
+    const int ex = i % EX, ey = (i / EX) % EY, ez = i / (EX * EY);
+    const int gx = x0 - R + ex, gy = y0 - R + ey, gz = z0 - R + ez;
+    v[u] = 0;
+    if (i < kIn && gx >= 0 && gy >= 0 && gz >= 0 && gx < nx && gy < ny && gz < nz)
+      v[u] = in[((int64_t)gz * ny + gy) * nx + gx] != 0;
+  }
+#pragma unroll
+  for (int u = 0; u < kLoads; ++u)
+    if (tid + 256 * u < kIn) s_in[tid + 256 * u] = v[u];
+  __syncthreads();
+  for (int i = tid; i < kBTX * EY * EZ; i += 256) {
+    const int ox = i % kBTX, r = i / kBTX;  // r = ez * EY + ey
+    const uint8_t* src = s_in + r * EX + ox;
+    float acc = 0.f;
+#pragma unroll
+    for (int t = 0; t <= 2 * R; ++t) acc += taps.w[t] * (float)src[t];
+    s_x[i] = acc;
+  }
+  __syncthreads();
+  for (int i = tid; i < kBTX * kBTY * EZ; i += 256) {
+    const int ox = i % kBTX, oy = (i / kBTX) % kBTY, ez = i / (kBTX * kBTY);
+    const float* src = s_x + (ez * EY + oy) * kBTX + ox;
+    float acc = 0.f;
+#pragma unroll
+    for (int t = 0; t <= 2 * R; ++t) acc += taps.w[t] * src[t * kBTX];
+    s_y[i] = acc;
+  }
+  __syncthreads();
+  for (int i = tid; i < kBTX * kBTY * kBTZ; i += 256) {
+    const int ox = i % kBTX, oy = (i / kBTX) % kBTY, oz = i / (kBTX * kBTY);
+    const int gx = x0 + ox, gy = y0 + oy, gz = z0 + oz;
+    if (gx >= nx || gy >= ny || gz >= nz) continue;
+    const float* src = s_y + (oz * kBTY + oy) * kBTX + ox;
+    float acc = 0.f;
+#pragma unroll
+    for (int t = 0; t <= 2 * R; ++t) acc += taps.w[t] * src[t * kBTX * kBTY];
+    const int64_t v = ((int64_t)gz * ny + gy) * nx + gx;
+    if (out_blur) out_blur[v] = acc;
+    if (out_mask) out_mask[v] = acc >= thr ? 1 : 0;
+  }
+}
+
+template <int R>
+cudaError_t launch_blur_fused(const uint8_t* in, int nx, int ny, int nz, const Taps& taps, float thr,
+                              float* out_blur, uint8_t* out_mask, cudaStream_t s) {
+  constexpr size_t smem = fused_blur_smem<R>();
+  static bool attr_set = false;  // per template instance; the value never changes
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_blur_fused<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const dim3 grid((unsigned)((nx + kBTX - 1) / kBTX), (unsigned)((ny + kBTY - 1) / kBTY),
+                  (unsigned)((nz + kBTZ - 1) / kBTZ));
+  k_blur_fused<R><<<grid, 256, smem, s>>>(in, nx, ny, nz, taps, thr, out_blur, out_mask);
+  return cudaGetLastError();
+}
+
+cudaError_t blur_fused(int R, const uint8_t* in, int nx, int ny, int nz, const Taps& taps, float thr,
+                       float* out_blur, uint8_t* out_mask, cudaStream_t s) {
+  switch (R) {
+    case 1: return launch_blur_fused<1>(in, nx, ny, nz, taps, thr, out_blur, out_mask, s);
+    case 2: return launch_blur_fused<2>(in, nx, ny, nz, taps, thr, out_blur, out_mask, s);
+    case 3: return launch_blur_fused<3>(in, nx, ny, nz, taps, thr, out_blur, out_mask, s);
+    case 4: return launch_blur_fused<4>(in, nx, ny, nz, taps, thr, out_blur, out_mask, s);
+    default: return cudaErrorInvalidValue;
   }
 }
 
@@ -196,7 +332,8 @@ __global__ void k_sel_pick(SelState* st, int shift, uint32_t* hist) {
 }
 
 // ---------------------------------------------------------------------------
-// sign: union-find over free voxels (labels v + 1; 0 = the padded frame)
+// sign: union-find over the free runs of the rows (a run's label is its
+// first voxel's index + 1; 0 = the padded frame)
 // ---------------------------------------------------------------------------
 
 // Root of x.  Parents only ever decrease along a path, so the walk ends
@@ -234,55 +371,133 @@ __device__ __forceinline__ void uf_unite(uint32_t* parent, uint32_t a, uint32_t 
   atomicOr(err, 2);
 }
 
-__device__ __forceinline__ bool bit_at(const uint32_t* __restrict__ bits, const BitGrid& g,
-                                       int64_t row, int x) {
-  return (bits[row * g.mw + (x >> 5)] >> (x & 31)) & 1u;
+// Free runs of a row, 32 words at a time: lane l holds word xw = base + l.
+struct RowChunk {
+  uint32_t F;   // free bits of the word (0 past the row)
+  uint32_t st;  // run starts: free bits whose x - 1 is not free, or x = 0
+  int before;   // position in the row of the last run start before this word (-1: none)
+};
+
+// One chunk of a row.  carry_pos / carry_bit: the last start position and
+// the free bit 31 of the previous chunk's last word (updated).
+__device__ __forceinline__ RowChunk row_chunk(const uint32_t* __restrict__ Vb, const BitGrid& g,
+                                              int64_t row, int base, int lane, int& carry_pos,
+                                              uint32_t& carry_bit) {
+  const int xw = base + lane;
+  RowChunk c;
+  c.F = xw < g.mw ? ~Vb[row * g.mw + xw] & valid_bits(g, xw) : 0u;
+  uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, c.F, 1) >> 31;
+  if (lane == 0) prev = carry_bit;
+  c.st = c.F & ~((c.F << 1) | prev);
+  int incl = c.st ? xw * 32 + 31 - __clz(c.st) : -1;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int o = __shfl_up_sync(0xFFFFFFFFu, incl, off);
+    if (lane >= off) incl = max(incl, o);
+  }
+  incl = max(incl, carry_pos);
+  int excl = __shfl_up_sync(0xFFFFFFFFu, incl, 1);
+  if (lane == 0) excl = carry_pos;
+  c.before = excl;
+  carry_pos = __shfl_sync(0xFFFFFFFFu, incl, 31);
+  carry_bit = __shfl_sync(0xFFFFFFFFu, c.F, 31) >> 31;
+  return c;
 }
 
-// parent[v + 1] = 0 for a free voxel on a face of the grid, else v + 1
-__global__ void k_uf_init(const uint32_t* __restrict__ Vb, BitGrid g, uint32_t* __restrict__ parent) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (blockIdx.y == 0 && x == 0) parent[0] = 0;
-  if (x >= g.nx) return;
-  for (int64_t row = blockIdx.y; row < g.rows(); row += gridDim.y) {
+// label (run start + 1, as a voxel index of the row) of the run holding the
+// free bit s of word xw
+__device__ __forceinline__ uint32_t run_label(const RowChunk& c, int xw, int s, int64_t row, int nx) {
+  const uint32_t m = c.st & ((2u << s) - 1u);
+  const int pos = m ? xw * 32 + 31 - __clz(m) : c.before;
+  return (uint32_t)(row * nx + pos + 1);
+}
+
+// Every run start gets its own label as parent, or 0 when the run touches
+// the padded frame: a run on a face row (y or z at the grid's border), the
+// run starting at x = 0 and the run holding x = nx - 1.  One warp per row.
+__global__ void k_run_init(const uint32_t* __restrict__ Vb, BitGrid g, uint32_t* __restrict__ parent) {
+  const int lane = threadIdx.x & 31;
+  const int64_t n_warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  if (blockIdx.x == 0 && threadIdx.x == 0) parent[0] = 0;
+  for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < g.rows(); row += n_warps) {
     const int j = (int)(row % g.ny), k = (int)(row / g.ny);
-    const int64_t v = row * g.nx + x;
-    const bool face = x == 0 || j == 0 || k == 0 || x == g.nx - 1 || j == g.ny - 1 || k == g.nz - 1;
-    const bool free_ = !bit_at(Vb, g, row, x);
-    parent[v + 1] = (free_ && face) ? 0u : (uint32_t)(v + 1);
+    const bool face = j == 0 || k == 0 || j == g.ny - 1 || k == g.nz - 1;
+    int cp = -1;
+    uint32_t cb = 0;
+    for (int base = 0; base < g.mw; base += 32) {
+      const RowChunk c = row_chunk(Vb, g, row, base, lane, cp, cb);
+      const int xw = base + lane;
+      for (uint32_t m = c.st; m; m &= m - 1) {
+        const int x = xw * 32 + __ffs(m) - 1;
+        const uint32_t L = (uint32_t)(row * g.nx + x + 1);
+        parent[L] = (face || x == 0) ? 0u : L;
+      }
+    }
+    __syncwarp();
+    const int xl = g.nx - 1;
+    if (lane == 0 && cp >= 0 && !((Vb[row * g.mw + (xl >> 5)] >> (xl & 31)) & 1u))
+      parent[(uint32_t)(row * g.nx + cp + 1)] = 0u;
   }
 }
 
-// every free voxel joins its free -x, -y and -z neighbours
-__global__ void k_uf_merge(const uint32_t* __restrict__ Vb, BitGrid g, uint32_t* parent, int* err) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= g.nx) return;
-  const uint32_t limit = (uint32_t)(g.rows() * g.nx + 2);
-  for (int64_t row = blockIdx.y; row < g.rows(); row += gridDim.y) {
-    if (bit_at(Vb, g, row, x)) continue;
-    const int j = (int)(row % g.ny), k = (int)(row / g.ny);
-    const uint32_t a = (uint32_t)(row * g.nx + x + 1);
-    if (x > 0 && !bit_at(Vb, g, row, x - 1)) uf_unite(parent, a, a - 1, limit, err);
-    if (j > 0 && !bit_at(Vb, g, row - 1, x)) uf_unite(parent, a, a - (uint32_t)g.nx, limit, err);
-    if (k > 0 && !bit_at(Vb, g, row - g.ny, x))
-      uf_unite(parent, a, a - (uint32_t)((int64_t)g.nx * g.ny), limit, err);
-  }
-}
-
-// outside word: free voxels whose root is the frame
-__global__ void k_uf_outside(const uint32_t* __restrict__ Vb, BitGrid g, uint32_t* parent,
-                             uint32_t* __restrict__ Ob, int* err) {
+// Runs of adjacent rows (-y, -z) that share a free voxel are one component:
+// one union per overlap segment.  One warp per row.
+__global__ void k_run_union(const uint32_t* __restrict__ Vb, BitGrid g, uint32_t* parent, int* err) {
   const int lane = threadIdx.x & 31;
   const int64_t n_warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   const uint32_t limit = (uint32_t)(g.rows() * g.nx + 2);
-  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < g.words(); w += n_warps) {
-    const int64_t row = w / g.mw;
-    const int x = (int)(w - row * g.mw) * 32 + lane;
-    bool out = false;
-    if (x < g.nx && !((Vb[w] >> lane) & 1u))
-      out = uf_find(parent, (uint32_t)(row * g.nx + x + 1), limit, err) == 0u;
-    const uint32_t m = __ballot_sync(0xFFFFFFFFu, out);
-    if (lane == 0) Ob[w] = m;
+  for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < g.rows(); row += n_warps) {
+    const int j = (int)(row % g.ny), k = (int)(row / g.ny);
+    for (int nb = 0; nb < 2; ++nb) {
+      if (nb == 0 ? j == 0 : k == 0) continue;
+      const int64_t row2 = nb == 0 ? row - 1 : row - g.ny;
+      int cp = -1, cp2 = -1;
+      uint32_t cb = 0, cb2 = 0, ocarry = 0;
+      for (int base = 0; base < g.mw; base += 32) {
+        const RowChunk a = row_chunk(Vb, g, row, base, lane, cp, cb);
+        const RowChunk b = row_chunk(Vb, g, row2, base, lane, cp2, cb2);
+        const uint32_t O = a.F & b.F;
+        uint32_t oprev = __shfl_up_sync(0xFFFFFFFFu, O, 1) >> 31;
+        if (lane == 0) oprev = ocarry;
+        ocarry = __shfl_sync(0xFFFFFFFFu, O, 31) >> 31;
+        const int xw = base + lane;
+        for (uint32_t m = O & ~((O << 1) | oprev); m; m &= m - 1) {
+          const int s = __ffs(m) - 1;
+          uf_unite(parent, run_label(a, xw, s, row, g.nx), run_label(b, xw, s, row2, g.nx), limit, err);
+        }
+      }
+    }
+  }
+}
+
+// outside word: the free bits of runs whose root is the frame.  One warp per row.
+__global__ void k_run_outside(const uint32_t* __restrict__ Vb, BitGrid g, uint32_t* parent,
+                              uint32_t* __restrict__ Ob, int* err) {
+  const int lane = threadIdx.x & 31;
+  const int64_t n_warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const uint32_t limit = (uint32_t)(g.rows() * g.nx + 2);
+  for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < g.rows(); row += n_warps) {
+    int cp = -1;
+    uint32_t cb = 0;
+    for (int base = 0; base < g.mw; base += 32) {
+      const RowChunk c = row_chunk(Vb, g, row, base, lane, cp, cb);
+      const int xw = base + lane;
+      if (xw >= g.mw) continue;
+      uint32_t out = 0;
+      // the run entering from the previous word holds the free bits below the first start
+      if ((c.F & 1u) && !(c.st & 1u)) {
+        const uint32_t below = c.st ? ((1u << (__ffs(c.st) - 1)) - 1u) : 0xFFFFFFFFu;
+        if (uf_find(parent, (uint32_t)(row * g.nx + c.before + 1), limit, err) == 0u) out |= c.F & below;
+      }
+      for (uint32_t m = c.st; m; m &= m - 1) {
+        const int s = __ffs(m) - 1;
+        const uint32_t rest = m & (m - 1);
+        const uint32_t upto = rest ? ((1u << (__ffs(rest) - 1)) - 1u) : 0xFFFFFFFFu;
+        if (uf_find(parent, (uint32_t)(row * g.nx + xw * 32 + s + 1), limit, err) == 0u)
+          out |= c.F & upto & ~((1u << s) - 1u);
+      }
+      Ob[row * g.mw + xw] = out;
+    }
   }
 }
 
@@ -297,9 +512,9 @@ struct Nbr {
 };
 
 __device__ __forceinline__ Nbr neighbours(const uint32_t* __restrict__ B, const BitGrid& g, int64_t w) {
-  const int64_t row = w / g.mw;
-  const int xw = (int)(w - row * g.mw);
-  const int j = (int)(row % g.ny), k = (int)(row / g.ny);
+  const uint32_t row = (uint32_t)w / (uint32_t)g.mw;  // words < 2^31
+  const int xw = (int)((uint32_t)w - row * (uint32_t)g.mw);
+  const int j = (int)(row % (uint32_t)g.ny), k = (int)(row / (uint32_t)g.ny);
   const uint32_t c = B[w];
   const uint32_t prev = xw > 0 ? B[w - 1] : 0u, next = xw + 1 < g.mw ? B[w + 1] : 0u;
   Nbr n;
@@ -321,7 +536,7 @@ __device__ __forceinline__ Nbr neighbours(const uint32_t* __restrict__ B, const 
 __global__ void k_s0(const uint32_t* __restrict__ Vb, BitGrid g, uint32_t* __restrict__ S0) {
   for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < g.words();
        w += (int64_t)gridDim.x * blockDim.x) {
-    const int xw = (int)(w % g.mw);
+    const int xw = (int)((uint32_t)w % (uint32_t)g.mw);
     const uint32_t c = Vb[w];
     const Nbr n = neighbours(Vb, g, w);
     const uint32_t ex_m = xw == 0 ? ~1u : ~0u;
@@ -339,32 +554,64 @@ __global__ void k_dilate(const uint32_t* __restrict__ Din, BitGrid g, uint32_t* 
   for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < g.words();
        w += (int64_t)gridDim.x * blockDim.x) {
     const Nbr n = neighbours(Din, g, w);
-    Dout[w] = (Din[w] | n.xm | n.xp | n.ym | n.yp | n.zm | n.zp) & valid_bits(g, (int)(w % g.mw));
+    Dout[w] = (Din[w] | n.xm | n.xp | n.ym | n.yp | n.zm | n.zp) &
+              valid_bits(g, (int)((uint32_t)w % (uint32_t)g.mw));
   }
 }
 
-// eq. phi per voxel from the sign word and the first shell mask holding it
+// eq. phi from the sign word and the shell masks.  The masks are nested (S_0
+// within D_1 within ...), so p = L + 1 - (masks holding the voxel).  A warp
+// takes 32 consecutive words: lane l loads word l's sign and masks
+// (coalesced, all in flight together) and folds the masks into a bit-sliced
+// count (plane q holds bit q of every voxel's count); then for each of the
+// 32 words the warp broadcasts its planes and writes its 32 voxels' phi in
+// one coalesced store.
+constexpr int kPhiPlanes = 8;  // counts up to L + 1 <= 255
+
 __global__ void k_phi(const uint32_t* __restrict__ Ob, const uint32_t* __restrict__ D, int L, BitGrid g,
                       float h, float r, float* __restrict__ phi, uint8_t* __restrict__ out_outside,
                       uint8_t* __restrict__ out_shell) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= g.nx) return;
-  const int64_t nw = g.words();
-  for (int64_t row = blockIdx.y; row < g.rows(); row += gridDim.y) {
-    const int64_t w = row * g.mw + (x >> 5);
-    const int b = x & 31;
-    int p = 255;
-    for (int m = 0; m <= L; ++m)
-      if ((D[(int64_t)m * nw + w] >> b) & 1u) {
-        p = m;
-        break;
+  const int lane = threadIdx.x & 31;
+  const uint32_t nw = (uint32_t)g.words();  // < 2^31
+  const int planes = 32 - __clz(L + 1);
+  const uint32_t n_warps = gridDim.x * (blockDim.x >> 5);
+  for (uint32_t w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5 << 5; w0 < nw; w0 += n_warps * 32) {
+    const uint32_t w = w0 + lane;
+    uint32_t ob = 0, c[kPhiPlanes];
+#pragma unroll
+    for (int q = 0; q < kPhiPlanes; ++q) c[q] = 0;
+    if (w < nw) {
+      ob = Ob[w];
+      for (int m = 0; m <= L; ++m) {
+        uint32_t carry = D[(size_t)m * nw + w];
+#pragma unroll
+        for (int q = 0; q < kPhiPlanes; ++q) {
+          const uint32_t t = c[q] & carry;
+          c[q] ^= carry;
+          carry = t;
+        }
       }
-    const bool out = (Ob[w] >> b) & 1u;
-    const float delta = p == 255 ? r : fminf(((float)p + 0.5f) * h, r);
-    const int64_t v = row * g.nx + x;
-    phi[v] = out ? delta : -delta;
-    if (out_outside) out_outside[v] = out ? 1 : 0;
-    if (out_shell) out_shell[v] = (uint8_t)p;
+    }
+    const int nwords = (int)min(32u, nw - w0);
+    for (int jw = 0; jw < nwords; ++jw) {
+      const uint32_t ww = w0 + jw;
+      const uint32_t row = ww / (uint32_t)g.mw;
+      const int x = (int)(ww - row * (uint32_t)g.mw) * 32 + lane;
+      int held = 0;
+#pragma unroll
+      for (int q = 0; q < kPhiPlanes; ++q) {
+        if (q >= planes) break;
+        held |= (int)((__shfl_sync(0xFFFFFFFFu, c[q], jw) >> lane) & 1u) << q;
+      }
+      const bool out = (__shfl_sync(0xFFFFFFFFu, ob, jw) >> lane) & 1u;
+      if (x >= g.nx) continue;
+      const int p = held ? L + 1 - held : 255;
+      const float delta = p == 255 ? r : fminf(((float)p + 0.5f) * h, r);
+      const int64_t v = (int64_t)row * g.nx + x;
+      phi[v] = out ? delta : -delta;
+      if (out_outside) out_outside[v] = out ? 1 : 0;
+      if (out_shell) out_shell[v] = (uint8_t)p;
+    }
   }
 }
 
@@ -419,26 +666,70 @@ __device__ __forceinline__ uint32_t tri_count(const uint32_t C[8], uint32_t cube
   return n;
 }
 
-// per word: the seven crossing words and the vertex / triangle counts
+// the cubes of a word that hold triangles (corners not all on one side)
+__device__ __forceinline__ uint32_t active_cubes(const uint32_t C[8], uint32_t cubes) {
+  uint32_t all1 = ~0u, any1 = 0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    all1 &= C[c];
+    any1 |= C[c];
+  }
+  return cubes & any1 & ~all1;
+}
+
+// per word: the seven crossing words, the vertex and triangle counts, and
+// the samples with a vertex (low half) and the cubes with a triangle (high
+// half) of cnt_a
 __global__ void k_mt_count(const uint32_t* __restrict__ I, BitGrid m, uint32_t* __restrict__ X,
-                           unsigned long long* __restrict__ cnt_v, unsigned long long* __restrict__ cnt_t) {
+                           unsigned long long* __restrict__ cnt_v, unsigned long long* __restrict__ cnt_t,
+                           unsigned long long* __restrict__ cnt_a) {
   const int64_t nw = m.words();
   for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nw;
        w += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t row = w / m.mw;
-    const int xw = (int)(w - row * m.mw);
-    const int j = (int)(row % m.ny), k = (int)(row / m.ny);
+    const uint32_t row = (uint32_t)w / (uint32_t)m.mw;  // words < 2^31
+    const int xw = (int)((uint32_t)w - row * (uint32_t)m.mw);
+    const int j = (int)(row % (uint32_t)m.ny), k = (int)(row / (uint32_t)m.ny);
     uint32_t C[8], Xw[7];
     corner_words(I, m, j, k, xw, C);
     crossing_words(C, m, j, k, xw, Xw);
-    uint32_t nv = 0;
+    uint32_t nv = 0, any = 0;
 #pragma unroll
     for (int t = 0; t < 7; ++t) {
       X[t * nw + w] = Xw[t];
       nv += __popc(Xw[t]);
+      any |= Xw[t];
     }
+    const uint32_t cubes = cube_bits(m, j, k, xw);
     cnt_v[w] = nv;
-    cnt_t[w] = tri_count(C, cube_bits(m, j, k, xw));
+    cnt_t[w] = tri_count(C, cubes);
+    cnt_a[w] = (unsigned long long)__popc(any) | ((unsigned long long)__popc(active_cubes(C, cubes)) << 32);
+  }
+}
+
+// the ids (32 w + b) of the samples with a vertex and of the cubes with a
+// triangle, in order
+__global__ void k_mt_list(const uint32_t* __restrict__ I, BitGrid m, const uint32_t* __restrict__ X,
+                          const unsigned long long* __restrict__ base_a, uint32_t* __restrict__ samples,
+                          uint32_t* __restrict__ cubes_out) {
+  const int64_t nw = m.words();
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nw;
+       w += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long b0 = base_a[w], b1 = base_a[w + 1];
+    if (b0 == b1) continue;
+    uint32_t any = 0;
+#pragma unroll
+    for (int t = 0; t < 7; ++t) any |= X[t * nw + w];
+    uint32_t pos = (uint32_t)(b0 & 0xFFFFFFFFull);
+    for (uint32_t M = any; M; M &= M - 1) samples[pos++] = (uint32_t)w * 32u + (uint32_t)(__ffs(M) - 1);
+    if ((b0 >> 32) == (b1 >> 32)) continue;
+    const uint32_t row = (uint32_t)w / (uint32_t)m.mw;
+    const int xw = (int)((uint32_t)w - row * (uint32_t)m.mw);
+    const int j = (int)(row % (uint32_t)m.ny), k = (int)(row / (uint32_t)m.ny);
+    uint32_t C[8];
+    corner_words(I, m, j, k, xw, C);
+    pos = (uint32_t)(b0 >> 32);
+    for (uint32_t M = active_cubes(C, cube_bits(m, j, k, xw)); M; M &= M - 1)
+      cubes_out[pos++] = (uint32_t)w * 32u + (uint32_t)(__ffs(M) - 1);
   }
 }
 
@@ -455,6 +746,7 @@ struct EmitArgs {
   float* verts;
   int32_t* tris;
   float* normals;
+  int64_t n_verts, n_tris;  // totals: every write is checked against them
 };
 
 __device__ __forceinline__ float sample_phi(const EmitArgs& a, int x, int j, int k) {
@@ -477,6 +769,7 @@ __device__ void sample_grad(const EmitArgs& a, int x, int j, int k, float g[3]) 
 }
 
 __device__ void emit_vertex(const EmitArgs& a, int x, int j, int k, int t, int64_t id) {
+  if (id >= a.n_verts) return;
   const int dx = t & 1, dy = (t >> 1) & 1, dz = (t >> 2) & 1;
   const float fa = sample_phi(a, x, j, k), fb = sample_phi(a, x + dx, j + dy, k + dz);
   const float tau = (a.iso - fa) / (fb - fa);
@@ -555,6 +848,7 @@ __device__ __forceinline__ void emit_tri(const EmitArgs& a, const int tet[4], co
   const int3 V = make_int3(mp[2].x - mp[0].x, mp[2].y - mp[0].y, mp[2].z - mp[0].z);
   const int3 N = make_int3(U.y * V.z - U.z * V.y, U.z * V.x - U.x * V.z, U.x * V.y - U.y * V.x);
   const bool flip = N.x * G.x + N.y * G.y + N.z * G.z < 0;
+  if (id >= a.n_tris) return;
   int32_t ids[3];
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
@@ -567,79 +861,85 @@ __device__ __forceinline__ void emit_tri(const EmitArgs& a, const int tet[4], co
   a.tris[id * 3 + 2] = flip ? ids[1] : ids[2];
 }
 
-__global__ void k_mt_emit(EmitArgs a) {
+// word id -> (j, k, xw) of the sample grid
+__device__ __forceinline__ void word_coords(const BitGrid& m, uint32_t w, int* j, int* k, int* xw) {
+  const uint32_t row = w / (uint32_t)m.mw;
+  *xw = (int)(w - row * (uint32_t)m.mw);
+  *j = (int)(row % (uint32_t)m.ny);
+  *k = (int)(row / (uint32_t)m.ny);
+}
+
+// one thread per sample with a vertex: its vertices, by type, from the
+// word's vertex offset and the crossings of the lower samples in the word
+__global__ void k_mt_verts(EmitArgs a, const uint32_t* __restrict__ samples, uint32_t n_samples) {
   const int64_t nw = a.m.words();
-  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nw;
-       w += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t row = w / a.m.mw;
-    const int xw = (int)(w - row * a.m.mw);
-    const int j = (int)(row % a.m.ny), k = (int)(row / a.m.ny);
-    uint32_t Xw[7], any = 0;
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n_samples; q += gridDim.x * blockDim.x) {
+    const uint32_t id = samples[q], w = id >> 5, b = id & 31u;
+    int j, k, xw;
+    word_coords(a.m, w, &j, &k, &xw);
+    uint32_t ty = 0, before = 0;
 #pragma unroll
-    for (int t = 0; t < 7; ++t) {
-      Xw[t] = a.X[t * nw + w];
-      any |= Xw[t];
+    for (int t = 1; t <= 7; ++t) {
+      const uint32_t xt = a.X[(t - 1) * nw + w];
+      ty |= ((xt >> b) & 1u) << t;
+      before += __popc(xt & ((1u << b) - 1u));
     }
-    // vertices, by sample then type
-    int64_t vid = (int64_t)a.base_v[w];
-    for (uint32_t M = any; M; M &= M - 1) {
-      const int b = __ffs(M) - 1;
+    int64_t vid = (int64_t)a.base_v[w] + before;
 #pragma unroll 1
-      for (int t = 1; t <= 7; ++t)
-        if ((Xw[t - 1] >> b) & 1u) emit_vertex(a, xw * 32 + b, j, k, t, vid++);
-    }
-    // triangles, by cube, tetrahedron, then the documented split
-    const uint32_t cubes = cube_bits(a.m, j, k, xw);
-    if (!cubes) continue;
+    for (int t = 1; t <= 7; ++t)
+      if ((ty >> t) & 1u) emit_vertex(a, xw * 32 + (int)b, j, k, t, vid++);
+  }
+}
+
+// one thread per cube with a triangle: its triangles by tetrahedron, from
+// the word's triangle offset plus the bit-sliced count of the lower cubes
+__global__ void k_mt_tris(EmitArgs a, const uint32_t* __restrict__ cubes_in, uint32_t n_cubes) {
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n_cubes; q += gridDim.x * blockDim.x) {
+    const uint32_t id = cubes_in[q], w = id >> 5;
+    const int b = (int)(id & 31u);
+    int j, k, xw;
+    word_coords(a.m, w, &j, &k, &xw);
     uint32_t C[8];
     corner_words(a.I, a.m, j, k, xw, C);
-    uint32_t all1 = ~0u, any1 = 0;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      all1 &= C[c];
-      any1 |= C[c];
-    }
-    int64_t tid = (int64_t)a.base_t[w];
-    for (uint32_t M = cubes & any1 & ~all1; M; M &= M - 1) {
-      const int b = __ffs(M) - 1;
-      const int x = xw * 32 + b;
-      uint32_t first[8], types[8];  // corner 7 owns no edge of its cube
+    const uint32_t below = (1u << b) - 1u;
+    int64_t tid = (int64_t)a.base_t[w] + tri_count(C, cube_bits(a.m, j, k, xw) & below);
+    const int x = xw * 32 + b;
+    uint32_t first[8], types[8];  // corner 7 owns no edge of its cube
 #pragma unroll 1
-      for (int c = 0; c < 7; ++c)
-        owner_info(a, x + (c & 1), j + ((c >> 1) & 1), k + ((c >> 2) & 1), &first[c], &types[c]);
+    for (int c = 0; c < 7; ++c)
+      owner_info(a, x + (c & 1), j + ((c >> 1) & 1), k + ((c >> 2) & 1), &first[c], &types[c]);
 #pragma unroll 1
-      for (int T = 0; T < 6; ++T) {
-        const int tet[4] = {0, kTetMid[T][0], kTetMid[T][1], 7};
-        bool in[4];
-        int nin = 0;
+    for (int T = 0; T < 6; ++T) {
+      const int tet[4] = {0, kTetMid[T][0], kTetMid[T][1], 7};
+      bool in[4];
+      int nin = 0;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          in[q] = (C[tet[q]] >> b) & 1u;
-          nin += in[q];
+      for (int q4 = 0; q4 < 4; ++q4) {
+        in[q4] = (C[tet[q4]] >> b) & 1u;
+        nin += in[q4];
+      }
+      if (nin == 0 || nin == 4) continue;
+      if (nin & 1) {
+        const bool lone_in = nin == 1;
+        int lone = 0, o[3], no = 0;
+#pragma unroll
+        for (int q4 = 0; q4 < 4; ++q4) {
+          if (in[q4] == lone_in) lone = q4;
+          else o[no++] = q4;
         }
-        if (nin == 0 || nin == 4) continue;
-        if (nin & 1) {
-          const bool lone_in = nin == 1;
-          int lone = 0, o[3], no = 0;
+        const int e[3][2] = {{tet[lone], tet[o[0]]}, {tet[lone], tet[o[1]]}, {tet[lone], tet[o[2]]}};
+        emit_tri(a, tet, in, e, first, types, tid++);
+      } else {
+        int ins[2], outs[2], ni = 0, nu = 0;
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            if (in[q] == lone_in) lone = q;
-            else o[no++] = q;
-          }
-          const int e[3][2] = {{tet[lone], tet[o[0]]}, {tet[lone], tet[o[1]]}, {tet[lone], tet[o[2]]}};
-          emit_tri(a, tet, in, e, first, types, tid++);
-        } else {
-          int ins[2], outs[2], ni = 0, nu = 0;
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            if (in[q]) ins[ni++] = tet[q];
-            else outs[nu++] = tet[q];
-          }
-          const int e1[3][2] = {{ins[0], outs[0]}, {ins[0], outs[1]}, {ins[1], outs[1]}};
-          const int e2[3][2] = {{ins[0], outs[0]}, {ins[1], outs[1]}, {ins[1], outs[0]}};
-          emit_tri(a, tet, in, e1, first, types, tid++);
-          emit_tri(a, tet, in, e2, first, types, tid++);
+        for (int q4 = 0; q4 < 4; ++q4) {
+          if (in[q4]) ins[ni++] = tet[q4];
+          else outs[nu++] = tet[q4];
         }
+        const int e1[3][2] = {{ins[0], outs[0]}, {ins[0], outs[1]}, {ins[1], outs[1]}};
+        const int e2[3][2] = {{ins[0], outs[0]}, {ins[1], outs[1]}, {ins[1], outs[0]}};
+        emit_tri(a, tet, in, e1, first, types, tid++);
+        emit_tri(a, tet, in, e2, first, types, tid++);
       }
     }
   }
@@ -654,9 +954,9 @@ struct Buf {
 };
 
 struct Scratch {
-  Buf bits_a, bits_b, shells, parent, x_words, cnt_v, cnt_t, scan_tmp, blur_a, blur_b, sel;
+  Buf bits_a, bits_b, shells, parent, x_words, cnt_v, cnt_t, cnt_a, lists, scan_tmp, blur_a, blur_b, sel;
   int* err = nullptr;        // device: union-find limit reached (bit 0 find, bit 1 unite)
-  unsigned long long* host = nullptr;  // pinned: [0..1] counts read back, [2] the error flag
+  unsigned long long* host = nullptr;  // pinned: [0..1] counts read back, [2] the error flag, [3] active counts
   cudaEvent_t err_ready = nullptr;     // recorded after the flag's copy to host[2]
   int pending_err_check = 0;
   std::mutex mu;
@@ -738,10 +1038,13 @@ fgl_status check_grid(const fgl_grid* g, int64_t* n) {
   return FGL_OK;
 }
 
-// launch shapes: per-voxel kernels take (ceil(nx / 128), min(rows, 65535))
-// blocks of 128; per-word kernels a grid-stride of 256-thread blocks
+// launch shapes: per-voxel kernels take ceil(nx / 128) x R blocks of 128,
+// R rows at a time with R about 4096 / ceil(nx / 128) (a few thousand blocks,
+// each striding over many rows); per-word kernels a grid-stride of 256-thread
+// blocks
 dim3 voxel_grid(int nx, int64_t rows) {
-  return dim3((unsigned)((nx + 127) / 128), (unsigned)std::min<int64_t>(rows, 65535));
+  const int bx = (nx + 127) / 128;
+  return dim3((unsigned)bx, (unsigned)std::max<int64_t>(1, std::min<int64_t>(rows, 4096 / bx)));
 }
 unsigned word_blocks(int64_t items, int per_block) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>((items + per_block - 1) / per_block, 152 * 64));
@@ -796,16 +1099,26 @@ extern "C" fgl_status fgl_denoise(const uint8_t* surf, const fgl_grid* grid, flo
   std::lock_guard<std::mutex> lk(S.mu);
   MCUDA(ensure_small(S));
   const int nx = grid->dims[0], ny = grid->dims[1], nz = grid->dims[2];
-  MCUDA(ensure(S.blur_a, sizeof(float) * n, s));
-  if (!out_blur) MCUDA(ensure(S.blur_b, sizeof(float) * n, s));
-  float* A = (float*)S.blur_a.p;
+  const bool fused = taps.R <= 4;
+  // V' is materialised when the caller wants it or the quantile needs it
+  const bool need_vp = out_blur || mode == 1;
+  if (!out_blur && need_vp) MCUDA(ensure(S.blur_b, sizeof(float) * n, s));
   float* B = out_blur ? out_blur : (float*)S.blur_b.p;
-  const dim3 vg = voxel_grid(nx, (int64_t)ny * nz);
-  // x into B, y into A, z into B (the caller's buffer when given)
-  k_blur<0, uint8_t><<<vg, 128, 0, s>>>(surf, B, nx, ny, nz, taps);
-  k_blur<1, float><<<vg, 128, 0, s>>>(B, A, nx, ny, nz, taps);
-  k_blur<2, float><<<vg, 128, 0, s>>>(A, B, nx, ny, nz, taps);
-  MCUDA(cudaGetLastError());
+  if (fused) {
+    MCUDA(blur_fused(taps.R, surf, nx, ny, nz, taps, value, need_vp ? B : nullptr,
+                     mode == 0 ? out_mask : nullptr, s));
+  } else {
+    MCUDA(ensure(S.blur_a, sizeof(float) * n, s));
+    if (!out_blur) MCUDA(ensure(S.blur_b, sizeof(float) * n, s));
+    B = out_blur ? out_blur : (float*)S.blur_b.p;
+    float* A = (float*)S.blur_a.p;
+    const dim3 vg = voxel_grid(nx, (int64_t)ny * nz);
+    // x into B, y into A, z into B (the caller's buffer when given)
+    k_blur<0, uint8_t><<<vg, 128, 0, s>>>(surf, B, nx, ny, nz, taps);
+    k_blur<1, float><<<vg, 128, 0, s>>>(B, A, nx, ny, nz, taps);
+    k_blur<2, float><<<vg, 128, 0, s>>>(A, B, nx, ny, nz, taps);
+    MCUDA(cudaGetLastError());
+  }
   const uint32_t* thr_dev = nullptr;
   if (mode == 1) {
     MCUDA(ensure(S.sel, sizeof(SelState) + 256 * sizeof(uint32_t), s));
@@ -820,8 +1133,10 @@ extern "C" fgl_status fgl_denoise(const uint8_t* surf, const fgl_grid* grid, flo
     MCUDA(cudaGetLastError());
     thr_dev = &st->prefix;
   }
-  k_threshold<<<word_blocks(n, 1024), 256, 0, s>>>(B, n, value, thr_dev, out_mask);
-  MCUDA(cudaGetLastError());
+  if (!fused || mode == 1) {
+    k_threshold<<<word_blocks(n, 1024), 256, 0, s>>>(B, n, value, thr_dev, out_mask);
+    MCUDA(cudaGetLastError());
+  }
   if (out_threshold) {
     if (thr_dev) {
       uint32_t bits = 0;
@@ -869,15 +1184,16 @@ extern "C" fgl_status fgl_tsdf(const uint8_t* surf, const fgl_grid* grid, float 
   }
   int launches = 0;
   const dim3 vg = voxel_grid(g.nx, g.rows());
-  k_pack_u8<<<word_blocks(nw * 32, 256), 256, 0, s>>>(surf, g, Vb);
-  k_uf_init<<<vg, 128, 0, s>>>(Vb, g, parent);
-  k_uf_merge<<<vg, 128, 0, s>>>(Vb, g, parent, S.err);
-  k_uf_outside<<<word_blocks(nw * 32, 256), 256, 0, s>>>(Vb, g, parent, Ob, S.err);
+  k_pack_u8<<<word_blocks(g.rows() * 32, 256), 256, 0, s>>>(surf, g, Vb);
+  const unsigned rb = word_blocks(g.rows() * 32, 256);
+  k_run_init<<<rb, 256, 0, s>>>(Vb, g, parent);
+  k_run_union<<<rb, 256, 0, s>>>(Vb, g, parent, S.err);
+  k_run_outside<<<rb, 256, 0, s>>>(Vb, g, parent, Ob, S.err);
   k_s0<<<word_blocks(nw, 256), 256, 0, s>>>(Vb, g, D);
   launches += 5;
   for (int m = 1; m <= L; ++m, ++launches)
     k_dilate<<<word_blocks(nw, 256), 256, 0, s>>>(D + (m - 1) * nw, g, D + m * nw);
-  k_phi<<<vg, 128, 0, s>>>(Ob, D, L, g, grid->h, trunc, out_phi, out_outside, out_shell);
+  k_phi<<<word_blocks(nw, 256), 256, 0, s>>>(Ob, D, L, g, grid->h, trunc, out_phi, out_outside, out_shell);
   ++launches;
   MCUDA(cudaGetLastError());
   MCUDA(cudaMemcpyAsync(S.host + 2, S.err, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -916,6 +1232,8 @@ extern "C" fgl_status fgl_marching_tets(const float* phi, const fgl_grid* grid, 
   const int nx = grid->dims[0], ny = grid->dims[1], nz = grid->dims[2];
   const BitGrid m = make_bits((nx - 1) / step + 1, (ny - 1) / step + 1, (nz - 1) / step + 1);
   const int64_t nw = m.words();
+  if (nw * 32 > (int64_t)0xFFFFFFFFu)  // sample and cube ids are 32 w + b in 32 bits
+    return err(FGL_ERR_INVALID, "sample grid has more than 2^32 / 32 words (a very thin grid)");
   cudaStream_t s = (cudaStream_t)stream;
   Scratch& S = *get_scratch(s);
   std::lock_guard<std::mutex> lk(S.mu);
@@ -925,24 +1243,30 @@ extern "C" fgl_status fgl_marching_tets(const float* phi, const fgl_grid* grid, 
   MCUDA(ensure(S.x_words, sizeof(uint32_t) * nw * 7, s));
   MCUDA(ensure(S.cnt_v, sizeof(unsigned long long) * (nw + 1), s));
   MCUDA(ensure(S.cnt_t, sizeof(unsigned long long) * (nw + 1), s));
+  MCUDA(ensure(S.cnt_a, sizeof(unsigned long long) * (nw + 1), s));
   MCUDA(ensure(S.scan_tmp, sizeof(unsigned long long) * tmp_elems, s));
   uint32_t* I = (uint32_t*)S.bits_a.p;
   uint32_t* X = (uint32_t*)S.x_words.p;
   auto* cv = (unsigned long long*)S.cnt_v.p;
   auto* ct = (unsigned long long*)S.cnt_t.p;
+  auto* ca = (unsigned long long*)S.cnt_a.p;
   auto* tmp = (unsigned long long*)S.scan_tmp.p;
   int launches = 0;
-  k_pack_inside<<<word_blocks(nw * 32, 256), 256, 0, s>>>(phi, nx, ny, step, m, iso, I);
-  k_mt_count<<<word_blocks(nw, 256), 256, 0, s>>>(I, m, X, cv, ct);
+  k_pack_inside<<<word_blocks(m.rows() * 32, 256), 256, 0, s>>>(phi, nx, ny, step, m, iso, I);
+  k_mt_count<<<word_blocks(nw, 256), 256, 0, s>>>(I, m, X, cv, ct, ca);
   MCUDA(cudaGetLastError());
   MCUDA(cudaMemsetAsync(cv + nw, 0, sizeof(unsigned long long), s));
   MCUDA(cudaMemsetAsync(ct + nw, 0, sizeof(unsigned long long), s));
+  MCUDA(cudaMemsetAsync(ca + nw, 0, sizeof(unsigned long long), s));
   MCUDA(scan_exclusive_u64(cv, nw + 1, tmp, tmp_elems, s, &launches));
   MCUDA(scan_exclusive_u64(ct, nw + 1, tmp, tmp_elems, s, &launches));
+  MCUDA(scan_exclusive_u64(ca, nw + 1, tmp, tmp_elems, s, &launches));
   MCUDA(cudaMemcpyAsync(S.host, cv + nw, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
   MCUDA(cudaMemcpyAsync(S.host + 1, ct + nw, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  MCUDA(cudaMemcpyAsync(S.host + 3, ca + nw, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
   MCUDA(cudaStreamSynchronize(s));
   const int64_t nv = (int64_t)S.host[0], nt = (int64_t)S.host[1];
+  const uint32_t n_samples = (uint32_t)(S.host[3] & 0xFFFFFFFFull), n_cubes = (uint32_t)(S.host[3] >> 32);
   *n_verts = nv;
   *n_tris = nt;
   if (nv >= ((int64_t)1 << 31) || nt >= ((int64_t)1 << 31))
@@ -969,7 +1293,14 @@ extern "C" fgl_status fgl_marching_tets(const float* phi, const fgl_grid* grid, 
   a.verts = out_verts;
   a.tris = out_tris;
   a.normals = out_normals;
-  k_mt_emit<<<word_blocks(nw, 128), 128, 0, s>>>(a);
+  a.n_verts = nv;
+  a.n_tris = nt;
+  MCUDA(ensure(S.lists, sizeof(uint32_t) * ((size_t)n_samples + n_cubes + 1), s));
+  uint32_t* samples = (uint32_t*)S.lists.p;
+  uint32_t* cubes = samples + n_samples;
+  k_mt_list<<<word_blocks(nw, 256), 256, 0, s>>>(I, m, X, ca, samples, cubes);
+  if (n_samples) k_mt_verts<<<word_blocks(n_samples, 256), 256, 0, s>>>(a, samples, n_samples);
+  if (n_cubes) k_mt_tris<<<word_blocks(n_cubes, 256), 256, 0, s>>>(a, cubes, n_cubes);
   MCUDA(cudaGetLastError());
   return FGL_OK;
 }

@@ -64,10 +64,15 @@ __global__ void k_radix_hist(const uint32_t* __restrict__ keys, int64_t n, int s
   h[threadIdx.x] = 0;
   __syncthreads();
   const int64_t base = (int64_t)blockIdx.x * (kSortThreads * kSortRounds);
+  uint32_t d[kSortRounds];  // every key loaded before the first count: one memory latency
+#pragma unroll
   for (int r = 0; r < kSortRounds; ++r) {
     const int64_t i = base + r * kSortThreads + threadIdx.x;
-    if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+    d[r] = i < n ? (keys[i] >> shift) & 255u : 256u;
   }
+#pragma unroll
+  for (int r = 0; r < kSortRounds; ++r)
+    if (d[r] < 256u) atomicAdd(&h[d[r]], 1u);
   __syncthreads();
   hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
 }
@@ -75,20 +80,29 @@ __global__ void k_radix_hist(const uint32_t* __restrict__ keys, int64_t n, int s
 // Stable scatter.  Each warp owns a contiguous run of kSortRounds * 32 items
 // (warp w of the block: items [w*R*32, (w+1)*R*32) of the block's slice), so
 // index order is (warp, round, lane).  Pass 1 counts each warp's digits with
-// __match_any_sync; one block barrier turns those counts into per-warp bases;
-// pass 2 ranks every item inside its warp (earlier rounds, then lower lanes
-// in the same round) and writes it out.
+// __match_any_sync; a block barrier turns those counts into block-local
+// offsets (digit-major, then warp); pass 2 ranks every item inside its warp
+// (earlier rounds, then lower lanes in the same round) and places it in
+// shared memory, sorted by digit; the write-out then copies the block's
+// digit runs to their global offsets, consecutive threads writing
+// consecutive addresses.
+constexpr int kSortItems = kSortThreads * kSortRounds;
+
 __global__ void k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                                 int64_t n, int shift, const uint32_t* __restrict__ offs,
                                 int nblocks, uint32_t* __restrict__ kout,
                                 uint32_t* __restrict__ vout) {
   constexpr int NW = kSortThreads / 32;
-  __shared__ uint32_t wbase[NW][256];  // digit counts, then per-warp base offsets
+  __shared__ uint32_t wbase[NW][256];  // digit counts, then per-warp local offsets
+  __shared__ uint32_t lbase[256];      // block-local start of each digit's run
+  __shared__ uint32_t gbase[256];      // global start of this block's run of each digit
+  __shared__ uint32_t wsum[NW];
+  __shared__ uint32_t sk[kSortItems], sv[kSortItems];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   for (int k = 0; k < NW; ++k) wbase[k][t] = 0;
   __syncthreads();
-  const int64_t base = (int64_t)blockIdx.x * (kSortThreads * kSortRounds) +
-                       (int64_t)w * (32 * kSortRounds);
+  const int64_t block0 = (int64_t)blockIdx.x * kSortItems;
+  const int64_t base = block0 + (int64_t)w * (32 * kSortRounds);
   const unsigned lt = (1u << lane) - 1u;
   for (int r = 0; r < kSortRounds; ++r) {
     const int64_t i = base + r * 32 + lane;
@@ -99,8 +113,23 @@ __global__ void k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t
   }
   __syncthreads();
   {
-    // thread t = digit t: exclusive prefix over warps, plus the block's global offset
-    uint32_t run = offs[(int64_t)t * nblocks + blockIdx.x];
+    // thread t = digit t: the block's count of t, its exclusive prefix over
+    // digits (warp scan, then the warp totals), and per-warp offsets
+    uint32_t tot = 0;
+    for (int k = 0; k < NW; ++k) tot += wbase[k][t];
+    uint32_t incl = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if (lane >= o) incl += u;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    uint32_t before = 0;
+    for (int k = 0; k < w; ++k) before += wsum[k];
+    uint32_t run = before + incl - tot;
+    lbase[t] = run;
+    gbase[t] = offs[(int64_t)t * nblocks + blockIdx.x];
     for (int k = 0; k < NW; ++k) {
       const uint32_t c = wbase[k][t];
       wbase[k][t] = run;
@@ -115,12 +144,21 @@ __global__ void k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t
     const unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
     if (d < 256u) {
       const uint32_t pos = wbase[w][d] + __popc(peers & lt);
-      kout[pos] = key;
-      vout[pos] = vin[i];
+      sk[pos] = key;
+      sv[pos] = vin[i];
     }
     __syncwarp();
     if (d < 256u && __popc(peers & lt) == 0) wbase[w][d] += __popc(peers);
     __syncwarp();
+  }
+  __syncthreads();
+  const int cnt = n - block0 < (int64_t)kSortItems ? (int)(n - block0) : kSortItems;
+  for (int i = t; i < cnt; i += kSortThreads) {
+    const uint32_t key = sk[i];
+    const uint32_t d = (key >> shift) & 255u;
+    const uint32_t pos = gbase[d] + (uint32_t)i - lbase[d];
+    kout[pos] = key;
+    vout[pos] = sv[i];
   }
 }
 
@@ -171,7 +209,7 @@ cudaError_t scan_exclusive_u64(unsigned long long* x, int64_t n, unsigned long l
 }
 
 size_t radix_sort_tmp_elems(int64_t n) {
-  const int items = kSortThreads * kSortRounds;
+  const int items = kSortItems;
   const int64_t nblocks = (n + items - 1) / items;
   const int64_t nh = 256 * nblocks;
   return (size_t)nh + scan_tmp_elems(nh);
@@ -182,7 +220,7 @@ cudaError_t radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t*
                              bool* in_second) {
   *in_second = false;
   if (n <= 0) return cudaSuccess;
-  const int items = kSortThreads * kSortRounds;
+  const int items = kSortItems;
   const int nblocks = (int)((n + items - 1) / items);
   const int64_t nh = (int64_t)256 * nblocks;
   const size_t tmp_h = scan_tmp_elems(nh);

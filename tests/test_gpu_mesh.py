@@ -45,7 +45,7 @@ def hollow_sphere(n, c, r0, r1):
 
 TSDF_CASES = [((23, 17, 70), 0.2, 0.02, 0.05), ((9, 40, 33), 0.45, 0.03, 0.09),
               ((30, 31, 65), 0.05, 0.015, 0.06), ((1, 1, 1), 0.5, 0.1, 0.1), ((1, 5, 1), 0.5, 0.1, 0.25),
-              ((7, 1, 97), 0.3, 0.01, 0.035)]
+              ((7, 1, 97), 0.3, 0.01, 0.035), ((4, 6, 1100), 0.08, 0.02, 0.05)]
 
 
 @pytest.mark.parametrize("shape,p,h,r", TSDF_CASES)
@@ -76,7 +76,8 @@ def test_tsdf_cavities_and_degenerate_grids():
 
 def test_tsdf_large_grid_vs_oracle():
     """A 160 x 150 x 170 grid (4.1 M voxels, 5 words a row) of thin shells,
-    slabs and noise: bit-exact."""
+    slabs and noise: bit-exact.  (Rows longer than 32 words -- two warp
+    chunks -- are in the (4, 6, 1100) case above.)"""
     rng = np.random.default_rng(77)
     shape = (170, 150, 160)
     V = hollow_sphere(shape, (80.2, 75.5, 85.3), 50.0, 51.5)
