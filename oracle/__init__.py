@@ -390,6 +390,25 @@ def marching_tets(phi, origin, h: float, iso: float = 0.0, step: int = 1, normal
     return verts, tris, nrm
 
 
+def mesh_from_gaussians(mu, scale, quat, alpha, origin, h: float, dims, theta: float = 0.5,
+                        trunc: float = 0.06, sigma="half-voxel", tau: float = 0.5, iso: float = 0.0,
+                        step: int = 1, B: int = 8):
+    """Sec. IV-A then IV-B, the oracle's steps in order: eq. D(v), eqs. V_occ
+    and Surf, eq. V' with eq. rethresh (default sigma = h / 2, tau = 1/2;
+    sigma=None skips them), the TSDF and its iso level set.  Returns (verts,
+    tris)."""
+    D, _ = density(mu, scale, quat, alpha, origin, h, dims, B)
+    _, surf = occupancy(D, theta)
+    if isinstance(sigma, str):
+        sigma = 0.5 * h
+    if sigma:
+        sv = np.float64(np.float32(sigma)) / np.float64(np.float32(h))
+        surf, _ = rethreshold(blur(surf, sv), "fixed", tau)
+    phi, _, _ = tsdf(surf, h, trunc)
+    v, t, _ = marching_tets(phi, origin, h, iso=iso, step=step)
+    return v, t
+
+
 def blur_tolerance(radius: int) -> float:
     """Absolute tolerance of a float32 eq. V' (values in [0, 1]): three passes
     of 2R + 1 float32 products and sums, each within 2^-24 relative, on

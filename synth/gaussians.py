@@ -1,5 +1,6 @@
-"""Seeded 3D Gaussian scenes and their host mesher (TSDF + marching
-tetrahedra), the input generator of the heterogeneous ray-casting workload.
+"""Seeded 3D Gaussian scenes, the input of the Gaussian-to-occupancy and
+mesh-reconstruction steps and (through a mesher passed in by the caller) of
+the heterogeneous ray-casting workload.  No step of the method lives here.
 
 The paper converts pretrained 3DGS assets to meshes (Sec. IV-A/B).  With no
 assets available, Gaussians are drawn on the surfaces of a procedural room:
@@ -12,43 +13,9 @@ opacity uniform in [0.3, 1].
 
 from __future__ import annotations
 
-import ctypes
 import dataclasses
-import os
-import subprocess
-import threading
 
 import numpy as np
-
-_HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "mesher.cpp")
-_LIB = os.path.join(_HERE, "_build", "libmesher.so")
-_lock = threading.Lock()
-_lib = None
-
-
-def build(force: bool = False) -> str:
-    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.run(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-pthread", _SRC, "-o", tmp],
-                       check=True)
-        os.replace(tmp, _LIB)
-    return _LIB
-
-
-def _load():
-    global _lib
-    with _lock:
-        if _lib is None:
-            build()
-            L = ctypes.CDLL(_LIB)
-            P, I64, I32, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
-            L.mesher_run.argtypes = [P, P, P, P, I64, D, D, D, I32, P, P, P, P, P]
-            L.mesher_run.restype = I32
-            L.mesher_free.argtypes = [P]
-            _lib = L
-    return _lib
 
 
 @dataclasses.dataclass
@@ -131,32 +98,13 @@ def gaussian_room(seed: int, room=(6.0, 5.0, 3.0), n_gauss: int = 200_000, n_box
     return gs, obs
 
 
-def mesh_from_gaussians(gs: GaussianSet, voxel: float, theta: float = 0.5, trunc: float = 0.06,
-                        threads: int = 0):
-    """Run the host mesher; returns (verts f32 [nv,3], tris i32 [nt,3], stats)."""
-    L = _load()
-    mu = np.ascontiguousarray(gs.mu, np.float32)
-    sc = np.ascontiguousarray(gs.scale, np.float32)
-    qu = np.ascontiguousarray(gs.quat, np.float32)
-    al = np.ascontiguousarray(gs.alpha, np.float32)
-    pv, pt = ctypes.c_void_p(), ctypes.c_void_p()
-    nv, nt = ctypes.c_int64(), ctypes.c_int64()
-    stats = np.zeros(8, np.float64)
-    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
-    rc = L.mesher_run(p(mu), p(sc), p(qu), p(al), len(al), float(voxel), float(theta), float(trunc),
-                      int(threads), ctypes.byref(pv), ctypes.byref(nv), ctypes.byref(pt),
-                      ctypes.byref(nt), p(stats))
-    if rc != 0:
-        raise RuntimeError(f"mesher failed (code {rc})")
-    try:
-        v = np.ctypeslib.as_array(ctypes.cast(pv, ctypes.POINTER(ctypes.c_float)), (nv.value * 3,)).copy()
-        t = np.ctypeslib.as_array(ctypes.cast(pt, ctypes.POINTER(ctypes.c_int32)), (nt.value * 3,)).copy()
-    finally:
-        L.mesher_free(pv)
-        L.mesher_free(pt)
-    st = {"grid": stats[:3].astype(int).tolist(), "occupied": int(stats[3]), "surface_voxels": int(stats[4]),
-          "outside_voxels": int(stats[5])}
-    return v.reshape(-1, 3), t.reshape(-1, 3), st
+def grid_around(lo, hi, h: float, margin: float):
+    """A voxel grid (origin, dims) of spacing h covering the box [lo, hi]
+    grown by margin on every side."""
+    lo = np.asarray(lo, np.float64) - margin
+    hi = np.asarray(hi, np.float64) + margin
+    dims = tuple(int(np.ceil((hi[a] - lo[a]) / h)) for a in range(3))
+    return tuple(float(x) for x in lo), dims
 
 
 def edge_manifold_report(tris: np.ndarray):

@@ -9,10 +9,12 @@
                   seeded SE(3) random walk (0.1 m / 2 deg per step) over 100
                   steps, 16 x 360 rays per environment (23.6 M rays per step),
                   max range 120 m.
-  hetero_batch  : 8 meshes extracted by the host mesher (TSDF + marching
-                  tetrahedra) from 50k-2M seeded Gaussians on open-topped
-                  rooms of growing size, voxels 5 cm -> 2 cm (about 50k -> 5M
-                  triangles); 256 environments assigned round-robin to the
+  hetero_batch  : 8 meshes extracted (density, TSDF, marching tetrahedra;
+                  the mesher is passed in: the GPU pipeline in the bench, the
+                  oracle's in the tests) from 50k-2M seeded Gaussians on
+                  open-topped rooms of growing size, voxels 5 cm -> 2 cm
+                  (about 90k -> 5M triangles), each on a grid covering its room
+                  plus MESH_MARGIN; 256 environments assigned round-robin to the
                   meshes, each with a sensor drawn from 16/32/64/128 beams x
                   360-2048 azimuths or the 20k-ray rosette.
 """
@@ -96,20 +98,36 @@ class MeshSpec:
     stats: dict
 
 
+# grid margin around each room: 3 sigma of the largest Gaussian (20 cm), the
+# 6 cm TSDF band and a few voxels, so the level set never meets the grid's faces
+MESH_MARGIN = 0.75
+
 _HETERO_CACHE: dict = {}
 
 
-def hetero_meshes(seed: int = 4, ladder=None) -> List[MeshSpec]:
-    """The heterogeneous workload's meshes (cached per process)."""
+def hetero_grid(room, h):
+    """(origin, dims) of a ladder set's grid: the room plus MESH_MARGIN."""
+    from .gaussians import grid_around
+    return grid_around((0.0, 0.0, 0.0), room, h, MESH_MARGIN)
+
+
+def hetero_meshes(mesher, seed: int = 4, ladder=None) -> List[MeshSpec]:
+    """The heterogeneous workload's meshes: each ladder set's Gaussians on its
+    hetero_grid, turned into a mesh by mesher(gs, origin, h, dims) ->
+    (verts f32 [nv, 3], tris i32 [nt, 3]).  Cached per process, mesher and
+    ladder."""
     from . import gaussians
     ladder = HETERO_LADDER if ladder is None else ladder
-    key = (seed, tuple(map(tuple, [(r, b, s, n, h) for r, b, s, n, h in ladder])))
+    key = (getattr(mesher, "__qualname__", repr(mesher)), seed,
+           tuple(map(tuple, [(r, b, s, n, h) for r, b, s, n, h in ladder])))
     if key not in _HETERO_CACHE:
         out = []
         for k, (room, nb, ns, ng, h) in enumerate(ladder):
             gs, obs = gaussians.gaussian_room(seed * 100 + k, room, ng, nb, ns, with_obstacles=True)
-            v, t, st = gaussians.mesh_from_gaussians(gs, h)
-            out.append(MeshSpec(v, t, obs, h, ng, st))
+            origin, dims = hetero_grid(room, h)
+            v, t = mesher(gs, origin, h, dims)
+            out.append(MeshSpec(np.ascontiguousarray(v, np.float32), np.ascontiguousarray(t, np.int32),
+                                obs, h, ng, {"dims": dims}))
         _HETERO_CACHE[key] = out
     return _HETERO_CACHE[key]
 

@@ -318,11 +318,16 @@ def test_batched_walk_full_size_sampled(indoor_oracle):
 
 
 # ---------------------------------------------------------------------------
-# heterogeneous batch: meshes from the host mesher, mixed sensors, one launch
+# heterogeneous batch: meshes from the oracle's 3DGS-to-mesh steps (an oracle
+# input never comes from the CUDA path), mixed sensors, one launch
 # ---------------------------------------------------------------------------
+def oracle_mesher(gs, origin, h, dims):
+    return oracle.mesh_from_gaussians(gs.mu, gs.scale, gs.quat, gs.alpha, origin, h, dims)
+
+
 def test_hetero_batch_vs_oracle():
     ladder = workloads.HETERO_LADDER[:4]
-    meshes = workloads.hetero_meshes(4, ladder)
+    meshes = workloads.hetero_meshes(oracle_mesher, 4, ladder)
     tables = workloads.hetero_sensors(4)
     envs = workloads.hetero_envs(4, meshes, n_env=48)
     scenes = [fgl.Scene(m.verts, m.tris, width=8 if k % 2 == 0 else 4) for k, m in enumerate(meshes)]

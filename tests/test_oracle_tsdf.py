@@ -304,3 +304,43 @@ def test_hollow_shell_pipeline_gives_one_outer_surface():
     # one component (Euler 2, not 4 for two nested spheres), around the shell's
     # outer face at 9 voxels (staircase: within a voxel diagonal)
     assert rad.min() > 7.9 * 0.01 and rad.max() < 10.0 * 0.01
+
+
+# -- the whole oracle pipeline from Gaussians (Sec. IV-A then IV-B) ---------------
+
+def test_pipeline_single_gaussian_gives_its_level_ball():
+    """One isotropic Gaussian (sigma s, alpha 1): D(x) = exp(-|x|^2 / (2 s^2))
+    exceeds theta inside the ball of radius s sqrt(2 ln(1/theta)).  The mesh
+    wraps that ball's one-voxel surface shell: a closed sphere-like surface
+    within a voxel and a half of the radius, with or without the denoising."""
+    from synth.gaussians import grid_around
+    s, theta, h = 0.1, 0.5, 0.01
+    R = s * np.sqrt(2 * np.log(1 / theta))
+    origin, dims = grid_around((0, 0, 0), (0, 0, 0), h, 0.2)
+    one = lambda a: np.asarray(a, np.float32).reshape(1, -1)
+    for sigma in (None, "half-voxel"):
+        v, t = oracle.mesh_from_gaussians(one([0, 0, 0]), one([s, s, s]), one([1, 0, 0, 0]), one([1.0]),
+                                          origin, h, dims, theta=theta, trunc=0.03, sigma=sigma)
+        r = np.linalg.norm(v, axis=1)
+        assert abs(np.median(r) - R) < 1.5 * h and r.max() - r.min() < 3 * h
+        closed, oriented, ne = edge_stats(t)
+        assert closed and oriented and len(v) - ne + len(t) == 2
+
+
+def test_pipeline_closed_shell_of_gaussians_keeps_its_cavity_inside():
+    """Gaussians on a closed sphere of radius 0.5 m: the flood fill never
+    reaches the inside, so the mesh is one outward surface just outside the
+    shell (no inner surface)."""
+    from synth.gaussians import grid_around
+    rng = np.random.default_rng(1)
+    n = 30_000
+    p = rng.standard_normal((n, 3))
+    p = 0.5 * p / np.linalg.norm(p, axis=1, keepdims=True)
+    origin, dims = grid_around((-0.5, -0.5, -0.5), (0.5, 0.5, 0.5), 0.02, 0.25)
+    v, t = oracle.mesh_from_gaussians(p.astype(np.float32), np.full((n, 3), 0.03, np.float32),
+                                      np.tile(np.array([1, 0, 0, 0], np.float32), (n, 1)),
+                                      np.ones(n, np.float32), origin, 0.02, dims, theta=0.5)
+    r = np.linalg.norm(v, axis=1)
+    assert r.min() > 0.5 and r.max() < 0.62
+    closed, oriented, ne = edge_stats(t)
+    assert closed and oriented and len(v) - ne + len(t) == 2 and signed_volume(v, t) > 0
