@@ -245,18 +245,23 @@ __device__ __forceinline__ void child_box(const float4* nbox, const float4* lbox
 }
 
 // Bottom up from every leaf: the second child to reach a node writes both
-// children's boxes into it and its own box, and climbs on.
+// children's boxes into it and its own box, and climbs on.  A child arrives
+// with atomicMax(flags, height << 1 | 1): the first sees 0 and stops, the
+// second reads the other subtree's height, so the root's climb carries the
+// tree's exact height (a leaf counts 1).
 __global__ void k_lbvh_bounds(LbvhNode* nodes, const int32_t* __restrict__ leaf_parent,
                               uint32_t* flags, float4* nbox, const float4* __restrict__ lbox,
                               int64_t n, int32_t* depth) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   int p = leaf_parent[k];
-  int steps = 1;
+  int height = 1;
   while (p >= 0) {
     __threadfence();
-    if (atomicAdd(&flags[p], 1u) == 0u) return;  // the other child is not done yet
+    const uint32_t old = atomicMax(&flags[p], ((uint32_t)height << 1) | 1u);
+    if (old == 0u) return;  // the other child is not done yet
     __threadfence();
+    height = max(height, (int)(old >> 1)) + 1;
     const int l = nodes[p].d.x, r = nodes[p].d.y;
     float4 llo, lhi, rlo, rhi;
     child_box(nbox, lbox, l, llo, lhi);
@@ -266,10 +271,9 @@ __global__ void k_lbvh_bounds(LbvhNode* nodes, const int32_t* __restrict__ leaf_
     nodes[p].c = make_float4(rlo.z, rhi.x, rhi.y, rhi.z);
     nbox[2 * (int64_t)p] = make_float4(fminf(llo.x, rlo.x), fminf(llo.y, rlo.y), fminf(llo.z, rlo.z), 0.f);
     nbox[2 * (int64_t)p + 1] = make_float4(fmaxf(lhi.x, rhi.x), fmaxf(lhi.y, rhi.y), fmaxf(lhi.z, rhi.z), 0.f);
-    ++steps;
     p = p == 0 ? -1 : nodes[p].d.z;
   }
-  atomicMax(depth, steps);
+  atomicMax(depth, height);
 }
 
 // ---------------------------------------------------------------------------

@@ -61,6 +61,16 @@ def check_structure(lb, verts, tris):
         ch = np.maximum(lbox[child, 3:], rbox[child, 3:])
         assert np.all(box[it, :3] <= cl) and np.all(box[it, 3:] >= ch)
     assert st["depth"] >= int(np.ceil(np.log2(nt))) and st["overflow"] == 0
+    # the reported depth is the tree's exact height (a leaf counts 1)
+    order, stack = [], [0]
+    while stack:
+        q = stack.pop()
+        order.append(q)
+        stack.extend(int(c) for c in d[q, :2] if c >= 0)
+    height = np.zeros(len(d), np.int64)
+    for q in reversed(order):
+        height[q] = 1 + max((height[c] if c >= 0 else 1) for c in d[q, :2])
+    assert st["depth"] == height[0]
     return st
 
 
