@@ -180,6 +180,9 @@ struct BatchCtx {
   // end-to-end staging
   void* d_io = nullptr;
   size_t io_cap = 0;
+  cudaStream_t copy_stream = nullptr;  // device-to-host copies of chunked host casts
+  cudaEvent_t chunk_done[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t copies_done = nullptr;
   std::mutex mu;
 };
 std::mutex g_ctx_mu;
@@ -260,8 +263,11 @@ fgl_status grid_for(int W, bool tmin, const Opts& o, int* grid) {
 // caller outside any graph capture.
 fgl_status enqueue_batch(BatchCtx& c, const std::vector<Group>& groups,
                          const std::vector<size_t>& offsets, const Opts& o,
-                         const fgl_cast_item* items, int n, cudaStream_t s) {
+                         const fgl_cast_item* items, int n, cudaStream_t s,
+                         bool staged_event = false) {
   FGL_CUDA(cudaMemcpyAsync(c.d_scratch, c.h_staging, c.table_bytes, cudaMemcpyHostToDevice, s));
+  // outside a capture: the pinned table may be overwritten once this copy ran
+  if (staged_event) FGL_CUDA(cudaEventRecord(c.staged, s));
   for (size_t g = 0; g < groups.size(); ++g) {
     int grid = 0;
     fgl_status st = grid_for(groups[g].W, groups[g].tmin, o, &grid);
@@ -377,10 +383,7 @@ fgl_status run_batched(const fgl_cast_item* items, int n, const Opts& o, cudaStr
     c.table_bytes = table.size();
   }
   if (!o.graph) {
-    fgl_status st = enqueue_batch(c, groups, offsets, o, items, n, s);
-    if (st != FGL_OK) return st;
-    FGL_CUDA(cudaEventRecord(c.staged, s));
-    return FGL_OK;
+    return enqueue_batch(c, groups, offsets, o, items, n, s, /*staged_event=*/true);
   }
 
   // graph key: the table bytes plus the launch configuration
@@ -762,8 +765,10 @@ fgl_status fgl_cast_batched_host(const fgl_cast_item* items, int32_t n_items,
     }
   }
   std::vector<fgl_cast_item> dev(items, items + n_items);
+  size_t total_rays = 0;
   for (int i = 0; i < n_items; ++i) {
     size_t nr = (size_t)items[i].n_env * items[i].sensor->n_rays;
+    total_rays += nr;
     float* dp = (float*)((char*)c.d_io + pose_off[i]);
     float* dr = (float*)((char*)c.d_io + out_off[i]);
     int32_t* dt = (int32_t*)(dr + nr);
@@ -774,14 +779,88 @@ fgl_status fgl_cast_batched_host(const fgl_cast_item* items, int32_t n_items,
     dev[i].out_range = dr;
     dev[i].out_tri = dt;
   }
-  st = run_batched(dev.data(), n_items, o, s);
-  if (st != FGL_OK) return st;
-  for (int i = 0; i < n_items; ++i) {
-    size_t nr = (size_t)items[i].n_env * items[i].sensor->n_rays;
-    if (!nr) continue;
-    FGL_CUDA(cudaMemcpyAsync(items[i].out_range, dev[i].out_range, nr * 4, cudaMemcpyDeviceToHost, s));
-    FGL_CUDA(cudaMemcpyAsync(items[i].out_tri, dev[i].out_tri, nr * 4, cudaMemcpyDeviceToHost, s));
+  // Large batches run in up to kHostChunks chunks of whole environments:
+  // chunk k's results travel to the host on a second stream while chunk k+1
+  // casts, so only the last chunk's copy is exposed; chunk sizes shrink
+  // (C, C-1, ..., 1 parts) to keep that last copy small.  Chunks launch
+  // directly (each has its own work table, so one cached graph would be
+  // re-captured every time).
+  constexpr int kHostChunks = 4;
+  constexpr size_t kChunkMinRays = (size_t)4 << 20;
+  const int chunks = (int)std::max<size_t>(1, std::min<size_t>(kHostChunks, total_rays / kChunkMinRays));
+  if (chunks == 1) {
+    st = run_batched(dev.data(), n_items, o, s);
+    if (st != FGL_OK) return st;
+    for (int i = 0; i < n_items; ++i) {
+      size_t nr = (size_t)items[i].n_env * items[i].sensor->n_rays;
+      if (!nr) continue;
+      FGL_CUDA(cudaMemcpyAsync(items[i].out_range, dev[i].out_range, nr * 4, cudaMemcpyDeviceToHost, s));
+      FGL_CUDA(cudaMemcpyAsync(items[i].out_tri, dev[i].out_tri, nr * 4, cudaMemcpyDeviceToHost, s));
+    }
+    return fgl_sync(stream);
   }
+  {
+    std::lock_guard<std::mutex> lk(c.mu);
+    if (!c.copy_stream) FGL_CUDA(cudaStreamCreateWithFlags(&c.copy_stream, cudaStreamNonBlocking));
+    for (int k = 0; k < kHostChunks; ++k)
+      if (!c.chunk_done[k]) FGL_CUDA(cudaEventCreateWithFlags(&c.chunk_done[k], cudaEventDisableTiming));
+    if (!c.copies_done) FGL_CUDA(cudaEventCreateWithFlags(&c.copies_done, cudaEventDisableTiming));
+  }
+  Opts oc = o;
+  oc.graph = 0;
+  size_t done = 0;  // rays cast so far
+  int i = 0, env = 0;
+  const size_t parts = (size_t)chunks * (chunks + 1) / 2;
+  size_t upto = 0;
+  for (int k = 0; k < chunks; ++k) {
+    upto += (size_t)(chunks - k);
+    const size_t goal = total_rays / parts * upto + total_rays % parts * upto / parts;
+    std::vector<fgl_cast_item> sub;
+    struct Span { int item, e0, e1; };
+    std::vector<Span> spans;
+    while (i < n_items && (done < goal || k == chunks - 1)) {
+      const size_t per_env = (size_t)items[i].sensor->n_rays;
+      const int left = items[i].n_env - env;
+      if (left <= 0 || per_env == 0) {
+        ++i;
+        env = 0;
+        continue;
+      }
+      int take = left;
+      if (k < chunks - 1) {
+        const size_t want = (goal - done + per_env - 1) / per_env;
+        take = (int)std::min<size_t>((size_t)left, std::max<size_t>(1, want));
+      }
+      fgl_cast_item it = dev[i];
+      it.n_env = take;
+      it.poses = dev[i].poses + (size_t)env * 12;
+      it.out_range = dev[i].out_range + (size_t)env * per_env;
+      it.out_tri = dev[i].out_tri + (size_t)env * per_env;
+      sub.push_back(it);
+      spans.push_back({i, env, env + take});
+      done += (size_t)take * per_env;
+      env += take;
+      if (env >= items[i].n_env) {
+        ++i;
+        env = 0;
+      }
+    }
+    if (sub.empty()) continue;
+    st = run_batched(sub.data(), (int)sub.size(), oc, s);
+    if (st != FGL_OK) return st;
+    FGL_CUDA(cudaEventRecord(c.chunk_done[k], s));
+    FGL_CUDA(cudaStreamWaitEvent(c.copy_stream, c.chunk_done[k], 0));
+    for (const Span& sp : spans) {
+      const size_t per_env = (size_t)items[sp.item].sensor->n_rays;
+      const size_t a = (size_t)sp.e0 * per_env, nr = (size_t)(sp.e1 - sp.e0) * per_env;
+      FGL_CUDA(cudaMemcpyAsync(items[sp.item].out_range + a, dev[sp.item].out_range + a, nr * 4,
+                               cudaMemcpyDeviceToHost, c.copy_stream));
+      FGL_CUDA(cudaMemcpyAsync(items[sp.item].out_tri + a, dev[sp.item].out_tri + a, nr * 4,
+                               cudaMemcpyDeviceToHost, c.copy_stream));
+    }
+  }
+  FGL_CUDA(cudaEventRecord(c.copies_done, c.copy_stream));
+  FGL_CUDA(cudaStreamWaitEvent(s, c.copies_done, 0));  // the caller's stream sees the copies
   return fgl_sync(stream);
 }
 

@@ -350,3 +350,34 @@ def test_hetero_batch_vs_oracle():
         rep = parity_report(osc, o[idx], d[idx], 30.0, gr[idx], gi[idx])
         assert_parity(rep)
         assert np.all(gi >= -1)
+
+
+# ---------------------------------------------------------------------------
+# end-to-end host entry (fgl_cast_batched_host): one launch for small batches,
+# chunks whose copies overlap the next chunk's cast for large ones -- both
+# bitwise equal to the device-buffer batched call
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n_big,n_small", [(3, 5), (200, 100)])
+def test_host_entry_equals_device_batched(n_big, n_small):
+    v, t, obs = synth.tiny_room_scene(6)
+    scene = fgl.Scene(v, t)
+    big = fgl.Sensor.from_table(synth.grid_sensor(32, -16.0, 15.0, 1800))
+    small = fgl.Sensor.from_table(synth.grid_sensor(16, -15.0, 15.0, 360))
+    rng = np.random.default_rng(n_big)
+    Pb = synth.sample_free_pose(rng, obs, n_big, upright=False)
+    Ps = synth.sample_free_pose(rng, obs, n_small, upright=False)
+    n_rays = n_big * big.n_rays + n_small * small.n_rays
+    hb_r = torch.empty(n_big * big.n_rays, dtype=torch.float32).pin_memory()
+    hb_i = torch.empty(n_big * big.n_rays, dtype=torch.int32).pin_memory()
+    hs_r = torch.empty(n_small * small.n_rays, dtype=torch.float32).pin_memory()
+    hs_i = torch.empty(n_small * small.n_rays, dtype=torch.int32).pin_memory()
+    hb_r.fill_(-7.0)
+    hs_i.fill_(-7)
+    stream = torch.cuda.Stream()
+    fgl.cast_batched_host([(scene, big, torch.from_numpy(Pb).pin_memory(), 60.0, hb_r, hb_i),
+                           (scene, small, torch.from_numpy(Ps).pin_memory(), 60.0, hs_r, hs_i, 0.4)],
+                          stream=stream)
+    (db_r, db_i), (ds_r, ds_i) = run_batched([(scene, big, Pb, 60.0), (scene, small, Ps, 60.0, 0.4)])
+    assert np.array_equal(hb_r.numpy(), db_r) and np.array_equal(hb_i.numpy(), db_i)
+    assert np.array_equal(hs_r.numpy(), ds_r) and np.array_equal(hs_i.numpy(), ds_i)
+    assert (n_rays >= 8 << 20) == (n_big == 200)            # the large case takes the chunked path
