@@ -62,6 +62,7 @@ def lib():
             L.orc_cast.argtypes = [P, P, P, I64, D, D, I32, P, P, P]
             L.orc_validate.argtypes = [P, P, P, I64, D, D, P, P, I32, P]
             L.orc_tri_test.argtypes = [P, P, P, P, P, P]
+            L.orc_edge_measure.argtypes = [P, P, P, I64, P, D, I32, P]
             L.orc_tri_test.restype = I32
             L.orc_instance_rays.argtypes = [P, P, P, I64, P, P]
             L.orc_gauss_tile_ranges.argtypes = [P, P, P, I64, P, ctypes.c_float, I32, P]
@@ -188,6 +189,17 @@ class Scene:
         lib().orc_cast(self._h, _ptr(o), _ptr(d), n, float(min_range), float(max_range), int(nthreads), _ptr(t),
                        _ptr(ids), _ptr(fl) if flags else None)
         return t, ids, fl
+
+    def edge_measure(self, o, d, t_star, cap: float = 1e-5, nthreads: int = 0) -> np.ndarray:
+        """Per ray: the smallest (ray-line to triangle-edge distance) / L_k over
+        the EDGE flag's window [-1e-4, t* + tol(t*)], capped at `cap`; the EDGE
+        flag is set exactly where this is below 1e-6."""
+        o = np.ascontiguousarray(o, np.float32).reshape(-1, 3)
+        d = np.ascontiguousarray(d, np.float32).reshape(-1, 3)
+        t = np.ascontiguousarray(t_star, np.float64)
+        out = np.empty(len(o), np.float64)
+        lib().orc_edge_measure(self._h, _ptr(o), _ptr(d), len(o), _ptr(t), float(cap), int(nthreads), _ptr(out))
+        return out
 
     def validate(self, o, d, max_range, rng, ids, nthreads: int = 0, min_range: float = 0.0) -> np.ndarray:
         """Per ray: is (range, id) an acceptable FP32 answer?  (bool array)"""

@@ -352,6 +352,32 @@ uint8_t flags_for(const Scene& s, V3 o, V3 d, double Rmin, double R, double t_st
   return fl;
 }
 
+// The continuous form of the EDGE flag: the smallest distance from the ray
+// line to an edge segment of any triangle k, divided by L_k, over ray
+// parameters in the flag's window [-1e-4, t* + tol(t*)]; values of at least
+// `cap` come back as `cap`.  EDGE is set exactly when this is below 1e-6.
+double edge_measure(const Scene& s, V3 o, V3 d, double t_star, double cap) {
+  const double tw0 = -kAbsTol, tw1 = t_star + tol(t_star);
+  double best = cap;
+  auto visit = [&](int64_t k) {
+    V3 p[3] = {s.vert(k, 0), s.vert(k, 1), s.vert(k, 2)};
+    double L = 0.0;
+    for (int i = 0; i < 3; ++i) L = std::max(L, norm(sub(p[i], o)));
+    if (!(L > 0.0)) return;
+    for (int i = 0; i < 3; ++i) {
+      double tlo, thi;
+      const double dist = line_segment_dist(o, d, p[i], p[(i + 1) % 3], &tlo, &thi);
+      if (thi >= tw0 && tlo <= tw1) best = std::min(best, dist / L);
+    }
+  };
+  if (!s.use_bvh) {
+    for (int64_t k = 0; k < s.nt; ++k) visit(k);
+  } else {
+    bvh_visit(s, o, d, tw0, tw1, 1.01 * cap, visit);
+  }
+  return best;
+}
+
 // Is (range, id) an acceptable FP32 answer for this ray?  Accepted when
 //  * id >= 0: triangle id's plane is crossed within tol of `range`, the
 //    crossing lies in [Rmin - tol(Rmin), R + tol(R)] (from -1e-4 when
@@ -535,6 +561,13 @@ void orc_validate(void* h, const float* o, const float* d, int64_t n, double min
     out_ok[i] = validate_one(s, ld3(o, i), ld3(d, i), min_range, max_range, (double)range[i], id[i])
                     ? 1 : 0;
   });
+}
+
+// Per ray, edge_measure (above) for the nearest-hit range t_star[i].
+void orc_edge_measure(void* h, const float* o, const float* d, int64_t n, const double* t_star,
+                      double cap, int nthreads, double* out) {
+  const Scene& s = *static_cast<Scene*>(h);
+  parallel_for(n, nthreads, [&](int64_t i) { out[i] = edge_measure(s, ld3(o, i), ld3(d, i), t_star[i], cap); });
 }
 
 // One FP64 ray/triangle test; returns 1 and the line parameter on a hit.

@@ -381,3 +381,43 @@ def test_host_entry_equals_device_batched(n_big, n_small):
     assert np.array_equal(hb_r.numpy(), db_r) and np.array_equal(hb_i.numpy(), db_i)
     assert np.array_equal(hs_r.numpy(), ds_r) and np.array_equal(hs_i.numpy(), ds_i)
     assert (n_rays >= 8 << 20) == (n_big == 200)            # the large case takes the chunked path
+
+
+# ---------------------------------------------------------------------------
+# evidence for the reading of "within 1e-6 (relative) of a triangle edge":
+# GPU/oracle id mismatches against the oracle's edge measure (distance to the
+# nearest edge over the triangle's distance scale L_k), swept over thresholds
+# ---------------------------------------------------------------------------
+SWEEP = (1e-8, 3e-8, 1e-7, 3e-7, 1e-6, 3e-6, 1e-5)
+
+
+def sweep_counts(osc, o, d, max_range, gr, gi):
+    r_o, i_o, fl = osc.cast(o, d, max_range)
+    m = osc.edge_measure(o, d, r_o, cap=1e-4)
+    bad = (gi != i_o) & ((fl & (oracle.FLAG_TIE | oracle.FLAG_RANGE)) == 0)
+    return [int((bad & (m >= tau)).sum()) for tau in SWEEP], int(bad.sum()), len(o)
+
+
+def test_edge_threshold_sweep():
+    rows = []
+    w = workloads.indoor_scan(2)
+    scene = fgl.Scene(w.verts, w.tris)
+    P = np.concatenate([w.poses, synth.sample_free_pose(np.random.default_rng(21), w.obstacles, 3)])
+    se = fgl.Sensor.from_table(w.sensor)
+    (gr, gi), = run_batched([(scene, se, P, w.max_range)])
+    o, d = oracle.world_rays(oracle.sensor_dirs(w.sensor.elev, w.sensor.azim), P)
+    rows.append(("indoor 1M tris", *sweep_counts(oracle.Scene(w.verts, w.tris), o, d, w.max_range, gr, gi)))
+    meshes = workloads.hetero_meshes(oracle_mesher, 4, workloads.HETERO_LADDER[:4])
+    mh = meshes[3]                                            # 3.5 cm marching-tetrahedra triangles
+    tab = synth.grid_sensor(64, -25.0, 25.0, 2048)
+    Ph = synth.sample_free_pose(np.random.default_rng(22), mh.obstacles, 3, margin=0.25)
+    (gr, gi), = run_batched([(fgl.Scene(mh.verts, mh.tris), fgl.Sensor.from_table(tab), Ph, 30.0)])
+    o, d = oracle.world_rays(oracle.sensor_dirs(tab.elev, tab.azim), Ph)
+    rows.append((f"hetero mesh {len(mh.tris)} tris", *sweep_counts(oracle.Scene(mh.verts, mh.tris), o, d,
+                                                                   30.0, gr, gi)))
+    print("\nid mismatches (TIE/RANGE rays excluded) among rays whose edge measure is >= tau")
+    print("case".ljust(28) + "".join(f"{t:>9.0e}" for t in SWEEP) + "   all  rays")
+    for name, counts, total, n in rows:
+        print(name.ljust(28) + "".join(f"{c:>9d}" for c in counts) + f"{total:>6d}{n:>8d}")
+    for _, counts, _, _ in rows:
+        assert counts[SWEEP.index(1e-6)] == 0

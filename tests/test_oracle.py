@@ -543,3 +543,54 @@ def test_instances_match_the_union_mesh_moved_in_fp64():
         gi = np.where(inst[sl] < 0, ids[sl], np.array(offs)[inst[sl] + 1] + ids[sl])
         gi = np.where(ids[sl] < 0, -1, gi)
         assert np.mean(gi[ok] == iu[ok]) > 0.999
+
+
+@pytest.mark.parametrize("bvh", [False, True])
+def test_edge_measure_is_the_continuous_edge_flag(bvh):
+    """edge_measure (smallest ray-to-edge distance over L_k in the flag's
+    window) is below 1e-6 exactly where the EDGE flag is set; a ray aimed at
+    an edge's midpoint measures ~0, and nudging it sideways by a known angle
+    raises the measure by that angle's chord over L (closed form)."""
+    uv, ut = synth.icosphere_unit(3)
+    v = (uv * 2.0).astype(np.float32)
+    sc = oracle.Scene(v, ut, bvh=bvh)
+    rng = np.random.default_rng(7)
+    # rays from outside at the midpoints of 200 edges facing the origin (on a
+    # convex mesh the first crossing), plus 2000 random rays
+    eye = np.array([0.3, -0.2, 9.0])
+    allmid = 0.5 * (v[ut[:, 0]].astype(np.float64) + v[ut[:, 1]])
+    front = np.nonzero(np.einsum("ij,ij->i", allmid, eye - allmid) > 0.3 * np.linalg.norm(allmid, axis=1)
+                       * np.linalg.norm(eye - allmid, axis=1))[0]
+    k = rng.choice(front, 200, replace=False)
+    mid = allmid[k]
+    o = np.tile(eye[None], (200, 1))
+    d = mid - o
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    o2 = rng.uniform(-6, 6, (2000, 3))
+    d2 = rng.standard_normal((2000, 3))
+    d2 /= np.linalg.norm(d2, axis=1, keepdims=True)
+    O = np.concatenate([o, o2]).astype(np.float32)
+    D = np.concatenate([d, d2]).astype(np.float32)
+    r, ids, fl = sc.cast(O, D, 50.0)
+    m = sc.edge_measure(O, D, r, cap=1e-3)
+    assert np.array_equal((fl & oracle.FLAG_EDGE) != 0, m < 1e-6)
+    aimed = m[:200]
+    assert np.all(aimed < 1e-6)                               # float32 rounding of the aim only
+    # a sideways nudge by angle a (perpendicular to the edge) moves the line
+    # a |p - o| from the edge point p: the measure is a |p - o| / L_k, L_k the
+    # farthest vertex of the nearer triangle -- unless the nudged ray hits
+    # before the edge's closest approach (the edge then lies beyond the hit,
+    # outside the window, and the measure is the cap)
+    a = 2e-4
+    perp = np.cross(d, (v[ut[k, 1]] - v[ut[k, 0]]).astype(np.float64))
+    perp /= np.linalg.norm(perp, axis=1, keepdims=True)
+    dn = d + a * perp
+    dn /= np.linalg.norm(dn, axis=1, keepdims=True)
+    rn, idn, fln = sc.cast(o.astype(np.float32), dn.astype(np.float32), 50.0)
+    mn = sc.edge_measure(o.astype(np.float32), dn.astype(np.float32), rn, cap=1e-3)
+    assert not np.any(fln & oracle.FLAG_EDGE)
+    L = np.linalg.norm(v[ut[idn]].astype(np.float64) - eye, axis=2).max(axis=1)
+    ratio = mn * L / (a * np.linalg.norm(mid - eye, axis=1))
+    near = mn < 1e-3
+    assert near.mean() > 0.3 and np.all(mn[~near] == 1e-3)
+    assert np.all((ratio[near] > 0.95) & (ratio[near] < 1.01))
