@@ -192,10 +192,30 @@ def oracle_sample(w, step_poses, n_env_sample: int, seed: int = 0, osc=None):
     return osc, o, d, envs
 
 
-def time_oracle(osc, o, d, max_range):
+def time_oracle(osc, o, d, max_range, nthreads: int = 0):
     t0 = time.perf_counter()
-    osc.cast(o, d, max_range, flags=False)
+    osc.cast(o, d, max_range, flags=False, nthreads=nthreads)
     return time.perf_counter() - t0
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine)."""
+    import platform
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.machine()
 
 
 # ---------------------------------------------------------------------------
@@ -396,6 +416,15 @@ def main():
                 "peak_source": peak_kind, "bytes_per_ray": round(b_ray, 1),
                 "node_visits_per_ray": round(c_nodes / max(1, c_rays), 2),
                 "tri_tests_per_ray": round(c_tris / max(1, c_rays), 2)}
+    # measured traffic beside the cost model: DRAM bytes of one full launch and
+    # L2 (lts__t_bytes) bytes per ray from the committed ncu captures, as rates
+    tr = roofline["traffic"]
+    lpr = read_profile("k_persistent", "lts_bytes_per_ray")
+    if tr is not None:
+        roofline["dram_gbs_measured"] = round(tr / (kern_ms / 1e3) / 1e9, 1)
+    if lpr is not None:
+        roofline["l2_bytes_per_ray"] = lpr
+        roofline["l2_gbs_measured"] = round(lpr * n_rays / (kern_ms / 1e3) / 1e9, 1)
     # instruction issue, the kernel's actual limiter: warp instructions per ray
     # (ncu, same kernel sources) x rays / kernel time, against 4 warp
     # instructions per SM per cycle at the SM clock sampled during the run
@@ -473,10 +502,14 @@ def main():
     if rank == 0 and ws == 1 and not args.no_cpu:
         osc, o, d, envs = oracle_sample(w, walk[args.warmup % S], 256)
         t = time_oracle(osc, o, d, w.max_range)
+        n1 = len(o) // 16                                   # one core on a sixteenth of the sample
+        t1 = time_oracle(osc, o[:n1], d[:n1], w.max_range, nthreads=1)
         cpu = {"value": round(len(o) / t / 1e9, 6), "unit": UNIT, "cores": os.cpu_count(),
-               "kind": "oracle",
+               "kind": "oracle", "cpu_model": cpu_model(),
+               "single_core_value": round(n1 / t1 / 1e9, 7),
                "sample": f"{len(envs)} of {n_env} envs x {sensor.n_rays} rays (one step), FP64 "
-                         f"median-split BVH, no ambiguity flags, {t:.1f} s"}
+                         f"median-split BVH, no ambiguity flags, {t:.1f} s on all cores; "
+                         f"{n1} rays on one core, {t1:.1f} s"}
 
     if rank == 0:
         line = {
