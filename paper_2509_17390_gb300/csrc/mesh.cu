@@ -249,12 +249,9 @@ template <int R>
 cudaError_t launch_blur_fused(const uint8_t* in, int nx, int ny, int nz, const Taps& taps, float thr,
                               float* out_blur, uint8_t* out_mask, cudaStream_t s) {
   constexpr size_t smem = fused_blur_smem<R>();
-  static bool attr_set = false;  // per template instance; the value never changes
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_blur_fused<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  // set on every call: the attribute belongs to the current device
+  cudaError_t e = cudaFuncSetAttribute(k_blur_fused<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   const dim3 grid((unsigned)((nx + kBTX - 1) / kBTX), (unsigned)((ny + kBTY - 1) / kBTY),
                   (unsigned)((nz + kBTZ - 1) / kBTZ));
   k_blur_fused<R><<<grid, 256, smem, s>>>(in, nx, ny, nz, taps, thr, out_blur, out_mask);
@@ -533,7 +530,8 @@ __device__ __forceinline__ Nbr neighbours(const uint32_t* __restrict__ B, const 
 }
 
 // eq. S_0: a voxel with an in-grid face neighbour of the other value
-__global__ void k_s0(const uint32_t* __restrict__ Vb, BitGrid g, uint32_t* __restrict__ S0) {
+__global__ void k_s0(const uint32_t* __restrict__ Vb, BitGrid g, uint32_t* __restrict__ S0,
+                     uint32_t* __restrict__ planes, int n_planes) {
   for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < g.words();
        w += (int64_t)gridDim.x * blockDim.x) {
     const int xw = (int)((uint32_t)w % (uint32_t)g.mw);
@@ -545,53 +543,58 @@ __global__ void k_s0(const uint32_t* __restrict__ Vb, BitGrid g, uint32_t* __res
     if (n.has_yp) d |= c ^ n.yp;
     if (n.has_zm) d |= c ^ n.zm;
     if (n.has_zp) d |= c ^ n.zp;
-    S0[w] = d & valid_bits(g, xw);
+    d &= valid_bits(g, xw);
+    S0[w] = d;
+    // the shell count of every voxel starts at [voxel in S_0]
+    const int64_t nw = g.words();
+    planes[w] = d;
+    for (int q = 1; q < n_planes; ++q) planes[(int64_t)q * nw + w] = 0u;
   }
 }
 
-// one shell: the mask grown by its face neighbours (padding bits stay zero)
-__global__ void k_dilate(const uint32_t* __restrict__ Din, BitGrid g, uint32_t* __restrict__ Dout) {
-  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < g.words();
+// one shell: the mask grown by its face neighbours (padding bits stay zero),
+// added into the bit-sliced per-voxel count of masks holding the voxel
+// (plane q = bit q of the count)
+__global__ void k_dilate(const uint32_t* __restrict__ Din, BitGrid g, uint32_t* __restrict__ Dout,
+                         uint32_t* __restrict__ planes, int n_planes) {
+  const int64_t nw = g.words();
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nw;
        w += (int64_t)gridDim.x * blockDim.x) {
     const Nbr n = neighbours(Din, g, w);
-    Dout[w] = (Din[w] | n.xm | n.xp | n.ym | n.yp | n.zm | n.zp) &
-              valid_bits(g, (int)((uint32_t)w % (uint32_t)g.mw));
+    const uint32_t d = (Din[w] | n.xm | n.xp | n.ym | n.yp | n.zm | n.zp) &
+                       valid_bits(g, (int)((uint32_t)w % (uint32_t)g.mw));
+    Dout[w] = d;
+    uint32_t carry = d;
+    for (int q = 0; q < n_planes && carry; ++q) {
+      const uint32_t c = planes[(int64_t)q * nw + w];
+      planes[(int64_t)q * nw + w] = c ^ carry;
+      carry &= c;
+    }
   }
 }
 
-// eq. phi from the sign word and the shell masks.  The masks are nested (S_0
-// within D_1 within ...), so p = L + 1 - (masks holding the voxel).  A warp
-// takes 32 consecutive words: lane l loads word l's sign and masks
-// (coalesced, all in flight together) and folds the masks into a bit-sliced
-// count (plane q holds bit q of every voxel's count); then for each of the
-// 32 words the warp broadcasts its planes and writes its 32 voxels' phi in
-// one coalesced store.
+// eq. phi from the sign word and the shell count planes.  The masks are
+// nested (S_0 within D_1 within ...), so p = L + 1 - (masks holding the
+// voxel), the count kept bit-sliced in `planes` (plane q = bit q).  A warp
+// takes 32 consecutive words: lane l loads word l's sign and planes
+// (coalesced, all in flight together); then for each of the 32 words the
+// warp broadcasts its planes and writes its 32 voxels' phi in one coalesced
+// store.
 constexpr int kPhiPlanes = 8;  // counts up to L + 1 <= 255
 
-__global__ void k_phi(const uint32_t* __restrict__ Ob, const uint32_t* __restrict__ D, int L, BitGrid g,
-                      float h, float r, float* __restrict__ phi, uint8_t* __restrict__ out_outside,
+__global__ void k_phi(const uint32_t* __restrict__ Ob, const uint32_t* __restrict__ planes, int L,
+                      BitGrid g, float h, float r, float* __restrict__ phi, uint8_t* __restrict__ out_outside,
                       uint8_t* __restrict__ out_shell) {
   const int lane = threadIdx.x & 31;
   const uint32_t nw = (uint32_t)g.words();  // < 2^31
-  const int planes = 32 - __clz(L + 1);
+  const int n_planes = 32 - __clz(L + 1);
   const uint32_t n_warps = gridDim.x * (blockDim.x >> 5);
   for (uint32_t w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5 << 5; w0 < nw; w0 += n_warps * 32) {
     const uint32_t w = w0 + lane;
     uint32_t ob = 0, c[kPhiPlanes];
 #pragma unroll
-    for (int q = 0; q < kPhiPlanes; ++q) c[q] = 0;
-    if (w < nw) {
-      ob = Ob[w];
-      for (int m = 0; m <= L; ++m) {
-        uint32_t carry = D[(size_t)m * nw + w];
-#pragma unroll
-        for (int q = 0; q < kPhiPlanes; ++q) {
-          const uint32_t t = c[q] & carry;
-          c[q] ^= carry;
-          carry = t;
-        }
-      }
-    }
+    for (int q = 0; q < kPhiPlanes; ++q) c[q] = (w < nw && q < n_planes) ? planes[(size_t)q * nw + w] : 0u;
+    if (w < nw) ob = Ob[w];
     const int nwords = (int)min(32u, nw - w0);
     for (int jw = 0; jw < nwords; ++jw) {
       const uint32_t ww = w0 + jw;
@@ -600,7 +603,7 @@ __global__ void k_phi(const uint32_t* __restrict__ Ob, const uint32_t* __restric
       int held = 0;
 #pragma unroll
       for (int q = 0; q < kPhiPlanes; ++q) {
-        if (q >= planes) break;
+        if (q >= n_planes) break;
         held |= (int)((__shfl_sync(0xFFFFFFFFu, c[q], jw) >> lane) & 1u) << q;
       }
       const bool out = (__shfl_sync(0xFFFFFFFFu, ob, jw) >> lane) & 1u;
@@ -1169,7 +1172,8 @@ extern "C" fgl_status fgl_tsdf(const uint8_t* surf, const fgl_grid* grid, float 
   const int64_t nw = g.words();
   MCUDA(ensure(S.bits_a, sizeof(uint32_t) * nw, s));
   MCUDA(ensure(S.bits_b, sizeof(uint32_t) * nw, s));
-  MCUDA(ensure(S.shells, sizeof(uint32_t) * nw * (L + 1), s));
+  const int n_planes = 32 - __builtin_clz((unsigned)(L + 1));  // bits of the count L + 1
+  MCUDA(ensure(S.shells, sizeof(uint32_t) * nw * (2 + n_planes), s));
   MCUDA(ensure(S.parent, sizeof(uint32_t) * (n + 1), s));
   uint32_t* Vb = (uint32_t*)S.bits_a.p;
   uint32_t* Ob = (uint32_t*)S.bits_b.p;
@@ -1189,11 +1193,14 @@ extern "C" fgl_status fgl_tsdf(const uint8_t* surf, const fgl_grid* grid, float 
   k_run_init<<<rb, 256, 0, s>>>(Vb, g, parent);
   k_run_union<<<rb, 256, 0, s>>>(Vb, g, parent, S.err);
   k_run_outside<<<rb, 256, 0, s>>>(Vb, g, parent, Ob, S.err);
-  k_s0<<<word_blocks(nw, 256), 256, 0, s>>>(Vb, g, D);
+  uint32_t* Dm[2] = {D, D + nw};       // ping-pong shell masks
+  uint32_t* planes = D + 2 * nw;       // bit-sliced counts of the masks holding each voxel
+  k_s0<<<word_blocks(nw, 256), 256, 0, s>>>(Vb, g, Dm[0], planes, n_planes);
   launches += 5;
   for (int m = 1; m <= L; ++m, ++launches)
-    k_dilate<<<word_blocks(nw, 256), 256, 0, s>>>(D + (m - 1) * nw, g, D + m * nw);
-  k_phi<<<word_blocks(nw, 256), 256, 0, s>>>(Ob, D, L, g, grid->h, trunc, out_phi, out_outside, out_shell);
+    k_dilate<<<word_blocks(nw, 256), 256, 0, s>>>(Dm[(m - 1) & 1], g, Dm[m & 1], planes, n_planes);
+  k_phi<<<word_blocks(nw, 256), 256, 0, s>>>(Ob, planes, L, g, grid->h, trunc, out_phi, out_outside,
+                                             out_shell);
   ++launches;
   MCUDA(cudaGetLastError());
   MCUDA(cudaMemcpyAsync(S.host + 2, S.err, sizeof(int), cudaMemcpyDeviceToHost, s));
