@@ -68,6 +68,7 @@ def lib():
             L.orc_gauss_tile_ranges.argtypes = [P, P, P, I64, P, ctypes.c_float, I32, P]
             L.orc_density.argtypes = [P, P, P, P, I64, P, ctypes.c_float, P, I32, I32, P, P]
             L.orc_occupancy.argtypes = [P, P, D, P, P]
+            L.orc_density_tiles.argtypes = [P, P, P, P, I64, P, ctypes.c_float, P, I32, P, I64, I32, P, P]
             F = ctypes.c_float
             L.orc_blur.argtypes = [P, I64, I64, I64, D, I32, P]
             L.orc_outside.argtypes = [P, I64, I64, I64, P]
@@ -269,6 +270,21 @@ def density(mu, scale, quat, alpha, origin, h, dims, B, nthreads: int = 0):
     A = np.empty((nz, ny, nx), np.float64)
     lib().orc_density(_ptr(mu), _ptr(scale), _ptr(quat), _ptr(alpha), len(mu), _ptr(o), float(h),
                       _ptr(dm), int(B), int(nthreads), _ptr(D), _ptr(A))
+    return D, A
+
+
+def density_tiles(mu, scale, quat, alpha, origin, h, dims, B, tiles, nthreads: int = 0):
+    """Eq. D(v) and A(v) on the voxels of the listed tiles only (tile id
+    (c*ty + b)*tx + a): two arrays [n_tiles, B, B, B] indexed [tile, k, j, i]
+    (voxel (aB + i, bB + j, cB + k)), NaN past the grid's faces."""
+    mu, scale, quat, alpha = _f32(mu, 3), _f32(scale, 3), _f32(quat, 4), _f32(alpha, 0)
+    o = np.ascontiguousarray(origin, np.float32)
+    dm = np.ascontiguousarray(dims, np.int32)
+    t = np.ascontiguousarray(tiles, np.int64)
+    D = np.empty((len(t), B, B, B), np.float64)
+    A = np.empty((len(t), B, B, B), np.float64)
+    lib().orc_density_tiles(_ptr(mu), _ptr(scale), _ptr(quat), _ptr(alpha), len(mu), _ptr(o), float(h),
+                            _ptr(dm), int(B), _ptr(t), len(t), int(nthreads), _ptr(D), _ptr(A))
     return D, A
 
 

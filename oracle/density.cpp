@@ -175,6 +175,58 @@ void orc_gauss_tile_ranges(const float* mu, const float* scale, const float* qua
   }
 }
 
+}  // extern "C"
+
+namespace {
+
+// Eq. D(v) and A(v) over the voxels of tile (a, b, c): its candidates are the
+// Gaussians whose tile range holds it; voxel (i, j, k) of the grid goes to
+// put(i, j, k, D, A).
+template <class Put>
+void tile_density(const std::vector<TileRange>& tr, const std::vector<G64>& g, const float o[3], float h,
+                  int64_t nx, int64_t ny, int64_t nz, int64_t B, int64_t a, int64_t b, int64_t c,
+                  Put&& put) {
+  const int64_t n = (int64_t)tr.size();
+  std::vector<int64_t> cand;
+  for (int64_t i = 0; i < n; ++i) {
+    const TileRange& r = tr[i];
+    if (r.lo[0] <= a && a <= r.hi[0] && r.lo[1] <= b && b <= r.hi[1] && r.lo[2] <= c && c <= r.hi[2])
+      cand.push_back(i);
+  }
+  for (int64_t k = c * B; k < std::min(nz, c * B + B); ++k)
+    for (int64_t j = b * B; j < std::min(ny, b * B + B); ++j)
+      for (int64_t ii = a * B; ii < std::min(nx, a * B + B); ++ii) {
+        const double v[3] = {(double)o[0] + ((double)ii + 0.5) * (double)h,
+                             (double)o[1] + ((double)j + 0.5) * (double)h,
+                             (double)o[2] + ((double)k + 0.5) * (double)h};
+        double D = 0.0, A = 0.0;
+        for (int64_t gi : cand) {
+          const G64& G = g[gi];
+          const double d[3] = {v[0] - G.mu[0], v[1] - G.mu[1], v[2] - G.mu[2]};
+          double qf = 0.0;
+          for (int p = 0; p < 3; ++p)
+            for (int r = 0; r < 3; ++r) qf += d[p] * G.P[p][r] * d[r];
+          D += G.a2 * std::exp(-0.5 * qf);
+          A += G.a2;
+        }
+        put(ii, j, k, D, A);
+      }
+}
+
+void prep_all(const float* mu, const float* scale, const float* quat, const float* alpha, int64_t n,
+              const float o[3], float h, int32_t B, std::vector<TileRange>& tr, std::vector<G64>& g) {
+  tr.resize(n);
+  g.resize(n);
+  for (int64_t i = 0; i < n; ++i) {
+    tr[i] = tile_range(mu + 3 * i, scale + 3 * i, quat + 4 * i, o, h, B);
+    g[i] = prep64(mu + 3 * i, scale + 3 * i, quat + 4 * i, alpha[i]);
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
 // Density D(v) and A(v) (see the header) on the nx*ny*nz grid.
 void orc_density(const float* mu, const float* scale, const float* quat, const float* alpha,
                  int64_t n, const float* origin, float h, const int32_t* dims, int32_t B,
@@ -182,40 +234,44 @@ void orc_density(const float* mu, const float* scale, const float* quat, const f
   const float o[3] = {origin[0], origin[1], origin[2]};
   const int64_t nx = dims[0], ny = dims[1], nz = dims[2];
   const int64_t tx = (nx + B - 1) / B, ty = (ny + B - 1) / B, tz = (nz + B - 1) / B;
-  std::vector<TileRange> tr(n);
-  std::vector<G64> g(n);
-  for (int64_t i = 0; i < n; ++i) {
-    tr[i] = tile_range(mu + 3 * i, scale + 3 * i, quat + 4 * i, o, h, B);
-    g[i] = prep64(mu + 3 * i, scale + 3 * i, quat + 4 * i, alpha[i]);
-  }
+  std::vector<TileRange> tr;
+  std::vector<G64> g;
+  prep_all(mu, scale, quat, alpha, n, o, h, B, tr, g);
   parallel_for(tx * ty * tz, nthreads, [&](int64_t t) {
-    const int64_t a = t % tx, b = (t / tx) % ty, c = t / (tx * ty);
-    std::vector<int64_t> cand;
-    for (int64_t i = 0; i < n; ++i) {
-      const TileRange& r = tr[i];
-      if (r.lo[0] <= a && a <= r.hi[0] && r.lo[1] <= b && b <= r.hi[1] && r.lo[2] <= c && c <= r.hi[2])
-        cand.push_back(i);
-    }
-    for (int64_t k = c * B; k < std::min(nz, c * B + B); ++k)
-      for (int64_t j = b * B; j < std::min(ny, b * B + B); ++j)
-        for (int64_t ii = a * B; ii < std::min(nx, a * B + B); ++ii) {
-          const double v[3] = {(double)o[0] + ((double)ii + 0.5) * (double)h,
-                               (double)o[1] + ((double)j + 0.5) * (double)h,
-                               (double)o[2] + ((double)k + 0.5) * (double)h};
-          double D = 0.0, A = 0.0;
-          for (int64_t gi : cand) {
-            const G64& G = g[gi];
-            const double d[3] = {v[0] - G.mu[0], v[1] - G.mu[1], v[2] - G.mu[2]};
-            double qf = 0.0;
-            for (int p = 0; p < 3; ++p)
-              for (int r = 0; r < 3; ++r) qf += d[p] * G.P[p][r] * d[r];
-            D += G.a2 * std::exp(-0.5 * qf);
-            A += G.a2;
-          }
-          const int64_t idx = (k * ny + j) * nx + ii;
-          out_D[idx] = D;
-          if (out_A) out_A[idx] = A;
-        }
+    tile_density(tr, g, o, h, nx, ny, nz, B, t % tx, (t / tx) % ty, t / (tx * ty),
+                 [&](int64_t i, int64_t j, int64_t k, double D, double A) {
+                   const int64_t idx = (k * ny + j) * nx + i;
+                   out_D[idx] = D;
+                   if (out_A) out_A[idx] = A;
+                 });
+  });
+}
+
+// The same for the listed tiles only (tile ids (c ty + b) tx + a): out_D and
+// out_A hold [n_list][B^3] values, voxel (i, j, k) of tile t at
+// ((k - cB) B + (j - bB)) B + (i - aB); slots past the grid's faces are NaN.
+void orc_density_tiles(const float* mu, const float* scale, const float* quat, const float* alpha,
+                       int64_t n, const float* origin, float h, const int32_t* dims, int32_t B,
+                       const int64_t* tiles, int64_t n_list, int nthreads, double* out_D, double* out_A) {
+  const float o[3] = {origin[0], origin[1], origin[2]};
+  const int64_t nx = dims[0], ny = dims[1], nz = dims[2];
+  const int64_t tx = (nx + B - 1) / B, ty = (ny + B - 1) / B;
+  std::vector<TileRange> tr;
+  std::vector<G64> g;
+  prep_all(mu, scale, quat, alpha, n, o, h, B, tr, g);
+  const int64_t B3 = (int64_t)B * B * B;
+  for (int64_t q = 0; q < n_list * B3; ++q) {
+    out_D[q] = std::nan("");
+    out_A[q] = std::nan("");
+  }
+  parallel_for(n_list, nthreads, [&](int64_t q) {
+    const int64_t t = tiles[q], a = t % tx, b = (t / tx) % ty, c = t / (tx * ty);
+    tile_density(tr, g, o, h, nx, ny, nz, B, a, b, c,
+                 [&](int64_t i, int64_t j, int64_t k, double D, double A) {
+                   const int64_t slot = q * B3 + ((k - c * B) * B + (j - b * B)) * B + (i - a * B);
+                   out_D[slot] = D;
+                   out_A[slot] = A;
+                 });
   });
 }
 

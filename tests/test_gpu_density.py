@@ -126,3 +126,30 @@ def test_argument_errors():
         with pytest.raises(fgl.FglError):
             fgl.gaussian_density(t, t, q, a, args["origin"], args["h"], args["dims"],
                                  tile=kw.get("tile", 0))
+
+
+def test_largest_ladder_set_sampled_tiles_vs_oracle():
+    """The occupancy bench's largest set (2 M Gaussians, 330 x 280 x 180
+    voxels of 2 cm, 8^3 tiles) in the bench's launch configuration: the pair
+    count exact, and 64 tiles (32 at random, 32 holding occupied voxels)
+    voxel by voxel against the oracle's density on those tiles."""
+    from synth import gaussians, workloads
+    room, nb, ns, ng, h = workloads.HETERO_LADDER[7]
+    gs = gaussians.gaussian_room(4 * 100 + 7, room, ng, nb, ns)
+    origin = (-0.3, -0.3, -0.3)
+    dims = tuple(int(np.ceil((room[a] + 0.6) / h)) for a in range(3))
+    D, occ, surf, st = run_gpu(gs.mu, gs.scale, gs.quat, gs.alpha, origin, h, dims, 0.5, 8)
+    assert st["n_pairs"] == expected_pairs(gs.mu, gs.scale, gs.quat, origin, h, dims, 8)
+    nt = [(d + 7) // 8 for d in dims]
+    rng = np.random.default_rng(77)
+    occ_tiles = np.unique(((np.nonzero(occ)[0] // 8) * nt[1] + np.nonzero(occ)[1] // 8) * nt[0]
+                          + np.nonzero(occ)[2] // 8)
+    tiles = np.concatenate([rng.choice(nt[0] * nt[1] * nt[2], 32, replace=False),
+                            rng.choice(occ_tiles, 32, replace=False)])
+    Do, Ao = oracle.density_tiles(gs.mu, gs.scale, gs.quat, gs.alpha, origin, h, dims, 8, tiles)
+    for q, t in enumerate(tiles):
+        a, b, c = t % nt[0], (t // nt[0]) % nt[1], t // (nt[0] * nt[1])
+        g = D[c * 8:c * 8 + 8, b * 8:b * 8 + 8, a * 8:a * 8 + 8].astype(np.float64)
+        o = Do[q][:g.shape[0], :g.shape[1], :g.shape[2]]
+        tol = oracle.density_tolerance(o, Ao[q][:g.shape[0], :g.shape[1], :g.shape[2]])
+        assert np.all(np.abs(g - o) <= tol), (int(t), float(np.max(np.abs(g - o) / tol)))

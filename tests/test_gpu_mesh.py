@@ -196,9 +196,13 @@ def test_marching_tets_edge_cases_and_capacity():
 # -- the GPU pipeline: Gaussians -> mesh -------------------------------------------
 
 def edge_stats(tris):
-    e = np.concatenate([tris[:, [0, 1]], tris[:, [1, 2]], tris[:, [2, 0]]])
-    _, cu_ = np.unique(np.sort(e, axis=1), axis=0, return_counts=True)
-    _, cd = np.unique(e, axis=0, return_counts=True)
+    """(every undirected edge in exactly two triangles, every directed edge in one)."""
+    t = np.asarray(tris, np.int64)
+    a = np.concatenate([t[:, 0], t[:, 1], t[:, 2]])
+    b = np.concatenate([t[:, 1], t[:, 2], t[:, 0]])
+    n = int(t.max()) + 1 if len(t) else 1
+    _, cu_ = np.unique(np.minimum(a, b) * n + np.maximum(a, b), return_counts=True)
+    _, cd = np.unique(a * n + b, return_counts=True)
     return bool(np.all(cu_ == 2)), bool(np.all(cd == 1))
 
 
@@ -234,3 +238,38 @@ def test_pipeline_from_gaussians_matches_oracle_steps():
     assert np.max(np.abs(v.cpu().numpy() - vo)) <= oracle.vertex_tolerance(vo, h)
     closed, oriented = edge_stats(tr)
     assert closed and oriented and len(tr) > 10_000
+
+
+def test_fullsize_mesh_steps_vs_oracle():
+    """The mesh bench's largest set (2 M Gaussians, 375 x 325 x 225 voxels of
+    2 cm = 27.4 M voxels) in the bench's configuration, from the GPU's own
+    surface grid: V' within the blur bound and the mask exact away from the
+    threshold; the TSDF of the GPU's mask bit-exact; its marching-tetrahedra
+    mesh (5 M triangles) triangle for triangle, vertices within tolerance,
+    closed and consistently oriented."""
+    from synth import gaussians, workloads
+    room, nb, ns, ng, h = workloads.HETERO_LADDER[7]
+    gs = gaussians.gaussian_room(4 * 100 + 7, room, ng, nb, ns)
+    origin, dims = workloads.hetero_grid(room, h)
+    t = lambda a: cu(a)
+    _, _, surf, _ = fgl.gaussian_density(t(gs.mu), t(gs.scale), t(gs.quat), t(gs.alpha), origin, h, dims)
+    mask, vp, _ = fgl.denoise(surf, h, 0.5 * h, tau=0.5, blur=True)
+    S = surf.cpu().numpy()
+    sv = np.float64(np.float32(0.5 * h)) / np.float64(np.float32(h))
+    vp_o = oracle.blur(S, sv)
+    tol = oracle.blur_tolerance(oracle.blur_radius(sv))
+    assert np.abs(vp.cpu().numpy() - vp_o).max() <= tol
+    M = mask.cpu().numpy()
+    clear = np.abs(vp_o - 0.5) > tol
+    assert np.array_equal(M[clear], (vp_o[clear] >= 0.5).astype(np.uint8))
+    del vp, vp_o, clear
+    phi, _, _, _ = fgl.tsdf(mask, h, 0.06)
+    phi_o, _, _ = oracle.tsdf(M, h, 0.06)
+    assert np.array_equal(phi.cpu().numpy(), phi_o)
+    v, tr, _ = fgl.marching_tets(phi, origin, h)
+    vo, to, _ = oracle.marching_tets(phi_o, origin, h)
+    tr = tr.cpu().numpy()
+    assert len(to) > 4_000_000 and np.array_equal(tr, to)
+    assert np.max(np.abs(v.cpu().numpy() - vo)) <= oracle.vertex_tolerance(vo, h)
+    closed, oriented = edge_stats(tr)
+    assert closed and oriented

@@ -148,3 +148,27 @@ def test_threshold_is_strict():
     D[1, 1, 1] = np.nextafter(0.5, 1)
     occ, surf = oracle.occupancy(D, 0.5)
     assert occ.sum() == 1 and surf.sum() == 1
+
+
+def test_density_on_listed_tiles_equals_the_full_grid():
+    """orc_density_tiles (the full-size GPU tests' sampled oracle) returns the
+    full-grid density's values, bit for bit, on the listed tiles (ragged
+    tiles past the faces marked NaN)."""
+    rng = np.random.default_rng(1)
+    n = 300
+    mu = rng.uniform(0.1, 0.9, (n, 3)).astype(np.float32)
+    sc = np.exp(rng.uniform(np.log(0.02), np.log(0.15), (n, 3))).astype(np.float32)
+    q = rng.standard_normal((n, 4)).astype(np.float32)
+    al = rng.uniform(0.3, 1, n).astype(np.float32)
+    dims, h, o = (21, 19, 17), 0.05, (0.0, 0.0, 0.0)
+    D, A = oracle.density(mu, sc, q, al, o, h, dims, 8)
+    tiles = np.array([0, 5, 13, 26])
+    Dt, At = oracle.density_tiles(mu, sc, q, al, o, h, dims, 8, tiles)
+    for k, t in enumerate(tiles):
+        a, b, c = t % 3, (t // 3) % 3, t // 9
+        sub = D[c * 8:c * 8 + 8, b * 8:b * 8 + 8, a * 8:a * 8 + 8]
+        subA = A[c * 8:c * 8 + 8, b * 8:b * 8 + 8, a * 8:a * 8 + 8]
+        blk = Dt[k][:sub.shape[0], :sub.shape[1], :sub.shape[2]]
+        blkA = At[k][:sub.shape[0], :sub.shape[1], :sub.shape[2]]
+        assert np.array_equal(sub, blk) and np.array_equal(subA, blkA)
+        assert np.isnan(Dt[k]).sum() == 512 - sub.size
