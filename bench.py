@@ -627,32 +627,12 @@ def run_walk_instances(args):
     import torch
     import paper_2509_17390_gb300 as fgl
     from synth import workloads
-    import synth
     ws, rank, local = dist_setup(args.gpus)
     n_steps = args.warmup + args.steps
-    w = workloads.batched_walk(2, n_env=args.n_env, n_steps=min(n_steps, 100))
+    wi = workloads.walk_instances(2, args.n_env, min(n_steps, 100))
+    w, meshes, IP = wi.walk, wi.meshes, wi.poses
     n_env, S = args.n_env, w.poses.shape[0]
-    uv, ut = synth.icosphere_unit(3)
-    meshes = [((0.3 * uv).astype(np.float32), ut),
-              synth.aabb_box((-0.4, -0.3, -0.3), (0.4, 0.3, 0.3), 4),
-              synth.aabb_box((-0.25, -0.25, -0.25), (0.25, 0.25, 0.25), 4),
-              synth.aabb_box((-0.1, -0.1, -0.9), (0.1, 0.1, 0.9), 3)]
     K = len(meshes)
-    # instance k of environment e rides near that environment's sensor (0.6-1.2 m
-    # away horizontally: the walk's scene is cluttered, half of its returns lie
-    # within 0.5 m), turning and drifting from step to step
-    rng = np.random.default_rng(77)
-    ang = rng.uniform(0, 2 * np.pi, (n_env, K))
-    rad = rng.uniform(0.6, 1.2, (n_env, K))
-    base = np.stack([rad * np.cos(ang), rad * np.sin(ang), rng.uniform(-0.2, 0.2, (n_env, K))], -1)
-    yaw0 = rng.uniform(0, 2 * np.pi, (n_env, K))
-    IP = np.zeros((S, n_env, K, 3, 4), np.float32)
-    for st in range(S):
-        a = yaw0 + 0.05 * st
-        c, sn = np.cos(a), np.sin(a)
-        IP[st, :, :, 0, 0], IP[st, :, :, 0, 1], IP[st, :, :, 1, 0], IP[st, :, :, 1, 1] = c, -sn, sn, c
-        IP[st, :, :, 2, 2] = 1
-        IP[st, :, :, :, 3] = w.poses[st][:, None, :, 3] + base + 0.005 * st
     dev = torch.device("cuda", torch.cuda.current_device())
     scene = fgl.Scene(w.verts, w.tris, width=args.width)
     inst = [fgl.Scene(v, t, width=args.width) for v, t in meshes]

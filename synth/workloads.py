@@ -149,3 +149,41 @@ def hetero_envs(seed: int, meshes: List[MeshSpec], n_env: int = 256):
         P = _poses.sample_free_pose(rng, meshes[m].obstacles, 1, margin=0.25)
         envs.append((m, s, P[0]))
     return envs
+
+
+@dataclasses.dataclass
+class WalkInstances:
+    meshes: list          # [(verts f32 [nv, 3], tris i32 [nt, 3])] in instance frames
+    poses: np.ndarray     # [S, n_env, K, 3, 4] instance-to-world per step
+    walk: object          # the batched_walk these ride on
+
+
+def walk_instances(seed: int, n_env: int, n_steps: int, walk=None) -> WalkInstances:
+    """Four rigid instances per environment of the batched walk (an
+    icosphere of radius 0.3 m, two subdivided boxes and a 1.8 m pillar), each
+    0.6-1.2 m from its environment's sensor horizontally (the walk's scene is
+    cluttered: half of its returns lie within 0.5 m), turning 0.05 rad and
+    drifting 5 mm a step."""
+    from .scenes import aabb_box, icosphere_unit
+    w = batched_walk(seed, n_env=n_env, n_steps=n_steps) if walk is None else walk
+    S = w.poses.shape[0]
+    uv, ut = icosphere_unit(3)
+    meshes = [((0.3 * uv).astype(np.float32), ut),
+              aabb_box((-0.4, -0.3, -0.3), (0.4, 0.3, 0.3), 4),
+              aabb_box((-0.25, -0.25, -0.25), (0.25, 0.25, 0.25), 4),
+              aabb_box((-0.1, -0.1, -0.9), (0.1, 0.1, 0.9), 3)]
+    K = len(meshes)
+    rng = np.random.default_rng(77)
+    ang = rng.uniform(0, 2 * np.pi, (n_env, K))
+    rad = rng.uniform(0.6, 1.2, (n_env, K))
+    base = np.stack([rad * np.cos(ang), rad * np.sin(ang), rng.uniform(-0.2, 0.2, (n_env, K))], -1)
+    yaw0 = rng.uniform(0, 2 * np.pi, (n_env, K))
+    IP = np.zeros((S, n_env, K, 3, 4), np.float32)
+    for st in range(S):
+        a = yaw0 + 0.05 * st
+        c, sn = np.cos(a), np.sin(a)
+        IP[st, :, :, 0, 0], IP[st, :, :, 0, 1], IP[st, :, :, 1, 0], IP[st, :, :, 1, 1] = c, -sn, sn, c
+        IP[st, :, :, 2, 2] = 1
+        IP[st, :, :, :, 3] = w.poses[st][:, None, :, 3] + base + 0.005 * st
+    return WalkInstances(meshes, IP, w)
+

@@ -129,3 +129,31 @@ def test_no_instances_points_and_out_instance():
     fgl.sync()
     assert np.array_equal(gr, plain[0].cpu().numpy()) and np.array_equal(gi, plain[1].cpu().numpy())
     assert np.all(np.isfinite(pts[gi >= 0])) and np.all(np.isnan(pts[gi < 0]))
+
+
+def test_walk_instances_fullsize_sampled_vs_oracle():
+    """The walk_instances bench configuration (4096 environments x 5,760
+    rays on the 1,000,300-triangle scene, four moving rigid instances each,
+    the return points) cast in one batched launch: 48 sampled environments,
+    all their rays, against the oracle's scene-plus-instances cast."""
+    from synth import workloads
+    wi = workloads.walk_instances(2, 4096, 3)
+    w, IP = wi.walk, wi.poses[2]
+    scene = fgl.Scene(w.verts, w.tris)
+    inst = [fgl.Scene(v, t) for v, t in wi.meshes]
+    se = fgl.Sensor.from_table(w.sensor)
+    P = w.poses[2]
+    gr, gi, ginst, pts = gpu_cast(scene, se, P, w.max_range, inst, IP, graph=True, stream=torch.cuda.Stream())
+    envs = np.sort(np.random.default_rng(5).choice(4096, 48, replace=False))
+    n = se.n_rays
+    o, d = oracle.world_rays(oracle.sensor_dirs(w.sensor.elev, w.sensor.azim), P[envs])
+    r_o, i_o, inst_o, fl = oracle.cast_with_instances(oracle.Scene(w.verts, w.tris),
+                                                      [oracle.Scene(v, t) for v, t in wi.meshes],
+                                                      o, d, IP[envs], n, w.max_range)
+    sel = (envs[:, None] * n + np.arange(n)[None, :]).ravel()
+    check(gr[sel], gi[sel], ginst[sel], r_o, i_o, inst_o, fl, w.max_range)
+    assert (ginst[sel] >= 0).mean() > 0.05                    # the instances are in view
+    hit = gi[sel] >= 0
+    ref = o.astype(np.float64) + gr[sel].astype(np.float64)[:, None] * d.astype(np.float64)
+    err = np.abs(pts[sel][hit] - ref[hit]).max(axis=1)
+    assert np.all(err <= 4e-7 * (np.abs(ref[hit]).max(axis=1) + 1))
