@@ -1005,11 +1005,14 @@ def run_mesh(args):
     launches = 0
     voxels = 0
     evals, dens_ms = 0, 0.0
+    per_set_ms = []
     for S, c in zip(sets, caps):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
         _, _, dst, tst = one(S, c, ev)
         torch.cuda.synchronize()
-        stage += [ev[i].elapsed_time(ev[i + 1]) for i in range(4)]
+        st4 = [ev[i].elapsed_time(ev[i + 1]) for i in range(4)]
+        stage += st4
+        per_set_ms.append(round(sum(st4), 3))
         evals += dst["n_pairs"] * 512
         dens_ms += dst["ms_density"]
         nx, ny, nz = S["dims"]
@@ -1102,7 +1105,8 @@ def run_mesh(args):
                            "voxels_per_step": voxels, "meshes_per_step": len(sets),
                            "l2": "flushed between timed steps (256 MiB write)",
                            "sets": [{"gaussians": S["n"], "voxel_m": S["h"], "dims": S["dims"],
-                                     "verts": c[0], "tris": c[1]} for S, c in zip(sets, caps)],
+                                     "verts": c[0], "tris": c[1], "ms_3dgs_to_mesh": m}
+                                    for S, c, m in zip(sets, caps, per_set_ms)],
                            "stage_ms": {"density": round(stage[0], 3), "denoise": round(stage[1], 3),
                                         "tsdf": round(stage[2], 3), "marching_tets": round(stage[3], 3)}},
                 "gpu_launches": args.steps * launches,
