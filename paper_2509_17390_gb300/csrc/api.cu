@@ -13,6 +13,7 @@
 
 #include "fgl.h"
 #include "fgl_internal.h"
+#include "nvtx_range.h"
 #include "kernels.h"
 
 using namespace fgl;
@@ -706,6 +707,7 @@ fgl_status fgl_cast_lbvh(fgl_lbvh lbvh, fgl_sensor sensor, const float* poses, i
 
 fgl_status fgl_cast_batched(const fgl_cast_item* items, int32_t n_items, const fgl_batch_opts* opts,
                             fgl_stream stream) {
+  fgl::NvtxRange range("fgl_cast_batched");
   if (n_items < 0) return fail(FGL_ERR_INVALID, "n_items < 0");
   if (n_items > 0 && !items) return fail(FGL_ERR_INVALID, "items is null");
   for (int i = 0; i < n_items; ++i) {
@@ -721,6 +723,7 @@ fgl_status fgl_cast_batched(const fgl_cast_item* items, int32_t n_items, const f
 
 fgl_status fgl_cast_batched_host(const fgl_cast_item* items, int32_t n_items,
                                  const fgl_batch_opts* opts, fgl_stream stream) {
+  fgl::NvtxRange range("fgl_cast_batched_host");
   if (n_items < 0) return fail(FGL_ERR_INVALID, "n_items < 0");
   if (n_items > 0 && !items) return fail(FGL_ERR_INVALID, "items is null");
   for (int i = 0; i < n_items; ++i) {

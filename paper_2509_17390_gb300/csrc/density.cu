@@ -34,6 +34,7 @@
 
 #include "fgl.h"
 #include "fgl_internal.h"
+#include "nvtx_range.h"
 #include "ptx_ops.cuh"
 #include "sort.h"
 
@@ -405,6 +406,7 @@ extern "C" fgl_status fgl_gaussian_density(const fgl_gaussians* gs, const fgl_gr
                                            float theta, float* out_density, uint8_t* out_occ,
                                            uint8_t* out_surf, fgl_density_stats* stats,
                                            fgl_stream stream) {
+  fgl::NvtxRange range("fgl_gaussian_density");
   if (!gs || !grid) return err(FGL_ERR_INVALID, "null gaussians or grid");
   if (gs->n < 0) return err(FGL_ERR_INVALID, "n < 0");
   if (gs->n > 0 && (!gs->mu || !gs->scale || !gs->quat || !gs->opacity))

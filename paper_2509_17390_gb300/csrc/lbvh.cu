@@ -28,6 +28,7 @@
 
 #include "fgl.h"
 #include "fgl_internal.h"
+#include "nvtx_range.h"
 #include "sort.h"
 #include "trace.cuh"
 
@@ -434,6 +435,7 @@ cudaError_t launch_lbvh_cast(const fgl_lbvh_s* L, const void* dirs, const float*
 
 extern "C" fgl_status fgl_lbvh_build(const float* d_verts, int64_t nv, const int32_t* d_tris,
                                      int64_t nt, fgl_stream stream, fgl_lbvh* out) {
+  fgl::NvtxRange range("fgl_lbvh_build");
   if (!out) return err(FGL_ERR_INVALID, "out is null");
   if (!d_verts || !d_tris) return err(FGL_ERR_INVALID, "null vertex or triangle pointer");
   if (nv < 1 || nt < 1) return err(FGL_ERR_INVALID, "mesh needs at least one vertex and triangle");

@@ -42,6 +42,7 @@
 
 #include "fgl.h"
 #include "fgl_internal.h"
+#include "nvtx_range.h"
 #include "sort.h"
 
 namespace fgl {
@@ -1081,6 +1082,7 @@ using namespace fgl;
 extern "C" fgl_status fgl_denoise(const uint8_t* surf, const fgl_grid* grid, float sigma, int32_t mode,
                                   float value, float* out_blur, uint8_t* out_mask, float* out_threshold,
                                   fgl_stream stream) {
+  fgl::NvtxRange range("fgl_denoise");
   int64_t n = 0;
   if (fgl_status st = check_grid(grid, &n)) return st;
   if (!surf || !out_mask) return err(FGL_ERR_INVALID, "null surf or out_mask");
@@ -1156,6 +1158,7 @@ extern "C" fgl_status fgl_denoise(const uint8_t* surf, const fgl_grid* grid, flo
 extern "C" fgl_status fgl_tsdf(const uint8_t* surf, const fgl_grid* grid, float trunc, float* out_phi,
                                uint8_t* out_outside, uint8_t* out_shell, fgl_tsdf_stats* stats,
                                fgl_stream stream) {
+  fgl::NvtxRange range("fgl_tsdf");
   int64_t n = 0;
   if (fgl_status st = check_grid(grid, &n)) return st;
   if (!surf || !out_phi) return err(FGL_ERR_INVALID, "null surf or out_phi");
@@ -1228,6 +1231,7 @@ extern "C" fgl_status fgl_marching_tets(const float* phi, const fgl_grid* grid, 
                                         float* out_verts, int64_t vert_capacity, int32_t* out_tris,
                                         int64_t tri_capacity, float* out_normals, int64_t* n_verts,
                                         int64_t* n_tris, fgl_stream stream) {
+  fgl::NvtxRange range("fgl_marching_tets");
   int64_t n = 0;
   if (fgl_status st = check_grid(grid, &n)) return st;
   if (!phi || !n_verts || !n_tris) return err(FGL_ERR_INVALID, "null phi or count pointer");

@@ -35,6 +35,7 @@
 #include <vector>
 
 #include "fgl.h"
+#include "nvtx_range.h"
 
 namespace fgl {
 void record_error(int status, const char* msg);  // api.cu
@@ -279,6 +280,7 @@ void worker_main(fgl_server_s* Sp) {
     // while the other runs
     S.cv_tick.wait(lk, [&] { return S.stop || S.ticks.size() < 2; });
     if (S.stop) break;
+    fgl::NvtxRange range("fgl_server tick");
     admit(S);
     // pack the tick
     items.clear();
