@@ -273,3 +273,60 @@ def test_fullsize_mesh_steps_vs_oracle():
     assert np.max(np.abs(v.cpu().numpy() - vo)) <= oracle.vertex_tolerance(vo, h)
     closed, oriented = edge_stats(tr)
     assert closed and oriented
+
+
+@pytest.mark.parametrize("h,r", [(0.01, 0.5), (0.01, 2.535)])
+def test_tsdf_wide_bands(h, r):
+    """Bands of L = 51 and the maximum 254 shells (6 and 8 count planes)."""
+    V = hollow_sphere((60, 70, 90), (40.3, 33.1, 28.7), 15.0, 16.0)
+    V[:, 5, :] = 1
+    phi, out, sh, st = fgl.tsdf(cu(V), h, r, outside=True, shell=True)
+    phi_o, out_o, p_o = oracle.tsdf(V, h, r)
+    assert st["n_layers"] == oracle.band_layers(h, r)
+    assert np.array_equal(out.cpu().numpy(), out_o)
+    assert np.array_equal(sh.cpu().numpy(), p_o)
+    assert np.array_equal(phi.cpu().numpy(), phi_o)
+
+
+@pytest.mark.parametrize("quantile", [None, 0.8])
+def test_denoise_three_pass_path(quantile):
+    """sigma of 1.7 voxels (6 taps a side): the three-pass blur, at a grid of
+    several hundred thousand voxels, with a fixed and a quantile threshold."""
+    rng = np.random.default_rng(8)
+    V = random_binary(rng, (40, 60, 150), 0.1)
+    h, sigma = 0.02, np.float32(1.7 * 0.02)
+    mask, vp, thr = fgl.denoise(cu(V), h, float(sigma), tau=0.2, quantile=quantile, blur=True)
+    sv = np.float64(sigma) / np.float64(np.float32(h))
+    R = oracle.blur_radius(sv)
+    assert R == 6
+    vp_o = oracle.blur(V, sv, R)
+    tol = oracle.blur_tolerance(R)
+    g = vp.cpu().numpy()
+    assert np.abs(g.astype(np.float64) - vp_o).max() <= tol
+    if quantile is None:
+        clear = np.abs(vp_o - np.float32(0.2)) > tol
+        assert np.array_equal(mask.cpu().numpy()[clear], (vp_o[clear] >= np.float32(0.2)).astype(np.uint8))
+    else:
+        m_own, thr_own = oracle.rethreshold(g, "quantile", quantile)
+        assert np.float32(thr) == np.float32(thr_own) and np.array_equal(mask.cpu().numpy(), m_own)
+
+
+def test_pipeline_mc_step_two():
+    """mesh_from_gaussians with mc_step 2 equals the oracle's marching
+    tetrahedra at step 2 on the GPU's TSDF, and stays closed."""
+    from synth import gaussians
+    gs = gaussians.gaussian_room(12, (2.0, 1.5, 1.0), 30_000, 1, 1)
+    h = 0.03
+    origin, dims = gaussians.grid_around((0, 0, 0), (2.0, 1.5, 1.0), h, 0.6)
+    t = lambda a: cu(a)
+    _, _, surf, _ = fgl.gaussian_density(t(gs.mu), t(gs.scale), t(gs.quat), t(gs.alpha), origin, h, dims)
+    mask, _, _ = fgl.denoise(surf, h, 0.5 * h)
+    phi, _, _, _ = fgl.tsdf(mask, h, 0.06)
+    v2, t2, _ = fgl.mesh_from_gaussians(t(gs.mu), t(gs.scale), t(gs.quat), t(gs.alpha), origin, h, dims,
+                                        step=2)
+    vo, to, _ = oracle.marching_tets(phi.cpu().numpy(), origin, h, step=2)
+    t2 = t2.cpu().numpy()
+    assert np.array_equal(t2, to) and len(to) > 5000
+    assert np.max(np.abs(v2.cpu().numpy() - vo)) <= oracle.vertex_tolerance(vo, 2 * h)
+    closed, oriented = edge_stats(t2)
+    assert closed and oriented
