@@ -79,6 +79,7 @@ def gaussian_room(seed: int, room=(6.0, 5.0, 3.0), n_gauss: int = 200_000, n_box
     spheres = []
     for _ in range(n_spheres):
         r = rng.uniform(0.2, 0.6)
+        r = min(r, 0.5 * L[2] - 1e-3)             # a sphere fits under the room's height
         c = np.r_[r + 0.3 + rng.uniform(0, 1, 2) * (L[:2] - 2 * r - 0.6), rng.uniform(r, L[2] - r)]
         spheres.append((c, r))
     mu = _sample_surfaces(rng, rects, spheres, n_gauss)
