@@ -48,12 +48,17 @@ UNIT = "Grays/s"
 WORKLOAD = ("batched_walk: 4096 envs x (16 beams -15..+15 deg x 360 az) = 23,592,960 rays/step "
             "on the 1,000,300-tri seeded indoor mesh (20x15x4 m room, 2000 icospheres, 834 "
             "boxes), per-env seeded SE(3) random walk 0.1 m / 2 deg per step, max range 120 m")
-KERNEL_SOURCES = ["paper_2509_17390_gb300/csrc/trace.cuh", "paper_2509_17390_gb300/csrc/kernels.cu"]
+# the sources each profiled kernel is built from: a committed ncu figure is
+# used only while its kernel's sources are unchanged
+KERNEL_SOURCES = {
+    "k_persistent": ["paper_2509_17390_gb300/csrc/trace.cuh", "paper_2509_17390_gb300/csrc/kernels.cu"],
+    "k_lbvh_cast": ["paper_2509_17390_gb300/csrc/trace.cuh", "paper_2509_17390_gb300/csrc/lbvh.cu"],
+}
 
 
-def kernel_hash() -> str:
+def kernel_hash(name: str = "k_persistent") -> str:
     h = hashlib.sha256()
-    for p in KERNEL_SOURCES:
+    for p in KERNEL_SOURCES[name]:
         h.update(open(os.path.join(ROOT, p), "rb").read())
     return h.hexdigest()[:16]
 
@@ -72,7 +77,7 @@ def read_profile(name: str, field: str):
     try:
         d = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
         e = d.get(name)
-        if e and e.get("kernel_hash") == kernel_hash() and e.get(field) is not None:
+        if e and e.get("kernel_hash") == kernel_hash(name) and e.get(field) is not None:
             return float(e[field])
     except Exception:
         pass
@@ -190,6 +195,36 @@ def oracle_sample(w, step_poses, n_env_sample: int, seed: int = 0, osc=None):
     dirs = oracle.sensor_dirs(w.sensor.elev, w.sensor.azim)
     o, d = oracle.world_rays(dirs, step_poses[envs])
     return osc, o, d, envs
+
+
+def counted_bytes(fgl, items, stream, opts=None):
+    """Algorithmic bytes of casting `items` once (eq. cost(r_j) as bytes): a
+    counting pass per item (node visits x its scene's node size + triangle
+    tests x 48 B + 24 B of direction and result per ray).  Returns (bytes,
+    rays, node visits, triangle tests)."""
+    tot_b = tot_r = tot_n = tot_t = 0
+    for it in items:
+        sc, se = it[0], it[1]
+        copts = fgl.BatchOpts(count_work=1, packet_rays=opts.packet_rays if opts else 0,
+                              block_threads=opts.block_threads if opts else 0)
+        fgl.work_counters()
+        fgl.cast_batched([it], copts, stream=stream)
+        fgl.sync(stream)
+        r, n, t = fgl.work_counters()
+        tot_b += n * sc.stats()["node_stride"] + t * 48 + r * 24
+        tot_r, tot_n, tot_t = tot_r + r, tot_n + n, tot_t + t
+    return tot_b, tot_r, tot_n, tot_t
+
+
+def hbm_roofline(bytes_, seconds, rays, nodes, tris, kernel="k_persistent"):
+    peak, kind = read_peaks()
+    achieved = bytes_ / seconds / 1e9
+    return {"bound": "hbm", "kernel": kernel, "achieved": round(achieved, 1), "peak": peak,
+            "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None, "peak_source": kind,
+            "bytes_per_ray": round(bytes_ / max(1, rays), 1),
+            "node_visits_per_ray": round(nodes / max(1, rays), 2),
+            "tri_tests_per_ray": round(tris / max(1, rays), 2),
+            "basis": "algorithmic bytes of eq. cost(r_j) from a counting pass"}
 
 
 def time_oracle(osc, o, d, max_range, nthreads: int = 0):
@@ -688,6 +723,12 @@ def run_walk_instances(args):
     clocks = clk.summary()
     tot0 = timed(False)
     seen = float((out_k >= 0).float().mean().item())
+    # the dominant kernel is the scene cast (k_persistent): its cost-model
+    # bytes from a counting pass, over its own time (the step without instances)
+    with torch.cuda.stream(stream):
+        pose_state.copy_(walk_d[args.warmup % S])
+    cb, cr, cn, ct = counted_bytes(fgl, items0, stream, opts)
+    roofline = hbm_roofline(cb, tot0 / args.steps, cr, cn, ct, kernel="k_persistent (the scene cast)")
     if rank == 0:
         line = {"metric": "Grays/s @4096 envs x 1M tris + 4 moving instances per env (with return points)",
                 "value": round(ws * n_rays * args.steps / tot / 1e9, 4), "unit": UNIT, "n_gpus": ws,
@@ -701,7 +742,7 @@ def run_walk_instances(args):
                            "returns_on_instances": round(seen, 4),
                            "l2": "flushed between timed steps (256 MiB write)"},
                 "without_instances_ms_per_step": round(tot0 * 1e3 / args.steps, 3),
-                "gpu_launches": args.steps * (1 + K + 1), "clocks": clocks}
+                "gpu_launches": args.steps * (1 + K + 1), "roofline": roofline, "clocks": clocks}
         print(json.dumps(line), flush=True)
 
 
@@ -779,6 +820,20 @@ def run_lbvh(args):
     clocks = clk.summary()
     t_wide = timed(cast_wide)
     t_dyn = timed(dynamic)
+    # the LBVH cast is bound by instruction issue like the wide kernel: warp
+    # instructions per ray (ncu, committed with its sources' hash) x rays/s
+    # against 4 warp instructions per SM per cycle at the sampled clock
+    roofline = None
+    ipr = read_profile("k_lbvh_cast", "warp_inst_per_ray")
+    if ipr is not None:
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = (clocks or {}).get("sm_mhz") or 2070.0
+        ach = ipr * n_rays * args.steps / t_lbvh / 1e9
+        pk = 4.0 * sms * mhz * 1e6 / 1e9
+        roofline = {"bound": "issue", "kernel": "k_lbvh_cast", "achieved": round(ach, 1), "peak": round(pk, 1),
+                    "unit": "G warp-inst/s", "frac": round(ach / pk, 4), "warp_inst_per_ray": ipr,
+                    "traffic": read_profile("k_lbvh_cast", "dram_bytes_per_launch"),
+                    "peak_basis": f"4 x {sms} SMs x {mhz:.0f} MHz"}
     if rank == 0:
         line = {"metric": "Grays/s @4096 envs x 1M tris, GPU-built triangle LBVH cast one thread per beam",
                 "value": round(ws * n_rays * args.steps / t_lbvh / 1e9, 4), "unit": UNIT, "n_gpus": ws,
@@ -795,7 +850,7 @@ def run_lbvh(args):
                 "dynamic_rebuild_and_cast": {"ms_per_step": round(t_dyn * 1e3 / args.steps, 3),
                                              "value": round(ws * n_rays * args.steps / t_dyn / 1e9, 4),
                                              "unit": UNIT},
-                "gpu_launches": args.steps, "clocks": clocks}
+                "gpu_launches": args.steps, "roofline": roofline, "clocks": clocks}
         print(json.dumps(line), flush=True)
 
 
@@ -1149,6 +1204,8 @@ def run_hetero(args):
     fgl.sync(stream)
     tot = barrier_max(sum(a.elapsed_time(b) for a, b in ev) / 1e3, ws)
     value = ws * n_rays * args.steps / tot / 1e9
+    cb, cr, cn, ct = counted_bytes(fgl, items, stream, opts)
+    roofline = hbm_roofline(cb, tot / args.steps, cr, cn, ct)
     # the plain form: one fgl_cast launch per environment
     L = fgl.lib()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -1192,7 +1249,7 @@ def run_hetero(args):
                                        "rosette, max range 30 m", "rays_per_step": n_rays,
                            "l2": "flushed between timed steps (256 MiB write)", **info},
                 "gpu_launches": args.steps * len(set(widths.values())), "per_env_launch": per_env,
-                "cpu_baseline": cpu, "clocks": clk.summary()}
+                "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
 
 
