@@ -988,6 +988,9 @@ def run_occupancy(args):
         print(json.dumps(line), flush=True)
 
 
+MESH_STREAMS = 4  # streams (and host threads) the mesh workload's 8 sets share
+
+
 def gpu_mesher(gs, origin, h, dims):
     """The library's 3DGS-to-mesh pipeline (Sec. IV-A, IV-B) on one Gaussian
     set: the heterogeneous workload's meshes."""
@@ -1019,7 +1022,11 @@ def _scan_launches(n):
 def run_mesh(args):
     """3DGS to mesh on the GPU (Sec. IV-A then IV-B) over the 8 ladder sets:
     density and surface shell, denoising (sigma = h / 2, tau = 1/2), the
-    narrow-band TSDF (r = 0.06 m) and marching tetrahedra."""
+    narrow-band TSDF (r = 0.06 m) and marching tetrahedra.  The sets run on
+    MESH_STREAMS streams from as many host threads (largest set first, each to
+    the least-loaded stream), so one mesh's host synchronisations (sizing the
+    pair buffers, reading the mesh counts) overlap other meshes' kernels."""
+    import concurrent.futures
     import torch
     import paper_2509_17390_gb300 as fgl
     ws, rank, local = dist_setup(args.gpus)
@@ -1027,35 +1034,62 @@ def run_mesh(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.Stream(device=dev)
     theta, trunc = 0.5, 0.06
+    streams = [torch.cuda.Stream(device=dev) for _ in range(MESH_STREAMS)]
+    assign = [[] for _ in streams]
+    load = [0] * len(streams)
+    for i in sorted(range(len(sets)), key=lambda i: -int(np.prod(sets[i]["dims"]))):
+        k = int(np.argmin(load))
+        assign[k].append(i)
+        load[k] += int(np.prod(sets[i]["dims"]))
+    pool = concurrent.futures.ThreadPoolExecutor(len(streams))
 
-    def one(S, cap, ev=None):
+    def one(S, cap, st=None, ev=None):
+        st = stream if st is None else st
         h = S["h"]
         if ev:
-            ev[0].record(stream)
+            ev[0].record(st)
         _, _, surf, dst = fgl.gaussian_density(*S["dev"], S["origin"], h, S["dims"], theta=theta,
-                                               stream=stream, timing=bool(ev))
+                                               stream=st, timing=bool(ev))
         if ev:
-            ev[1].record(stream)
-        mask, _, _ = fgl.denoise(surf, h, 0.5 * h, tau=0.5, stream=stream)
+            ev[1].record(st)
+        mask, _, _ = fgl.denoise(surf, h, 0.5 * h, tau=0.5, stream=st)
         if ev:
-            ev[2].record(stream)
-        phi, _, _, tst = fgl.tsdf(mask, h, trunc, stream=stream)
+            ev[2].record(st)
+        phi, _, _, tst = fgl.tsdf(mask, h, trunc, stream=st)
         if ev:
-            ev[3].record(stream)
-        v, t, _ = fgl.marching_tets(phi, S["origin"], h, capacity=cap, stream=stream)
+            ev[3].record(st)
+        v, t, _ = fgl.marching_tets(phi, S["origin"], h, capacity=cap, stream=st)
         if ev:
-            ev[4].record(stream)
+            ev[4].record(st)
         return v, t, dst, tst
+
+    def all_sets(per_set):
+        """per_set(i, stream) for every set, the streams' threads in parallel,
+        bracketed on `stream` (returns after enqueueing; the caller times)."""
+        start = torch.cuda.Event()
+        start.record(stream)
+
+        def work(k):
+            st = streams[k]
+            st.wait_event(start)
+            with torch.cuda.stream(st):                # allocations follow the stream
+                for i in assign[k]:
+                    per_set(i, st)
+            done = torch.cuda.Event()
+            done.record(st)
+            return done
+
+        for done in pool.map(work, range(len(streams))):
+            stream.wait_event(done)
 
     caps = [None] * len(sets)
     for i, S in enumerate(sets):                          # counts, to size the outputs once
         v, t, _, _ = one(S, None)
         caps[i] = (len(v), len(t))
     for _ in range(args.warmup):
-        for S, c in zip(sets, caps):
-            one(S, c)
+        all_sets(lambda i, st: one(sets[i], caps[i], st))
     torch.cuda.synchronize()
-    # per-stage event times (an untimed pass)
+    # per-stage event times (an untimed pass, one set at a time on one stream)
     stage = np.zeros(4)
     launches = 0
     voxels = 0
@@ -1063,7 +1097,7 @@ def run_mesh(args):
     per_set_ms = []
     for S, c in zip(sets, caps):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
-        _, _, dst, tst = one(S, c, ev)
+        _, _, dst, tst = one(S, c, ev=ev)
         torch.cuda.synchronize()
         st4 = [ev[i].elapsed_time(ev[i + 1]) for i in range(4)]
         stage += st4
@@ -1087,8 +1121,7 @@ def run_mesh(args):
             with torch.cuda.stream(stream):
                 flush.fill_(k & 0xFF)
                 evs[k][0].record(stream)
-            for S, c in zip(sets, caps):
-                one(S, c)
+            all_sets(lambda i, st: one(sets[i], caps[i], st))
             with torch.cuda.stream(stream):
                 evs[k][1].record(stream)
         torch.cuda.synchronize()
@@ -1119,14 +1152,15 @@ def run_mesh(args):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(stream)
-        for S, h, c, a, b in zip(sets, host, caps, hv, ht):
-            with torch.cuda.stream(stream):
-                for d_, h_ in zip(S["dev"], h):
-                    d_.copy_(h_, non_blocking=True)
-            v, t, _, _ = one(S, c)
-            with torch.cuda.stream(stream):
-                a.copy_(v, non_blocking=True)
-                b.copy_(t, non_blocking=True)
+
+        def e2e_set(i, st):                            # on stream st (the current stream)
+            for d_, h_ in zip(sets[i]["dev"], host[i]):
+                d_.copy_(h_, non_blocking=True)
+            v, t, _, _ = one(sets[i], caps[i], st)
+            hv[i].copy_(v, non_blocking=True)
+            ht[i].copy_(t, non_blocking=True)
+
+        all_sets(e2e_set)
         e1.record(stream)
         e1.synchronize()
         e_s = e0.elapsed_time(e1) / 1e3
@@ -1157,6 +1191,7 @@ def run_mesh(args):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
                 "config": {"workload": "mesh: the hetero ladder's Gaussian sets (50k-2M Gaussians on procedural open-topped rooms), grids = room + 0.75 m at 5-2 cm voxels, theta 0.5, blur sigma h/2 with tau 1/2, TSDF r = 0.06 m, iso 0, mc_step 1",
+                           "streams": len(streams),
                            "voxels_per_step": voxels, "meshes_per_step": len(sets),
                            "l2": "flushed between timed steps (256 MiB write)",
                            "sets": [{"gaussians": S["n"], "voxel_m": S["h"], "dims": S["dims"],
