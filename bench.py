@@ -878,7 +878,6 @@ def run_occupancy(args):
     ws, rank, local = dist_setup(args.gpus)
     sets = occupancy_setup(torch)
     dev = torch.device("cuda", torch.cuda.current_device())
-    stream = torch.cuda.Stream(device=dev)
     outs = []
     for S in sets:
         nx, ny, nz = S["dims"]
@@ -886,25 +885,27 @@ def run_occupancy(args):
                      torch.empty((nz, ny, nx), dtype=torch.uint8, device=dev),
                      torch.empty((nz, ny, nx), dtype=torch.uint8, device=dev)))
     theta = 0.5
+    ss = SetStreams(torch, dev, [int(np.prod(S["dims"])) for S in sets], MESH_STREAMS)
+    stream = ss.main
 
-    def step(timing=False):
-        st_all = []
-        for S, (D, O, U) in zip(sets, outs):
-            _, _, _, st = fgl.gaussian_density(*S["dev"], S["origin"], S["h"], S["dims"], theta=theta,
-                                               out_density=D, out_occ=O, out_surf=U, stream=stream,
-                                               timing=timing)
-            st_all.append(st)
-        return st_all
+    def one(i, st, timing=False):
+        S = sets[i]
+        D, O, U = outs[i]
+        return fgl.gaussian_density(*S["dev"], S["origin"], S["h"], S["dims"], theta=theta, out_density=D,
+                                    out_occ=O, out_surf=U, stream=st, timing=timing)[3]
 
     for _ in range(args.warmup):
-        step()
-    stats = step(timing=True)                       # per-kernel event times (untimed pass)
+        ss.run(one)
+    torch.cuda.synchronize()
+    # per-kernel event times: untimed passes, one set at a time on one stream
+    passes = [[one(i, stream, timing=True) for i in range(len(sets))] for _ in range(3)]
+    stats = passes[0]
     evals = sum(st["n_pairs"] * 512 for st in stats)   # 8^3 voxel evaluations per candidate pair
     voxels = sum(st["n_voxels"] for st in stats)
+    dens_ms = [sum(st["ms_density"] for st in p_) for p_ in passes]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    dens_ms = []
     barrier(ws)
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
@@ -912,10 +913,9 @@ def run_occupancy(args):
             with torch.cuda.stream(stream):
                 flush.fill_(k & 0xFF)
                 ev[k][0].record(stream)
-            st_k = step(timing=True)
+            ss.run(one)
             with torch.cuda.stream(stream):
                 ev[k][1].record(stream)
-            dens_ms.append(sum(st["ms_density"] for st in st_k))
         torch.cuda.synchronize()
     tot = barrier_max(sum(a.elapsed_time(b) for a, b in ev) / 1e3, ws)
     value = ws * evals * args.steps / tot / 1e9
@@ -924,7 +924,7 @@ def run_occupancy(args):
     # at 16 per SM per cycle: at 4.9e12 ex2/s (2.07 GHz, 152 SMs) ncu shows the
     # XU pipe at 50% of its instruction peak with math-pipe throttle as the top
     # stall, i.e. ex2 takes two of the pipe's issue slots
-    kern_s = float(np.mean(dens_ms)) / 1e3
+    kern_s = float(np.median(dens_ms)) / 1e3
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     mhz = (clocks or {}).get("sm_mhz") or 2070.0
     peak = 16.0 * sms * mhz * 1e6 / 1e9
@@ -947,14 +947,14 @@ def run_occupancy(args):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(stream)
-        for S, h, (D, O, U), hs in zip(sets, host, outs, hsurf):
-            with torch.cuda.stream(stream):
-                for d_, h_ in zip(S["dev"], h):
-                    d_.copy_(h_, non_blocking=True)
-            fgl.gaussian_density(*S["dev"], S["origin"], S["h"], S["dims"], theta=theta,
-                                 out_density=D, out_occ=O, out_surf=U, stream=stream)
-            with torch.cuda.stream(stream):
-                hs.copy_(U, non_blocking=True)
+
+        def e2e_set(i, st):                            # on stream st (the current stream)
+            for d_, h_ in zip(sets[i]["dev"], host[i]):
+                d_.copy_(h_, non_blocking=True)
+            one(i, st)
+            hsurf[i].copy_(outs[i][2], non_blocking=True)
+
+        ss.run(e2e_set)
         e1.record(stream)
         e1.synchronize()
         e_s = e0.elapsed_time(e1) / 1e3
@@ -988,7 +988,47 @@ def run_occupancy(args):
         print(json.dumps(line), flush=True)
 
 
-MESH_STREAMS = 4  # streams (and host threads) the mesh workload's 8 sets share
+MESH_STREAMS = 4  # streams (and host threads) the 8 sets of the mesh and occupancy workloads share
+
+
+class SetStreams:
+    """A workload's sets spread over n streams driven by n host threads
+    (largest set first, each to the least-loaded stream), so one set's host
+    synchronisations overlap the others' kernels; run() brackets all of
+    them on the `main` stream."""
+
+    def __init__(self, torch, dev, sizes, n):
+        import concurrent.futures
+        self.torch = torch
+        self.main = torch.cuda.Stream(device=dev)
+        self.streams = [torch.cuda.Stream(device=dev) for _ in range(n)]
+        self.assign = [[] for _ in range(n)]
+        load = [0] * n
+        for i in sorted(range(len(sizes)), key=lambda i: -sizes[i]):
+            k = int(np.argmin(load))
+            self.assign[k].append(i)
+            load[k] += sizes[i]
+        self.pool = concurrent.futures.ThreadPoolExecutor(n)
+
+    def run(self, per_set):
+        """per_set(i, stream) for every set, with `stream` current in its
+        thread (allocations follow it); returns once everything is enqueued."""
+        torch = self.torch
+        start = torch.cuda.Event()
+        start.record(self.main)
+
+        def work(k):
+            st = self.streams[k]
+            st.wait_event(start)
+            with torch.cuda.stream(st):
+                for i in self.assign[k]:
+                    per_set(i, st)
+            done = torch.cuda.Event()
+            done.record(st)
+            return done
+
+        for done in self.pool.map(work, range(len(self.streams))):
+            self.main.wait_event(done)
 
 
 def gpu_mesher(gs, origin, h, dims):
@@ -1032,16 +1072,10 @@ def run_mesh(args):
     ws, rank, local = dist_setup(args.gpus)
     sets = mesh_setup(torch)
     dev = torch.device("cuda", torch.cuda.current_device())
-    stream = torch.cuda.Stream(device=dev)
     theta, trunc = 0.5, 0.06
-    streams = [torch.cuda.Stream(device=dev) for _ in range(MESH_STREAMS)]
-    assign = [[] for _ in streams]
-    load = [0] * len(streams)
-    for i in sorted(range(len(sets)), key=lambda i: -int(np.prod(sets[i]["dims"]))):
-        k = int(np.argmin(load))
-        assign[k].append(i)
-        load[k] += int(np.prod(sets[i]["dims"]))
-    pool = concurrent.futures.ThreadPoolExecutor(len(streams))
+    ss = SetStreams(torch, dev, [int(np.prod(S["dims"])) for S in sets], MESH_STREAMS)
+    stream = ss.main
+    all_sets = ss.run
 
     def one(S, cap, st=None, ev=None):
         st = stream if st is None else st
@@ -1062,25 +1096,6 @@ def run_mesh(args):
         if ev:
             ev[4].record(st)
         return v, t, dst, tst
-
-    def all_sets(per_set):
-        """per_set(i, stream) for every set, the streams' threads in parallel,
-        bracketed on `stream` (returns after enqueueing; the caller times)."""
-        start = torch.cuda.Event()
-        start.record(stream)
-
-        def work(k):
-            st = streams[k]
-            st.wait_event(start)
-            with torch.cuda.stream(st):                # allocations follow the stream
-                for i in assign[k]:
-                    per_set(i, st)
-            done = torch.cuda.Event()
-            done.record(st)
-            return done
-
-        for done in pool.map(work, range(len(streams))):
-            stream.wait_event(done)
 
     caps = [None] * len(sets)
     for i, S in enumerate(sets):                          # counts, to size the outputs once
@@ -1191,7 +1206,7 @@ def run_mesh(args):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
                 "config": {"workload": "mesh: the hetero ladder's Gaussian sets (50k-2M Gaussians on procedural open-topped rooms), grids = room + 0.75 m at 5-2 cm voxels, theta 0.5, blur sigma h/2 with tau 1/2, TSDF r = 0.06 m, iso 0, mc_step 1",
-                           "streams": len(streams),
+                           "streams": len(ss.streams),
                            "voxels_per_step": voxels, "meshes_per_step": len(sets),
                            "l2": "flushed between timed steps (256 MiB write)",
                            "sets": [{"gaussians": S["n"], "voxel_m": S["h"], "dims": S["dims"],
