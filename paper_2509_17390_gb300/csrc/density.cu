@@ -194,13 +194,32 @@ __global__ void k_emit(const int4* __restrict__ ranges, const unsigned long long
   }
 }
 
+// begin/end of every tile's run in the sorted keys: a grid-stride loop, four
+// strided keys a thread per step with their neighbours loaded together
+constexpr int kBoundsUnroll = 4;
+
 __global__ void k_tile_bounds(const uint32_t* __restrict__ keys, int64_t n,
                               uint32_t* __restrict__ begin, uint32_t* __restrict__ end) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const uint32_t k = keys[i];
-  if (i == 0 || keys[i - 1] != k) begin[k] = (uint32_t)i;
-  if (i == n - 1 || keys[i + 1] != k) end[k] = (uint32_t)(i + 1);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += stride * kBoundsUnroll) {
+    uint32_t k[kBoundsUnroll], kp[kBoundsUnroll], kn[kBoundsUnroll];
+#pragma unroll
+    for (int u = 0; u < kBoundsUnroll; ++u) {
+      const int64_t i = i0 + u * stride;
+      if (i < n) {
+        k[u] = keys[i];
+        kp[u] = i > 0 ? keys[i - 1] : ~k[u];
+        kn[u] = i + 1 < n ? keys[i + 1] : ~k[u];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kBoundsUnroll; ++u) {
+      const int64_t i = i0 + u * stride;
+      if (i >= n) break;
+      if (kp[u] != k[u]) begin[k[u]] = (uint32_t)i;
+      if (kn[u] != k[u]) end[k[u]] = (uint32_t)(i + 1);
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -493,8 +512,9 @@ extern "C" fgl_status fgl_gaussian_density(const fgl_gaussians* gs, const fgl_gr
       k0 = k1;
       v0 = v1;
     }
-    k_tile_bounds<<<(unsigned)((n_pairs + 255) / 256), 256, 0, s>>>(k0, (int64_t)n_pairs, begin,
-                                                                     end);
+    const int64_t tb_blocks = std::min<int64_t>((n_pairs + 256 * kBoundsUnroll - 1) / (256 * kBoundsUnroll),
+                                                (int64_t)152 * 32);
+    k_tile_bounds<<<(unsigned)std::max<int64_t>(1, tb_blocks), 256, 0, s>>>(k0, (int64_t)n_pairs, begin, end);
     ++launches;
     DCUDA(cudaGetLastError());
     if (timing) DCUDA(cudaEventRecord(S.ev[1], s));
