@@ -282,7 +282,42 @@ fgl_status enqueue_batch(BatchCtx& c, const std::vector<Group>& groups,
     const fgl_cast_item& it = items[i];
     if (it.n_env == 0 || !has_extras(it)) continue;
     const ItemDesc d = make_desc(it);
-    for (int k = 0; k < it.n_instances; ++k) {
+    // every instance in one launch when they share a width (the usual case)
+    bool fuse = it.n_instances > 0 && it.n_instances <= kMaxFusedInstances;
+    for (int k = 1; fuse && k < it.n_instances; ++k)
+      fuse = it.instances[k]->bvh.width == it.instances[0]->bvh.width;
+    if (fuse) {
+      InstanceSet a{};
+      a.base.dirs = d.dirs;
+      a.base.poses = d.poses;
+      a.base.n_env = d.n_env;
+      a.base.n_rays = d.n_rays;
+      a.base.width = it.instances[0]->bvh.width;
+      a.base.n_inst = it.n_instances;
+      a.base.k = 0;
+      a.base.inst_poses = it.instance_poses;
+      a.base.min_range = it.min_range;
+      a.base.out_range = it.out_range;
+      a.base.out_tri = it.out_tri;
+      a.base.out_inst = it.out_instance;
+      for (int k = 0; k < it.n_instances; ++k) {
+        const HostBVH& hb = it.instances[k]->bvh;
+        a.nodes[k] = it.instances[k]->d_nodes;
+        a.tris[k] = it.instances[k]->d_tris;
+        double c[3], r2 = 0.0;
+        for (int q = 0; q < 3; ++q) {
+          c[q] = 0.5 * ((double)hb.lo[q] + (double)hb.hi[q]);
+          a.sphere[k][q] = (float)c[q];
+          // the radius from the rounded centre to the farther face, squared
+          const double e = std::max(std::fabs((double)hb.hi[q] - (double)a.sphere[k][q]),
+                                    std::fabs((double)a.sphere[k][q] - (double)hb.lo[q]));
+          r2 += e * e;
+        }
+        a.sphere[k][3] = std::nextafter((float)std::sqrt(r2), INFINITY);
+      }
+      FGL_CUDA(launch_instances_fused(a, it.min_range > 0.f, 128, o.sdepth, s));
+    }
+    for (int k = 0; !fuse && k < it.n_instances; ++k) {
       const fgl_scene is = it.instances[k];
       InstancePass a;
       a.dirs = d.dirs;

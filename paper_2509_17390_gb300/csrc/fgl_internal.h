@@ -132,6 +132,16 @@ struct InstancePass {
   int32_t* out_inst;        // may be null
 };
 
+// All instances of an item in one launch (same width, at most
+// kMaxFusedInstances): `base` as for one pass (its nodes, tris and k unused).
+constexpr int kMaxFusedInstances = 16;
+struct InstanceSet {
+  InstancePass base;
+  const void* nodes[kMaxFusedInstances];
+  const void* tris[kMaxFusedInstances];
+  float sphere[kMaxFusedInstances][4];  // instance-frame bounding sphere: centre, radius (rounded up)
+};
+
 struct alignas(16) BatchHeader {
   unsigned long long head;   // next packet to hand out (atomic)
   int64_t n_packets;

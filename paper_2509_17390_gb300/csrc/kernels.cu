@@ -316,6 +316,108 @@ __global__ void __maxnreg__(72) k_instance_pass(const InstancePass a, int sdepth
   }
 }
 
+// Every instance of an item in one pass (all of one width): a ray's world
+// ray and its return so far stay in registers while it is moved into each
+// instance's frame in turn (instance order) and cast there, pruned by that
+// return, replacing it only when strictly nearer -- the per-instance passes'
+// result, bit for bit, with the ray's record read and written once.
+template <int W, bool TMIN>
+__global__ void __maxnreg__(72) k_instances_fused(const InstanceSet a, int sdepth) {
+  using Keys = typename dev::KeyWords<W>::T;
+  const unsigned FULL = 0xFFFFFFFFu;
+  const Smem<W> sm = smem_layout<W>(sdepth);
+  const int lane = threadIdx.x & 31;
+  const InstancePass& b = a.base;
+  if (b.width != W) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&g_status, 2u);
+    return;
+  }
+  const int64_t total = (int64_t)b.n_env * b.n_rays;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = gid < total;
+  int64_t o_idx = 0;
+  int env = 0;
+  float ox = 0.f, oy = 0.f, oz = 0.f, dx = 0.f, dy = 0.f, dz = 1.f;
+  float cur_t = 0.f;
+  int32_t cur_id = -1, cur_k = -1;
+  if (live) {
+    env = (int)(gid / b.n_rays);
+    const int j = (int)(gid - (int64_t)env * b.n_rays);
+    const float4 ds = __ldg((const float4*)b.dirs + j);
+    o_idx = (int64_t)env * b.n_rays + __float_as_int(ds.w);
+    dev::world_ray(b.poses + 12 * (int64_t)env, ds, ox, oy, oz, dx, dy, dz);
+    cur_t = b.out_range[o_idx];
+    cur_id = b.out_tri[o_idx];
+  }
+  uint2 ls[kStackLocal];
+  Keys lq[kStackLocal];
+  const dev::StackRefs<Keys> st{sm.ss, sm.sq, ls, lq, (int)blockDim.x, sdepth};
+  for (int k = 0; k < b.n_inst; ++k) {
+    dev::Tracer<W, false, TMIN> tr;
+    tr.tg = make_uint2(0u, 0u);
+    tr.ng = make_uint2(0u, 0u);
+    bool done = !live;
+    if (live) {
+      const float* P = b.inst_poses + 12 * ((int64_t)env * b.n_inst + k);
+      float R[12];
+#pragma unroll
+      for (int i = 0; i < 12; ++i) R[i] = __ldg(P + i);
+      // cull with the instance's bounding sphere moved into the world: skip
+      // when the ray line misses it, it lies behind the origin or wholly
+      // beyond the return so far.  A margin of 1e-4 of its distance covers the
+      // float32 error of these few products many times over, and the miss
+      // test adds 1e-6 dist^2 for the cancellation in dist^2 - tca^2
+      // (at most a few units of 2^-23 dist^2).
+      const float* sp = a.sphere[k];
+      const float cx = R[0] * sp[0] + R[1] * sp[1] + R[2] * sp[2] + R[3] - ox;
+      const float cy = R[4] * sp[0] + R[5] * sp[1] + R[6] * sp[2] + R[7] - oy;
+      const float cz = R[8] * sp[0] + R[9] * sp[1] + R[10] * sp[2] + R[11] - oz;
+      const float dist2 = cx * cx + cy * cy + cz * cz;
+      const float tca = cx * dx + cy * dy + cz * dz;
+      const float rr = sp[3] + 1e-4f * (sqrtf(dist2) + sp[3]) + 1e-5f;
+      const float perp2 = dist2 - tca * tca;
+      const bool outside = dist2 > rr * rr;
+      done = outside && (perp2 > rr * rr + 1e-6f * dist2 || tca < -rr || tca - rr > cur_t);
+      if (!done) {
+        const float u0 = __fsub_rn(ox, R[3]), u1 = __fsub_rn(oy, R[7]), u2 = __fsub_rn(oz, R[11]);
+        float lo[3], ld[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          lo[i] = __fadd_rn(__fadd_rn(__fmul_rn(R[i], u0), __fmul_rn(R[4 + i], u1)), __fmul_rn(R[8 + i], u2));
+          ld[i] = __fadd_rn(__fadd_rn(__fmul_rn(R[i], dx), __fmul_rn(R[4 + i], dy)), __fmul_rn(R[8 + i], dz));
+        }
+        dev::setup_ray(tr.r, lo[0], lo[1], lo[2], ld[0], ld[1], ld[2]);
+        tr.start(a.nodes[k], a.tris[k], b.min_range, cur_t);
+      } else {
+        tr.best_id = dev::kNoHit;
+      }
+    }
+    while (__any_sync(FULL, !done)) {
+      bool ok = true;
+      if (!done) ok = tr.descend(st);
+      dev::tri_phase_warp(tr, sm.keys, lane);
+      if (!done) {
+        if (!ok) {
+          atomicOr(&g_status, 1u);
+          done = true;
+        } else {
+          done = tr.finish(st);
+        }
+      }
+    }
+    if (live && tr.best_id != dev::kNoHit && (cur_id < 0 || tr.best_t < cur_t)) {
+      cur_t = tr.best_t;
+      cur_id = tr.best_id;
+      cur_k = k;
+    }
+  }
+  if (live) {
+    b.out_range[o_idx] = cur_t;
+    b.out_tri[o_idx] = cur_id;
+    if (b.out_inst) b.out_inst[o_idx] = cur_k;
+  }
+}
+
 // World-frame return points: p_i = o_i + (t * d_i) (two roundings), NaN on a miss.
 __global__ void k_points(const float4* __restrict__ dirs, const float* __restrict__ poses,
                          int n_env, int n_rays, const float* __restrict__ range,
@@ -439,6 +541,23 @@ cudaError_t launch_instance_pass(const InstancePass& a, bool tmin, int block, in
     if (e != cudaSuccess) return e;
   }
   InstancePass arg = a;
+  void* args[] = {&arg, &sdepth};
+  return cudaLaunchKernel(fn, dim3((unsigned)((total + block - 1) / block)), dim3(block), args, smem, s);
+}
+
+cudaError_t launch_instances_fused(const InstanceSet& a, bool tmin, int block, int sdepth,
+                                   cudaStream_t s) {
+  const int64_t total = (int64_t)a.base.n_env * a.base.n_rays;
+  if (total == 0 || a.base.n_inst == 0) return cudaSuccess;
+  void* fn;
+  if (a.base.width == 8) fn = tmin ? (void*)k_instances_fused<8, true> : (void*)k_instances_fused<8, false>;
+  else fn = tmin ? (void*)k_instances_fused<4, true> : (void*)k_instances_fused<4, false>;
+  const size_t smem = stack_smem_bytes(a.base.width, block, sdepth);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  InstanceSet arg = a;
   void* args[] = {&arg, &sdepth};
   return cudaLaunchKernel(fn, dim3((unsigned)((total + block - 1) / block)), dim3(block), args, smem, s);
 }

@@ -30,6 +30,9 @@ cudaError_t launch_persistent(int W, bool count, bool tmin, void* scratch, int g
 
 // Instance pass (see InstancePass in fgl_internal.h): one launch per item
 // and instance, after the scene pass.
+// All instances of an item in one launch (same width, at most kMaxFusedInstances).
+cudaError_t launch_instances_fused(const InstanceSet& a, bool tmin, int block, int sdepth,
+                                   cudaStream_t s);
 cudaError_t launch_instance_pass(const InstancePass& a, bool tmin, int block, int sdepth,
                                  cudaStream_t s);
 

@@ -157,3 +157,20 @@ def test_walk_instances_fullsize_sampled_vs_oracle():
     ref = o.astype(np.float64) + gr[sel].astype(np.float64)[:, None] * d.astype(np.float64)
     err = np.abs(pts[sel][hit] - ref[hit]).max(axis=1)
     assert np.all(err <= 4e-7 * (np.abs(ref[hit]).max(axis=1) + 1))
+
+
+@pytest.mark.parametrize("min_range", [0.0, 0.7])
+def test_fused_instance_pass_equals_per_instance_passes(min_range):
+    """Instances of one width go through one fused launch, mixed widths
+    through one pass per instance; widths never change a result, so both
+    give the same ranges, triangles, instances and points bit for bit."""
+    vs, ts, meshes, P, IP = instance_setup(9, 8, 3)
+    se = fgl.Sensor.from_table(synth.grid_sensor(16, -15, 15, 360))
+    scene = fgl.Scene(vs, ts)
+    fused = [fgl.Scene(v, t, width=8) for v, t in meshes]
+    mixed = [fgl.Scene(v, t, width=w) for (v, t), w in zip(meshes, (8, 4, 8))]
+    a = gpu_cast(scene, se, P, 100.0, fused, IP, min_range=min_range)
+    b = gpu_cast(scene, se, P, 100.0, mixed, IP, min_range=min_range)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y, equal_nan=True)
+    assert (a[2] >= 0).sum() > 300
