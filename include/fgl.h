@@ -55,8 +55,10 @@ typedef enum {
   FGL_ERR_BUDGET = 4,    /* serving: request larger than the HBM budget */
   FGL_ERR_TIMEOUT = 5,   /* serving: wait timed out */
   FGL_ERR_CANCELLED = 6, /* serving: request cancelled */
-  FGL_ERR_DEVICE = 7,    /* a kernel reported an error (traversal stack overflow) */
-  FGL_ERR_CAPACITY = 8   /* output buffers too small; the needed counts are reported */
+  FGL_ERR_DEVICE = 7,    /* a kernel reported an error (traversal stack overflow; in the
+                            checked library also an index out of range) */
+  FGL_ERR_CAPACITY = 8,  /* output buffers too small; the needed counts are reported */
+  FGL_ERR_INTERNAL = 9   /* serving: a host exception in the server's worker thread */
 } fgl_status;
 
 typedef struct fgl_scene_s* fgl_scene;
@@ -234,7 +236,7 @@ fgl_status fgl_cast_batched_host(const fgl_cast_item* items, int32_t n_items,
  * interface for such callers, not part of the method.
  *   Same arguments, layouts and results as fgl_cast_batched (use_graph is
  *   ignored); the caller still owns poses and outputs.  The work-queue scratch
- *   is a fixed array of ~20 KiB inside the library (held by every GPU that
+ *   is a fixed array of ~25 KiB inside the library (held by every GPU that
  *   loads it until the process exits), so a call allocates nothing on the
  *   device, and nothing on the host when it succeeds.
  *   Limit: at most 256 items per call; more is rejected with FGL_ERR_INVALID.
@@ -295,7 +297,9 @@ typedef struct {
   int64_t n_tris;
   int64_t n_nodes;          /* internal nodes (n_tris - 1); leaves hold one triangle */
   int32_t depth;            /* levels of the binary tree (root = 1) */
-  int32_t overflow;         /* 1 when a cast's traversal stack overflowed (returns then wrong) */
+  int32_t overflow;         /* bit 0: a cast's traversal stack overflowed (returns then wrong);
+                               bit 1: a node or triangle index was out of range (checked
+                               library only) */
   float build_ms;           /* host-observed build time of the last build, synchronised */
   float margin;             /* outward margin of every leaf box (metres) */
   float centroid_lo[3];     /* the box the Morton codes quantise (triangle centroids) */
@@ -562,6 +566,12 @@ fgl_status fgl_server_reset_stats(fgl_server server);
 /* Fault injection for tests: the next n admissions fail their device
  * allocation (those requests complete with FGL_ERR_OOM). */
 fgl_status fgl_server_inject_alloc_failures(fgl_server server, int32_t n);
+/* Fault injection for tests: the next n ticks that have work throw a host
+ * exception in the worker thread after they are packed and before their
+ * launch.  The worker contains it: the requests with chunks in that tick
+ * complete with FGL_ERR_INTERNAL (FGL_ERR_OOM for a failed host allocation),
+ * no other request is affected, and the server keeps serving. */
+fgl_status fgl_server_inject_worker_faults(fgl_server server, int32_t n);
 /* Wait (up to 60 s) for in-flight ticks, stop the threads, free buffers. */
 fgl_status fgl_server_destroy(fgl_server server);
 

@@ -26,6 +26,7 @@ __all__ = ["Scene", "Sensor", "BatchOpts", "cast", "cast_opts", "cast_batched",
 FGL_OK, FGL_ERR_INVALID, FGL_ERR_OOM, FGL_ERR_CUDA = 0, 1, 2, 3
 FGL_ERR_BUDGET, FGL_ERR_TIMEOUT, FGL_ERR_CANCELLED, FGL_ERR_DEVICE = 4, 5, 6, 7
 FGL_ERR_CAPACITY = 8
+FGL_ERR_INTERNAL = 9
 STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "BUDGET", 5: "TIMEOUT",
                 6: "CANCELLED", 7: "DEVICE", 8: "CAPACITY"}
 
@@ -72,13 +73,16 @@ _lock = threading.Lock()
 
 
 def lib():
-    """Load (building in-tree first if needed) libfgl.so."""
+    """Load (building in-tree first if needed) libfgl.so; with the
+    environment variable FGL_CHECKED=1 set before the first call, the checked
+    library libfgl_checked.so (bounds-checked traversal, for debugging)."""
     global _lib
     with _lock:
         if _lib is None:
-            path = build_native.LIB
+            checked = os.environ.get("FGL_CHECKED") == "1"
+            path = build_native.LIB_CHECKED if checked else build_native.LIB
             if not os.path.exists(path):
-                build_native.build()
+                build_native.build(checked=checked)
             L = ctypes.CDLL(path)
             sig = {
                 "fgl_scene_build": ([P, I64, P, I64, P, P], I32),
@@ -107,6 +111,7 @@ def lib():
                 "fgl_server_get_stats": ([P, P], I32),
                 "fgl_server_reset_stats": ([P], I32),
                 "fgl_server_inject_alloc_failures": ([P, I32], I32),
+                "fgl_server_inject_worker_faults": ([P, I32], I32),
                 "fgl_server_destroy": ([P], I32),
                 "fgl_sync": ([P], I32),
                 "fgl_work_counters": ([P, P, P], I32),
@@ -725,6 +730,11 @@ class Server:
 
     def inject_alloc_failures(self, n: int):
         _check(lib().fgl_server_inject_alloc_failures(self._h, n))
+
+    def inject_worker_faults(self, n: int):
+        """The next n ticks with work throw a host exception in the worker
+        (fgl_server_inject_worker_faults)."""
+        _check(lib().fgl_server_inject_worker_faults(self._h, n))
 
     def stats(self) -> dict:
         s = ServerStats()

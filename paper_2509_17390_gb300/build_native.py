@@ -1,7 +1,11 @@
 """Build libfgl.so in-tree (nvcc for sm_103a, g++ for host-only sources).
 
 Translation units compile in parallel; the library links the CUDA runtime
-statically, so it only needs the driver at run time.
+statically, so it only needs the driver at run time.  `build(checked=True)`
+builds the checked library instead (libfgl_checked.so, -DFGL_CHECKED: the
+traversal kernels compare every node and triangle index with the scene's
+record counts before reading and report FGL_ERR_DEVICE instead of reading
+out of range), the debugging stand-in for a memory checker.
 """
 
 from __future__ import annotations
@@ -16,6 +20,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libfgl.so")
+BUILD_CHECKED = os.path.join(PKG, "_build_checked")
+LIB_CHECKED = os.path.join(BUILD_CHECKED, "libfgl_checked.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",
@@ -43,19 +49,21 @@ def _stale(out: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every translation unit that changed and link libfgl.so."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """Compile every translation unit that changed and link libfgl.so (or,
+    with checked=True, libfgl_checked.so)."""
+    build_dir, lib = (BUILD_CHECKED, LIB_CHECKED) if checked else (BUILD, LIB)
+    os.makedirs(build_dir, exist_ok=True)
     hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(INCLUDE, "fgl.h")]
     jobs, objs = [], []
     nvcc = _nvcc()
     for src in CU_SOURCES + CPP_SOURCES:
         path = os.path.join(CSRC, src)
-        obj = os.path.join(BUILD, src + ".o")
+        obj = os.path.join(build_dir, src + ".o")
         objs.append(obj)
         if force or _stale(obj, [path] + hdrs):
             if src.endswith(".cu"):
-                cmd = [nvcc] + NVCC_FLAGS + ["-c", path, "-o", obj]
+                cmd = [nvcc] + NVCC_FLAGS + (["-DFGL_CHECKED=1"] if checked else []) + ["-c", path, "-o", obj]
             else:
                 cmd = ["g++"] + GXX_FLAGS + ["-c", path, "-o", obj]
             jobs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
@@ -66,13 +74,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
             raise RuntimeError("compilation failed: " + " ".join(cmd))
         if verbose and out:
             sys.stderr.write(out.decode(errors="replace"))
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or jobs or _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-Xcompiler", "-pthread"]
         subprocess.run(cmd, check=True)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, checked="--checked" in sys.argv))

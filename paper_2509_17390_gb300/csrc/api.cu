@@ -147,6 +147,9 @@ fgl_status check_item(const fgl_cast_item& it, int idx) {
 // Items with instances or point output need launches beyond the scene pass.
 bool has_extras(const fgl_cast_item& it) { return it.n_instances > 0 || it.out_points; }
 
+// a record count for the checked library's bounds checks (saturated)
+uint32_t count32(int64_t n) { return n < 0 ? 0u : n > 0xFFFFFFFFll ? 0xFFFFFFFFu : (uint32_t)n; }
+
 ItemDesc make_desc(const fgl_cast_item& it) {
   ItemDesc d;
   std::memset(&d, 0, sizeof(d));
@@ -161,6 +164,8 @@ ItemDesc make_desc(const fgl_cast_item& it) {
   d.max_range = it.max_range;
   d.width = it.scene->bvh.width;
   d.min_range = it.min_range;
+  d.n_nodes = count32(it.scene->bvh.n_nodes);
+  d.n_tris = count32(it.scene->bvh.n_tris);
   return d;
 }
 
@@ -304,6 +309,8 @@ fgl_status enqueue_batch(BatchCtx& c, const std::vector<Group>& groups,
         const HostBVH& hb = it.instances[k]->bvh;
         a.nodes[k] = it.instances[k]->d_nodes;
         a.tris[k] = it.instances[k]->d_tris;
+        a.n_nodes[k] = count32(hb.n_nodes);
+        a.n_tris[k] = count32(hb.n_tris);
         double c[3], r2 = 0.0;
         for (int q = 0; q < 3; ++q) {
           c[q] = 0.5 * ((double)hb.lo[q] + (double)hb.hi[q]);
@@ -326,6 +333,8 @@ fgl_status enqueue_batch(BatchCtx& c, const std::vector<Group>& groups,
       a.n_rays = d.n_rays;
       a.nodes = is->d_nodes;
       a.tris = is->d_tris;
+      a.n_nodes = count32(is->bvh.n_nodes);
+      a.n_tris = count32(is->bvh.n_tris);
       a.width = is->bvh.width;
       a.n_inst = it.n_instances;
       a.k = k;
@@ -1003,6 +1012,7 @@ fgl_status fgl_sync(fgl_stream stream) {
   unsigned st = 0;
   FGL_CUDA(read_and_clear_status(&st));
   if (st & 2u) return fail(FGL_ERR_DEVICE, "a kernel was handed an item of another BVH width");
+  if (st & 4u) return fail(FGL_ERR_DEVICE, "a node or triangle index out of range (checked library)");
   if (st) return fail(FGL_ERR_DEVICE, "traversal stack overflow in a kernel");
   return FGL_OK;
 }

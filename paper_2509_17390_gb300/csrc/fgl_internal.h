@@ -111,8 +111,10 @@ struct alignas(16) ItemDesc {
   float max_range;
   int32_t width;         // BVH width of `nodes`; a kernel for another width skips the item
   float min_range;       // t_min: hits nearer than this are discarded
+  uint32_t n_nodes;      // record counts of `nodes` and `tris` (saturated at 2^32 - 1),
+  uint32_t n_tris;       // for the checked library's bounds checks
 };
-static_assert(sizeof(ItemDesc) == 80, "ItemDesc layout");
+static_assert(sizeof(ItemDesc) == 96, "ItemDesc layout");
 
 // One instance pass: cast the rays of an item against instance k of each
 // environment (its BVH in its own frame, its pose per environment), keeping
@@ -123,6 +125,7 @@ struct InstancePass {
   int32_t n_env, n_rays;
   const void* nodes;        // the instance's BVH
   const void* tris;
+  uint32_t n_nodes, n_tris; // their record counts (bounds checks of the checked library)
   int32_t width;
   int32_t n_inst, k;
   const float* inst_poses;  // [n_env][n_inst][12] world-from-local
@@ -140,6 +143,7 @@ struct InstanceSet {
   const void* nodes[kMaxFusedInstances];
   const void* tris[kMaxFusedInstances];
   float sphere[kMaxFusedInstances][4];  // instance-frame bounding sphere: centre, radius (rounded up)
+  uint32_t n_nodes[kMaxFusedInstances], n_tris[kMaxFusedInstances];  // record counts
 };
 
 struct alignas(16) BatchHeader {

@@ -88,7 +88,7 @@ __global__ void __maxnreg__(72) k_plain(const ItemDesc it, int sdepth, int tri_m
     float ox, oy, oz, dx, dy, dz;
     dev::world_ray(it.poses + 12 * (int64_t)env, ds, ox, oy, oz, dx, dy, dz);
     dev::setup_ray(tr.r, ox, oy, oz, dx, dy, dz);
-    tr.start(it.nodes, it.tris, it.min_range, it.max_range);
+    tr.start(it.nodes, it.tris, it.min_range, it.max_range, it.n_nodes, it.n_tris);
   }
   uint2 ls[kStackLocal];
   Keys lq[kStackLocal];
@@ -97,10 +97,10 @@ __global__ void __maxnreg__(72) k_plain(const ItemDesc it, int sdepth, int tri_m
     while (__any_sync(FULL, !done)) {
       bool ok = true;
       if (!done) ok = tr.descend(st);
-      dev::tri_phase_warp(tr, sm.keys, lane);
+      dev::tri_phase_warp(tr, sm.keys, lane, &g_status);
       if (!done) {
         if (!ok) {
-          atomicOr(&g_status, 1u);
+          atomicOr(&g_status, tr.fail_bits());
           done = true;
         } else {
           done = tr.finish(st);
@@ -195,7 +195,7 @@ __global__ void __maxnreg__(72) k_persistent(BatchHeader* __restrict__ hdr,
             c_nodes += tr.n_nodes;
             c_tris += tr.n_tris;
           }
-          tr.start(it.nodes, it.tris, it.min_range, it.max_range);
+          tr.start(it.nodes, it.tris, it.min_range, it.max_range, it.n_nodes, it.n_tris);
           const int64_t o = (int64_t)pk_env * it.n_rays + __float_as_int(ds.w);
           out_r = it.out_range + o;
           out_t = it.out_tri + o;
@@ -214,10 +214,10 @@ __global__ void __maxnreg__(72) k_persistent(BatchHeader* __restrict__ hdr,
     if (tri_mode != 1) {
       bool ok = true;
       if (active) ok = tr.descend(st);
-      dev::tri_phase_warp(tr, sm.keys, lane);
+      dev::tri_phase_warp(tr, sm.keys, lane, &g_status);
       if (active) {
         if (!ok) {
-          atomicOr(&g_status, 1u);
+          atomicOr(&g_status, tr.fail_bits());
           fin = true;
         } else {
           fin = tr.finish(st);
@@ -286,7 +286,7 @@ __global__ void __maxnreg__(72) k_instance_pass(const InstancePass a, int sdepth
     cur_t = a.out_range[o_idx];
     cur_id = a.out_tri[o_idx];
     dev::setup_ray(tr.r, lo[0], lo[1], lo[2], ld[0], ld[1], ld[2]);
-    tr.start(a.nodes, a.tris, a.min_range, cur_t);
+    tr.start(a.nodes, a.tris, a.min_range, cur_t, a.n_nodes, a.n_tris);
   }
   uint2 ls[kStackLocal];
   Keys lq[kStackLocal];
@@ -294,10 +294,10 @@ __global__ void __maxnreg__(72) k_instance_pass(const InstancePass a, int sdepth
   while (__any_sync(FULL, !done)) {
     bool ok = true;
     if (!done) ok = tr.descend(st);
-    dev::tri_phase_warp(tr, sm.keys, lane);
+    dev::tri_phase_warp(tr, sm.keys, lane, &g_status);
     if (!done) {
       if (!ok) {
-        atomicOr(&g_status, 1u);
+        atomicOr(&g_status, tr.fail_bits());
         done = true;
       } else {
         done = tr.finish(st);
@@ -387,7 +387,7 @@ __global__ void __maxnreg__(72) k_instances_fused(const InstanceSet a, int sdept
           ld[i] = __fadd_rn(__fadd_rn(__fmul_rn(R[i], dx), __fmul_rn(R[4 + i], dy)), __fmul_rn(R[8 + i], dz));
         }
         dev::setup_ray(tr.r, lo[0], lo[1], lo[2], ld[0], ld[1], ld[2]);
-        tr.start(a.nodes[k], a.tris[k], b.min_range, cur_t);
+        tr.start(a.nodes[k], a.tris[k], b.min_range, cur_t, a.n_nodes[k], a.n_tris[k]);
       } else {
         tr.best_id = dev::kNoHit;
       }
@@ -395,10 +395,10 @@ __global__ void __maxnreg__(72) k_instances_fused(const InstanceSet a, int sdept
     while (__any_sync(FULL, !done)) {
       bool ok = true;
       if (!done) ok = tr.descend(st);
-      dev::tri_phase_warp(tr, sm.keys, lane);
+      dev::tri_phase_warp(tr, sm.keys, lane, &g_status);
       if (!done) {
         if (!ok) {
-          atomicOr(&g_status, 1u);
+          atomicOr(&g_status, tr.fail_bits());
           done = true;
         } else {
           done = tr.finish(st);

@@ -38,7 +38,8 @@ using namespace fgl;
 struct fgl_lbvh_s {
   int device = -1;
   int64_t nt = 0;
-  unsigned* status = nullptr;  // device word: bit 0 = a cast's stack overflowed
+  unsigned* status = nullptr;  // device word: bit 0 = a cast's stack overflowed, bit 2 = an
+                               // index out of range (checked library)
   void* nodes = nullptr;   // (nt - 1) x 64 B
   void* tris = nullptr;    // nt x 48 B, Morton order
   void* work = nullptr;    // build scratch
@@ -323,6 +324,12 @@ __global__ void k_lbvh_cast(const LbvhCast a, unsigned* status) {
   const float tmin = TMIN ? a.min_range : 0.f;
   const float nox = -ox * tr.r.ix, noy = -oy * tr.r.iy, noz = -oz * tr.r.iz;
   auto test_tri = [&](int64_t k) {
+#ifdef FGL_CHECKED
+    if (k < 0 || k >= (int64_t)a.nt) {  // checked library: no read past the triangles
+      atomicOr(status, 4u);
+      return;
+    }
+#endif
     const float4* tp = a.tris + 3 * k;
     const float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
     tr.consider(dev::tri_hit(tr.r, v0, v1, v2, tr.best_t), __float_as_int(v0.w));
@@ -335,6 +342,12 @@ __global__ void k_lbvh_cast(const LbvhCast a, unsigned* status) {
     int sp = 0;
     int node = 0;
     for (;;) {
+#ifdef FGL_CHECKED
+      if (node < 0 || (int64_t)node >= (int64_t)a.nt - 1) {  // checked library: no read past the nodes
+        atomicOr(status, 4u);
+        break;
+      }
+#endif
       const LbvhNode* nd = a.nodes + node;
       const float4 A = __ldg(&nd->a), B = __ldg(&nd->b), C = __ldg(&nd->c);
       const int4 D = __ldg(&nd->d);
@@ -571,7 +584,7 @@ extern "C" fgl_status fgl_lbvh_get_stats(fgl_lbvh L, fgl_lbvh_stats* o) {
   o->build_ms = L->build_ms;
   unsigned st = 0;
   if (L->status) LCUDA(cudaMemcpy(&st, L->status, sizeof(st), cudaMemcpyDeviceToHost));
-  o->overflow = (int32_t)(st & 1u);
+  o->overflow = (int32_t)((st & 1u) | ((st & 4u) ? 2u : 0u));
   o->margin = L->margin;
   for (int a = 0; a < 3; ++a) {
     o->centroid_lo[a] = L->lo[a];

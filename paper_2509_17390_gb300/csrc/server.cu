@@ -29,6 +29,8 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <new>
+#include <stdexcept>
 #include <string>
 #include <thread>
 #include <unordered_map>
@@ -140,6 +142,7 @@ struct fgl_server_s {
   uint64_t lru_clock = 0;
   int64_t used_bytes = 0;
   int inject_alloc_fail = 0;
+  int inject_worker_fault = 0;
   PinnedPool pinned;
 
   // stats
@@ -281,89 +284,116 @@ void worker_main(fgl_server_s* Sp) {
     S.cv_tick.wait(lk, [&] { return S.stop || S.ticks.size() < 2; });
     if (S.stop) break;
     fgl::NvtxRange range("fgl_server tick");
-    admit(S);
-    // pack the tick
-    items.clear();
-    int64_t budget = S.o.tick_rays;
     Tick t;
     t.id = S.next_tick;
-    if (S.o.mode == 0) {
-      for (int64_t tk : S.active) {
-        Request& q = *S.reqs[tk];
-        if (q.cancel || q.env_next >= q.r.n_env || budget <= 0) continue;
-        int64_t fit = budget / std::max<int32_t>(1, q.n_rays);
-        int32_t chunk = (int32_t)std::min<int64_t>(q.r.n_env - q.env_next, std::max<int64_t>(1, fit));
-        fgl_cast_item it{};
-        it.scene = S.scenes[q.r.scene_id].scene;
-        it.sensor = S.sensors[q.r.sensor_id].sensor;
-        it.poses = q.d_poses + (size_t)q.env_next * 12;
-        it.n_env = chunk;
-        it.max_range = q.r.max_range;
-        it.min_range = q.r.min_range;
-        it.out_range = q.d_range + (size_t)q.env_next * q.n_rays;
-        it.out_tri = q.d_tri + (size_t)q.env_next * q.n_rays;
-        items.push_back(it);
-        q.env_next += chunk;
-        q.last_tick = t.id;
-        if (q.env_next >= q.r.n_env) t.finishing.push_back(tk);
-        budget -= (int64_t)chunk * q.n_rays;
-      }
-    } else {
-      // per-environment launches, one request at a time in arrival order
-      for (int64_t tk : S.active) {
-        Request& q = *S.reqs[tk];
-        if (q.cancel || q.env_next >= q.r.n_env) continue;
-        for (int32_t e = 0; e < q.r.n_env; ++e) {
+    bool counted = false;  // the tick id is taken (next_tick advanced)
+    int status = FGL_OK;
+    // An exception while a tick is packed or launched (an allocation that
+    // fails, or one injected by fgl_server_inject_worker_faults) fails the
+    // requests with chunks in this tick, and only them; the tick is still
+    // queued, without a launch, so that their buffers are freed once the
+    // ticks before it (which may write into them) are done.
+    try {
+      admit(S);
+      items.clear();
+      int64_t budget = S.o.tick_rays;
+      if (S.o.mode == 0) {
+        for (int64_t tk : S.active) {
+          Request& q = *S.reqs[tk];
+          if (q.cancel || q.env_next >= q.r.n_env || budget <= 0) continue;
+          int64_t fit = budget / std::max<int32_t>(1, q.n_rays);
+          int32_t chunk = (int32_t)std::min<int64_t>(q.r.n_env - q.env_next, std::max<int64_t>(1, fit));
           fgl_cast_item it{};
           it.scene = S.scenes[q.r.scene_id].scene;
           it.sensor = S.sensors[q.r.sensor_id].sensor;
-          it.poses = q.d_poses + (size_t)e * 12;
-          it.n_env = 1;
+          it.poses = q.d_poses + (size_t)q.env_next * 12;
+          it.n_env = chunk;
           it.max_range = q.r.max_range;
           it.min_range = q.r.min_range;
-          it.out_range = q.d_range + (size_t)e * q.n_rays;
-          it.out_tri = q.d_tri + (size_t)e * q.n_rays;
+          it.out_range = q.d_range + (size_t)q.env_next * q.n_rays;
+          it.out_tri = q.d_tri + (size_t)q.env_next * q.n_rays;
           items.push_back(it);
+          q.env_next += chunk;
+          q.last_tick = t.id;
+          if (q.env_next >= q.r.n_env) t.finishing.push_back(tk);
+          budget -= (int64_t)chunk * q.n_rays;
         }
-        q.env_next = q.r.n_env;
-        q.last_tick = t.id;
-        t.finishing.push_back(tk);
-        break;
+      } else {
+        // per-environment launches, one request at a time in arrival order
+        for (int64_t tk : S.active) {
+          Request& q = *S.reqs[tk];
+          if (q.cancel || q.env_next >= q.r.n_env) continue;
+          for (int32_t e = 0; e < q.r.n_env; ++e) {
+            fgl_cast_item it{};
+            it.scene = S.scenes[q.r.scene_id].scene;
+            it.sensor = S.sensors[q.r.sensor_id].sensor;
+            it.poses = q.d_poses + (size_t)e * 12;
+            it.n_env = 1;
+            it.max_range = q.r.max_range;
+            it.min_range = q.r.min_range;
+            it.out_range = q.d_range + (size_t)e * q.n_rays;
+            it.out_tri = q.d_tri + (size_t)e * q.n_rays;
+            items.push_back(it);
+          }
+          q.env_next = q.r.n_env;
+          q.last_tick = t.id;
+          t.finishing.push_back(tk);
+          break;
+        }
       }
-    }
-    // cancelled active requests with nothing in flight complete right away
-    for (size_t i = 0; i < S.active.size();) {
-      Request& q = *S.reqs[S.active[i]];
-      if (q.cancel && (q.last_tick < 0 || q.last_tick < S.next_tick - (int64_t)S.ticks.size())) {
-        detach_request(S, q);
-        free_request(S, q);
-        finish_request(S, q, FGL_ERR_CANCELLED);
+      // cancelled active requests with nothing in flight complete right away
+      for (size_t i = 0; i < S.active.size();) {
+        Request& q = *S.reqs[S.active[i]];
+        if (q.cancel && (q.last_tick < 0 || q.last_tick < S.next_tick - (int64_t)S.ticks.size())) {
+          detach_request(S, q);
+          free_request(S, q);
+          finish_request(S, q, FGL_ERR_CANCELLED);
+          continue;
+        }
+        ++i;
+      }
+      if (items.empty()) {
+        S.cv_work.wait_for(lk, std::chrono::milliseconds(2));
         continue;
       }
-      ++i;
-    }
-    if (items.empty()) {
-      S.cv_work.wait_for(lk, std::chrono::milliseconds(2));
-      continue;
-    }
-    ++S.next_tick;
-    ++S.n_ticks;
-    lk.unlock();
-    int status = FGL_OK;
-    if (S.o.mode == 0) {
-      status = fgl_cast_batched(items.data(), (int32_t)items.size(), &S.o.opts, S.compute);
-    } else {
-      for (const fgl_cast_item& it : items) {
-        status = it.min_range > 0.f
-                     ? fgl_cast_batched(&it, 1, &S.o.opts, S.compute)
-                     : fgl_cast(it.scene, it.sensor, it.poses, 1, it.max_range, it.out_range,
-                                it.out_tri, S.compute);
-        if (status != FGL_OK) break;
+      ++S.next_tick;
+      ++S.n_ticks;
+      counted = true;
+      if (S.inject_worker_fault > 0) {
+        --S.inject_worker_fault;
+        throw std::runtime_error("injected worker fault");
+      }
+      lk.unlock();
+      if (S.o.mode == 0) {
+        status = fgl_cast_batched(items.data(), (int32_t)items.size(), &S.o.opts, S.compute);
+      } else {
+        for (const fgl_cast_item& it : items) {
+          status = it.min_range > 0.f
+                       ? fgl_cast_batched(&it, 1, &S.o.opts, S.compute)
+                       : fgl_cast(it.scene, it.sensor, it.poses, 1, it.max_range, it.out_range,
+                                  it.out_tri, S.compute);
+          if (status != FGL_OK) break;
+        }
+      }
+      lk.lock();
+    } catch (const std::exception& ex) {
+      if (!lk.owns_lock()) lk.lock();
+      status = dynamic_cast<const std::bad_alloc*>(&ex) ? FGL_ERR_OOM : FGL_ERR_INTERNAL;
+      if (!counted) {
+        ++S.next_tick;
+        ++S.n_ticks;
+      }
+      // every request with a chunk in this tick ends here, with the error
+      t.finishing.clear();
+      for (int64_t tk : S.active) {
+        Request& q = *S.reqs[tk];
+        if (q.last_tick != t.id) continue;
+        q.env_next = q.r.n_env;
+        t.finishing.push_back(tk);
       }
     }
     cudaEventCreateWithFlags(&t.done, cudaEventDisableTiming);
     cudaEventRecord(t.done, S.compute);
-    lk.lock();
     if (status != FGL_OK) {
       for (int64_t tk : t.finishing) S.reqs[tk]->status = status;
     }
@@ -557,6 +587,7 @@ fgl_status fgl_server_wait(fgl_server S, int64_t ticket, int32_t timeout_ms, fgl
   if (st != FGL_OK) {
     return set_err(st, st == FGL_ERR_CANCELLED ? "request cancelled"
                        : st == FGL_ERR_OOM ? "device allocation for the request failed"
+                       : st == FGL_ERR_INTERNAL ? "a host exception in the server's worker failed the request"
                                            : "request failed");
   }
   return FGL_OK;
@@ -576,6 +607,13 @@ fgl_status fgl_server_inject_alloc_failures(fgl_server S, int32_t n) {
   if (!S || n < 0) return set_err(FGL_ERR_INVALID, "bad argument");
   std::lock_guard<std::mutex> lk(S->mu);
   S->inject_alloc_fail = n;
+  return FGL_OK;
+}
+
+fgl_status fgl_server_inject_worker_faults(fgl_server S, int32_t n) {
+  if (!S || n < 0) return set_err(FGL_ERR_INVALID, "bad argument");
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->inject_worker_fault = n;
   return FGL_OK;
 }
 

@@ -291,6 +291,11 @@ struct StackRefs {
 // TMIN: the rays may have a minimum range t_min > 0 (eq. t_j*: hits nearer
 // than it are discarded); without it t_min is the constant 0 and costs no
 // register.
+//
+// Built with FGL_CHECKED (the checked library), every node and triangle
+// index is compared with the scene's record counts before it is read; an
+// index out of range abandons the ray and sets status bit 2 (FGL_ERR_DEVICE
+// on the host) instead of reading past the arrays.
 template <int W, bool COUNT, bool TMIN = false>
 struct Tracer {
   using Keys = typename KeyWords<W>::T;
@@ -304,11 +309,23 @@ struct Tracer {
   const uint4* __restrict__ nodes;
   const float4* __restrict__ tris;
   uint32_t n_nodes, n_tris;
+#ifdef FGL_CHECKED
+  uint32_t lim_nodes = 0, lim_tris = 0;  // the scene's node and triangle record counts
+  bool bad_index = false;
+#endif
 
   __device__ __forceinline__ void start(const void* node_ptr, const void* tri_ptr, float min_range,
-                                        float max_range) {
+                                        float max_range, uint32_t node_count, uint32_t tri_count) {
     nodes = (const uint4*)node_ptr;
     tris = (const float4*)tri_ptr;
+#ifdef FGL_CHECKED
+    lim_nodes = node_count;
+    lim_tris = tri_count;
+    bad_index = false;
+#else
+    (void)node_count;
+    (void)tri_count;
+#endif
     tmin_ = TMIN ? min_range : 0.f;
     best_t = max_range;
     best_id = kNoHit;
@@ -363,6 +380,12 @@ struct Tracer {
       const uint32_t code = key & (W - 1);
       key_clear(kq, code);
       const uint32_t child = ng.x + __popc(ng.y & ((1u << code) - 1u) & 0xFFu);
+#ifdef FGL_CHECKED
+      if (child >= lim_nodes) {
+        bad_index = true;
+        return false;
+      }
+#endif
       if (key_any(kq)) {
         if (!push(ng, kq, st)) return false;
       }
@@ -399,6 +422,12 @@ struct Tracer {
       }
       const uint32_t pos = __ffs(tg.y) - 1;
       tg.y &= tg.y - 1;
+#ifdef FGL_CHECKED
+      if ((size_t)tg.x + pos >= lim_tris) {
+        bad_index = true;
+        return false;
+      }
+#endif
       const float4* tp = tris + 3 * ((size_t)tg.x + pos);
       const float4 a = ldg4f(tp), b = ldg4f(tp + 1), c = ldg4f(tp + 2);
       if (COUNT) ++n_tris;
@@ -422,12 +451,22 @@ struct Tracer {
     }
   }
 
+  // Status bits of a ray abandoned by descend() or tri_serial(): 1 for a
+  // stack overflow, 4 for an index out of range (checked library only).
+  __device__ __forceinline__ unsigned fail_bits() const {
+#ifdef FGL_CHECKED
+    return bad_index ? 4u : 1u;
+#else
+    return 1u;
+#endif
+  }
+
   // Lane-serial step (descend + tri_serial + finish).  Returns true when the
   // ray is finished.
   __device__ __forceinline__ bool step(const StackRefs<Keys>& st, int postpone_lanes,
                                        unsigned* status) {
     if (!descend(st) || !tri_serial(st, postpone_lanes)) {
-      atomicOr(status, 1u);
+      atomicOr(status, fail_bits());
       return true;
     }
     return finish(st);
@@ -466,10 +505,11 @@ __device__ __forceinline__ unsigned long long hit_key(float t, int32_t id) {
 // its ray's best (t, id) by a 64-bit atomic minimum on a per-lane
 // shared-memory key -- the same lexicographic minimum as the lane-serial
 // path.  All 32 lanes of the warp must call this together; lanes without a
-// ray simply have no triangles.  `keys` points at the warp's 32 slots.
+// ray simply have no triangles.  `keys` points at the warp's 32 slots;
+// `status` takes bit 4 for a triangle index out of range (checked library).
 template <int W, bool COUNT, bool TMIN>
 __device__ __forceinline__ void tri_phase_warp(Tracer<W, COUNT, TMIN>& tr, unsigned long long* keys,
-                                               int lane) {
+                                               int lane, unsigned* status) {
   const unsigned FULL = 0xFFFFFFFFu;
   const uint32_t bits = tr.tg.y & 0x00FFFFFFu;
   const int cnt = __popc(bits);
@@ -509,9 +549,20 @@ __device__ __forceinline__ void tri_phase_warp(Tracer<W, COUNT, TMIN>& tr, unsig
     q.k = __shfl_sync(FULL, tr.r.k, owner);
     const float o_best = __shfl_sync(FULL, tr.best_t, owner);
     const float o_tmin = TMIN ? __shfl_sync(FULL, tr.tmin_, owner) : 0.f;
+#ifdef FGL_CHECKED
+    const uint32_t o_lim = __shfl_sync(FULL, tr.lim_tris, owner);
+#endif
     if (p < total) {
       const uint32_t k = (uint32_t)(p - (o_incl - o_cnt));
       const uint32_t pos = nth_set_bit(o_bits, k);
+#ifdef FGL_CHECKED
+      if ((size_t)o_base + pos >= o_lim) {
+        atomicOr(status, 4u);
+        continue;
+      }
+#else
+      (void)status;
+#endif
       const float4* tp = (const float4*)(((uint64_t)tp_hi << 32) | tp_lo) + 3 * ((size_t)o_base + pos);
       const float4 a = ldg4f(tp), bb = ldg4f(tp + 1), c = ldg4f(tp + 2);
       if (COUNT) ++tr.n_tris;

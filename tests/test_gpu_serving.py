@@ -144,6 +144,43 @@ def test_serving_budget_rejection_and_faults(world):
     srv.close()
 
 
+def test_serving_contains_worker_exceptions(world):
+    """A host exception in the worker thread (injected between packing a tick
+    and launching it) fails exactly the requests with chunks in that tick,
+    with FGL_ERR_INTERNAL: a request split over several ticks ends once, its
+    later chunks unscheduled; concurrent and later requests complete bitwise
+    equal to casting them alone; the server keeps serving and holds no
+    request's buffers afterwards."""
+    scenes, sensors, obs = world
+    P = synth.sample_free_pose(np.random.default_rng(21), obs[1], 6)
+    n = 6 * sensors[1].n_rays
+    ar, ai = alone(scenes[1], sensors[1], P, 50.0)
+    bufs = [(np.empty(n, np.float32), np.empty(n, np.int32)) for _ in range(12)]
+
+    def exact(k):
+        return np.array_equal(bufs[k][0], ar) and np.array_equal(bufs[k][1], ai)
+
+    for tick_rays in (0, 2 * sensors[1].n_rays):       # one tick a request / three ticks
+        srv = fgl.Server(tick_rays=tick_rays)
+        sid, tid = srv.add_scene(scenes[1]), srv.add_sensor(sensors[1])
+        b = 0 if tick_rays == 0 else 6
+        srv.inject_worker_faults(1)
+        t0 = srv.submit(sid, tid, P, 50.0, *bufs[b])
+        assert srv.wait(t0, 60000, check=False)["status"] == fgl.FGL_ERR_INTERNAL
+        t1 = srv.submit(sid, tid, P, 50.0, *bufs[b + 1])
+        assert srv.wait(t1, 60000, check=False)["status"] == fgl.FGL_OK and exact(b + 1)
+        srv.inject_worker_faults(1)
+        tk = [srv.submit(sid, tid, P, 50.0, *bufs[b + 2 + k]) for k in range(4)]
+        st = [srv.wait(t, 60000, check=False)["status"] for t in tk]
+        assert fgl.FGL_ERR_INTERNAL in st
+        assert all(s == fgl.FGL_ERR_INTERNAL or (s == fgl.FGL_OK and exact(b + 2 + k))
+                   for k, s in enumerate(st))
+        s2 = srv.stats()
+        assert s2["rejected"] == 1 + st.count(fgl.FGL_ERR_INTERNAL) and s2["active"] == 0
+        assert s2["pending"] == 0 and s2["completed"] == 1 + st.count(fgl.FGL_OK)
+        srv.close()
+
+
 def test_autotune_keeps_results_and_caches(world, tmp_path):
     scenes, sensors, obs = world
     P = synth.sample_free_pose(np.random.default_rng(8), obs[1], 64, upright=False)
