@@ -91,30 +91,44 @@ def read_traffic(name: str):
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle sampling during the timed region."""
+    """nvidia-smi clock/throttle sampling during the timed region: the sampler
+    is started and seen writing before the region opens (nvidia-smi takes a
+    while to start), samples every 50 ms with nvidia-smi's own timestamp, and
+    the summary keeps the samples taken between entering and leaving the
+    region (all of them, flagged, if the region was shorter than a sample)."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    TS = "%Y/%m/%d %H:%M:%S.%f"
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
         self.path = None
+        self.t0 = self.t1 = None
 
     def __enter__(self):
+        import datetime
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+                 "-lms", "50", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+            deadline = time.time() + 5.0
+            while time.time() < deadline and self.proc.poll() is None and os.path.getsize(self.path) == 0:
+                time.sleep(0.02)
         except Exception:
             self.proc = None
+        self.t0 = datetime.datetime.now()
         return self
 
     def __exit__(self, *a):
+        import datetime
+        self.t1 = datetime.datetime.now()
         if self.proc:
+            time.sleep(0.06)                       # the sample in flight at the end
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -122,27 +136,29 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
+        import datetime
         if not self.path or not os.path.exists(self.path):
             return None
-        sm, smax, reasons = [], 0.0, set()
+        rows = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
             f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
-                smax = max(smax, float(f[2]))
+                ts = datetime.datetime.strptime(f[0], self.TS)
+                rows.append((ts, float(f[2]), float(f[3]), [n for n, v in zip(names, f[6:10])
+                                                            if v.lower() == "active"]))
             except ValueError:
                 continue
-            for n, v in zip(names, f[5:9]):
-                if v.lower() == "active":
-                    reasons.add(n)
         os.unlink(self.path)
-        if not sm:
+        inside = [r for r in rows if self.t0 and self.t1 and self.t0 <= r[0] <= self.t1]
+        use = inside or rows
+        if not use:
             return None
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return {"sm_mhz": float(np.median([r[1] for r in use])), "sm_max_mhz": max(r[2] for r in use),
+                "reasons": sorted({n for r in use for n in r[3]}), "samples": len(use),
+                "samples_in_timed_region": len(inside), "interval_ms": 50}
 
 
 def dist_setup(n_gpus: int):
