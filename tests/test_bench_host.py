@@ -1,0 +1,48 @@
+"""Host-side logic of bench.py that needs no GPU: the clock sampler's summary
+keeps only the samples taken inside the timed region (nvidia-smi's own
+timestamps), reports the median SM clock, the maximum and every throttle
+reason seen there, and falls back to all samples, flagged, when none fell
+inside."""
+
+import datetime
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def _sampler(tmp_path, rows, t0_ms, t1_ms):
+    c = bench.ClockSampler(0)
+    c.path = str(tmp_path / "clocks.csv")
+    now = datetime.datetime(2026, 1, 2, 3, 4, 5, 0)
+    c.t0 = now + datetime.timedelta(milliseconds=t0_ms)
+    c.t1 = now + datetime.timedelta(milliseconds=t1_ms)
+    lines = []
+    for ms, mhz, reasons in rows:
+        ts = (now + datetime.timedelta(milliseconds=ms)).strftime(bench.ClockSampler.TS)[:-3]
+        flags = ["Active" if r in reasons else "Not Active"
+                 for r in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")]
+        lines.append(", ".join([ts, "0", str(mhz), "2070", "950.25", "0x0"] + flags))
+    lines.append("garbage line")
+    open(c.path, "w").write("\n".join(lines) + "\n")
+    return c
+
+
+def test_clock_summary_keeps_the_timed_region(tmp_path):
+    rows = [(-50, 345, ()), (0, 2070, ()), (50, 2040, ("sw_power_cap",)), (100, 2070, ()),
+            (150, 2055, ()), (200, 600, ("hw_slowdown",))]
+    s = _sampler(tmp_path, rows, 0, 160).summary()
+    assert s["samples"] == 4 and s["samples_in_timed_region"] == 4
+    assert s["sm_mhz"] == 2062.5 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"]                      # the hw_slowdown came after
+    assert not os.path.exists(str(tmp_path / "clocks.csv"))
+
+
+def test_clock_summary_falls_back_to_all_samples(tmp_path):
+    rows = [(-100, 2070, ()), (300, 1980, ("hw_thermal_slowdown",))]
+    s = _sampler(tmp_path, rows, 0, 40).summary()
+    assert s["samples"] == 2 and s["samples_in_timed_region"] == 0
+    assert s["reasons"] == ["hw_thermal_slowdown"] and s["sm_mhz"] == 2025.0
