@@ -1346,7 +1346,9 @@ def run_serve(args):
     rate = 0.7 * sat["rays_per_s"] / mean_rays
     srv.reset_stats()
     cal_trace = make_trace(rng, rate, 3.0, 4096, pool, len(meshes), pick)
-    cal = replay(srv, cal_trace, sids, tids, n_rays_of, arena, 30.0)
+    with ClockSampler(local) as clk:
+        cal = replay(srv, cal_trace, sids, tids, n_rays_of, arena, 30.0)
+    clocks = clk.summary()
     st = srv.stats()
     pre, acc = [], 0
     for tr in cal_trace:
@@ -1371,6 +1373,7 @@ def run_serve(args):
                 "saturation_2000rps": f(sat), "at_70pct": {**f(cal), "rate_req_per_s": round(rate, 2)},
                 "same_prefix": {"batched": f(preb), "per_env_launch": f(prep)},
                 "server": {"evictions": st["evictions"], "uploads": st["uploads"], "ticks": st["ticks"]},
+                "clocks": clocks,
                 "config": {"workload": "serve: Poisson arrivals of 1-4096 env poses (log-uniform) over the "
                                        "8 heterogeneous scenes, 21 sensors, 150 GiB budget, 32 Mi-ray ticks",
                            **info}}
