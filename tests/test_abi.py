@@ -210,3 +210,22 @@ def test_mesh_argument_validation_without_gpu():
                                ctypes.byref(nv), ctypes.byref(nt), None) == E
     assert L.fgl_marching_tets(None, ctypes.byref(good), 0.0, 1, None, 0, None, 0, None,
                                ctypes.byref(nv), ctypes.byref(nt), None) == E
+
+
+def test_checked_library_loads_and_exports_every_declared_symbol():
+    """FGL_CHECKED=1 makes the binding load the bounds-checked build
+    (libfgl_checked.so), which exports the same C ABI.  A child process, since
+    a process loads one of the two libraries."""
+    import subprocess
+    import sys
+    from paper_2509_17390_gb300 import build_native
+    build_native.build(checked=True)
+    code = ("import json, paper_2509_17390_gb300 as f; L = f.lib(); "
+            "import sys; names = json.loads(sys.argv[1]); "
+            "missing = [n for n in names if not hasattr(L, n)]; "
+            "print(L._name); assert not missing, missing")
+    import json
+    r = subprocess.run([sys.executable, "-c", code, json.dumps(declared_functions())], cwd=ROOT,
+                       env=dict(os.environ, FGL_CHECKED="1"), capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.strip().endswith("libfgl_checked.so")
