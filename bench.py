@@ -1287,6 +1287,30 @@ def run_hetero(args):
     e1.synchronize()
     per_env = {"value": round(n_rays / (e0.elapsed_time(e1) / 1e3) / 1e9, 4), "unit": UNIT,
                "launches_per_step": len(envs)}
+    # end to end through the host-buffer entry point: every item's poses from
+    # page-locked host memory in, its ranges and ids out, inside the timing
+    e2e = None
+    if not args.no_e2e:
+        hitems = []
+        for sc, se, P, R, r, i in items:
+            hitems.append((sc, se, P.cpu().pin_memory(), R, torch.empty(r.numel()).pin_memory(),
+                           torch.empty(i.numel(), dtype=torch.int32).pin_memory()))
+        for _ in range(2):
+            fgl.cast_batched_host(hitems, opts, stream=stream)
+        ksteps = max(3, min(args.steps, 10))
+        t_e = 0.0
+        for _ in range(ksteps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fgl.cast_batched_host(hitems, opts, stream=stream)
+            t_e += time.perf_counter() - t0
+        t_e = barrier_max(t_e, ws)
+        same = all(torch.equal(h[4], it[4].cpu()) and torch.equal(h[5], it[5].cpu())
+                   for h, it in zip(hitems, items))
+        e2e = {"value": round(ws * n_rays * ksteps / t_e / 1e9, 4), "unit": UNIT,
+               "h2d_bytes_per_step": sum(it[2].numel() * 4 for it in items),
+               "d2h_bytes_per_step": n_rays * 8, "ms_per_step": round(t_e * 1e3 / ksteps, 3),
+               "results_equal_device_path": bool(same)}
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         import oracle
@@ -1319,7 +1343,7 @@ def run_hetero(args):
                                        "rosette, max range 30 m", "rays_per_step": n_rays,
                            "l2": "flushed between timed steps (256 MiB write)", **info},
                 "gpu_launches": args.steps * len(set(widths.values())), "per_env_launch": per_env,
-                "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary()}
+                "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
 
 
