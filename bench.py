@@ -740,6 +740,45 @@ def run_walk_instances(args):
     clocks = clk.summary()
     tot0 = timed(False)
     seen = float((out_k >= 0).float().mean().item())
+    # end to end through the public API: the step's sensor and instance poses
+    # from page-locked host memory in, ranges, ids, instances and points out
+    e2e = None
+    if not args.no_e2e:
+        hp = torch.empty((n_env, 3, 4), dtype=torch.float32).pin_memory()
+        hip = torch.empty((n_env, K, 3, 4), dtype=torch.float32).pin_memory()
+        hr = torch.empty(n_rays, dtype=torch.float32).pin_memory()
+        hi = torch.empty(n_rays, dtype=torch.int32).pin_memory()
+        hk = torch.empty(n_rays, dtype=torch.int32).pin_memory()
+        hpt = torch.empty((n_rays, 3), dtype=torch.float32).pin_memory()
+
+        def e2e_step(s):
+            hp.copy_(torch.from_numpy(w.poses[s % S]))
+            hip.copy_(torch.from_numpy(IP[s % S]))
+            with torch.cuda.stream(stream):
+                pose_state.copy_(hp, non_blocking=True)
+                ip_state.copy_(hip, non_blocking=True)
+            fgl.cast_batched(items, opts, stream=stream, arr=arr)
+            with torch.cuda.stream(stream):
+                hr.copy_(out_r, non_blocking=True)
+                hi.copy_(out_i, non_blocking=True)
+                hk.copy_(out_k, non_blocking=True)
+                hpt.copy_(out_p, non_blocking=True)
+            stream.synchronize()
+
+        for k in range(2):
+            e2e_step(k)
+        ksteps = max(3, min(args.steps, 10))
+        t_e = 0.0
+        for k in range(ksteps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e2e_step(args.warmup + k)
+            t_e += time.perf_counter() - t0
+        fgl.sync(stream)
+        t_e = barrier_max(t_e, ws)
+        e2e = {"value": round(ws * n_rays * ksteps / t_e / 1e9, 4), "unit": UNIT,
+               "h2d_bytes_per_step": n_env * 48 * (1 + K), "d2h_bytes_per_step": n_rays * 24,
+               "ms_per_step": round(t_e * 1e3 / ksteps, 3)}
     # the dominant kernel is the scene cast (k_persistent): its cost-model
     # bytes from a counting pass, over its own time (the step without instances)
     with torch.cuda.stream(stream):
@@ -759,7 +798,8 @@ def run_walk_instances(args):
                            "returns_on_instances": round(seen, 4),
                            "l2": "flushed between timed steps (256 MiB write)"},
                 "without_instances_ms_per_step": round(tot0 * 1e3 / args.steps, 3),
-                "gpu_launches": args.steps * (1 + K + 1), "roofline": roofline, "clocks": clocks}
+                "gpu_launches": args.steps * 3,   # scene cast, fused instance pass, return points
+                "e2e": e2e, "roofline": roofline, "clocks": clocks}
         print(json.dumps(line), flush=True)
 
 
