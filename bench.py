@@ -740,8 +740,8 @@ def run_walk_instances(args):
     clocks = clk.summary()
     tot0 = timed(False)
     seen = float((out_k >= 0).float().mean().item())
-    # end to end through the public API: the step's sensor and instance poses
-    # from page-locked host memory in, ranges, ids, instances and points out
+    # end to end through the host-buffer entry: the step's sensor and instance
+    # poses from page-locked host memory in, ranges, ids, instances and points out
     e2e = None
     if not args.no_e2e:
         hp = torch.empty((n_env, 3, 4), dtype=torch.float32).pin_memory()
@@ -751,19 +751,13 @@ def run_walk_instances(args):
         hk = torch.empty(n_rays, dtype=torch.int32).pin_memory()
         hpt = torch.empty((n_rays, 3), dtype=torch.float32).pin_memory()
 
-        def e2e_step(s):
+        hitems = [(scene, sensor, hp, w.max_range, hr, hi, 0.0,
+                   {"instances": inst, "instance_poses": hip, "out_instance": hk, "points": hpt})]
+
+        def e2e_step(s):                # fgl_cast_batched_host: chunked, copies overlap the casts
             hp.copy_(torch.from_numpy(w.poses[s % S]))
             hip.copy_(torch.from_numpy(IP[s % S]))
-            with torch.cuda.stream(stream):
-                pose_state.copy_(hp, non_blocking=True)
-                ip_state.copy_(hip, non_blocking=True)
-            fgl.cast_batched(items, opts, stream=stream, arr=arr)
-            with torch.cuda.stream(stream):
-                hr.copy_(out_r, non_blocking=True)
-                hi.copy_(out_i, non_blocking=True)
-                hk.copy_(out_k, non_blocking=True)
-                hpt.copy_(out_p, non_blocking=True)
-            stream.synchronize()
+            fgl.cast_batched_host(hitems, opts, stream=stream)
 
         for k in range(2):
             e2e_step(k)

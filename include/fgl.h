@@ -223,9 +223,12 @@ fgl_status fgl_cast_batched(const fgl_cast_item* items, int32_t n_items,
                             const fgl_batch_opts* opts, fgl_stream stream);
 
 /* End-to-end form of fgl_cast_batched for callers holding HOST buffers:
- * items[i].poses / out_range / out_tri are host pointers (page-locked for
- * full speed).  Copies poses to library-owned device staging, runs the
- * batched kernel, copies results back and synchronizes the stream. */
+ * items[i].poses / out_range / out_tri -- and, when used, instance_poses,
+ * out_instance and out_points -- are host pointers (page-locked for full
+ * speed).  Copies the poses to library-owned device staging, runs the
+ * batched kernels (instances and return points included), copies the results
+ * back and synchronizes the stream.  Large batches run in up to 4 chunks of
+ * whole environments whose copies back overlap the next chunk's cast. */
 fgl_status fgl_cast_batched_host(const fgl_cast_item* items, int32_t n_items,
                                  const fgl_batch_opts* opts, fgl_stream stream);
 

@@ -376,14 +376,29 @@ def autotune(items: Sequence[tuple], start: Optional[BatchOpts] = None, reps: in
 
 def cast_batched_host(items: Sequence[tuple], opts: Optional[BatchOpts] = None, stream=None):
     """End-to-end batched form (fgl_cast_batched_host): poses and outputs are
-    host tensors/arrays (page-locked for full speed); blocks until done."""
+    host tensors/arrays (page-locked for full speed), item tuples as for
+    cast_batched (extras included, all on the host); blocks until done."""
     arr = (CastItem * max(1, len(items)))()
+    keep = []
     for i, item in enumerate(items):
         sc, se, poses, rmax, orng, otri = item[:6]
-        rmin = float(item[6]) if len(item) > 6 else 0.0
+        rmin = float(item[6]) if len(item) > 6 and item[6] is not None else 0.0
+        ex = item[7] if len(item) > 7 and item[7] else {}
         n_env = int(np.prod(poses.shape)) // 12
-        arr[i] = CastItem(sc.handle, se.handle, _host_ptr(poses), n_env, float(rmax),
-                          _host_ptr(orng), _host_ptr(otri), rmin)
+        c = CastItem(sc.handle, se.handle, _host_ptr(poses), n_env, float(rmax),
+                     _host_ptr(orng), _host_ptr(otri), rmin)
+        if ex.get("points") is not None:
+            c.out_points = _host_ptr(ex["points"])
+        insts = ex.get("instances") or []
+        if insts:
+            h = (P * len(insts))(*[x.handle for x in insts])
+            keep.append(h)
+            c.n_instances = len(insts)
+            c.instances = ctypes.cast(h, P)
+            c.instance_poses = _host_ptr(ex["instance_poses"])
+        if ex.get("out_instance") is not None:
+            c.out_instance = _host_ptr(ex["out_instance"])
+        arr[i] = c
     _check(lib().fgl_cast_batched_host(arr, len(items), ctypes.byref(opts) if opts else None,
                                        _stream_handle(stream)))
 

@@ -773,26 +773,32 @@ fgl_status fgl_cast_batched_host(const fgl_cast_item* items, int32_t n_items,
   for (int i = 0; i < n_items; ++i) {
     fgl_status st = check_item(items[i], i);
     if (st != FGL_OK) return st;
-    if (has_extras(items[i]) || items[i].out_instance)
-      return fail(FGL_ERR_INVALID, "item " + std::to_string(i) +
-                                       ": instances and return points need fgl_cast_batched");
   }
   Opts o;
   fgl_status st = resolve_opts(opts, &o);
   if (st != FGL_OK) return st;
   if (n_items == 0) return FGL_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  // device staging: poses then outputs of every item, 256-byte aligned
-  std::vector<size_t> pose_off(n_items), out_off(n_items);
+  // device staging, 256-byte aligned: every item's poses and instance poses,
+  // then its ranges + ids, instance indices and points
+  std::vector<size_t> pose_off(n_items), ipose_off(n_items), out_off(n_items), inst_off(n_items),
+      pts_off(n_items);
   size_t total = 0;
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   for (int i = 0; i < n_items; ++i) {
     pose_off[i] = total;
     total = al(total + (size_t)items[i].n_env * 48);
+    ipose_off[i] = total;
+    if (items[i].n_instances > 0) total = al(total + (size_t)items[i].n_env * items[i].n_instances * 48);
   }
   for (int i = 0; i < n_items; ++i) {
+    const size_t nr = (size_t)items[i].n_env * items[i].sensor->n_rays;
     out_off[i] = total;
-    total = al(total + (size_t)items[i].n_env * items[i].sensor->n_rays * 8);
+    total = al(total + nr * 8);
+    inst_off[i] = total;
+    if (items[i].out_instance) total = al(total + nr * 4);
+    pts_off[i] = total;
+    if (items[i].out_points) total = al(total + nr * 12);
   }
   BatchCtx& c = *get_ctx(s);
   {
@@ -825,7 +831,32 @@ fgl_status fgl_cast_batched_host(const fgl_cast_item* items, int32_t n_items,
     dev[i].poses = dp;
     dev[i].out_range = dr;
     dev[i].out_tri = dt;
+    if (items[i].n_instances > 0) {
+      float* dip = (float*)((char*)c.d_io + ipose_off[i]);
+      if (items[i].n_env)
+        FGL_CUDA(cudaMemcpyAsync(dip, items[i].instance_poses,
+                                 (size_t)items[i].n_env * items[i].n_instances * 48,
+                                 cudaMemcpyHostToDevice, s));
+      dev[i].instance_poses = dip;
+    }
+    if (items[i].out_instance) dev[i].out_instance = (int32_t*)((char*)c.d_io + inst_off[i]);
+    if (items[i].out_points) dev[i].out_points = (float*)((char*)c.d_io + pts_off[i]);
   }
+  // results of items [e0, e1) of item i back to the host on stream `cs`
+  auto copy_back = [&](int i, size_t e0, size_t e1, cudaStream_t cs) -> fgl_status {
+    const size_t per_env = (size_t)items[i].sensor->n_rays;
+    const size_t a = e0 * per_env, nr = (e1 - e0) * per_env;
+    if (!nr) return FGL_OK;
+    FGL_CUDA(cudaMemcpyAsync(items[i].out_range + a, dev[i].out_range + a, nr * 4, cudaMemcpyDeviceToHost, cs));
+    FGL_CUDA(cudaMemcpyAsync(items[i].out_tri + a, dev[i].out_tri + a, nr * 4, cudaMemcpyDeviceToHost, cs));
+    if (items[i].out_instance)
+      FGL_CUDA(cudaMemcpyAsync(items[i].out_instance + a, dev[i].out_instance + a, nr * 4,
+                               cudaMemcpyDeviceToHost, cs));
+    if (items[i].out_points)
+      FGL_CUDA(cudaMemcpyAsync(items[i].out_points + 3 * a, dev[i].out_points + 3 * a, nr * 12,
+                               cudaMemcpyDeviceToHost, cs));
+    return FGL_OK;
+  };
   // Large batches run in up to kHostChunks chunks of whole environments:
   // chunk k's results travel to the host on a second stream while chunk k+1
   // casts, so only the last chunk's copy is exposed; chunk sizes shrink
@@ -839,10 +870,8 @@ fgl_status fgl_cast_batched_host(const fgl_cast_item* items, int32_t n_items,
     st = run_batched(dev.data(), n_items, o, s);
     if (st != FGL_OK) return st;
     for (int i = 0; i < n_items; ++i) {
-      size_t nr = (size_t)items[i].n_env * items[i].sensor->n_rays;
-      if (!nr) continue;
-      FGL_CUDA(cudaMemcpyAsync(items[i].out_range, dev[i].out_range, nr * 4, cudaMemcpyDeviceToHost, s));
-      FGL_CUDA(cudaMemcpyAsync(items[i].out_tri, dev[i].out_tri, nr * 4, cudaMemcpyDeviceToHost, s));
+      st = copy_back(i, 0, (size_t)items[i].n_env, s);
+      if (st != FGL_OK) return st;
     }
     return fgl_sync(stream);
   }
@@ -883,6 +912,9 @@ fgl_status fgl_cast_batched_host(const fgl_cast_item* items, int32_t n_items,
       it.poses = dev[i].poses + (size_t)env * 12;
       it.out_range = dev[i].out_range + (size_t)env * per_env;
       it.out_tri = dev[i].out_tri + (size_t)env * per_env;
+      if (it.n_instances > 0) it.instance_poses = dev[i].instance_poses + (size_t)env * it.n_instances * 12;
+      if (it.out_instance) it.out_instance = dev[i].out_instance + (size_t)env * per_env;
+      if (it.out_points) it.out_points = dev[i].out_points + (size_t)env * per_env * 3;
       sub.push_back(it);
       spans.push_back({i, env, env + take});
       done += (size_t)take * per_env;
@@ -898,12 +930,8 @@ fgl_status fgl_cast_batched_host(const fgl_cast_item* items, int32_t n_items,
     FGL_CUDA(cudaEventRecord(c.chunk_done[k], s));
     FGL_CUDA(cudaStreamWaitEvent(c.copy_stream, c.chunk_done[k], 0));
     for (const Span& sp : spans) {
-      const size_t per_env = (size_t)items[sp.item].sensor->n_rays;
-      const size_t a = (size_t)sp.e0 * per_env, nr = (size_t)(sp.e1 - sp.e0) * per_env;
-      FGL_CUDA(cudaMemcpyAsync(items[sp.item].out_range + a, dev[sp.item].out_range + a, nr * 4,
-                               cudaMemcpyDeviceToHost, c.copy_stream));
-      FGL_CUDA(cudaMemcpyAsync(items[sp.item].out_tri + a, dev[sp.item].out_tri + a, nr * 4,
-                               cudaMemcpyDeviceToHost, c.copy_stream));
+      st = copy_back(sp.item, (size_t)sp.e0, (size_t)sp.e1, c.copy_stream);
+      if (st != FGL_OK) return st;
     }
   }
   FGL_CUDA(cudaEventRecord(c.copies_done, c.copy_stream));

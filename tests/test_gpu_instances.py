@@ -174,3 +174,28 @@ def test_fused_instance_pass_equals_per_instance_passes(min_range):
     for x, y in zip(a, b):
         assert np.array_equal(x, y, equal_nan=True)
     assert (a[2] >= 0).sum() > 300
+
+
+@pytest.mark.parametrize("n_env", [6, 1500])
+def test_host_entry_with_instances_equals_device_entry(n_env):
+    """fgl_cast_batched_host with instances, instance indices and return
+    points in host memory (one launch for 6 environments; 1,500 x 5,760 =
+    8.6 M rays run as overlapped chunks) returns what fgl_cast_batched returns
+    from device memory, bit for bit."""
+    vs, ts, meshes, P, IP = instance_setup(11, n_env, 3)
+    se = fgl.Sensor.from_table(synth.grid_sensor(16, -15, 15, 360))
+    scene = fgl.Scene(vs, ts)
+    inst = [fgl.Scene(v, t, width=8) for v, t in meshes]
+    dev = gpu_cast(scene, se, P, 100.0, inst, IP, min_range=0.2)
+    n = n_env * se.n_rays
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).pin_memory()
+    hr = torch.full((n,), -7.0).pin_memory()
+    hi = torch.full((n,), -7, dtype=torch.int32).pin_memory()
+    hk = torch.full((n,), -7, dtype=torch.int32).pin_memory()
+    hp = torch.full((n, 3), -7.0).pin_memory()
+    fgl.cast_batched_host([(scene, se, pin(P), 100.0, hr, hi, 0.2,
+                            {"instances": inst, "instance_poses": pin(IP), "out_instance": hk,
+                             "points": hp})])
+    for x, y in zip(dev, (hr.numpy(), hi.numpy(), hk.numpy(), hp.numpy())):
+        assert np.array_equal(x, y, equal_nan=True)
+    assert (dev[2] >= 0).sum() > 50
