@@ -114,22 +114,23 @@ def hetero_grid(room, h):
 def hetero_meshes(mesher, seed: int = 4, ladder=None) -> List[MeshSpec]:
     """The heterogeneous workload's meshes: each ladder set's Gaussians on its
     hetero_grid, turned into a mesh by mesher(gs, origin, h, dims) ->
-    (verts f32 [nv, 3], tris i32 [nt, 3]).  Cached per process, mesher and
-    ladder."""
+    (verts f32 [nv, 3], tris i32 [nt, 3]).  Set k of the ladder uses seed
+    seed * 100 + k.  Cached per process, mesher, seed and set, so a prefix of
+    the ladder shares its meshes with the whole ladder."""
     from . import gaussians
     ladder = HETERO_LADDER if ladder is None else ladder
-    key = (getattr(mesher, "__qualname__", repr(mesher)), seed,
-           tuple(map(tuple, [(r, b, s, n, h) for r, b, s, n, h in ladder])))
-    if key not in _HETERO_CACHE:
-        out = []
-        for k, (room, nb, ns, ng, h) in enumerate(ladder):
+    name = getattr(mesher, "__qualname__", repr(mesher))
+    out = []
+    for k, (room, nb, ns, ng, h) in enumerate(ladder):
+        key = (name, seed, k, (tuple(room), nb, ns, ng, h))
+        if key not in _HETERO_CACHE:
             gs, obs = gaussians.gaussian_room(seed * 100 + k, room, ng, nb, ns, with_obstacles=True)
             origin, dims = hetero_grid(room, h)
             v, t = mesher(gs, origin, h, dims)
-            out.append(MeshSpec(np.ascontiguousarray(v, np.float32), np.ascontiguousarray(t, np.int32),
-                                obs, h, ng, {"dims": dims}))
-        _HETERO_CACHE[key] = out
-    return _HETERO_CACHE[key]
+            _HETERO_CACHE[key] = MeshSpec(np.ascontiguousarray(v, np.float32),
+                                          np.ascontiguousarray(t, np.int32), obs, h, ng, {"dims": dims})
+        out.append(_HETERO_CACHE[key])
+    return out
 
 
 def hetero_sensors(seed: int = 4):

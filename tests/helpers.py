@@ -33,3 +33,9 @@ def parity_report(osc: "oracle.Scene", o, d, max_range, gpu_range, gpu_id, min_r
 def assert_parity(rep):
     assert rep["bad"] == 0, rep
     assert rep["invalid_flagged"] == 0, rep
+
+
+def oracle_mesher(gs, origin, h, dims):
+    """The 3DGS-to-mesh steps of the oracle (density, denoise, TSDF, marching
+    tetrahedra) as a mesher for synth.workloads.hetero_meshes."""
+    return oracle.mesh_from_gaussians(gs.mu, gs.scale, gs.quat, gs.alpha, origin, h, dims)

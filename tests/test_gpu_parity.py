@@ -14,7 +14,7 @@ import pytest
 import oracle
 import synth
 from synth import workloads
-from tests.helpers import assert_parity, parity_report
+from tests.helpers import assert_parity, oracle_mesher, parity_report
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -67,6 +67,7 @@ def run_batched(items_np, opts=None, stream=None):
         i = torch.full((n,), -7, dtype=torch.int32, device="cuda")
         items.append((sc, se, poses, R, r, i) + tuple(it[4:]))
         outs.append((r, i))
+    torch.cuda.synchronize()            # the fills above ran on the current stream
     fgl.cast_batched(items, opts, stream=stream)
     fgl.sync(stream)
     return [(r.cpu().numpy(), i.cpu().numpy()) for r, i in outs]
@@ -299,6 +300,7 @@ def test_batched_walk_full_size_sampled(indoor_oracle):
     i = torch.full((n,), -3, dtype=torch.int32, device="cuda")
     stream = torch.cuda.Stream()
     opts = fgl.BatchOpts(use_graph=1)
+    torch.cuda.synchronize()            # the fills above ran on the current stream
     for _ in range(2):
         fgl.cast_batched([(scene, sensor, poses, w.max_range, r, i)], opts, stream=stream)
     fgl.sync(stream)
@@ -318,38 +320,56 @@ def test_batched_walk_full_size_sampled(indoor_oracle):
 
 
 # ---------------------------------------------------------------------------
-# heterogeneous batch: meshes from the oracle's 3DGS-to-mesh steps (an oracle
-# input never comes from the CUDA path), mixed sensors, one launch
+# heterogeneous batch at its stated size: all 8 ladder meshes (86k - 5.05M
+# triangles) from the oracle's 3DGS-to-mesh steps (an oracle input never comes
+# from the CUDA path), the 256 environments and full sensor mix of the bench,
+# one graph-captured launch per BVH width
 # ---------------------------------------------------------------------------
-def oracle_mesher(gs, origin, h, dims):
-    return oracle.mesh_from_gaussians(gs.mu, gs.scale, gs.quat, gs.alpha, origin, h, dims)
+def hetero_sample(rng, n_env, n_rays, whole_max=65536, env_rays=16384, extra=2000):
+    """Indices into a group's rays (env-major): its first environment whole
+    (or env_rays random rays of it when it has more than whole_max), plus
+    `extra` random rays of the group's other environments."""
+    first = np.arange(n_rays) if n_rays <= whole_max else rng.choice(n_rays, env_rays, replace=False)
+    rest = np.empty(0, np.int64)
+    if n_env > 1:
+        rest = n_rays + rng.choice((n_env - 1) * n_rays, min(extra, (n_env - 1) * n_rays), replace=False)
+    return np.unique(np.concatenate([first, rest]))
 
 
-def test_hetero_batch_vs_oracle():
-    ladder = workloads.HETERO_LADDER[:4]
-    meshes = workloads.hetero_meshes(oracle_mesher, 4, ladder)
+def test_hetero_batch_full_ladder_vs_oracle():
+    meshes = workloads.hetero_meshes(oracle_mesher, 4)
+    assert len(meshes) == 8 and len(meshes[-1].tris) > 4_000_000
     tables = workloads.hetero_sensors(4)
-    envs = workloads.hetero_envs(4, meshes, n_env=48)
+    envs = workloads.hetero_envs(4, meshes, n_env=256)
     scenes = [fgl.Scene(m.verts, m.tris, width=8 if k % 2 == 0 else 4) for k, m in enumerate(meshes)]
     groups = {}
     for m, s, P in envs:
         groups.setdefault((m, s), []).append(P)
     sensors = {s: fgl.Sensor.from_table(tables[s]) for (_, s) in groups}
+    assert len({s for (_, s) in groups}) == len(tables)          # every sensor of the mix is cast
     items, keys = [], []
     for (m, s), Ps in sorted(groups.items()):
         P = np.stack(Ps)
         items.append((scenes[m], sensors[s], P, 30.0))
         keys.append((m, s, P))
-    outs = run_batched(items, fgl.BatchOpts(packet_rays=128))
+    stream = torch.cuda.Stream()
+    outs = run_batched(items, fgl.BatchOpts(use_graph=1), stream=stream)
     rng = np.random.default_rng(3)
-    for (m, s, P), (gr, gi) in zip(keys, outs):
-        tab = tables[s]
-        o, d = oracle.world_rays(oracle.sensor_dirs(tab.elev, tab.azim), P)
-        idx = rng.choice(len(o), min(len(o), 4000), replace=False)
+    checked = np.zeros(len(meshes), np.int64)
+    for m in range(len(meshes)):
         osc = oracle.Scene(meshes[m].verts, meshes[m].tris, bvh=True)
-        rep = parity_report(osc, o[idx], d[idx], 30.0, gr[idx], gi[idx])
-        assert_parity(rep)
-        assert np.all(gi >= -1)
+        for (mk, s, P), (gr, gi) in zip(keys, outs):
+            if mk != m:
+                continue
+            assert np.all(gi >= -1) and np.all(gr <= np.float32(30.0))
+            tab = tables[s]
+            idx = hetero_sample(rng, P.shape[0], tab.n_rays)
+            o, d = oracle.world_rays(oracle.sensor_dirs(tab.elev, tab.azim), P)
+            rep = parity_report(osc, o[idx], d[idx], 30.0, gr[idx], gi[idx])
+            assert_parity(rep)
+            checked[m] += len(idx)
+        del osc
+    assert checked.min() >= 20000, checked
 
 
 # ---------------------------------------------------------------------------
