@@ -232,10 +232,10 @@ fgl_status fgl_cast_batched(const fgl_cast_item* items, int32_t n_items,
 fgl_status fgl_cast_batched_host(const fgl_cast_item* items, int32_t n_items,
                                  const fgl_batch_opts* opts, fgl_stream stream);
 
-/* fgl_cast_batched for callers that cannot allocate device memory (code
- * running during CUDA graph capture, real-time loops that must not trigger an
- * allocator's device synchronisation, processes whose device memory belongs to
- * a pool they do not own).  The paper has no counterpart: this is an
+/* fgl_cast_batched for callers that cannot allocate device memory (real-time
+ * loops that must not trigger an allocator's device synchronisation, plugins
+ * inside an application that owns every device allocation, processes whose
+ * device memory belongs to a pool they do not own).  The paper has no counterpart: this is an
  * interface for such callers, not part of the method.
  *   Same arguments, layouts and results as fgl_cast_batched (use_graph is
  *   ignored); the caller still owns poses and outputs.  The work-queue scratch
@@ -244,7 +244,8 @@ fgl_status fgl_cast_batched_host(const fgl_cast_item* items, int32_t n_items,
  *   device, and nothing on the host when it succeeds.
  *   Limit: at most 256 items per call; more is rejected with FGL_ERR_INVALID.
  *   The first call on each device looks up the array's device address (with
- *   that device current); make that first call before any stream capture.
+ *   that device current); make that first call before any stream capture
+ *   begins.
  *   All calls share the array and reset its queue head: calls whose work
  *   overlaps on the GPU race, so issue them on one stream or order them. */
 fgl_status fgl_cast_batched_static(const fgl_cast_item* items, int32_t n_items,
@@ -280,8 +281,17 @@ fgl_status fgl_autotune(const fgl_cast_item* items, int32_t n_items, const fgl_t
 fgl_status fgl_sync(fgl_stream stream);
 
 /* Totals accumulated by count_work launches since the last call (then reset):
- * rays traced, wide-node visits, triangle tests. */
+ * rays traced, wide-node visits, triangle tests (the N_nodes and K of the
+ * paper's per-ray cost, eq. cost(r_j)). */
 fgl_status fgl_work_counters(uint64_t* rays, uint64_t* node_visits, uint64_t* tri_tests);
+/* The same counters plus the phases of the batched kernel, for attributing
+ * its work (no counterpart in the paper), written to out[0..n-1] (n <= 8)
+ * and then reset: [0] rays, [1] node visits, [2] triangle tests, [3] warp
+ * iterations of the persistent kernel's main loop, [4] active lanes summed
+ * over those iterations, [5] pooled leaf-test rounds (32 tests each at
+ * most), [6] stack entries popped after the leaf tests, [7] ray packets
+ * drawn by warps. */
+fgl_status fgl_work_phase_counters(uint64_t* out, int32_t n);
 
 /* Debug export of the float32 world rays the kernels trace (eq. r_j):
  * out_o, out_d device float32 [n_env * n_rays][3]. */
@@ -493,37 +503,67 @@ fgl_status fgl_marching_tets(const float* phi, const fgl_grid* grid, float iso, 
 /* ------------------------------------------------------------------------ */
 /* The paper batches thousands of environments on one GPU (Sec. IV-C; Table
  * I) but describes no request serving; this layer schedules the same casts.
- * Requests (scene, sensor, n_env host poses, host output buffers) arrive at
- * any time.  A worker admits them in arrival order while their device memory
- * (poses + results) plus any scene that must be uploaded fits the HBM budget,
+ * Requests (scene, sensor, n_env environment poses, host output buffers)
+ * arrive at any time.  The poses are either carried by the request or kept
+ * on the device in the server's environment slots across requests (see
+ * fgl_pose_source).  A worker admits requests in arrival order while their
+ * device memory (own poses + results) plus any scene that must be uploaded
+ * fits the HBM budget,
  * evicting least-recently-used idle scenes (the scene keeps its host copy, so
  * re-admission is an upload).  Every tick packs up to tick_rays rays from all
  * admitted requests into one batched launch, so large requests advance over
  * several ticks and requests that arrive meanwhile join the next tick.
- * Results are copied to the caller's host buffers before the request
- * completes; latency is submission -> results in host memory.  mode 1 serves
+ * The result copies of the requests a tick finishes are queued right behind
+ * it; a request completes once its results are in the caller's host buffers,
+ * and its latency is submission -> results in host memory.  mode 1 serves
  * the same requests the plain way (one fgl_cast per environment, one request
  * at a time) for comparison. */
 typedef struct fgl_server_s* fgl_server;
 
 typedef struct {
   int64_t hbm_budget_bytes;  /* device bytes for resident scenes + admitted
-                                requests (0 = 150 GiB) */
+                                requests + the environment slot table (0 = 150 GiB) */
   int64_t tick_rays;         /* rays per tick (0 = 16 Mi) */
   int32_t max_active;        /* admitted requests at once (0 = 4096) */
   int32_t mode;              /* 0 = continuous batching, 1 = one launch per env */
   fgl_batch_opts opts;       /* launch options of a tick (use_graph ignored) */
+  int32_t env_capacity;      /* resident environment slots (0 = 65536; at most 2^24):
+                                48 B of device memory each, held from creation */
 } fgl_server_opts;
+
+/* Where a request's environment poses come from.  The server keeps a table
+ * of environment slots whose poses live on the device across requests
+ * (fgl_server_add_envs); a request either carries its own poses or names a
+ * range of slots [env_first, env_first + n_env).  Slot updates are applied
+ * when the request is admitted, in admission order; a request that updates
+ * slots is admitted only once no admitted request uses any of them, and a
+ * request that only scans slots waits for admitted requests updating them --
+ * so each request scans exactly the poses the requests submitted before it
+ * left there. */
+typedef enum {
+  FGL_POSES_REQUEST = 0,          /* poses: host [n_env][3][4], copied at submit, used by
+                                     this request only (env_first ignored) */
+  FGL_POSES_SLOTS = 1,            /* scan the slots' current poses (poses may be NULL):
+                                     no pose bytes move */
+  FGL_POSES_SLOTS_SET_HOST = 2,   /* overwrite the slots with host poses (copied at
+                                     submit), then scan them */
+  FGL_POSES_SLOTS_SET_DEVICE = 3  /* overwrite the slots with device poses (copied on the
+                                     device at admission; keep them unchanged until the
+                                     request completes), then scan them */
+} fgl_pose_source;
 
 typedef struct {
   int32_t scene_id;          /* from fgl_server_add_scene */
   int32_t sensor_id;         /* from fgl_server_add_sensor */
   int32_t n_env;             /* >= 1 */
   float max_range;
-  const float* poses;        /* host float32 [n_env][3][4]; copied by submit */
-  float* out_range;          /* host float32 [n_env * n_rays]; page-locked is fastest */
+  const float* poses;        /* float32 [n_env][3][4], host or device per pose_source */
+  float* out_range;          /* host float32 [n_env * n_rays]; page-locked is fastest
+                                (pageable buffers are staged through page-locked memory) */
   int32_t* out_tri;          /* host int32  [n_env * n_rays] */
   float min_range;           /* t_min, as in fgl_cast_item (0 = none) */
+  int32_t pose_source;       /* fgl_pose_source (0 = the request's own host poses) */
+  int32_t env_first;         /* first environment slot (pose_source >= FGL_POSES_SLOTS) */
 } fgl_request;
 
 typedef struct {
@@ -545,15 +585,29 @@ typedef struct {
 } fgl_server_stats;
 
 /* Create a server on the current device (worker + completion threads, two
- * streams).  Errors: FGL_ERR_INVALID (mode), FGL_ERR_CUDA. */
+ * streams, the environment slot table).  Errors: FGL_ERR_INVALID (mode,
+ * env_capacity), FGL_ERR_BUDGET (slot table larger than the budget),
+ * FGL_ERR_OOM, FGL_ERR_CUDA. */
 fgl_status fgl_server_create(const fgl_server_opts* opts, fgl_server* out);
+/* Register n_env environment slots holding the given initial poses (host
+ * float32 [n_env][3][4], copied synchronously); their ids are
+ * [*env_first, *env_first + n_env).  Slots live until fgl_server_destroy.
+ * Errors: FGL_ERR_INVALID (null, n_env < 1, non-finite pose),
+ * FGL_ERR_CAPACITY (more slots than env_capacity), FGL_ERR_CUDA. */
+fgl_status fgl_server_add_envs(fgl_server server, int32_t n_env, const float* poses,
+                               int32_t* env_first);
+/* Copy the poses of slots [env_first, env_first + n_env) to host memory
+ * (float32 [n_env][3][4]) as every request admitted so far left them; waits
+ * for those updates.  Errors: FGL_ERR_INVALID (range), FGL_ERR_CUDA. */
+fgl_status fgl_server_read_poses(fgl_server server, int32_t env_first, int32_t n_env, float* out);
 /* Register a scene / sensor (the caller keeps ownership and must keep them
  * alive until fgl_server_destroy; the server uploads / evicts scenes). */
 fgl_status fgl_server_add_scene(fgl_server server, fgl_scene scene, int32_t* scene_id);
 fgl_status fgl_server_add_sensor(fgl_server server, fgl_sensor sensor, int32_t* sensor_id);
 /* Queue a request.  Errors (synchronous): FGL_ERR_INVALID for unknown ids,
- * n_env < 1, null buffers, non-finite poses or max_range; FGL_ERR_BUDGET when
- * the request and its scene exceed the whole budget. */
+ * n_env < 1, a slot range outside the registered environments, null buffers,
+ * non-finite host poses or max_range; FGL_ERR_BUDGET when the request and its
+ * scene exceed the whole budget. */
 fgl_status fgl_server_submit(fgl_server server, const fgl_request* req, int64_t* ticket);
 /* Wait for a request (timeout_ms < 0: forever); on return the ticket is
  * released.  Returns the request's status (FGL_ERR_TIMEOUT if still running,

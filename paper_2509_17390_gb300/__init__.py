@@ -106,6 +106,8 @@ def lib():
                 "fgl_server_add_scene": ([P, P, P], I32),
                 "fgl_server_add_sensor": ([P, P, P], I32),
                 "fgl_server_submit": ([P, P, P], I32),
+                "fgl_server_add_envs": ([P, I32, P, P], I32),
+                "fgl_server_read_poses": ([P, I32, I32, P], I32),
                 "fgl_server_wait": ([P, I64, I32, P], I32),
                 "fgl_server_cancel": ([P, I64], I32),
                 "fgl_server_get_stats": ([P, P], I32),
@@ -115,6 +117,7 @@ def lib():
                 "fgl_server_destroy": ([P], I32),
                 "fgl_sync": ([P], I32),
                 "fgl_work_counters": ([P, P, P], I32),
+                "fgl_work_phase_counters": ([P, I32], I32),
                 "fgl_world_rays": ([P, P, I32, P, P, P], I32),
                 "fgl_gaussian_density": ([P, P, F32, P, P, P, P, P], I32),
                 "fgl_lbvh_build": ([P, I64, P, I64, P, P], I32),
@@ -674,17 +677,33 @@ def work_counters():
     return int(r.value), int(n.value), int(t.value)
 
 
+PHASE_COUNTERS = ("rays", "node_visits", "tri_tests", "warp_iterations", "active_lane_iterations",
+                  "tri_rounds", "finish_pops", "packets")
+
+
+def work_phase_counters() -> dict:
+    """Every count_work counter (fgl_work_phase_counters), then reset."""
+    out = (ctypes.c_uint64 * len(PHASE_COUNTERS))()
+    _check(lib().fgl_work_phase_counters(out, len(PHASE_COUNTERS)))
+    return {k: int(v) for k, v in zip(PHASE_COUNTERS, out)}
+
+
 # ---------------------------------------------------------------------------
 # serving (fgl_server_*)
 # ---------------------------------------------------------------------------
 class ServerOpts(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", I64), ("tick_rays", I64), ("max_active", I32),
-                ("mode", I32), ("opts", BatchOpts)]
+                ("mode", I32), ("opts", BatchOpts), ("env_capacity", I32)]
+
+
+# fgl_pose_source
+POSES_REQUEST, POSES_SLOTS, POSES_SLOTS_SET_HOST, POSES_SLOTS_SET_DEVICE = 0, 1, 2, 3
 
 
 class Request(ctypes.Structure):
     _fields_ = [("scene_id", I32), ("sensor_id", I32), ("n_env", I32), ("max_range", F32),
-                ("poses", P), ("out_range", P), ("out_tri", P), ("min_range", F32)]
+                ("poses", P), ("out_range", P), ("out_tri", P), ("min_range", F32),
+                ("pose_source", I32), ("env_first", I32)]
 
 
 class RequestInfo(ctypes.Structure):
@@ -703,8 +722,9 @@ class Server:
     registered with it must stay alive until close()."""
 
     def __init__(self, hbm_budget_bytes: int = 0, tick_rays: int = 0, max_active: int = 0,
-                 mode: int = 0, opts: Optional[BatchOpts] = None):
-        o = ServerOpts(hbm_budget_bytes, tick_rays, max_active, mode, opts or BatchOpts())
+                 mode: int = 0, opts: Optional[BatchOpts] = None, env_capacity: int = 0):
+        o = ServerOpts(hbm_budget_bytes, tick_rays, max_active, mode, opts or BatchOpts(),
+                       env_capacity)
         h = P()
         _check(lib().fgl_server_create(ctypes.byref(o), ctypes.byref(h)))
         self._h = h
@@ -722,12 +742,44 @@ class Server:
         self._keep.append(sensor)
         return i.value
 
+    def add_envs(self, poses) -> int:
+        """Register environment slots holding `poses` (host float32
+        [n_env, 3, 4]); returns the first slot id (fgl_server_add_envs)."""
+        P_ = np.ascontiguousarray(poses, np.float32)
+        first = I32()
+        _check(lib().fgl_server_add_envs(self._h, P_.size // 12, P_.ctypes.data_as(P),
+                                         ctypes.byref(first)))
+        return first.value
+
+    def read_poses(self, env_first: int, n_env: int) -> np.ndarray:
+        """The slots' current poses as the admitted requests left them."""
+        out = np.empty((n_env, 3, 4), np.float32)
+        _check(lib().fgl_server_read_poses(self._h, env_first, n_env, out.ctypes.data_as(P)))
+        return out
+
     def submit(self, scene_id: int, sensor_id: int, poses, max_range: float, out_range, out_tri,
-               min_range: float = 0.0) -> int:
-        """poses: host float32 [n_env,3,4]; outputs: host arrays/tensors."""
-        n_env = int(np.prod(poses.shape)) // 12
-        r = Request(scene_id, sensor_id, n_env, float(max_range), _host_ptr(poses),
-                    _host_ptr(out_range), _host_ptr(out_tri), float(min_range))
+               min_range: float = 0.0, env_first: Optional[int] = None, n_env: Optional[int] = None) -> int:
+        """Without env_first: poses are host float32 [n_env,3,4] carried by the
+        request.  With env_first: the request scans resident slots
+        [env_first, env_first + n_env); poses None scans them as they are, a
+        host array or a CUDA tensor overwrites them first.  Outputs: host
+        arrays/tensors."""
+        if env_first is None:
+            src, first = POSES_REQUEST, 0
+            n_env = int(np.prod(poses.shape)) // 12
+            ptr = _host_ptr(poses)
+        else:
+            first = int(env_first)
+            if poses is None:
+                src, ptr = POSES_SLOTS, None
+                assert n_env is not None, "n_env is needed when no poses are given"
+            else:
+                n_env = int(np.prod(poses.shape)) // 12
+                dev = getattr(poses, "is_cuda", False)
+                src = POSES_SLOTS_SET_DEVICE if dev else POSES_SLOTS_SET_HOST
+                ptr = _dev_ptr(poses, "float32", n_env * 12, "poses") if dev else _host_ptr(poses)
+        r = Request(scene_id, sensor_id, int(n_env), float(max_range), ptr,
+                    _host_ptr(out_range), _host_ptr(out_tri), float(min_range), src, first)
         t = I64()
         _check(lib().fgl_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
         return t.value

@@ -8,13 +8,23 @@
 // caller's host buffers; per-request latency is measured from submission to
 // results-in-host-memory.
 //
+// Per-environment pose state stays on the device: the server owns a table of
+// environment slots (48-byte poses, created by fgl_server_add_envs), and a
+// request may scan a range of slots as they are, or first overwrite them from
+// host or device memory.  Updates happen in admission order on the compute
+// stream; a request that writes slots is admitted only once no admitted
+// request uses them, and one that reads slots waits for admitted writers of
+// them, so every request scans the poses that the requests before it left.
+//
 // The paper runs batched environments on one GPU (Sec. IV-C, last paragraph
 // of "GPU-accelerated ray-casting"; Table I) but describes no request
 // serving; this layer only schedules the same casts.
 //
-// Threads: a worker admits requests and launches ticks on the compute stream;
-// a completion thread waits for the ticks in order, copies finished
-// requests' results to the host (copy stream) and wakes waiters.  Faults are
+// Threads: a worker admits requests, launches ticks on the compute stream and
+// right behind each tick enqueues the result copies of the requests it
+// finishes on the copy stream (after the tick's event), one copy per output
+// array; a completion thread waits for one event per tick (its copies done),
+// moves results staged for pageable caller buffers, and wakes waiters.  Faults are
 // reported per request; nothing here waits on the GPU without a host-side
 // timeout on the caller's side (fgl_server_wait takes one).
 #include <cuda_runtime.h>
@@ -97,27 +107,40 @@ struct PinnedPool {
   }
 };
 
+// Results of at most this many bytes bound for pageable caller memory are
+// staged in page-locked memory (larger ones are copied synchronously by the
+// completion thread).
+constexpr int64_t kStageMax = (int64_t)256 << 20;
+
 struct Request {
   int64_t ticket = 0;
   fgl_request r{};
-  float* poses = nullptr;      // page-locked host copy taken at submit
+  float* poses = nullptr;      // page-locked host copy of host poses taken at submit
   size_t poses_cls = 0;
+  void* stage = nullptr;       // page-locked result staging for pageable outputs
+  size_t stage_cls = 0;
+  bool pageable = false;       // an output buffer is pageable host memory
   int32_t n_rays = 0;
   int64_t bytes = 0;           // device bytes while active
   ReqState state = PENDING;
   int status = FGL_OK;
   bool cancel = false;
   Clock::time_point t_submit, t_admit, t_done;
-  float* d_poses = nullptr;    // device
+  void* d_buf = nullptr;       // device allocation: [poses |] ranges | ids
+  const float* d_poses = nullptr;  // poses the casts read (own buffer or the slot table)
   float* d_range = nullptr;
   int32_t* d_tri = nullptr;
   int32_t env_next = 0;        // next environment to schedule
   int64_t last_tick = -1;      // last tick that holds one of its chunks
+  bool slots = false;          // scans resident environment slots
+  bool writes = false;         // overwrites them first
+  bool copy_queued = false;    // its result copies are enqueued
 };
 
 struct Tick {
   int64_t id = 0;
-  cudaEvent_t done = nullptr;
+  cudaEvent_t done = nullptr;    // compute stream: the tick's casts
+  cudaEvent_t copied = nullptr;  // copy stream: after `done` and the result copies
   std::vector<int64_t> finishing;  // tickets whose last chunk is in this tick
 };
 
@@ -145,6 +168,12 @@ struct fgl_server_s {
   int inject_worker_fault = 0;
   PinnedPool pinned;
 
+  // resident environment slots: poses on the device, per-slot use counts
+  float* d_env = nullptr;           // [env_capacity][12]
+  int32_t n_envs = 0;
+  std::vector<int32_t> env_readers;  // admitted requests using the slot
+  std::vector<uint8_t> env_writer;   // an admitted request overwrote it
+
   // stats
   int64_t submitted = 0, completed = 0, rejected = 0, cancelled = 0, evictions = 0, uploads = 0,
           n_ticks = 0, rays_done = 0;
@@ -162,9 +191,13 @@ fgl_status set_err(int status, const std::string& m) {
   return (fgl_status)status;
 }
 
-int64_t request_bytes(int32_t n_env, int32_t n_rays) {
-  return (int64_t)n_env * 48 + (int64_t)n_env * n_rays * 8;
+// Device bytes a request holds while admitted: its poses (unless it scans
+// resident slots) and its results.
+int64_t request_bytes(int32_t n_env, int32_t n_rays, bool slots) {
+  return (slots ? 0 : (int64_t)n_env * 48) + (int64_t)n_env * n_rays * 8;
 }
+
+bool uses_slots(int32_t src) { return src >= FGL_POSES_SLOTS && src <= FGL_POSES_SLOTS_SET_DEVICE; }
 
 // Make room for `need` bytes by evicting idle resident scenes (least recently
 // used first), never the scene `keep`.  Caller holds the lock.
@@ -211,15 +244,35 @@ void detach_request(fgl_server_s& S, Request& q) {
 // Free an admitted request's device buffers and its share of the budget.
 // Caller holds the lock; the request is already detached.
 void free_request(fgl_server_s& S, Request& q) {
-  if (q.d_poses) {
-    cudaFreeAsync(q.d_poses, S.copy);
+  if (q.d_buf) {
+    cudaFreeAsync(q.d_buf, S.copy);
+    q.d_buf = nullptr;
     q.d_poses = nullptr;
     q.d_range = nullptr;
     q.d_tri = nullptr;
   }
+  if (q.slots) {
+    for (int32_t e = q.r.env_first; e < q.r.env_first + q.r.n_env; ++e) {
+      S.env_readers[e] -= 1;
+      if (q.writes) S.env_writer[e] = 0;
+    }
+    q.slots = false;
+  }
   S.used_bytes -= q.bytes;
   q.bytes = 0;
   S.scenes[q.r.scene_id].active -= 1;
+}
+
+// May `q` be admitted now as far as its environment slots go?  A writer
+// needs slots no admitted request uses; a reader needs slots no admitted
+// request overwrote.  Caller holds the lock.
+bool slots_free(const fgl_server_s& S, const Request& q) {
+  const bool writes = q.r.pose_source != FGL_POSES_SLOTS;
+  for (int32_t e = q.r.env_first; e < q.r.env_first + q.r.n_env; ++e) {
+    if (S.env_writer[e]) return false;
+    if (writes && S.env_readers[e] > 0) return false;
+  }
+  return true;
 }
 
 // Admit pending requests in arrival order while memory and slots allow.
@@ -232,6 +285,8 @@ void admit(fgl_server_s& S) {
       finish_request(S, q, FGL_ERR_CANCELLED);
       continue;
     }
+    const bool slots = uses_slots(q.r.pose_source);
+    if (slots && !slots_free(S, q)) break;  // FIFO: wait for the slots' earlier users
     SceneEntry& se = S.scenes[q.r.scene_id];
     const int64_t need = q.bytes + (se.resident ? 0 : se.bytes);
     if (!make_room(S, need, q.r.scene_id)) break;  // wait for memory to free up
@@ -245,7 +300,7 @@ void admit(fgl_server_s& S) {
       S.used_bytes += se.bytes;
       ++S.uploads;
     }
-    // device buffers: poses | ranges | ids (stream-ordered allocation)
+    // device buffers: [poses |] ranges | ids (stream-ordered allocation)
     void* base = nullptr;
     cudaError_t e = cudaErrorMemoryAllocation;
     if (S.inject_alloc_fail > 0) {
@@ -260,10 +315,28 @@ void admit(fgl_server_s& S) {
       continue;
     }
     S.pending.pop_front();
-    q.d_poses = (float*)base;
-    q.d_range = q.d_poses + (size_t)q.r.n_env * 12;
-    q.d_tri = (int32_t*)(q.d_range + (size_t)q.r.n_env * q.n_rays);
-    cudaMemcpyAsync(q.d_poses, q.poses, (size_t)q.r.n_env * 48, cudaMemcpyHostToDevice, S.compute);
+    q.d_buf = base;
+    const size_t n_env = (size_t)q.r.n_env;
+    float* own_poses = slots ? nullptr : (float*)base;
+    q.d_range = (float*)base + (slots ? 0 : n_env * 12);
+    q.d_tri = (int32_t*)(q.d_range + n_env * q.n_rays);
+    if (!slots) {
+      q.d_poses = own_poses;
+      cudaMemcpyAsync(own_poses, q.poses, n_env * 48, cudaMemcpyHostToDevice, S.compute);
+    } else {
+      float* slot = S.d_env + (size_t)q.r.env_first * 12;
+      q.d_poses = slot;
+      if (q.r.pose_source == FGL_POSES_SLOTS_SET_HOST)
+        cudaMemcpyAsync(slot, q.poses, n_env * 48, cudaMemcpyHostToDevice, S.compute);
+      else if (q.r.pose_source == FGL_POSES_SLOTS_SET_DEVICE)
+        cudaMemcpyAsync(slot, q.r.poses, n_env * 48, cudaMemcpyDeviceToDevice, S.compute);
+      q.slots = true;
+      q.writes = q.r.pose_source != FGL_POSES_SLOTS;
+      for (int32_t k = q.r.env_first; k < q.r.env_first + q.r.n_env; ++k) {
+        S.env_readers[k] += 1;
+        if (q.writes) S.env_writer[k] = 1;
+      }
+    }
     S.used_bytes += q.bytes;
     se.active += 1;
     se.last_use = ++S.lru_clock;
@@ -271,6 +344,25 @@ void admit(fgl_server_s& S) {
     q.t_admit = Clock::now();
     S.active.push_back(q.ticket);
   }
+}
+
+// Enqueue the device-to-host copies of a finished request's results on the
+// copy stream (which already waits for the tick): straight into the caller's
+// buffers when they are page-locked, else into the request's page-locked
+// staging.  Large results bound for pageable memory are left to the
+// completion thread.  Returns false when a copy could not be enqueued.
+bool enqueue_result_copies(fgl_server_s& S, Request& q) {
+  const size_t nr = (size_t)q.r.n_env * q.n_rays;
+  if (q.pageable && !q.stage) return true;  // copied synchronously on completion
+  float* dr = q.pageable ? (float*)q.stage : q.r.out_range;
+  int32_t* dt = q.pageable ? (int32_t*)((float*)q.stage + nr) : q.r.out_tri;
+  if (cudaMemcpyAsync(dr, q.d_range, nr * 4, cudaMemcpyDeviceToHost, S.copy) != cudaSuccess ||
+      cudaMemcpyAsync(dt, q.d_tri, nr * 4, cudaMemcpyDeviceToHost, S.copy) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  q.copy_queued = true;
+  return true;
 }
 
 void worker_main(fgl_server_s* Sp) {
@@ -393,10 +485,20 @@ void worker_main(fgl_server_s* Sp) {
       }
     }
     cudaEventCreateWithFlags(&t.done, cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&t.copied, cudaEventDisableTiming);
     cudaEventRecord(t.done, S.compute);
-    if (status != FGL_OK) {
-      for (int64_t tk : t.finishing) S.reqs[tk]->status = status;
+    // the copy stream follows the tick; the results of the requests it
+    // finishes go back right behind it, with no host round trip in between
+    cudaStreamWaitEvent(S.copy, t.done, 0);
+    for (int64_t tk : t.finishing) {
+      Request& q = *S.reqs[tk];
+      if (status != FGL_OK) {
+        q.status = status;
+      } else if (q.status == FGL_OK && !q.cancel && !enqueue_result_copies(S, q)) {
+        q.status = FGL_ERR_CUDA;
+      }
     }
+    cudaEventRecord(t.copied, S.copy);
     S.ticks.push_back(std::move(t));
     S.cv_work.notify_all();
   }
@@ -410,17 +512,19 @@ void completer_main(fgl_server_s* Sp) {
     S.cv_work.wait(lk, [&] { return S.stop || !S.ticks.empty(); });
     if (S.ticks.empty() && S.stop) break;
     if (S.ticks.empty()) continue;
-    cudaEvent_t ev = S.ticks.front().done;
+    // one wait per tick: its casts and the result copies queued behind them
+    cudaEvent_t ev = S.ticks.front().copied;
     lk.unlock();
     cudaError_t e = cudaEventSynchronize(ev);
     lk.lock();
     Tick t = std::move(S.ticks.front());
     S.ticks.pop_front();
     cudaEventDestroy(t.done);
+    cudaEventDestroy(t.copied);
     S.cv_tick.notify_all();
     S.cv_done.notify_all();
-    // results of requests that finished in this tick go back to the host;
-    // detach them first so the worker cannot cancel or free them meanwhile
+    // detach the requests that finished in this tick first, so the worker
+    // cannot cancel or free them meanwhile
     std::vector<Request*> fin;
     for (int64_t tk : t.finishing) {
       Request* q = S.reqs[tk].get();
@@ -430,14 +534,20 @@ void completer_main(fgl_server_s* Sp) {
     lk.unlock();
     for (Request* q : fin) {
       int st = (e == cudaSuccess) ? q->status : FGL_ERR_CUDA;
-      if (st == FGL_OK && !q->cancel) {
-        const size_t nr = (size_t)q->r.n_env * q->n_rays;
-        cudaError_t c1 = cudaMemcpyAsync(q->r.out_range, q->d_range, nr * 4, cudaMemcpyDeviceToHost, S.copy);
-        cudaError_t c2 = cudaMemcpyAsync(q->r.out_tri, q->d_tri, nr * 4, cudaMemcpyDeviceToHost, S.copy);
-        cudaError_t c3 = cudaStreamSynchronize(S.copy);
-        if (c1 != cudaSuccess || c2 != cudaSuccess || c3 != cudaSuccess) st = FGL_ERR_CUDA;
-      } else if (q->cancel) {
+      if (q->cancel) {
         st = FGL_ERR_CANCELLED;
+      } else if (st == FGL_OK) {
+        const size_t nr = (size_t)q->r.n_env * q->n_rays;
+        if (q->copy_queued && q->pageable) {
+          std::memcpy(q->r.out_range, q->stage, nr * 4);
+          std::memcpy(q->r.out_tri, (const float*)q->stage + nr, nr * 4);
+        } else if (!q->copy_queued) {  // large results for pageable memory
+          if (cudaMemcpy(q->r.out_range, q->d_range, nr * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+              cudaMemcpy(q->r.out_tri, q->d_tri, nr * 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            cudaGetLastError();
+            st = FGL_ERR_CUDA;
+          }
+        }
       }
       q->status = st;
     }
@@ -472,11 +582,26 @@ fgl_status fgl_server_create(const fgl_server_opts* opts, fgl_server* out) {
   if (S->o.tick_rays <= 0) S->o.tick_rays = (int64_t)16 << 20;
   if (S->o.max_active <= 0) S->o.max_active = 4096;
   if (S->o.mode != 0 && S->o.mode != 1) return set_err(FGL_ERR_INVALID, "mode must be 0 or 1");
+  if (S->o.env_capacity < 0 || S->o.env_capacity > (1 << 24))
+    return set_err(FGL_ERR_INVALID, "env_capacity must be in [0, 2^24]");
+  if (S->o.env_capacity == 0) S->o.env_capacity = 65536;
   S->o.opts.use_graph = 0;
   if (cudaGetDevice(&S->device) != cudaSuccess) return set_err(FGL_ERR_CUDA, "no CUDA device");
+  const int64_t env_bytes = (int64_t)S->o.env_capacity * 48;
+  if (env_bytes >= S->o.hbm_budget_bytes)
+    return set_err(FGL_ERR_BUDGET, "the environment slot table does not fit the budget");
+  if (cudaMalloc(&S->d_env, (size_t)env_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(FGL_ERR_OOM, "cannot allocate the environment slot table");
+  }
+  S->used_bytes = env_bytes;
+  S->env_readers.assign(S->o.env_capacity, 0);
+  S->env_writer.assign(S->o.env_capacity, 0);
   if (cudaStreamCreateWithFlags(&S->compute, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&S->copy, cudaStreamNonBlocking) != cudaSuccess)
+      cudaStreamCreateWithFlags(&S->copy, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaFree(S->d_env);
     return set_err(FGL_ERR_CUDA, "cannot create streams");
+  }
   fgl_server_s* raw = S.release();
   raw->worker = std::thread(worker_main, raw);
   raw->completer = std::thread(completer_main, raw);
@@ -519,6 +644,59 @@ fgl_status fgl_server_add_sensor(fgl_server S, fgl_sensor sensor, int32_t* senso
   return FGL_OK;
 }
 
+fgl_status fgl_server_add_envs(fgl_server S, int32_t n_env, const float* poses, int32_t* env_first) {
+  if (!S || !poses || !env_first) return set_err(FGL_ERR_INVALID, "null argument");
+  if (n_env < 1) return set_err(FGL_ERR_INVALID, "n_env must be >= 1");
+  for (int64_t i = 0; i < 12 * (int64_t)n_env; ++i)
+    if (!std::isfinite(poses[i])) return set_err(FGL_ERR_INVALID, "non-finite pose");
+  std::lock_guard<std::mutex> lk(S->mu);
+  if ((int64_t)S->n_envs + n_env > S->o.env_capacity)
+    return set_err(FGL_ERR_CAPACITY, "environment slots exhausted (raise env_capacity)");
+  const int32_t first = S->n_envs;
+  // New slots: no admitted request can name them yet, so a synchronous copy
+  // (on no stream of the server's) finishes before any later request reads them.
+  cudaError_t e = cudaMemcpy(S->d_env + (size_t)first * 12, poses, (size_t)n_env * 48,
+                             cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(FGL_ERR_CUDA, std::string("uploading environment poses: ") + cudaGetErrorString(e));
+  }
+  S->n_envs += n_env;
+  *env_first = first;
+  return FGL_OK;
+}
+
+fgl_status fgl_server_read_poses(fgl_server S, int32_t env_first, int32_t n_env, float* out) {
+  if (!S || !out) return set_err(FGL_ERR_INVALID, "null argument");
+  size_t cls = 0;
+  void* stage = nullptr;
+  cudaEvent_t ev = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (n_env < 1 || env_first < 0 || (int64_t)env_first + n_env > S->n_envs)
+      return set_err(FGL_ERR_INVALID, "slot range outside the registered environments");
+    stage = S->pinned.get((size_t)n_env * 48, &cls);
+    if (!stage) return set_err(FGL_ERR_OOM, "cannot allocate page-locked staging");
+    // behind every update of the requests admitted so far
+    if (cudaMemcpyAsync(stage, S->d_env + (size_t)env_first * 12, (size_t)n_env * 48,
+                        cudaMemcpyDeviceToHost, S->compute) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(ev, S->compute) != cudaSuccess) {
+      cudaGetLastError();
+      if (ev) cudaEventDestroy(ev);
+      S->pinned.put(stage, cls);
+      return set_err(FGL_ERR_CUDA, "reading environment poses");
+    }
+  }
+  cudaError_t e = cudaEventSynchronize(ev);
+  cudaEventDestroy(ev);
+  if (e == cudaSuccess) std::memcpy(out, stage, (size_t)n_env * 48);
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->pinned.put(stage, cls);
+  if (e != cudaSuccess) return set_err(FGL_ERR_CUDA, cudaGetErrorString(e));
+  return FGL_OK;
+}
+
 fgl_status fgl_server_submit(fgl_server S, const fgl_request* r, int64_t* ticket) {
   if (!S || !r || !ticket) return set_err(FGL_ERR_INVALID, "null argument");
   std::unique_ptr<Request> q(new Request());
@@ -532,23 +710,53 @@ fgl_status fgl_server_submit(fgl_server S, const fgl_request* r, int64_t* ticket
       return set_err(FGL_ERR_INVALID, "unknown sensor id");
     q->n_rays = S->sensors[r->sensor_id].n_rays;
     if (r->n_env < 1) return set_err(FGL_ERR_INVALID, "n_env must be >= 1");
-    if (!r->poses || !r->out_range || !r->out_tri) return set_err(FGL_ERR_INVALID, "null buffer");
+    if (r->pose_source < FGL_POSES_REQUEST || r->pose_source > FGL_POSES_SLOTS_SET_DEVICE)
+      return set_err(FGL_ERR_INVALID, "unknown pose_source");
+    if (uses_slots(r->pose_source) &&
+        (r->env_first < 0 || (int64_t)r->env_first + r->n_env > S->n_envs))
+      return set_err(FGL_ERR_INVALID, "slot range outside the registered environments");
+    const bool needs_poses = r->pose_source != FGL_POSES_SLOTS;
+    if ((needs_poses && !r->poses) || !r->out_range || !r->out_tri)
+      return set_err(FGL_ERR_INVALID, "null buffer");
     if (!(std::isfinite(r->max_range) && r->max_range > 0.f))
       return set_err(FGL_ERR_INVALID, "max_range must be finite and > 0");
     if (!(r->min_range >= 0.f && r->min_range < r->max_range))
       return set_err(FGL_ERR_INVALID, "min_range must satisfy 0 <= min_range < max_range");
-    q->bytes = request_bytes(r->n_env, q->n_rays);
-    if (q->bytes + S->scenes[r->scene_id].bytes > S->o.hbm_budget_bytes) {
+    q->bytes = request_bytes(r->n_env, q->n_rays, uses_slots(r->pose_source));
+    if (q->bytes + S->scenes[r->scene_id].bytes + (int64_t)S->o.env_capacity * 48 >
+        S->o.hbm_budget_bytes) {
       ++S->rejected;
       return set_err(FGL_ERR_BUDGET, "request needs more device memory than the whole budget");
     }
   }
-  for (int64_t i = 0; i < 12 * (int64_t)r->n_env; ++i)
-    if (!std::isfinite(r->poses[i])) return set_err(FGL_ERR_INVALID, "non-finite pose");
+  const bool host_poses = r->pose_source == FGL_POSES_REQUEST || r->pose_source == FGL_POSES_SLOTS_SET_HOST;
+  if (host_poses) {
+    for (int64_t i = 0; i < 12 * (int64_t)r->n_env; ++i)
+      if (!std::isfinite(r->poses[i])) return set_err(FGL_ERR_INVALID, "non-finite pose");
+  }
+  // pageable output buffers get page-locked staging, so the copies behind a
+  // tick never wait on the host
+  bool pageable = false;
+  for (const void* p : {(const void*)r->out_range, (const void*)r->out_tri}) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+      cudaGetLastError();
+      pageable = true;
+    } else if (a.type != cudaMemoryTypeHost) {
+      pageable = true;
+    }
+  }
+  const size_t res_bytes = (size_t)r->n_env * q->n_rays * 8;
   std::lock_guard<std::mutex> lk(S->mu);
-  q->poses = (float*)S->pinned.get((size_t)r->n_env * 48, &q->poses_cls);
-  if (!q->poses) return set_err(FGL_ERR_OOM, "cannot allocate page-locked pose staging");
-  std::memcpy(q->poses, r->poses, (size_t)r->n_env * 48);
+  if (host_poses) {
+    q->poses = (float*)S->pinned.get((size_t)r->n_env * 48, &q->poses_cls);
+    if (!q->poses) return set_err(FGL_ERR_OOM, "cannot allocate page-locked pose staging");
+    std::memcpy(q->poses, r->poses, (size_t)r->n_env * 48);
+  }
+  q->pageable = pageable;
+  if (pageable && (int64_t)res_bytes <= kStageMax) {
+    q->stage = S->pinned.get(res_bytes, &q->stage_cls);  // NULL: copied synchronously instead
+  }
   q->ticket = S->next_ticket++;
   *ticket = q->ticket;
   if (!S->have_first) {
@@ -583,6 +791,8 @@ fgl_status fgl_server_wait(fgl_server S, int64_t ticket, int32_t timeout_ms, fgl
   int st = q.status;
   S->pinned.put(q.poses, q.poses_cls);
   q.poses = nullptr;
+  S->pinned.put(q.stage, q.stage_cls);
+  q.stage = nullptr;
   S->reqs.erase(it);
   if (st != FGL_OK) {
     return set_err(st, st == FGL_ERR_CANCELLED ? "request cancelled"
@@ -668,11 +878,14 @@ fgl_status fgl_server_destroy(fgl_server S) {
   cudaStreamSynchronize(S->copy);
   for (auto& kv : S->reqs) {
     Request& q = *kv.second;
-    if (q.d_poses) cudaFree(q.d_poses);
+    if (q.d_buf) cudaFree(q.d_buf);
   }
   for (SceneEntry& e : S->scenes) e.active = 0;
-  for (auto& kv : S->reqs)
+  for (auto& kv : S->reqs) {
     if (kv.second->poses) cudaFreeHost(kv.second->poses);
+    if (kv.second->stage) cudaFreeHost(kv.second->stage);
+  }
+  cudaFree(S->d_env);
   S->pinned.release_all();
   cudaStreamDestroy(S->compute);
   cudaStreamDestroy(S->copy);

@@ -13,8 +13,10 @@ import os
 import numpy as np
 import pytest
 
+import oracle
 import synth
 from synth import workloads
+from tests.helpers import assert_parity, oracle_mesher, parity_report
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -35,10 +37,17 @@ def world():
     return scenes, sensors, obs
 
 
-def alone(scene, sensor, P, R):
+def alone(scene, sensor, P, R, min_range=0.0):
     scene.upload()          # a server may have evicted it (no-op when resident)
     poses = torch.from_numpy(np.ascontiguousarray(P, np.float32)).cuda()
-    r, i = fgl.cast(scene, sensor, poses, R)
+    if min_range == 0.0:
+        r, i = fgl.cast(scene, sensor, poses, R)
+    else:
+        n = P.shape[0] * sensor.n_rays
+        r = torch.empty(n, dtype=torch.float32, device="cuda")
+        i = torch.empty(n, dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+        fgl.cast_batched([(scene, sensor, poses, R, r, i, min_range)])
     fgl.sync()
     return r.cpu().numpy(), i.cpu().numpy()
 
@@ -179,6 +188,150 @@ def test_serving_contains_worker_exceptions(world):
         assert s2["rejected"] == 1 + st.count(fgl.FGL_ERR_INTERNAL) and s2["active"] == 0
         assert s2["pending"] == 0 and s2["completed"] == 1 + st.count(fgl.FGL_OK)
         srv.close()
+
+
+def test_serving_env_slots_keep_poses_on_device(world):
+    """Per-environment pose state resident on the device: requests scan slot
+    ranges as they are, overwrite them from host or from device memory first,
+    or carry their own poses, all submitted at once.  Each result equals,
+    bitwise, casting alone the poses its slots held at its turn in
+    submission order (earlier requests' updates applied, later ones not), and
+    the slots read back as the last update left them."""
+    scenes, sensors, obs = world
+    rng = np.random.default_rng(31)
+    srv = fgl.Server(tick_rays=150_000, env_capacity=100)
+    sid = [srv.add_scene(s) for s in scenes]
+    tid = [srv.add_sensor(s) for s in sensors]
+    P0 = synth.sample_free_pose(rng, obs[1], 40, upright=False)
+    first = srv.add_envs(P0)
+    assert first == 0 and np.array_equal(srv.read_poses(0, 40), P0)
+    Pa = synth.sample_free_pose(rng, obs[1], 20)
+    Pb = synth.sample_free_pose(rng, obs[1], 20, upright=False)
+    Pb_dev = torch.from_numpy(Pb).cuda()
+    Q = synth.sample_free_pose(rng, obs[1], 7)
+    state = P0.copy()
+    # (scene, sensor, slot range or None, update (None / host / device), own poses, min_range)
+    plan = [(1, 0, (0, 40), None, None, 0.0),
+            (1, 1, (0, 20), "host", Pa, 0.0),
+            (2, 0, (0, 40), None, None, 0.0),
+            (1, 2, (10, 30), "device", Pb, 0.0),
+            (1, 0, (5, 35), None, None, 0.5),
+            (2, 1, None, None, Q, 0.0),
+            (1, 0, (0, 40), None, None, 0.0),
+            (2, 2, (30, 40), "host", Pa[:10], 0.0)]
+    tickets, outs, expect = [], [], []
+    for k, (si, ti, rg, upd, P, rmin) in enumerate(plan):
+        if rg is None:
+            used = P
+        else:
+            a, b = rg
+            if upd is not None:
+                state[a:b] = P
+            used = state[a:b].copy()
+        n = used.shape[0] * sensors[ti].n_rays
+        if k % 2:
+            r, i = np.empty(n, np.float32), np.empty(n, np.int32)             # pageable
+        else:
+            r = torch.empty(n, dtype=torch.float32).pin_memory()
+            i = torch.empty(n, dtype=torch.int32).pin_memory()
+        if rg is None:
+            t = srv.submit(sid[si], tid[ti], P, 50.0, r, i, min_range=rmin)
+        elif upd is None:
+            t = srv.submit(sid[si], tid[ti], None, 50.0, r, i, min_range=rmin, env_first=rg[0],
+                           n_env=rg[1] - rg[0])
+        else:
+            t = srv.submit(sid[si], tid[ti], Pb_dev if upd == "device" else P, 50.0, r, i,
+                           min_range=rmin, env_first=rg[0])
+        tickets.append(t)
+        outs.append((r, i))
+        expect.append((si, ti, used, rmin))
+    for t in tickets:
+        srv.wait(t, timeout_ms=120000)
+    for (si, ti, used, rmin), (r, i) in zip(expect, outs):
+        ar, ai = alone(scenes[si], sensors[ti], used, 50.0, rmin)
+        assert np.array_equal(ar, np.asarray(r)) and np.array_equal(ai, np.asarray(i))
+    assert np.array_equal(srv.read_poses(0, 40), state)
+    # slot ranges are checked at submission, capacity at registration
+    ro, io = np.empty(sensors[0].n_rays, np.float32), np.empty(sensors[0].n_rays, np.int32)
+    with pytest.raises(fgl.FglError) as e:
+        srv.submit(sid[0], tid[0], None, 10.0, ro, io, env_first=40, n_env=1)
+    assert e.value.status == fgl.FGL_ERR_INVALID
+    assert srv.add_envs(np.concatenate([P0, P0[:20]])) == 40      # fills the 100 slots
+    with pytest.raises(fgl.FglError) as e:
+        srv.add_envs(P0[:1])
+    assert e.value.status == fgl.FGL_ERR_CAPACITY
+    assert srv.stats()["active"] == 0
+    srv.close()
+
+
+def test_serving_hetero_mix_vs_oracle():
+    """The served workload's scene and sensor mix -- the 8 heterogeneous
+    meshes (86k - 5.05M triangles, from the oracle's own 3DGS-to-mesh steps),
+    the 21 sensors, a minimum range on some requests, poses carried by the
+    request or kept in resident slots and updated from host or device memory
+    -- submitted at once under continuous batching.  Every request equals its
+    cast alone bitwise and, on a sample of its rays, the FP64 oracle."""
+    meshes = workloads.hetero_meshes(oracle_mesher, 4)
+    tables = workloads.hetero_sensors(4)
+    scenes = [fgl.Scene(m.verts, m.tris, width=8 if k % 2 == 0 else 4) for k, m in enumerate(meshes)]
+    sensors = [fgl.Sensor.from_table(t) for t in tables]
+    rng = np.random.default_rng(51)
+    srv = fgl.Server(tick_rays=2 << 20, env_capacity=8 * 32)
+    sid = [srv.add_scene(s) for s in scenes]
+    tid = [srv.add_sensor(s) for s in sensors]
+    pools = [synth.sample_free_pose(rng, m.obstacles, 32, margin=0.25) for m in meshes]
+    firsts = [srv.add_envs(P) for P in pools]
+    state = [P.copy() for P in pools]
+    tickets, keep, expect = [], [], []
+    for k in range(40):
+        m = int(rng.integers(len(meshes)))
+        ti = int(rng.integers(len(tables)))
+        n_env = max(1, int(np.exp(rng.uniform(0, np.log(12)))))
+        if sensors[ti].n_rays > 100_000:
+            n_env = min(n_env, 3)
+        rmin = 0.3 if k % 3 == 0 else 0.0
+        src = int(rng.integers(4))
+        n = n_env * sensors[ti].n_rays
+        if k % 2:
+            r, i = np.empty(n, np.float32), np.empty(n, np.int32)
+        else:
+            r = torch.empty(n, dtype=torch.float32).pin_memory()
+            i = torch.empty(n, dtype=torch.int32).pin_memory()
+        a = int(rng.integers(0, 32 - n_env + 1))
+        if src == 0:
+            used = synth.sample_free_pose(rng, meshes[m].obstacles, n_env, margin=0.25)
+            t = srv.submit(sid[m], tid[ti], used, 30.0, r, i, min_range=rmin)
+        elif src == 1:
+            used = state[m][a:a + n_env].copy()
+            t = srv.submit(sid[m], tid[ti], None, 30.0, r, i, min_range=rmin,
+                           env_first=firsts[m] + a, n_env=n_env)
+        else:
+            used = synth.sample_free_pose(rng, meshes[m].obstacles, n_env, margin=0.25)
+            state[m][a:a + n_env] = used
+            src_p = torch.from_numpy(used).cuda() if src == 3 else used
+            t = srv.submit(sid[m], tid[ti], src_p, 30.0, r, i, min_range=rmin,
+                           env_first=firsts[m] + a)
+            keep.append(src_p)                     # a device update must outlive the request
+        tickets.append(t)
+        expect.append((m, ti, used, rmin, r, i))
+    infos = [srv.wait(t, timeout_ms=300000) for t in tickets]
+    assert srv.stats()["completed"] == 40
+    assert all(x["status"] == fgl.FGL_OK for x in infos)
+    osc = {}
+    for m, ti, used, rmin, r, i in expect:
+        gr, gi = np.asarray(r), np.asarray(i)
+        ar, ai = alone(scenes[m], sensors[ti], used, 30.0, rmin)
+        assert np.array_equal(ar, gr) and np.array_equal(ai, gi)
+        if m not in osc:
+            osc[m] = oracle.Scene(meshes[m].verts, meshes[m].tris, bvh=True)
+        tab = tables[ti]
+        o, d = oracle.world_rays(oracle.sensor_dirs(tab.elev, tab.azim), used)
+        idx = rng.choice(len(o), min(len(o), 3000), replace=False)
+        rep = parity_report(osc[m], o[idx], d[idx], 30.0, gr[idx], gi[idx], min_range=rmin)
+        assert_parity(rep)
+    for m in range(len(meshes)):
+        assert np.array_equal(srv.read_poses(firsts[m], 32), state[m])
+    srv.close()
 
 
 def test_autotune_keeps_results_and_caches(world, tmp_path):
