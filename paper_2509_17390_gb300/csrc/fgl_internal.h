@@ -71,6 +71,8 @@ constexpr int kTriFloats = 12;
 // most two entries per level of the wide tree, so the builder rejects trees
 // deeper than kMaxWideDepth.
 constexpr int kStackLocal = 64;
+// Work counters of count_work launches (see g_counters in kernels.cu).
+constexpr int kWorkCounters = 8;
 constexpr int kMaxWideDepth = 30;
 
 struct HostBVH {

@@ -17,21 +17,22 @@
 namespace fgl {
 
 __device__ unsigned int g_status;  // bit 0: stack overflow; bit 1: item of another width
-__device__ unsigned long long g_counters[3];  // rays, node visits, triangle tests
+// count_work counters: rays, node visits, triangle tests, then the batched
+// kernel's phases -- warp iterations of its main loop, active lanes summed
+// over those iterations, pooled leaf-test rounds, stack entries popped by
+// finish(), and refill passes (one per new ray packet a warp draws from)
+__device__ unsigned long long g_counters[kWorkCounters];
 
 namespace {
 
 template <bool COUNT>
-__device__ __forceinline__ void flush_counters(uint32_t rays, uint32_t nodes, uint32_t tris) {
+__device__ __forceinline__ void flush_counters(const uint32_t (&c)[kWorkCounters]) {
   if (!COUNT) return;
   const unsigned full = __activemask();
-  unsigned long long r = __reduce_add_sync(full, rays);
-  unsigned long long n = __reduce_add_sync(full, nodes);
-  unsigned long long t = __reduce_add_sync(full, tris);
-  if ((threadIdx.x & 31) == (__ffs(full) - 1)) {
-    atomicAdd(&g_counters[0], r);
-    atomicAdd(&g_counters[1], n);
-    atomicAdd(&g_counters[2], t);
+#pragma unroll
+  for (int k = 0; k < kWorkCounters; ++k) {
+    const unsigned long long v = __reduce_add_sync(full, c[k]);
+    if ((threadIdx.x & 31) == (__ffs(full) - 1) && v) atomicAdd(&g_counters[k], v);
   }
 }
 
@@ -80,7 +81,7 @@ __global__ void __maxnreg__(72) k_plain(const ItemDesc it, int sdepth, int tri_m
   dev::Tracer<W, COUNT> tr;
   tr.tg = make_uint2(0u, 0u);
   tr.ng = make_uint2(0u, 0u);
-  if (COUNT) tr.n_nodes = tr.n_tris = 0;
+  if (COUNT) tr.n_nodes = tr.n_tris = tr.n_rounds = tr.n_pops = 0;
   if (!done) {
     env = (int)(gid / it.n_rays);
     const int j = (int)(gid - (int64_t)env * it.n_rays);
@@ -118,10 +119,14 @@ __global__ void __maxnreg__(72) k_plain(const ItemDesc it, int sdepth, int tri_m
     int32_t id;
     tr.result(rg, id);
     const int64_t o = (int64_t)env * it.n_rays + __float_as_int(ds.w);
-    it.out_range[o] = rg;
-    it.out_tri[o] = id;
+    __stcs(it.out_range + o, rg);  // results are read by the host, not again here:
+    __stcs(it.out_tri + o, id);     // evict-first, so they do not push the BVH out of L2
   }
-  if (COUNT) flush_counters<COUNT>(gid < total ? 1u : 0u, tr.n_nodes, tr.n_tris);
+  if (COUNT) {
+    const uint32_t c[kWorkCounters] = {gid < total ? 1u : 0u, tr.n_nodes, tr.n_tris, 0u, 0u,
+                                       tr.n_rounds, tr.n_pops, 0u};
+    flush_counters<COUNT>(c);
+  }
 }
 
 template <int W, bool COUNT, bool TMIN>
@@ -146,11 +151,11 @@ __global__ void __maxnreg__(72) k_persistent(BatchHeader* __restrict__ hdr,
   dev::Tracer<W, COUNT, TMIN> tr;
   tr.tg = make_uint2(0u, 0u);
   tr.ng = make_uint2(0u, 0u);
-  if (COUNT) tr.n_nodes = tr.n_tris = 0;
+  if (COUNT) tr.n_nodes = tr.n_tris = tr.n_rounds = tr.n_pops = 0;
   bool active = false;
   float* out_r = nullptr;
   int32_t* out_t = nullptr;
-  uint32_t c_rays = 0, c_nodes = 0, c_tris = 0;
+  uint32_t c_rays = 0, c_nodes = 0, c_tris = 0, c_iters = 0, c_lane_iters = 0, c_refills = 0;
 
   for (;;) {
     unsigned idle = __ballot_sync(FULL, !active);
@@ -177,6 +182,7 @@ __global__ void __maxnreg__(72) k_persistent(BatchHeader* __restrict__ hdr,
           const int chunk = (int)(local - (int64_t)pk_env * ppe);
           pk_next = chunk * P;
           pk_end = min(pk_next + P, items[lo].n_rays);
+          if (COUNT && lane == 0) ++c_refills;
         }
         if (items[pk_item].width != W) {  // never read nodes laid out for another width
           if (lane == 0) atomicOr(&g_status, 2u);
@@ -194,6 +200,7 @@ __global__ void __maxnreg__(72) k_persistent(BatchHeader* __restrict__ hdr,
           if (COUNT) {
             c_nodes += tr.n_nodes;
             c_tris += tr.n_tris;
+            tr.n_nodes = tr.n_tris = 0;
           }
           tr.start(it.nodes, it.tris, it.min_range, it.max_range, it.n_nodes, it.n_tris);
           const int64_t o = (int64_t)pk_env * it.n_rays + __float_as_int(ds.w);
@@ -211,6 +218,10 @@ __global__ void __maxnreg__(72) k_persistent(BatchHeader* __restrict__ hdr,
       continue;
     }
     bool fin = false;
+    if (COUNT) {
+      c_iters += lane == 0 ? 1u : 0u;
+      c_lane_iters += active ? 1u : 0u;
+    }
     if (tri_mode != 1) {
       bool ok = true;
       if (active) ok = tr.descend(st);
@@ -231,13 +242,17 @@ __global__ void __maxnreg__(72) k_persistent(BatchHeader* __restrict__ hdr,
       float rg;
       int32_t id;
       tr.result(rg, id);
-      *out_r = rg;
-      *out_t = id;
+      __stcs(out_r, rg);  // evict-first: keep L2 for the BVH
+      __stcs(out_t, id);
       active = false;
       if (COUNT) ++c_rays;
     }
   }
-  if (COUNT) flush_counters<COUNT>(c_rays, c_nodes + tr.n_nodes, c_tris + tr.n_tris);
+  if (COUNT) {
+    const uint32_t c[kWorkCounters] = {c_rays, c_nodes + tr.n_nodes, c_tris + tr.n_tris, c_iters,
+                                       c_lane_iters, tr.n_rounds, tr.n_pops, c_refills};
+    flush_counters<COUNT>(c);
+  }
 }
 
 // Second pass over one item for instance k: every ray, moved into the
@@ -412,9 +427,9 @@ __global__ void __maxnreg__(72) k_instances_fused(const InstanceSet a, int sdept
     }
   }
   if (live) {
-    b.out_range[o_idx] = cur_t;
-    b.out_tri[o_idx] = cur_id;
-    if (b.out_inst) b.out_inst[o_idx] = cur_k;
+    __stcs(b.out_range + o_idx, cur_t);
+    __stcs(b.out_tri + o_idx, cur_id);
+    if (b.out_inst) __stcs(b.out_inst + o_idx, cur_k);
   }
 }
 
@@ -434,9 +449,9 @@ __global__ void k_points(const float4* __restrict__ dirs, const float* __restric
   const float t = range[o];
   const bool hit = tri[o] >= 0;
   const float nan = __int_as_float(0x7FC00000);
-  out[3 * o + 0] = hit ? __fadd_rn(ox, __fmul_rn(t, dx)) : nan;
-  out[3 * o + 1] = hit ? __fadd_rn(oy, __fmul_rn(t, dy)) : nan;
-  out[3 * o + 2] = hit ? __fadd_rn(oz, __fmul_rn(t, dz)) : nan;
+  __stcs(out + 3 * o + 0, hit ? __fadd_rn(ox, __fmul_rn(t, dx)) : nan);
+  __stcs(out + 3 * o + 1, hit ? __fadd_rn(oy, __fmul_rn(t, dy)) : nan);
+  __stcs(out + 3 * o + 2, hit ? __fadd_rn(oz, __fmul_rn(t, dz)) : nan);
 }
 
 __global__ void k_world_rays(const float4* __restrict__ dirs, const float* __restrict__ poses,
@@ -590,10 +605,10 @@ cudaError_t read_and_clear_status(unsigned* st) {
   return e;
 }
 
-cudaError_t read_and_clear_counters(unsigned long long* c3) {
-  cudaError_t e = cudaMemcpyFromSymbol(c3, g_counters, 3 * sizeof(unsigned long long));
+cudaError_t read_and_clear_counters(unsigned long long* c) {
+  cudaError_t e = cudaMemcpyFromSymbol(c, g_counters, kWorkCounters * sizeof(unsigned long long));
   if (e != cudaSuccess) return e;
-  unsigned long long z[3] = {0, 0, 0};
+  unsigned long long z[kWorkCounters] = {};
   return cudaMemcpyToSymbol(g_counters, z, sizeof(z));
 }
 

@@ -50,6 +50,6 @@ cudaError_t launch_world_rays(const void* dirs, const float* poses, int n_env, i
 
 // Device-side error word (bit 0: traversal stack overflow) and work counters.
 cudaError_t read_and_clear_status(unsigned* st);
-cudaError_t read_and_clear_counters(unsigned long long* c3);
+cudaError_t read_and_clear_counters(unsigned long long* c);  // kWorkCounters values
 
 }  // namespace fgl

@@ -400,8 +400,8 @@ __global__ void k_lbvh_cast(const LbvhCast a, unsigned* status) {
   int32_t id;
   tr.result(rg, id);
   const int64_t o = (int64_t)env * a.n_rays + __float_as_int(ds.w);
-  a.out_range[o] = rg;
-  a.out_tri[o] = id;
+  __stcs(a.out_range + o, rg);  // evict-first: keep L2 for the tree
+  __stcs(a.out_tri + o, id);
 }
 
 fgl_status err(int status, const std::string& msg) {

@@ -308,7 +308,8 @@ struct Tracer {
   int sp;
   const uint4* __restrict__ nodes;
   const float4* __restrict__ tris;
-  uint32_t n_nodes, n_tris;
+  uint32_t n_nodes, n_tris;  // count_work: this ray's node visits and triangle tests
+  uint32_t n_rounds, n_pops;  // count_work: this lane's pooled rounds (lane 0) and finish() pops
 #ifdef FGL_CHECKED
   uint32_t lim_nodes = 0, lim_tris = 0;  // the scene's node and triangle record counts
   bool bad_index = false;
@@ -446,6 +447,7 @@ struct Tracer {
     for (;;) {
       if (sp == 0) return true;
       pop(st);
+      if (COUNT) ++n_pops;
       if (!(ng.y & kGroupPending)) return false;
       if ((key_min(kq) & (0xFFFFu ^ (W - 1))) <= hb) return false;
     }
@@ -521,6 +523,7 @@ __device__ __forceinline__ void tri_phase_warp(Tracer<W, COUNT, TMIN>& tr, unsig
   }
   const int total = __shfl_sync(FULL, incl, 31);
   if (total == 0) return;
+  if (COUNT && lane == 0) tr.n_rounds += (uint32_t)(total + 31) / 32u;
   if (cnt) keys[lane] = hit_key(tr.best_t, tr.best_id);
   __syncwarp();
   const uint64_t tri_ptr = (uint64_t)tr.tris;
