@@ -86,7 +86,15 @@ struct Opts {
       count = 0, tri_mode = 0;
 };
 
-fgl_status resolve_opts(const fgl_batch_opts* o, Opts* r) {
+}  // namespace
+
+namespace fgl {
+
+// Defaults and range checks of fgl_batch_opts, shared by every batched entry
+// point (the allocation-free one included).  Returns nullptr when the options
+// are valid, else a constant message; nothing is allocated either way.
+const char* launch_opts(const fgl_batch_opts* o, int* packet, int* block, int* sdepth, int* bpsm,
+                        int* graph, int* refill, int* postpone, int* count, int* tri_mode) {
   Opts d;
   if (o) {
     if (o->packet_rays) d.packet = o->packet_rays;
@@ -100,14 +108,35 @@ fgl_status resolve_opts(const fgl_batch_opts* o, Opts* r) {
     d.tri_mode = o->tri_mode;
   }
   if (d.packet < 32 || d.packet % 32 || d.packet > (1 << 20))
-    return fail(FGL_ERR_INVALID, "packet_rays must be a positive multiple of 32");
+    return "packet_rays must be a positive multiple of 32";
   if (d.block < 32 || d.block % 32 || d.block > 512)
-    return fail(FGL_ERR_INVALID, "block_threads must be a multiple of 32 in [32, 512]");
-  if (d.sdepth < 0 || d.sdepth > 64) return fail(FGL_ERR_INVALID, "stack_smem must be in [0, 64]");
-  if (d.bpsm < 0 || d.bpsm > 64) return fail(FGL_ERR_INVALID, "blocks_per_sm must be in [0, 64]");
-  if (d.refill < 1 || d.refill > 32) return fail(FGL_ERR_INVALID, "refill_min must be in [1, 32]");
-  if (d.postpone > 100) return fail(FGL_ERR_INVALID, "postpone_pct must be <= 100");
-  if (d.tri_mode != 0 && d.tri_mode != 1) return fail(FGL_ERR_INVALID, "tri_mode must be 0 or 1");
+    return "block_threads must be a multiple of 32 in [32, 512]";
+  if (d.sdepth < 0 || d.sdepth > 64) return "stack_smem must be in [0, 64]";
+  if (d.bpsm < 0 || d.bpsm > 64) return "blocks_per_sm must be in [0, 64]";
+  if (d.refill < 1 || d.refill > 32) return "refill_min must be in [1, 32]";
+  if (d.postpone > 100) return "postpone_pct must be <= 100";
+  if (d.tri_mode != 0 && d.tri_mode != 1) return "tri_mode must be 0 or 1";
+  *packet = d.packet;
+  *block = d.block;
+  *sdepth = d.sdepth;
+  *bpsm = d.bpsm;
+  *graph = d.graph;
+  *refill = d.refill;
+  *postpone = d.postpone;
+  *count = d.count;
+  *tri_mode = d.tri_mode;
+  return nullptr;
+}
+
+}  // namespace fgl
+
+namespace {
+
+fgl_status resolve_opts(const fgl_batch_opts* o, Opts* r) {
+  Opts d;
+  const char* msg = launch_opts(o, &d.packet, &d.block, &d.sdepth, &d.bpsm, &d.graph, &d.refill,
+                                &d.postpone, &d.count, &d.tri_mode);
+  if (msg) return fail(FGL_ERR_INVALID, msg);
   DeviceInfo di;
   fgl_status s = device_info(&di);
   if (s != FGL_OK) return s;
@@ -1046,12 +1075,21 @@ fgl_status fgl_sync(fgl_stream stream) {
 }
 
 fgl_status fgl_work_counters(uint64_t* rays, uint64_t* nodes, uint64_t* tris) {
-  unsigned long long c[3];
+  unsigned long long c[kWorkCounters];
   FGL_CUDA(cudaDeviceSynchronize());
   FGL_CUDA(read_and_clear_counters(c));
   if (rays) *rays = c[0];
   if (nodes) *nodes = c[1];
   if (tris) *tris = c[2];
+  return FGL_OK;
+}
+
+fgl_status fgl_work_phase_counters(uint64_t* out, int32_t n) {
+  if (!out || n < 1 || n > kWorkCounters) return fail(FGL_ERR_INVALID, "need 1 <= n <= 8 and out");
+  unsigned long long c[kWorkCounters];
+  FGL_CUDA(cudaDeviceSynchronize());
+  FGL_CUDA(read_and_clear_counters(c));
+  for (int k = 0; k < n; ++k) out[k] = c[k];
   return FGL_OK;
 }
 

@@ -1,11 +1,11 @@
 // fgl_cast_batched_static: the batched cast for callers that cannot allocate
 // device memory.
 //
-// Some callers must not call cudaMalloc (or any allocator) at all: code that
-// runs while a CUDA graph is being captured, host threads of a real-time
-// simulation loop where an allocation's implicit device synchronisation is
-// not acceptable, or processes whose device memory is fully handed to a
-// pooling allocator they do not own.  fgl_cast_batched keeps its work-queue
+// Some callers must not call cudaMalloc (or any allocator) at all: host
+// threads of a real-time simulation loop where an allocation's implicit device
+// synchronisation is not acceptable, plugins inside a host application that
+// owns every device allocation, or processes whose device memory is fully
+// handed to a pooling allocator they do not own.  fgl_cast_batched keeps its work-queue
 // scratch (queue head + item table) in library-allocated, per-stream device
 // memory; this entry point instead keeps it in one fixed, file-scope device
 // array, so a call allocates nothing on the device (and nothing on the host
@@ -26,8 +26,11 @@
 #include "kernels.h"
 
 namespace fgl {
-// Allocation-free item check + descriptor fill (api.cu).
+// Allocation-free item check + descriptor fill, and launch-option defaults and
+// checks (api.cu); both return a constant message, or nullptr when valid.
 const char* static_item_desc(const fgl_cast_item& it, ItemDesc* d, int* width);
+const char* launch_opts(const fgl_batch_opts* o, int* packet, int* block, int* sdepth, int* bpsm,
+                        int* graph, int* refill, int* postpone, int* count, int* tri_mode);
 }  // namespace fgl
 
 using namespace fgl;
@@ -44,13 +47,15 @@ static_assert(kStaticBytes % 16 == 0, "scratch is copied in 16-byte words");
 // its device address comes from cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
 
-// The table image travels as a kernel parameter (about 20.6 KB, within the
-// 32,764-byte parameter limit), so no host staging buffer is needed either.
+// The table image travels as a kernel parameter (16 + 2 * 64 + 256 * 96 =
+// 24,720 bytes, within the 32,764-byte parameter limit), so no host staging
+// buffer is needed either.
 struct StaticImage {
   uint32_t n_words;
   uint32_t pad[3];
   uint4 words[kStaticWords];
 };
+static_assert(sizeof(StaticImage) <= 32764, "the table image must fit the kernel parameter space");
 
 __global__ void k_static_table(const StaticImage img, uint4* __restrict__ dst) {
   for (uint32_t i = threadIdx.x; i < img.n_words; i += blockDim.x) dst[i] = img.words[i];
@@ -101,30 +106,22 @@ extern "C" fgl_status fgl_cast_batched_static(const fgl_cast_item* items, int32_
                "split the batch or use fgl_cast_batched");
   if (n_items > 0 && !items) return err(FGL_ERR_INVALID, "items is null");
 
-  // launch options (same meaning and defaults as fgl_cast_batched; use_graph is ignored)
-  int packet = 32, block = 128, sdepth = 8, bpsm = 0, refill = 32, postpone = 20, count = 0,
-      tri_mode = 0;
-  if (opts) {
-    if (opts->packet_rays) packet = opts->packet_rays;
-    if (opts->block_threads) block = opts->block_threads;
-    if (opts->stack_smem) sdepth = opts->stack_smem;
-    if (opts->blocks_per_sm) bpsm = opts->blocks_per_sm;
-    if (opts->refill_min) refill = opts->refill_min;
-    if (opts->postpone_pct) postpone = opts->postpone_pct;
-    count = opts->count_work ? 1 : 0;
-    tri_mode = opts->tri_mode;
-  }
-  if (packet < 32 || packet % 32 || packet > (1 << 20))
-    return err(FGL_ERR_INVALID, "packet_rays must be a positive multiple of 32");
-  if (block < 32 || block % 32 || block > 512)
-    return err(FGL_ERR_INVALID, "block_threads must be a multiple of 32 in [32, 512]");
-  if (sdepth < 0 || sdepth > 64) return err(FGL_ERR_INVALID, "stack_smem must be in [0, 64]");
-  if (bpsm < 0 || bpsm > 64) return err(FGL_ERR_INVALID, "blocks_per_sm must be in [0, 64]");
-  if (refill < 1 || refill > 32) return err(FGL_ERR_INVALID, "refill_min must be in [1, 32]");
-  if (postpone > 100) return err(FGL_ERR_INVALID, "postpone_pct must be <= 100");
-  if (tri_mode != 0 && tri_mode != 1) return err(FGL_ERR_INVALID, "tri_mode must be 0 or 1");
+  // launch options (same meaning, defaults and checks as fgl_cast_batched;
+  // use_graph is ignored)
+  int packet, block, sdepth, bpsm, graph, refill, postpone, count, tri_mode;
+  const char* bad = launch_opts(opts, &packet, &block, &sdepth, &bpsm, &graph, &refill, &postpone,
+                                &count, &tri_mode);
+  if (bad) return err(FGL_ERR_INVALID, bad);
+  (void)graph;
 
-  // item descriptors, grouped by BVH width, written straight into the image
+  // item descriptors, checked once each, then grouped by BVH width straight
+  // into the image
+  ItemDesc descs[kStaticMaxItems];
+  int widths[kStaticMaxItems];
+  for (int i = 0; i < n_items; ++i) {
+    const char* msg = static_item_desc(items[i], &descs[i], &widths[i]);
+    if (msg) return err(FGL_ERR_INVALID, msg);
+  }
   StaticImage img;
   img.n_words = 0;
   size_t group_off[kMaxGroups] = {0, 0};
@@ -141,11 +138,8 @@ extern "C" fgl_status fgl_cast_batched_static(const fgl_cast_item* items, int32_
     int64_t packets = 0;
     bool tmin = false;
     for (int i = 0; i < n_items; ++i) {
-      ItemDesc d;
-      int width = 0;
-      const char* msg = static_item_desc(items[i], &d, &width);
-      if (msg) return err(FGL_ERR_INVALID, msg);
-      if (width != W || d.n_env == 0) continue;
+      ItemDesc d = descs[i];
+      if (widths[i] != W || d.n_env == 0) continue;
       d.pk_per_env = (d.n_rays + packet - 1) / packet;
       d.pk_begin = packets;
       packets += (int64_t)d.pk_per_env * d.n_env;
