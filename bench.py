@@ -246,28 +246,28 @@ def hbm_roofline(bytes_, seconds, rays, nodes, tris, kernel="k_persistent"):
             "basis": "algorithmic bytes of eq. cost(r_j) from a counting pass"}
 
 
-def l2_copy_peak(dev, mib: int = 24, reps: int = 50):
-    """L2 copy bandwidth measured here: a {mib} MiB -> {mib} MiB device copy
-    that stays resident in L2 (48 MiB in all, well under the 129 MB L2),
-    repeated after warm-up and timed with CUDA events; bytes = read + write."""
+def l2_read_peak(dev, mib: int = 32, reps: int = 20):
+    """L2 read bandwidth measured here: the library's probe reads a {mib} MiB
+    device buffer (resident in the 129 MB L2 after a warm-up pass) `reps`
+    times with 16-byte L1-bypassing loads on 4 x 512 threads per SM, timed
+    with CUDA events; best of 5."""
     import torch
-    a = torch.empty(mib << 18, dtype=torch.float32, device=dev).fill_(1.0)
-    b = torch.empty_like(a)
-    for _ in range(10):
-        b.copy_(a)
+    import paper_2509_17390_gb300 as fgl
+    a = torch.ones(mib << 18, dtype=torch.float32, device=dev)
+    sink = torch.zeros(1, dtype=torch.int32, device=dev)
+    fgl.probe_l2_read(a, 2, sink)
     best = None
-    for _ in range(3):
+    for _ in range(5):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        for _ in range(reps):
-            b.copy_(a)
+        fgl.probe_l2_read(a, reps, sink)
         e1.record()
         e1.synchronize()
-        gbs = 2 * (mib << 20) * reps / (e0.elapsed_time(e1) / 1e3) / 1e9
+        gbs = (mib << 20) * reps / (e0.elapsed_time(e1) / 1e3) / 1e9
         best = gbs if best is None else max(best, gbs)
-    del a, b
-    return {"gbs": round(best, 1), "basis": f"torch copy of {mib} MiB to {mib} MiB resident in L2, "
-                                            f"{reps} back to back, best of 3, read + write bytes"}
+    del a
+    return {"gbs": round(best, 1), "basis": f"fgl_probe_l2_read: {mib} MiB resident buffer read {reps} "
+                                            f"times with 16-byte L2 loads, best of 5 (read bytes)"}
 
 
 def time_oracle(osc, o, d, max_range, nthreads: int = 0):
@@ -463,6 +463,8 @@ def main():
     ap.add_argument("--workload", default="walk",
                     choices=["walk", "hetero", "serve", "occupancy", "walk_instances", "lbvh", "mesh"])
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-poses", default="slots", choices=["slots", "request"],
+                    help="served walk: poses in device-resident slots (default) or carried by each request")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -575,7 +577,7 @@ def main():
     lpr = read_profile("k_persistent", "lts_bytes_per_ray")
     if tr is not None:
         roofline["dram_gbs_measured"] = round(tr / (kern_ms / 1e3) / 1e9, 1)
-    l2pk = l2_copy_peak(dev)
+    l2pk = l2_read_peak(dev)
     if lpr is not None:
         l2 = lpr * n_rays / (kern_ms / 1e3) / 1e9
         roofline["l2"] = {"achieved": round(l2, 1), "peak": l2pk["gbs"], "unit": "GB/s",
@@ -663,7 +665,8 @@ def main():
     # served: continuous batching vs one launch per env on Poisson traces
     served = None
     if not args.no_serve:
-        served = served_walk(fgl, scene, sensor, walk, walk_d, w.max_range, value, rank)
+        served = served_walk(fgl, scene, sensor, walk, walk_d, w.max_range, value, rank,
+                             slots=args.serve_poses == "slots")
 
     # CPU oracle on a bounded sample (rank 0, N = 1 only)
     cpu = None
@@ -699,7 +702,7 @@ def main():
         dist.destroy_process_group()
 
 
-def served_walk(fgl, scene, sensor, walk, walk_d, max_range, grays, rank):
+def served_walk(fgl, scene, sensor, walk, walk_d, max_range, grays, rank, slots=True):
     """Poisson requests of 1-4096 walk environments (log-uniform) at 70% of
     the measured batched capacity for 2 s through the continuous-batching
     server, the environments' poses kept on the device (each request
@@ -720,7 +723,9 @@ def served_walk(fgl, scene, sensor, walk, walk_d, max_range, grays, rank):
     srv = fgl.Server(tick_rays=16 << 20, env_capacity=65536)
     sid, tid = srv.add_scene(scene), srv.add_sensor(sensor)
     plan = SlotPlan(srv, [walk_d.reshape(-1, 3, 4)], 65536, seed=12 + rank)
-    strace = slot_trace(trace, plan)
+    strace = slot_trace(trace, plan) if slots else trace
+    if not slots:
+        out["poses"] = "carried by each request from host memory (n_env x 48 B host->device)"
     res = replay_runs(srv, strace, [sid], [tid], [sensor.n_rays], arena, max_range)
     out.update({"requests": res["requests"], "p50_ms": round(res["p50_ms"], 2),
                 "p99_ms": round(res["p99_ms"], 2), "value": round(res["rays_per_s"] / 1e9, 4),
@@ -729,7 +734,7 @@ def served_walk(fgl, scene, sensor, walk, walk_d, max_range, grays, rank):
     # the same trace prefix through both servers (the plain server falls behind)
     pre, acc = [], 0
     for tr in strace:
-        acc += tr[4][1].shape[0] * sensor.n_rays
+        acc += (tr[3].shape[0] if tr[3] is not None else tr[4][1].shape[0]) * sensor.n_rays
         pre.append(tr)
         if acc > 2.5e8:
             break

@@ -293,6 +293,16 @@ fgl_status fgl_work_counters(uint64_t* rays, uint64_t* node_visits, uint64_t* tr
  * drawn by warps. */
 fgl_status fgl_work_phase_counters(uint64_t* out, int32_t n);
 
+/* Bandwidth probe for the roofline (no counterpart in the paper): reads the
+ * device buffer buf (16-byte aligned, `bytes` a multiple of 16) `reps` times
+ * with 16-byte loads that bypass L1, on a grid of 4 blocks of 512 threads
+ * per SM; time it with events on `stream` to get the L2 read bandwidth of a
+ * buffer that stays resident in L2.  sink: device uint32 (written only with
+ * a value no load can produce, i.e. in practice never).  Errors:
+ * FGL_ERR_INVALID for null pointers, sizes or alignment. */
+fgl_status fgl_probe_l2_read(const void* buf, int64_t bytes, int32_t reps, uint32_t* sink,
+                             fgl_stream stream);
+
 /* Debug export of the float32 world rays the kernels trace (eq. r_j):
  * out_o, out_d device float32 [n_env * n_rays][3]. */
 fgl_status fgl_world_rays(fgl_sensor sensor, const float* poses, int32_t n_env, float* out_o,

@@ -119,6 +119,7 @@ def lib():
                 "fgl_work_counters": ([P, P, P], I32),
                 "fgl_work_phase_counters": ([P, I32], I32),
                 "fgl_world_rays": ([P, P, I32, P, P, P], I32),
+                "fgl_probe_l2_read": ([P, I64, I32, P, P], I32),
                 "fgl_gaussian_density": ([P, P, F32, P, P, P, P, P], I32),
                 "fgl_lbvh_build": ([P, I64, P, I64, P, P], I32),
                 "fgl_lbvh_destroy": ([P], I32),
@@ -675,6 +676,14 @@ def work_counters():
     r, n, t = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
     _check(lib().fgl_work_counters(ctypes.byref(r), ctypes.byref(n), ctypes.byref(t)))
     return int(r.value), int(n.value), int(t.value)
+
+
+def probe_l2_read(buf, reps: int, sink, stream=None):
+    """fgl_probe_l2_read over a CUDA tensor `buf` (its whole storage), `reps`
+    passes; `sink` a one-element int32 CUDA tensor."""
+    nbytes = buf.numel() * buf.element_size()
+    _check(lib().fgl_probe_l2_read(buf.data_ptr(), nbytes - nbytes % 16, int(reps), sink.data_ptr(),
+                                   _stream_handle(stream)))
 
 
 PHASE_COUNTERS = ("rays", "node_visits", "tri_tests", "warp_iterations", "active_lane_iterations",

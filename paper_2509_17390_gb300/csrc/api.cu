@@ -1093,6 +1093,19 @@ fgl_status fgl_work_phase_counters(uint64_t* out, int32_t n) {
   return FGL_OK;
 }
 
+fgl_status fgl_probe_l2_read(const void* buf, int64_t bytes, int32_t reps, uint32_t* sink,
+                             fgl_stream stream) {
+  if (!buf || !sink) return fail(FGL_ERR_INVALID, "null buffer or sink");
+  if (bytes < 16 || bytes % 16 || reps < 1)
+    return fail(FGL_ERR_INVALID, "bytes must be a positive multiple of 16 and reps >= 1");
+  if ((uintptr_t)buf % 16) return fail(FGL_ERR_INVALID, "buf must be 16-byte aligned");
+  DeviceInfo di;
+  fgl_status st = device_info(&di);
+  if (st != FGL_OK) return st;
+  FGL_CUDA(launch_l2_read(buf, bytes, reps, (unsigned*)sink, di.sm_count, (cudaStream_t)stream));
+  return FGL_OK;
+}
+
 fgl_status fgl_world_rays(fgl_sensor sensor, const float* poses, int32_t n_env, float* out_o,
                           float* out_d, fgl_stream stream) {
   if (!sensor) return fail(FGL_ERR_INVALID, "null sensor");

@@ -9,6 +9,7 @@
 //                  enough lanes are idle, so warps stay full while the
 //                  per-ray work (eq. cost(r_j)) varies.
 //   k_world_rays : debug export of the float32 rays of eq. r_j.
+//   k_l2_read    : bandwidth probe, 16-byte L2 reads of a resident buffer.
 #include <cuda_runtime.h>
 
 #include "kernels.h"
@@ -454,6 +455,31 @@ __global__ void k_points(const float4* __restrict__ dirs, const float* __restric
   __stcs(out + 3 * o + 2, hit ? __fadd_rn(oz, __fmul_rn(t, dz)) : nan);
 }
 
+// Every thread reads 16-byte words of `buf` (L2 only: ld.global.cg) in a
+// grid-stride loop, `reps` times over, and folds them into one word so the
+// loads cannot be dropped; block 0's thread 0 publishes the fold of its own
+// reads only when it is a value no read can produce alone (never, in
+// practice), keeping the store off the timed path.
+__global__ void k_l2_read(const uint4* __restrict__ buf, int64_t n16, int reps,
+                          unsigned* __restrict__ sink) {
+  uint32_t acc = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int r = 0; r < reps; ++r) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < n16; i += 4 * stride) {  // four independent loads in flight
+      const uint4 a = __ldcg(buf + i), b = __ldcg(buf + i + stride);
+      const uint4 c = __ldcg(buf + i + 2 * stride), d = __ldcg(buf + i + 3 * stride);
+      acc ^= (a.x ^ a.y ^ a.z ^ a.w) ^ (b.x ^ b.y ^ b.z ^ b.w) ^ (c.x ^ c.y ^ c.z ^ c.w) ^
+             (d.x ^ d.y ^ d.z ^ d.w);
+    }
+    for (; i < n16; i += stride) {
+      const uint4 v = __ldcg(buf + i);
+      acc ^= v.x ^ v.y ^ v.z ^ v.w;
+    }
+  }
+  if (acc == 0x5A17C0DEu) atomicXor(sink, acc);
+}
+
 __global__ void k_world_rays(const float4* __restrict__ dirs, const float* __restrict__ poses,
                              int n_env, int n_rays, float* __restrict__ out_o,
                              float* __restrict__ out_d) {
@@ -582,6 +608,13 @@ cudaError_t launch_points(const ItemDesc& it, float* out, cudaStream_t s) {
   if (total == 0) return cudaSuccess;
   k_points<<<(unsigned)((total + 255) / 256), 256, 0, s>>>((const float4*)it.dirs, it.poses, it.n_env,
                                                           it.n_rays, it.out_range, it.out_tri, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_l2_read(const void* buf, int64_t bytes, int reps, unsigned* sink, int sms,
+                           cudaStream_t s) {
+  if (bytes < 16 || reps < 1) return cudaSuccess;
+  k_l2_read<<<sms * 4, 512, 0, s>>>((const uint4*)buf, bytes / 16, reps, sink);
   return cudaGetLastError();
 }
 

@@ -45,6 +45,8 @@ cudaError_t launch_lbvh_cast(const fgl_lbvh_s* L, const void* dirs, const float*
                              int32_t* out_tri, cudaStream_t s);
 
 // Debug export of world rays (beam order).
+cudaError_t launch_l2_read(const void* buf, int64_t bytes, int reps, unsigned* sink, int sms,
+                           cudaStream_t s);
 cudaError_t launch_world_rays(const void* dirs, const float* poses, int n_env, int n_rays,
                               float* out_o, float* out_d, cudaStream_t s);
 

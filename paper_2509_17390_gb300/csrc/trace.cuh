@@ -514,6 +514,9 @@ __device__ __forceinline__ void tri_phase_warp(Tracer<W, COUNT, TMIN>& tr, unsig
                                                int lane, unsigned* status) {
   const unsigned FULL = 0xFFFFFFFFu;
   const uint32_t bits = tr.tg.y & 0x00FFFFFFu;
+  // about half of the traversal steps leave no leaf triangle on any lane:
+  // one vote skips the prefix sum then
+  if (__ballot_sync(FULL, bits != 0u) == 0u) return;
   const int cnt = __popc(bits);
   int incl = cnt;
 #pragma unroll
@@ -522,7 +525,6 @@ __device__ __forceinline__ void tri_phase_warp(Tracer<W, COUNT, TMIN>& tr, unsig
     if (lane >= o) incl += v;
   }
   const int total = __shfl_sync(FULL, incl, 31);
-  if (total == 0) return;
   if (COUNT && lane == 0) tr.n_rounds += (uint32_t)(total + 31) / 32u;
   if (cnt) keys[lane] = hit_key(tr.best_t, tr.best_id);
   __syncwarp();
