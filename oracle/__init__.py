@@ -23,6 +23,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.cpp")
 _SRC_DENSITY = os.path.join(_HERE, "density.cpp")
 _SRC_TSDF = os.path.join(_HERE, "tsdf.cpp")
+_SRC_EFFECTS = os.path.join(_HERE, "effects.cpp")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
@@ -34,11 +35,11 @@ FLAG_EDGE, FLAG_TIE, FLAG_RANGE = 1, 2, 4
 def build(force: bool = False) -> str:
     """Compile liboracle.so (g++, FP64, no FMA contraction)."""
     os.makedirs(_BUILD, exist_ok=True)
-    newest = max(os.path.getmtime(f) for f in (_SRC, _SRC_DENSITY, _SRC_TSDF))
+    newest = max(os.path.getmtime(f) for f in (_SRC, _SRC_DENSITY, _SRC_TSDF, _SRC_EFFECTS))
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-               "-shared", "-pthread", _SRC, _SRC_DENSITY, _SRC_TSDF, "-o", tmp]
+               "-shared", "-pthread", _SRC, _SRC_DENSITY, _SRC_TSDF, _SRC_EFFECTS, "-o", tmp]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -73,9 +74,13 @@ def lib():
             L.orc_blur.argtypes = [P, I64, I64, I64, D, I32, P]
             L.orc_outside.argtypes = [P, I64, I64, I64, P]
             L.orc_shell.argtypes = [P, I64, I64, I64, I32, P]
-            L.orc_tsdf.argtypes = [P, P, I64, F, F, P]
+            L.orc_tsdf.argtypes = [P, P, I64, F, F, I32, P]
             L.orc_marching_tets.argtypes = [P, I64, I64, I64, P, F, F, I32, I32, P, P, P, P, P]
             L.orc_tsdf_free.argtypes = [P]
+            U64 = ctypes.c_uint64
+            L.orc_philox4x32.argtypes = [P, P, I32, P]
+            L.orc_sensor_effects.argtypes = [U64, ctypes.c_uint32, ctypes.c_int32, D, D, D, D, I64, I64,
+                                             P, P, P]
             _lib = L
     return _lib
 
@@ -153,6 +158,32 @@ def cast_with_instances(static: "Scene", instances, o, d, inst_poses, n_rays, ma
         i = np.where(take, ik, i)
         inst = np.where(take, k, inst).astype(np.int32)
     return r, i, inst, fl
+
+
+def philox4x32(ctr, key, rounds: int = 10) -> np.ndarray:
+    """Philox-4x32 (Salmon et al. 2011) of one counter (4 uint32) under one
+    key (2 uint32): 4 uint32 words."""
+    c = np.ascontiguousarray(ctr, np.uint32).reshape(4)
+    k = np.ascontiguousarray(key, np.uint32).reshape(2)
+    out = np.empty(4, np.uint32)
+    lib().orc_philox4x32(_ptr(c), _ptr(k), int(rounds), _ptr(out))
+    return out
+
+
+def sensor_effects(range_, tri, n_env: int, seed: int, step: int = 0, env_offset: int = 0,
+                   drop_prob: float = 0.0, sigma0: float = 0.0, sigma1: float = 0.0,
+                   max_range: float = 100.0):
+    """Seeded return dropout and range noise on cast returns [n_env * n_rays]
+    (see effects.cpp): returns (range f32, tri i32, dropped u8) copies."""
+    r = np.array(range_, np.float32, copy=True).reshape(-1)
+    t = np.array(tri, np.int32, copy=True).reshape(-1)
+    if len(r) != len(t) or len(r) % max(1, n_env):
+        raise ValueError("range and tri must hold n_env * n_rays values")
+    dropped = np.empty(len(r), np.uint8)
+    lib().orc_sensor_effects(int(seed), int(step), int(env_offset), float(drop_prob), float(sigma0),
+                             float(sigma1), float(max_range), int(n_env), len(r) // max(1, n_env),
+                             _ptr(r), _ptr(t), _ptr(dropped))
+    return r, t, dropped
 
 
 class Scene:
@@ -373,15 +404,19 @@ def band_layers(h: float, r: float) -> int:
     return int(np.ceil(np.float64(np.float32(r)) / np.float64(np.float32(h))))
 
 
-def tsdf(V, h: float, r: float):
-    """Eq. phi = clip(s (p + 1/2) h, -r, r) for a surface grid V [nz, ny, nx];
-    returns (phi f32, outside u8, p u8)."""
+def tsdf(V, h: float, r: float, delta: str = "half"):
+    """Eq. phi = clip(s delta, -r, r) for a surface grid V [nz, ny, nx], with
+    eq. delta read as (p + 1/2) h (delta="half", the default) or literally as
+    p h (delta="literal"); returns (phi f32, outside u8, p u8)."""
+    if delta not in ("half", "literal"):
+        raise ValueError("delta must be 'half' or 'literal'")
     V = np.ascontiguousarray(V, np.uint8)
     L = min(band_layers(h, r), 254)
     out = outside(V)
     p = shell(V, L)
     phi = np.empty(V.shape, np.float32)
-    if lib().orc_tsdf(_ptr(out), _ptr(p), V.size, float(h), float(r), _ptr(phi)):
+    if lib().orc_tsdf(_ptr(out), _ptr(p), V.size, float(h), float(r), 1 if delta == "literal" else 0,
+                      _ptr(phi)):
         raise ValueError("orc_tsdf: bad arguments")
     return phi, out, p
 

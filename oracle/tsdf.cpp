@@ -30,7 +30,9 @@
 //             with delta = p h exactly, every voxel of S_0 -- on both sides of
 //             the interface -- would sit at phi = 0 and the level set would
 //             pass through grid points; (p + 1/2) h puts it midway between the
-//             two sides of S_0.  Computed in FP64 and rounded once to float32.
+//             two sides of S_0.  The literal eq. delta, delta = p h, is the
+//             other mode (literal = 1).  Computed in FP64, rounded once to
+//             float32.
 //   surface   the level set phi = iso by marching tetrahedra on the sample
 //             grid of every step-th voxel (paper's mc_step): each cube of
 //             eight samples is split into the six tetrahedra around its
@@ -186,12 +188,15 @@ int orc_shell(const uint8_t* V, int64_t nx, int64_t ny, int64_t nz, int32_t L, u
   return 0;
 }
 
-// eq. phi from the sign and the shell index.
-int orc_tsdf(const uint8_t* outside, const uint8_t* p, int64_t n, float h, float r, float* phi) {
+// eq. phi from the sign and the shell index; eq. delta as (p + 1/2) h, or
+// literally as p h when `literal` is nonzero.
+int orc_tsdf(const uint8_t* outside, const uint8_t* p, int64_t n, float h, float r, int literal,
+             float* phi) {
   if (n < 0 || !(h > 0) || !(r > 0)) return 1;
+  const double off = literal ? 0.0 : 0.5;
   for (int64_t v = 0; v < n; ++v) {
     const double s = outside[v] ? 1.0 : -1.0;
-    const double delta = p[v] == 255 ? (double)r : ((double)p[v] + 0.5) * (double)h;
+    const double delta = p[v] == 255 ? (double)r : ((double)p[v] + off) * (double)h;
     phi[v] = (float)(s * std::min(delta, (double)r));
   }
   return 0;

@@ -146,6 +146,46 @@ def test_tsdf_values_and_band():
     assert np.all(np.abs(phi) <= np.float32(r))
 
 
+def test_tsdf_literal_delta_single_voxel_closed_form():
+    """Eq. delta read literally (p h): one occupied voxel gives phi = -0 on it,
+    +0 on its six face neighbours (both sides of S_0 at zero) and (D - 1) h at
+    taxicab distance D >= 1, clipped to r; the default reading is the same
+    field moved by h/2 away from zero (-h/2 on the voxel, (D - 1/2) h around)."""
+    V = np.zeros((11, 11, 11), np.uint8)
+    c = 5
+    V[c, c, c] = 1
+    h, r = 0.01, 0.035
+    z, y, x = np.indices(V.shape)
+    D = (np.abs(z - c) + np.abs(y - c) + np.abs(x - c)).astype(np.float64)
+    hf, rf = np.float64(np.float32(h)), np.float64(np.float32(r))
+    lit, out, p = oracle.tsdf(V, h, r, delta="literal")
+    ref = np.where(D == 0, -0.0, np.minimum(np.maximum(D - 1, 0) * hf, rf)).astype(np.float32)
+    assert np.array_equal(lit, ref)
+    assert np.signbit(lit[c, c, c]) and not np.signbit(lit[c, c, c + 1]) and lit[c, c, c + 1] == 0
+    half, _, _ = oracle.tsdf(V, h, r)
+    ref_h = np.where(D == 0, -0.5 * hf, np.minimum((np.maximum(D - 1, 0) + 0.5) * hf, rf)).astype(np.float32)
+    assert np.array_equal(half, ref_h)
+    with pytest.raises(ValueError):
+        oracle.tsdf(V, h, r, delta="p")
+
+
+def test_tsdf_literal_delta_surface_offset():
+    """A 6-voxel-thick slab: with the literal eq. delta the iso = 0 surface
+    runs through the centres of the slab's outer voxel layers, h/2 inside the
+    default reading's, which lies on the slab's faces."""
+    V = np.zeros((20, 12, 12), np.uint8)
+    V[7:13, :, :] = 1
+    h, r = 0.1, 0.35
+    z_lo_face, z_hi_face = 7 * h, 13 * h              # the slab's faces (voxel k spans [k h, (k+1) h])
+    for delta, lo, hi in (("half", z_lo_face, z_hi_face), ("literal", z_lo_face + h / 2, z_hi_face - h / 2)):
+        phi, _, _ = oracle.tsdf(V, h, r, delta=delta)
+        v, t, _ = oracle.marching_tets(phi, (0.0, 0.0, 0.0), h)
+        # away from the grid's side faces the surface is the two planes
+        inner = (v[:, 0] > 2 * h) & (v[:, 0] < 9 * h) & (v[:, 1] > 2 * h) & (v[:, 1] < 9 * h)
+        zs = np.unique(np.round(v[inner, 2].astype(np.float64), 6))
+        assert np.allclose(zs, [lo, hi], atol=1e-6), (delta, zs)
+
+
 # -- isosurface -----------------------------------------------------------------
 
 def edge_stats(tris):
