@@ -105,7 +105,7 @@ __global__ void __maxnreg__(72) k_plain(const ItemDesc it, int sdepth, int tri_m
           atomicOr(&g_status, tr.fail_bits());
           done = true;
         } else {
-          done = tr.finish(st);
+          done = tr.finish_pooled(st);
         }
       }
     }
@@ -232,7 +232,7 @@ __global__ void __maxnreg__(72) k_persistent(BatchHeader* __restrict__ hdr,
           atomicOr(&g_status, tr.fail_bits());
           fin = true;
         } else {
-          fin = tr.finish(st);
+          fin = tr.finish_pooled(st);
         }
       }
     } else if (active) {
@@ -316,7 +316,7 @@ __global__ void __maxnreg__(72) k_instance_pass(const InstancePass a, int sdepth
         atomicOr(&g_status, tr.fail_bits());
         done = true;
       } else {
-        done = tr.finish(st);
+        done = tr.finish_pooled(st);
       }
     }
   }
@@ -417,7 +417,7 @@ __global__ void __maxnreg__(72) k_instances_fused(const InstanceSet a, int sdept
           atomicOr(&g_status, tr.fail_bits());
           done = true;
         } else {
-          done = tr.finish(st);
+          done = tr.finish_pooled(st);
         }
       }
     }

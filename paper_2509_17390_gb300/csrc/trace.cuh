@@ -172,12 +172,14 @@ __device__ __forceinline__ void key_clear(uint2& k, uint32_t c) {
   else k.x |= h;
 }
 __device__ __forceinline__ void key_clear(uint4& k, uint32_t c) {
-  const uint32_t h = 0xFFFFu << ((c & 1u) << 4);
-  const uint32_t w = c >> 1;
-  k.x |= w == 0u ? h : 0u;
-  k.y |= w == 1u ? h : 0u;
-  k.z |= w == 2u ? h : 0u;
-  k.w |= w == 3u ? h : 0u;
+  // slot c's 16 bits within the 64-bit half (words x,y or z,w) that holds it
+  const uint64_t m = 0xFFFFull << ((c & 3u) << 4);
+  const uint32_t hi = 0u - ((c >> 2) & 1u);  // all ones for slots 4..7
+  const uint32_t ml = (uint32_t)m, mh = (uint32_t)(m >> 32);
+  k.x |= ml & ~hi;
+  k.y |= mh & ~hi;
+  k.z |= ml & hi;
+  k.w |= mh & hi;
 }
 __device__ __forceinline__ bool key_any(const uint2& k) { return (k.x & k.y) != 0xFFFFFFFFu; }
 __device__ __forceinline__ bool key_any(const uint4& k) {
@@ -437,6 +439,19 @@ struct Tracer {
     return true;
   }
 
+  // finish() for the pooled leaf tests, where the stack holds node groups
+  // only (no postponed triangle groups), so a popped group needs no type test.
+  __device__ __forceinline__ bool finish_pooled(const StackRefs<Keys>& st) {
+    if (ng.y & kGroupPending) return false;
+    const uint32_t hb = half_rp(best_t);
+    for (;;) {
+      if (sp == 0) return true;
+      pop(st);
+      if (COUNT) ++n_pops;
+      if ((key_min(kq) & (0xFFFFu ^ (W - 1))) <= hb) return false;
+    }
+  }
+
   // After the leaf tests: once the current node group has no pending child,
   // pop until a group with a child not beyond the best hit (or a postponed
   // triangle group) is on top; dead groups cost a shared-memory load each
@@ -538,8 +553,7 @@ __device__ __forceinline__ void tri_phase_warp(Tracer<W, COUNT, TMIN>& tr, unsig
       if (v <= p) lo += s;
     }
     const int owner = lo < 31 ? lo : 31;
-    const int o_incl = __shfl_sync(FULL, incl, owner);
-    const int o_cnt = __shfl_sync(FULL, cnt, owner);
+    const int o_excl = __shfl_sync(FULL, incl - cnt, owner);
     const uint32_t o_bits = __shfl_sync(FULL, bits, owner);
     const uint32_t o_base = __shfl_sync(FULL, tr.tg.x, owner);
     const uint32_t tp_lo = __shfl_sync(FULL, (uint32_t)tri_ptr, owner);
@@ -558,7 +572,7 @@ __device__ __forceinline__ void tri_phase_warp(Tracer<W, COUNT, TMIN>& tr, unsig
     const uint32_t o_lim = __shfl_sync(FULL, tr.lim_tris, owner);
 #endif
     if (p < total) {
-      const uint32_t k = (uint32_t)(p - (o_incl - o_cnt));
+      const uint32_t k = (uint32_t)(p - o_excl);
       const uint32_t pos = nth_set_bit(o_bits, k);
 #ifdef FGL_CHECKED
       if ((size_t)o_base + pos >= o_lim) {
