@@ -584,8 +584,8 @@ __global__ void k_dilate(const uint32_t* __restrict__ Din, BitGrid g, uint32_t* 
 constexpr int kPhiPlanes = 8;  // counts up to L + 1 <= 255
 
 __global__ void k_phi(const uint32_t* __restrict__ Ob, const uint32_t* __restrict__ planes, int L,
-                      BitGrid g, float h, float r, float* __restrict__ phi, uint8_t* __restrict__ out_outside,
-                      uint8_t* __restrict__ out_shell) {
+                      BitGrid g, float h, float r, float off, float* __restrict__ phi,
+                      uint8_t* __restrict__ out_outside, uint8_t* __restrict__ out_shell) {
   const int lane = threadIdx.x & 31;
   const uint32_t nw = (uint32_t)g.words();  // < 2^31
   const int n_planes = 32 - __clz(L + 1);
@@ -610,7 +610,9 @@ __global__ void k_phi(const uint32_t* __restrict__ Ob, const uint32_t* __restric
       const bool out = (__shfl_sync(0xFFFFFFFFu, ob, jw) >> lane) & 1u;
       if (x >= g.nx) continue;
       const int p = held ? L + 1 - held : 255;
-      const float delta = p == 255 ? r : fminf(((float)p + 0.5f) * h, r);
+      // (p + off) is exact in float32, so its product with h rounds once,
+      // like the product of the exact values
+      const float delta = p == 255 ? r : fminf(((float)p + off) * h, r);
       const int64_t v = (int64_t)row * g.nx + x;
       phi[v] = out ? delta : -delta;
       if (out_outside) out_outside[v] = out ? 1 : 0;
@@ -1163,6 +1165,8 @@ extern "C" fgl_status fgl_tsdf(const uint8_t* surf, const fgl_grid* grid, float 
   if (fgl_status st = check_grid(grid, &n)) return st;
   if (!surf || !out_phi) return err(FGL_ERR_INVALID, "null surf or out_phi");
   if (!(std::isfinite(trunc) && trunc > 0.f)) return err(FGL_ERR_INVALID, "trunc must be finite and > 0");
+  if (stats && stats->delta_mode != 0 && stats->delta_mode != 1)
+    return err(FGL_ERR_INVALID, "delta_mode must be 0 or 1");
   const double Ld = std::ceil((double)trunc / (double)grid->h);
   if (Ld > 254) return err(FGL_ERR_INVALID, "truncation band wider than 254 voxels");
   const int L = (int)Ld;
@@ -1202,8 +1206,9 @@ extern "C" fgl_status fgl_tsdf(const uint8_t* surf, const fgl_grid* grid, float 
   launches += 5;
   for (int m = 1; m <= L; ++m, ++launches)
     k_dilate<<<word_blocks(nw, 256), 256, 0, s>>>(Dm[(m - 1) & 1], g, Dm[m & 1], planes, n_planes);
-  k_phi<<<word_blocks(nw, 256), 256, 0, s>>>(Ob, planes, L, g, grid->h, trunc, out_phi, out_outside,
-                                             out_shell);
+  const float off = stats && stats->delta_mode == 1 ? 0.f : 0.5f;
+  k_phi<<<word_blocks(nw, 256), 256, 0, s>>>(Ob, planes, L, g, grid->h, trunc, off, out_phi,
+                                             out_outside, out_shell);
   ++launches;
   MCUDA(cudaGetLastError());
   MCUDA(cudaMemcpyAsync(S.host + 2, S.err, sizeof(int), cudaMemcpyDeviceToHost, s));
