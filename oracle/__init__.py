@@ -174,7 +174,11 @@ def sensor_effects(range_, tri, n_env: int, seed: int, step: int = 0, env_offset
                    drop_prob: float = 0.0, sigma0: float = 0.0, sigma1: float = 0.0,
                    max_range: float = 100.0):
     """Seeded return dropout and range noise on cast returns [n_env * n_rays]
-    (see effects.cpp): returns (range f32, tri i32, dropped u8) copies."""
+    (see effects.cpp): returns (range f32, tri i32, dropped u8) copies.  The
+    parameters are float32 values (as a caller of the library passes them):
+    they are rounded to float32 first."""
+    f32 = lambda x: float(np.float32(x))
+    drop_prob, sigma0, sigma1, max_range = f32(drop_prob), f32(sigma0), f32(sigma1), f32(max_range)
     r = np.array(range_, np.float32, copy=True).reshape(-1)
     t = np.array(tri, np.int32, copy=True).reshape(-1)
     if len(r) != len(t) or len(r) % max(1, n_env):

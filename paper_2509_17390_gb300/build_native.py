@@ -30,7 +30,7 @@ GXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-fno-fast-math"
              "-I" + INCLUDE, "-I" + CSRC]
 
 CU_SOURCES = ["kernels.cu", "api.cu", "static_batch.cu", "server.cu", "density.cu", "sort.cu", "lbvh.cu",
-              "mesh.cu"]
+              "mesh.cu", "effects.cu"]
 CPP_SOURCES = ["bvh_build.cpp"]
 HEADERS = ["fgl_internal.h", "kernels.h", "trace.cuh", "ptx_ops.cuh", "sort.h", "nvtx_range.h"]
 
