@@ -293,6 +293,37 @@ fgl_status fgl_work_counters(uint64_t* rays, uint64_t* node_visits, uint64_t* tr
  * drawn by warps. */
 fgl_status fgl_work_phase_counters(uint64_t* out, int32_t n);
 
+/* Optional sensor effects on cast returns, applied in place after a cast
+ * (the paper models the return as the nearest hit only, eq. t_j*, and leaves
+ * richer sensor physics to future work, Sec. VI; these are an extension):
+ *   random words  Philox-4x32-10 (Salmon et al., SC 2011), key (seed low 32
+ *                 bits, seed high 32 bits), counter (ray j, env_offset + e,
+ *                 step, 0) for ray j of environment e -> x0..x3;
+ *   dropout       a hit is dropped, i.e. reported as the miss (max_range, -1),
+ *                 when (x0 >> 8) * 2^-24 < drop_prob (exact in float32);
+ *   range noise   a kept hit at range t becomes t + (sigma0 + sigma1 t) n,
+ *                 n = sqrt(-2 ln u1) cos(2 pi u2) (Box-Muller) with
+ *                 u1 = ((x1 >> 8) + 1) 2^-24, u2 = (x2 >> 8) 2^-24, in
+ *                 float32, clamped to [0, max_range];
+ *   misses are unchanged.  Dropout decisions are exact; noisy ranges carry
+ *   float32 rounding (a few ulp of t plus ~1e-6 of the noise term).
+ *   range, tri: device [n_env * n_rays] returns of one cast item (ray j of
+ *   environment e at e * n_rays + j).  Errors: FGL_ERR_INVALID (null,
+ *   drop_prob outside [0, 1], negative or non-finite sigma, max_range,
+ *   env_offset), FGL_ERR_CUDA. */
+typedef struct {
+  uint64_t seed;
+  uint32_t step;          /* frame counter: each step draws anew */
+  int32_t env_offset;     /* counter id of the first environment (>= 0) */
+  float drop_prob;        /* probability that a hit is dropped */
+  float noise_sigma0;     /* range noise standard deviation at range 0 (m) */
+  float noise_sigma1;     /* ... growing by this much per metre of range */
+  float max_range;        /* the cast's max_range: dropped returns report it */
+} fgl_sensor_effects;
+
+fgl_status fgl_apply_sensor_effects(const fgl_sensor_effects* fx, float* range, int32_t* tri,
+                                    int32_t n_env, int32_t n_rays, fgl_stream stream);
+
 /* Bandwidth probe for the roofline (no counterpart in the paper): reads the
  * device buffer buf (16-byte aligned, `bytes` a multiple of 16) `reps` times
  * with 16-byte loads that bypass L1, on a grid of 4 blocks of 512 threads
@@ -452,6 +483,8 @@ typedef struct {
   int32_t n_layers;      /* out: shells grown, L = ceil(trunc / h) */
   int32_t n_launches;    /* out: kernels the call launched */
   float ms_total;        /* out (timing): first to last launch */
+  int32_t delta_mode;    /* in: eq. delta as (p + 1/2) h (0, the default) or literally as
+                            p h (1); see fgl_tsdf */
 } fgl_tsdf_stats;
 
 /* The narrow-band TSDF of a surface grid V (nonzero byte = surface voxel):
@@ -463,12 +496,16 @@ typedef struct {
  *          p(x) = first m with x in S_m, for m <= L = ceil(trunc / h);
  *   phi    = s * min((p + 1/2) h, trunc), and s * trunc where p > L (eq. phi;
  *          the half voxel places the zero crossing between the two sides of
- *          S_0 instead of on grid points).
- * phi is float32 and exact: (p + 1/2) h rounds once.
+ *          S_0 instead of on grid points).  With stats->delta_mode = 1 the
+ *          distance is eq. delta literally, p h: both sides of S_0 then sit
+ *          at phi = +-0, and the iso = 0 level set passes through the
+ *          centres of the occupied S_0 voxels, h/2 inside the default's.
+ * phi is float32 and exact: (p + 1/2) h (or p h) rounds once.
  *   out_phi: float [N]; out_outside: u8 s > 0 (may be NULL); out_shell: u8
  *   p, 255 beyond L (may be NULL); stats may be NULL.
  * Asynchronous unless stats->timing.  Errors: FGL_ERR_INVALID (null pointers,
- * bad grid, more than 2^31 - 2 voxels, trunc <= 0, L > 254), FGL_ERR_CUDA,
+ * bad grid, more than 2^31 - 2 voxels, trunc <= 0, L > 254, delta_mode not 0
+ * or 1), FGL_ERR_CUDA,
  * FGL_ERR_DEVICE (reported by the next call on the stream: a union-find
  * loop hit its N + 2 step bound, which correct input cannot cause). */
 fgl_status fgl_tsdf(const uint8_t* surf, const fgl_grid* grid, float trunc, float* out_phi,

@@ -120,6 +120,7 @@ def lib():
                 "fgl_work_phase_counters": ([P, I32], I32),
                 "fgl_world_rays": ([P, P, I32, P, P, P], I32),
                 "fgl_probe_l2_read": ([P, I64, I32, P, P], I32),
+                "fgl_apply_sensor_effects": ([P, P, P, I32, I32, P], I32),
                 "fgl_gaussian_density": ([P, P, F32, P, P, P, P, P], I32),
                 "fgl_lbvh_build": ([P, I64, P, I64, P, P], I32),
                 "fgl_lbvh_destroy": ([P], I32),
@@ -556,7 +557,8 @@ def gaussian_density(mu, scale, quat, opacity, origin, h: float, dims, theta: fl
 # mesh reconstruction (fgl_denoise, fgl_tsdf, fgl_marching_tets; Sec. IV-B)
 # ---------------------------------------------------------------------------
 class TsdfStats(ctypes.Structure):
-    _fields_ = [("timing", I32), ("n_layers", I32), ("n_launches", I32), ("ms_total", F32)]
+    _fields_ = [("timing", I32), ("n_layers", I32), ("n_launches", I32), ("ms_total", F32),
+                ("delta_mode", I32)]
 
 
 def _grid_of(shape, origin, h):
@@ -584,9 +586,12 @@ def denoise(surf, h: float, sigma: float, tau: float = 0.5, quantile=None, blur:
 
 
 def tsdf(surf, h: float, trunc: float, outside: bool = False, shell: bool = False,
-         timing: bool = False, stream=None):
-    """Narrow-band TSDF (fgl_tsdf) of a u8 surface grid [nz, ny, nx]:
+         timing: bool = False, stream=None, delta: str = "half"):
+    """Narrow-band TSDF (fgl_tsdf) of a u8 surface grid [nz, ny, nx], eq.
+    delta as (p + 1/2) h (delta="half") or literally p h (delta="literal"):
     returns (phi f32, outside u8 or None, shell index u8 or None, stats)."""
+    if delta not in ("half", "literal"):
+        raise ValueError("delta must be 'half' or 'literal'")
     import torch
     g, n = _grid_of(surf.shape, (0.0, 0.0, 0.0), h)
     dev = surf.device
@@ -595,6 +600,7 @@ def tsdf(surf, h: float, trunc: float, outside: bool = False, shell: bool = Fals
     sh = torch.empty(surf.shape, dtype=torch.uint8, device=dev) if shell else None
     st = TsdfStats()
     st.timing = 1 if timing else 0
+    st.delta_mode = 1 if delta == "literal" else 0
     _check(lib().fgl_tsdf(_dev_ptr(surf, "uint8", n, "surf"), ctypes.byref(g), float(trunc),
                           _dev_ptr(phi, "float32", n, "phi"),
                           _dev_ptr(out, "uint8", n, "outside") if outside else None,
@@ -676,6 +682,26 @@ def work_counters():
     r, n, t = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
     _check(lib().fgl_work_counters(ctypes.byref(r), ctypes.byref(n), ctypes.byref(t)))
     return int(r.value), int(n.value), int(t.value)
+
+
+class SensorEffects(ctypes.Structure):
+    _fields_ = [("seed", U64), ("step", ctypes.c_uint32), ("env_offset", I32), ("drop_prob", F32),
+                ("noise_sigma0", F32), ("noise_sigma1", F32), ("max_range", F32)]
+
+
+def apply_sensor_effects(range_, tri, n_env: int, seed: int, step: int = 0, env_offset: int = 0,
+                         drop_prob: float = 0.0, sigma0: float = 0.0, sigma1: float = 0.0,
+                         max_range: float = 100.0, stream=None):
+    """fgl_apply_sensor_effects in place on one cast item's CUDA outputs
+    (range float32, tri int32, n_env * n_rays each)."""
+    n = range_.numel()
+    if n_env < 1 or n % n_env:
+        raise ValueError("range must hold n_env * n_rays values")
+    fx = SensorEffects(int(seed), int(step), int(env_offset), float(drop_prob), float(sigma0),
+                       float(sigma1), float(max_range))
+    _check(lib().fgl_apply_sensor_effects(ctypes.byref(fx), _dev_ptr(range_, "float32", n, "range"),
+                                          _dev_ptr(tri, "int32", n, "tri"), int(n_env), n // n_env,
+                                          _stream_handle(stream)))
 
 
 def probe_l2_read(buf, reps: int, sink, stream=None):

@@ -60,6 +60,24 @@ def test_tsdf_bit_exact(shape, p, h, r):
     assert st["n_layers"] == oracle.band_layers(h, r) and st["ms_total"] > 0
 
 
+@pytest.mark.parametrize("shape,p,h,r", TSDF_CASES[:3])
+def test_tsdf_literal_delta_bit_exact_and_mesh(shape, p, h, r):
+    """Eq. delta read literally (p h): phi bit-exact (signed zeros included),
+    and its iso = 0 marching-tetrahedra mesh equal to the oracle's."""
+    rng = np.random.default_rng(sum(shape) + 1)
+    V = random_binary(rng, shape, p)
+    phi, _, _, _ = fgl.tsdf(cu(V), h, r, delta="literal")
+    phi_o, _, _ = oracle.tsdf(V, h, r, delta="literal")
+    assert np.array_equal(phi.cpu().numpy().view(np.uint32), phi_o.view(np.uint32))
+    v, t, _ = fgl.marching_tets(phi, (0.0, 0.0, 0.0), h)
+    torch.cuda.synchronize()
+    v_o, t_o, _ = oracle.marching_tets(phi_o, (0.0, 0.0, 0.0), h)
+    assert np.array_equal(t.cpu().numpy(), t_o)
+    assert np.max(np.abs(v.cpu().numpy() - v_o), initial=0.0) <= oracle.vertex_tolerance(v_o, h)
+    with pytest.raises(ValueError):
+        fgl.tsdf(cu(V), h, r, delta="p")
+
+
 def test_tsdf_cavities_and_degenerate_grids():
     V = hollow_sphere((40, 36, 45), (22.3, 17.6, 20.1), 9.0, 10.5)
     V[2:6, 2:6, 2:6] = 1
