@@ -526,12 +526,13 @@ def main():
     copts = fgl.BatchOpts(packet_rays=args.packet, block_threads=args.block, stack_smem=args.sdepth,
                           refill_min=args.refill, postpone_pct=args.postpone, count_work=1,
                           tri_mode=args.tri)
-    fgl.work_counters()
+    fgl.work_phase_counters()
     with torch.cuda.stream(stream):
         pose_state.copy_(walk_d[args.warmup % S])
     fgl.cast_batched(items, copts, stream=stream)
     fgl.sync(stream)
-    c_rays, c_nodes, c_tris = fgl.work_counters()
+    phases = fgl.work_phase_counters()
+    c_rays, c_nodes, c_tris = phases["rays"], phases["node_visits"], phases["tri_tests"]
     st = scene.stats()
     # eq. cost(r_j) as bytes: S_io = 8 B of output per ray (pose and direction
     # reads are broadcast across the rays of an environment and not counted)
@@ -569,7 +570,8 @@ def main():
                          "triangle tests x 48 B + 8 B of output per ray (counted in a pass "
                          "outside the timing); the kernel reads them from L1/L2, not HBM",
                 "node_visits_per_ray": round(c_nodes / max(1, c_rays), 2),
-                "tri_tests_per_ray": round(c_tris / max(1, c_rays), 2)}
+                "tri_tests_per_ray": round(c_tris / max(1, c_rays), 2),
+                "phases_per_ray": {k: round(v / max(1, c_rays), 4) for k, v in phases.items() if k != "rays"}}
     # measured traffic beside the cost model: DRAM bytes of one full launch and
     # L2 (lts__t_bytes) bytes per ray from the committed ncu captures, as rates;
     # the L2 rate against an L2 copy bandwidth measured here
