@@ -490,6 +490,15 @@ void worker_main(fgl_server_s* Sp) {
     // the copy stream follows the tick; the results of the requests it
     // finishes go back right behind it, with no host round trip in between
     cudaStreamWaitEvent(S.copy, t.done, 0);
+    if (status != FGL_OK) {
+      // every request with a chunk in a failed tick carries the error; the
+      // ones that continue still run their later chunks (their buffers are
+      // freed only after their last tick) and end with it
+      for (int64_t tk : S.active) {
+        Request& q = *S.reqs[tk];
+        if (q.last_tick == t.id && q.status == FGL_OK) q.status = status;
+      }
+    }
     for (int64_t tk : t.finishing) {
       Request& q = *S.reqs[tk];
       if (status != FGL_OK) {
