@@ -226,9 +226,12 @@ fgl_status fgl_cast_batched(const fgl_cast_item* items, int32_t n_items,
  * items[i].poses / out_range / out_tri -- and, when used, instance_poses,
  * out_instance and out_points -- are host pointers (page-locked for full
  * speed).  Copies the poses to library-owned device staging, runs the
- * batched kernels (instances and return points included), copies the results
- * back and synchronizes the stream.  Large batches run in up to 4 chunks of
- * whole environments whose copies back overlap the next chunk's cast. */
+ * batched kernels (instances and return points included) and synchronizes
+ * the stream.  When every item's out_range and out_tri are page-locked and
+ * it has no instances or points, the kernel stores the returns straight into
+ * them over the host link as it runs; otherwise the results are cast into
+ * device staging and copied back, large batches in up to 4 chunks of whole
+ * environments whose copies back overlap the next chunk's cast. */
 fgl_status fgl_cast_batched_host(const fgl_cast_item* items, int32_t n_items,
                                  const fgl_batch_opts* opts, fgl_stream stream);
 

@@ -494,6 +494,19 @@ fgl_status run_batched(const fgl_cast_item* items, int n, const Opts& o, cudaStr
   return FGL_OK;
 }
 
+// Whether p is page-locked host memory the current device can address, and
+// its device address.
+bool host_mapped(const void* p, void** dev) {
+  cudaPointerAttributes a;
+  if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (a.type != cudaMemoryTypeHost || !a.devicePointer) return false;
+  *dev = a.devicePointer;
+  return true;
+}
+
 }  // namespace
 
 namespace fgl {
@@ -870,6 +883,29 @@ fgl_status fgl_cast_batched_host(const fgl_cast_item* items, int32_t n_items,
     }
     if (items[i].out_instance) dev[i].out_instance = (int32_t*)((char*)c.d_io + inst_off[i]);
     if (items[i].out_points) dev[i].out_points = (float*)((char*)c.d_io + pts_off[i]);
+  }
+  // Page-locked (device-mapped) result buffers: the kernel stores the returns
+  // straight into them over the host link while it runs, so nothing is
+  // copied back after the cast.  Items with instances or return points keep
+  // the staged path (their later passes read the returns back).
+  bool mapped = true;
+  std::vector<void*> m_range(n_items), m_tri(n_items);
+  for (int i = 0; i < n_items && mapped; ++i) {
+    if (items[i].n_instances > 0 || items[i].out_points || items[i].out_instance) {
+      mapped = false;
+      break;
+    }
+    if (!items[i].n_env) continue;
+    mapped = host_mapped(items[i].out_range, &m_range[i]) && host_mapped(items[i].out_tri, &m_tri[i]);
+  }
+  if (mapped) {
+    for (int i = 0; i < n_items; ++i) {
+      dev[i].out_range = (float*)m_range[i];
+      dev[i].out_tri = (int32_t*)m_tri[i];
+    }
+    st = run_batched(dev.data(), n_items, o, s);
+    if (st != FGL_OK) return st;
+    return fgl_sync(stream);
   }
   // results of items [e0, e1) of item i back to the host on stream `cs`
   auto copy_back = [&](int i, size_t e0, size_t e1, cudaStream_t cs) -> fgl_status {

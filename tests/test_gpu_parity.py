@@ -377,8 +377,13 @@ def test_hetero_batch_full_ladder_vs_oracle():
 # chunks whose copies overlap the next chunk's cast for large ones -- both
 # bitwise equal to the device-buffer batched call
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("n_big,n_small", [(3, 5), (200, 100)])
-def test_host_entry_equals_device_batched(n_big, n_small):
+@pytest.mark.parametrize("n_big,n_small,pinned", [(3, 5, True), (200, 100, True), (3, 5, False),
+                                                  (200, 100, False)])
+def test_host_entry_equals_device_batched(n_big, n_small, pinned):
+    """Page-locked outputs take the path where the kernel stores the returns
+    straight into host memory; pageable ones the staged path (one launch for
+    small batches, overlapped chunks for large ones).  Both equal the
+    device-buffer call bit for bit."""
     v, t, obs = synth.tiny_room_scene(6)
     scene = fgl.Scene(v, t)
     big = fgl.Sensor.from_table(synth.grid_sensor(32, -16.0, 15.0, 1800))
@@ -387,10 +392,11 @@ def test_host_entry_equals_device_batched(n_big, n_small):
     Pb = synth.sample_free_pose(rng, obs, n_big, upright=False)
     Ps = synth.sample_free_pose(rng, obs, n_small, upright=False)
     n_rays = n_big * big.n_rays + n_small * small.n_rays
-    hb_r = torch.empty(n_big * big.n_rays, dtype=torch.float32).pin_memory()
-    hb_i = torch.empty(n_big * big.n_rays, dtype=torch.int32).pin_memory()
-    hs_r = torch.empty(n_small * small.n_rays, dtype=torch.float32).pin_memory()
-    hs_i = torch.empty(n_small * small.n_rays, dtype=torch.int32).pin_memory()
+    pin = (lambda t: t.pin_memory()) if pinned else (lambda t: t)
+    hb_r = pin(torch.empty(n_big * big.n_rays, dtype=torch.float32))
+    hb_i = pin(torch.empty(n_big * big.n_rays, dtype=torch.int32))
+    hs_r = pin(torch.empty(n_small * small.n_rays, dtype=torch.float32))
+    hs_i = pin(torch.empty(n_small * small.n_rays, dtype=torch.int32))
     hb_r.fill_(-7.0)
     hs_i.fill_(-7)
     stream = torch.cuda.Stream()
