@@ -370,6 +370,8 @@ class SlotPlan:
             a = 0
         self.next[sc] = a + n_env
         src = self.sources[sc]
+        if n_env > src.shape[0]:
+            raise ValueError("a request needs more environments than its pose source holds")
         off = int(self.rng.integers(0, src.shape[0] - n_env + 1))
         return self.first[sc] + a, src[off:off + n_env]
 
@@ -1541,7 +1543,10 @@ def run_serve(args):
     pool = {m: _poses.sample_free_pose(rng, spec.obstacles, 2048, margin=0.25)
             for m, spec in enumerate(meshes)}
     dev = torch.device("cuda", torch.cuda.current_device())
-    pool_d = [torch.from_numpy(pool[m]).to(dev) for m in range(len(meshes))]
+    # device pose sources, the 2,048 free poses of each scene repeated to 8,192
+    # so that a request of up to 4,096 environments takes a contiguous slice
+    pool_d = [torch.from_numpy(np.ascontiguousarray(np.concatenate([pool[m]] * 4))).to(dev)
+              for m in range(len(meshes))]
     n_rays_of = [s.n_rays for s in all_sensors]
     pick = lambda r, sc: int(r.integers(len(all_sensors)))
     arena = OutputArena(24 << 30)
