@@ -54,7 +54,9 @@ WORKLOAD = ("batched_walk: 4096 envs x (16 beams -15..+15 deg x 360 az) = 23,592
 # the sources each profiled kernel is built from: a committed ncu figure is
 # used only while its kernel's sources are unchanged
 KERNEL_SOURCES = {
-    "k_persistent": ["paper_2509_17390_gb300/csrc/trace.cuh", "paper_2509_17390_gb300/csrc/kernels.cu"],
+    # the wide kernel's work per ray also depends on the tree its builder makes
+    "k_persistent": ["paper_2509_17390_gb300/csrc/trace.cuh", "paper_2509_17390_gb300/csrc/kernels.cu",
+                     "paper_2509_17390_gb300/csrc/bvh_build.cpp"],
     "k_lbvh_cast": ["paper_2509_17390_gb300/csrc/trace.cuh", "paper_2509_17390_gb300/csrc/lbvh.cu"],
 }
 
