@@ -46,3 +46,45 @@ def test_clock_summary_falls_back_to_all_samples(tmp_path):
     s = _sampler(tmp_path, rows, 0, 40).summary()
     assert s["samples"] == 2 and s["samples_in_timed_region"] == 0
     assert s["reasons"] == ["hw_thermal_slowdown"] and s["sm_mhz"] == 2025.0
+
+
+class _FakeServer:
+    """Stands in for fgl.Server in the slot-plan tests (no GPU)."""
+
+    def __init__(self):
+        self.n = 0
+        self.added = []
+
+    def add_envs(self, poses):
+        first = self.n
+        self.n += len(poses)
+        self.added.append(poses)
+        return first
+
+
+def test_slot_plan_rings_and_sources():
+    """Each scene owns a ring of slots; a request takes the next n_env slots
+    of its scene's ring (wrapping to the start when it would run past the
+    end) and a contiguous slice of that scene's pose source."""
+    torch = __import__("pytest").importorskip("torch")
+    import numpy as np
+    src = [torch.arange(10 * 12, dtype=torch.float32).reshape(10, 3, 4),
+           torch.zeros(6, 3, 4)]
+    srv = _FakeServer()
+    plan = bench.SlotPlan(srv, src, 8, seed=1)
+    assert srv.n == 16 and plan.first == [0, 8]
+    assert np.array_equal(srv.added[0][:8], src[0][:8].numpy())          # initial poses from the source
+    assert np.array_equal(srv.added[1][6:], src[1][:2].numpy())          # a short source repeats
+    f, v = plan.take(0, 5)
+    assert f == 0 and v.shape == (5, 3, 4)
+    f, v = plan.take(0, 3)
+    assert f == 5
+    f, v = plan.take(0, 2)                                               # 8 + 2 > 8: back to the start
+    assert f == 0
+    f, v = plan.take(1, 4)
+    assert f == 8
+    with __import__("pytest").raises(ValueError):
+        plan.take(1, 7)                                                  # more than its source holds
+    trace = [(0.1, 0, 0, np.zeros((3, 3, 4), np.float32)), (0.2, 1, 0, np.zeros((2, 3, 4), np.float32))]
+    st = bench.slot_trace(trace, bench.SlotPlan(_FakeServer(), src, 8, seed=2))
+    assert [e[3] for e in st] == [None, None] and [e[4][1].shape[0] for e in st] == [3, 2]
