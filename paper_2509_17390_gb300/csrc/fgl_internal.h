@@ -73,6 +73,8 @@ constexpr int kTriFloats = 12;
 constexpr int kStackLocal = 64;
 // Work counters of count_work launches (see g_counters in kernels.cu).
 constexpr int kWorkCounters = 8;
+// Warps a traversal block may hold (block_threads <= 512).
+constexpr int kMaxBlockWarps = 16;
 constexpr int kMaxWideDepth = 30;
 
 struct HostBVH {

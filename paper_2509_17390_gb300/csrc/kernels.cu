@@ -138,29 +138,44 @@ __global__ void __maxnreg__(72) k_persistent(BatchHeader* __restrict__ hdr,
   const unsigned FULL = 0xFFFFFFFFu;
   const Smem<W> sm = smem_layout<W>(sdepth);
   const int lane = threadIdx.x & 31;
-  const int64_t n_packets = hdr->n_packets;
-  const int n_items = hdr->n_items;
-  const int P = hdr->packet_rays;
   uint2 ls[kStackLocal];
   Keys lq[kStackLocal];
   const dev::StackRefs<Keys> st{sm.ss, sm.sq, ls, lq, (int)blockDim.x, sdepth};
 
-  // warp-uniform packet cursor
-  int pk_item = 0, pk_env = 0, pk_next = 0, pk_end = 0;
-  bool drained = false;
+  // The warp's packet cursor (item, environment, next ray, end ray) and its
+  // drained flag live in shared memory between refills, and the batch header
+  // is re-read at refill time: registers stay free for the traversal (the
+  // kernel runs under a 72-register cap).
+  __shared__ int4 s_cur[kMaxBlockWarps];
+  __shared__ int s_drained[kMaxBlockWarps];
+  const int wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    s_cur[wid] = make_int4(0, 0, 0, 0);
+    s_drained[wid] = 0;
+  }
+  __syncwarp();
   // lane state
   dev::Tracer<W, COUNT, TMIN> tr;
   tr.tg = make_uint2(0u, 0u);
   tr.ng = make_uint2(0u, 0u);
   if (COUNT) tr.n_nodes = tr.n_tris = tr.n_rounds = tr.n_pops = 0;
   bool active = false;
-  float* out_r = nullptr;
-  int32_t* out_t = nullptr;
+  int out_item = 0;    // the lane's ray: its item and output offset
+  int64_t out_o = 0;
   uint32_t c_rays = 0, c_nodes = 0, c_tris = 0, c_iters = 0, c_lane_iters = 0, c_refills = 0;
 
   for (;;) {
     unsigned idle = __ballot_sync(FULL, !active);
-    if (!drained && (idle == FULL || __popc(idle) >= refill_min)) {
+    if (!s_drained[wid] && (idle == FULL || __popc(idle) >= refill_min)) {
+      const int64_t n_packets = hdr->n_packets;
+      const int n_items = hdr->n_items;
+      const int P = hdr->packet_rays;
+      int4 cur = s_cur[wid];
+      int& pk_item = cur.x;
+      int& pk_env = cur.y;
+      int& pk_next = cur.z;
+      int& pk_end = cur.w;
+      bool drained = false;
       while (idle) {
         if (pk_next >= pk_end) {
           unsigned long long p = 0;
@@ -204,18 +219,23 @@ __global__ void __maxnreg__(72) k_persistent(BatchHeader* __restrict__ hdr,
             tr.n_nodes = tr.n_tris = 0;
           }
           tr.start(it.nodes, it.tris, it.min_range, it.max_range, it.n_nodes, it.n_tris);
-          const int64_t o = (int64_t)pk_env * it.n_rays + __float_as_int(ds.w);
-          out_r = it.out_range + o;
-          out_t = it.out_tri + o;
+          out_o = (int64_t)pk_env * it.n_rays + __float_as_int(ds.w);
+          out_item = pk_item;
           active = true;
         }
         pk_next += min(__popc(idle), avail);
         idle = __ballot_sync(FULL, !active);
       }
+      __syncwarp();
+      if (lane == 0) {
+        s_cur[wid] = cur;
+        s_drained[wid] = drained ? 1 : 0;
+      }
+      __syncwarp();
     }
     const unsigned act = __ballot_sync(FULL, active);
     if (act == 0) {
-      if (drained) break;
+      if (s_drained[wid]) break;
       continue;
     }
     bool fin = false;
@@ -243,8 +263,8 @@ __global__ void __maxnreg__(72) k_persistent(BatchHeader* __restrict__ hdr,
       float rg;
       int32_t id;
       tr.result(rg, id);
-      __stcs(out_r, rg);  // evict-first: keep L2 for the BVH
-      __stcs(out_t, id);
+      __stcs(items[out_item].out_range + out_o, rg);  // evict-first: keep L2 for the BVH
+      __stcs(items[out_item].out_tri + out_o, id);
       active = false;
       if (COUNT) ++c_rays;
     }
