@@ -1,11 +1,13 @@
 """GPU tests of the batching runtime: autotuner and serving loop.
 
 The serving contract: every request's result is the same as casting it
-alone (bitwise here; the task's contract only asks for the tolerance), under
-continuous batching with other requests of different sizes, with eviction
-under a small HBM budget, and with host-side faults (injected allocation
-failures, cancellations, malformed requests) affecting only their own
-requests.
+alone (bitwise here; the parity contract only asks for the range tolerance),
+under continuous batching with other requests of different sizes, with
+eviction under a small HBM budget, with poses kept in the server's
+device-resident environment slots and updated from host or device memory,
+and with host-side faults (injected allocation failures, cancellations,
+malformed requests) affecting only their own requests.  The served mix of the
+heterogeneous scenes is also checked against the FP64 oracle.
 """
 
 import os
