@@ -806,11 +806,34 @@ def hetero_setup(fgl, seed=4, n_env=256, ladder=None):
             if best is None or res["best_ms"] < best[1]:
                 best = (W, res["best_ms"])
         widths[m] = best[0] if best else 8
+    # mixed widths cost one launch (and one drain) per width: keep the mix only
+    # if it beats a single width over the whole batch
+    def batch_ms(ws_, reps=3):
+        its = items_for(ws_)
+        arr_ = fgl.make_items(its)
+        o = fgl.BatchOpts(use_graph=1)
+        for _ in range(2):
+            fgl.cast_batched(its, o, stream=stream, arr=arr_)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fgl.cast_batched(its, o, stream=stream, arr=arr_)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+    if len(set(widths.values())) > 1:
+        cands = {"mixed": dict(widths), "all 8": {m: 8 for m in widths}, "all 4": {m: 4 for m in widths}}
+        timed = {k: batch_ms(v) for k, v in cands.items()}
+        widths = cands[min(timed, key=timed.get)]
+        width_choice = {k: round(v, 3) for k, v in timed.items()}
+    else:
+        width_choice = None
     items = items_for(widths)
     opts, tune = fgl.autotune(items, fgl.BatchOpts(use_graph=1), reps=3, passes=2, stream=stream)
     info = {"meshes": [{"tris": int(len(sp.tris)), "gaussians": sp.n_gauss, "voxel_m": sp.voxel,
                         "width": widths[m]} for m, sp in enumerate(meshes)],
             "mesher_s": round(t_mesh, 2), "bvh_build_s": round(t_build, 1),
+            "width_choice_ms": width_choice,
             "autotune": {"opts": opts.as_dict(), "best_ms": round(tune["best_ms"], 3),
                          "start_ms": round(tune["start_ms"], 3), "trials": tune["trials"]}}
     return meshes, tables, envs, groups, scenes, sensors, widths, items, opts, stream, info
