@@ -615,6 +615,28 @@ def main():
                            "frac": max(meas.values()) if meas else None,
                            "fractions": {"hbm_cost_model": roofline["frac"], **meas}}
 
+    # the optional sensor effects (dropout 5%, range noise 1 cm + 0.1%) on one
+    # step's returns, timed alone: an HBM-bound pass, 8 B read + 8 B written a
+    # return (the noise and the dropout decisions are drawn per hit)
+    ev_fx = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    fx_ms = []
+    for k in range(4):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0xFF)
+            ev_fx[0].record(stream)
+        fgl.apply_sensor_effects(out_r, out_i, n_env, seed=7, step=k, drop_prob=0.05, sigma0=0.01,
+                                 sigma1=0.001, max_range=w.max_range, stream=stream)
+        with torch.cuda.stream(stream):
+            ev_fx[1].record(stream)
+        ev_fx[1].synchronize()
+        if k:
+            fx_ms.append(ev_fx[0].elapsed_time(ev_fx[1]))
+    fx_s = float(np.mean(fx_ms)) / 1e3
+    effects = {"kernel": "k_effects", "ms": round(fx_s * 1e3, 4), "bound": "hbm",
+               "achieved": round(16 * n_rays / fx_s / 1e9, 1), "peak": peak, "unit": "GB/s",
+               "frac": round(16 * n_rays / fx_s / 1e9 / peak, 4),
+               "basis": "at most 8 B read + 8 B written per return (misses: 4 B read), L2 flushed before each pass"}
+
     # per-env launch (plain form): one fgl_cast per environment
     per_env = None
     if not args.no_per_env:
@@ -699,7 +721,8 @@ def main():
                        "between timed steps (256 MiB write)", "bvh_width": st["width"],
                        "opts": opts.as_dict(), "scene_tris": st["n_tris"],
                        "rays_per_step": n_rays, "frames_per_s": round(ws * n_env / (ms / 1e3), 1)},
-            "gpu_launches": args.steps, "roofline": roofline, "roofline_issue": roofline_issue, "e2e": e2e,
+            "gpu_launches": args.steps, "roofline": roofline, "roofline_issue": roofline_issue,
+            "sensor_effects": effects, "e2e": e2e,
             "per_env_launch": per_env, "served": served, "cpu_baseline": cpu, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

@@ -166,7 +166,7 @@ __global__ void __maxnreg__(72) k_persistent(BatchHeader* __restrict__ hdr,
 
   for (;;) {
     unsigned idle = __ballot_sync(FULL, !active);
-    if (!s_drained[wid] && (idle == FULL || __popc(idle) >= refill_min)) {
+    if ((idle == FULL || __popc(idle) >= refill_min) && !s_drained[wid]) {
       const int64_t n_packets = hdr->n_packets;
       const int n_items = hdr->n_items;
       const int P = hdr->packet_rays;
