@@ -70,7 +70,7 @@ typedef struct fgl_sensor_s* fgl_sensor;
 
 typedef struct {
   int32_t width;      /* children per BVH node: 4 or 8 (0 = 8) */
-  int32_t sah_bins;   /* binned-SAH bins per axis (0 = 32) */
+  int32_t sah_bins;   /* binned-SAH bins per axis (0 = 128) */
   int32_t n_threads;  /* host build threads (0 = all cores) */
   int32_t upload;     /* 1 = upload to the current CUDA device (default when
                          opts is NULL); 0 = host-only build (tests, offline) */

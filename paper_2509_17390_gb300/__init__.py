@@ -175,7 +175,7 @@ def _dev_ptr(t, dtype_name: str, numel: int, what: str) -> int:
 class Scene:
     """A triangle mesh with its wide BVH (fgl_scene_build)."""
 
-    def __init__(self, verts, tris, width: int = 8, sah_bins: int = 32, n_threads: int = 0,
+    def __init__(self, verts, tris, width: int = 8, sah_bins: int = 0, n_threads: int = 0,
                  upload: bool = True):
         v = np.ascontiguousarray(verts, np.float32).reshape(-1, 3)
         t = np.ascontiguousarray(tris, np.int32).reshape(-1, 3)

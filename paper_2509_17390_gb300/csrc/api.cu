@@ -548,7 +548,7 @@ fgl_status fgl_scene_build(const float* verts, int64_t nv, const int32_t* tris, 
   *out = nullptr;
   if (!verts || !tris) return fail(FGL_ERR_INVALID, "null vertex or triangle pointer");
   if (nv < 1 || nt < 1) return fail(FGL_ERR_INVALID, "mesh needs at least one vertex and triangle");
-  int width = 8, bins = 32, threads = 0, upload = 1;
+  int width = 8, bins = 128, threads = 0, upload = 1;
   if (opts) {
     if (opts->width) width = opts->width;
     if (opts->sah_bins) bins = opts->sah_bins;

@@ -314,7 +314,7 @@ int build_bvh(const float* V, int64_t nv, const int32_t* T, int64_t nt, int widt
     *err = "too many triangles (max 2^30)";
     return 1;
   }
-  if (bins <= 1) bins = 32;
+  if (bins <= 1) bins = 128;
   if (threads <= 0) threads = (int)std::max(1u, std::thread::hardware_concurrency());
 
   std::vector<Box> tbox(nt);
