@@ -548,7 +548,7 @@ fgl_status fgl_scene_build(const float* verts, int64_t nv, const int32_t* tris, 
   *out = nullptr;
   if (!verts || !tris) return fail(FGL_ERR_INVALID, "null vertex or triangle pointer");
   if (nv < 1 || nt < 1) return fail(FGL_ERR_INVALID, "mesh needs at least one vertex and triangle");
-  int width = 8, bins = 128, threads = 0, upload = 1;
+  int width = 8, bins = 0, threads = 0, upload = 1;  // bins 0: the builder's default
   if (opts) {
     if (opts->width) width = opts->width;
     if (opts->sah_bins) bins = opts->sah_bins;
@@ -556,7 +556,7 @@ fgl_status fgl_scene_build(const float* verts, int64_t nv, const int32_t* tris, 
     upload = opts->upload;
   }
   if (width != 4 && width != 8) return fail(FGL_ERR_INVALID, "width must be 4 or 8");
-  if (bins < 2 || bins > 256) return fail(FGL_ERR_INVALID, "sah_bins must be in [2, 256]");
+  if (bins != 0 && (bins < 2 || bins > 256)) return fail(FGL_ERR_INVALID, "sah_bins must be in [2, 256]");
   std::unique_ptr<fgl_scene_s> s(new (std::nothrow) fgl_scene_s());
   if (!s) return fail(FGL_ERR_OOM, "host allocation failed");
   std::string err;
