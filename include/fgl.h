@@ -82,21 +82,22 @@ typedef struct {
   int64_t node_bytes;   /* bytes of the node array (node_stride * n_nodes) */
   int64_t tri_bytes;    /* bytes of the leaf triangle array (48 * n_tris) */
   int32_t width;        /* children per node */
-  int32_t node_stride;  /* bytes per node record (112 for width 8, 64 for 4) */
+  int32_t node_stride;  /* bytes per node record (256 for width 8, 144 for 4) */
   int32_t depth;        /* levels of the wide tree (root = 1) */
   int32_t resident;     /* 1 when the arrays are on the device */
   double sah_cost;      /* SAH cost of the wide tree (node visits + tri tests, area-weighted) */
   double build_ms;      /* host build time */
   float bounds_lo[3];   /* scene bounds */
   float bounds_hi[3];
-  float margin;         /* outward margin added to every quantized child box (metres) */
+  float margin;         /* outward margin added to every child box (metres) */
 } fgl_scene_stats;
 
 /* Build a scene from a triangle mesh (the mesh M of eq. t_j*).
  *   verts: host float32 [nv][3]; tris: host int32 [nt][3] vertex ids.
  *   Builds a binned-SAH binary BVH, collapses it to `width`-wide nodes with
- *   8-bit child boxes rounded outward (plus a margin covering float32
- *   rounding of the traversal's slab test), re-orders triangles into leaf
+ *   float32 child boxes stored as offsets from the node corner, rounded
+ *   outward (plus a margin covering float32 rounding of the traversal's
+ *   slab test), re-orders triangles into leaf
  *   order (48 bytes each) and, when opts->upload != 0, copies both arrays to
  *   the current device (synchronously).  The scene owns its device memory
  *   until fgl_scene_destroy and keeps its host copy for re-upload.
@@ -109,9 +110,10 @@ fgl_status fgl_scene_get_stats(fgl_scene scene, fgl_scene_stats* out);
 /* Copy the host node / triangle arrays (sizes from the stats) -- for tests. */
 fgl_status fgl_scene_export(fgl_scene scene, void* nodes, int64_t node_bytes, void* tris,
                             int64_t tri_bytes);
-/* Check, with the float32 decode arithmetic of the traversal, that every
- * quantized child box contains its subtree's triangles grown by the margin
- * plus one quantum of that node's axis scale.
+/* Check, in double arithmetic, that every child box (node corner plus the
+ * stored float offsets) contains its subtree's triangles grown by the
+ * margin, and the tree's structure (child indices, hit bits, every
+ * triangle referenced once).
  * Writes the number of violations to *n_bad (0 for a correct build). */
 fgl_status fgl_scene_verify(fgl_scene scene, int64_t* n_bad);
 /* Upload (if evicted) / drop the device copy, keeping the host copy. */

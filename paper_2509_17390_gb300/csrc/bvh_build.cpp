@@ -1,15 +1,17 @@
 // Host BVH builder: binned-SAH binary tree -> SAH-optimal collapse to W-wide nodes
-// -> octant codes -> 8-bit quantized child boxes rounded outward.
+// -> octant codes -> float32 child boxes relative to the node corner, rounded
+// outward.
 //
 // The paper traverses a triangle LBVH built with Karras' method (Sec. IV-C,
 // "GPU-accelerated ray-casting"; Sec. IV-A for the LBVH routine).  Here the
 // tree is built once per scene on the host with the surface-area heuristic,
 // which gives fewer node visits per ray (the N_nodes term of eq. cost(r_j)),
-// and stored as compressed wide nodes so that one 112-byte read tests eight
-// children (the "memory layout" point at the end of Sec. IV-C).
+// and stored as wide nodes whose child planes sit in six contiguous blocks,
+// so that a ray loads its near and far planes of eight children with twelve
+// 16-byte reads and tests them with no decoding (the "memory layout" point at
+// the end of Sec. IV-C).
 //
-// Compiled without FMA contraction; the one fused operation the traversal
-// relies on (box decode) is written as std::fmaf explicitly.
+// Compiled without FMA contraction, so every bound is computed as written.
 
 #include <algorithm>
 #include <atomic>
@@ -221,7 +223,17 @@ void assign_codes(const std::vector<Box>& kids, const Box& parent, int width,
   }
 }
 
-inline float decode(uint8_t q, float scale, float p) { return std::fmaf((float)q, scale, p); }
+// Nearest float at or below / at or above x.
+inline float float_down(double x) {
+  float f = (float)x;
+  if ((double)f > x) f = std::nextafterf(f, -std::numeric_limits<float>::infinity());
+  return f;
+}
+inline float float_up(double x) {
+  float f = (float)x;
+  if ((double)f < x) f = std::nextafterf(f, std::numeric_limits<float>::infinity());
+  return f;
+}
 
 // SAH-optimal collapse of the binary tree into W-wide nodes, by dynamic
 // programming over the binary nodes (the conversion of Ylitie, Karras &
@@ -348,8 +360,9 @@ int build_bvh(const float* V, int64_t nv, const int32_t* T, int64_t nt, int widt
     for (int a = 0; a < 3; ++a) cen[3 * k + a] = 0.5f * b.lo[a] + 0.5f * b.hi[a];
     scene.grow(b);
   }
-  // Outward margin on every quantized box: covers the float32 rounding of
-  // the traversal's slab test for ray origins with coordinates up to M.
+  // Outward margin on every child box: covers the float32 rounding of the
+  // traversal's slab test for ray origins with coordinates up to M (that
+  // rounding moves a plane by a few units of 2^-24 M).
   const double margin = std::ldexp(M, -17);
 
   BinaryBuilder bb(tbox, cen, nt, bins, threads);
@@ -440,53 +453,27 @@ int build_bvh(const float* V, int64_t nv, const int32_t* T, int64_t nt, int widt
       return 1;
     }
 
-    // ---- quantize the child boxes ----------------------------------------
-    // Each decoded child box must contain the child's content grown by the
-    // margin plus one quantum 2^k on every side (the traversal's plane
-    // offsets round by up to half a quantum).
+    // ---- child boxes as float offsets from the node corner ----------------
+    // p = the children's lowest planes less the margin, rounded down to a
+    // float; each child plane is p + off with off a float rounded outward, so
+    // that the exact sum p + off bounds the child's content grown by the
+    // margin on every side.
     float p[3];
-    int e[3];
-    uint8_t q[6][8];
-    std::memset(q, 0, sizeof(q));
+    float pln[6][8];
+    std::memset(pln, 0, sizeof(pln));
     for (int a = 0; a < 3; ++a) {
-      double lo_c = std::numeric_limits<double>::infinity(), hi_c = -lo_c;
+      double lo_c = std::numeric_limits<double>::infinity();
+      for (int i = 0; i < n; ++i) lo_c = std::min(lo_c, (double)kb[i].lo[a] - margin);
+      const float pa = float_down(lo_c);
       for (int i = 0; i < n; ++i) {
-        lo_c = std::min(lo_c, (double)kb[i].lo[a] - margin);
-        hi_c = std::max(hi_c, (double)kb[i].hi[a] + margin);
-      }
-      int k = (int)std::ceil(std::log2((hi_c - lo_c) / 253.0));
-      k = std::max(k, -126);
-      float pa = 0.f;
-      for (;; ++k) {
-        if (k > 120) {
-          *err = "scene extent too large to quantize";
-          return 1;
-        }
-        const float scale = std::ldexp(1.0f, k);
-        const double sq = (double)scale;
-        pa = (float)(lo_c - sq);
-        if ((double)pa > lo_c - sq) pa = std::nextafterf(pa, -std::numeric_limits<float>::infinity());
-        bool ok = true;
-        for (int j = 0; j < n && ok; ++j) {
-          int i = pos[j];
-          const double lt = (double)kb[i].lo[a] - margin - sq;
-          const double ht = (double)kb[i].hi[a] + margin + sq;
-          double ql = std::floor((lt - (double)pa) / sq);
-          double qh = std::ceil((ht - (double)pa) / sq);
-          ql = std::max(0.0, std::min(255.0, ql));
-          while (ql > 0 && (double)decode((uint8_t)ql, scale, pa) > lt) ql -= 1.0;
-          if ((double)decode((uint8_t)ql, scale, pa) > lt) ok = false;
-          if (qh < 0) qh = 0;
-          while (qh <= 255 && (double)decode((uint8_t)std::min(qh, 255.0), scale, pa) < ht) qh += 1.0;
-          if (qh > 255) ok = false;
-          if (!ok) break;
-          q[a][code[i]] = (uint8_t)ql;
-          q[3 + a][code[i]] = (uint8_t)qh;
-        }
-        if (ok) break;
+        const double lt = (double)kb[i].lo[a] - margin, ht = (double)kb[i].hi[a] + margin;
+        float ol = float_down(lt - (double)pa), oh = float_up(ht - (double)pa);
+        while ((double)pa + (double)ol > lt) ol = std::nextafterf(ol, -std::numeric_limits<float>::infinity());
+        while ((double)pa + (double)oh < ht) oh = std::nextafterf(oh, std::numeric_limits<float>::infinity());
+        pln[a][code[i]] = ol;
+        pln[3 + a][code[i]] = oh;
       }
       p[a] = pa;
-      e[a] = k + 127;
     }
 
     size_t off = nodes.size();
@@ -495,13 +482,12 @@ int build_bvh(const float* V, int64_t nv, const int32_t* T, int64_t nt, int widt
     std::memcpy(rec + 0, &p[0], 4);
     std::memcpy(rec + 4, &p[1], 4);
     std::memcpy(rec + 8, &p[2], 4);
-    uint32_t packed = (uint32_t)e[0] | ((uint32_t)e[1] << 8) | ((uint32_t)e[2] << 16) | (imask << 24);
-    std::memcpy(rec + 12, &packed, 4);
+    std::memcpy(rec + 12, &imask, 4);
     uint32_t cb = (uint32_t)child_base, tb = (uint32_t)tri_base;
     std::memcpy(rec + 16, &cb, 4);
     std::memcpy(rec + 20, &tb, 4);
+    for (int r = 0; r < 6; ++r) std::memcpy(rec + node_plane_offset() + 4 * r * W, pln[r], 4 * W);
     std::memcpy(rec + node_hb_offset(W), hb, 4 * W);
-    for (int r = 0; r < 6; ++r) std::memcpy(rec + node_q_offset(W) + r * W, q[r], W);
   }
 
   if (max_depth > kMaxWideDepth) {
@@ -543,17 +529,12 @@ int64_t verify_bvh(const HostBVH& b, std::string* first_error) {
   for (int64_t ni = N - 1; ni >= 0; --ni) {
     const uint8_t* rec = b.nodes.data() + ni * S;
     float p[3];
-    uint32_t packed, cbase, tbase;
+    uint32_t imask, cbase, tbase;
     std::memcpy(p, rec, 12);
-    std::memcpy(&packed, rec + 12, 4);
+    std::memcpy(&imask, rec + 12, 4);
     std::memcpy(&cbase, rec + 16, 4);
     std::memcpy(&tbase, rec + 20, 4);
-    uint32_t imask = packed >> 24;
-    float scale[3];
-    for (int a = 0; a < 3; ++a) {
-      uint32_t bits = ((packed >> (8 * a)) & 0xFFu) << 23;
-      std::memcpy(&scale[a], &bits, 4);
-    }
+    if (imask >> W) fail("imask has bits beyond the node width at node " + std::to_string(ni));
     Box all;
     all.reset();
     for (int j = 0; j < W; ++j) {
@@ -595,10 +576,11 @@ int64_t verify_bvh(const HostBVH& b, std::string* first_error) {
         }
       }
       for (int a = 0; a < 3; ++a) {
-        float dlo = decode(rec[node_q_offset(W) + a * W + j], scale[a], p[a]);
-        float dhi = decode(rec[node_q_offset(W) + (3 + a) * W + j], scale[a], p[a]);
-        const double g = m + (double)scale[a];  // margin plus one quantum
-        if (!((double)dlo <= (double)cbx.lo[a] - g) || !((double)dhi >= (double)cbx.hi[a] + g))
+        float olo, ohi;
+        std::memcpy(&olo, rec + node_plane_offset() + 4 * (a * W + j), 4);
+        std::memcpy(&ohi, rec + node_plane_offset() + 4 * ((3 + a) * W + j), 4);
+        const double dlo = (double)p[a] + (double)olo, dhi = (double)p[a] + (double)ohi;
+        if (!(dlo <= (double)cbx.lo[a] - m) || !(dhi >= (double)cbx.hi[a] + m))
           fail("child box does not contain its content (node " + std::to_string(ni) + ", pos " +
                std::to_string(j) + ", axis " + std::to_string(a) + ")");
       }

@@ -21,13 +21,14 @@ void record_error(int status, const char* msg);
 // Wide BVH node record (W children, W in {4, 8}); 16-byte aligned so the
 // traversal reads it with 16-byte vector loads.
 //
-//   bytes  0..15 : float px, py, pz          quantization origin (node corner)
-//                  uint32  ex | ey<<8 | ez<<16 | imask<<24
-//                          e* = biased float exponent of the per-axis scale
-//                          2^(e-127); imask bit c set when the child with
-//                          octant code c is an internal node
-//   bytes 16..23 : uint32 child_base         node index of the first internal child
+//   bytes  0..15 : float px, py, pz          node corner: the origin of the child planes
+//                  uint32 imask              bit c set when the child in slot c is an
+//                                            internal node (bits >= W zero)
+//   bytes 16..31 : uint32 child_base         node index of the first internal child
 //                  uint32 tri_base           index of the node's first leaf triangle
+//                  8 bytes zero
+//   planes       : float off[6][W]           child boxes as offsets from the corner, in
+//                                            six blocks: lo_x, lo_y, lo_z, hi_x, hi_y, hi_z
 //   hit bits     : uint32 hb[W]              per child slot, the bits a hit on that
 //                                             child contributes to the traversal's
 //                                             group words: internal child in slot c:
@@ -35,16 +36,16 @@ void record_error(int status, const char* msg);
 //                                             unary triangle count (1, 3, 7), off =
 //                                             offset of its first triangle from
 //                                             tri_base (off + count <= 24); empty: 0
-//   quantized    : uint8 q[6][W]             child boxes in units of the scale:
-//                                             lo_x, lo_y, lo_z, hi_x, hi_y, hi_z
 //
-//   width 8 (112 B): hb at bytes 80..111, q at 32..79, bytes 24..31 zero
-//   width 4 ( 64 B): hb at bytes 24..39, q at 40..63
+//   width 8 (256 B): planes at bytes 32..223, hb at 224..255
+//   width 4 (144 B): planes at bytes 32..127, hb at 128..143
 //
-// Decoding a box coordinate is fmaf(q, 2^(e-127), p) in float32; the builder
-// rounds outward so that every decoded child box contains the child's content
-// grown by `margin` plus one quantum 2^(e-127) on every side, and verifies the
-// decoded boxes with exactly that arithmetic.
+// The builder rounds every offset outward so that the exact sum p + off
+// bounds the child's content grown by `margin` on every side, and verifies
+// that with double arithmetic.  The traversal takes a plane's ray parameter
+// as fma(off, 1/d, (p - o) * (1/d)) in float32; its rounding moves a plane by
+// a few units of 2^-24 times the coordinates involved, which the margin
+// covers.  Empty slots have hb = 0 (their planes are never used).
 //
 // Every child sits in the slot equal to its octant code c (width 8: bits
 // x, y, z; width 4: bits x, y), so slots of a partly filled node may be empty.
@@ -58,9 +59,10 @@ void record_error(int status, const char* msg);
 constexpr int kMaxLeafTris = 3;
 constexpr int kMaxNodeTris = 24;
 
-FGL_HD constexpr int node_stride(int width) { return width == 8 ? 112 : 64; }
-FGL_HD constexpr int node_hb_offset(int width) { return width == 8 ? 80 : 24; }
-FGL_HD constexpr int node_q_offset(int width) { return width == 8 ? 32 : 40; }
+FGL_HD constexpr int node_plane_offset() { return 32; }
+FGL_HD constexpr int node_hb_offset(int width) { return 32 + 24 * width; }
+FGL_HD constexpr int node_stride(int width) { return node_hb_offset(width) + 4 * width; }
+static_assert(node_stride(8) == 256 && node_stride(4) == 144, "node record sizes");
 
 // Leaf triangle record: 3 x float4 = 48 bytes
 //   {v0.x, v0.y, v0.z, id as int bits}, {v1.xyz, 0}, {v2.xyz, 0}
@@ -79,7 +81,7 @@ constexpr int kMaxWideDepth = 30;
 
 struct HostBVH {
   int width = 8;
-  int stride = 80;
+  int stride = node_stride(8);
   int64_t n_tris = 0;
   int64_t n_nodes = 0;
   int depth = 0;

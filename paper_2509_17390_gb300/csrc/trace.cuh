@@ -5,8 +5,8 @@
 // Result determinism: every (ray, triangle) pair is evaluated with the same
 // float32 operations wherever it happens, and the kept hit is the
 // lexicographic minimum of (t, triangle id); boxes are culled only when their
-// entry exceeds the best t strictly, and quantized boxes are conservative
-// with a margin, so no variant (width, stack split, packet shape, postponing,
+// entry exceeds the best t strictly, and child boxes are conservative with
+// a margin, so no variant (width, stack split, packet shape, postponing,
 // batching) can change a result.
 #pragma once
 
@@ -20,12 +20,6 @@ namespace fgl {
 namespace dev {
 
 constexpr int32_t kNoHit = 0x7FFFFFFF;
-
-// Byte `sel & 3` of `w` placed under the exponent of 2^23: the float
-// 2^23 + b, exactly.  The traversal folds the -2^23 into its plane offsets.
-__device__ __forceinline__ float byte_magic(uint32_t w, uint32_t sel) {
-  return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7440u | sel));
-}
 
 __device__ __forceinline__ float sel3(float x, float y, float z, uint32_t k) {
   return k == 0 ? x : (k == 1 ? y : z);
@@ -190,68 +184,74 @@ __device__ __forceinline__ bool key_any(const uint4& k) {
 // (triangle groups use bits 0-23 only).
 constexpr uint32_t kGroupPending = 0x80000000u;
 
-// Slab test of the W children of one quantized node.  A child box plane is
-// p + q * 2^e along each axis, so its ray parameter is q * S + B with
-// S = 2^e * inv_d and B = (p - o) * inv_d.  The byte q is read as the float
-// 2^23 + q (one byte permute) and the plane offset absorbs the 2^23 once per
-// node: t = fma(2^23 + q, S, B - 2^23 * S).  Rounding B - 2^23 * S costs at
-// most half a quantum, which the builder covers by growing every child box
-// one extra quantum.  The near and far planes of an axis go through one
-// packed f32x2 FMA.  A hit child contributes its precomputed hit bits (its
-// leaf triangles' bits, or bit 24 + slot for an internal child).  Returns the node group (child_base, pending flag |
-// imask), the triangle group (tri_base, leaf triangle bits) and the keys of
-// the hit internal children.
+// Slab test of the W children of one node.  A child plane is p + off along
+// its axis, so its ray parameter is off * (1/d) + (p - o) * (1/d): one fma a
+// plane after three multiplies a node.  The planes sit in six blocks (lo x,
+// y, z, hi x, y, z); the ray takes its near and far block of each axis by
+// address (the hi block is the near one along a negative direction), and one
+// packed f32x2 FMA gives the same plane of two children.  A hit child
+// contributes its precomputed hit bits (its leaf triangles' bits, or bit
+// 24 + slot for an internal child).  Returns the node group (child_base,
+// pending flag | imask), the triangle group (tri_base, leaf triangle bits)
+// and the keys of the hit internal children.
 template <int W>
 __device__ __forceinline__ void intersect_node(const Ray& r, const uint4* __restrict__ nd,
                                                float tmin, float tmax, uint2& ng, uint2& tg,
                                                typename KeyWords<W>::T& kq) {
+  constexpr int QB = W / 4;  // 16-byte loads per plane block
   const uint4 h0 = ldg4(nd), h1 = ldg4(nd + 1);
-  uint32_t lox[2], loy[2], loz[2], hix[2], hiy[2], hiz[2], hb[W];
-  if (W == 8) {
-    const uint4 q0 = ldg4(nd + 2), q1 = ldg4(nd + 3), q2 = ldg4(nd + 4);
-    const uint4 m0 = ldg4(nd + 5), m1 = ldg4(nd + 6);
-    lox[0] = q0.x; lox[1] = q0.y; loy[0] = q0.z; loy[1] = q0.w;
-    loz[0] = q1.x; loz[1] = q1.y; hix[0] = q1.z; hix[1] = q1.w;
-    hiy[0] = q2.x; hiy[1] = q2.y; hiz[0] = q2.z; hiz[1] = q2.w;
-    hb[0] = m0.x; hb[1] = m0.y; hb[2] = m0.z; hb[3] = m0.w;
-    hb[4 % W] = m1.x; hb[5 % W] = m1.y; hb[6 % W] = m1.z; hb[7 % W] = m1.w;
-  } else {
-    const uint4 q0 = ldg4(nd + 2), q1 = ldg4(nd + 3);
-    hb[0] = h1.z; hb[1] = h1.w; hb[2] = q0.x; hb[3 % W] = q0.y;
-    lox[0] = q0.z; loy[0] = q0.w; loz[0] = q1.x; hix[0] = q1.y;
-    hiy[0] = q1.z; hiz[0] = q1.w;
-    lox[1] = loy[1] = loz[1] = hix[1] = hiy[1] = hiz[1] = 0;
-  }
-  const uint32_t e = h0.w;
-  const float Sx = __fmul_rn(__uint_as_float((e & 0xFFu) << 23), r.ix);
-  const float Sy = __fmul_rn(__uint_as_float(((e >> 8) & 0xFFu) << 23), r.iy);
-  const float Sz = __fmul_rn(__uint_as_float(((e >> 16) & 0xFFu) << 23), r.iz);
-  const float Bx = fmaf(-8388608.0f, Sx, __fmul_rn(__fsub_rn(__uint_as_float(h0.x), r.ox), r.ix));
-  const float By = fmaf(-8388608.0f, Sy, __fmul_rn(__fsub_rn(__uint_as_float(h0.y), r.oy), r.iy));
-  const float Bz = fmaf(-8388608.0f, Sz, __fmul_rn(__fsub_rn(__uint_as_float(h0.z), r.oz), r.iz));
-  const uint64_t S2x = pack2f(Sx, Sx), S2y = pack2f(Sy, Sy), S2z = pack2f(Sz, Sz);
+  const float Bx = __fmul_rn(__fsub_rn(__uint_as_float(h0.x), r.ox), r.ix);
+  const float By = __fmul_rn(__fsub_rn(__uint_as_float(h0.y), r.oy), r.iy);
+  const float Bz = __fmul_rn(__fsub_rn(__uint_as_float(h0.z), r.oz), r.iz);
+  const uint64_t S2x = pack2f(r.ix, r.ix), S2y = pack2f(r.iy, r.iy), S2z = pack2f(r.iz, r.iz);
   const uint64_t B2x = pack2f(Bx, Bx), B2y = pack2f(By, By), B2z = pack2f(Bz, Bz);
-  const bool fx = r.oct & 1u, fy = r.oct & 2u, fz = r.oct & 4u;
+  const float4* pl = (const float4*)(nd + 2);
+  const int sx = (r.oct & 1u) ? 3 * QB : 0, sy = (r.oct & 2u) ? 3 * QB : 0, sz = (r.oct & 4u) ? 3 * QB : 0;
+  const float4* nxp = pl + sx;
+  const float4* fxp = pl + (3 * QB - sx);
+  const float4* nyp = pl + QB + sy;
+  const float4* fyp = pl + QB + (3 * QB - sy);
+  const float4* nzp = pl + 2 * QB + sz;
+  const float4* fzp = pl + 2 * QB + (3 * QB - sz);
+  uint32_t hb[W];
+  {
+    const uint4 m0 = ldg4(nd + 2 + 6 * QB);
+    hb[0] = m0.x; hb[1] = m0.y; hb[2] = m0.z; hb[3] = m0.w;
+    if constexpr (W == 8) {
+      const uint4 m1 = ldg4(nd + 3 + 6 * QB);
+      hb[4 % W] = m1.x; hb[5 % W] = m1.y; hb[6 % W] = m1.z; hb[7 % W] = m1.w;
+    }
+  }
   uint32_t hits = 0;
   float tn_all[W];
 #pragma unroll
-  for (int i = 0; i < W; ++i) {
-    const int w = i >> 2;
-    const uint32_t s = (uint32_t)(i & 3);
-    const uint32_t nxw = fx ? hix[w] : lox[w], fxw = fx ? lox[w] : hix[w];
-    const uint32_t nyw = fy ? hiy[w] : loy[w], fyw = fy ? loy[w] : hiy[w];
-    const uint32_t nzw = fz ? hiz[w] : loz[w], fzw = fz ? loz[w] : hiz[w];
-    float tnx, tfx, tny, tfy, tnz, tfz;
-    unpack2f(ffma2(pack2f(byte_magic(nxw, s), byte_magic(fxw, s)), S2x, B2x), tnx, tfx);
-    unpack2f(ffma2(pack2f(byte_magic(nyw, s), byte_magic(fyw, s)), S2y, B2y), tny, tfy);
-    unpack2f(ffma2(pack2f(byte_magic(nzw, s), byte_magic(fzw, s)), S2z, B2z), tnz, tfz);
-    const float tn = max3f(tnx, tny, fmaxf(tnz, tmin));
-    const float tf = min3f(tfx, tfy, fminf(tfz, tmax));
-    tn_all[i] = tn;
-    if (tn <= tf) hits |= hb[i];
+  for (int hf = 0; hf < QB; ++hf) {
+    const float4 anx = __ldg(nxp + hf), afx = __ldg(fxp + hf);
+    const float4 any = __ldg(nyp + hf), afy = __ldg(fyp + hf);
+    const float4 anz = __ldg(nzp + hf), afz = __ldg(fzp + hf);
+#pragma unroll
+    for (int pr = 0; pr < 2; ++pr) {
+      // children i and i + 1 of this block
+      float tnx0, tnx1, tfx0, tfx1, tny0, tny1, tfy0, tfy1, tnz0, tnz1, tfz0, tfz1;
+      unpack2f(ffma2(pack2f(pr ? anx.z : anx.x, pr ? anx.w : anx.y), S2x, B2x), tnx0, tnx1);
+      unpack2f(ffma2(pack2f(pr ? afx.z : afx.x, pr ? afx.w : afx.y), S2x, B2x), tfx0, tfx1);
+      unpack2f(ffma2(pack2f(pr ? any.z : any.x, pr ? any.w : any.y), S2y, B2y), tny0, tny1);
+      unpack2f(ffma2(pack2f(pr ? afy.z : afy.x, pr ? afy.w : afy.y), S2y, B2y), tfy0, tfy1);
+      unpack2f(ffma2(pack2f(pr ? anz.z : anz.x, pr ? anz.w : anz.y), S2z, B2z), tnz0, tnz1);
+      unpack2f(ffma2(pack2f(pr ? afz.z : afz.x, pr ? afz.w : afz.y), S2z, B2z), tfz0, tfz1);
+      const int i = hf * 4 + pr * 2;
+      const float tn0 = max3f(tnx0, tny0, fmaxf(tnz0, tmin));
+      const float tf0 = min3f(tfx0, tfy0, fminf(tfz0, tmax));
+      const float tn1 = max3f(tnx1, tny1, fmaxf(tnz1, tmin));
+      const float tf1 = min3f(tfx1, tfy1, fminf(tfz1, tmax));
+      tn_all[i] = tn0;
+      tn_all[i + 1] = tn1;
+      if (tn0 <= tf0) hits |= hb[i];
+      if (tn1 <= tf1) hits |= hb[i + 1];
+    }
   }
   const uint32_t v = hits >> 24;  // hit internal children, by slot
-  ng = make_uint2(h1.x, (v ? kGroupPending : 0u) | (e >> 24));
+  ng = make_uint2(h1.x, (v ? kGroupPending : 0u) | h0.w);
   tg = make_uint2(h1.y, hits & 0x00FFFFFFu);
   // Keys: bit 8j+7 of t0 (t1) is set when slot j (4+j) is NOT a hit internal
   // child; a sign-replicating byte permute widens it to the slot's 16 bits.

@@ -1,6 +1,6 @@
 """CPU-side checks of the C-ABI library: it loads, exports every entry point
 include/fgl.h declares, validates arguments, and its host BVH builder makes
-conservative quantized boxes (checked here independently of the library's
+conservative child boxes (checked here independently of the library's
 own verifier)."""
 
 import ctypes
@@ -44,25 +44,22 @@ def test_header_compiles_as_c(tmp_path):
 # host builder
 # ---------------------------------------------------------------------------
 def decode_nodes(nodes: np.ndarray, width: int):
-    """Node records as laid out by the builder: width 8 in 112 B (hit bits at
-    80, quantized planes at 32), width 4 in 64 B (hit bits at 24, planes at 40)."""
-    S, HB, Q = (112, 80, 32) if width == 8 else (64, 24, 40)
+    """Node records as laid out by the builder: a 32-byte header (corner p,
+    imask, child_base, tri_base), six blocks of `width` float offsets (lo x,
+    y, z, hi x, y, z), then the hit bits: 256 B for width 8, 144 B for 4."""
+    S = 32 + 28 * width
     rec = nodes.reshape(-1, S)
     p = rec[:, 0:12].copy().view(np.float32)
-    packed = rec[:, 12:16].copy().view(np.uint32)[:, 0]
-    e = np.stack([(packed >> (8 * a)) & 0xFF for a in range(3)], 1).astype(np.uint32)
-    scale = (e << 23).view(np.float32)
-    imask = packed >> 24
+    imask = rec[:, 12:16].copy().view(np.uint32)[:, 0]
     base = rec[:, 16:24].copy().view(np.uint32)
-    hb = rec[:, HB:HB + 4 * width].copy().view(np.uint32)
-    q = rec[:, Q:Q + 6 * width].reshape(-1, 6, width).astype(np.float32)
-    lo = (q[:, 0:3] * scale[:, :, None]).astype(np.float32) + p[:, :, None]   # q*2^e is exact
-    hi = (q[:, 3:6] * scale[:, :, None]).astype(np.float32) + p[:, :, None]
-    return dict(p=p, imask=imask, child_base=base[:, 0], tri_base=base[:, 1], hb=hb, lo=lo, hi=hi,
-                scale=scale)
+    off = rec[:, 32:32 + 24 * width].copy().view(np.float32).reshape(-1, 6, width).astype(np.float64)
+    hb = rec[:, 32 + 24 * width:S].copy().view(np.uint32)
+    lo = p[:, :, None].astype(np.float64) + off[:, 0:3]     # summed in double, as the builder checks
+    hi = p[:, :, None].astype(np.float64) + off[:, 3:6]
+    return dict(p=p, imask=imask, child_base=base[:, 0], tri_base=base[:, 1], hb=hb, lo=lo, hi=hi)
 
 
-def check_tree(v, t, width):
+def check_tree(v, t, width, want_boxes=False):
     sc = fgl.Scene(v, t, width=width, upload=False)
     st = sc.stats()
     nodes, tris = sc.export()
@@ -76,6 +73,7 @@ def check_tree(v, t, width):
     N = st["n_nodes"]
     clo = np.full((N, 3), np.inf)
     chi = np.full((N, 3), -np.inf)
+    boxes = []
     for ni in range(N - 1, -1, -1):
         for j in range(width):
             hb = int(D["hb"][ni, j])
@@ -95,20 +93,20 @@ def check_tree(v, t, width):
                 k = int(D["tri_base"][ni]) + off
                 pts = tv[k:k + cnt].reshape(-1, 3).astype(np.float64)
                 lo, hi = pts.min(0), pts.max(0)
-            g = m + D["scale"][ni].astype(np.float64)        # margin + one quantum
-            assert np.all(D["lo"][ni, :, j].astype(np.float64) <= lo - g), (ni, j)
-            assert np.all(D["hi"][ni, :, j].astype(np.float64) >= hi + g), (ni, j)
+            assert np.all(D["lo"][ni, :, j] <= lo - m), (ni, j)       # content grown by the margin
+            assert np.all(D["hi"][ni, :, j] >= hi + m), (ni, j)
             clo[ni] = np.minimum(clo[ni], lo)
             chi[ni] = np.maximum(chi[ni], hi)
+            boxes.append((ni, j, lo, hi))
     assert sc.verify() == 0
-    return st
+    return (st, D, boxes) if want_boxes else st
 
 
 @pytest.mark.parametrize("width", [8, 4])
 def test_builder_boxes_conservative_tiny_room(width):
     v, t, _ = synth.tiny_room_scene(1)
     st = check_tree(v, t, width)
-    assert st["width"] == width and st["node_stride"] == (112 if width == 8 else 64)
+    assert st["width"] == width and st["node_stride"] == (256 if width == 8 else 144)
 
 
 @pytest.mark.parametrize("width", [8, 4])
@@ -119,6 +117,84 @@ def test_builder_boxes_conservative_random_soup(width):
     v = v.astype(np.float32)
     t = np.arange(len(v), dtype=np.int32).reshape(-1, 3)
     check_tree(v, t, width)
+
+
+def _f32(x):
+    return np.asarray(x, np.float64).astype(np.float32).astype(np.float64)
+
+
+def _slab_hits_f32(D, ni, j, o, ix, tmax):
+    """The traversal's slab test of child slot j of node ni in float32:
+    t = fma(off, 1/d, (p - o) * (1/d)) per plane (the product of two floats is
+    exact in double, then one rounding), near plane by the sign of 1/d."""
+    p = D["p"][ni].astype(np.float64)
+    lo = D["lo"][ni, :, j] - p          # the stored offsets
+    hi = D["hi"][ni, :, j] - p
+    B = _f32(_f32(p[None] - o) * ix)
+    tlo = _f32(lo[None] * ix + B)
+    thi = _f32(hi[None] * ix + B)
+    near = np.where(ix < 0, thi, tlo)
+    far = np.where(ix < 0, tlo, thi)
+    tn = np.maximum(near.max(1), 0.0)
+    tf = np.minimum(far.min(1), tmax)
+    return tn <= tf
+
+
+def _rays_at_box(rng, lo, hi, slo, shi, k):
+    """k rays from origins anywhere in the scene box [slo, shi] aimed at points
+    on the surface of [lo, hi] (faces, edges and corners): float32 origin and
+    direction, approximate reciprocal within 2^-22 as on the device."""
+    tgt = rng.uniform(lo, hi, (k, 3))
+    ax = rng.integers(0, 3, k)
+    side = rng.integers(0, 2, k)
+    tgt[np.arange(k), ax] = np.where(side == 1, hi[ax], lo[ax])
+    corner = rng.random(k) < 0.25
+    tgt[corner] = np.where(rng.integers(0, 2, (int(corner.sum()), 3)) == 1, hi, lo)
+    o = _f32(rng.uniform(slo, shi, (k, 3)))
+    d = _f32(tgt - o)
+    d = np.where(np.abs(d) < 1e-20, 1e-20, d)
+    ix = _f32(1.0 / d * (1.0 + rng.uniform(-1, 1, (k, 3)) * 2.0 ** -22))
+    return o, d, ix
+
+
+def _true_hits(lo, hi, o, d, tmax):
+    with np.errstate(divide="ignore", invalid="ignore"):
+        t1 = (lo[None] - o) / d
+        t2 = (hi[None] - o) / d
+    tn = np.maximum(np.minimum(t1, t2).max(1), 0.0)
+    tf = np.minimum(np.maximum(t1, t2).min(1), tmax)
+    return tn <= tf
+
+
+@pytest.mark.parametrize("case", ["room", "soup", "far"])
+def test_slab_test_conservative_in_float32(case):
+    """The stored child boxes with the builder's margin survive the
+    traversal's float32 plane arithmetic: every ray that truly meets a
+    child's content box (here aimed at its faces, edges and corners, the
+    grazing cases) passes the emulated slab test of that child."""
+    rng = np.random.default_rng(11)
+    if case == "room":
+        v, t, _ = synth.tiny_room_scene(1)
+    elif case == "soup":
+        c = rng.uniform(-30, 30, (1500, 1, 3))
+        v = (c + rng.uniform(0.001, 2.0, (1500, 1, 1)) * rng.standard_normal((1500, 3, 3))).reshape(-1, 3)
+        t = np.arange(len(v), dtype=np.int32).reshape(-1, 3)
+    else:  # small triangles far from the origin
+        c = 1e4 + rng.uniform(-5, 5, (600, 1, 3))
+        v = (c + 1e-2 * rng.standard_normal((600, 3, 3))).reshape(-1, 3)
+        t = np.arange(len(v), dtype=np.int32).reshape(-1, 3)
+    v = v.astype(np.float32)
+    st, D, boxes = check_tree(v, t, 8, want_boxes=True)
+    slo, shi = np.array(st["bounds_lo"], np.float64), np.array(st["bounds_hi"], np.float64)
+    tmax = 4.0 * float(np.linalg.norm(shi - slo)) + 1.0
+    n_true = 0
+    for ni, j, lo, hi in boxes[:4000]:
+        o, d, ix = _rays_at_box(rng, lo, hi, slo, shi, 24)
+        truth = _true_hits(lo, hi, o, d, tmax)
+        got = _slab_hits_f32(D, ni, j, o, ix, tmax)
+        n_true += int(truth.sum())
+        assert not np.any(truth & ~got), (case, ni, j)
+    assert n_true > 1000
 
 
 def test_builder_degenerate_inputs():
