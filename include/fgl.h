@@ -193,7 +193,7 @@ typedef struct {
 typedef struct {
   int32_t packet_rays;    /* rays per work packet (0 = 32; multiple of 32) */
   int32_t block_threads;  /* threads per block (0 = 128; multiple of 32, <= 512) */
-  int32_t stack_smem;     /* traversal stack entries kept in shared memory (0 = 8) */
+  int32_t stack_smem;     /* traversal stack entries kept in shared memory (0 = 6) */
   int32_t blocks_per_sm;  /* persistent blocks per SM (0 = as many as fit) */
   int32_t use_graph;      /* 1 = capture the launch sequence in a CUDA graph and
                              replay it while the item layout is unchanged */

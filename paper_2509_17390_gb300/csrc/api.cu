@@ -82,7 +82,7 @@ fgl_status device_info(DeviceInfo* out) {
 // option defaults
 // ---------------------------------------------------------------------------
 struct Opts {
-  int packet = 32, block = 128, sdepth = 8, bpsm = 0, graph = 0, refill = 32, postpone = 20,
+  int packet = 32, block = 128, sdepth = 6, bpsm = 0, graph = 0, refill = 32, postpone = 20,
       count = 0, tri_mode = 0;
 };
 

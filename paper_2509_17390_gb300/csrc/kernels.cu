@@ -131,7 +131,7 @@ __global__ void __maxnreg__(72) k_plain(const ItemDesc it, int sdepth, int tri_m
 }
 
 template <int W, bool COUNT, bool TMIN>
-__global__ void __maxnreg__(72) k_persistent(BatchHeader* __restrict__ hdr,
+__global__ void __maxnreg__(TMIN ? 72 : 64) k_persistent(BatchHeader* __restrict__ hdr,
                                                     const ItemDesc* __restrict__ items, int sdepth,
                                                     int refill_min, int tri_mode, int postpone_pct) {
   using Keys = typename dev::KeyWords<W>::T;
@@ -145,7 +145,8 @@ __global__ void __maxnreg__(72) k_persistent(BatchHeader* __restrict__ hdr,
   // The warp's packet cursor (item, environment, next ray, end ray) and its
   // drained flag live in shared memory between refills, and the batch header
   // is re-read at refill time: registers stay free for the traversal (the
-  // kernel runs under a 72-register cap).
+  // kernel runs under a 64-register cap, eight 128-thread blocks an SM; the
+  // t_min form keeps 72, where 64 would spill).
   __shared__ int4 s_cur[kMaxBlockWarps];
   __shared__ int s_drained[kMaxBlockWarps];
   const int wid = threadIdx.x >> 5;
