@@ -13,15 +13,13 @@ Printed JSON line (rank 0):
   e2e              same metric through fgl_cast_batched_host with pinned host
                    buffers (poses H2D and ranges+ids D2H inside the timed region)
   per_env_launch   the plain form: one fgl_cast launch per environment
-  roofline         algorithmic node + triangle + 8 B output bytes per launch /
-                   kernel time against the measured HBM copy bandwidth (the
-                   cost model of eq. cost(r_j) as bytes; the kernel is served
-                   from L1/L2), with the L2 rate (ncu lts__t_bytes per ray)
-                   against an L2 copy bandwidth measured here, and `limiter`
-                   naming the larger measured fraction
-  roofline_issue   warp instructions per ray (ncu, same sources) x rays / kernel
-                   time against 4 warp instructions per SM per cycle: the
-                   kernel's actual limiter
+  roofline         the dominant kernel's bound, instruction issue: executed warp
+                   instructions per ray (ncu capture of the same sources) x
+                   rays / kernel time against 4 warp schedulers x SMs x the
+                   sampled SM clock; beside it the cost model of eq. cost(r_j)
+                   as bytes against the measured HBM copy bandwidth (node and
+                   triangle bytes are served by L1/L2, so it can exceed 1), the
+                   measured DRAM and L2 rates, and `limiter`
   cpu_baseline     the FP64 oracle on the host cores over a bounded sample
 
 --impl reference times the FP64 CPU oracle (the only reference this method
@@ -76,17 +74,45 @@ def read_peaks():
         return 6800.0, "fallback"
 
 
-def read_profile(name: str, field: str):
+def read_profile(name: str, field: str, entry: str = None):
     """A per-launch figure from the committed ncu summary (profiles/traffic.json),
-    if it was taken on the current kernel sources."""
+    if it was taken on the current kernel sources.  `entry` names a workload's
+    own capture of kernel `name` (default: the kernel's entry itself)."""
     try:
         d = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-        e = d.get(name)
+        e = d.get(entry or name)
         if e and e.get("kernel_hash") == kernel_hash(name) and e.get(field) is not None:
             return float(e[field])
     except Exception:
         pass
     return None
+
+
+def issue_roofline(kernel, entry, rays_per_s, clocks, dev, extra=None):
+    """The ray-casting kernels' bound: instruction issue.  Executed warp
+    instructions per ray (ncu smsp__inst_executed.sum of a committed capture
+    on the current sources) x rays/s, against the issue rate of the unit
+    counts and the clock: 4 warp schedulers per SM, one instruction each per
+    cycle, x SMs x the median SM clock sampled in the timed region.  None
+    when no capture matches the sources."""
+    ipr = read_profile(kernel, "warp_inst_per_ray", entry)
+    if ipr is None:
+        return None
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = (clocks or {}).get("sm_mhz") or (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak = 4.0 * sms * mhz * 1e6 / 1e9
+    ach = ipr * rays_per_s / 1e9
+    out = {"bound": "alu", "kernel": kernel, "achieved": round(ach, 1), "peak": round(peak, 1),
+           "unit": "G warp-inst/s", "frac": round(ach / peak, 4),
+           "traffic": read_profile(kernel, "dram_bytes_per_launch", entry),
+           "warp_inst_per_ray": ipr, "peak_source": "derived",
+           "peak_basis": f"4 warp schedulers x {sms} SMs x {mhz:.0f} MHz (median SM clock of the timed region)",
+           "basis": "instruction issue: executed warp instructions per ray (ncu, same kernel sources) "
+                    "x rays / kernel time; the kernel's nodes and triangles come from L1/L2, and "
+                    "its issue slots, not HBM, bound it"}
+    if extra:
+        out.update(extra)
+    return out
 
 
 def read_traffic(name: str):
@@ -95,12 +121,25 @@ def read_traffic(name: str):
     return read_profile(name, "dram_bytes_per_launch")
 
 
+def _nvtx(push: bool):
+    try:
+        import torch
+        if push:
+            torch.cuda.nvtx.range_push("bench_timed")
+        else:
+            torch.cuda.nvtx.range_pop()
+    except Exception:
+        pass
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle sampling during the timed region: the sampler
     is started and seen writing before the region opens (nvidia-smi takes a
     while to start), samples every 50 ms with nvidia-smi's own timestamp, and
     the summary keeps the samples taken between entering and leaving the
-    region (all of them, flagged, if the region was shorter than a sample)."""
+    region (all of them, flagged, if the region was shorter than a sample).
+    The region is also an NVTX range named "bench_timed", so that a profiler
+    can take its launches alone (ncu --nvtx --nvtx-include bench_timed/)."""
 
     Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -127,10 +166,12 @@ class ClockSampler:
         except Exception:
             self.proc = None
         self.t0 = datetime.datetime.now()
+        _nvtx(True)
         return self
 
     def __exit__(self, *a):
         import datetime
+        _nvtx(False)
         self.t1 = datetime.datetime.now()
         if self.proc:
             time.sleep(0.06)                       # the sample in flight at the end
@@ -567,53 +608,44 @@ def main():
     kern_ms = float(np.mean(step_ms))
     peak, peak_kind = read_peaks()
     achieved = b_ray * n_rays / (kern_ms / 1e3) / 1e9
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": read_traffic("k_persistent"),
-                "peak_source": peak_kind, "bytes_per_ray": round(b_ray, 1),
-                "basis": "cost model of eq. cost(r_j) as bytes: node visits x node size + "
-                         "triangle tests x 48 B + 8 B of output per ray (counted in a pass "
-                         "outside the timing); the kernel reads them from L1/L2, not HBM",
-                "node_visits_per_ray": round(c_nodes / max(1, c_rays), 2),
-                "tri_tests_per_ray": round(c_tris / max(1, c_rays), 2),
-                "phases_per_ray": {k: round(v / max(1, c_rays), 4) for k, v in phases.items() if k != "rays"}}
+    # eq. cost(r_j) as bytes against HBM (the cost model's figure; above 1
+    # because the node and triangle bytes are served by L1/L2, not HBM)
+    cost_model = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                  "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+                  "bytes_per_ray": round(b_ray, 1),
+                  "basis": "node visits x node size + triangle tests x 48 B + 8 B of output per "
+                           "ray (counted in a pass outside the timing), as if each came from HBM",
+                  "node_visits_per_ray": round(c_nodes / max(1, c_rays), 2),
+                  "tri_tests_per_ray": round(c_tris / max(1, c_rays), 2),
+                  "phases_per_ray": {k: round(v / max(1, c_rays), 4) for k, v in phases.items() if k != "rays"}}
     # measured traffic beside the cost model: DRAM bytes of one full launch and
     # L2 (lts__t_bytes) bytes per ray from the committed ncu captures, as rates;
     # the L2 rate against an L2 copy bandwidth measured here
-    tr = roofline["traffic"]
+    traffic = read_traffic("k_persistent")
+    measured = {"dram_bytes_per_launch": traffic}
+    if traffic is not None:
+        measured["dram_gbs"] = round(traffic / (kern_ms / 1e3) / 1e9, 1)
+        measured["dram_frac"] = round(traffic / (kern_ms / 1e3) / 1e9 / peak, 4)
     lpr = read_profile("k_persistent", "lts_bytes_per_ray")
-    if tr is not None:
-        roofline["dram_gbs_measured"] = round(tr / (kern_ms / 1e3) / 1e9, 1)
     l2pk = l2_read_peak(dev)
+    l2 = {"achieved": None, "peak": l2pk["gbs"], "unit": "GB/s", "peak_basis": l2pk["basis"]}
     if lpr is not None:
-        l2 = lpr * n_rays / (kern_ms / 1e3) / 1e9
-        roofline["l2"] = {"achieved": round(l2, 1), "peak": l2pk["gbs"], "unit": "GB/s",
-                          "frac": round(l2 / l2pk["gbs"], 4), "bytes_per_ray": lpr,
-                          "peak_basis": l2pk["basis"]}
-    else:
-        roofline["l2"] = {"achieved": None, "peak": l2pk["gbs"], "unit": "GB/s",
-                          "peak_basis": l2pk["basis"]}
-    # instruction issue, the kernel's actual limiter: warp instructions per ray
-    # (ncu, same kernel sources) x rays / kernel time, against 4 warp
-    # instructions per SM per cycle at the SM clock sampled during the run
-    ipr = read_profile("k_persistent", "warp_inst_per_ray")
-    roofline_issue = None
-    if ipr is not None:
-        sms = torch.cuda.get_device_properties(dev).multi_processor_count
-        mhz = (clocks or {}).get("sm_mhz") or (clocks or {}).get("sm_max_mhz") or 2070.0
-        ipeak = 4.0 * sms * mhz * 1e6 / 1e9
-        iach = ipr * n_rays / (kern_ms / 1e3) / 1e9
-        roofline_issue = {"bound": "issue", "achieved": round(iach, 1), "peak": round(ipeak, 1),
-                          "unit": "G warp-inst/s", "frac": round(iach / ipeak, 4),
-                          "warp_inst_per_ray": ipr, "peak_basis": f"4 x {sms} SMs x {mhz:.0f} MHz"}
-    # what limits the kernel: the larger of the measured L2 and issue
-    # fractions (the cost-model HBM figure counts node and triangle bytes as
-    # if each came from HBM, while measured DRAM traffic is far lower)
-    meas = {"l2": roofline["l2"].get("frac"),
-            "issue": roofline_issue["frac"] if roofline_issue else None}
-    meas = {k: v for k, v in meas.items() if v is not None}
-    roofline["limiter"] = {"kind": max(meas, key=meas.get) if meas else "unknown",
-                           "frac": max(meas.values()) if meas else None,
-                           "fractions": {"hbm_cost_model": roofline["frac"], **meas}}
+        l2a = lpr * n_rays / (kern_ms / 1e3) / 1e9
+        l2.update({"achieved": round(l2a, 1), "frac": round(l2a / l2pk["gbs"], 4), "bytes_per_ray": lpr})
+    # the bound: instruction issue (executed warp instructions per ray from the
+    # committed capture of these sources); without a matching capture the
+    # line falls back to the cost model
+    rps = n_rays / (kern_ms / 1e3)
+    roofline = issue_roofline("k_persistent", None, rps, clocks, dev,
+                              {"cost_model": cost_model, "dram": measured, "l2": l2})
+    if roofline is None:
+        roofline = dict(cost_model, traffic=traffic, dram=measured, l2=l2,
+                        note="no ncu capture of the current kernel sources: the issue bound is unmeasured")
+    fr = {"issue": roofline["frac"] if roofline["bound"] == "alu" else None,
+          "l2": l2.get("frac"), "dram": measured.get("dram_frac")}
+    fr = {k: v for k, v in fr.items() if v is not None}
+    roofline["limiter"] = {"kind": max(fr, key=fr.get) if fr else "unknown",
+                           "fractions": {**fr, "hbm_cost_model": cost_model["frac"]}}
 
     # the optional sensor effects (dropout 5%, range noise 1 cm + 0.1%) on one
     # step's returns, timed alone: an HBM-bound pass, 8 B read + 8 B written a
@@ -721,7 +753,7 @@ def main():
                        "between timed steps (256 MiB write)", "bvh_width": st["width"],
                        "opts": opts.as_dict(), "scene_tris": st["n_tris"],
                        "rays_per_step": n_rays, "frames_per_s": round(ws * n_env / (ms / 1e3), 1)},
-            "gpu_launches": args.steps, "roofline": roofline, "roofline_issue": roofline_issue,
+            "gpu_launches": args.steps, "roofline": roofline,
             "sensor_effects": effects, "e2e": e2e,
             "per_env_launch": per_env, "served": served, "cpu_baseline": cpu, "clocks": clocks,
         }
@@ -969,7 +1001,13 @@ def run_walk_instances(args):
     with torch.cuda.stream(stream):
         pose_state.copy_(walk_d[args.warmup % S])
     cb, cr, cn, ct = counted_bytes(fgl, items0, stream, opts)
-    roofline = hbm_roofline(cb, tot0 / args.steps, cr, cn, ct, kernel="k_persistent (the scene cast)")
+    cost = hbm_roofline(cb, tot0 / args.steps, cr, cn, ct, kernel="k_persistent (the scene cast)")
+    roofline = issue_roofline("k_persistent", "k_persistent@walk_instances", n_rays * args.steps / tot0,
+                              clocks, torch.device("cuda"), {"cost_model": cost,
+                              "note": "the scene cast, over its own time (the step without instances)"})
+    if roofline is None:
+        roofline = dict(cost, note="no ncu capture of the current kernel sources on this workload: "
+                                   "the issue bound is unmeasured")
     if rank == 0:
         line = {"metric": "Grays/s @4096 envs x 1M tris + 4 moving instances per env (with return points)",
                 "value": round(ws * n_rays * args.steps / tot / 1e9, 4), "unit": UNIT, "n_gpus": ws,
@@ -1072,10 +1110,11 @@ def run_lbvh(args):
         mhz = (clocks or {}).get("sm_mhz") or 2070.0
         ach = ipr * n_rays * args.steps / t_lbvh / 1e9
         pk = 4.0 * sms * mhz * 1e6 / 1e9
-        roofline = {"bound": "issue", "kernel": "k_lbvh_cast", "achieved": round(ach, 1), "peak": round(pk, 1),
+        roofline = {"bound": "alu", "kernel": "k_lbvh_cast", "achieved": round(ach, 1), "peak": round(pk, 1),
                     "unit": "G warp-inst/s", "frac": round(ach / pk, 4), "warp_inst_per_ray": ipr,
                     "traffic": read_profile("k_lbvh_cast", "dram_bytes_per_launch"),
-                    "peak_basis": f"4 x {sms} SMs x {mhz:.0f} MHz"}
+                    "peak_source": "derived",
+                    "peak_basis": f"4 warp schedulers x {sms} SMs x {mhz:.0f} MHz (instruction issue)"}
     if rank == 0:
         line = {"metric": "Grays/s @4096 envs x 1M tris, GPU-built triangle LBVH cast one thread per beam",
                 "value": round(ws * n_rays * args.steps / t_lbvh / 1e9, 4), "unit": UNIT, "n_gpus": ws,
@@ -1496,8 +1535,14 @@ def run_hetero(args):
     fgl.sync(stream)
     tot = barrier_max(sum(a.elapsed_time(b) for a, b in ev) / 1e3, ws)
     value = ws * n_rays * args.steps / tot / 1e9
+    clocks = clk.summary()
     cb, cr, cn, ct = counted_bytes(fgl, items, stream, opts)
-    roofline = hbm_roofline(cb, tot / args.steps, cr, cn, ct)
+    cost = hbm_roofline(cb, tot / args.steps, cr, cn, ct)
+    roofline = issue_roofline("k_persistent", "k_persistent@hetero", n_rays * args.steps / tot,
+                              clocks, torch.device("cuda"), {"cost_model": cost})
+    if roofline is None:
+        roofline = dict(cost, note="no ncu capture of the current kernel sources on this workload: "
+                                   "the issue bound is unmeasured")
     # the plain form: one fgl_cast launch per environment
     L = fgl.lib()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -1568,7 +1613,7 @@ def run_hetero(args):
                                        "rosette, max range 30 m", "rays_per_step": n_rays,
                            "l2": "flushed between timed steps (256 MiB write)", **info},
                 "gpu_launches": args.steps * len(set(widths.values())), "per_env_launch": per_env,
-                "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary()}
+                "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks}
         print(json.dumps(line), flush=True)
 
 
