@@ -95,6 +95,7 @@ def issue_roofline(kernel, entry, rays_per_s, clocks, dev, extra=None):
     counts and the clock: 4 warp schedulers per SM, one instruction each per
     cycle, x SMs x the median SM clock sampled in the timed region.  None
     when no capture matches the sources."""
+    import torch
     ipr = read_profile(kernel, "warp_inst_per_ray", entry)
     if ipr is None:
         return None
