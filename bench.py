@@ -776,10 +776,13 @@ def served_walk(fgl, scene, sensor, walk, walk_d, max_range, grays, rank, slots=
     rng = np.random.default_rng(11 + rank)
     pool = {0: walk.reshape(-1, 3, 4)}
     mean_env = (4096 - 1) / np.log(4096)
-    arena = OutputArena(2 << 30)
-    srv = fgl.Server(tick_rays=16 << 20, env_capacity=65536)
+    # result space and environment slots sized so that neither wraps onto a
+    # request still in flight within about 300 ms at this load (a wrap makes
+    # the replayer or the server wait, which would add to the measured tail)
+    arena = OutputArena(8 << 30)
+    srv = fgl.Server(tick_rays=16 << 20, env_capacity=262144)
     sid, tid = srv.add_scene(scene), srv.add_sensor(sensor)
-    plan = SlotPlan(srv, [walk_d.reshape(-1, 3, 4)], 65536, seed=12 + rank)
+    plan = SlotPlan(srv, [walk_d.reshape(-1, 3, 4)], 262144, seed=12 + rank)
     conv = (lambda tr: slot_trace(tr, plan)) if slots else (lambda tr: tr)
     sat_rate = 2.0 * grays * 1e9 / (mean_env * sensor.n_rays)
     sat_trace = conv(make_trace(rng, sat_rate, 1.0, 4096, pool, 1, lambda r, sc: 0))
@@ -790,7 +793,7 @@ def served_walk(fgl, scene, sensor, walk, walk_d, max_range, grays, rank, slots=
     trace = conv(make_trace(rng, rate, 2.0, 4096, pool, 1, lambda r, sc: 0))
     out = {"load": "Poisson, 70% of the server's sustained rate (measured at twice the kernel's "
                    "capacity over 1 s), 2 s window; n_env log-uniform 1-4096",
-           "poses": "device-resident environment slots (65,536), each request overwrites its "
+           "poses": "device-resident environment slots (262,144), each request overwrites its "
                     "slots from the device-resident walk: 0 pose bytes host->device" if slots else
                     "carried by each request from host memory (n_env x 48 B host->device)",
            "saturated": {"requests": sat["requests"], "Grays_s": round(sat["rays_per_s"] / 1e9, 4)},
@@ -810,9 +813,9 @@ def served_walk(fgl, scene, sensor, walk, walk_d, max_range, grays, rank, slots=
             break
     resb = replay(srv, pre, [sid], [tid], [sensor.n_rays], arena, max_range)
     srv.close()
-    srvp = fgl.Server(mode=1, env_capacity=65536)
+    srvp = fgl.Server(mode=1, env_capacity=262144)
     sid, tid = srvp.add_scene(scene), srvp.add_sensor(sensor)
-    SlotPlan(srvp, [walk_d.reshape(-1, 3, 4)], 65536)      # same slot ids
+    SlotPlan(srvp, [walk_d.reshape(-1, 3, 4)], 262144)     # same slot ids
     resp = replay(srvp, pre, [sid], [tid], [sensor.n_rays], arena, max_range)
     srvp.close()
     f = lambda r: {"p50_ms": round(r["p50_ms"], 2), "p99_ms": round(r["p99_ms"], 2),
@@ -1643,9 +1646,12 @@ def run_serve(args):
               for m in range(len(meshes))]
     n_rays_of = [s.n_rays for s in all_sensors]
     pick = lambda r, sc: int(r.integers(len(all_sensors)))
-    arena = OutputArena(24 << 30)
+    # result space that wraps about every 2 s at this load, well after the
+    # slowest request of a replay finished (a wrap onto a request still in
+    # flight makes the replayer wait, which would add to the measured latency)
+    arena = OutputArena(48 << 30)
     opts.use_graph = 0
-    per_scene = 8192
+    per_scene = 32768                               # slots per scene: a ring that wraps every few seconds
     srv = fgl.Server(hbm_budget_bytes=150 << 30, tick_rays=32 << 20, opts=opts,
                      env_capacity=per_scene * len(meshes))
     sids = [srv.add_scene(scenes[m][widths[m]]) for m in range(len(meshes))]
