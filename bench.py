@@ -1700,7 +1700,7 @@ def run_serve(args):
                 "clocks": clocks,
                 "config": {"workload": "serve: Poisson arrivals of 1-4096 environments (log-uniform) over "
                                        "the 8 heterogeneous scenes, 21 sensors, 150 GiB budget, 32 Mi-ray "
-                                       "ticks; poses in device-resident slots (8,192 a scene) updated "
+                                       "ticks; poses in device-resident slots (32,768 a scene) updated "
                                        "from device memory by each request", **info}}
         print(json.dumps(line), flush=True)
 
