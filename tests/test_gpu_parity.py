@@ -111,6 +111,34 @@ def test_tiny_cast_vs_brute_force(tiny, width):
     assert rep["hits"] == rep["n"]          # closed room: every ray hits
 
 
+@pytest.mark.parametrize("offset", [(0.0, 0.0, 0.0), (100.0, -60.0, 40.0)])
+@pytest.mark.parametrize("width", [8, 4])
+def test_translated_room_and_axis_aligned_beams(tiny, width, offset):
+    """The child boxes' margin against the traversal's float32 plane
+    arithmetic on the GPU: the tiny room moved away from the origin (the
+    margin scales with the coordinates), seen through beams along the axes
+    (direction components exactly 0, the reciprocal's clamp) and the grid
+    sensor, from upright and tilted poses."""
+    w, P = tiny
+    off = np.asarray(offset, np.float64)
+    v = (w.verts.astype(np.float64) + off).astype(np.float32)
+    Pt = P.astype(np.float64).copy()
+    Pt[:, :, 3] += off
+    Pa = synth.pose_from_yaw(P[:3, :, 3].astype(np.float64) + off, [0.0, 0.0, 0.0])
+    Pt = np.concatenate([Pt, Pa]).astype(np.float32)
+    sc = fgl.Scene(v, w.tris, width=width)
+    osc = oracle.Scene(v, w.tris, bvh=False)
+    el = np.repeat([0.0, 0.4, -0.4], 4)
+    az = np.tile([0.0, 0.5 * np.pi, np.pi, 1.5 * np.pi], 3)
+    for tab_el, tab_az, se in ((w.sensor.elev, w.sensor.azim, fgl.Sensor.from_table(w.sensor)),
+                               (el, az, fgl.Sensor(el, az, rows=3, cols=4))):
+        gr, gi = run_plain(sc, se, Pt, w.max_range)
+        o, d = oracle.world_rays(oracle.sensor_dirs(tab_el, tab_az), Pt)
+        rep = parity_report(osc, o, d, w.max_range, gr, gi)
+        assert_parity(rep)
+        assert rep["hits"] == rep["n"]      # closed room: every ray hits
+
+
 @pytest.mark.parametrize("width", [8, 4])
 def test_indoor_scan_vs_bvh_oracle(indoor, indoor_scenes, indoor_oracle, width):
     w = indoor
