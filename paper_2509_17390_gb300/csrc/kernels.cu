@@ -130,6 +130,13 @@ __global__ void __maxnreg__(72) k_plain(const ItemDesc it, int sdepth, int tri_m
   }
 }
 
+// Store a parked result (range bits << 32 | id) of a batched item; evict-first,
+// so the results do not push the BVH out of L2.
+__device__ __forceinline__ void store_parked(const ItemDesc& it, int64_t o, unsigned long long k) {
+  __stcs(it.out_range + o, __uint_as_float((uint32_t)(k >> 32)));
+  __stcs(it.out_tri + o, (int32_t)(uint32_t)k);
+}
+
 template <int W, bool COUNT, bool TMIN>
 __global__ void __maxnreg__(TMIN ? 72 : 64) k_persistent(BatchHeader* __restrict__ hdr,
                                                     const ItemDesc* __restrict__ items, int sdepth,
@@ -161,6 +168,12 @@ __global__ void __maxnreg__(TMIN ? 72 : 64) k_persistent(BatchHeader* __restrict
   tr.ng = make_uint2(0u, 0u);
   if (COUNT) tr.n_nodes = tr.n_tris = tr.n_rounds = tr.n_pops = 0;
   bool active = false;
+  // A finished lane parks its (range, id) in its own hit-key slot, which the
+  // pooled leaf tests never touch while the lane is idle, and the idle lanes
+  // store their parked results together at the next refill (or at exit): the
+  // stores of a packet then coalesce into whole sectors, which matters most
+  // when the outputs are page-locked host memory.
+  bool parked = false;
   int out_item = 0;    // the lane's ray: its item and output offset
   int64_t out_o = 0;
   uint32_t c_rays = 0, c_nodes = 0, c_tris = 0, c_iters = 0, c_lane_iters = 0, c_refills = 0;
@@ -168,6 +181,10 @@ __global__ void __maxnreg__(TMIN ? 72 : 64) k_persistent(BatchHeader* __restrict
   for (;;) {
     unsigned idle = __ballot_sync(FULL, !active);
     if ((idle == FULL || __popc(idle) >= refill_min) && !s_drained[wid]) {
+      if (parked) {
+        store_parked(items[out_item], out_o, sm.keys[lane]);
+        parked = false;
+      }
       const int64_t n_packets = hdr->n_packets;
       const int n_items = hdr->n_items;
       const int P = hdr->packet_rays;
@@ -236,7 +253,10 @@ __global__ void __maxnreg__(TMIN ? 72 : 64) k_persistent(BatchHeader* __restrict
     }
     const unsigned act = __ballot_sync(FULL, active);
     if (act == 0) {
-      if (s_drained[wid]) break;
+      if (s_drained[wid]) {
+        if (parked) store_parked(items[out_item], out_o, sm.keys[lane]);
+        break;
+      }
       continue;
     }
     bool fin = false;
@@ -264,8 +284,8 @@ __global__ void __maxnreg__(TMIN ? 72 : 64) k_persistent(BatchHeader* __restrict
       float rg;
       int32_t id;
       tr.result(rg, id);
-      __stcs(items[out_item].out_range + out_o, rg);  // evict-first: keep L2 for the BVH
-      __stcs(items[out_item].out_tri + out_o, id);
+      sm.keys[lane] = ((unsigned long long)__float_as_uint(rg) << 32) | (uint32_t)id;
+      parked = true;
       active = false;
       if (COUNT) ++c_rays;
     }
