@@ -1340,10 +1340,6 @@ def mesh_setup(torch):
     return sets
 
 
-def _scan_launches(n):
-    return 1 if n <= 2048 else 2 + _scan_launches((n + 2047) // 2048)
-
-
 def run_mesh(args):
     """3DGS to mesh on the GPU (Sec. IV-A then IV-B) over the 8 ladder sets:
     density and surface shell, denoising (sigma = h / 2, tau = 1/2), the
@@ -1406,11 +1402,10 @@ def run_mesh(args):
         dens_ms += dst["ms_density"]
         nx, ny, nz = S["dims"]
         voxels += nx * ny * nz
-        nw = ny * nz * ((nx + 31) // 32)
         # density; the fused blur (sigma = h/2: 2 taps a side) thresholds in the
-        # same launch; TSDF; marching tetrahedra: pack, count, three scans,
-        # list, vertices, triangles
-        launches += dst["n_launches"] + 1 + tst["n_launches"] + 5 + 3 * _scan_launches(nw + 1)
+        # same launch; TSDF; marching tetrahedra: pack, count (with the offsets
+        # within chunks), chunk offsets, list, vertices, triangles
+        launches += dst["n_launches"] + 1 + tst["n_launches"] + 6
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]

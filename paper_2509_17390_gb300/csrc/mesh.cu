@@ -10,25 +10,29 @@
 // instruction.
 //
 // fgl_denoise        eq. V' as three separable passes (float32 taps rounded
-//                    from FP64 weights, sums in ascending tap order), then
-//                    eq. rethresh with a fixed tau or the exact order statistic
-//                    of rank floor(q (N - 1)) by a four-pass radix select on
-//                    the float bit patterns (V' >= 0, so they sort as u32).
+//                    from FP64 weights, sums in ascending tap order; for up to
+//                    4 taps a side one kernel marching along z, the x pass a
+//                    table lookup on the input bits), then eq. rethresh with a
+//                    fixed tau or the exact order statistic of rank
+//                    floor(q (N - 1)) by a four-pass radix select on the float
+//                    bit patterns (V' >= 0, so they sort as u32).
 // fgl_tsdf           sign: a lock-free union-find over the free x-runs of the
 //                    rows with a virtual root 0 standing for the padded frame
 //                    (every run touching the grid's faces starts linked to
 //                    it; a link always goes from the larger root to the
 //                    smaller, so the frame's component ends under 0): runs of
 //                    adjacent rows that overlap are united once per overlap
-//                    segment, a warp per row; no flood rounds.  Shells: S_0 from word XORs with the six
-//                    neighbours, then L = ceil(r / h) word dilations; p(x) is
-//                    the first mask holding x.  phi = s min((p + 1/2) h, r).
+//                    segment -- inside tiles of rows in shared memory, across
+//                    tiles in global memory; no flood rounds.  Shells: S_0 from
+//                    word XORs with the six neighbours, then L = ceil(r / h)
+//                    word dilations; p(x) is the first mask holding x.
+//                    phi = s min((p + 1/2) h, r).
 // fgl_marching_tets  sign bits of the sample grid; per word, the crossing
 //                    edges of the seven types and the triangles of the six
-//                    tetrahedra counted bit-sliced over 32 samples; two
-//                    exclusive scans give every word its vertex and triangle
-//                    offsets; the emit pass writes both in the canonical order
-//                    documented in fgl.h.
+//                    tetrahedra counted bit-sliced over 32 samples; offsets
+//                    scanned within chunks of words, then over the chunks;
+//                    the emit pass writes vertices and triangles in the
+//                    canonical order documented in fgl.h.
 
 #include <cuda_runtime.h>
 
@@ -43,18 +47,45 @@
 #include "fgl.h"
 #include "fgl_internal.h"
 #include "nvtx_range.h"
-#include "sort.h"
 
 namespace fgl {
 namespace {
 
+// Division by a divisor fixed for the launch: one multiply-high, a subtract,
+// an add and two shifts, exact for every 32-bit dividend (Granlund and
+// Montgomery, "Division by invariant integers using multiplication", 1994,
+// the unsigned case with a 33-bit multiplier split as m + 2^32).
+struct FastDiv {
+  uint32_t m = 1, s1 = 0, s2 = 0;
+  __device__ __forceinline__ uint32_t div(uint32_t n) const {
+    const uint32_t t = __umulhi(m, n);
+    return (t + ((n - t) >> s1)) >> s2;
+  }
+};
+
+FastDiv make_div(uint32_t d) {  // d >= 1
+  uint32_t l = 0;
+  while (((uint64_t)1 << l) < d) ++l;  // ceil(log2 d)
+  FastDiv f;
+  f.m = (uint32_t)((((uint64_t)1 << 32) * (((uint64_t)1 << l) - d)) / d + 1);
+  f.s1 = l < 1 ? l : 1;
+  f.s2 = l > 0 ? l - 1 : 0;
+  return f;
+}
+
 struct BitGrid {
   int32_t nx, ny, nz, mw;
+  FastDiv by_mw, by_ny;  // word -> row, row -> plane
   __host__ __device__ int64_t rows() const { return (int64_t)ny * nz; }
   __host__ __device__ int64_t words() const { return rows() * mw; }
 };
 
-BitGrid make_bits(int nx, int ny, int nz) { return BitGrid{nx, ny, nz, (nx + 31) / 32}; }
+BitGrid make_bits(int nx, int ny, int nz) {
+  BitGrid g{nx, ny, nz, (nx + 31) / 32};
+  g.by_mw = make_div((uint32_t)g.mw);
+  g.by_ny = make_div((uint32_t)ny);
+  return g;
+}
 
 // bits of word xw that hold voxels (x < nx)
 __device__ __forceinline__ uint32_t valid_bits(const BitGrid& g, int xw) {
@@ -174,88 +205,120 @@ __global__ void k_blur(const TIn* __restrict__ in, float* __restrict__ out, int 
   }
 }
 
-// Fused eq. V' for R <= 4: one block per 32 x 8 x 8 output tile stages the
-// input with a halo of R in shared memory as 0/1 bytes, then the x, y and z
-// passes run in shared memory and the tile writes V' (when asked) and the
-// fixed-threshold mask (when asked).  Taps sum in the same ascending order
-// as k_blur; a tap outside the grid adds w * 0, which leaves the sum bitwise
-// unchanged, so both paths agree bit for bit.
-constexpr int kBTX = 32, kBTY = 8, kBTZ = 8;
+// Fused eq. V' for R <= 4, marching along z.  A block owns a 32 x 32 column
+// of outputs over zc planes; warp w computes rows 4w .. 4w + 3 for x = lane.
+// Per input plane: each warp loads 1/8 of its 32 + 2R rows of 32 + 2R voxels
+// (coalesced byte loads issued a plane ahead) and turns them into bits by
+// ballot; the x pass is a table lookup on those bits -- the input is 0/1, so
+// a voxel's x sum is fixed by its 2R + 1 bits, and the table holds those
+// sums accumulated exactly as the three-pass kernel does (a fused
+// multiply-add a tap, ascending); the y pass reads the x sums from shared
+// memory; the z pass runs over the last 2R + 1 y sums of each row, kept in
+// registers (the plane loop is unrolled 2R + 1 times, so the ring never
+// moves).  Voxels outside the grid read as 0, and a tap past the border adds
+// w * 0, which leaves the sum bitwise unchanged: both paths agree bit for
+// bit.  One barrier a plane.
+constexpr int kBTX = 32, kBTY = 32, kBQ = kBTY / 8;  // kBQ rows a thread
 
 template <int R>
-constexpr size_t fused_blur_smem() {
-  return ((size_t)(kBTX + 2 * R) * (kBTY + 2 * R) * (kBTZ + 2 * R) + 15) / 16 * 16 +
-         sizeof(float) * ((size_t)kBTX * (kBTY + 2 * R) * (kBTZ + 2 * R) + (size_t)kBTX * kBTY * (kBTZ + 2 * R));
-}
-
-template <int R>
-__global__ void __launch_bounds__(256) k_blur_fused(const uint8_t* __restrict__ in, int nx, int ny, int nz,
-                                                    Taps taps, float thr, float* __restrict__ out_blur,
+__global__ void __launch_bounds__(256, 4) k_blur_fused(const uint8_t* __restrict__ in, int nx, int ny, int nz,
+                                                    int zc, Taps taps, float thr, float* __restrict__ out_blur,
                                                     uint8_t* __restrict__ out_mask) {
-  constexpr int EX = kBTX + 2 * R, EY = kBTY + 2 * R, EZ = kBTZ + 2 * R;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  uint8_t* s_in = smem_raw;
-  float* s_x = (float*)(smem_raw + ((size_t)EX * EY * EZ + 15) / 16 * 16);  // [EZ][EY][kBTX]
-  float* s_y = s_x + kBTX * EY * EZ;                                        // [EZ][kBTY][kBTX]
-  const int x0 = blockIdx.x * kBTX, y0 = blockIdx.y * kBTY, z0 = blockIdx.z * kBTZ;
-  const int tid = threadIdx.x;
-  constexpr int kIn = EX * EY * EZ, kLoads = (kIn + 255) / 256;
-  uint8_t v[kLoads];  // every load issued before the first shared store: one memory latency
+  constexpr int K = 2 * R + 1, EY = kBTY + 2 * R, NT = 1 << K, RPW = (EY + 7) / 8;
+  __shared__ float s_tab[NT];
+  __shared__ float s_x[2][EY][kBTX];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int x0 = blockIdx.x * kBTX, y0 = blockIdx.y * kBTY, z0 = blockIdx.z * zc;
+  const int n_planes = min(zc, nz - z0) + 2 * R;  // input planes z0 - R, ...
+  float w[K];
 #pragma unroll
-  for (int u = 0; u < kLoads; ++u) {
-    const int i = tid + 256 * u;
-    const int ex = i % EX, ey = (i / EX) % EY, ez = i / (EX * EY);
-    const int gx = x0 - R + ex, gy = y0 - R + ey, gz = z0 - R + ez;
-    v[u] = 0;
-    if (i < kIn && gx >= 0 && gy >= 0 && gz >= 0 && gx < nx && gy < ny && gz < nz)
-      v[u] = in[((int64_t)gz * ny + gy) * nx + gx] != 0;
-  }
-#pragma unroll
-  for (int u = 0; u < kLoads; ++u)
-    if (tid + 256 * u < kIn) s_in[tid + 256 * u] = v[u];
-  __syncthreads();
-  for (int i = tid; i < kBTX * EY * EZ; i += 256) {
-    const int ox = i % kBTX, r = i / kBTX;  // r = ez * EY + ey
-    const uint8_t* src = s_in + r * EX + ox;
+  for (int t = 0; t < K; ++t) w[t] = taps.w[t];
+  for (int p = tid; p < NT; p += 256) {
     float acc = 0.f;
 #pragma unroll
-    for (int t = 0; t <= 2 * R; ++t) acc += taps.w[t] * (float)src[t];
-    s_x[i] = acc;
+    for (int t = 0; t < K; ++t) acc = __fmaf_rn(w[t], ((p >> t) & 1) ? 1.f : 0.f, acc);
+    s_tab[p] = acc;
   }
-  __syncthreads();
-  for (int i = tid; i < kBTX * kBTY * EZ; i += 256) {
-    const int ox = i % kBTX, oy = (i / kBTX) % kBTY, ez = i / (kBTX * kBTY);
-    const float* src = s_x + (ez * EY + oy) * kBTX + ox;
-    float acc = 0.f;
+  // this warp's input rows r = wid + 8 rr; lane l holds x = x0 - R + l and x0 - R + 32 + l
+  const int gx0 = x0 - R + lane, gx1 = x0 - R + 32 + lane;
+  const bool c0 = gx0 >= 0 && gx0 < nx, c1 = lane < 2 * R && gx1 < nx;
+  uint32_t rows_ok = 0;
 #pragma unroll
-    for (int t = 0; t <= 2 * R; ++t) acc += taps.w[t] * src[t * kBTX];
-    s_y[i] = acc;
+  for (int rr = 0; rr < RPW; ++rr) {
+    const int r = wid + 8 * rr, gy = y0 - R + r;
+    if (r < EY && gy >= 0 && gy < ny) rows_ok |= 1u << rr;
   }
-  __syncthreads();
-  for (int i = tid; i < kBTX * kBTY * kBTZ; i += 256) {
-    const int ox = i % kBTX, oy = (i / kBTX) % kBTY, oz = i / (kBTX * kBTY);
-    const int gx = x0 + ox, gy = y0 + oy, gz = z0 + oz;
-    if (gx >= nx || gy >= ny || gz >= nz) continue;
-    const float* src = s_y + (oz * kBTY + oy) * kBTX + ox;
-    float acc = 0.f;
+  uint32_t v[RPW][2];
+  auto load_plane = [&](int z) {
+    const bool z_ok = z >= 0 && z < nz;
 #pragma unroll
-    for (int t = 0; t <= 2 * R; ++t) acc += taps.w[t] * src[t * kBTX * kBTY];
-    const int64_t v = ((int64_t)gz * ny + gy) * nx + gx;
-    if (out_blur) out_blur[v] = acc;
-    if (out_mask) out_mask[v] = acc >= thr ? 1 : 0;
+    for (int rr = 0; rr < RPW; ++rr) {
+      const bool ok = z_ok && ((rows_ok >> rr) & 1u);
+      const int64_t row = ((int64_t)z * ny + (y0 - R + wid + 8 * rr)) * nx;
+      v[rr][0] = (ok && c0) ? in[row + gx0] : 0u;
+      v[rr][1] = (ok && c1) ? in[row + gx1] : 0u;
+    }
+  };
+  load_plane(z0 - R);
+  __syncthreads();  // the table
+  float ring[kBQ][K];  // y sums of the last K planes; slot u holds plane pz = u (mod K)
+#pragma unroll
+  for (int q = 0; q < kBQ; ++q)
+#pragma unroll
+    for (int t = 0; t < K; ++t) ring[q][t] = 0.f;
+  const int gx = x0 + lane, gy0 = y0 + kBQ * wid;
+  for (int pz0 = 0; pz0 < n_planes; pz0 += K) {
+#pragma unroll
+    for (int u = 0; u < K; ++u) {
+      const int pz = pz0 + u;
+      if (pz >= n_planes) break;  // block-uniform
+      const int buf = pz & 1;
+#pragma unroll
+      for (int rr = 0; rr < RPW; ++rr) {
+        const unsigned long long lo = __ballot_sync(0xFFFFFFFFu, v[rr][0] != 0u);
+        const unsigned long long hi = __ballot_sync(0xFFFFFFFFu, v[rr][1] != 0u);
+        const int r = wid + 8 * rr;
+        if (r < EY) s_x[buf][r][lane] = s_tab[(uint32_t)((lo | (hi << 32)) >> lane) & (uint32_t)(NT - 1)];
+      }
+      if (pz + 1 < n_planes) load_plane(z0 - R + pz + 1);
+      __syncthreads();
+      float xs[kBQ + 2 * R];
+#pragma unroll
+      for (int i = 0; i < kBQ + 2 * R; ++i) xs[i] = s_x[buf][kBQ * wid + i][lane];
+#pragma unroll
+      for (int q = 0; q < kBQ; ++q) {
+        float yv = 0.f;
+#pragma unroll
+        for (int t = 0; t < K; ++t) yv = __fmaf_rn(w[t], xs[q + t], yv);
+        ring[q][u] = yv;
+      }
+      if (pz >= 2 * R && gx < nx) {
+        const int64_t zrow = (int64_t)(z0 + pz - 2 * R) * ny;
+#pragma unroll
+        for (int q = 0; q < kBQ; ++q) {
+          const int gy = gy0 + q;
+          if (gy >= ny) break;
+          float acc = 0.f;
+#pragma unroll
+          for (int t = 0; t < K; ++t) acc = __fmaf_rn(w[t], ring[q][(u + 1 + t) % K], acc);
+          const int64_t o = (zrow + gy) * nx + gx;
+          if (out_blur) out_blur[o] = acc;
+          if (out_mask) out_mask[o] = acc >= thr ? 1 : 0;
+        }
+      }
+    }
   }
 }
 
 template <int R>
 cudaError_t launch_blur_fused(const uint8_t* in, int nx, int ny, int nz, const Taps& taps, float thr,
                               float* out_blur, uint8_t* out_mask, cudaStream_t s) {
-  constexpr size_t smem = fused_blur_smem<R>();
-  // set on every call: the attribute belongs to the current device
-  cudaError_t e = cudaFuncSetAttribute(k_blur_fused<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  const int64_t bxy = (int64_t)((nx + kBTX - 1) / kBTX) * ((ny + kBTY - 1) / kBTY);
+  int zc = 32;  // shorter columns when there are too few for four blocks an SM
+  while (zc > 8 && bxy * ((nz + zc - 1) / zc) < 4 * 152) zc /= 2;
   const dim3 grid((unsigned)((nx + kBTX - 1) / kBTX), (unsigned)((ny + kBTY - 1) / kBTY),
-                  (unsigned)((nz + kBTZ - 1) / kBTZ));
-  k_blur_fused<R><<<grid, 256, smem, s>>>(in, nx, ny, nz, taps, thr, out_blur, out_mask);
+                  (unsigned)((nz + zc - 1) / zc));
+  k_blur_fused<R><<<grid, 256, 0, s>>>(in, nx, ny, nz, zc, taps, thr, out_blur, out_mask);
   return cudaGetLastError();
 }
 
@@ -439,15 +502,21 @@ __global__ void k_run_init(const uint32_t* __restrict__ Vb, BitGrid g, uint32_t*
 }
 
 // Runs of adjacent rows (-y, -z) that share a free voxel are one component:
-// one union per overlap segment.  One warp per row.
-__global__ void k_run_union(const uint32_t* __restrict__ Vb, BitGrid g, uint32_t* parent, int* err) {
+// one union per overlap segment.  One warp per row.  With tile flags (from
+// k_run_tiles) a pair of rows inside one tile is skipped unless that tile
+// fell back to the global path: its unions are done already.
+__global__ void k_run_union(const uint32_t* __restrict__ Vb, BitGrid g, uint32_t* parent, int* err,
+                            int ty, int tz, const uint8_t* __restrict__ tile_global) {
   const int lane = threadIdx.x & 31;
   const int64_t n_warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   const uint32_t limit = (uint32_t)(g.rows() * g.nx + 2);
+  const int n_ty = tile_global ? (g.ny + ty - 1) / ty : 0;
   for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < g.rows(); row += n_warps) {
     const int j = (int)(row % g.ny), k = (int)(row / g.ny);
+    const bool all_pairs = !tile_global || tile_global[(k / tz) * n_ty + j / ty];
     for (int nb = 0; nb < 2; ++nb) {
       if (nb == 0 ? j == 0 : k == 0) continue;
+      if (!all_pairs && (nb == 0 ? j % ty : k % tz) != 0) continue;
       const int64_t row2 = nb == 0 ? row - 1 : row - g.ny;
       int cp = -1, cp2 = -1;
       uint32_t cb = 0, cb2 = 0, ocarry = 0;
@@ -465,6 +534,237 @@ __global__ void k_run_union(const uint32_t* __restrict__ Vb, BitGrid g, uint32_t
         }
       }
     }
+  }
+}
+
+// Tiled first pass: one block per tile of ty x tz rows (all of x) does, in
+// shared memory, what k_run_init and the tile's own k_run_union pairs do in
+// global memory, then writes every run's global parent as the label of its
+// tile-local root (0 for the frame).  Local run ids follow the tile's (k, j,
+// x) order, which is the order of the global labels, so "larger root under
+// smaller" holds for the written parents and k_run_union's cross-tile
+// unions keep every invariant.  A tile with more than `cap` runs writes the
+// plain initial parents instead and is flagged for the global path.
+constexpr int kTileThreads = 256;
+
+struct TilePlan {
+  int ty = 0, tz = 0, cap = 0;  // ty = 0: no tiles (rows too long)
+  int64_t n_tiles = 0;
+  size_t smem = 0;
+};
+
+TilePlan plan_tiles(const BitGrid& g) {
+  TilePlan p;
+  if (g.mw > 32) return p;
+  auto count = [&](int t) { return (int64_t)((g.ny + t - 1) / t) * ((g.nz + t - 1) / t); };
+  const int t = count(8) >= 152 ? 8 : 4;  // smaller tiles when 8 x 8 would leave SMs idle
+  p.ty = p.tz = t;
+  p.cap = 16 * t * t;                      // 16 runs a row on average
+  p.n_tiles = count(t);
+  p.smem = sizeof(uint32_t) * ((size_t)3 * t * t * g.mw + t * t + 2 * ((size_t)p.cap + 1) + 33);
+  return p;
+}
+
+// exclusive block-wide sum of v over the 256 threads in thread order, plus
+// *carry (shared; raised by the block total)
+__device__ __forceinline__ uint32_t tile_scan(uint32_t v, uint32_t* warp_tot, uint32_t* carry) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= o) incl += u;
+  }
+  if (lane == 31) warp_tot[wid] = incl;
+  __syncthreads();
+  uint32_t before = *carry;
+  for (int w = 0; w < wid; ++w) before += warp_tot[w];
+  uint32_t total = 0;
+  for (int w = 0; w < kTileThreads / 32; ++w) total += warp_tot[w];
+  __syncthreads();
+  if (threadIdx.x == 0) *carry += total;
+  __syncthreads();
+  return before + incl - v;
+}
+
+__device__ __forceinline__ uint32_t tile_find(volatile uint32_t* par, uint32_t x, uint32_t limit, int* err) {
+  for (uint32_t it = 0; it < limit; ++it) {
+    const uint32_t p = par[x];
+    if (p == x) return x;
+    const uint32_t gp = par[p];
+    if (gp != p) par[x] = gp;
+    x = gp;
+  }
+  atomicOr(err, 4);
+  return x;
+}
+
+__device__ __forceinline__ void tile_unite(uint32_t* par, uint32_t a, uint32_t b, uint32_t limit, int* err) {
+  for (uint32_t it = 0; it < limit; ++it) {
+    a = tile_find(par, a, limit, err);
+    b = tile_find(par, b, limit, err);
+    if (a == b) return;
+    if (a < b) {
+      const uint32_t t = a;
+      a = b;
+      b = t;
+    }
+    if (atomicCAS(par + a, a, b) == a) return;
+  }
+  atomicOr(err, 8);
+}
+
+__global__ void __launch_bounds__(kTileThreads) k_run_tiles(const uint8_t* __restrict__ surf, BitGrid g, int ty,
+                                                            int tz, int cap, uint32_t* __restrict__ Vb,
+                                                            uint32_t* __restrict__ parent,
+                                                            uint8_t* __restrict__ tile_global, uint32_t* __restrict__ roots,
+                                                            uint32_t* __restrict__ n_roots, uint32_t roots_cap,
+                                                            int* err) {
+  extern __shared__ uint32_t tsm[];
+  const int rows_t = ty * tz, mw = g.mw, nwt = rows_t * mw;
+  uint32_t* sF = tsm;                        // free bits of the tile's words
+  uint32_t* sSt = sF + nwt;                  // run starts
+  uint32_t* sOff = sSt + nwt;                // run starts before the word, in tile order
+  int* sLast = (int*)(sOff + nwt);           // per row: start of the run holding x = nx - 1, or -1
+  uint32_t* sPar = (uint32_t*)(sLast + rows_t);  // local parents; id 0 is the frame
+  uint32_t* sLab = sPar + cap + 1;           // local id -> global label
+  uint32_t* sWarp = sLab + cap + 1;          // 8 warp totals and the running carry
+  uint32_t* sCarry = sWarp + 32;
+  const int tid = threadIdx.x;
+  const int n_ty = (g.ny + ty - 1) / ty;
+  const int j0 = (int)(blockIdx.x % (unsigned)n_ty) * ty, k0 = (int)(blockIdx.x / (unsigned)n_ty) * tz;
+  const int lane = tid & 31, wid = tid >> 5;
+  if (blockIdx.x == 0 && tid == 0) parent[0] = 0;
+  if (tid == 0) *sCarry = 0;
+  // the tile's rows packed from the surface bytes (a warp a row, a ballot a
+  // word): the bit grid the later kernels read, and the free bits here
+  for (int lr = wid; lr < rows_t; lr += kTileThreads / 32) {
+    const int j = j0 + lr % ty, k = k0 + lr / ty;
+    uint32_t mine = 0;
+    if (j < g.ny && k < g.nz) {  // warp-uniform
+      const int64_t row = (int64_t)k * g.ny + j;
+      const uint8_t* src = surf + row * g.nx;
+#pragma unroll 4
+      for (int xw = 0; xw < mw; ++xw) {
+        const int x = xw * 32 + lane;
+        const uint32_t b = __ballot_sync(0xFFFFFFFFu, x < g.nx && src[x] != 0);
+        if (lane == xw) mine = b;
+      }
+      if (lane < mw) Vb[row * mw + lane] = mine;
+    }
+    if (lane < mw) sF[lr * mw + lane] = (j < g.ny && k < g.nz) ? ~mine & valid_bits(g, lane) : 0u;
+  }
+  __syncthreads();
+  for (int i0 = 0; i0 < nwt; i0 += kTileThreads) {  // block-uniform trip count
+    const int i = i0 + tid;
+    uint32_t c = 0;
+    if (i < nwt) {
+      const uint32_t F = sF[i];
+      const uint32_t prev = (i % mw) ? sF[i - 1] >> 31 : 0u;
+      const uint32_t st = F & ~((F << 1) | prev);
+      sSt[i] = st;
+      c = __popc(st);
+    }
+    const uint32_t off = tile_scan(c, sWarp, sCarry);
+    if (i < nwt) sOff[i] = off;
+  }
+  if (tid < rows_t) {
+    const int j = j0 + tid % ty, k = k0 + tid / ty;
+    const int xl = g.nx - 1;
+    int last = -1;
+    if (j < g.ny && k < g.nz && ((sF[tid * mw + (xl >> 5)] >> (xl & 31)) & 1u)) {
+      for (int xw = mw - 1; xw >= 0 && last < 0; --xw) {
+        const uint32_t st = sSt[tid * mw + xw];
+        if (st) last = xw * 32 + 31 - __clz(st);
+      }
+    }
+    sLast[tid] = last;
+  }
+  __syncthreads();
+  const uint32_t n_runs = *sCarry;
+  const bool global_path = n_runs > (uint32_t)cap;  // block-uniform
+  for (int i = tid; i < nwt; i += kTileThreads) {
+    const uint32_t st = sSt[i];
+    if (!st) continue;
+    const int lr = i / mw, xw = i - lr * mw;
+    const int j = j0 + lr % ty, k = k0 + lr / ty;
+    const bool face = j == 0 || k == 0 || j == g.ny - 1 || k == g.nz - 1;
+    const uint32_t row_base = (uint32_t)(((int64_t)k * g.ny + j) * g.nx) + 1u;
+    uint32_t id = sOff[i];
+    for (uint32_t m = st; m; m &= m - 1) {
+      const int x = xw * 32 + __ffs(m) - 1;
+      const bool frame = face || x == 0 || x == sLast[lr];
+      const uint32_t L = row_base + (uint32_t)x;
+      ++id;
+      if (global_path) {
+        parent[L] = frame ? 0u : L;
+        if (!frame) {
+          const uint32_t at = atomicAdd(n_roots, 1u);
+          if (at < roots_cap) roots[at] = L;
+        }
+      } else {
+        sLab[id] = L;
+        sPar[id] = frame ? 0u : id;
+      }
+    }
+  }
+  if (tid == 0) tile_global[blockIdx.x] = global_path ? 1 : 0;
+  if (global_path) return;
+  if (tid == 0) sPar[0] = sLab[0] = 0u;
+  __syncthreads();
+  // unions of the tile's own adjacent-row pairs, one task per (pair, word)
+  const uint32_t limit = n_runs + 2;
+  const int n_py = (ty - 1) * tz, n_pairs = n_py + ty * (tz - 1);
+  for (int t = tid; t < n_pairs * mw; t += kTileThreads) {
+    const int p = t / mw, xw = t - p * mw;
+    int a, b;
+    if (p < n_py) {
+      a = (p / (ty - 1)) * ty + p % (ty - 1) + 1;
+      b = a - 1;
+    } else {
+      a = p - n_py + ty;
+      b = a - ty;
+    }
+    const int ia = a * mw + xw, ib = b * mw + xw;
+    const uint32_t O = sF[ia] & sF[ib];
+    if (!O) continue;
+    const uint32_t oprev = xw ? (sF[ia - 1] & sF[ib - 1]) >> 31 : 0u;
+    for (uint32_t m = O & ~((O << 1) | oprev); m; m &= m - 1) {
+      const int s = __ffs(m) - 1;
+      const uint32_t below = (2u << s) - 1u;
+      const uint32_t ma = sSt[ia] & below, mb = sSt[ib] & below;
+      tile_unite(sPar, sOff[ia] + (ma ? __popc(ma) : 0), sOff[ib] + (mb ? __popc(mb) : 0), limit, err);
+    }
+  }
+  __syncthreads();
+  // the written parents; the tile's own roots (but the frame) go on the root list
+  for (uint32_t id0 = 0; id0 < n_runs; id0 += kTileThreads) {  // block-uniform trip count
+    const uint32_t id = id0 + 1 + tid;
+    bool root = false;
+    if (id <= n_runs) {
+      const uint32_t r = tile_find(sPar, id, limit, err);
+      parent[sLab[id]] = r ? sLab[r] : 0u;
+      root = r == id;
+    }
+    const uint32_t m = __ballot_sync(0xFFFFFFFFu, root);
+    if (m) {
+      uint32_t at = 0;
+      if (lane == 0) at = atomicAdd(n_roots, (uint32_t)__popc(m));
+      at = __shfl_sync(0xFFFFFFFFu, at, 0) + __popc(m & ((1u << lane) - 1u));
+      if (root && at < roots_cap) roots[at] = sLab[id];
+    }
+  }
+}
+
+// Every listed root (a tile's root after its own unions) points at the root
+// of its final set: after k_run_union nothing links any more, so the finds
+// only shorten paths, and k_run_outside's finds take at most three loads.
+__global__ void k_root_flatten(const uint32_t* __restrict__ roots, const uint32_t* __restrict__ n_roots,
+                               uint32_t roots_cap, uint32_t* parent, uint32_t limit, int* err) {
+  const uint32_t n = min(*n_roots, roots_cap);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t L = roots[i];
+    __stcg(parent + L, uf_find(parent, L, limit, err));
   }
 }
 
@@ -510,9 +810,10 @@ struct Nbr {
 };
 
 __device__ __forceinline__ Nbr neighbours(const uint32_t* __restrict__ B, const BitGrid& g, int64_t w) {
-  const uint32_t row = (uint32_t)w / (uint32_t)g.mw;  // words < 2^31
+  const uint32_t row = g.by_mw.div((uint32_t)w);  // words < 2^31
   const int xw = (int)((uint32_t)w - row * (uint32_t)g.mw);
-  const int j = (int)(row % (uint32_t)g.ny), k = (int)(row / (uint32_t)g.ny);
+  const uint32_t kk = g.by_ny.div(row);
+  const int j = (int)(row - kk * (uint32_t)g.ny), k = (int)kk;
   const uint32_t c = B[w];
   const uint32_t prev = xw > 0 ? B[w - 1] : 0u, next = xw + 1 < g.mw ? B[w + 1] : 0u;
   Nbr n;
@@ -535,7 +836,7 @@ __global__ void k_s0(const uint32_t* __restrict__ Vb, BitGrid g, uint32_t* __res
                      uint32_t* __restrict__ planes, int n_planes) {
   for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < g.words();
        w += (int64_t)gridDim.x * blockDim.x) {
-    const int xw = (int)((uint32_t)w % (uint32_t)g.mw);
+    const int xw = (int)((uint32_t)w - g.by_mw.div((uint32_t)w) * (uint32_t)g.mw);
     const uint32_t c = Vb[w];
     const Nbr n = neighbours(Vb, g, w);
     const uint32_t ex_m = xw == 0 ? ~1u : ~0u;
@@ -563,7 +864,7 @@ __global__ void k_dilate(const uint32_t* __restrict__ Din, BitGrid g, uint32_t* 
        w += (int64_t)gridDim.x * blockDim.x) {
     const Nbr n = neighbours(Din, g, w);
     const uint32_t d = (Din[w] | n.xm | n.xp | n.ym | n.yp | n.zm | n.zp) &
-                       valid_bits(g, (int)((uint32_t)w % (uint32_t)g.mw));
+                       valid_bits(g, (int)((uint32_t)w - g.by_mw.div((uint32_t)w) * (uint32_t)g.mw));
     Dout[w] = d;
     uint32_t carry = d;
     for (int q = 0; q < n_planes && carry; ++q) {
@@ -597,10 +898,16 @@ __global__ void k_phi(const uint32_t* __restrict__ Ob, const uint32_t* __restric
     for (int q = 0; q < kPhiPlanes; ++q) c[q] = (w < nw && q < n_planes) ? planes[(size_t)q * nw + w] : 0u;
     if (w < nw) ob = Ob[w];
     const int nwords = (int)min(32u, nw - w0);
+    uint32_t row = g.by_mw.div(w0);  // the broadcast word's row and x word, stepped along
+    int xw = (int)(w0 - row * (uint32_t)g.mw);
+    int64_t row_base = (int64_t)row * g.nx;
     for (int jw = 0; jw < nwords; ++jw) {
-      const uint32_t ww = w0 + jw;
-      const uint32_t row = ww / (uint32_t)g.mw;
-      const int x = (int)(ww - row * (uint32_t)g.mw) * 32 + lane;
+      const int x = xw * 32 + lane;
+      const int64_t v = row_base + x;
+      if (++xw == g.mw) {
+        xw = 0;
+        row_base += g.nx;
+      }
       int held = 0;
 #pragma unroll
       for (int q = 0; q < kPhiPlanes; ++q) {
@@ -613,7 +920,6 @@ __global__ void k_phi(const uint32_t* __restrict__ Ob, const uint32_t* __restric
       // (p + off) is exact in float32, so its product with h rounds once,
       // like the product of the exact values
       const float delta = p == 255 ? r : fminf(((float)p + off) * h, r);
-      const int64_t v = (int64_t)row * g.nx + x;
       phi[v] = out ? delta : -delta;
       if (out_outside) out_outside[v] = out ? 1 : 0;
       if (out_shell) out_shell[v] = (uint8_t)p;
@@ -683,44 +989,178 @@ __device__ __forceinline__ uint32_t active_cubes(const uint32_t C[8], uint32_t c
   return cubes & any1 & ~all1;
 }
 
-// per word: the seven crossing words, the vertex and triangle counts, and
-// the samples with a vertex (low half) and the cubes with a triangle (high
-// half) of cnt_a
-__global__ void k_mt_count(const uint32_t* __restrict__ I, BitGrid m, uint32_t* __restrict__ X,
-                           unsigned long long* __restrict__ cnt_v, unsigned long long* __restrict__ cnt_t,
-                           unsigned long long* __restrict__ cnt_a) {
+// Offsets.  The words (plus the end position nw, which counts nothing) split
+// into chunks of kMtChunk; a word's vertex, triangle and active-sample |
+// active-cube offsets are its chunk's prefix (pre[3 c + q], q = vertex,
+// triangle, active) plus the exclusive sum of the lower words of its chunk
+// (loc_v, loc_t, loc_a).  Every sum stays below 2^32 within a chunk, and the
+// two halves of an active count each below 2^32 overall (samples < 2^32).
+constexpr int kMtChunkLog = 11, kMtChunk = 1 << kMtChunkLog, kMtThreads = 256;
+constexpr int kMtPer = kMtChunk / kMtThreads;  // words a thread counts
+
+__device__ __forceinline__ unsigned long long mt_base(const unsigned long long* __restrict__ pre, int q,
+                                                      uint32_t loc, int64_t w) {
+  return pre[3 * (w >> kMtChunkLog) + q] + loc;
+}
+
+__device__ __forceinline__ int mt_pad(int p) { return p + (p >> 5); }  // no bank conflicts at stride kMtPer
+
+// Per word of chunk blockIdx.x: the seven crossing words, then its offsets
+// within the chunk; the chunk's totals go to pre[3 c + q].  Counts are staged
+// in shared memory so the loads and stores stay coalesced while each thread
+// scans kMtPer consecutive words.
+__global__ void __launch_bounds__(kMtThreads) k_mt_count(const uint32_t* __restrict__ I, BitGrid m,
+                                                         uint32_t* __restrict__ X, uint32_t* __restrict__ loc_v,
+                                                         uint32_t* __restrict__ loc_t,
+                                                         unsigned long long* __restrict__ loc_a,
+                                                         unsigned long long* __restrict__ pre) {
+  constexpr int kPad = kMtChunk + kMtChunk / 32;
+  __shared__ uint32_t sc[4][kPad];  // vertices, triangles, active samples, active cubes
+  __shared__ uint32_t warp_tot[kMtThreads / 32][4];
   const int64_t nw = m.words();
-  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nw;
-       w += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t row = (uint32_t)w / (uint32_t)m.mw;  // words < 2^31
-    const int xw = (int)((uint32_t)w - row * (uint32_t)m.mw);
-    const int j = (int)(row % (uint32_t)m.ny), k = (int)(row / (uint32_t)m.ny);
-    uint32_t C[8], Xw[7];
-    corner_words(I, m, j, k, xw, C);
-    crossing_words(C, m, j, k, xw, Xw);
-    uint32_t nv = 0, any = 0;
+  const int64_t base = (int64_t)blockIdx.x * kMtChunk;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+#pragma unroll 1
+  for (int u = 0; u < kMtPer; ++u) {
+    const int idx = u * kMtThreads + tid;
+    const int64_t w = base + idx;
+    uint32_t nv = 0, nt = 0, ns = 0, nc = 0;
+    if (w < nw) {
+      const uint32_t row = (uint32_t)w / (uint32_t)m.mw;  // words < 2^31
+      const int xw = (int)((uint32_t)w - row * (uint32_t)m.mw);
+      const int j = (int)(row % (uint32_t)m.ny), k = (int)(row / (uint32_t)m.ny);
+      uint32_t C[8], Xw[7];
+      corner_words(I, m, j, k, xw, C);
+      crossing_words(C, m, j, k, xw, Xw);
+      uint32_t any = 0;
 #pragma unroll
-    for (int t = 0; t < 7; ++t) {
-      X[t * nw + w] = Xw[t];
-      nv += __popc(Xw[t]);
-      any |= Xw[t];
+      for (int t = 0; t < 7; ++t) {
+        X[t * nw + w] = Xw[t];
+        nv += __popc(Xw[t]);
+        any |= Xw[t];
+      }
+      const uint32_t cubes = cube_bits(m, j, k, xw);
+      nt = tri_count(C, cubes);
+      ns = __popc(any);
+      nc = __popc(active_cubes(C, cubes));
     }
-    const uint32_t cubes = cube_bits(m, j, k, xw);
-    cnt_v[w] = nv;
-    cnt_t[w] = tri_count(C, cubes);
-    cnt_a[w] = (unsigned long long)__popc(any) | ((unsigned long long)__popc(active_cubes(C, cubes)) << 32);
+    const int pi = mt_pad(idx);
+    sc[0][pi] = nv;
+    sc[1][pi] = nt;
+    sc[2][pi] = ns;
+    sc[3][pi] = nc;
   }
+  __syncthreads();
+  uint32_t run[4] = {0, 0, 0, 0};  // this thread's words: exclusive sums in place
+#pragma unroll
+  for (int u = 0; u < kMtPer; ++u) {
+    const int pi = mt_pad(tid * kMtPer + u);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t c = sc[q][pi];
+      sc[q][pi] = run[q];
+      run[q] += c;
+    }
+  }
+  uint32_t incl[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    incl[q] = run[q];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl[q], o);
+      if (lane >= o) incl[q] += v;
+    }
+    if (lane == 31) warp_tot[wid][q] = incl[q];
+  }
+  __syncthreads();
+  uint32_t off[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    off[q] = incl[q] - run[q];
+    for (int v = 0; v < wid; ++v) off[q] += warp_tot[v][q];
+  }
+#pragma unroll
+  for (int u = 0; u < kMtPer; ++u) {
+    const int pi = mt_pad(tid * kMtPer + u);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) sc[q][pi] += off[q];
+  }
+  if (tid == kMtThreads - 1) {  // chunk totals
+    pre[3 * blockIdx.x + 0] = off[0] + run[0];
+    pre[3 * blockIdx.x + 1] = off[1] + run[1];
+    pre[3 * blockIdx.x + 2] = (unsigned long long)(off[2] + run[2]) | ((unsigned long long)(off[3] + run[3]) << 32);
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int u = 0; u < kMtPer; ++u) {
+    const int idx = u * kMtThreads + tid;
+    const int64_t w = base + idx;
+    if (w > nw) break;
+    const int pi = mt_pad(idx);
+    loc_v[w] = sc[0][pi];
+    loc_t[w] = sc[1][pi];
+    loc_a[w] = (unsigned long long)sc[2][pi] | ((unsigned long long)sc[3][pi] << 32);
+  }
+}
+
+// Chunk totals to exclusive chunk prefixes in place; the grand totals at
+// pre[3 n_chunks + q].  One block.
+__global__ void __launch_bounds__(1024) k_mt_chunks(unsigned long long* __restrict__ pre, int64_t n_chunks) {
+  __shared__ unsigned long long warp_tot[3][32];  // inclusive, then exclusive over the warps
+  __shared__ unsigned long long carry[3];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (tid < 3) carry[tid] = 0;
+  __syncthreads();
+  for (int64_t c0 = 0; c0 < n_chunks; c0 += 1024) {  // block-uniform trip count
+    const int64_t c = c0 + tid;
+    unsigned long long v[3], incl[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      v[q] = c < n_chunks ? pre[3 * c + q] : 0ull;
+      incl[q] = v[q];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long u = __shfl_up_sync(0xFFFFFFFFu, incl[q], o);
+        if (lane >= o) incl[q] += u;
+      }
+      if (lane == 31) warp_tot[q][wid] = incl[q];
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const unsigned long long t = warp_tot[q][lane];
+        unsigned long long wi = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const unsigned long long u = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+          if (lane >= o) wi += u;
+        }
+        warp_tot[q][lane] = carry[q] + wi - t;
+        __syncwarp();
+        if (lane == 31) carry[q] += wi;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+      if (c < n_chunks) pre[3 * c + q] = warp_tot[q][wid] + incl[q] - v[q];
+    __syncthreads();
+  }
+  if (tid < 3) pre[3 * n_chunks + tid] = carry[tid];
 }
 
 // the ids (32 w + b) of the samples with a vertex and of the cubes with a
 // triangle, in order
 __global__ void k_mt_list(const uint32_t* __restrict__ I, BitGrid m, const uint32_t* __restrict__ X,
-                          const unsigned long long* __restrict__ base_a, uint32_t* __restrict__ samples,
-                          uint32_t* __restrict__ cubes_out) {
+                          const unsigned long long* __restrict__ pre, const unsigned long long* __restrict__ loc_a,
+                          uint32_t* __restrict__ samples, uint32_t* __restrict__ cubes_out) {
   const int64_t nw = m.words();
   for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nw;
        w += (int64_t)gridDim.x * blockDim.x) {
-    const unsigned long long b0 = base_a[w], b1 = base_a[w + 1];
+    const unsigned long long b0 = pre[3 * (w >> kMtChunkLog) + 2] + loc_a[w];
+    const unsigned long long b1 = pre[3 * ((w + 1) >> kMtChunkLog) + 2] + loc_a[w + 1];
     if (b0 == b1) continue;
     uint32_t any = 0;
 #pragma unroll
@@ -747,8 +1187,9 @@ struct EmitArgs {
   float ox, oy, oz, h, iso;
   const uint32_t* I;
   const uint32_t* X;
-  const unsigned long long* base_v;
-  const unsigned long long* base_t;
+  const unsigned long long* pre;  // chunk prefixes (see k_mt_count)
+  const uint32_t* loc_v;
+  const uint32_t* loc_t;
   float* verts;
   int32_t* tris;
   float* normals;
@@ -811,7 +1252,7 @@ __device__ __forceinline__ void owner_info(const EmitArgs& a, int x, int j, int 
   const int64_t w = ((int64_t)k * a.m.ny + j) * a.m.mw + (x >> 5);
   const int b = x & 31;
   const uint32_t below = (1u << b) - 1u;
-  uint32_t f = (uint32_t)a.base_v[w], ty = 0;
+  uint32_t f = (uint32_t)mt_base(a.pre, 0, a.loc_v[w], w), ty = 0;
 #pragma unroll
   for (int t = 1; t <= 7; ++t) {
     const uint32_t xw = __ldg(a.X + (t - 1) * nw + w);
@@ -890,7 +1331,7 @@ __global__ void k_mt_verts(EmitArgs a, const uint32_t* __restrict__ samples, uin
       ty |= ((xt >> b) & 1u) << t;
       before += __popc(xt & ((1u << b) - 1u));
     }
-    int64_t vid = (int64_t)a.base_v[w] + before;
+    int64_t vid = (int64_t)mt_base(a.pre, 0, a.loc_v[w], w) + before;
 #pragma unroll 1
     for (int t = 1; t <= 7; ++t)
       if ((ty >> t) & 1u) emit_vertex(a, xw * 32 + (int)b, j, k, t, vid++);
@@ -908,7 +1349,7 @@ __global__ void k_mt_tris(EmitArgs a, const uint32_t* __restrict__ cubes_in, uin
     uint32_t C[8];
     corner_words(a.I, a.m, j, k, xw, C);
     const uint32_t below = (1u << b) - 1u;
-    int64_t tid = (int64_t)a.base_t[w] + tri_count(C, cube_bits(a.m, j, k, xw) & below);
+    int64_t tid = (int64_t)mt_base(a.pre, 1, a.loc_t[w], w) + tri_count(C, cube_bits(a.m, j, k, xw) & below);
     const int x = xw * 32 + b;
     uint32_t first[8], types[8];  // corner 7 owns no edge of its cube
 #pragma unroll 1
@@ -960,9 +1401,9 @@ struct Buf {
 };
 
 struct Scratch {
-  Buf bits_a, bits_b, shells, parent, x_words, cnt_v, cnt_t, cnt_a, lists, scan_tmp, blur_a, blur_b, sel;
-  int* err = nullptr;        // device: union-find limit reached (bit 0 find, bit 1 unite)
-  unsigned long long* host = nullptr;  // pinned: [0..1] counts read back, [2] the error flag, [3] active counts
+  Buf bits_a, bits_b, shells, parent, tiles, roots, x_words, cnt_v, cnt_t, cnt_a, lists, scan_tmp, blur_a, blur_b, sel;
+  int* err = nullptr;        // device: union-find limit reached (bits 0/1 global find/unite, 2/3 in a tile)
+  unsigned long long* host = nullptr;  // pinned: [2] the TSDF error flag, [4..6] the mesh totals read back
   cudaEvent_t err_ready = nullptr;     // recorded after the flag's copy to host[2]
   int pending_err_check = 0;
   std::mutex mu;
@@ -1010,9 +1451,9 @@ cudaError_t ensure_small(Scratch& S) {
     if (e != cudaSuccess) return e;
   }
   if (!S.host) {
-    cudaError_t e = cudaMallocHost(&S.host, 4 * sizeof(unsigned long long));
+    cudaError_t e = cudaMallocHost(&S.host, 8 * sizeof(unsigned long long));
     if (e != cudaSuccess) return e;
-    std::memset(S.host, 0, 4 * sizeof(unsigned long long));
+    std::memset(S.host, 0, 8 * sizeof(unsigned long long));
   }
   return cudaSuccess;
 }
@@ -1182,6 +1623,13 @@ extern "C" fgl_status fgl_tsdf(const uint8_t* surf, const fgl_grid* grid, float 
   const int n_planes = 32 - __builtin_clz((unsigned)(L + 1));  // bits of the count L + 1
   MCUDA(ensure(S.shells, sizeof(uint32_t) * nw * (2 + n_planes), s));
   MCUDA(ensure(S.parent, sizeof(uint32_t) * (n + 1), s));
+  const TilePlan tp = plan_tiles(g);
+  // root list: at most one entry a run, (nx + 1) / 2 runs a row
+  const uint32_t roots_cap = (uint32_t)std::min<int64_t>((g.rows() * (g.nx + 1)) / 2 + 1, 0xFFFFFFFFll);
+  if (tp.ty) {
+    MCUDA(ensure(S.tiles, (size_t)tp.n_tiles + 16, s));
+    MCUDA(ensure(S.roots, sizeof(uint32_t) * roots_cap, s));
+  }
   uint32_t* Vb = (uint32_t*)S.bits_a.p;
   uint32_t* Ob = (uint32_t*)S.bits_b.p;
   uint32_t* D = (uint32_t*)S.shells.p;
@@ -1195,15 +1643,30 @@ extern "C" fgl_status fgl_tsdf(const uint8_t* surf, const fgl_grid* grid, float 
   }
   int launches = 0;
   const dim3 vg = voxel_grid(g.nx, g.rows());
-  k_pack_u8<<<word_blocks(g.rows() * 32, 256), 256, 0, s>>>(surf, g, Vb);
   const unsigned rb = word_blocks(g.rows() * 32, 256);
-  k_run_init<<<rb, 256, 0, s>>>(Vb, g, parent);
-  k_run_union<<<rb, 256, 0, s>>>(Vb, g, parent, S.err);
+  if (tp.ty) {  // tiles pack the surface themselves
+    uint8_t* tile_global = (uint8_t*)S.tiles.p;
+    // the root counter: the word after the tile flags
+    uint32_t* n_roots = (uint32_t*)(tile_global + ((tp.n_tiles + 3) & ~(int64_t)3));
+    MCUDA(cudaMemsetAsync(n_roots, 0, sizeof(uint32_t), s));
+    k_run_tiles<<<(unsigned)tp.n_tiles, kTileThreads, tp.smem, s>>>(surf, g, tp.ty, tp.tz, tp.cap, Vb, parent,
+                                                                  tile_global, (uint32_t*)S.roots.p, n_roots,
+                                                                  roots_cap, S.err);
+    k_run_union<<<rb, 256, 0, s>>>(Vb, g, parent, S.err, tp.ty, tp.tz, tile_global);
+    k_root_flatten<<<152 * 4, 256, 0, s>>>((const uint32_t*)S.roots.p, n_roots, roots_cap, parent,
+                                           (uint32_t)(g.rows() * g.nx + 2), S.err);
+    launches += 3;
+  } else {
+    k_pack_u8<<<word_blocks(g.rows() * 32, 256), 256, 0, s>>>(surf, g, Vb);
+    k_run_init<<<rb, 256, 0, s>>>(Vb, g, parent);
+    k_run_union<<<rb, 256, 0, s>>>(Vb, g, parent, S.err, 1, 1, nullptr);
+    launches += 3;
+  }
   k_run_outside<<<rb, 256, 0, s>>>(Vb, g, parent, Ob, S.err);
   uint32_t* Dm[2] = {D, D + nw};       // ping-pong shell masks
   uint32_t* planes = D + 2 * nw;       // bit-sliced counts of the masks holding each voxel
   k_s0<<<word_blocks(nw, 256), 256, 0, s>>>(Vb, g, Dm[0], planes, n_planes);
-  launches += 5;
+  launches += 2;
   for (int m = 1; m <= L; ++m, ++launches)
     k_dilate<<<word_blocks(nw, 256), 256, 0, s>>>(Dm[(m - 1) & 1], g, Dm[m & 1], planes, n_planes);
   const float off = stats && stats->delta_mode == 1 ? 0.f : 0.5f;
@@ -1254,35 +1717,28 @@ extern "C" fgl_status fgl_marching_tets(const float* phi, const fgl_grid* grid, 
   Scratch& S = *get_scratch(s);
   std::lock_guard<std::mutex> lk(S.mu);
   MCUDA(ensure_small(S));
-  const size_t tmp_elems = scan_tmp_elems(nw + 1);
+  const int64_t n_chunks = nw / kMtChunk + 1;  // positions 0 .. nw
   MCUDA(ensure(S.bits_a, sizeof(uint32_t) * nw, s));
   MCUDA(ensure(S.x_words, sizeof(uint32_t) * nw * 7, s));
-  MCUDA(ensure(S.cnt_v, sizeof(unsigned long long) * (nw + 1), s));
-  MCUDA(ensure(S.cnt_t, sizeof(unsigned long long) * (nw + 1), s));
+  MCUDA(ensure(S.cnt_v, sizeof(uint32_t) * (nw + 1), s));
+  MCUDA(ensure(S.cnt_t, sizeof(uint32_t) * (nw + 1), s));
   MCUDA(ensure(S.cnt_a, sizeof(unsigned long long) * (nw + 1), s));
-  MCUDA(ensure(S.scan_tmp, sizeof(unsigned long long) * tmp_elems, s));
+  MCUDA(ensure(S.scan_tmp, sizeof(unsigned long long) * 3 * (n_chunks + 1), s));
   uint32_t* I = (uint32_t*)S.bits_a.p;
   uint32_t* X = (uint32_t*)S.x_words.p;
-  auto* cv = (unsigned long long*)S.cnt_v.p;
-  auto* ct = (unsigned long long*)S.cnt_t.p;
-  auto* ca = (unsigned long long*)S.cnt_a.p;
-  auto* tmp = (unsigned long long*)S.scan_tmp.p;
-  int launches = 0;
+  auto* lv = (uint32_t*)S.cnt_v.p;
+  auto* lt = (uint32_t*)S.cnt_t.p;
+  auto* la = (unsigned long long*)S.cnt_a.p;
+  auto* pre = (unsigned long long*)S.scan_tmp.p;
   k_pack_inside<<<word_blocks(m.rows() * 32, 256), 256, 0, s>>>(phi, nx, ny, step, m, iso, I);
-  k_mt_count<<<word_blocks(nw, 256), 256, 0, s>>>(I, m, X, cv, ct, ca);
+  k_mt_count<<<(unsigned)n_chunks, kMtThreads, 0, s>>>(I, m, X, lv, lt, la, pre);
+  k_mt_chunks<<<1, 1024, 0, s>>>(pre, n_chunks);
   MCUDA(cudaGetLastError());
-  MCUDA(cudaMemsetAsync(cv + nw, 0, sizeof(unsigned long long), s));
-  MCUDA(cudaMemsetAsync(ct + nw, 0, sizeof(unsigned long long), s));
-  MCUDA(cudaMemsetAsync(ca + nw, 0, sizeof(unsigned long long), s));
-  MCUDA(scan_exclusive_u64(cv, nw + 1, tmp, tmp_elems, s, &launches));
-  MCUDA(scan_exclusive_u64(ct, nw + 1, tmp, tmp_elems, s, &launches));
-  MCUDA(scan_exclusive_u64(ca, nw + 1, tmp, tmp_elems, s, &launches));
-  MCUDA(cudaMemcpyAsync(S.host, cv + nw, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-  MCUDA(cudaMemcpyAsync(S.host + 1, ct + nw, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-  MCUDA(cudaMemcpyAsync(S.host + 3, ca + nw, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  // totals: vertices, triangles, active samples | active cubes
+  MCUDA(cudaMemcpyAsync(S.host + 4, pre + 3 * n_chunks, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
   MCUDA(cudaStreamSynchronize(s));
-  const int64_t nv = (int64_t)S.host[0], nt = (int64_t)S.host[1];
-  const uint32_t n_samples = (uint32_t)(S.host[3] & 0xFFFFFFFFull), n_cubes = (uint32_t)(S.host[3] >> 32);
+  const int64_t nv = (int64_t)S.host[4], nt = (int64_t)S.host[5];
+  const uint32_t n_samples = (uint32_t)(S.host[6] & 0xFFFFFFFFull), n_cubes = (uint32_t)(S.host[6] >> 32);
   *n_verts = nv;
   *n_tris = nt;
   if (nv >= ((int64_t)1 << 31) || nt >= ((int64_t)1 << 31))
@@ -1304,8 +1760,9 @@ extern "C" fgl_status fgl_marching_tets(const float* phi, const fgl_grid* grid, 
   a.iso = iso;
   a.I = I;
   a.X = X;
-  a.base_v = cv;
-  a.base_t = ct;
+  a.pre = pre;
+  a.loc_v = lv;
+  a.loc_t = lt;
   a.verts = out_verts;
   a.tris = out_tris;
   a.normals = out_normals;
@@ -1314,7 +1771,7 @@ extern "C" fgl_status fgl_marching_tets(const float* phi, const fgl_grid* grid, 
   MCUDA(ensure(S.lists, sizeof(uint32_t) * ((size_t)n_samples + n_cubes + 1), s));
   uint32_t* samples = (uint32_t*)S.lists.p;
   uint32_t* cubes = samples + n_samples;
-  k_mt_list<<<word_blocks(nw, 256), 256, 0, s>>>(I, m, X, ca, samples, cubes);
+  k_mt_list<<<word_blocks(nw, 256), 256, 0, s>>>(I, m, X, pre, la, samples, cubes);
   if (n_samples) k_mt_verts<<<word_blocks(n_samples, 256), 256, 0, s>>>(a, samples, n_samples);
   if (n_cubes) k_mt_tris<<<word_blocks(n_cubes, 256), 256, 0, s>>>(a, cubes, n_cubes);
   MCUDA(cudaGetLastError());

@@ -348,3 +348,82 @@ def test_pipeline_mc_step_two():
     assert np.max(np.abs(v2.cpu().numpy() - vo)) <= oracle.vertex_tolerance(vo, 2 * h)
     closed, oriented = edge_stats(t2)
     assert closed and oriented
+
+
+# -- tiled sign, z-marching blur, chunked mesh offsets -----------------------------
+
+def boxes_with_corridors(shape, rng):
+    """Dense noise in the low z slab (many runs a row: those row tiles take
+    the global union-find path) and, above it, two hollow boxes split by
+    walls every 10 rows in y, each wall open at alternating x ends, so the
+    free space winds through many row tiles.  Box A has a hole in its outer
+    wall (its inside is reached from the frame only along the winding
+    corridor); box B is closed (its inside is not), and holds a closed cell
+    of its own."""
+    nz, ny, nx = shape
+    V = np.zeros(shape, np.uint8)
+    zs = nz // 3
+    V[:zs] = (rng.random((zs, ny, nx)) < 0.45).astype(np.uint8)
+    half = nx // 2
+    for x0, x1, hole in ((2, half - 2, True), (half + 2, nx - 2, False)):
+        z0, z1, y0, y1 = zs + 3, nz - 3, 3, ny - 3
+        V[z0:z1, y0:y1, x0:x1] = 1
+        V[z0 + 1:z1 - 1, y0 + 1:y1 - 1, x0 + 1:x1 - 1] = 0
+        for i, yw in enumerate(range(y0 + 10, y1 - 2, 10)):
+            V[z0:z1, yw, x0:x1] = 1
+            xo = x0 + 2 if i % 2 == 0 else x1 - 3
+            V[(z0 + z1) // 2, yw, xo] = 0                       # a one-voxel door
+        if hole:
+            V[(z0 + z1) // 2, y0, x0 + 2] = 0
+        else:
+            c = ((z0 + z1) // 2, y0 + 5, (x0 + x1) // 2)
+            V[c[0] - 2:c[0] + 3, c[1] - 2:c[1] + 3, c[2] - 2:c[2] + 3] = 1
+            V[c[0] - 1:c[0] + 2, c[1] - 1:c[1] + 2, c[2] - 1:c[2] + 2] = 0
+    return V
+
+
+@pytest.mark.parametrize("shape", [(100, 110, 200), (30, 40, 70), (14, 130, 1000)])
+def test_tsdf_tiles_mixed_paths_vs_oracle(shape):
+    """Row tiles of 8 x 8 (the first shape), 4 x 4 (the second; too few 8 x 8
+    tiles) and rows of 32 words (the third): tiles solved in shared memory
+    next to tiles on the global path, components crossing many tile faces,
+    a winding corridor to the frame and a closed box: sign, shells and phi
+    bit-exact."""
+    rng = np.random.default_rng(shape[0])
+    V = boxes_with_corridors(shape, rng)
+    phi, out, sh, _ = fgl.tsdf(cu(V), 0.02, 0.05, outside=True, shell=True)
+    phi_o, out_o, p_o = oracle.tsdf(V, 0.02, 0.05)
+    o = out.cpu().numpy()
+    assert np.array_equal(o, out_o)
+    assert np.array_equal(sh.cpu().numpy(), p_o)
+    assert np.array_equal(phi.cpu().numpy().view(np.uint32), phi_o.view(np.uint32))
+    nz, ny, nx = shape
+    zm = (nz // 3 + 3 + nz - 3) // 2
+    assert o[zm, ny // 2, nx // 4] == 1 and o[zm, ny // 2, 3 * nx // 4] == 0
+
+
+@pytest.mark.parametrize("sigma_vox", [0.3, 0.6, 0.9, 1.2])
+def test_denoise_many_z_chunks(sigma_vox):
+    """Taps R = 1..4 on 6 M voxels: the fused blur's z columns (32 planes, the
+    last one ragged) within the FP64 blur's tolerance, the mask exactly
+    V' >= tau of the GPU's own V'."""
+    rng = np.random.default_rng(21)
+    V = random_binary(rng, (100, 200, 300), 0.15)
+    h = 0.02
+    sigma = np.float32(sigma_vox * h)
+    mask, vp, _ = fgl.denoise(cu(V), h, float(sigma), tau=0.25, blur=True)
+    sv = np.float64(sigma) / np.float64(np.float32(h))
+    R = oracle.blur_radius(sv)
+    assert R == round(sigma_vox / 0.3)
+    g = vp.cpu().numpy()
+    assert np.abs(g.astype(np.float64) - oracle.blur(V, sv, R)).max() <= oracle.blur_tolerance(R)
+    assert np.array_equal(mask.cpu().numpy(), (g >= np.float32(0.25)).astype(np.uint8))
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 128), (39, 35, 96), (1, 2049, 20), (1, 2048, 20), (3, 700, 64)])
+def test_marching_tets_chunk_boundaries(shape):
+    """Sample grids of 4096, 4095, 2049, 2048 and 4200 words (offsets are
+    scanned in chunks of 2048 words, the end position included): triangle
+    lists exact, vertices within tolerance."""
+    rng = np.random.default_rng(shape[1])
+    check_mt(rng.standard_normal(shape).astype(np.float32), (0.1, -0.2, 0.3), 0.05, normals=True)
