@@ -221,7 +221,7 @@ __global__ void k_blur(const TIn* __restrict__ in, float* __restrict__ out, int 
 constexpr int kBTX = 32, kBTY = 32, kBQ = kBTY / 8;  // kBQ rows a thread
 
 template <int R>
-__global__ void __launch_bounds__(256, 4) k_blur_fused(const uint8_t* __restrict__ in, int nx, int ny, int nz,
+__global__ void __launch_bounds__(256, R <= 2 ? 4 : 3) k_blur_fused(const uint8_t* __restrict__ in, int nx, int ny, int nz,
                                                     int zc, Taps taps, float thr, float* __restrict__ out_blur,
                                                     uint8_t* __restrict__ out_mask) {
   constexpr int K = 2 * R + 1, EY = kBTY + 2 * R, NT = 1 << K, RPW = (EY + 7) / 8;
@@ -242,6 +242,8 @@ __global__ void __launch_bounds__(256, 4) k_blur_fused(const uint8_t* __restrict
   // this warp's input rows r = wid + 8 rr; lane l holds x = x0 - R + l and x0 - R + 32 + l
   const int gx0 = x0 - R + lane, gx1 = x0 - R + 32 + lane;
   const bool c0 = gx0 >= 0 && gx0 < nx, c1 = lane < 2 * R && gx1 < nx;
+  const int64_t plane = (int64_t)ny * nx;
+  const int off0 = (y0 - R + wid) * nx + gx0;  // offset in a plane of row rr = 0 (ny nx < 2^31)
   uint32_t rows_ok = 0;
 #pragma unroll
   for (int rr = 0; rr < RPW; ++rr) {
@@ -250,13 +252,14 @@ __global__ void __launch_bounds__(256, 4) k_blur_fused(const uint8_t* __restrict
   }
   uint32_t v[RPW][2];
   auto load_plane = [&](int z) {
-    const bool z_ok = z >= 0 && z < nz;
+    const uint32_t ok_rows = (z >= 0 && z < nz) ? rows_ok : 0u;
+    const uint8_t* pl = in + (int64_t)z * plane;
 #pragma unroll
     for (int rr = 0; rr < RPW; ++rr) {
-      const bool ok = z_ok && ((rows_ok >> rr) & 1u);
-      const int64_t row = ((int64_t)z * ny + (y0 - R + wid + 8 * rr)) * nx;
-      v[rr][0] = (ok && c0) ? in[row + gx0] : 0u;
-      v[rr][1] = (ok && c1) ? in[row + gx1] : 0u;
+      const bool ok = (ok_rows >> rr) & 1u;
+      const int o = off0 + 8 * rr * nx;
+      v[rr][0] = (ok && c0) ? pl[o] : 0u;
+      v[rr][1] = (ok && c1) ? pl[o + 32] : 0u;
     }
   };
   load_plane(z0 - R);
@@ -267,6 +270,7 @@ __global__ void __launch_bounds__(256, 4) k_blur_fused(const uint8_t* __restrict
 #pragma unroll
     for (int t = 0; t < K; ++t) ring[q][t] = 0.f;
   const int gx = x0 + lane, gy0 = y0 + kBQ * wid;
+  const int out0 = gy0 * nx + gx;  // offset in a plane of this thread's first output row
   for (int pz0 = 0; pz0 < n_planes; pz0 += K) {
 #pragma unroll
     for (int u = 0; u < K; ++u) {
@@ -275,10 +279,10 @@ __global__ void __launch_bounds__(256, 4) k_blur_fused(const uint8_t* __restrict
       const int buf = pz & 1;
 #pragma unroll
       for (int rr = 0; rr < RPW; ++rr) {
-        const unsigned long long lo = __ballot_sync(0xFFFFFFFFu, v[rr][0] != 0u);
-        const unsigned long long hi = __ballot_sync(0xFFFFFFFFu, v[rr][1] != 0u);
+        const uint32_t lo = __ballot_sync(0xFFFFFFFFu, v[rr][0] != 0u);
+        const uint32_t hi = __ballot_sync(0xFFFFFFFFu, v[rr][1] != 0u);
         const int r = wid + 8 * rr;
-        if (r < EY) s_x[buf][r][lane] = s_tab[(uint32_t)((lo | (hi << 32)) >> lane) & (uint32_t)(NT - 1)];
+        if (r < EY) s_x[buf][r][lane] = s_tab[__funnelshift_r(lo, hi, lane) & (uint32_t)(NT - 1)];
       }
       if (pz + 1 < n_planes) load_plane(z0 - R + pz + 1);
       __syncthreads();
@@ -293,15 +297,14 @@ __global__ void __launch_bounds__(256, 4) k_blur_fused(const uint8_t* __restrict
         ring[q][u] = yv;
       }
       if (pz >= 2 * R && gx < nx) {
-        const int64_t zrow = (int64_t)(z0 + pz - 2 * R) * ny;
+        const int64_t zo = (int64_t)(z0 + pz - 2 * R) * plane;
 #pragma unroll
         for (int q = 0; q < kBQ; ++q) {
-          const int gy = gy0 + q;
-          if (gy >= ny) break;
+          if (gy0 + q >= ny) break;
           float acc = 0.f;
 #pragma unroll
           for (int t = 0; t < K; ++t) acc = __fmaf_rn(w[t], ring[q][(u + 1 + t) % K], acc);
-          const int64_t o = (zrow + gy) * nx + gx;
+          const int64_t o = zo + (out0 + q * nx);
           if (out_blur) out_blur[o] = acc;
           if (out_mask) out_mask[o] = acc >= thr ? 1 : 0;
         }
@@ -412,14 +415,46 @@ __device__ __forceinline__ uint32_t uf_find(uint32_t* parent, uint32_t x, uint32
   return x;
 }
 
-// Link the two roots, the larger under the smaller.  A failed exchange means
-// another thread linked the root first, so the next root is strictly smaller:
-// at most N + 2 rounds.
+// Root of x while nothing links or compresses (k_run_outside): the parents
+// are read-only for the whole launch, so the walk reads them through the
+// read-only cache, and the runs of one tile share their chain there.
+__device__ __forceinline__ uint32_t uf_root_ro(const uint32_t* __restrict__ parent, uint32_t x, uint32_t limit,
+                                               int* err) {
+  for (uint32_t it = 0; it < limit; ++it) {
+    const uint32_t p = __ldg(parent + x);
+    if (p == x) return x;
+    x = p;
+  }
+  atomicOr(err, 1);
+  return x;
+}
+
+// The same walk through the L1 cache, which other SMs' links do not update:
+// a stale parent is an older ancestor (parents only ever decrease along a
+// path), so the walk still ends, at a root or at a node since linked under
+// one -- a vertex of the right set either way.
+__device__ __forceinline__ uint32_t uf_find_cached(uint32_t* parent, uint32_t x, uint32_t limit, int* err) {
+  for (uint32_t it = 0; it < limit; ++it) {
+    const uint32_t p = parent[x];
+    if (p == x) return x;
+    const uint32_t gp = parent[p];
+    if (gp != p) __stcg(parent + x, gp);
+    x = gp;
+  }
+  atomicOr(err, 1);
+  return x;
+}
+
+// Link the two roots, the larger under the smaller.  The first try walks
+// through L1 (two walks ending at one vertex are one set; the exchange only
+// succeeds on a true root); after a failed exchange the walks read L2, so a
+// failure means another thread linked the root first and the next root is
+// strictly smaller: at most N + 2 rounds.
 __device__ __forceinline__ void uf_unite(uint32_t* parent, uint32_t a, uint32_t b, uint32_t limit,
                                          int* err) {
   for (uint32_t it = 0; it < limit; ++it) {
-    a = uf_find(parent, a, limit, err);
-    b = uf_find(parent, b, limit, err);
+    a = it ? uf_find(parent, a, limit, err) : uf_find_cached(parent, a, limit, err);
+    b = it ? uf_find(parent, b, limit, err) : uf_find_cached(parent, b, limit, err);
     if (a == b) return;
     if (a < b) {
       const uint32_t t = a;
@@ -617,9 +652,7 @@ __device__ __forceinline__ void tile_unite(uint32_t* par, uint32_t a, uint32_t b
 __global__ void __launch_bounds__(kTileThreads) k_run_tiles(const uint8_t* __restrict__ surf, BitGrid g, int ty,
                                                             int tz, int cap, uint32_t* __restrict__ Vb,
                                                             uint32_t* __restrict__ parent,
-                                                            uint8_t* __restrict__ tile_global, uint32_t* __restrict__ roots,
-                                                            uint32_t* __restrict__ n_roots, uint32_t roots_cap,
-                                                            int* err) {
+                                                            uint8_t* __restrict__ tile_global, int* err) {
   extern __shared__ uint32_t tsm[];
   const int rows_t = ty * tz, mw = g.mw, nwt = rows_t * mw;
   uint32_t* sF = tsm;                        // free bits of the tile's words
@@ -638,21 +671,31 @@ __global__ void __launch_bounds__(kTileThreads) k_run_tiles(const uint8_t* __res
   if (tid == 0) *sCarry = 0;
   // the tile's rows packed from the surface bytes (a warp a row, a ballot a
   // word): the bit grid the later kernels read, and the free bits here
-  for (int lr = wid; lr < rows_t; lr += kTileThreads / 32) {
-    const int j = j0 + lr % ty, k = k0 + lr / ty;
-    uint32_t mine = 0;
-    if (j < g.ny && k < g.nz) {  // warp-uniform
-      const int64_t row = (int64_t)k * g.ny + j;
-      const uint8_t* src = surf + row * g.nx;
+  for (int lr0 = wid; lr0 < rows_t; lr0 += kTileThreads / 16) {  // two rows a pass: more loads in flight
+    const int lr1 = lr0 + kTileThreads / 32;
+    const int ja = j0 + lr0 % ty, ka = k0 + lr0 / ty, jb = j0 + lr1 % ty, kb = k0 + lr1 / ty;
+    const bool in_a = ja < g.ny && ka < g.nz, in_b = lr1 < rows_t && jb < g.ny && kb < g.nz;  // warp-uniform
+    const uint8_t* src_a = surf + ((int64_t)ka * g.ny + ja) * g.nx;
+    const uint8_t* src_b = surf + ((int64_t)kb * g.ny + jb) * g.nx;
+    uint32_t mine_a = 0, mine_b = 0;
 #pragma unroll 4
-      for (int xw = 0; xw < mw; ++xw) {
-        const int x = xw * 32 + lane;
-        const uint32_t b = __ballot_sync(0xFFFFFFFFu, x < g.nx && src[x] != 0);
-        if (lane == xw) mine = b;
+    for (int xw = 0; xw < mw; ++xw) {
+      const int x = xw * 32 + lane;
+      const uint32_t ba = __ballot_sync(0xFFFFFFFFu, in_a && x < g.nx && src_a[x] != 0);
+      const uint32_t bb = __ballot_sync(0xFFFFFFFFu, in_b && x < g.nx && src_b[x] != 0);
+      if (lane == xw) {
+        mine_a = ba;
+        mine_b = bb;
       }
-      if (lane < mw) Vb[row * mw + lane] = mine;
     }
-    if (lane < mw) sF[lr * mw + lane] = (j < g.ny && k < g.nz) ? ~mine & valid_bits(g, lane) : 0u;
+    if (lane < mw) {
+      if (in_a) Vb[((int64_t)ka * g.ny + ja) * mw + lane] = mine_a;
+      sF[lr0 * mw + lane] = in_a ? ~mine_a & valid_bits(g, lane) : 0u;
+      if (lr1 < rows_t) {
+        if (in_b) Vb[((int64_t)kb * g.ny + jb) * mw + lane] = mine_b;
+        sF[lr1 * mw + lane] = in_b ? ~mine_b & valid_bits(g, lane) : 0u;
+      }
+    }
   }
   __syncthreads();
   for (int i0 = 0; i0 < nwt; i0 += kTileThreads) {  // block-uniform trip count
@@ -698,10 +741,6 @@ __global__ void __launch_bounds__(kTileThreads) k_run_tiles(const uint8_t* __res
       ++id;
       if (global_path) {
         parent[L] = frame ? 0u : L;
-        if (!frame) {
-          const uint32_t at = atomicAdd(n_roots, 1u);
-          if (at < roots_cap) roots[at] = L;
-        }
       } else {
         sLab[id] = L;
         sPar[id] = frame ? 0u : id;
@@ -712,64 +751,44 @@ __global__ void __launch_bounds__(kTileThreads) k_run_tiles(const uint8_t* __res
   if (global_path) return;
   if (tid == 0) sPar[0] = sLab[0] = 0u;
   __syncthreads();
-  // unions of the tile's own adjacent-row pairs, one task per (pair, word)
+  // unions of the tile's own adjacent-row pairs, one task per (pair, word):
+  // the y pairs of every z slice first, then the z pairs, so that no chain of
+  // links grows longer than a slice before the slices join
   const uint32_t limit = n_runs + 2;
-  const int n_py = (ty - 1) * tz, n_pairs = n_py + ty * (tz - 1);
-  for (int t = tid; t < n_pairs * mw; t += kTileThreads) {
-    const int p = t / mw, xw = t - p * mw;
-    int a, b;
-    if (p < n_py) {
-      a = (p / (ty - 1)) * ty + p % (ty - 1) + 1;
-      b = a - 1;
-    } else {
-      a = p - n_py + ty;
-      b = a - ty;
+  const int n_py = (ty - 1) * tz, n_pz = ty * (tz - 1);
+  for (int phase = 0; phase < 2; ++phase) {
+    const int n_tasks = (phase == 0 ? n_py : n_pz) * mw;
+    for (int t = tid; t < n_tasks; t += kTileThreads) {
+      const int p = t / mw, xw = t - p * mw;
+      int a, b;
+      if (phase == 0) {
+        a = (p / (ty - 1)) * ty + p % (ty - 1) + 1;
+        b = a - 1;
+      } else {
+        a = p + ty;
+        b = a - ty;
+      }
+      const int ia = a * mw + xw, ib = b * mw + xw;
+      const uint32_t O = sF[ia] & sF[ib];
+      if (!O) continue;
+      const uint32_t oprev = xw ? (sF[ia - 1] & sF[ib - 1]) >> 31 : 0u;
+      for (uint32_t m = O & ~((O << 1) | oprev); m; m &= m - 1) {
+        const int s = __ffs(m) - 1;
+        const uint32_t below = (2u << s) - 1u;
+        const uint32_t ma = sSt[ia] & below, mb = sSt[ib] & below;
+        tile_unite(sPar, sOff[ia] + (ma ? __popc(ma) : 0), sOff[ib] + (mb ? __popc(mb) : 0), limit, err);
+      }
     }
-    const int ia = a * mw + xw, ib = b * mw + xw;
-    const uint32_t O = sF[ia] & sF[ib];
-    if (!O) continue;
-    const uint32_t oprev = xw ? (sF[ia - 1] & sF[ib - 1]) >> 31 : 0u;
-    for (uint32_t m = O & ~((O << 1) | oprev); m; m &= m - 1) {
-      const int s = __ffs(m) - 1;
-      const uint32_t below = (2u << s) - 1u;
-      const uint32_t ma = sSt[ia] & below, mb = sSt[ib] & below;
-      tile_unite(sPar, sOff[ia] + (ma ? __popc(ma) : 0), sOff[ib] + (mb ? __popc(mb) : 0), limit, err);
-    }
+    __syncthreads();
   }
-  __syncthreads();
-  // the written parents; the tile's own roots (but the frame) go on the root list
-  for (uint32_t id0 = 0; id0 < n_runs; id0 += kTileThreads) {  // block-uniform trip count
-    const uint32_t id = id0 + 1 + tid;
-    bool root = false;
-    if (id <= n_runs) {
-      const uint32_t r = tile_find(sPar, id, limit, err);
-      parent[sLab[id]] = r ? sLab[r] : 0u;
-      root = r == id;
-    }
-    const uint32_t m = __ballot_sync(0xFFFFFFFFu, root);
-    if (m) {
-      uint32_t at = 0;
-      if (lane == 0) at = atomicAdd(n_roots, (uint32_t)__popc(m));
-      at = __shfl_sync(0xFFFFFFFFu, at, 0) + __popc(m & ((1u << lane) - 1u));
-      if (root && at < roots_cap) roots[at] = sLab[id];
-    }
-  }
-}
-
-// Every listed root (a tile's root after its own unions) points at the root
-// of its final set: after k_run_union nothing links any more, so the finds
-// only shorten paths, and k_run_outside's finds take at most three loads.
-__global__ void k_root_flatten(const uint32_t* __restrict__ roots, const uint32_t* __restrict__ n_roots,
-                               uint32_t roots_cap, uint32_t* parent, uint32_t limit, int* err) {
-  const uint32_t n = min(*n_roots, roots_cap);
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const uint32_t L = roots[i];
-    __stcg(parent + L, uf_find(parent, L, limit, err));
+  for (uint32_t id = 1 + tid; id <= n_runs; id += kTileThreads) {
+    const uint32_t r = tile_find(sPar, id, limit, err);
+    parent[sLab[id]] = r ? sLab[r] : 0u;
   }
 }
 
 // outside word: the free bits of runs whose root is the frame.  One warp per row.
-__global__ void k_run_outside(const uint32_t* __restrict__ Vb, BitGrid g, uint32_t* parent,
+__global__ void k_run_outside(const uint32_t* __restrict__ Vb, BitGrid g, const uint32_t* __restrict__ parent,
                               uint32_t* __restrict__ Ob, int* err) {
   const int lane = threadIdx.x & 31;
   const int64_t n_warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -785,13 +804,13 @@ __global__ void k_run_outside(const uint32_t* __restrict__ Vb, BitGrid g, uint32
       // the run entering from the previous word holds the free bits below the first start
       if ((c.F & 1u) && !(c.st & 1u)) {
         const uint32_t below = c.st ? ((1u << (__ffs(c.st) - 1)) - 1u) : 0xFFFFFFFFu;
-        if (uf_find(parent, (uint32_t)(row * g.nx + c.before + 1), limit, err) == 0u) out |= c.F & below;
+        if (uf_root_ro(parent, (uint32_t)(row * g.nx + c.before + 1), limit, err) == 0u) out |= c.F & below;
       }
       for (uint32_t m = c.st; m; m &= m - 1) {
         const int s = __ffs(m) - 1;
         const uint32_t rest = m & (m - 1);
         const uint32_t upto = rest ? ((1u << (__ffs(rest) - 1)) - 1u) : 0xFFFFFFFFu;
-        if (uf_find(parent, (uint32_t)(row * g.nx + xw * 32 + s + 1), limit, err) == 0u)
+        if (uf_root_ro(parent, (uint32_t)(row * g.nx + xw * 32 + s + 1), limit, err) == 0u)
           out |= c.F & upto & ~((1u << s) - 1u);
       }
       Ob[row * g.mw + xw] = out;
@@ -887,10 +906,20 @@ constexpr int kPhiPlanes = 8;  // counts up to L + 1 <= 255
 __global__ void k_phi(const uint32_t* __restrict__ Ob, const uint32_t* __restrict__ planes, int L,
                       BitGrid g, float h, float r, float off, float* __restrict__ phi,
                       uint8_t* __restrict__ out_outside, uint8_t* __restrict__ out_shell) {
+  __shared__ float s_delta[256];  // distance by the count of masks holding the voxel
+  __shared__ uint8_t s_p[256];     // shell index by that count
   const int lane = threadIdx.x & 31;
   const uint32_t nw = (uint32_t)g.words();  // < 2^31
   const int n_planes = 32 - __clz(L + 1);
   const uint32_t n_warps = gridDim.x * (blockDim.x >> 5);
+  for (int held = threadIdx.x; held < 256; held += blockDim.x) {
+    const int p = held ? max(L + 1 - held, 0) : 255;
+    // (p + off) is exact in float32, so its product with h rounds once,
+    // like the product of the exact values
+    s_delta[held] = p == 255 ? r : fminf(((float)p + off) * h, r);
+    s_p[held] = (uint8_t)p;
+  }
+  __syncthreads();
   for (uint32_t w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5 << 5; w0 < nw; w0 += n_warps * 32) {
     const uint32_t w = w0 + lane;
     uint32_t ob = 0, c[kPhiPlanes];
@@ -916,13 +945,10 @@ __global__ void k_phi(const uint32_t* __restrict__ Ob, const uint32_t* __restric
       }
       const bool out = (__shfl_sync(0xFFFFFFFFu, ob, jw) >> lane) & 1u;
       if (x >= g.nx) continue;
-      const int p = held ? L + 1 - held : 255;
-      // (p + off) is exact in float32, so its product with h rounds once,
-      // like the product of the exact values
-      const float delta = p == 255 ? r : fminf(((float)p + off) * h, r);
+      const float delta = s_delta[held];
       phi[v] = out ? delta : -delta;
       if (out_outside) out_outside[v] = out ? 1 : 0;
-      if (out_shell) out_shell[v] = (uint8_t)p;
+      if (out_shell) out_shell[v] = s_p[held];
     }
   }
 }
@@ -1245,36 +1271,29 @@ __device__ void emit_vertex(const EmitArgs& a, int x, int j, int k, int t, int64
   }
 }
 
-// first vertex id of sample (x, j, k) and the set of its edge types (bit t)
-__device__ __forceinline__ void owner_info(const EmitArgs& a, int x, int j, int k, uint32_t* first,
-                                           uint32_t* types) {
-  const int64_t nw = a.m.words();
-  const int64_t w = ((int64_t)k * a.m.ny + j) * a.m.mw + (x >> 5);
-  const int b = x & 31;
-  const uint32_t below = (1u << b) - 1u;
-  uint32_t f = (uint32_t)mt_base(a.pre, 0, a.loc_v[w], w), ty = 0;
-#pragma unroll
-  for (int t = 1; t <= 7; ++t) {
-    const uint32_t xw = __ldg(a.X + (t - 1) * nw + w);
-    f += __popc(xw & below);
-    ty |= ((xw >> b) & 1u) << t;
-  }
-  *first = f;
-  *types = ty;
-}
-
 __device__ __forceinline__ int3 corner_xyz(int c) { return make_int3(c & 1, (c >> 1) & 1, (c >> 2) & 1); }
 
-// one triangle on the edges (p0, q0), (p1, q1), (p2, q2) of a tetrahedron
-// with the given corner set and inside flags; oriented towards the outside
-__device__ __forceinline__ void emit_tri(const EmitArgs& a, const int tet[4], const bool in[4],
-                                         const int e[3][2], const uint32_t first[8],
-                                         const uint32_t types[8], int64_t id) {
-  // doubled edge midpoints (integers) and the inside-to-outside direction
-  int3 mp[3];
+// Triangle table: for tetrahedron T (corners 0, kTetMid[T][0], kTetMid[T][1],
+// 7 at positions 0..3) and the inside pattern of those corners (bit q =
+// position q inside), its triangles, each as the three tetrahedron edges its
+// vertices lie on, in output order.  Edge numbers: 0 (0,1) 1 (0,2) 2 (0,3)
+// 3 (1,2) 4 (1,3) 5 (2,3) in positions.  Entry: bits 0-1 the count, triangle
+// m at bits 2 + 9 m, its vertex v at 3 v within.
+//   one corner on its side: one triangle on the three edges from that
+//     corner, the others in position order;
+//   two inside: two triangles (i0,o0)(i0,o1)(i1,o1) and (i0,o0)(i1,o1)(i1,o0);
+//   each oriented so its normal points from the inside corners to the outside
+//   ones (integer cross product of the doubled edge midpoints).
+__device__ __forceinline__ int tet_edge(int qa, int qb) {
+  const int lo = min(qa, qb), hi = max(qa, qb);
+  return lo == 0 ? hi - 1 : lo + hi;  // (0,1) 0 (0,2) 1 (0,3) 2 (1,2) 3 (1,3) 4 (2,3) 5
+}
+
+__device__ uint32_t tet_triangle(const int tet[4], const bool in[4], const int e[3][2]) {
+  int3 mp[3];  // doubled edge midpoints
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
-    const int3 u = corner_xyz(e[q][0]), v = corner_xyz(e[q][1]);
+    const int3 u = corner_xyz(tet[e[q][0]]), v = corner_xyz(tet[e[q][1]]);
     mp[q] = make_int3(u.x + v.x, u.y + v.y, u.z + v.z);
   }
   int nin = 0;
@@ -1295,17 +1314,40 @@ __device__ __forceinline__ void emit_tri(const EmitArgs& a, const int tet[4], co
   const int3 V = make_int3(mp[2].x - mp[0].x, mp[2].y - mp[0].y, mp[2].z - mp[0].z);
   const int3 N = make_int3(U.y * V.z - U.z * V.y, U.z * V.x - U.x * V.z, U.x * V.y - U.y * V.x);
   const bool flip = N.x * G.x + N.y * G.y + N.z * G.z < 0;
-  if (id >= a.n_tris) return;
-  int32_t ids[3];
+  const int order[3] = {0, flip ? 2 : 1, flip ? 1 : 2};
+  uint32_t code = 0;
 #pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    const int lo = min(e[q][0], e[q][1]), hi = max(e[q][0], e[q][1]);
-    const int t = hi ^ lo;
-    ids[q] = (int32_t)(first[lo] + __popc(types[lo] & ((1u << t) - 1u)));
+  for (int v = 0; v < 3; ++v) code |= (uint32_t)tet_edge(e[order[v]][0], e[order[v]][1]) << (3 * v);
+  return code;
+}
+
+__device__ uint32_t tet_entry(int T, int pat) {
+  const int tet[4] = {0, kTetMid[T][0], kTetMid[T][1], 7};
+  bool in[4];
+  int nin = 0;
+  for (int q = 0; q < 4; ++q) {
+    in[q] = (pat >> q) & 1;
+    nin += in[q];
   }
-  a.tris[id * 3 + 0] = ids[0];
-  a.tris[id * 3 + 1] = flip ? ids[2] : ids[1];
-  a.tris[id * 3 + 2] = flip ? ids[1] : ids[2];
+  if (nin == 0 || nin == 4) return 0;
+  if (nin & 1) {
+    const bool lone_in = nin == 1;
+    int lone = 0, o[3], no = 0;
+    for (int q = 0; q < 4; ++q) {
+      if (in[q] == lone_in) lone = q;
+      else o[no++] = q;
+    }
+    const int e[3][2] = {{lone, o[0]}, {lone, o[1]}, {lone, o[2]}};
+    return 1u | tet_triangle(tet, in, e) << 2;
+  }
+  int ins[2], outs[2], ni = 0, nu = 0;
+  for (int q = 0; q < 4; ++q) {
+    if (in[q]) ins[ni++] = q;
+    else outs[nu++] = q;
+  }
+  const int e1[3][2] = {{ins[0], outs[0]}, {ins[0], outs[1]}, {ins[1], outs[1]}};
+  const int e2[3][2] = {{ins[0], outs[0]}, {ins[1], outs[1]}, {ins[1], outs[0]}};
+  return 2u | tet_triangle(tet, in, e1) << 2 | tet_triangle(tet, in, e2) << 11;
 }
 
 // word id -> (j, k, xw) of the sample grid
@@ -1339,8 +1381,23 @@ __global__ void k_mt_verts(EmitArgs a, const uint32_t* __restrict__ samples, uin
 }
 
 // one thread per cube with a triangle: its triangles by tetrahedron, from
-// the word's triangle offset plus the bit-sliced count of the lower cubes
-__global__ void k_mt_tris(EmitArgs a, const uint32_t* __restrict__ cubes_in, uint32_t n_cubes) {
+// the word's triangle offset plus the bit-sliced count of the lower cubes.
+// Corner c = dx + 2 dy + 4 dz owns the edges of types t from its sample; its
+// first vertex is the word's vertex offset plus the crossings of the lower
+// samples of the word.  Corners 0..6 sit in four words (one a (dy, dz)
+// row; the dx = 1 corner in the next word when x is its word's last bit).
+// Each thread keeps its corners' (first vertex, edge types) in its own
+// column of shared memory, so a vertex can name its corner at run time.
+constexpr int kMtTriThreads = 256;
+
+__global__ void __launch_bounds__(kMtTriThreads) k_mt_tris(EmitArgs a, const uint32_t* __restrict__ cubes_in,
+                                                           uint32_t n_cubes) {
+  __shared__ uint32_t s_tet[6 * 16];
+  __shared__ uint32_t s_first[7][kMtTriThreads], s_types[7][kMtTriThreads];
+  for (int i = threadIdx.x; i < 6 * 16; i += blockDim.x) s_tet[i] = tet_entry(i >> 4, i & 15);
+  __syncthreads();
+  const int tx = threadIdx.x;
+  const int64_t nw = a.m.words();
   for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n_cubes; q += gridDim.x * blockDim.x) {
     const uint32_t id = cubes_in[q], w = id >> 5;
     const int b = (int)(id & 31u);
@@ -1350,43 +1407,52 @@ __global__ void k_mt_tris(EmitArgs a, const uint32_t* __restrict__ cubes_in, uin
     corner_words(a.I, a.m, j, k, xw, C);
     const uint32_t below = (1u << b) - 1u;
     int64_t tid = (int64_t)mt_base(a.pre, 1, a.loc_t[w], w) + tri_count(C, cube_bits(a.m, j, k, xw) & below);
-    const int x = xw * 32 + b;
-    uint32_t first[8], types[8];  // corner 7 owns no edge of its cube
-#pragma unroll 1
-    for (int c = 0; c < 7; ++c)
-      owner_info(a, x + (c & 1), j + ((c >> 1) & 1), k + ((c >> 2) & 1), &first[c], &types[c]);
+    uint32_t cb = 0;  // bit c: corner c inside
+#pragma unroll
+    for (int c = 0; c < 8; ++c) cb |= ((C[c] >> b) & 1u) << c;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {  // rows (dy, dz) = (r & 1, r >> 1)
+      const int c0 = 2 * (r & 1) + 4 * (r >> 1);
+      const int64_t wr = ((int64_t)(k + (r >> 1)) * a.m.ny + (j + (r & 1))) * a.m.mw + xw;
+      uint32_t f = (uint32_t)mt_base(a.pre, 0, a.loc_v[wr], wr), ty = 0, ty1 = 0;
+#pragma unroll
+      for (int t = 1; t <= 7; ++t) {
+        const uint32_t xt = __ldg(a.X + (t - 1) * nw + wr);
+        f += __popc(xt & below);
+        ty |= ((xt >> b) & 1u) << t;
+        if (b < 31) ty1 |= ((xt >> (b + 1)) & 1u) << t;
+      }
+      s_first[c0][tx] = f;
+      s_types[c0][tx] = ty;
+      if (c0 + 1 < 7) {  // the dx = 1 corner
+        uint32_t f1 = f + __popc(ty);
+        if (b == 31) {
+          f1 = (uint32_t)mt_base(a.pre, 0, a.loc_v[wr + 1], wr + 1);
+#pragma unroll
+          for (int t = 1; t <= 7; ++t) ty1 |= (__ldg(a.X + (t - 1) * nw + wr + 1) & 1u) << t;
+        }
+        s_first[c0 + 1][tx] = f1;
+        s_types[c0 + 1][tx] = ty1;
+      }
+    }
 #pragma unroll 1
     for (int T = 0; T < 6; ++T) {
-      const int tet[4] = {0, kTetMid[T][0], kTetMid[T][1], 7};
-      bool in[4];
-      int nin = 0;
+      const int m0 = kTetMid[T][0], m1 = kTetMid[T][1];
+      const uint32_t pat = (cb & 1u) | ((cb >> m0) & 1u) << 1 | ((cb >> m1) & 1u) << 2 | ((cb >> 7) & 1u) << 3;
+      const uint32_t ent = s_tet[T * 16 + pat];
+      for (uint32_t m = 0; m < (ent & 3u); ++m, ++tid) {
+        const uint32_t code = ent >> (2 + 9 * m);
+        if (tid >= a.n_tris) continue;
 #pragma unroll
-      for (int q4 = 0; q4 < 4; ++q4) {
-        in[q4] = (C[tet[q4]] >> b) & 1u;
-        nin += in[q4];
-      }
-      if (nin == 0 || nin == 4) continue;
-      if (nin & 1) {
-        const bool lone_in = nin == 1;
-        int lone = 0, o[3], no = 0;
-#pragma unroll
-        for (int q4 = 0; q4 < 4; ++q4) {
-          if (in[q4] == lone_in) lone = q4;
-          else o[no++] = q4;
+        for (int v = 0; v < 3; ++v) {
+          // edge e joins positions (qa, qb), qa < qb; position q is corner 0, m0, m1 or 7
+          const int e = (int)((code >> (3 * v)) & 7u);
+          const int qa = e < 3 ? 0 : (e < 5 ? 1 : 2), qb = e < 3 ? e + 1 : (e < 5 ? e - 1 : 3);
+          const int lo = qa == 0 ? 0 : (qa == 1 ? m0 : m1);
+          const int hi = qb == 1 ? m0 : (qb == 2 ? m1 : 7);
+          const int t = hi ^ lo;
+          a.tris[tid * 3 + v] = (int32_t)(s_first[lo][tx] + __popc(s_types[lo][tx] & ((1u << t) - 1u)));
         }
-        const int e[3][2] = {{tet[lone], tet[o[0]]}, {tet[lone], tet[o[1]]}, {tet[lone], tet[o[2]]}};
-        emit_tri(a, tet, in, e, first, types, tid++);
-      } else {
-        int ins[2], outs[2], ni = 0, nu = 0;
-#pragma unroll
-        for (int q4 = 0; q4 < 4; ++q4) {
-          if (in[q4]) ins[ni++] = tet[q4];
-          else outs[nu++] = tet[q4];
-        }
-        const int e1[3][2] = {{ins[0], outs[0]}, {ins[0], outs[1]}, {ins[1], outs[1]}};
-        const int e2[3][2] = {{ins[0], outs[0]}, {ins[1], outs[1]}, {ins[1], outs[0]}};
-        emit_tri(a, tet, in, e1, first, types, tid++);
-        emit_tri(a, tet, in, e2, first, types, tid++);
       }
     }
   }
@@ -1401,7 +1467,7 @@ struct Buf {
 };
 
 struct Scratch {
-  Buf bits_a, bits_b, shells, parent, tiles, roots, x_words, cnt_v, cnt_t, cnt_a, lists, scan_tmp, blur_a, blur_b, sel;
+  Buf bits_a, bits_b, shells, parent, tiles, x_words, cnt_v, cnt_t, cnt_a, lists, scan_tmp, blur_a, blur_b, sel;
   int* err = nullptr;        // device: union-find limit reached (bits 0/1 global find/unite, 2/3 in a tile)
   unsigned long long* host = nullptr;  // pinned: [2] the TSDF error flag, [4..6] the mesh totals read back
   cudaEvent_t err_ready = nullptr;     // recorded after the flag's copy to host[2]
@@ -1624,12 +1690,7 @@ extern "C" fgl_status fgl_tsdf(const uint8_t* surf, const fgl_grid* grid, float 
   MCUDA(ensure(S.shells, sizeof(uint32_t) * nw * (2 + n_planes), s));
   MCUDA(ensure(S.parent, sizeof(uint32_t) * (n + 1), s));
   const TilePlan tp = plan_tiles(g);
-  // root list: at most one entry a run, (nx + 1) / 2 runs a row
-  const uint32_t roots_cap = (uint32_t)std::min<int64_t>((g.rows() * (g.nx + 1)) / 2 + 1, 0xFFFFFFFFll);
-  if (tp.ty) {
-    MCUDA(ensure(S.tiles, (size_t)tp.n_tiles + 16, s));
-    MCUDA(ensure(S.roots, sizeof(uint32_t) * roots_cap, s));
-  }
+  if (tp.ty) MCUDA(ensure(S.tiles, (size_t)tp.n_tiles, s));
   uint32_t* Vb = (uint32_t*)S.bits_a.p;
   uint32_t* Ob = (uint32_t*)S.bits_b.p;
   uint32_t* D = (uint32_t*)S.shells.p;
@@ -1646,16 +1707,10 @@ extern "C" fgl_status fgl_tsdf(const uint8_t* surf, const fgl_grid* grid, float 
   const unsigned rb = word_blocks(g.rows() * 32, 256);
   if (tp.ty) {  // tiles pack the surface themselves
     uint8_t* tile_global = (uint8_t*)S.tiles.p;
-    // the root counter: the word after the tile flags
-    uint32_t* n_roots = (uint32_t*)(tile_global + ((tp.n_tiles + 3) & ~(int64_t)3));
-    MCUDA(cudaMemsetAsync(n_roots, 0, sizeof(uint32_t), s));
     k_run_tiles<<<(unsigned)tp.n_tiles, kTileThreads, tp.smem, s>>>(surf, g, tp.ty, tp.tz, tp.cap, Vb, parent,
-                                                                  tile_global, (uint32_t*)S.roots.p, n_roots,
-                                                                  roots_cap, S.err);
+                                                                  tile_global, S.err);
     k_run_union<<<rb, 256, 0, s>>>(Vb, g, parent, S.err, tp.ty, tp.tz, tile_global);
-    k_root_flatten<<<152 * 4, 256, 0, s>>>((const uint32_t*)S.roots.p, n_roots, roots_cap, parent,
-                                           (uint32_t)(g.rows() * g.nx + 2), S.err);
-    launches += 3;
+    launches += 2;
   } else {
     k_pack_u8<<<word_blocks(g.rows() * 32, 256), 256, 0, s>>>(surf, g, Vb);
     k_run_init<<<rb, 256, 0, s>>>(Vb, g, parent);
