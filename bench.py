@@ -383,6 +383,15 @@ def make_trace(rng, rate: float, window_s: float, max_env: int, pose_pool, n_sce
     return out
 
 
+def scale_to_load(trace, window_s: float, n_rays_of, rays_per_s: float):
+    """The trace (arrival, scene, sensor, poses, ...) with its arrival times
+    stretched so that it offers rays_per_s over its stretched window:
+    (scaled trace, new window in s)."""
+    offered = sum(e[3].shape[0] * n_rays_of[e[2]] for e in trace) / window_s
+    f = offered / rays_per_s
+    return [(e[0] * f,) + tuple(e[1:]) for e in trace], window_s * f
+
+
 class SlotPlan:
     """Device-resident pose state for a trace: each scene owns a ring of
     `per_scene` server environment slots, and each request takes the next
@@ -1662,10 +1671,9 @@ def run_serve(args):
     # sustained rate (request sizes are heavy-tailed: the rate above, set
     # from the saturation trace's mean size, offers more or less than that)
     raw = make_trace(rng, rate, 8.0, 4096, pool, len(meshes), pick)
-    offered = sum(P.shape[0] * n_rays_of[se] for (_, _, se, P) in raw) / 8.0
-    stretch = offered / (0.7 * sat["rays_per_s"])
-    cal_trace = slot_trace([(ta * stretch, sc, se, P) for (ta, sc, se, P) in raw], plan)
-    rate = len(raw) / (8.0 * stretch)
+    raw, window = scale_to_load(raw, 8.0, n_rays_of, 0.7 * sat["rays_per_s"])
+    cal_trace = slot_trace(raw, plan)
+    rate = len(raw) / window
     with ClockSampler(local) as clk:
         cal = replay_runs(srv, cal_trace, sids, tids, n_rays_of, arena, 30.0, runs=3)
     clocks = clk.summary()

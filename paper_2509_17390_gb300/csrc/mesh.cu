@@ -669,8 +669,9 @@ __global__ void __launch_bounds__(kTileThreads) k_run_tiles(const uint8_t* __res
   const int lane = tid & 31, wid = tid >> 5;
   if (blockIdx.x == 0 && tid == 0) parent[0] = 0;
   if (tid == 0) *sCarry = 0;
-  // the tile's rows packed from the surface bytes (a warp a row, a ballot a
-  // word): the bit grid the later kernels read, and the free bits here
+  // the tile's rows packed from the surface bytes (a warp two rows at a
+  // time, a ballot a word): the bit grid the later kernels read, and the
+  // free bits here
   for (int lr0 = wid; lr0 < rows_t; lr0 += kTileThreads / 16) {  // two rows a pass: more loads in flight
     const int lr1 = lr0 + kTileThreads / 32;
     const int ja = j0 + lr0 % ty, ka = k0 + lr0 / ty, jb = j0 + lr1 % ty, kb = k0 + lr1 / ty;

@@ -2,7 +2,7 @@
 keeps only the samples taken inside the timed region (nvidia-smi's own
 timestamps), reports the median SM clock, the maximum and every throttle
 reason seen there, and falls back to all samples, flagged, when none fell
-inside."""
+inside; the serve workload's trace is scaled to its offered load."""
 
 import datetime
 import os
@@ -10,6 +10,8 @@ import sys
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
+
+import pytest  # noqa: E402
 
 import bench  # noqa: E402
 
@@ -88,3 +90,20 @@ def test_slot_plan_rings_and_sources():
     trace = [(0.1, 0, 0, np.zeros((3, 3, 4), np.float32)), (0.2, 1, 0, np.zeros((2, 3, 4), np.float32))]
     st = bench.slot_trace(trace, bench.SlotPlan(_FakeServer(), src, 8, seed=2))
     assert [e[3] for e in st] == [None, None] and [e[4][1].shape[0] for e in st] == [3, 2]
+
+
+def test_serve_trace_scaled_to_the_offered_load():
+    """The serve workload's trace keeps its requests and order; its arrival
+    times stretch so that the rays it offers over the stretched window equal
+    the target (here a request of 3 environments on a 1,000-ray sensor and
+    one of 5 on a 10-ray sensor: 3,050 rays over 2 s offered as 500 rays/s
+    need a 6.1 s window)."""
+    import numpy as np
+    P3, P5 = np.zeros((3, 3, 4), np.float32), np.zeros((5, 3, 4), np.float32)
+    trace = [(0.5, 0, 0, P3), (1.5, 1, 1, P5)]
+    out, window = bench.scale_to_load(trace, 2.0, [1000, 10], 500.0)
+    assert window == pytest.approx(6.1)
+    assert [e[0] for e in out] == pytest.approx([0.5 * 3.05, 1.5 * 3.05])
+    assert [e[1:3] for e in out] == [(0, 0), (1, 1)] and out[0][3] is P3
+    offered = sum(e[3].shape[0] * [1000, 10][e[2]] for e in out) / window
+    assert offered == pytest.approx(500.0)
