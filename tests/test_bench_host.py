@@ -107,3 +107,16 @@ def test_serve_trace_scaled_to_the_offered_load():
     assert [e[1:3] for e in out] == [(0, 0), (1, 1)] and out[0][3] is P3
     offered = sum(e[3].shape[0] * [1000, 10][e[2]] for e in out) / window
     assert offered == pytest.approx(500.0)
+
+
+def test_mesh_group_roofline_on_the_largest_set():
+    """The mesh line's largest-set figure takes the set with the most voxels
+    and divides its algorithmic bytes by its three Sec. IV-B stages only."""
+    voxels = [1000, 8000, 27]
+    caps = [(10, 20), (100, 200), (1, 1)]
+    stages = [[9.0, 1.0, 1.0, 1.0], [50.0, 0.5, 1.0, 0.5], [1.0, 1.0, 1.0, 1.0]]
+    r = bench.mesh_group_roofline(voxels, caps, stages, peak_gbs=1.0)
+    nbytes = 11 * 8000 + 12 * 300
+    assert r["voxels"] == 8000 and r["bytes"] == nbytes and r["ms"] == pytest.approx(2.0)
+    assert r["achieved"] == pytest.approx(nbytes / 2e-3 / 1e9, abs=0.05)
+    assert r["frac"] == pytest.approx(nbytes / 2e-3 / 1e9, rel=1e-3)
