@@ -1829,7 +1829,7 @@ extern "C" fgl_status fgl_marching_tets(const float* phi, const fgl_grid* grid, 
   uint32_t* cubes = samples + n_samples;
   k_mt_list<<<word_blocks(nw, 256), 256, 0, s>>>(I, m, X, pre, la, samples, cubes);
   if (n_samples) k_mt_verts<<<word_blocks(n_samples, 256), 256, 0, s>>>(a, samples, n_samples);
-  if (n_cubes) k_mt_tris<<<word_blocks(n_cubes, 256), 256, 0, s>>>(a, cubes, n_cubes);
+  if (n_cubes) k_mt_tris<<<word_blocks(n_cubes, kMtTriThreads), kMtTriThreads, 0, s>>>(a, cubes, n_cubes);
   MCUDA(cudaGetLastError());
   return FGL_OK;
 }
